@@ -345,6 +345,11 @@ def _row_constraint_update(w: np.ndarray, Bc_J: np.ndarray, target: np.ndarray) 
     return w - (resid @ np.linalg.pinv(G)) @ Bc_J.T
 
 
+def _row_least_squares(Bc_J: np.ndarray, target: np.ndarray) -> np.ndarray:
+    """Least-squares (minimum-norm) solution of the row system ``w @ Bc_J = target``."""
+    return (target @ np.linalg.pinv(Bc_J.T @ Bc_J)) @ Bc_J.T
+
+
 def clair_algorithm1(Ahat, cf: np.ndarray, B: np.ndarray, Wpat: sp.csc_matrix,
                      params: Params) -> sp.csc_matrix:
     """Algorithm 1 of the paper on operator ``Ahat``: returns the F-rows ``W`` (n x n_c,
@@ -352,7 +357,8 @@ def clair_algorithm1(Ahat, cf: np.ndarray, B: np.ndarray, Wpat: sp.csc_matrix,
 
     Steps, in the paper's order:
       * tentative ``w_t`` from ``[-A_fc, I]`` on the pattern;
-      * enforce ``Q w_t = B|_F`` row by row (minimal-norm least squares, ``w B_c = B``);
+      * enforce ``Q w_t = B|_F`` row by row: each F row of ``w_t`` becomes the least-squares
+        (minimum-norm) solution of ``w B_c = B`` on its pattern;
       * block inverses of ``A_ff^{(i)}`` (``A_ff`` restricted to ``W_i`` in rows and
         columns), exact or diagonal;
       * k times: ``wbar = Ahat_ff^-1 (-a_fc - A_ff w_t)`` per column block, project
@@ -403,9 +409,11 @@ def clair_algorithm1(Ahat, cf: np.ndarray, B: np.ndarray, Wpat: sp.csc_matrix,
             w[i][pos_in_col[(int(j), int(i))]] = v
 
     if params.constrain:
+        # "least squares solution to w B_c = B" per F row: the minimum-norm solution (the
+        # pattern of [-A_fc, I] fixes where w_t may be nonzero; its values are replaced)
         for j in rows_nz:
-            J, wj = gather_row(w_t, j)
-            scatter_row(w_t, j, J, _row_constraint_update(wj, Bc[J], B[j]))
+            J, _ = gather_row(w_t, j)
+            scatter_row(w_t, j, J, _row_least_squares(Bc[J], B[j]))
 
     blocks = [block(cols_of[i], cols_of[i]) for i in range(nc)]
     rhs = [-block(cols_of[i], [cpts[i]])[:, 0] for i in range(nc)]
