@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the CLAIR AMG hot path on one GB300 (or N independent replicas).
+
+One step = the whole hot path on the 1024x1024 2D upwind advection-diffusion workload
+(velocity angle pi/6, eps = 1e-2, pattern degree m = 2, B = 1): CLAIR setup (strength,
+splitting, weight, mode smoothing, patterns, batched local solves, constraint projection,
+Galerkin products over all levels) and the V(1,1)-preconditioned FGMRES solve to a 1e-8
+relative true residual.  Inputs are resident in HBM before the timed region; the L2 is
+flushed (256 MiB write) before every timed step, outside the step's CUDA events.
+
+value = R rows built per step / seconds per step (MIXED precision: FP32 local solves and
+V-cycle, FP64 FGMRES); the FP64 path is timed beside it ("fp64").  `e2e` repeats the step
+from pinned host buffers with the host->device copies of A, B, f and the device->host copy
+of u inside the timed region.  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "R rows/s in setup; time-to-1e-8 rel residual, mixed vs FP64 path, 1 GB300"
+UNIT = "R rows/s"
+PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["clair", "reference"], default="clair")
+    ap.add_argument("--nside", type=int, default=1024)
+    ap.add_argument("--eps", type=float, default=1e-2)
+    ap.add_argument("--degree", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-nside", type=int, default=128)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return dict(PEAK_FALLBACK), "fallback"
+
+
+def workload(args):
+    import workloads
+    return workloads.config2(eps=args.eps, degree=args.degree, nside=args.nside)
+
+
+# ----------------------------------------------------------------------------------------
+# Clocks during the timed region
+# ----------------------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_index)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------------------
+# Algorithmic traffic of one V(1,1) cycle (MIXED: 4-byte values and vectors)
+# ----------------------------------------------------------------------------------------
+def vcycle_bytes(levels, s=4):
+    """Bytes one V(1,1) cycle must move, level by level: each Jacobi sweep reads the rows
+    of its subset (s+4 bytes per entry), the row pointers, cf, dinv, b and the incoming
+    x and writes x; residual, restriction and interpolation are SpMVs; the coarsest
+    level is a dense n^2 product."""
+    total = 0.0
+    for L in levels:
+        n, nnz = L["n"], L["nnz"]
+        if L["nc"] == 0:
+            total += s * n * n + 2 * s * n
+            continue
+        nc, nnzR, nnzP, nnzF, nF = L["nc"], L["nnz_R"], L["nnz_P"], L["nnz_F"], L["n"] - L["nc"]
+        nnzC = nnz - nnzF
+        sweep = lambda nnzX, nX: (s + 4) * nnzX + 4 * (n + 1) + n + 2 * s * nX + 2 * s * n
+        total += (2 * s + 1) * n + s * n                        # first C sweep from x = 0
+        total += 2 * sweep(nnzF, nF)                           # two F sweeps
+        total += (s + 4) * nnz + 4 * (n + 1) + 3 * s * n       # residual
+        total += (s + 4) * nnzR + 4 * (nc + 1) + s * n + s * nc  # restriction
+        total += (s + 4) * nnzP + 4 * (n + 1) + s * nc + 2 * s * n  # interpolation
+        total += 2 * sweep(nnzF, nF) + sweep(nnzC, nc)         # F, F, C post sweeps
+        total += 2 * s * n                                      # copy
+    return total
+
+
+def level_summary(cl, h):
+    import torch
+    st = cl.clair_stats(h)
+    out = []
+    for k in range(st.levels):
+        v = cl.clair_level_view(h, k)
+        d = {"n": v["n"], "nc": v["nc"], "nnz": int(v["A_col"].numel())}
+        if v["nc"]:
+            cf = v["cf"].to(torch.int32)
+            rl = (v["A_rowptr"][1:] - v["A_rowptr"][:-1])
+            d["nnz_F"] = int(rl[cf == 0].sum().item())
+            d["nnz_R"] = int(v["R_col"].numel())
+            d["nnz_P"] = int(v["P_col"].numel())
+        out.append(d)
+    return out
+
+
+# ----------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------
+def run_clair(args):
+    import numpy as np
+    import torch
+
+    from paper_2307_00229_gb300 import clair as cl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cl.load()
+    prob = workload(args)
+    A = prob.A
+    dev = torch.device("cuda", local)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    rowptr, col, val = t(A.rowptr, torch.int32), t(A.col, torch.int32), t(A.val, torch.float64)
+    B, f = t(prob.B, torch.float64), t(prob.f, torch.float64)
+    u = torch.zeros_like(f)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def params(precision):
+        p = cl.clair_params_default()
+        p.degree = args.degree
+        p.precision = precision
+        return p
+
+    def step(p):
+        h = cl.clair_setup(rowptr, col, val, B, p)
+        u.zero_()
+        st, its, rel = cl.clair_solve(h, f, u, raise_not_converged=False)
+        return h, st, its, rel
+
+    def timed(precision, steps, warmup, e2e=False):
+        p = params(precision)
+        host = None
+        if e2e:
+            host = {k: v.cpu().pin_memory() for k, v in
+                    (("rowptr", rowptr), ("col", col), ("val", val), ("B", B), ("f", f))}
+            u_host = torch.empty(u.shape, dtype=torch.float64).pin_memory()
+        for _ in range(warmup):
+            h, *_ = step(p)
+            cl.clair_free(h)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        times, its_l, rel_l, stats = [], [], [], None
+        launches0 = cl.clair_kernel_launches()
+        wall0 = time.perf_counter()
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if e2e:
+                for name, dst in (("rowptr", rowptr), ("col", col), ("val", val), ("B", B), ("f", f)):
+                    dst.copy_(host[name], non_blocking=True)
+            h, st, its, rel = step(p)
+            if e2e:
+                u_host.copy_(u, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            its_l.append(its)
+            rel_l.append(rel)
+            stats = (cl.clair_stats(h), level_summary(cl, h))
+            cl.clair_free(h)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        launches = cl.clair_kernel_launches() - launches0
+        if dist:
+            dist.barrier()
+        ms = statistics.mean(times)
+        if dist:
+            tt = torch.tensor([ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        bytes_h2d = sum(x.numel() * x.element_size() for x in host.values()) if e2e else 0
+        return {"ms": ms, "times": times, "its": its_l, "rel": rel_l, "stats": stats[0],
+                "levels": stats[1], "wall": wall, "launches": launches // max(steps, 1),
+                "h2d": bytes_h2d, "d2h": u.numel() * 8 if e2e else 0}
+
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[local])
+        except ValueError:
+            pass
+    sampler = ClockSampler(gpu_index)
+    mixed = timed(cl.CLAIR_MIXED, args.steps, args.warmup)
+    clocks = sampler.stop()
+    fp64 = timed(cl.CLAIR_FP64, args.fp64_steps, 1)
+    e2e = timed(cl.CLAIR_MIXED, max(1, min(args.steps, 3)), 1, e2e=True)
+
+    st = mixed["stats"]
+    rows = int(st.r_rows)
+    value = world * rows / (mixed["ms"] / 1e3)
+    pk, pk_kind = peaks()
+    phases = {name: st.phase_ms[i] for i, name in enumerate(cl.PHASES[:8])}
+    phases.update({name: st.solve_phase_ms[i] for i, name in enumerate(cl.PHASES) if i >= 8})
+    its = mixed["its"][-1]
+    # roofline of the dominant phase
+    vb = vcycle_bytes(mixed["levels"])
+    vcycle_ms = phases["vcycle"] / max(its, 1)
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x 2 x max clock
+    lsolve = {"bound": "alu", "achieved": st.lsolve_flops / (phases["local_solve"] * 1e-3) / 1e12,
+              "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,
+              "kernel": "lsolve_group/lsolve_cta (FP32 batched local LU)",
+              "share_of_step": phases["local_solve"] / mixed["ms"]}
+    lsolve["frac"] = lsolve["achieved"] / lsolve["peak"]
+    hbm = pk.get("hbm_gbs", PEAK_FALLBACK["hbm_gbs"])
+    vcyc = {"bound": "hbm", "achieved": vb / (vcycle_ms * 1e-3) / 1e9 if vcycle_ms > 0 else None,
+            "peak": hbm, "unit": "GB/s", "traffic": None, "bytes_per_cycle": vb,
+            "kernel": "V(1,1) cycle kernels (jacobi/spmv, FP32)",
+            "share_of_step": phases["vcycle"] / mixed["ms"]}
+    vcyc["frac"] = vcyc["achieved"] / vcyc["peak"] if vcyc["achieved"] else None
+    dominant, other = (lsolve, vcyc) if lsolve["share_of_step"] >= vcyc["share_of_step"] else (vcyc, lsolve)
+    dominant["peak_source"] = ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+                               if dominant["unit"] == "TFLOP/s" else f"{pk_kind} hbm_gbs")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mixed["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": prob.name, "n": A.n, "nnz": A.nnz, "eps": args.eps,
+                   "velocity_angle": "pi/6", "degree": args.degree, "coarsen": "FC",
+                   "precision": "mixed (FP32 local solves and V-cycle, FP64 FGMRES)",
+                   "parallelism": f"replicas x{world}", "l2": "flushed (256 MiB write) before each step"},
+        "time_to_1e8_ms": mixed["ms"], "iterations": its, "relres": mixed["rel"][-1],
+        "setup_ms": st.setup_ms, "r_rows": rows, "levels": st.levels,
+        "operator_complexity": st.operator_complexity,
+        "setup_rows_per_s": rows / (st.setup_ms / 1e3),
+        "phases_ms": phases,
+        "fp64": {"ms_per_step": fp64["ms"], "iterations": fp64["its"][-1], "relres": fp64["rel"][-1],
+                 "setup_ms": fp64["stats"].setup_ms, "value": world * rows / (fp64["ms"] / 1e3),
+                 "local_solve_ms": fp64["stats"].phase_ms[4]},
+        "mixed_speedup_vs_fp64": fp64["ms"] / mixed["ms"],
+        "e2e": {"value": world * rows / (e2e["ms"] / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                "ms_per_step": e2e["ms"]},
+        "roofline": dominant, "roofline_other": other,
+        "gpu_launches": mixed["launches"],
+        "clocks": clocks,
+        "step_times_ms": mixed["times"], "wall_s": mixed["wall"],
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ----------------------------------------------------------------------------------------
+def oracle_step(nside, eps, degree):
+    import numpy as np
+
+    import oracle as O
+    import workloads
+    prob = workloads.constdir_2d(nside, math.pi / 6, eps, seed=1, degree=degree)
+    p = O.Params(degree=degree)
+    t0 = time.perf_counter()
+    c0 = time.process_time()
+    H, x, its, hist = O.solve(prob.A, prob.f, prob.B, p)
+    dt = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    rows = sum(int(l.cf.sum()) for l in H.levels if l.cf is not None)
+    return rows, dt, cpu, its
+
+
+def cpu_baseline(args):
+    rows, dt, cpu, its = oracle_step(args.cpu_nside, args.eps, args.degree)
+    return {"value": rows / dt, "unit": UNIT, "cores": max(1, round(cpu / dt)), "kind": "oracle",
+            "sample": f"oracle setup + FGMRES solve of the same problem family at {args.cpu_nside}^2 "
+                      f"(eps={args.eps}, angle pi/6, m={args.degree}): {rows} R rows in {dt:.1f} s, "
+                      f"{its} iterations"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    nside = max(32, args.cpu_nside * 3 // 4)
+    for _ in range(args.warmup):
+        oracle_step(nside, args.eps, args.degree)
+    times, rows, cpus = [], 0, []
+    for _ in range(args.steps):
+        rows, dt, cpu, its = oracle_step(nside, args.eps, args.degree)
+        times.append(dt)
+        cpus.append(cpu)
+    ms = 1e3 * statistics.mean(times)
+    value = rows / (ms / 1e3)
+    cores = max(1, round(sum(cpus) / sum(times)))
+    sample = (f"oracle setup + FGMRES solve per step on the same problem family at {nside}^2 "
+              f"(eps={args.eps}, angle pi/6, m={args.degree}), {rows} R rows per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"constdir2d_{nside}_eps{args.eps:g}_m{args.degree}",
+                   "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_clair(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * clair.h - C ABI of the GB300 (sm_103a) library for constrained local approximate
+ * ideal restriction (CLAIR) algebraic multigrid, arXiv 2307.00229.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are square CSR operators: int32 row pointers (n+1) and column indices
+ *   (nnz, sorted ascending and unique within each row), float64 values.  All pointers
+ *   that carry vector or matrix data are DEVICE pointers unless the name ends in _host.
+ * - Inputs are borrowed: the library neither frees them nor keeps them after the call
+ *   returns (a hierarchy copies what it needs).  Outputs are caller-owned buffers of the
+ *   stated size.  A hierarchy (clair_h) owns every device buffer it allocates; free it
+ *   with clair_free.
+ * - `stream` is a cudaStream_t passed as void*; NULL is the legacy default stream.  Calls
+ *   that return host scalars synchronise that stream before returning.
+ * - Every call returns a clair_status and never aborts; clair_last_error() gives a
+ *   one-line description of the last failure on the calling thread.
+ * - Index convention for C/F splittings: cf[i] = 1 for a C-point, 0 for an F-point; the
+ *   coarse index of a C-point is its rank among C-points in increasing fine index.
+ */
+#ifndef CLAIR_H
+#define CLAIR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CLAIR_OK = 0,
+  CLAIR_ERR_ARG = 1,            /* invalid argument (null pointer, size, parameter) */
+  CLAIR_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  CLAIR_ERR_SINGULAR_BLOCK = 3, /* a local block had a zero pivot (its weights are set to 0) */
+  CLAIR_ERR_NONFINITE = 4,      /* NaN or Inf in an input or a result */
+  CLAIR_ERR_NOT_CONVERGED = 5,  /* FGMRES stopped at gmres_maxit above rtol */
+  CLAIR_ERR_CAPACITY = 6,       /* a size exceeded a kernel limit (e.g. local system > 256) */
+  CLAIR_ERR_UNSUPPORTED = 7     /* a parameter combination this build does not implement */
+} clair_status;
+
+enum { CLAIR_COARSEN_FC = 0, CLAIR_COARSEN_AGG = 1 };
+enum { CLAIR_FP64 = 0, CLAIR_MIXED = 1 };
+
+/* Solver parameters.  Defaults (clair_params_default) follow the nonsymmetric runs of
+ * Section 4.2: coarsening strength 0.25, interpolation strength 0.05, pattern degree
+ * m = 2 (Algorithm 1), B = 1 smoothed by 5 CFF sweeps per level (Section 4.1), weight
+ * 1/rho(D^-1 A) from 15 Arnoldi steps (Section 4), post-smoothing weight removed
+ * (Section 4.2), V(1,1) cycles inside right-preconditioned FGMRES. */
+typedef struct {
+  double theta_coarsen;   /* strength threshold for the C/F splitting */
+  double theta_interp;    /* strength threshold for the transfer patterns */
+  int degree;             /* sparsity pattern degree m of Algorithm 1 (1 or 2) */
+  int coarsen;            /* CLAIR_COARSEN_FC or CLAIR_COARSEN_AGG */
+  int b_smooth_iters;     /* CFF sweeps applied to the mode vector on each level */
+  int arnoldi_iters;      /* Arnoldi steps for rho(D^-1 A) */
+  int post_weighted;      /* 1: post-smoothing uses the weight too; 0: weight 1 */
+  int coarse_max;         /* a level with n <= coarse_max is solved directly */
+  int max_levels;         /* hard cap on the number of levels */
+  int precision;          /* CLAIR_FP64 or CLAIR_MIXED (FP32 V-cycle and local solves) */
+  int gmres_restart;      /* FGMRES restart length (<= 64) */
+  int gmres_maxit;        /* FGMRES iteration cap */
+  double rtol;            /* stop when ||f - A u||_2 <= rtol ||f||_2 (true FP64 residual) */
+  uint64_t seed;          /* seed of the Arnoldi start vectors (splitmix64, seed + level) */
+} clair_params;
+
+typedef struct clair_hierarchy* clair_h;
+
+/* Summary of a hierarchy (host struct filled by clair_stats). */
+typedef struct {
+  int levels;                 /* number of levels including the coarsest */
+  int64_t n[32];              /* unknowns per level */
+  int64_t nnz[32];            /* nnz(A_k) per level */
+  int64_t nnz_R[32];          /* nnz(R_k) including the identity entries */
+  int64_t nnz_P[32];          /* nnz(P_k) including the identity entries */
+  double omega[32];           /* relaxation weight per level */
+  double operator_complexity; /* sum_k nnz(A_k) / nnz(A_0) (Section 4) */
+  int64_t r_rows;             /* local systems solved for R over all levels */
+  int64_t p_cols;             /* local systems solved for P over all levels */
+  int64_t t_hist[9];          /* local system sizes T: <=8,16,32,64,128,256 (R and P) */
+  int64_t singular_blocks;    /* local blocks with a zero pivot */
+  int64_t empty_constraints;  /* F-points skipped by the projection (no C-point or B_c = 0) */
+  double setup_ms;            /* device time of the last clair_setup */
+  /* Device time per phase (CUDA events on the launching stream).  Index: 0 transpose,
+   * strength and splitting; 1 Arnoldi weight; 2 mode smoothing; 3 patterns; 4 local
+   * gathers and solves; 5 constraint projection; 6 Galerkin product; 7 coarsest inverse;
+   * 8 V-cycles; 9 FGMRES orthogonalisation and residuals. */
+  double phase_ms[10];        /* of the setup (entries 0-7) */
+  double solve_phase_ms[10];  /* of the last clair_solve (entries 8-9) */
+  double lsolve_flops;        /* sum over local systems of (2/3) T^3 + 2 T^2 */
+  double lsolve_min_bytes;    /* 12 nnz(A_k) per side (A read once) + 12 nnz(R_k) + 12 nnz(P_k) */
+  int64_t lsolve_gathered;    /* A entries read by the local gathers, repeats included */
+} clair_stats_t;
+
+/* Kernel launches issued by this library in this process so far (monotonic counter). */
+int64_t clair_kernel_launches(void);
+
+/* Fills *p with the defaults listed above. */
+clair_status clair_params_default(clair_params* p);
+
+/* CLAIR setup (hot path, part 1): per level, strength, C/F splitting, relaxation weight,
+ * mode smoothing, pattern, batched local solves and constraint projection for R (on A^T,
+ * Section 3.1.3) and P (on A, Algorithm 1), then A_c = R A P (Section 1), until
+ * n <= coarse_max or max_levels.
+ *   n, nnz, rowptr, col, val : the fine operator A (device CSR, see conventions)
+ *   B                        : device float64 [n], the near-nullspace candidate (k = 1)
+ *   p                        : host parameters (NULL = defaults)
+ *   out                      : receives the new hierarchy; *out = NULL on failure
+ * Synchronises `stream` once per level (coarse sizes are data-dependent). */
+clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col,
+                         const double* val, const double* B, const clair_params* p,
+                         void* stream, clair_h* out);
+
+/* Solve A u = f (hot path, part 2): right-preconditioned FGMRES(gmres_restart) in float64
+ * with one V(1,1) cycle (CFF pre, FFC post, Section 4) per iteration, FP32 cycle in
+ * CLAIR_MIXED mode.  Stops on the true float64 residual (restart = iterative refinement).
+ *   f     : device float64 [n]
+ *   u     : device float64 [n]; input initial guess, output solution
+ *   iters, relres : host outputs (iterations done, final ||f - A u|| / ||f||); may be NULL
+ * Returns CLAIR_ERR_NOT_CONVERGED if gmres_maxit is reached above rtol (u holds the
+ * last iterate).  Synchronises `stream` once per iteration. */
+clair_status clair_solve(clair_h h, const double* f, double* u, void* stream, int* iters,
+                         double* relres);
+
+/* One V(1,1) cycle x = M^-1 b on level `level` (x0 = 0), in the hierarchy's precision.
+ *   b, x : device float64 [n_level]. */
+clair_status clair_vcycle(clair_h h, int level, const double* b, double* x, void* stream);
+
+/* Host summary of the hierarchy. */
+clair_status clair_stats(clair_h h, clair_stats_t* out);
+
+/* Device views of level `level`, valid until clair_free.  Any output pointer may be NULL.
+ * For the coarsest level only n, nnz and the A arrays are set (the others NULL / 0).
+ *   A_*   : CSR of A_k (n x n)
+ *   R_*   : CSR of R_k (nc x n), identity entry stored at each C-point's own column
+ *   P_*   : CSR of P_k (n x nc), identity entry stored in each C-point's row
+ *   cf    : int8 [n] C/F splitting;  B_P, B_R: float64 [n] smoothed mode vectors for
+ *           P (operator A_k) and R (operator A_k^T);  omega: host scalar weight. */
+clair_status clair_level_view(clair_h h, int level, int* n, int* nc, int* nnz_A,
+                              const int** A_rowptr, const int** A_col, const double** A_val,
+                              int* nnz_R, const int** R_rowptr, const int** R_col,
+                              const double** R_val, int* nnz_P, const int** P_rowptr,
+                              const int** P_col, const double** P_val,
+                              const signed char** cf, const double** B_P,
+                              const double** B_R, double* omega);
+
+/* Releases every device buffer of the hierarchy.  NULL is accepted. */
+clair_status clair_free(clair_h h);
+
+/* Batched constrained local solves for given splitting and pattern (hot path steps
+ * local gather, local solve, constraint projection and scatter; Eqs. 2.8 and 3.1,
+ * Algorithm 1 with exact block inverses and k = 1, Remark 3.2, constraint Eq. 3.3).
+ * Computes the weights of P_hat = [W; I] for Algorithm 1 run on the operator Ahat,
+ * stored transposed: row i of the output is coarse point i, i.e. for Ahat = A^T this is
+ * directly the CSR of the restriction R.
+ *   n, Ahat_rowptr/col/val : the operator Algorithm 1 runs on (device CSR)
+ *   cf                     : device int8 [n] splitting
+ *   nc, Z_rowptr, Z_col    : device CSR pattern (nc x n), rows = coarse points, columns
+ *                            sorted, each row containing its own C-point column (identity)
+ *                            and the F-points of its local system (at most 128 of them)
+ *   B                      : device float64 [n] mode vector on the fine points
+ *   precision              : CLAIR_FP64 (float64 local solves) or CLAIR_MIXED (float32)
+ *   Z_val                  : device float64 [nnz] output weights (1 at identity entries)
+ *   singular_out, empty_out: host counts of zero-pivot blocks and skipped F-points (NULL ok)
+ * The projection needs the column view of the pattern; the call allocates it
+ * (stream-ordered) and releases it before returning. */
+clair_status clair_local_weights(int n, const int* Ahat_rowptr, const int* Ahat_col,
+                                 const double* Ahat_val, const signed char* cf, int nc,
+                                 const int* Z_rowptr, const int* Z_col, const double* B,
+                                 int precision, double* Z_val, void* stream,
+                                 int64_t* singular_out, int64_t* empty_out);
+
+/* One-line description of the last error on the calling thread ("" if none). */
+const char* clair_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLAIR_H */

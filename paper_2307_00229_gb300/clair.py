@@ -1,0 +1,249 @@
+"""Thin Python binding of ``libclair.so`` (the C ABI in include/clair.h).
+
+Argument marshalling only: every function has the name of the C entry point it calls,
+takes torch CUDA tensors where the C call takes device pointers, and raises ``ClairError``
+when the call returns a non-zero status.  No computation happens here; when the library
+is missing the import of this module fails loudly (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+_lib = None
+
+CLAIR_OK = 0
+CLAIR_ERR_ARG = 1
+CLAIR_ERR_CUDA = 2
+CLAIR_ERR_SINGULAR_BLOCK = 3
+CLAIR_ERR_NONFINITE = 4
+CLAIR_ERR_NOT_CONVERGED = 5
+CLAIR_ERR_CAPACITY = 6
+CLAIR_ERR_UNSUPPORTED = 7
+CLAIR_COARSEN_FC = 0
+CLAIR_COARSEN_AGG = 1
+CLAIR_FP64 = 0
+CLAIR_MIXED = 1
+
+
+class ClairError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"clair status {status}: {msg}")
+        self.status = status
+
+
+class clair_params(ctypes.Structure):
+    _fields_ = [
+        ("theta_coarsen", ctypes.c_double),
+        ("theta_interp", ctypes.c_double),
+        ("degree", ctypes.c_int),
+        ("coarsen", ctypes.c_int),
+        ("b_smooth_iters", ctypes.c_int),
+        ("arnoldi_iters", ctypes.c_int),
+        ("post_weighted", ctypes.c_int),
+        ("coarse_max", ctypes.c_int),
+        ("max_levels", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("gmres_restart", ctypes.c_int),
+        ("gmres_maxit", ctypes.c_int),
+        ("rtol", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class clair_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int),
+        ("n", ctypes.c_int64 * 32),
+        ("nnz", ctypes.c_int64 * 32),
+        ("nnz_R", ctypes.c_int64 * 32),
+        ("nnz_P", ctypes.c_int64 * 32),
+        ("omega", ctypes.c_double * 32),
+        ("operator_complexity", ctypes.c_double),
+        ("r_rows", ctypes.c_int64),
+        ("p_cols", ctypes.c_int64),
+        ("t_hist", ctypes.c_int64 * 9),
+        ("singular_blocks", ctypes.c_int64),
+        ("empty_constraints", ctypes.c_int64),
+        ("setup_ms", ctypes.c_double),
+        ("phase_ms", ctypes.c_double * 10),
+        ("solve_phase_ms", ctypes.c_double * 10),
+        ("lsolve_flops", ctypes.c_double),
+        ("lsolve_min_bytes", ctypes.c_double),
+        ("lsolve_gathered", ctypes.c_int64),
+    ]
+
+
+PHASES = ["split", "weight", "smooth", "pattern", "local_solve", "projection", "galerkin",
+          "coarse", "vcycle", "krylov"]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_PI = ctypes.POINTER(ctypes.c_int)
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+
+_SIGNATURES = {
+    "clair_params_default": (_I, [ctypes.POINTER(clair_params)]),
+    "clair_setup": (_I, [_I, _I, _P, _P, _P, _P, ctypes.POINTER(clair_params), _P,
+                         ctypes.POINTER(_P)]),
+    "clair_solve": (_I, [_P, _P, _P, _P, _PI, _PD]),
+    "clair_vcycle": (_I, [_P, _I, _P, _P, _P]),
+    "clair_stats": (_I, [_P, ctypes.POINTER(clair_stats_t)]),
+    "clair_level_view": (_I, [_P, _I, _PI, _PI, _PI, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                              ctypes.POINTER(_P), _PI, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                              ctypes.POINTER(_P), _PI, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                              ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                              ctypes.POINTER(_P), _PD]),
+    "clair_free": (_I, [_P]),
+    "clair_local_weights": (_I, [_I, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _PI64, _PI64]),
+    "clair_last_error": (ctypes.c_char_p, []),
+    "clair_kernel_launches": (ctypes.c_int64, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads ``libclair.so`` (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not found at {_build.LIB}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != CLAIR_OK:
+        raise ClairError(status, clair_last_error())
+
+
+def _dptr(t: torch.Tensor, dtype: torch.dtype) -> ctypes.c_void_p:
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == dtype):
+        raise TypeError(f"expected a contiguous CUDA {dtype} tensor, got {t.dtype} on {t.device}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def clair_last_error() -> str:
+    return load().clair_last_error().decode()
+
+
+def clair_kernel_launches() -> int:
+    return int(load().clair_kernel_launches())
+
+
+def clair_params_default() -> clair_params:
+    p = clair_params()
+    _check(load().clair_params_default(ctypes.byref(p)))
+    return p
+
+
+def clair_setup(rowptr, col, val, B, params: clair_params | None = None, stream=None) -> ctypes.c_void_p:
+    n = rowptr.numel() - 1
+    h = ctypes.c_void_p()
+    _check(load().clair_setup(n, col.numel(), _dptr(rowptr, torch.int32), _dptr(col, torch.int32),
+                              _dptr(val, torch.float64), _dptr(B, torch.float64),
+                              ctypes.byref(params) if params is not None else None,
+                              _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def clair_solve(h, f, u, stream=None, raise_not_converged: bool = True):
+    """Returns ``(status, iterations, relative residual)``."""
+    its, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+    st = load().clair_solve(h, _dptr(f, torch.float64), _dptr(u, torch.float64), _stream(stream),
+                            ctypes.byref(its), ctypes.byref(rel))
+    if st != CLAIR_OK and (st != CLAIR_ERR_NOT_CONVERGED or raise_not_converged):
+        _check(st)
+    return st, its.value, rel.value
+
+
+def clair_vcycle(h, level: int, b, x, stream=None):
+    _check(load().clair_vcycle(h, level, _dptr(b, torch.float64), _dptr(x, torch.float64),
+                               _stream(stream)))
+
+
+def clair_stats(h) -> clair_stats_t:
+    s = clair_stats_t()
+    _check(load().clair_stats(h, ctypes.byref(s)))
+    return s
+
+
+class _DeviceArray:
+    """Zero-copy view of library-owned device memory through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, count: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+def _view(ptr: ctypes.c_void_p, count: int, dtype: torch.dtype):
+    if not ptr.value or count <= 0:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    ts = {torch.int32: "<i4", torch.float64: "<f8", torch.int8: "|i1"}[dtype]
+    return torch.as_tensor(_DeviceArray(ptr.value, count, ts), device="cuda")
+
+
+def clair_level_view(h, level: int) -> dict:
+    """Zero-copy torch views of level ``level`` (valid until ``clair_free``)."""
+    n, nc, nnzA, nnzR, nnzP = (ctypes.c_int() for _ in range(5))
+    ptrs = [ctypes.c_void_p() for _ in range(12)]
+    om = ctypes.c_double()
+    _check(load().clair_level_view(
+        h, level, ctypes.byref(n), ctypes.byref(nc), ctypes.byref(nnzA), *(ctypes.byref(p) for p in ptrs[:3]),
+        ctypes.byref(nnzR), *(ctypes.byref(p) for p in ptrs[3:6]), ctypes.byref(nnzP),
+        *(ctypes.byref(p) for p in ptrs[6:9]), *(ctypes.byref(p) for p in ptrs[9:12]), ctypes.byref(om)))
+    N, NC = n.value, nc.value
+    out = {"n": N, "nc": NC, "omega": om.value,
+           "A_rowptr": _view(ptrs[0], N + 1, torch.int32), "A_col": _view(ptrs[1], nnzA.value, torch.int32),
+           "A_val": _view(ptrs[2], nnzA.value, torch.float64)}
+    if NC:
+        out.update({
+            "R_rowptr": _view(ptrs[3], NC + 1, torch.int32), "R_col": _view(ptrs[4], nnzR.value, torch.int32),
+            "R_val": _view(ptrs[5], nnzR.value, torch.float64),
+            "P_rowptr": _view(ptrs[6], N + 1, torch.int32), "P_col": _view(ptrs[7], nnzP.value, torch.int32),
+            "P_val": _view(ptrs[8], nnzP.value, torch.float64),
+            "cf": _view(ptrs[9], N, torch.int8), "B_P": _view(ptrs[10], N, torch.float64),
+            "B_R": _view(ptrs[11], N, torch.float64)})
+    return out
+
+
+def clair_free(h):
+    _check(load().clair_free(h))
+
+
+def clair_local_weights(Ahat_rowptr, Ahat_col, Ahat_val, cf, nc: int, Z_rowptr, Z_col, B,
+                        precision: int, Z_val, stream=None, raise_singular: bool = True):
+    """Returns ``(status, singular blocks, skipped F-points)``."""
+    sing, empty = ctypes.c_int64(0), ctypes.c_int64(0)
+    n = Ahat_rowptr.numel() - 1
+    st = load().clair_local_weights(
+        n, _dptr(Ahat_rowptr, torch.int32), _dptr(Ahat_col, torch.int32), _dptr(Ahat_val, torch.float64),
+        _dptr(cf, torch.int8), nc, _dptr(Z_rowptr, torch.int32), _dptr(Z_col, torch.int32),
+        _dptr(B, torch.float64), precision, _dptr(Z_val, torch.float64), _stream(stream),
+        ctypes.byref(sing), ctypes.byref(empty))
+    if st != CLAIR_OK and (st != CLAIR_ERR_SINGULAR_BLOCK or raise_singular):
+        _check(st)
+    return st, sing.value, empty.value

@@ -1,0 +1,216 @@
+// Internal helpers shared by the CUDA translation units of the CLAIR library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/clair.h"
+
+namespace clair {
+
+// ------------------------------------------------------------------------------------
+// Errors: every entry point returns a status; the message of the last failure is kept
+// per host thread.
+// ------------------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+
+struct Error {
+  clair_status st;
+};
+
+#define CLAIR_CUDA(call)                                                                  \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      ::clair::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      throw ::clair::Error{CLAIR_ERR_CUDA};                                               \
+    }                                                                                     \
+  } while (0)
+
+#define CLAIR_LAUNCHED() CLAIR_CUDA(cudaGetLastError())
+
+#define CLAIR_REQUIRE(cond, status, ...)  \
+  do {                                    \
+    if (!(cond)) {                        \
+      ::clair::set_error(__VA_ARGS__);    \
+      throw ::clair::Error{status};       \
+    }                                     \
+  } while (0)
+
+// ------------------------------------------------------------------------------------
+// Stream-ordered device buffers.
+// ------------------------------------------------------------------------------------
+template <class T>
+T* dalloc(size_t count, cudaStream_t s) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  CLAIR_CUDA(cudaMallocAsync(&p, count * sizeof(T), s));
+  return static_cast<T*>(p);
+}
+
+template <class T>
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+}
+
+// Device CSR matrix (values in float64 and, optionally, a float32 copy).
+struct Csr {
+  int rows = 0, cols = 0, nnz = 0;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* val = nullptr;
+  float* val32 = nullptr;
+  void release(cudaStream_t s) {
+    dfree(rowptr, s);
+    dfree(col, s);
+    dfree(val, s);
+    dfree(val32, s);
+  }
+};
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Number of SMs of the current device (cached per process).
+int sm_count();
+
+// ------------------------------------------------------------------------------------
+// Device utilities.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v, unsigned mask = 0xffffffffu) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
+template <int W, class T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, W);
+  return v;
+}
+
+// splitmix64 (Steele, Lea & Flood 2014): draw i of the stream seeded with `seed`.
+__device__ __forceinline__ double splitmix_pm1(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+// 'lowbias32' integer hash (C. Wellons, hash-prospector); a bijection of uint32.
+__host__ __device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// ------------------------------------------------------------------------------------
+// Host-callable building blocks (sparse.cu).
+// ------------------------------------------------------------------------------------
+// out[0] = 0, out[i+1] = sum_{k<=i} in[k]; returns out[n] (synchronises s).
+long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s, bool want_total = true);
+// Transpose (structure + values; perm[k] = source entry of output entry k); output
+// arrays are allocated here.  Rows of the result are sorted by column.
+void csr_transpose(const Csr& A, Csr& At, int** perm, cudaStream_t s);
+// max_{j != i} |a_ij| per row (0 for rows without off-diagonal entries).
+void row_max_offdiag(const Csr& A, double* out, cudaStream_t s);
+// y = alpha * A x + beta * y   (y may alias nothing; beta = 0 ignores y's input)
+void spmv(const Csr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s);
+void spmv32(const Csr& A, const float* x, float* y, float alpha, float beta, cudaStream_t s);
+// r = b - A x
+void residual(const Csr& A, const double* b, const double* x, double* r, cudaStream_t s);
+void residual32(const Csr& A, const float* b, const float* x, float* r, cudaStream_t s);
+// C = A * B (sparse-sparse, deterministic summation in A's row order, no FMA contraction)
+void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s);
+// Removes entries whose value is exactly zero (structure follows the values).
+void drop_zeros(Csr& C, cudaStream_t s);
+// Inverse diagonal (error if a diagonal entry is missing or zero).
+void inverse_diagonal(const Csr& A, double* dinv, cudaStream_t s);
+// Float copies.
+void to_float(const double* x, float* y, long long n, cudaStream_t s);
+void to_double(const float* x, double* y, long long n, cudaStream_t s);
+// Deterministic dot products: out[j] = <V_j, w> for j < m (V column-major n x m, ld = n).
+void multi_dot(const double* V, int m, const double* w, int n, double* out, double* partial,
+               cudaStream_t s);
+// w -= V[:, :m] * h  (h device)
+void multi_axpy(const double* V, int m, const double* h, double* w, int n, cudaStream_t s);
+// Gather: y[i] = x[idx[i]]
+void gather(const double* x, const int* idx, double* y, int n, cudaStream_t s);
+void gather_vals(const double* x, const int* perm, double* y, int n, cudaStream_t s);
+void scatter_vals(const double* x, const int* perm, double* y, int n, cudaStream_t s);
+// Caller-input validation (synchronises); throws CLAIR_ERR_ARG with a message.
+void validate_csr(const int* rowptr, const int* col, int rows, int cols, int nnz, const char* what,
+                  cudaStream_t s);
+void validate_cf(const signed char* cf, int n, cudaStream_t s);
+// Nonfinite check over a buffer; returns true if all finite (synchronises).
+bool all_finite(const double* x, long long n, cudaStream_t s);
+
+int partial_blocks();  // number of blocks used by the deterministic reductions
+
+// Counters of the batched local solves: zero-pivot blocks, F-points skipped by the
+// projection, systems per size bucket (T <= 8, 16, 32, 64, 128, larger), and the
+// algorithmic work: sum over systems of T^3, T^2 and T, and the gathered A entries.
+struct LocalStats {
+  long long singular = 0, empty = 0;
+  long long hist[6] = {0, 0, 0, 0, 0, 0};
+  double sum_t3 = 0, sum_t2 = 0, sum_t = 0;
+  long long gathered = 0;
+};
+
+// Kernel launches issued by this library (monotonic, process-wide).
+void count_launch();
+long long launch_count();
+
+// Device time per phase, measured with CUDA events on the launching stream.  Phases are
+// nested by nobody: begin() closes nothing, end() closes the last begin().
+enum Phase {
+  PH_SPLIT = 0,   // transpose, row maxima, strength, C/F splitting
+  PH_WEIGHT,      // Arnoldi relaxation weight
+  PH_SMOOTH,      // mode-vector smoothing
+  PH_PATTERN,     // transfer sparsity patterns
+  PH_LSOLVE,      // batched local gathers + solves (the hot kernels)
+  PH_PROJECT,     // transposes + constraint projection
+  PH_GALERKIN,    // R A P
+  PH_COARSE,      // coarsest inverse, float copies
+  PH_VCYCLE,      // V(1,1) cycles
+  PH_KRYLOV,      // FGMRES orthogonalisation, residuals, updates
+  PH_COUNT
+};
+
+class PhaseClock {
+ public:
+  void begin(int ph, cudaStream_t s);
+  void end(cudaStream_t s);
+  void collect(double* ms_out);  // synchronises; adds elapsed ms per phase; clears
+  ~PhaseClock();
+
+ private:
+  struct Mark {
+    int ph;
+    cudaEvent_t a, b;
+  };
+  Mark* marks_ = nullptr;
+  int n_ = 0, cap_ = 0;
+};
+PhaseClock* active_clock();
+void set_active_clock(PhaseClock* c);
+
+struct ClockScope {  // times a block of host code's launches into one phase
+  ClockScope(int ph, cudaStream_t s) : s_(s) {
+    if (active_clock()) active_clock()->begin(ph, s);
+  }
+  ~ClockScope() {
+    if (active_clock()) active_clock()->end(s_);
+  }
+  cudaStream_t s_;
+};
+
+}  // namespace clair

@@ -1,0 +1,828 @@
+// CLAIR hierarchy: setup (per level: strength, splitting, weight, smoothed modes, R and P
+// by Algorithm 1, Galerkin product) and solve (V(1,1) cycles inside right-preconditioned
+// flexible GMRES in float64), plus the C ABI declared in include/clair.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace clair {
+
+// --- functions of the other translation units -----------------------------------------
+void strength(const Csr& M, const double* thr, double theta, int mode, unsigned char* mask,
+              cudaStream_t s);
+void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsigned char* sAt,
+              signed char* cf, cudaStream_t s);
+void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf, const int* cpts,
+                   int nc, int n, int degree, Csr& Z, cudaStream_t s);
+template <class T>
+void jacobi(const Csr& A, const T* vals, const T* dinv, const signed char* cf, int which, T omega,
+            const T* b, const T* xin, T* xout, cudaStream_t s);
+template <class T>
+void jacobi_from_zero(int rows, const T* dinv, const signed char* cf, int which, T omega,
+                      const T* b, T* x, cudaStream_t s);
+double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed,
+                      double* omega_dev, cudaStream_t s);
+void dense_inverse(const Csr& A, double* Inv, cudaStream_t s);
+template <class T>
+void coarse_apply(const T* Inv, int n, const T* b, T* x, cudaStream_t s);
+int coarse_points(const signed char* cf, int n, int** cpts_out, cudaStream_t s);
+void transfer_weights(const Csr& Ahat, const signed char* cf, const int* cpts, Csr& Z,
+                      const double* B, int precision, LocalStats& st, Csr* keep_t,
+                      cudaStream_t s);
+const char* last_error();
+void clear_error();
+
+// --- hierarchy --------------------------------------------------------------------------
+struct Level {
+  Csr A, R, P;
+  int n = 0, nc = 0;
+  double* dinv = nullptr;
+  float* dinv32 = nullptr;
+  signed char* cf = nullptr;
+  int* cpts = nullptr;
+  double omega = 1.0;
+  double* B_P = nullptr;
+  double* B_R = nullptr;
+  // cycle work vectors
+  double *b64 = nullptr, *x64 = nullptr, *y64 = nullptr, *r64 = nullptr;
+  float *b32 = nullptr, *x32 = nullptr, *y32 = nullptr, *r32 = nullptr;
+};
+
+struct Krylov {
+  int n = 0, m = 0;
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;
+  double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *scal = nullptr, *partial = nullptr;
+  double* host = nullptr;  // pinned scalars
+};
+
+}  // namespace clair
+
+struct clair_hierarchy {
+  clair_params p;
+  std::vector<clair::Level> lv;
+  double* Inv = nullptr;     // coarsest dense inverse (float64, column-major)
+  float* Inv32 = nullptr;
+  int nL = 0;
+  cudaStream_t stream = nullptr;
+  clair::Krylov kr;
+  clair::LocalStats st;
+  double setup_ms = 0.0;
+  double phase_ms[clair::PH_COUNT] = {};   // setup, per phase
+  double solve_ms[clair::PH_COUNT] = {};   // last solve, per phase
+};
+
+namespace clair {
+
+static void to_float_copy(const double* x, float** y, long long n, cudaStream_t s) {
+  *y = dalloc<float>(n, s);
+  to_float(x, *y, n, s);
+}
+
+static void alloc_cycle(Level& L, cudaStream_t s) {
+  const int n = L.n;
+  L.b64 = dalloc<double>(n, s);
+  L.x64 = dalloc<double>(n, s);
+  L.y64 = dalloc<double>(n, s);
+  L.r64 = dalloc<double>(n, s);
+  L.b32 = dalloc<float>(n, s);
+  L.x32 = dalloc<float>(n, s);
+  L.y32 = dalloc<float>(n, s);
+  L.r32 = dalloc<float>(n, s);
+}
+
+static void release_level(Level& L, cudaStream_t s) {
+  L.A.release(s);
+  L.R.release(s);
+  L.P.release(s);
+  dfree(L.dinv, s);
+  dfree(L.dinv32, s);
+  dfree(L.cf, s);
+  dfree(L.cpts, s);
+  dfree(L.B_P, s);
+  dfree(L.B_R, s);
+  dfree(L.b64, s);
+  dfree(L.x64, s);
+  dfree(L.y64, s);
+  dfree(L.r64, s);
+  dfree(L.b32, s);
+  dfree(L.x32, s);
+  dfree(L.y32, s);
+  dfree(L.r32, s);
+}
+
+static void release_all(clair_hierarchy* h) {
+  cudaStream_t s = h->stream;
+  for (auto& L : h->lv) release_level(L, s);
+  h->lv.clear();
+  dfree(h->Inv, s);
+  dfree(h->Inv32, s);
+  Krylov& k = h->kr;
+  dfree(k.V, s);
+  dfree(k.Z, s);
+  dfree(k.w, s);
+  dfree(k.r, s);
+  dfree(k.H, s);
+  dfree(k.cs, s);
+  dfree(k.sn, s);
+  dfree(k.g, s);
+  dfree(k.y, s);
+  dfree(k.h1, s);
+  dfree(k.h2, s);
+  dfree(k.scal, s);
+  dfree(k.partial, s);
+  if (k.host) cudaFreeHost(k.host);
+  k.host = nullptr;
+}
+
+__global__ void inject(const double* __restrict__ x, const int* __restrict__ cpts, int nc,
+                       double* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nc) y[i] = x[cpts[i]];
+}
+
+// Builds the hierarchy from the fine operator (already copied into h->lv[0].A).
+static void setup_levels(clair_hierarchy* h, const double* B0) {
+  cudaStream_t s = h->stream;
+  const clair_params& p = h->p;
+  {
+    Level& L0 = h->lv[0];
+    L0.B_P = dalloc<double>(L0.n, s);
+    L0.B_R = dalloc<double>(L0.n, s);
+    CLAIR_CUDA(cudaMemcpyAsync(L0.B_P, B0, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, s));
+    CLAIR_CUDA(cudaMemcpyAsync(L0.B_R, B0, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, s));
+  }
+  double* omega_dev = dalloc<double>(1, s);
+  for (int k = 0;; ++k) {
+    Level& L = h->lv[k];
+    const int n = L.n;
+    L.dinv = dalloc<double>(n, s);
+    inverse_diagonal(L.A, L.dinv, s);
+    if (n <= p.coarse_max || k + 1 >= p.max_levels) break;
+
+    Csr At;
+    double* rmaxA = dalloc<double>(n, s);
+    double* rmaxAt = dalloc<double>(n, s);
+    unsigned char* sA = dalloc<unsigned char>(L.A.nnz, s);
+    unsigned char* sAt = dalloc<unsigned char>(L.A.nnz, s);
+    {
+      ClockScope clk(PH_SPLIT, s);
+      csr_transpose(L.A, At, nullptr, s);
+      row_max_offdiag(L.A, rmaxA, s);
+      row_max_offdiag(At, rmaxAt, s);
+      // coarsening strength S(A, theta_c): on A row-relative, on A^T via A's row maxima
+      strength(L.A, rmaxA, p.theta_coarsen, 0, sA, s);
+      strength(At, rmaxA, p.theta_coarsen, 1, sAt, s);
+      L.cf = dalloc<signed char>(n, s);
+      CLAIR_REQUIRE(p.coarsen == CLAIR_COARSEN_FC, CLAIR_ERR_UNSUPPORTED,
+                    "aggregation coarsening is not built yet");
+      split_fc(L.A, At, sA, sAt, L.cf, s);
+      L.nc = coarse_points(L.cf, n, &L.cpts, s);
+    }
+    if (L.nc == 0 || L.nc == n) {
+      dfree(L.cf, s);
+      dfree(L.cpts, s);
+      L.nc = 0;
+      At.release(s);
+      dfree(rmaxA, s);
+      dfree(rmaxAt, s);
+      dfree(sA, s);
+      dfree(sAt, s);
+      break;
+    }
+    // relaxation weight and smoothed modes (zero right-hand side), A for P, A^T for R
+    {
+      ClockScope clk(PH_WEIGHT, s);
+      L.omega = arnoldi_weight(L.A, L.dinv, p.arnoldi_iters, p.seed + (uint64_t)k, omega_dev, s);
+    }
+    {
+      ClockScope clk(PH_SMOOTH, s);
+      double* tmp = dalloc<double>(n, s);
+      for (int side = 0; side < 2; ++side) {
+        const Csr& M = side == 0 ? L.A : At;
+        double* Bv = side == 0 ? L.B_P : L.B_R;
+        for (int it = 0; it < p.b_smooth_iters; ++it) {
+          jacobi<double>(M, M.val, L.dinv, L.cf, 1, L.omega, nullptr, Bv, tmp, s);
+          jacobi<double>(M, M.val, L.dinv, L.cf, 0, L.omega, nullptr, tmp, Bv, s);
+          jacobi<double>(M, M.val, L.dinv, L.cf, 0, L.omega, nullptr, Bv, tmp, s);
+          CLAIR_CUDA(cudaMemcpyAsync(Bv, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        }
+      }
+      dfree(tmp, s);
+    }
+    // interpolation-strength masks for the two patterns
+    // R: Algorithm 1 on A^T, walked on A, S(A^T) uses the row maxima of A^T
+    // P: Algorithm 1 on A,   walked on A^T, S(A) uses the row maxima of A
+    unsigned char* sR = sA;   // reuse buffers (the splitting is done)
+    unsigned char* sP = sAt;
+    Csr Pt;
+    {
+      ClockScope clk(PH_PATTERN, s);
+      strength(L.A, rmaxAt, p.theta_interp, 1, sR, s);
+      strength(At, rmaxA, p.theta_interp, 1, sP, s);
+      build_pattern(L.A, sR, L.cf, L.cpts, L.nc, n, p.degree, L.R, s);
+      build_pattern(At, sP, L.cf, L.cpts, L.nc, n, p.degree, Pt, s);
+    }
+    transfer_weights(At, L.cf, L.cpts, L.R, L.B_R, p.precision, h->st, nullptr, s);
+    transfer_weights(L.A, L.cf, L.cpts, Pt, L.B_P, p.precision, h->st, &L.P, s);
+    Pt.release(s);
+    dfree(rmaxA, s);
+    dfree(rmaxAt, s);
+    dfree(sA, s);
+    dfree(sAt, s);
+    At.release(s);
+    // Galerkin coarse operator A_c = (R A) P
+    Csr RA, Ac;
+    ClockScope clk(PH_GALERKIN, s);
+    spgemm(L.R, L.A, RA, s);
+    spgemm(RA, L.P, Ac, s);
+    RA.release(s);
+    drop_zeros(Ac, s);  // exact cancellations leave no stored zeros
+    Level C;
+    C.A = Ac;
+    C.n = Ac.rows;
+    C.B_P = dalloc<double>(C.n, s);
+    C.B_R = dalloc<double>(C.n, s);
+    if (C.n) {
+      inject<<<ceil_div(C.n, 256), 256, 0, s>>>(L.B_P, L.cpts, C.n, C.B_P); ::clair::count_launch();
+      inject<<<ceil_div(C.n, 256), 256, 0, s>>>(L.B_R, L.cpts, C.n, C.B_R); ::clair::count_launch();
+    }
+    CLAIR_LAUNCHED();
+    h->lv.push_back(C);
+  }
+  dfree(omega_dev, s);
+  // coarsest level: dense inverse; float copies and work vectors everywhere
+  ClockScope clk(PH_COARSE, s);
+  Level& last = h->lv.back();
+  h->nL = last.n;
+  CLAIR_REQUIRE(h->nL <= 1024, CLAIR_ERR_CAPACITY,
+                "coarsest level has %d unknowns (> 1024): raise max_levels", h->nL);
+  h->Inv = dalloc<double>((size_t)h->nL * h->nL, s);
+  dense_inverse(last.A, h->Inv, s);
+  to_float_copy(h->Inv, &h->Inv32, (long long)h->nL * h->nL, s);
+  for (auto& L : h->lv) {
+    to_float_copy(L.A.val, &L.A.val32, L.A.nnz, s);
+    to_float_copy(L.dinv, &L.dinv32, L.n, s);
+    if (L.nc) {
+      to_float_copy(L.R.val, &L.R.val32, L.R.nnz, s);
+      to_float_copy(L.P.val, &L.P.val32, L.P.nnz, s);
+    }
+    alloc_cycle(L, s);
+  }
+}
+
+// --- V(1,1) cycle ---------------------------------------------------------------------
+template <class T>
+struct Vec {
+  static T* b(Level& L);
+  static T* x(Level& L);
+  static T* y(Level& L);
+  static T* r(Level& L);
+  static const T* aval(const Csr& M);
+  static const T* dinv(const Level& L);
+};
+template <>
+struct Vec<double> {
+  static double* b(Level& L) { return L.b64; }
+  static double* x(Level& L) { return L.x64; }
+  static double* y(Level& L) { return L.y64; }
+  static double* r(Level& L) { return L.r64; }
+  static const double* aval(const Csr& M) { return M.val; }
+  static const double* dinv(const Level& L) { return L.dinv; }
+};
+template <>
+struct Vec<float> {
+  static float* b(Level& L) { return L.b32; }
+  static float* x(Level& L) { return L.x32; }
+  static float* y(Level& L) { return L.y32; }
+  static float* r(Level& L) { return L.r32; }
+  static const float* aval(const Csr& M) { return M.val32; }
+  static const float* dinv(const Level& L) { return L.dinv32; }
+};
+
+template <class T>
+static void spmv_t(const Csr& A, const T* x, T* y, T alpha, T beta, cudaStream_t s);
+template <>
+void spmv_t<double>(const Csr& A, const double* x, double* y, double a, double b, cudaStream_t s) {
+  spmv(A, x, y, a, b, s);
+}
+template <>
+void spmv_t<float>(const Csr& A, const float* x, float* y, float a, float b, cudaStream_t s) {
+  spmv32(A, x, y, a, b, s);
+}
+template <class T>
+static void residual_t(const Csr& A, const T* b, const T* x, T* r, cudaStream_t s);
+template <>
+void residual_t<double>(const Csr& A, const double* b, const double* x, double* r, cudaStream_t s) {
+  residual(A, b, x, r, s);
+}
+template <>
+void residual_t<float>(const Csr& A, const float* b, const float* x, float* r, cudaStream_t s) {
+  residual32(A, b, x, r, s);
+}
+
+// Cycle on level k: input in Vec<T>::b(L_k), output in Vec<T>::x(L_k).
+template <class T>
+static void vcycle_level(clair_hierarchy* h, int k) {
+  cudaStream_t s = h->stream;
+  Level& L = h->lv[k];
+  T* b = Vec<T>::b(L);
+  T* x = Vec<T>::x(L);
+  T* y = Vec<T>::y(L);
+  if (k == (int)h->lv.size() - 1) {
+    const T* Inv = nullptr;
+    if constexpr (sizeof(T) == 8)
+      Inv = reinterpret_cast<const T*>(h->Inv);
+    else
+      Inv = reinterpret_cast<const T*>(h->Inv32);
+    coarse_apply<T>(Inv, L.n, b, x, s);
+    return;
+  }
+  const T* av = Vec<T>::aval(L.A);
+  const T* dv = Vec<T>::dinv(L);
+  const T w = (T)L.omega;
+  const T wpost = h->p.post_weighted ? w : T(1);
+  // CFF pre-smoothing from x = 0
+  jacobi_from_zero<T>(L.n, dv, L.cf, 1, w, b, x, s);
+  jacobi<T>(L.A, av, dv, L.cf, 0, w, b, x, y, s);
+  jacobi<T>(L.A, av, dv, L.cf, 0, w, b, y, x, s);
+  // residual, restriction, coarse cycle, interpolation
+  T* r = Vec<T>::r(L);
+  residual_t<T>(L.A, b, x, r, s);
+  Level& C = h->lv[k + 1];
+  spmv_t<T>(L.R, r, Vec<T>::b(C), T(1), T(0), s);
+  vcycle_level<T>(h, k + 1);
+  spmv_t<T>(L.P, Vec<T>::x(C), x, T(1), T(1), s);
+  // FFC post-smoothing
+  jacobi<T>(L.A, av, dv, L.cf, 0, wpost, b, x, y, s);
+  jacobi<T>(L.A, av, dv, L.cf, 0, wpost, b, y, x, s);
+  jacobi<T>(L.A, av, dv, L.cf, 1, wpost, b, x, y, s);
+  CLAIR_CUDA(cudaMemcpyAsync(x, y, sizeof(T) * L.n, cudaMemcpyDeviceToDevice, s));
+}
+
+// z = M^-1 v on level k (float64 in and out).
+static void apply_precond(clair_hierarchy* h, int k, const double* v, double* z) {
+  cudaStream_t s = h->stream;
+  Level& L = h->lv[k];
+  if (h->p.precision == CLAIR_MIXED) {
+    to_float(v, L.b32, L.n, s);
+    vcycle_level<float>(h, k);
+    to_double(L.x32, z, L.n, s);
+  } else {
+    CLAIR_CUDA(cudaMemcpyAsync(L.b64, v, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
+    vcycle_level<double>(h, k);
+    CLAIR_CUDA(cudaMemcpyAsync(z, L.x64, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+// --- FGMRES -----------------------------------------------------------------------------
+// scal: [0] ||f||^2, [1] beta^2, [2] ||w||^2, [3] inv norm, [4] |g_{j+1}|, [5] ||r||^2
+__global__ void gmres_start(double* __restrict__ g, int m, const double* __restrict__ scal,
+                            double* __restrict__ inv) {
+  if (threadIdx.x != 0) return;
+  const double beta = sqrt(scal[1]);
+  for (int i = 0; i <= m; ++i) g[i] = 0.0;
+  g[0] = beta;
+  *inv = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+
+__global__ void gmres_givens(double* __restrict__ H, int ldh, int j, const double* __restrict__ h1,
+                             const double* __restrict__ h2, double* __restrict__ cs,
+                             double* __restrict__ sn, double* __restrict__ g,
+                             double* __restrict__ scal) {
+  if (threadIdx.x != 0) return;
+  double* col = H + (long long)j * ldh;
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  const double hn = sqrt(scal[2]);
+  col[j + 1] = hn;
+  scal[3] = hn > 0.0 ? 1.0 / hn : 0.0;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  cs[j] = den > 0.0 ? col[j] / den : 1.0;
+  sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  scal[4] = fabs(g[j + 1]);
+}
+
+// y = R^-1 g (upper triangular, size jend); stores -y for the update x -= Z (-y).
+__global__ void gmres_backsolve(const double* __restrict__ H, int ldh, int jend,
+                                const double* __restrict__ g, double* __restrict__ ny) {
+  if (threadIdx.x != 0) return;
+  double y[64];
+  for (int i = jend - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int c = i + 1; c < jend; ++c) acc -= H[i + (long long)c * ldh] * y[c];
+    const double d = H[i + (long long)i * ldh];
+    y[i] = d != 0.0 ? acc / d : 0.0;
+  }
+  for (int i = 0; i < jend; ++i) ny[i] = -y[i];
+}
+
+__global__ void scale_into(const double* __restrict__ w, double* __restrict__ v, long long n,
+                           const double* __restrict__ s) {
+  const double f = *s;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    v[i] = w[i] * f;
+}
+
+static void alloc_krylov(clair_hierarchy* h) {
+  cudaStream_t s = h->stream;
+  Krylov& k = h->kr;
+  k.n = h->lv[0].n;
+  k.m = h->p.gmres_restart;
+  const long long n = k.n;
+  const int m = k.m;
+  k.V = dalloc<double>((m + 1) * n, s);
+  k.Z = dalloc<double>(m * n, s);
+  k.w = dalloc<double>(n, s);
+  k.r = dalloc<double>(n, s);
+  k.H = dalloc<double>((m + 1) * m, s);
+  k.cs = dalloc<double>(m, s);
+  k.sn = dalloc<double>(m, s);
+  k.g = dalloc<double>(m + 1, s);
+  k.y = dalloc<double>(m, s);
+  k.h1 = dalloc<double>(m + 1, s);
+  k.h2 = dalloc<double>(m + 1, s);
+  k.scal = dalloc<double>(8, s);
+  k.partial = dalloc<double>((size_t)partial_blocks() * (m + 2), s);
+  CLAIR_CUDA(cudaMallocHost(&k.host, sizeof(double) * 8));
+}
+
+static double read_scalar(clair_hierarchy* h, const double* dev) {
+  CLAIR_CUDA(cudaMemcpyAsync(h->kr.host, dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CLAIR_CUDA(cudaStreamSynchronize(h->stream));
+  return h->kr.host[0];
+}
+
+static clair_status fgmres(clair_hierarchy* h, const double* f, double* u, int* iters_out,
+                           double* relres_out) {
+  cudaStream_t s = h->stream;
+  Krylov& k = h->kr;
+  const Level& L0 = h->lv[0];
+  const int n = k.n, m = k.m;
+  const int grid = std::min(ceil_div(n, 256), 32 * sm_count());
+  multi_dot(f, 1, f, n, k.scal + 0, k.partial, s);
+  const double fnorm = sqrt(read_scalar(h, k.scal + 0));
+  int its = 0;
+  if (fnorm == 0.0) {
+    CLAIR_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, s));
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    return CLAIR_OK;
+  }
+  const double tol = h->p.rtol * fnorm;
+  residual(L0.A, f, u, k.r, s);
+  multi_dot(k.r, 1, k.r, n, k.scal + 1, k.partial, s);
+  double beta = sqrt(read_scalar(h, k.scal + 1));
+  CLAIR_REQUIRE(isfinite(beta), CLAIR_ERR_NONFINITE, "nonfinite initial residual");
+  while (beta > tol && its < h->p.gmres_maxit) {
+    gmres_start<<<1, 32, 0, s>>>(k.g, m, k.scal, k.scal + 3); ::clair::count_launch();
+    scale_into<<<grid, 256, 0, s>>>(k.r, k.V, n, k.scal + 3); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+    int jend = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = k.V + (size_t)j * n;
+      double* zj = k.Z + (size_t)j * n;
+      {
+        ClockScope clk(PH_VCYCLE, s);
+        apply_precond(h, 0, vj, zj);
+      }
+      ClockScope clk(PH_KRYLOV, s);
+      spmv(L0.A, zj, k.w, 1.0, 0.0, s);
+      multi_dot(k.V, j + 1, k.w, n, k.h1, k.partial, s);
+      multi_axpy(k.V, j + 1, k.h1, k.w, n, s);
+      multi_dot(k.V, j + 1, k.w, n, k.h2, k.partial, s);
+      multi_axpy(k.V, j + 1, k.h2, k.w, n, s);
+      multi_dot(k.w, 1, k.w, n, k.scal + 2, k.partial, s);
+      gmres_givens<<<1, 32, 0, s>>>(k.H, m + 1, j, k.h1, k.h2, k.cs, k.sn, k.g, k.scal); ::clair::count_launch();
+      scale_into<<<grid, 256, 0, s>>>(k.w, k.V + (size_t)(j + 1) * n, n, k.scal + 3); ::clair::count_launch();
+      CLAIR_LAUNCHED();
+      ++its;
+      jend = j + 1;
+      const double est = read_scalar(h, k.scal + 4);
+      CLAIR_REQUIRE(isfinite(est), CLAIR_ERR_NONFINITE, "nonfinite residual estimate");
+      if (est <= tol || its >= h->p.gmres_maxit) break;
+    }
+    gmres_backsolve<<<1, 32, 0, s>>>(k.H, m + 1, jend, k.g, k.y); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+    multi_axpy(k.Z, jend, k.y, u, n, s);
+    residual(L0.A, f, u, k.r, s);
+    multi_dot(k.r, 1, k.r, n, k.scal + 1, k.partial, s);
+    beta = sqrt(read_scalar(h, k.scal + 1));
+    CLAIR_REQUIRE(isfinite(beta), CLAIR_ERR_NONFINITE, "nonfinite residual");
+  }
+  if (iters_out) *iters_out = its;
+  if (relres_out) *relres_out = beta / fnorm;
+  return beta <= tol ? CLAIR_OK : CLAIR_ERR_NOT_CONVERGED;
+}
+
+}  // namespace clair
+
+// =======================================================================================
+// C ABI
+// =======================================================================================
+using namespace clair;
+
+#define CLAIR_API_BEGIN \
+  clear_error();        \
+  try {
+#define CLAIR_API_END                                    \
+  }                                                      \
+  catch (const Error& e) {                               \
+    return e.st;                                         \
+  }                                                      \
+  catch (...) {                                          \
+    set_error("unexpected host exception");              \
+    return CLAIR_ERR_CUDA;                               \
+  }                                                      \
+  return CLAIR_OK;
+
+extern "C" {
+
+clair_status clair_params_default(clair_params* p) {
+  if (!p) {
+    set_error("clair_params_default: null pointer");
+    return CLAIR_ERR_ARG;
+  }
+  p->theta_coarsen = 0.25;
+  p->theta_interp = 0.05;
+  p->degree = 2;
+  p->coarsen = CLAIR_COARSEN_FC;
+  p->b_smooth_iters = 5;
+  p->arnoldi_iters = 15;
+  p->post_weighted = 0;
+  p->coarse_max = 128;
+  p->max_levels = 25;
+  p->precision = CLAIR_FP64;
+  p->gmres_restart = 50;
+  p->gmres_maxit = 200;
+  p->rtol = 1e-8;
+  p->seed = 0x5EED;
+  return CLAIR_OK;
+}
+
+const char* clair_last_error(void) { return last_error(); }
+
+clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, const double* val,
+                         const double* B, const clair_params* pin, void* stream, clair_h* out) {
+  if (out) *out = nullptr;
+  CLAIR_API_BEGIN
+  CLAIR_REQUIRE(out && rowptr && col && val && B, CLAIR_ERR_ARG, "clair_setup: null pointer");
+  CLAIR_REQUIRE(n > 0 && nnz >= n, CLAIR_ERR_ARG, "clair_setup: bad sizes n=%d nnz=%d", n, nnz);
+  clair_params p;
+  if (pin)
+    p = *pin;
+  else
+    clair_params_default(&p);
+  CLAIR_REQUIRE(p.gmres_restart >= 1 && p.gmres_restart <= 64, CLAIR_ERR_ARG,
+                "gmres_restart must be in [1, 64]");
+  CLAIR_REQUIRE(p.precision == CLAIR_FP64 || p.precision == CLAIR_MIXED, CLAIR_ERR_ARG,
+                "unknown precision");
+  CLAIR_REQUIRE(p.max_levels >= 1 && p.max_levels <= 32, CLAIR_ERR_ARG, "max_levels in [1,32]");
+  CLAIR_REQUIRE(p.coarse_max >= 1 && p.coarse_max <= 1024, CLAIR_ERR_ARG,
+                "coarse_max in [1, 1024]");
+  CLAIR_REQUIRE(p.arnoldi_iters >= 1 && p.arnoldi_iters <= 60, CLAIR_ERR_ARG,
+                "arnoldi_iters in [1, 60]");
+  CLAIR_REQUIRE(p.degree == 1 || p.degree == 2, CLAIR_ERR_UNSUPPORTED, "degree must be 1 or 2");
+  CLAIR_REQUIRE(p.b_smooth_iters >= 0 && p.gmres_maxit >= 1 && p.rtol > 0.0, CLAIR_ERR_ARG,
+                "bad iteration counts or rtol");
+  clair_hierarchy* h = new clair_hierarchy();
+  h->p = p;
+  h->stream = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  try {
+    cudaStream_t s = h->stream;
+    CLAIR_CUDA(cudaEventCreate(&e0));
+    CLAIR_CUDA(cudaEventCreate(&e1));
+    CLAIR_CUDA(cudaEventRecord(e0, s));
+    Level L0;
+    L0.n = n;
+    L0.A.rows = L0.A.cols = n;
+    L0.A.nnz = nnz;
+    L0.A.rowptr = dalloc<int>(n + 1, s);
+    L0.A.col = dalloc<int>(nnz, s);
+    L0.A.val = dalloc<double>(nnz, s);
+    h->lv.push_back(L0);
+    CLAIR_CUDA(cudaMemcpyAsync(L0.A.rowptr, rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, s));
+    CLAIR_CUDA(cudaMemcpyAsync(L0.A.col, col, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, s));
+    CLAIR_CUDA(cudaMemcpyAsync(L0.A.val, val, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
+    validate_csr(rowptr, col, n, n, nnz, "A", s);
+    CLAIR_REQUIRE(all_finite(val, nnz, s), CLAIR_ERR_NONFINITE, "A has nonfinite values");
+    CLAIR_REQUIRE(all_finite(B, n, s), CLAIR_ERR_NONFINITE, "B has nonfinite values");
+    PhaseClock clock;
+    set_active_clock(&clock);
+    setup_levels(h, B);
+    alloc_krylov(h);
+    set_active_clock(nullptr);
+    clock.collect(h->phase_ms);
+    CLAIR_CUDA(cudaEventRecord(e1, s));
+    CLAIR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CLAIR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    h->setup_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  } catch (...) {
+    set_active_clock(nullptr);
+    release_all(h);
+    delete h;
+    throw;
+  }
+  *out = h;
+  CLAIR_API_END
+}
+
+clair_status clair_solve(clair_h h, const double* f, double* u, void* stream, int* iters,
+                         double* relres) {
+  CLAIR_API_BEGIN
+  CLAIR_REQUIRE(h && f && u, CLAIR_ERR_ARG, "clair_solve: null pointer");
+  cudaStream_t keep = h->stream;
+  h->stream = static_cast<cudaStream_t>(stream);
+  clair_status st;
+  PhaseClock clock;
+  set_active_clock(&clock);
+  for (double& v : h->solve_ms) v = 0.0;
+  try {
+    st = fgmres(h, f, u, iters, relres);
+  } catch (...) {
+    set_active_clock(nullptr);
+    h->stream = keep;
+    throw;
+  }
+  set_active_clock(nullptr);
+  clock.collect(h->solve_ms);
+  h->stream = keep;
+  if (st != CLAIR_OK) set_error("FGMRES did not reach rtol within gmres_maxit");
+  return st;
+  CLAIR_API_END
+}
+
+clair_status clair_vcycle(clair_h h, int level, const double* b, double* x, void* stream) {
+  CLAIR_API_BEGIN
+  CLAIR_REQUIRE(h && b && x, CLAIR_ERR_ARG, "clair_vcycle: null pointer");
+  CLAIR_REQUIRE(level >= 0 && level < (int)h->lv.size(), CLAIR_ERR_ARG, "bad level %d", level);
+  cudaStream_t keep = h->stream;
+  h->stream = static_cast<cudaStream_t>(stream);
+  try {
+    apply_precond(h, level, b, x);
+  } catch (...) {
+    h->stream = keep;
+    throw;
+  }
+  h->stream = keep;
+  CLAIR_API_END
+}
+
+clair_status clair_stats(clair_h h, clair_stats_t* o) {
+  CLAIR_API_BEGIN
+  CLAIR_REQUIRE(h && o, CLAIR_ERR_ARG, "clair_stats: null pointer");
+  memset(o, 0, sizeof(*o));
+  o->levels = (int)h->lv.size();
+  double nnz0 = h->lv[0].A.nnz, sum = 0.0;
+  for (size_t k = 0; k < h->lv.size() && k < 32; ++k) {
+    const Level& L = h->lv[k];
+    o->n[k] = L.n;
+    o->nnz[k] = L.A.nnz;
+    o->nnz_R[k] = L.nc ? L.R.nnz : 0;
+    o->nnz_P[k] = L.nc ? L.P.nnz : 0;
+    o->omega[k] = L.omega;
+    sum += L.A.nnz;
+    o->r_rows += L.nc;
+    o->p_cols += L.nc;
+  }
+  o->operator_complexity = sum / nnz0;
+  for (int b = 0; b < 6; ++b) o->t_hist[b] = h->st.hist[b];
+  o->singular_blocks = h->st.singular;
+  o->empty_constraints = h->st.empty;
+  o->setup_ms = h->setup_ms;
+  for (int i = 0; i < PH_COUNT && i < 10; ++i) {
+    o->phase_ms[i] = h->phase_ms[i];
+    o->solve_phase_ms[i] = h->solve_ms[i];
+  }
+  o->lsolve_flops = (2.0 / 3.0) * h->st.sum_t3 + 2.0 * h->st.sum_t2;
+  double minb = 0.0;
+  for (const Level& L : h->lv)
+    if (L.nc) minb += 2.0 * 12.0 * L.A.nnz + 12.0 * (double)L.R.nnz + 12.0 * (double)L.P.nnz;
+  o->lsolve_min_bytes = minb;
+  o->lsolve_gathered = h->st.gathered;
+  CLAIR_API_END
+}
+
+int64_t clair_kernel_launches(void) { return launch_count(); }
+
+clair_status clair_level_view(clair_h h, int level, int* n, int* nc, int* nnz_A,
+                              const int** A_rowptr, const int** A_col, const double** A_val,
+                              int* nnz_R, const int** R_rowptr, const int** R_col,
+                              const double** R_val, int* nnz_P, const int** P_rowptr,
+                              const int** P_col, const double** P_val, const signed char** cf,
+                              const double** B_P, const double** B_R, double* omega) {
+  CLAIR_API_BEGIN
+  CLAIR_REQUIRE(h, CLAIR_ERR_ARG, "clair_level_view: null handle");
+  CLAIR_REQUIRE(level >= 0 && level < (int)h->lv.size(), CLAIR_ERR_ARG, "bad level %d", level);
+  const Level& L = h->lv[level];
+  if (n) *n = L.n;
+  if (nc) *nc = L.nc;
+  if (nnz_A) *nnz_A = L.A.nnz;
+  if (A_rowptr) *A_rowptr = L.A.rowptr;
+  if (A_col) *A_col = L.A.col;
+  if (A_val) *A_val = L.A.val;
+  const bool has = L.nc > 0;
+  if (nnz_R) *nnz_R = has ? L.R.nnz : 0;
+  if (R_rowptr) *R_rowptr = has ? L.R.rowptr : nullptr;
+  if (R_col) *R_col = has ? L.R.col : nullptr;
+  if (R_val) *R_val = has ? L.R.val : nullptr;
+  if (nnz_P) *nnz_P = has ? L.P.nnz : 0;
+  if (P_rowptr) *P_rowptr = has ? L.P.rowptr : nullptr;
+  if (P_col) *P_col = has ? L.P.col : nullptr;
+  if (P_val) *P_val = has ? L.P.val : nullptr;
+  if (cf) *cf = has ? L.cf : nullptr;
+  if (B_P) *B_P = has ? L.B_P : nullptr;
+  if (B_R) *B_R = has ? L.B_R : nullptr;
+  if (omega) *omega = L.omega;
+  CLAIR_API_END
+}
+
+clair_status clair_free(clair_h h) {
+  CLAIR_API_BEGIN
+  if (!h) return CLAIR_OK;
+  release_all(h);
+  cudaStreamSynchronize(h->stream);
+  delete h;
+  CLAIR_API_END
+}
+
+clair_status clair_local_weights(int n, const int* Ahat_rowptr, const int* Ahat_col,
+                                 const double* Ahat_val, const signed char* cf, int nc,
+                                 const int* Z_rowptr, const int* Z_col, const double* B,
+                                 int precision, double* Z_val, void* stream,
+                                 int64_t* singular_out, int64_t* empty_out) {
+  CLAIR_API_BEGIN
+  CLAIR_REQUIRE(Ahat_rowptr && Ahat_col && Ahat_val && cf && Z_rowptr && Z_col && B && Z_val,
+                CLAIR_ERR_ARG, "clair_local_weights: null pointer");
+  CLAIR_REQUIRE(n > 0 && nc >= 0 && nc <= n, CLAIR_ERR_ARG, "clair_local_weights: bad sizes");
+  CLAIR_REQUIRE(precision == CLAIR_FP64 || precision == CLAIR_MIXED, CLAIR_ERR_ARG,
+                "unknown precision");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int nnzA = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&nnzA, Ahat_rowptr + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  validate_csr(Ahat_rowptr, Ahat_col, n, n, nnzA, "Ahat", s);
+  validate_cf(cf, n, s);
+  int* cpts = nullptr;
+  const int nc2 = coarse_points(cf, n, &cpts, s);
+  if (nc2 != nc) {
+    dfree(cpts, s);
+    CLAIR_REQUIRE(false, CLAIR_ERR_ARG, "nc=%d but cf has %d C-points", nc, nc2);
+  }
+  Csr Ahat;
+  Ahat.rows = Ahat.cols = n;
+  Ahat.rowptr = const_cast<int*>(Ahat_rowptr);
+  Ahat.col = const_cast<int*>(Ahat_col);
+  Ahat.val = const_cast<double*>(Ahat_val);
+  int nnzZ = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&nnzZ, Z_rowptr + nc, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  try {
+    validate_csr(Z_rowptr, Z_col, nc, n, nnzZ, "Z", s);
+  } catch (...) {
+    dfree(cpts, s);
+    throw;
+  }
+  Csr Z;
+  Z.rows = nc;
+  Z.cols = n;
+  Z.nnz = nnzZ;
+  Z.rowptr = const_cast<int*>(Z_rowptr);
+  Z.col = const_cast<int*>(Z_col);
+  Z.val = Z_val;
+  LocalStats st;
+  try {
+    transfer_weights(Ahat, cf, cpts, Z, B, precision, st, nullptr, s);
+  } catch (...) {
+    dfree(cpts, s);
+    throw;
+  }
+  dfree(cpts, s);
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  if (singular_out) *singular_out = st.singular;
+  if (empty_out) *empty_out = st.empty;
+  if (st.singular) {
+    set_error("%lld local blocks had a zero pivot", st.singular);
+    return CLAIR_ERR_SINGULAR_BLOCK;
+  }
+  CLAIR_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,495 @@
+// Batched constrained local solves (the CLAIR hot loop).
+//
+// For every coarse point i with pattern W_i = {l_1 < ... < l_T} (F-points), Algorithm 1
+// with exact block inverses and one iteration (Remark 3.2) needs the local lAIR system
+// (Eq. 3.1; Eq. 2.8 for the restriction, which is the same system on A^T):
+//     Ahat[W_i, W_i] w_i = -Ahat[W_i, i],
+// followed by the projection onto the mode constraint W B_c = B|_F (Eq. 3.3), which for
+// one mode vector and exact inverses reduces to, per F-point j with J_j = {i : j in W_i},
+//     w_ji <- w_ji - mu_j B_c(i),  mu_j = (sum_i w_ji B_c(i) - B_j) / sum_i B_c(i)^2.
+// (With the exact inverse, Algorithm 1 returns the Euclidean projection of the lAIR
+// weights onto {Q w = B|_F}; the tentative weights cancel.)
+//
+// Layout: the pattern is a CSR with one row per coarse point (the transposed P_hat), each
+// row holding the coarse point's own column (identity weight 1) and its F-points sorted.
+// Systems are bucketed by T: T <= 8, 16, 32 use G lanes of a warp per system (row p of
+// the local matrix lives in the registers of lane p; the pivot row is broadcast with
+// shuffles); 32 < T <= 128 uses one CTA per system with the matrix in shared memory.
+// Pivoting is partial (largest |entry| among rows not yet used, lowest row on ties),
+// done implicitly by marking rows instead of swapping them.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace clair {
+
+constexpr int LS_BUCKETS = 6;                     // T in [1,8], (8,16], (16,32], (32,64], (64,128], (128,256]
+__host__ __device__ inline int ls_bucket(int T) {
+  return T <= 8 ? 0 : T <= 16 ? 1 : T <= 32 ? 2 : T <= 64 ? 3 : T <= 128 ? 4 : 5;
+}
+
+// Position of column c in the sorted list z[0..T-1], or -1.
+__device__ __forceinline__ int find_sorted(const int* z, int T, int c) {
+  int lo = 0, hi = T - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int v = z[mid];
+    if (v == c) return mid;
+    if (v < c)
+      lo = mid + 1;
+    else
+      hi = mid - 1;
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------------------------
+// Sub-warp path: G lanes per system, G in {8, 16, 32}, T <= G.
+// ------------------------------------------------------------------------------------
+constexpr int LS_WARPS = 4;  // warps per block in the sub-warp path
+
+template <class Real, int G>
+__global__ void __launch_bounds__(32 * LS_WARPS)
+lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
+             const double* __restrict__ Aval, const int* __restrict__ Zrp,
+             const int* __restrict__ Zcol, const int* __restrict__ cpts,
+             const int* __restrict__ work, int nwork, double* __restrict__ Zval,
+             unsigned long long* __restrict__ nsingular) {
+  constexpr int GPW = 32 / G;
+  __shared__ int zl[LS_WARPS * GPW][G];
+  __shared__ Real tile[LS_WARPS * GPW][G][G + 1];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int gsub = lane / G;          // group within warp
+  const int p = lane % G;             // row owned by this lane
+  const int gib = wib * GPW + gsub;   // group within block
+  const long long item = ((long long)blockIdx.x * LS_WARPS + wib) * GPW + gsub;
+  const bool live = item < nwork;
+
+  int r = 0, i = 0, base = 0, len = 1;
+  if (live) {
+    r = work[item];
+    i = cpts[r];
+    base = Zrp[r];
+    len = Zrp[r + 1] - base;
+  }
+  const int T = len - 1;
+  // position d of the identity column within the row
+  int zc = (live && p < len) ? Zcol[base + p] : -1;
+  unsigned m = __ballot_sync(0xffffffffu, live && p < len && zc == i);
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gsub * G));
+  m &= gmask;
+  // the identity sits at position G (unseen by the G lanes) only when T == G
+  const int d = m ? (__ffs(m) - 1 - gsub * G) : T;
+  // F-only column list
+  int fcol = -1;
+  if (live && p < T) fcol = Zcol[base + p + (p >= d ? 1 : 0)];
+  zl[gib][p] = fcol;
+  __syncwarp();
+
+  // gather row p of the local matrix (row l_p of Ahat restricted to the pattern) and
+  // the right-hand side -Ahat[l_p, i]
+  Real rhs = 0;
+#pragma unroll
+  for (int q = 0; q < G; ++q) tile[gib][p][q] = Real(0);
+  if (live && p < T) {
+    for (int e = Arp[fcol]; e < Arp[fcol + 1]; ++e) {
+      const int c = Acol[e];
+      if (c == i) {
+        rhs = Real(-Aval[e]);
+      } else {
+        const int q = find_sorted(zl[gib], T, c);
+        if (q >= 0) tile[gib][p][q] = Real(Aval[e]);
+      }
+    }
+  }
+  Real a[G];
+#pragma unroll
+  for (int q = 0; q < G; ++q) a[q] = tile[gib][p][q];
+  Real b = rhs;
+
+  // elimination with implicit partial pivoting
+  bool done = !(live && p < T);
+  int mystep = -1;
+  int pivlane[G];
+  bool singular = false;
+#pragma unroll
+  for (int k = 0; k < G; ++k) {
+    Real v = done ? Real(-1) : (a[k] < 0 ? -a[k] : a[k]);
+    int who = p;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      Real v2 = __shfl_xor_sync(0xffffffffu, v, o, G);
+      int w2 = __shfl_xor_sync(0xffffffffu, who, o, G);
+      if (v2 > v || (v2 == v && w2 < who)) {
+        v = v2;
+        who = w2;
+      }
+    }
+    pivlane[k] = who;
+    const bool step = k < T;
+    if (step && !(v > Real(0))) singular = true;
+    const Real pk = __shfl_sync(0xffffffffu, a[k], who, G);
+    const Real pb = __shfl_sync(0xffffffffu, b, who, G);
+    const bool upd = step && !done && p != who && pk != Real(0);
+    const Real l = upd ? a[k] / pk : Real(0);
+    if (step && p == who) {
+      done = true;
+      mystep = k;
+    }
+#pragma unroll
+    for (int j = k + 1; j < G; ++j) {
+      const Real pj = __shfl_sync(0xffffffffu, a[j], who, G);
+      a[j] -= l * pj;
+    }
+    b -= l * pb;
+  }
+  // back substitution (right-looking): x_k from the lane that pivoted step k
+  Real myx = 0;
+#pragma unroll
+  for (int k = G - 1; k >= 0; --k) {
+    const int own = pivlane[k];
+    Real xk = (p == own && a[k] != Real(0)) ? b / a[k] : Real(0);
+    xk = __shfl_sync(0xffffffffu, xk, own, G);
+    if (k < T) {
+      if (p == k) myx = xk;
+      if (mystep >= 0 && mystep < k) b -= a[k] * xk;
+    }
+  }
+  // any lane of the group may have flagged a zero pivot (ballot before any exit)
+  const bool sing = (__ballot_sync(0xffffffffu, singular) & gmask) != 0;
+  if (!live) return;
+  if (p < T) Zval[base + p + (p >= d ? 1 : 0)] = sing ? 0.0 : (double)myx;
+  if (p == 0) {
+    Zval[base + d] = 1.0;
+    if (sing) atomicAdd(nsingular, 1ull);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// CTA path: one system per block of TMAX threads, T <= TMAX (64 or 128); the matrix
+// lives in shared memory, thread r owns row r.
+// ------------------------------------------------------------------------------------
+template <class Real, int TMAX>
+__global__ void __launch_bounds__(TMAX)
+lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
+           const double* __restrict__ Aval, const int* __restrict__ Zrp,
+           const int* __restrict__ Zcol, const int* __restrict__ cpts,
+           const int* __restrict__ work, double* __restrict__ Zval,
+           unsigned long long* __restrict__ nsingular) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int PITCH = TMAX + 1;
+  Real* tile = reinterpret_cast<Real*>(smem_raw);                 // TMAX x PITCH
+  Real* rhs = tile + TMAX * PITCH;                                  // TMAX
+  Real* xs = rhs + TMAX;                                            // TMAX
+  int* zl = reinterpret_cast<int*>(xs + TMAX);                      // TMAX
+  int* steprow = zl + TMAX;                                         // TMAX
+  __shared__ Real red_v[TMAX / 32];
+  __shared__ int red_w[TMAX / 32];
+  __shared__ int s_piv, s_d, s_sing;
+
+  const int t = threadIdx.x;
+  const int lane = t & 31, wid = t >> 5;
+  const int r = work[blockIdx.x];
+  const int i = cpts[r];
+  const int base = Zrp[r];
+  const int len = Zrp[r + 1] - base;
+  const int T = len - 1;
+  if (t == 0) {
+    s_d = T;  // position TMAX (unseen by the threads) only when T == TMAX
+    s_sing = 0;
+  }
+  __syncthreads();
+  if (t < len && Zcol[base + t] == i) s_d = t;
+  __syncthreads();
+  const int d = s_d;
+  if (t < T) zl[t] = Zcol[base + t + (t >= d ? 1 : 0)];
+  Real* row = tile + t * PITCH;
+  for (int q = 0; q < TMAX; ++q) row[q] = Real(0);
+  rhs[t] = Real(0);
+  __syncthreads();
+  if (t < T) {
+    const int l = zl[t];
+    for (int e = Arp[l]; e < Arp[l + 1]; ++e) {
+      const int c = Acol[e];
+      if (c == i) {
+        rhs[t] = Real(-Aval[e]);
+      } else {
+        const int q = find_sorted(zl, T, c);
+        if (q >= 0) row[q] = Real(Aval[e]);
+      }
+    }
+  }
+  bool done = t >= T;
+  int mystep = -1;
+  __syncthreads();
+  for (int k = 0; k < T; ++k) {
+    Real v = done ? Real(-1) : (row[k] < 0 ? -row[k] : row[k]);
+    int who = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      Real v2 = __shfl_xor_sync(0xffffffffu, v, o);
+      int w2 = __shfl_xor_sync(0xffffffffu, who, o);
+      if (v2 > v || (v2 == v && w2 < who)) {
+        v = v2;
+        who = w2;
+      }
+    }
+    if (lane == 0) {
+      red_v[wid] = v;
+      red_w[wid] = who;
+    }
+    __syncthreads();
+    if (t == 0) {
+      Real bv = red_v[0];
+      int bw = red_w[0];
+      for (int w = 1; w < TMAX / 32; ++w)
+        if (red_v[w] > bv || (red_v[w] == bv && red_w[w] < bw)) {
+          bv = red_v[w];
+          bw = red_w[w];
+        }
+      s_piv = bw;
+      steprow[k] = bw;
+      if (!(bv > Real(0))) s_sing = 1;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    const Real* prow = tile + piv * PITCH;
+    const Real pk = prow[k];
+    if (t == piv) {
+      done = true;
+      mystep = k;
+    } else if (!done && pk != Real(0)) {
+      const Real l = row[k] / pk;
+      for (int j = k + 1; j < T; ++j) row[j] -= l * prow[j];
+      rhs[t] -= l * rhs[piv];
+    }
+    __syncthreads();
+  }
+  for (int k = T - 1; k >= 0; --k) {
+    const int own = steprow[k];
+    if (t == own) xs[k] = row[k] != Real(0) ? rhs[t] / row[k] : Real(0);
+    __syncthreads();
+    const Real xk = xs[k];
+    if (mystep >= 0 && mystep < k) rhs[t] -= row[k] * xk;
+    __syncthreads();
+  }
+  const bool sing = s_sing != 0;
+  if (t < T) Zval[base + t + (t >= d ? 1 : 0)] = sing ? 0.0 : (double)xs[t];
+  if (t == 0) {
+    Zval[base + d] = 1.0;
+    if (sing) atomicAdd(nsingular, 1ull);
+  }
+}
+
+template <class Real, int TMAX>
+static size_t cta_smem() {
+  return sizeof(Real) * ((size_t)TMAX * (TMAX + 1) + 2 * TMAX) + sizeof(int) * 2 * TMAX;
+}
+
+// ------------------------------------------------------------------------------------
+// Bucketing and the projection.
+// ------------------------------------------------------------------------------------
+// work[0..2] = sum T^3, T^2, T; work[3] = A entries gathered (row lengths of the pattern's
+// F-points in Ahat)
+__global__ void bucket_rows(const int* __restrict__ Zrp, int nc, int* __restrict__ lists,
+                            int* __restrict__ counts, double* __restrict__ Zval,
+                            const int* __restrict__ Zcol, const int* __restrict__ cpts,
+                            const int* __restrict__ Arp, int* __restrict__ too_big,
+                            unsigned long long* __restrict__ work) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nc) return;
+  const int T = Zrp[r + 1] - Zrp[r] - 1;
+  if (T <= 0) {
+    if (T == 0) Zval[Zrp[r]] = 1.0;  // only the identity entry
+    return;
+  }
+  const int b = ls_bucket(T);
+  if (b >= 5) {
+    atomicAdd(too_big, 1);
+    return;
+  }
+  const int pos = atomicAdd(&counts[b], 1);
+  lists[(long long)b * nc + pos] = r;
+  unsigned long long g = 0;
+  for (int e = Zrp[r]; e < Zrp[r + 1]; ++e) {
+    const int l = Zcol[e];
+    if (l != cpts[r]) g += (unsigned long long)(Arp[l + 1] - Arp[l]);
+  }
+  const unsigned long long t = (unsigned long long)T;
+  atomicAdd(&work[0], t * t * t);
+  atomicAdd(&work[1], t * t);
+  atomicAdd(&work[2], t);
+  atomicAdd(&work[3], g);
+}
+
+// Projection on the transposed weights: rows are fine points j, entries (j, coarse i).
+template <int W>
+__global__ void project_rows(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
+                             double* __restrict__ Wval, int n, const signed char* __restrict__ cf,
+                             const double* __restrict__ Bc, const double* __restrict__ B,
+                             unsigned long long* __restrict__ nempty) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int j = (int)(t / W), lane = (int)(t % W);
+  // C rows hold the identity entry only; no early exit before the shuffles
+  const bool ok = j < n && !cf[j];
+  const int b = ok ? Wrp[j] : 0, e = ok ? Wrp[j + 1] : 0;
+  double g = 0.0, s = 0.0;
+  for (int k = b + lane; k < e; k += W) {
+    const double bc = Bc[Wcol[k]];
+    g += bc * bc;
+    s += Wval[k] * bc;
+  }
+  g = group_sum<W>(g);
+  s = group_sum<W>(s);
+  if (!ok) return;
+  if (g > 0.0) {
+    const double mu = (s - B[j]) / g;
+    for (int k = b + lane; k < e; k += W) Wval[k] -= mu * Bc[Wcol[k]];
+  } else if (lane == 0) {
+    atomicAdd(nempty, 1ull);
+  }
+}
+
+__global__ void coarse_of(const signed char* __restrict__ cf, const int* __restrict__ cidx_incl,
+                          int n, int* __restrict__ cpts) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n && cf[j]) cpts[cidx_incl[j]] = j;
+}
+
+__global__ void cf_to_int(const signed char* __restrict__ cf, int n, int* __restrict__ out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = cf[j] ? 1 : 0;
+}
+
+// cpts[k] = fine index of the k-th C-point; returns nc.
+int coarse_points(const signed char* cf, int n, int** cpts_out, cudaStream_t s) {
+  int* flag = dalloc<int>(n, s);
+  int* pre = dalloc<int>(n + 1, s);
+  if (n) cf_to_int<<<ceil_div(n, 256), 256, 0, s>>>(cf, n, flag); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int nc = (int)exclusive_scan(flag, pre, n, s, true);
+  int* cpts = dalloc<int>(nc, s);
+  if (n) coarse_of<<<ceil_div(n, 256), 256, 0, s>>>(cf, pre, n, cpts); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  dfree(flag, s);
+  dfree(pre, s);
+  *cpts_out = cpts;
+  return nc;
+}
+
+template <class Real>
+static void launch_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* cpts,
+                          const int* lists, const int* counts_h, int nc, double* Zval,
+                          unsigned long long* nsing, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)cta_smem<Real, 64>()));
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)cta_smem<Real, 128>()));
+    attr = true;
+  }
+  const int per_block[3] = {LS_WARPS * 4, LS_WARPS * 2, LS_WARPS};
+  if (counts_h[0])
+    lsolve_group<Real, 8><<<ceil_div(counts_h[0], per_block[0]), 32 * LS_WARPS, 0, s>>>(
+        Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts, lists + 0LL * nc, counts_h[0], Zval, nsing); ::clair::count_launch();
+  if (counts_h[1])
+    lsolve_group<Real, 16><<<ceil_div(counts_h[1], per_block[1]), 32 * LS_WARPS, 0, s>>>(
+        Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts, lists + 1LL * nc, counts_h[1], Zval, nsing); ::clair::count_launch();
+  if (counts_h[2])
+    lsolve_group<Real, 32><<<ceil_div(counts_h[2], per_block[2]), 32 * LS_WARPS, 0, s>>>(
+        Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts, lists + 2LL * nc, counts_h[2], Zval, nsing); ::clair::count_launch();
+  if (counts_h[3])
+    lsolve_cta<Real, 64><<<counts_h[3], 64, cta_smem<Real, 64>(), s>>>(
+        Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts, lists + 3LL * nc, Zval, nsing); ::clair::count_launch();
+  if (counts_h[4])
+    lsolve_cta<Real, 128><<<counts_h[4], 128, cta_smem<Real, 128>(), s>>>(
+        Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts, lists + 4LL * nc, Zval, nsing); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+}
+
+// Local lAIR solves for all coarse rows of the pattern Z (nc x n), values into Zval.
+void local_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* cpts, int nc,
+                  int precision, double* Zval, LocalStats& st, cudaStream_t s) {
+  int* lists = dalloc<int>((long long)LS_BUCKETS * std::max(nc, 1), s);
+  int* counts = dalloc<int>(LS_BUCKETS + 1, s);
+  unsigned long long* nsing = dalloc<unsigned long long>(5, s);  // [0] singular, [1..4] work
+  CLAIR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * (LS_BUCKETS + 1), s));
+  CLAIR_CUDA(cudaMemsetAsync(nsing, 0, 5 * sizeof(unsigned long long), s));
+  if (nc) bucket_rows<<<ceil_div(nc, 256), 256, 0, s>>>(Zrp, nc, lists, counts, Zval, Zcol, cpts,
+                                                        Ahat.rowptr, counts + LS_BUCKETS,
+                                                        nsing + 1); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int counts_h[LS_BUCKETS + 1];
+  CLAIR_CUDA(cudaMemcpyAsync(counts_h, counts, sizeof(counts_h), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  CLAIR_REQUIRE(counts_h[LS_BUCKETS] == 0, CLAIR_ERR_CAPACITY,
+                "%d local systems larger than 128 unknowns", counts_h[LS_BUCKETS]);
+  {
+    ClockScope clk(PH_LSOLVE, s);
+    if (precision == CLAIR_MIXED)
+      launch_solves<float>(Ahat, Zrp, Zcol, cpts, lists, counts_h, nc, Zval, nsing, s);
+    else
+      launch_solves<double>(Ahat, Zrp, Zcol, cpts, lists, counts_h, nc, Zval, nsing, s);
+  }
+  unsigned long long h[5] = {0, 0, 0, 0, 0};
+  CLAIR_CUDA(cudaMemcpyAsync(h, nsing, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  st.singular += (long long)h[0];
+  st.sum_t3 += (double)h[1];
+  st.sum_t2 += (double)h[2];
+  st.sum_t += (double)h[3];
+  st.gathered += (long long)h[4];
+  for (int b = 0; b < LS_BUCKETS; ++b) st.hist[b] += counts_h[b];
+  dfree(lists, s);
+  dfree(counts, s);
+  dfree(nsing, s);
+}
+
+// Projection of the transposed weights Wt (rows = fine points) onto the constraint.
+void project_constraint(Csr& Wt, const signed char* cf, const double* Bc, const double* B,
+                        LocalStats& st, cudaStream_t s) {
+  unsigned long long* nempty = dalloc<unsigned long long>(1, s);
+  CLAIR_CUDA(cudaMemsetAsync(nempty, 0, sizeof(unsigned long long), s));
+  if (Wt.rows) {
+    constexpr int W = 8;
+    project_rows<W><<<ceil_div((long long)Wt.rows * W, 256), 256, 0, s>>>(
+        Wt.rowptr, Wt.col, Wt.val, Wt.rows, cf, Bc, B, nempty); ::clair::count_launch();
+  }
+  CLAIR_LAUNCHED();
+  unsigned long long h = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&h, nempty, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  st.empty += (long long)h;
+  dfree(nempty, s);
+}
+
+// Full transfer-weight computation: local solves on Ahat over pattern Z (nc x n), then the
+// projection.  On return Z.val holds the projected weights (row = coarse point) and, if
+// keep_t is set, Zt receives the transposed operator (rows = fine points) with the same
+// projected values.
+void transfer_weights(const Csr& Ahat, const signed char* cf, const int* cpts, Csr& Z,
+                      const double* B, int precision, LocalStats& st, Csr* keep_t,
+                      cudaStream_t s) {
+  const int nc = Z.rows;
+  if (!Z.val) Z.val = dalloc<double>(Z.nnz, s);
+  local_solves(Ahat, Z.rowptr, Z.col, cpts, nc, precision, Z.val, st, s);
+  ClockScope clk(PH_PROJECT, s);
+  Csr Zt;
+  int* perm = nullptr;
+  csr_transpose(Z, Zt, &perm, s);
+  double* Bc = dalloc<double>(nc, s);
+  gather(B, cpts, Bc, nc, s);
+  project_constraint(Zt, cf, Bc, B, st, s);
+  scatter_vals(Zt.val, perm, Z.val, Z.nnz, s);
+  dfree(Bc, s);
+  dfree(perm, s);
+  if (keep_t)
+    *keep_t = Zt;
+  else
+    Zt.release(s);
+}
+
+}  // namespace clair

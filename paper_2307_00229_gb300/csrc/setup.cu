@@ -1,0 +1,571 @@
+// Setup kernels of the CLAIR hierarchy (one level at a time):
+//  * classical strength of connection (absolute values, Section 3.1.3) as masks over A
+//    and A^T,
+//  * the C/F splitting: a deterministic parallel independent-set reading of the
+//    Ruge-Stueben first pass ("FC"), keyed by (lambda_i, lowbias32(i)),
+//  * the sparsity pattern W = pattern(((S + I)^{m-1} T)|_F) of Algorithm 1 for m <= 2,
+//  * the relaxation weight 1/rho(D^-1 A) from Arnoldi (Section 4), with a Francis
+//    double-shift QR for the Ritz values,
+//  * weighted Jacobi on the C or F subset (CFF / FFC, Section 4; also smooths B),
+//  * the dense inverse of the coarsest operator.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "hessenberg.cuh"
+
+namespace clair {
+
+// ------------------------------------------------------------------------------------
+// Strength masks.  mode 0: entry (r, c) of M is strong iff |m_rc| >= theta * thr[r]
+// (row-relative, thr = row maxima of M); mode 1: iff |m_rc| >= theta * thr[c]
+// (column-relative: thr = row maxima of M^T).  Diagonal and zero entries are never strong.
+// ------------------------------------------------------------------------------------
+__global__ void strength_mask(const int* __restrict__ rowptr, const int* __restrict__ col,
+                              const double* __restrict__ val, int rows,
+                              const double* __restrict__ thr, double theta, int mode,
+                              unsigned char* __restrict__ mask) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+    const int c = col[e];
+    const double a = fabs(val[e]);
+    const double t = theta * (mode == 0 ? thr[r] : thr[c]);
+    mask[e] = (c != r && a > 0.0 && a >= t) ? 1 : 0;
+  }
+}
+
+void strength(const Csr& M, const double* thr, double theta, int mode, unsigned char* mask,
+              cudaStream_t s) {
+  if (!M.rows) return;
+  strength_mask<<<ceil_div(M.rows, 256), 256, 0, s>>>(M.rowptr, M.col, M.val, M.rows, thr, theta,
+                                                      mode, mask); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+}
+
+// ------------------------------------------------------------------------------------
+// C/F splitting.  sA: mask of S over A's entries (row i of A: S_ij, i depends on j);
+// sAt: mask over A^T's entries (row i of A^T: S_ji, j depends on i).
+// state: 0 undecided, 1 C, 2 F.
+// ------------------------------------------------------------------------------------
+enum : signed char { ST_U = 0, ST_C = 1, ST_F = 2 };
+
+__global__ void pmis_init(const int* __restrict__ Atrp, const unsigned char* __restrict__ sAt,
+                          int n, unsigned long long* __restrict__ key,
+                          signed char* __restrict__ state, int* __restrict__ mark) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned lam = 0;
+  for (int e = Atrp[i]; e < Atrp[i + 1]; ++e) lam += sAt[e];
+  key[i] = ((unsigned long long)lam << 32) | lowbias32((uint32_t)i);
+  state[i] = lam == 0 ? ST_F : ST_U;
+  mark[i] = -1;
+}
+
+// An undecided point whose key exceeds every undecided strong neighbour's becomes C.
+__global__ void pmis_select(const int* __restrict__ Arp, const int* __restrict__ Acol,
+                            const unsigned char* __restrict__ sA, const int* __restrict__ Atrp,
+                            const int* __restrict__ Atcol, const unsigned char* __restrict__ sAt,
+                            int n, const unsigned long long* __restrict__ key,
+                            const signed char* __restrict__ state, int* __restrict__ mark,
+                            int round) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || state[i] != ST_U) return;
+  const unsigned long long k = key[i];
+  for (int e = Arp[i]; e < Arp[i + 1]; ++e)
+    if (sA[e]) {
+      const int j = Acol[e];
+      if (state[j] == ST_U && key[j] > k) return;
+    }
+  for (int e = Atrp[i]; e < Atrp[i + 1]; ++e)
+    if (sAt[e]) {
+      const int j = Atcol[e];
+      if (state[j] == ST_U && key[j] > k) return;
+    }
+  mark[i] = round;
+}
+
+// New C-points are fixed; undecided points strongly depending on one become F.
+__global__ void pmis_update(const int* __restrict__ Arp, const int* __restrict__ Acol,
+                            const unsigned char* __restrict__ sA, int n,
+                            const int* __restrict__ mark, signed char* __restrict__ state,
+                            int round, int* __restrict__ remaining) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || state[i] != ST_U) return;
+  if (mark[i] == round) {
+    state[i] = ST_C;
+    return;
+  }
+  for (int e = Arp[i]; e < Arp[i + 1]; ++e)
+    if (sA[e] && mark[Acol[e]] == round) {
+      state[i] = ST_F;
+      return;
+    }
+  atomicAdd(remaining, 1);
+}
+
+// F-points with a strong dependence but none on a C-point.
+__global__ void pmis_fixup_find(const int* __restrict__ Arp, const int* __restrict__ Acol,
+                                const unsigned char* __restrict__ sA, int n,
+                                const signed char* __restrict__ state, int* __restrict__ mark) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  mark[i] = 0;
+  if (state[i] != ST_F) return;
+  bool has = false, hasc = false;
+  for (int e = Arp[i]; e < Arp[i + 1]; ++e)
+    if (sA[e]) {
+      has = true;
+      if (state[Acol[e]] == ST_C) hasc = true;
+    }
+  if (has && !hasc) mark[i] = 1;
+}
+
+__global__ void pmis_finish(int n, const int* __restrict__ mark, const signed char* __restrict__ state,
+                            signed char* __restrict__ cf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cf[i] = (state[i] == ST_C || mark[i] == 1) ? 1 : 0;
+}
+
+void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsigned char* sAt,
+              signed char* cf, cudaStream_t s) {
+  const int n = A.rows;
+  if (!n) return;
+  unsigned long long* key = dalloc<unsigned long long>(n, s);
+  signed char* state = dalloc<signed char>(n, s);
+  int* mark = dalloc<int>(n, s);
+  int* remaining = dalloc<int>(1, s);
+  const int g = ceil_div(n, 256);
+  pmis_init<<<g, 256, 0, s>>>(At.rowptr, sAt, n, key, state, mark); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  for (int round = 0;; ++round) {
+    CLAIR_REQUIRE(round < 10000, CLAIR_ERR_CAPACITY, "C/F splitting did not terminate");
+    CLAIR_CUDA(cudaMemsetAsync(remaining, 0, sizeof(int), s));
+    pmis_select<<<g, 256, 0, s>>>(A.rowptr, A.col, sA, At.rowptr, At.col, sAt, n, key, state, mark,
+                                  round); ::clair::count_launch();
+    pmis_update<<<g, 256, 0, s>>>(A.rowptr, A.col, sA, n, mark, state, round, remaining); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+    int h = 0;
+    CLAIR_CUDA(cudaMemcpyAsync(&h, remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    if (h == 0) break;
+  }
+  pmis_fixup_find<<<g, 256, 0, s>>>(A.rowptr, A.col, sA, n, state, mark); ::clair::count_launch();
+  pmis_finish<<<g, 256, 0, s>>>(n, mark, state, cf); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  dfree(key, s);
+  dfree(state, s);
+  dfree(mark, s);
+  dfree(remaining, s);
+}
+
+// ------------------------------------------------------------------------------------
+// Pattern of Algorithm 1 for the operator Ahat, walked on Ahat^T (= Wm): the column of
+// coarse point i collects the F-points j with S_ji (row i of Wm, strong in the column-
+// relative sense) and, for m = 2, the F-points j with S_jk for such an F-point k.  The C
+// column itself is added so every row carries its identity entry.  One warp per coarse
+// point with a shared-memory hash set; COUNT = true writes the row length, otherwise
+// the sorted row.
+// ------------------------------------------------------------------------------------
+constexpr int PT_CAP = 1024;
+constexpr int PT_WARPS = 4;
+
+__device__ __forceinline__ int pt_hash(int key) {
+  return (int)(((unsigned)key * 2654435761u) & (unsigned)(PT_CAP - 1));
+}
+
+__device__ __forceinline__ void pt_insert(int* keys, int key, int* fresh, int* err) {
+  int h = pt_hash(key);
+  for (int probe = 0; probe < PT_CAP; ++probe) {
+    int prev = atomicCAS(&keys[h], -1, key);
+    if (prev == -1) {
+      ++*fresh;
+      return;
+    }
+    if (prev == key) return;
+    h = (h + 1) & (PT_CAP - 1);
+  }
+  atomicExch(err, 1);
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(32 * PT_WARPS)
+pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
+               const unsigned char* __restrict__ sW, const signed char* __restrict__ cf,
+               const int* __restrict__ cpts, int nc, int degree, int* __restrict__ count,
+               const int* __restrict__ Zrp, int* __restrict__ Zcol, int* __restrict__ err) {
+  __shared__ int keys[PT_WARPS][PT_CAP];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * PT_WARPS + w;
+  if (r >= nc) return;  // warp-uniform
+  int* K = keys[w];
+  for (int t = lane; t < PT_CAP; t += 32) K[t] = -1;
+  __syncwarp();
+  const int i = cpts[r];
+  int fresh = 0;
+  if (lane == 0) pt_insert(K, i, &fresh, err);
+  for (int e = Wrp[i] + lane; e < Wrp[i + 1]; e += 32)
+    if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], &fresh, err);
+  if (degree >= 2) {
+    // second hop from every first-hop F-point, one first-hop point at a time
+    for (int e1 = Wrp[i]; e1 < Wrp[i + 1]; ++e1) {
+      const int k = Wcol[e1];
+      if (!sW[e1] || cf[k]) continue;
+      for (int e = Wrp[k] + lane; e < Wrp[k + 1]; e += 32)
+        if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], &fresh, err);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fresh += __shfl_xor_sync(0xffffffffu, fresh, o);
+  if (COUNT) {
+    if (lane == 0) count[r] = fresh;
+    return;
+  }
+  // compact occupied slots in place (reads of a chunk precede its writes), then rank-sort
+  int total = 0;
+  for (int c = 0; c < PT_CAP; c += 32) {
+    const int v = K[c + lane];
+    const unsigned occ = __ballot_sync(0xffffffffu, v >= 0);
+    __syncwarp();
+    if (v >= 0) K[total + __popc(occ & ((1u << lane) - 1u))] = v;
+    total += __popc(occ);
+    __syncwarp();
+  }
+  const int base = Zrp[r];
+  for (int t = lane; t < total; t += 32) {
+    const int v = K[t];
+    int rank = 0;
+    for (int u = 0; u < total; ++u) rank += K[u] < v;
+    Zcol[base + rank] = v;
+  }
+}
+
+// Builds the pattern CSR Z (nc rows) for Algorithm 1 on Ahat, walking Wm = Ahat^T with
+// its strength mask sW.
+void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf, const int* cpts,
+                   int nc, int n, int degree, Csr& Z, cudaStream_t s) {
+  CLAIR_REQUIRE(degree == 1 || degree == 2, CLAIR_ERR_UNSUPPORTED,
+                "pattern degree %d not supported (1 or 2)", degree);
+  Z.rows = nc;
+  Z.cols = n;
+  int* count = dalloc<int>(nc + 1, s);
+  int* err = dalloc<int>(1, s);
+  CLAIR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  const int g = ceil_div(nc, PT_WARPS);
+  if (nc)
+    pattern_kernel<true><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc, degree,
+                                                     count, nullptr, nullptr, err); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  Z.rowptr = dalloc<int>(nc + 1, s);
+  Z.nnz = (int)exclusive_scan(count, Z.rowptr, nc, s, true);
+  Z.col = dalloc<int>(Z.nnz, s);
+  if (nc)
+    pattern_kernel<false><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc, degree,
+                                                      nullptr, Z.rowptr, Z.col, err); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int h = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  dfree(count, s);
+  dfree(err, s);
+  CLAIR_REQUIRE(h == 0, CLAIR_ERR_CAPACITY, "pattern row exceeds %d entries", PT_CAP);
+}
+
+// ------------------------------------------------------------------------------------
+// Weighted Jacobi on the subset {cf == which}: x_out = x_in + omega D^-1 (b - A x_in) on
+// the subset, x_out = x_in elsewhere (b = NULL means a zero right-hand side).
+// ------------------------------------------------------------------------------------
+template <int W, class T>
+__global__ void jacobi_kernel(const int* __restrict__ rowptr, const int* __restrict__ col,
+                              const T* __restrict__ val, const T* __restrict__ dinv, int rows,
+                              const signed char* __restrict__ cf, int which, T omega,
+                              const T* __restrict__ b, const T* __restrict__ xin,
+                              T* __restrict__ xout) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int r = (int)(t / W), lane = (int)(t % W);
+  const bool ok = r < rows;
+  const bool act = ok && cf[r] == which;
+  T acc = 0;
+  if (act)
+    for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += W) acc += val[e] * __ldg(&xin[col[e]]);
+  acc = group_sum<W>(acc);
+  if (ok && lane == 0) {
+    const T xr = xin[r];
+    xout[r] = act ? xr + omega * dinv[r] * ((b ? b[r] : T(0)) - acc) : xr;
+  }
+}
+
+// First sweep of a cycle from x = 0: x = omega D^-1 b on the subset, 0 elsewhere.
+template <class T>
+__global__ void jacobi_first(const T* __restrict__ dinv, int rows, const signed char* __restrict__ cf,
+                             int which, T omega, const T* __restrict__ b, T* __restrict__ x) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
+       r += (long long)gridDim.x * blockDim.x)
+    x[r] = cf[r] == which ? omega * dinv[r] * b[r] : T(0);
+}
+
+static int lanes_of(const Csr& A) {
+  double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
+  int w = 2;
+  while (w < 32 && w < avg) w <<= 1;
+  return w;
+}
+
+#define CLAIR_DISPATCH_W2(W, ...)                            \
+  switch (W) {                                               \
+    case 2: { constexpr int WW = 2; __VA_ARGS__; ::clair::count_launch(); } break;   \
+    case 4: { constexpr int WW = 4; __VA_ARGS__; ::clair::count_launch(); } break;   \
+    case 8: { constexpr int WW = 8; __VA_ARGS__; ::clair::count_launch(); } break;   \
+    case 16: { constexpr int WW = 16; __VA_ARGS__; ::clair::count_launch(); } break; \
+    default: { constexpr int WW = 32; __VA_ARGS__; ::clair::count_launch(); } break; \
+  }
+
+template <class T>
+void jacobi(const Csr& A, const T* vals, const T* dinv, const signed char* cf, int which, T omega,
+            const T* b, const T* xin, T* xout, cudaStream_t s) {
+  if (!A.rows) return;
+  const int W = lanes_of(A);
+  const int blocks = ceil_div((long long)A.rows * W, 256);
+  CLAIR_DISPATCH_W2(W, (jacobi_kernel<WW, T><<<blocks, 256, 0, s>>>(A.rowptr, A.col, vals, dinv,
+                                                                    A.rows, cf, which, omega, b,
+                                                                    xin, xout)));
+  CLAIR_LAUNCHED();
+}
+template void jacobi<double>(const Csr&, const double*, const double*, const signed char*, int,
+                             double, const double*, const double*, double*, cudaStream_t);
+template void jacobi<float>(const Csr&, const float*, const float*, const signed char*, int, float,
+                            const float*, const float*, float*, cudaStream_t);
+
+template <class T>
+void jacobi_from_zero(int rows, const T* dinv, const signed char* cf, int which, T omega,
+                      const T* b, T* x, cudaStream_t s) {
+  if (!rows) return;
+  jacobi_first<T><<<std::min(ceil_div(rows, 256), 32 * sm_count()), 256, 0, s>>>(dinv, rows, cf,
+                                                                                 which, omega, b, x); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+}
+template void jacobi_from_zero<double>(int, const double*, const signed char*, int, double,
+                                       const double*, double*, cudaStream_t);
+template void jacobi_from_zero<float>(int, const float*, const signed char*, int, float, const float*,
+                                      float*, cudaStream_t);
+
+// ------------------------------------------------------------------------------------
+// Relaxation weight: Arnoldi on D^-1 A (classical Gram-Schmidt applied twice), start
+// vector splitmix64 in [-1, 1) seeded with `seed`; rho = max |Ritz value|.
+// ------------------------------------------------------------------------------------
+__global__ void arnoldi_start(double* __restrict__ v, int n, uint64_t seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    v[i] = splitmix_pm1(seed, (uint64_t)i);
+}
+
+__global__ void scale_by_inv_sqrt(double* __restrict__ v, int n, const double* __restrict__ nrm2) {
+  const double s = 1.0 / sqrt(*nrm2);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    v[i] *= s;
+}
+
+__global__ void dinv_scale(double* __restrict__ w, const double* __restrict__ dinv, int n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    w[i] *= dinv[i];
+}
+
+// After the two projection passes: H[:, j] = h1 + h2, H[j+1, j] = ||w||, breakdown test,
+// v_{j+1} scale.  state[0] = active steps (m until breakdown), state scalars in dev.
+__global__ void arnoldi_column(double* __restrict__ H, int ldh, int j, const double* __restrict__ h1,
+                               const double* __restrict__ h2, const double* __restrict__ wn2,
+                               const double* __restrict__ w0n2, int* __restrict__ steps,
+                               double* __restrict__ inv_norm) {
+  if (threadIdx.x != 0) return;
+  const bool active = *steps < 0;  // -1 while no breakdown
+  for (int i = 0; i <= j; ++i) H[i + (long long)j * ldh] = active ? h1[i] + h2[i] : 0.0;
+  const double hn = sqrt(*wn2);
+  H[j + 1 + (long long)j * ldh] = active ? hn : 0.0;
+  if (active && hn <= 1e-10 * sqrt(*w0n2)) *steps = j + 1;
+  *inv_norm = (active && hn > 0.0) ? 1.0 / hn : 0.0;
+}
+
+__global__ void scale_vec(const double* __restrict__ w, double* __restrict__ v, int n,
+                          const double* __restrict__ s) {
+  const double f = *s;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    v[i] = w[i] * f;
+}
+
+__global__ void ritz_kernel(double* __restrict__ H, int ldh, int m, const int* __restrict__ steps,
+                            double* __restrict__ omega) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = *steps < 0 ? m : *steps;
+  const double rho = hessenberg_spectral_radius(H, ldh, k);
+  *omega = rho > 0.0 ? 1.0 / rho : 1.0;
+}
+
+// omega = 1 / rho(D^-1 A) (device scalar *omega_dev); returns it on the host.
+double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed,
+                      double* omega_dev, cudaStream_t s) {
+  const int n = A.rows;
+  const int m = std::max(1, std::min(iters, n));
+  const int ldh = m + 1;
+  double* V = dalloc<double>((size_t)(m + 1) * n, s);
+  double* w = dalloc<double>(n, s);
+  double* H = dalloc<double>((size_t)ldh * m, s);
+  double* sc = dalloc<double>(2 * 64 + 8, s);  // h1[64], h2[64], wn2, w0n2, inv
+  double* h1 = sc;
+  double* h2 = sc + 64;
+  double* wn2 = sc + 128;
+  double* w0n2 = sc + 129;
+  double* inv = sc + 130;
+  int* steps = dalloc<int>(1, s);
+  double* partial = dalloc<double>((size_t)partial_blocks() * (m + 2), s);
+  const int grid = std::min(ceil_div(n, 256), 32 * sm_count());
+  CLAIR_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * ldh * m, s));
+  const int minus1 = -1;
+  CLAIR_CUDA(cudaMemcpyAsync(steps, &minus1, sizeof(int), cudaMemcpyHostToDevice, s));
+  arnoldi_start<<<grid, 256, 0, s>>>(V, n, seed); ::clair::count_launch();
+  multi_dot(V, 1, V, n, wn2, partial, s);
+  scale_by_inv_sqrt<<<grid, 256, 0, s>>>(V, n, wn2); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  for (int j = 0; j < m; ++j) {
+    double* vj = V + (size_t)j * n;
+    spmv(A, vj, w, 1.0, 0.0, s);
+    dinv_scale<<<grid, 256, 0, s>>>(w, dinv, n); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+    multi_dot(w, 1, w, n, w0n2, partial, s);
+    multi_dot(V, j + 1, w, n, h1, partial, s);
+    multi_axpy(V, j + 1, h1, w, n, s);
+    multi_dot(V, j + 1, w, n, h2, partial, s);
+    multi_axpy(V, j + 1, h2, w, n, s);
+    multi_dot(w, 1, w, n, wn2, partial, s);
+    arnoldi_column<<<1, 32, 0, s>>>(H, ldh, j, h1, h2, wn2, w0n2, steps, inv); ::clair::count_launch();
+    scale_vec<<<grid, 256, 0, s>>>(w, V + (size_t)(j + 1) * n, n, inv); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+  }
+  ritz_kernel<<<1, 32, 0, s>>>(H, ldh, m, steps, omega_dev); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  double om = 1.0;
+  CLAIR_CUDA(cudaMemcpyAsync(&om, omega_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  dfree(V, s);
+  dfree(w, s);
+  dfree(H, s);
+  dfree(sc, s);
+  dfree(steps, s);
+  dfree(partial, s);
+  return om;
+}
+
+// ------------------------------------------------------------------------------------
+// Coarsest level: dense inverse by Gauss-Jordan elimination with partial pivoting (one
+// block; n <= a few hundred).  M is n x n column-major in global memory, overwritten.
+// ------------------------------------------------------------------------------------
+__global__ void csr_to_dense(const int* __restrict__ rowptr, const int* __restrict__ col,
+                             const double* __restrict__ val, int n, double* __restrict__ M) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  for (int c = 0; c < n; ++c) M[r + (long long)c * n] = 0.0;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) M[r + (long long)col[e] * n] = val[e];
+}
+
+__global__ void gauss_jordan(double* __restrict__ M, double* __restrict__ Inv, int n,
+                             int* __restrict__ singular) {
+  // Inv starts as identity; row operations on [M | Inv].
+  __shared__ int s_piv;
+  __shared__ double s_pv;
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int idx = t; idx < n * n; idx += nt) Inv[idx] = (idx % n == idx / n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (t == 0) {
+      int p = k;
+      double best = fabs(M[k + (long long)k * n]);
+      for (int r = k + 1; r < n; ++r) {
+        const double v = fabs(M[r + (long long)k * n]);
+        if (v > best) {
+          best = v;
+          p = r;
+        }
+      }
+      s_piv = p;
+      s_pv = M[p + (long long)k * n];
+      if (best == 0.0) *singular = 1;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != k)
+      for (int c = t; c < n; c += nt) {
+        double a = M[k + (long long)c * n];
+        M[k + (long long)c * n] = M[p + (long long)c * n];
+        M[p + (long long)c * n] = a;
+        double b = Inv[k + (long long)c * n];
+        Inv[k + (long long)c * n] = Inv[p + (long long)c * n];
+        Inv[p + (long long)c * n] = b;
+      }
+    __syncthreads();
+    const double pv = s_pv;
+    for (int c = t; c < n; c += nt) {
+      if (pv != 0.0) {
+        M[k + (long long)c * n] /= pv;
+        Inv[k + (long long)c * n] /= pv;
+      }
+    }
+    __syncthreads();
+    // eliminate column k from every other row (rows split over threads)
+    for (int r = t; r < n; r += nt) {
+      if (r == k) continue;
+      const double f = M[r + (long long)k * n];
+      if (f == 0.0) continue;
+      for (int c = 0; c < n; ++c) {
+        M[r + (long long)c * n] -= f * M[k + (long long)c * n];
+        Inv[r + (long long)c * n] -= f * Inv[k + (long long)c * n];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void dense_inverse(const Csr& A, double* Inv, cudaStream_t s) {
+  const int n = A.rows;
+  double* M = dalloc<double>((size_t)n * n, s);
+  int* sing = dalloc<int>(1, s);
+  CLAIR_CUDA(cudaMemsetAsync(sing, 0, sizeof(int), s));
+  if (n) {
+    csr_to_dense<<<ceil_div(n, 128), 128, 0, s>>>(A.rowptr, A.col, A.val, n, M); ::clair::count_launch();
+    gauss_jordan<<<1, 256, 0, s>>>(M, Inv, n, sing); ::clair::count_launch();
+  }
+  CLAIR_LAUNCHED();
+  int h = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&h, sing, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  dfree(M, s);
+  dfree(sing, s);
+  CLAIR_REQUIRE(h == 0, CLAIR_ERR_SINGULAR_BLOCK, "coarsest operator is singular");
+}
+
+// x = Inv b for a dense n x n column-major Inv (one block).
+template <class T>
+__global__ void dense_gemv(const T* __restrict__ Inv, int n, const T* __restrict__ b,
+                           T* __restrict__ x) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    T acc = 0;
+    for (int c = 0; c < n; ++c) acc += Inv[r + (long long)c * n] * b[c];
+    x[r] = acc;
+  }
+}
+
+template <class T>
+void coarse_apply(const T* Inv, int n, const T* b, T* x, cudaStream_t s) {
+  if (!n) return;
+  dense_gemv<T><<<ceil_div(n, 128), 128, 0, s>>>(Inv, n, b, x); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+}
+template void coarse_apply<double>(const double*, int, const double*, double*, cudaStream_t);
+template void coarse_apply<float>(const float*, int, const float*, float*, cudaStream_t);
+
+}  // namespace clair

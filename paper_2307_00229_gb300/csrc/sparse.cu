@@ -1,0 +1,833 @@
+// Sparse building blocks of the CLAIR library: scan, deterministic CSR transpose,
+// row maxima, sub-warp SpMV, deterministic Gustavson SpGEMM for the Galerkin product
+// A_c = R A P (Section 1), and fixed-order reductions for the FP64 Krylov solver.
+#include <stdarg.h>
+
+#include <algorithm>
+#include <atomic>
+#include <vector>
+
+#include "common.cuh"
+
+namespace clair {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+const char* last_error() { return g_last_error.c_str(); }
+void clear_error() { g_last_error.clear(); }
+
+int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached = v > 0 ? v : 148;
+  }
+  return cached;
+}
+
+int partial_blocks() { return 2 * sm_count(); }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(); }
+
+static thread_local PhaseClock* g_clock = nullptr;
+PhaseClock* active_clock() { return g_clock; }
+void set_active_clock(PhaseClock* c) { g_clock = c; }
+
+void PhaseClock::begin(int ph, cudaStream_t s) {
+  if (n_ == cap_) {
+    int cap = cap_ ? 2 * cap_ : 64;
+    Mark* m = new Mark[cap];
+    for (int i = 0; i < n_; ++i) m[i] = marks_[i];
+    delete[] marks_;
+    marks_ = m;
+    cap_ = cap;
+  }
+  Mark& m = marks_[n_++];
+  m.ph = ph;
+  cudaEventCreate(&m.a);
+  cudaEventCreate(&m.b);
+  cudaEventRecord(m.a, s);
+}
+
+void PhaseClock::end(cudaStream_t s) {
+  if (n_) cudaEventRecord(marks_[n_ - 1].b, s);
+}
+
+void PhaseClock::collect(double* ms_out) {
+  if (n_) cudaEventSynchronize(marks_[n_ - 1].b);
+  for (int i = 0; i < n_; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, marks_[i].a, marks_[i].b) == cudaSuccess) ms_out[marks_[i].ph] += ms;
+    cudaEventDestroy(marks_[i].a);
+    cudaEventDestroy(marks_[i].b);
+  }
+  n_ = 0;
+}
+
+PhaseClock::~PhaseClock() {
+  for (int i = 0; i < n_; ++i) {
+    cudaEventDestroy(marks_[i].a);
+    cudaEventDestroy(marks_[i].b);
+  }
+  delete[] marks_;
+}
+
+// ------------------------------------------------------------------------------------
+// Exclusive scan (three phases: block sums, scan of sums in one block, block scans).
+// ------------------------------------------------------------------------------------
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <class T>
+__device__ T block_inclusive_scan(T v, T* sh) {
+  // Hillis-Steele over warps then across warp totals; blockDim.x == SCAN_THREADS.
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    T w = lane < (SCAN_THREADS / 32) ? sh[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  if (wid > 0) v += sh[wid - 1];
+  __syncthreads();
+  return v;
+}
+
+__global__ void scan_block_sums(const int* __restrict__ in, int n, long long* __restrict__ sums) {
+  __shared__ long long sh[32];
+  long long acc = 0;
+  const long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    long long i = base + k;
+    if (i < n) acc += in[i];
+  }
+  acc = block_inclusive_scan(acc, sh);
+  if (threadIdx.x == SCAN_THREADS - 1) sums[blockIdx.x] = acc;
+}
+
+__global__ void scan_sums(long long* sums, int nb) {
+  // single block; nb <= SCAN_TILE
+  __shared__ long long sh[32];
+  long long loc[SCAN_ITEMS];
+  long long acc = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int i = threadIdx.x * SCAN_ITEMS + k;
+    loc[k] = i < nb ? sums[i] : 0;
+    acc += loc[k];
+  }
+  long long incl = block_inclusive_scan(acc, sh);
+  long long run = incl - acc;  // exclusive prefix of this thread
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int i = threadIdx.x * SCAN_ITEMS + k;
+    if (i < nb) sums[i] = run;  // exclusive block offsets
+    run += loc[k];
+  }
+}
+
+__global__ void scan_apply(const int* __restrict__ in, int n, const long long* __restrict__ offs,
+                           int* __restrict__ out, int* __restrict__ overflow) {
+  __shared__ long long sh[32];
+  long long loc[SCAN_ITEMS];
+  long long acc = 0;
+  const long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    long long i = base + k;
+    loc[k] = i < n ? in[i] : 0;
+    acc += loc[k];
+  }
+  long long incl = block_inclusive_scan(acc, sh);
+  long long run = offs[blockIdx.x] + incl - acc;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    long long i = base + k;
+    run += loc[k];
+    if (i < n) {
+      if (run > 0x7fffffffLL) *overflow = 1;
+      out[i + 1] = (int)run;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+}
+
+long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s, bool want_total) {
+  const int nb = std::max(1, ceil_div(n, SCAN_TILE));
+  CLAIR_REQUIRE(nb <= SCAN_TILE, CLAIR_ERR_CAPACITY, "scan of %d items exceeds capacity", n);
+  long long* sums = dalloc<long long>(nb + 1, s);
+  int* ovf = dalloc<int>(1, s);
+  CLAIR_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+  scan_block_sums<<<nb, SCAN_THREADS, 0, s>>>(in, n, sums); ::clair::count_launch();
+  scan_sums<<<1, SCAN_THREADS, 0, s>>>(sums, nb); ::clair::count_launch();
+  scan_apply<<<nb, SCAN_THREADS, 0, s>>>(in, n, sums, out, ovf); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  long long total = 0;
+  if (want_total) {
+    int total32 = 0, h_ovf = 0;
+    CLAIR_CUDA(cudaMemcpyAsync(&total32, out + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaMemcpyAsync(&h_ovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    CLAIR_REQUIRE(!h_ovf, CLAIR_ERR_CAPACITY, "scan total exceeds int32");
+    total = total32;
+  }
+  dfree(sums, s);
+  dfree(ovf, s);
+  return total;
+}
+
+// ------------------------------------------------------------------------------------
+// CSR transpose: column counts, scan, atomic fill, then a per-row insertion sort makes
+// the result independent of the atomic order.
+// ------------------------------------------------------------------------------------
+__global__ void count_cols(const int* __restrict__ col, int nnz, int* __restrict__ cnt) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nnz;
+       e += (long long)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[col[e]], 1);
+}
+
+__global__ void transpose_fill(const int* __restrict__ rowptr, const int* __restrict__ col,
+                               int rows, int* __restrict__ cursor, int* __restrict__ col_t,
+                               int* __restrict__ perm) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+    int pos = atomicAdd(&cursor[col[e]], 1);
+    col_t[pos] = r;
+    perm[pos] = e;
+  }
+}
+
+__global__ void sort_segments(const int* __restrict__ rowptr, int rows, int* __restrict__ key,
+                              int* __restrict__ perm) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const int b = rowptr[r], e = rowptr[r + 1];
+  for (int i = b + 1; i < e; ++i) {
+    int k = key[i], p = perm[i], j = i - 1;
+    while (j >= b && key[j] > k) {
+      key[j + 1] = key[j];
+      perm[j + 1] = perm[j];
+      --j;
+    }
+    key[j + 1] = k;
+    perm[j + 1] = p;
+  }
+}
+
+__global__ void gather_kernel(const double* __restrict__ x, const int* __restrict__ idx,
+                              double* __restrict__ y, int n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[idx[i]];
+}
+
+__global__ void scatter_kernel(const double* __restrict__ x, const int* __restrict__ idx,
+                               double* __restrict__ y, int n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[idx[i]] = x[i];
+}
+
+static int grid_for(long long n, int threads = 256) {
+  long long g = (n + threads - 1) / threads;
+  long long cap = 32LL * sm_count();
+  return (int)std::max(1LL, std::min(g, cap));
+}
+
+void gather(const double* x, const int* idx, double* y, int n, cudaStream_t s) {
+  if (n <= 0) return;
+  gather_kernel<<<grid_for(n), 256, 0, s>>>(x, idx, y, n); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+}
+void gather_vals(const double* x, const int* perm, double* y, int n, cudaStream_t s) {
+  gather(x, perm, y, n, s);
+}
+void scatter_vals(const double* x, const int* perm, double* y, int n, cudaStream_t s) {
+  if (n <= 0) return;
+  scatter_kernel<<<grid_for(n), 256, 0, s>>>(x, perm, y, n); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+}
+
+void csr_transpose(const Csr& A, Csr& At, int** perm_out, cudaStream_t s) {
+  At.rows = A.cols;
+  At.cols = A.rows;
+  At.nnz = A.nnz;
+  int* cnt = dalloc<int>(A.cols + 1, s);
+  CLAIR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (A.cols + 1), s));
+  if (A.nnz) count_cols<<<grid_for(A.nnz), 256, 0, s>>>(A.col, A.nnz, cnt); ::clair::count_launch();
+  At.rowptr = dalloc<int>(A.cols + 1, s);
+  exclusive_scan(cnt, At.rowptr, A.cols, s, false);
+  CLAIR_CUDA(cudaMemcpyAsync(cnt, At.rowptr, sizeof(int) * A.cols, cudaMemcpyDeviceToDevice, s));
+  At.col = dalloc<int>(A.nnz, s);
+  int* perm = dalloc<int>(A.nnz, s);
+  if (A.rows) transpose_fill<<<ceil_div(A.rows, 256), 256, 0, s>>>(A.rowptr, A.col, A.rows, cnt,
+                                                                     At.col, perm); ::clair::count_launch();
+  if (At.rows) sort_segments<<<ceil_div(At.rows, 128), 128, 0, s>>>(At.rowptr, At.rows, At.col, perm); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  if (A.val) {
+    At.val = dalloc<double>(A.nnz, s);
+    gather(A.val, perm, At.val, A.nnz, s);
+  }
+  dfree(cnt, s);
+  if (perm_out)
+    *perm_out = perm;
+  else
+    dfree(perm, s);
+}
+
+// ------------------------------------------------------------------------------------
+// Row kernels with W lanes per row.
+// ------------------------------------------------------------------------------------
+static int lanes_for(const Csr& A) {
+  double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
+  int w = 2;
+  while (w < 32 && w < avg) w <<= 1;
+  return w;
+}
+
+template <int W>
+__global__ void rowmax_kernel(const int* __restrict__ rowptr, const int* __restrict__ col,
+                              const double* __restrict__ val, int rows, double* __restrict__ out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int r = (int)(t / W), lane = (int)(t % W);
+  const bool ok = r < rows;  // no early exit: every lane takes part in the shuffles
+  double m = 0.0;
+  if (ok)
+    for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += W)
+      if (col[e] != r) m = fmax(m, fabs(val[e]));
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o, W));
+  if (ok && lane == 0) out[r] = m;
+}
+
+#define CLAIR_DISPATCH_W(W, ...)             \
+  switch (W) {                               \
+    case 2: { constexpr int WW = 2; __VA_ARGS__; ::clair::count_launch(); } break;   \
+    case 4: { constexpr int WW = 4; __VA_ARGS__; ::clair::count_launch(); } break;   \
+    case 8: { constexpr int WW = 8; __VA_ARGS__; ::clair::count_launch(); } break;   \
+    case 16: { constexpr int WW = 16; __VA_ARGS__; ::clair::count_launch(); } break; \
+    default: { constexpr int WW = 32; __VA_ARGS__; ::clair::count_launch(); } break; \
+  }
+
+void row_max_offdiag(const Csr& A, double* out, cudaStream_t s) {
+  if (!A.rows) return;
+  int W = lanes_for(A);
+  long long threads = (long long)A.rows * W;
+  int blocks = ceil_div(threads, 256);
+  CLAIR_DISPATCH_W(W, rowmax_kernel<WW><<<blocks, 256, 0, s>>>(A.rowptr, A.col, A.val, A.rows, out));
+  CLAIR_LAUNCHED();
+}
+
+template <int W, class T, bool RESID>
+__global__ void spmv_kernel(const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const T* __restrict__ val, int rows, const T* __restrict__ x,
+                            const T* __restrict__ b, T* __restrict__ y, T alpha, T beta) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int r = (int)(t / W), lane = (int)(t % W);
+  const bool ok = r < rows;  // no early exit: every lane takes part in the shuffles
+  T acc = 0;
+  if (ok)
+    for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += W) acc += val[e] * __ldg(&x[col[e]]);
+  acc = group_sum<W>(acc);
+  if (ok && lane == 0) {
+    if (RESID)
+      y[r] = b[r] - acc;
+    else
+      y[r] = beta == T(0) ? alpha * acc : alpha * acc + beta * y[r];
+  }
+}
+
+template <class T, bool RESID>
+static void spmv_launch(const Csr& A, const T* vals, const T* x, const T* b, T* y, T alpha, T beta,
+                        cudaStream_t s) {
+  if (!A.rows) return;
+  int W = lanes_for(A);
+  long long threads = (long long)A.rows * W;
+  int blocks = ceil_div(threads, 256);
+  CLAIR_DISPATCH_W(W, (spmv_kernel<WW, T, RESID><<<blocks, 256, 0, s>>>(A.rowptr, A.col, vals, A.rows,
+                                                                       x, b, y, alpha, beta)));
+  CLAIR_LAUNCHED();
+}
+
+void spmv(const Csr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s) {
+  spmv_launch<double, false>(A, A.val, x, nullptr, y, alpha, beta, s);
+}
+void spmv32(const Csr& A, const float* x, float* y, float alpha, float beta, cudaStream_t s) {
+  spmv_launch<float, false>(A, A.val32, x, nullptr, y, alpha, beta, s);
+}
+void residual(const Csr& A, const double* b, const double* x, double* r, cudaStream_t s) {
+  spmv_launch<double, true>(A, A.val, x, b, r, 1.0, 0.0, s);
+}
+void residual32(const Csr& A, const float* b, const float* x, float* r, cudaStream_t s) {
+  spmv_launch<float, true>(A, A.val32, x, b, r, 1.f, 0.f, s);
+}
+
+__global__ void inv_diag_kernel(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                const double* __restrict__ val, int rows, double* __restrict__ dinv,
+                                int* __restrict__ bad) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  double d = 0.0;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e)
+    if (col[e] == r) d = val[e];
+  if (d == 0.0 || !isfinite(d)) atomicAdd(bad, 1);
+  dinv[r] = d != 0.0 ? 1.0 / d : 0.0;
+}
+
+void inverse_diagonal(const Csr& A, double* dinv, cudaStream_t s) {
+  int* bad = dalloc<int>(1, s);
+  CLAIR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  if (A.rows) inv_diag_kernel<<<ceil_div(A.rows, 256), 256, 0, s>>>(A.rowptr, A.col, A.val, A.rows,
+                                                                      dinv, bad); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int h = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  dfree(bad, s);
+  CLAIR_REQUIRE(h == 0, CLAIR_ERR_ARG, "%d rows with a missing, zero or nonfinite diagonal", h);
+}
+
+__global__ void to_float_kernel(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+__global__ void to_double_kernel(const float* __restrict__ x, double* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+void to_float(const double* x, float* y, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  to_float_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+}
+void to_double(const float* x, double* y, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  to_double_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+}
+
+// ------------------------------------------------------------------------------------
+// Deterministic multi-dot: partial sums per block in a fixed order, then a fixed-order
+// reduction of the partials.
+// ------------------------------------------------------------------------------------
+constexpr int DOT_THREADS = 256;
+constexpr int DOT_GROUP = 8;
+
+__global__ void multi_dot_partial(const double* __restrict__ V, int m, const double* __restrict__ w,
+                                  long long n, double* __restrict__ partial) {
+  __shared__ double sh[DOT_GROUP][DOT_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j0 = 0; j0 < m; j0 += DOT_GROUP) {
+    double acc[DOT_GROUP];
+#pragma unroll
+    for (int g = 0; g < DOT_GROUP; ++g) acc[g] = 0.0;
+    for (long long i = blockIdx.x * (long long)DOT_THREADS + threadIdx.x; i < n;
+         i += (long long)gridDim.x * DOT_THREADS) {
+      const double wi = w[i];
+#pragma unroll
+      for (int g = 0; g < DOT_GROUP; ++g)
+        if (j0 + g < m) acc[g] = fma(V[(long long)(j0 + g) * n + i], wi, acc[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < DOT_GROUP; ++g) {
+      double v = warp_sum(acc[g]);
+      if (lane == 0) sh[g][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < DOT_GROUP && j0 + threadIdx.x < m) {
+      double v = 0.0;
+      for (int k = 0; k < DOT_THREADS / 32; ++k) v += sh[threadIdx.x][k];
+      partial[(long long)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void multi_dot_final(const double* __restrict__ partial, int nblocks, int m,
+                                double* __restrict__ out) {
+  // one warp per vector, fixed order
+  const int j = blockIdx.x;
+  if (j >= m) return;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 32) v += partial[(long long)j * nblocks + b];
+  v = warp_sum(v);
+  if (threadIdx.x == 0) out[j] = v;
+}
+
+void multi_dot(const double* V, int m, const double* w, int n, double* out, double* partial,
+               cudaStream_t s) {
+  if (m <= 0) return;
+  int nb = partial_blocks();
+  multi_dot_partial<<<nb, DOT_THREADS, 0, s>>>(V, m, w, n, partial); ::clair::count_launch();
+  multi_dot_final<<<m, 32, 0, s>>>(partial, nb, m, out); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+}
+
+__global__ void multi_axpy_kernel(const double* __restrict__ V, int m, const double* __restrict__ h,
+                                  double* __restrict__ w, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double acc = w[i];
+    for (int j = 0; j < m; ++j) acc = fma(-h[j], V[(long long)j * n + i], acc);
+    w[i] = acc;
+  }
+}
+
+void multi_axpy(const double* V, int m, const double* h, double* w, int n, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return;
+  multi_axpy_kernel<<<grid_for(n), 256, 0, s>>>(V, m, h, w, n); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+}
+
+__global__ void finite_kernel(const double* __restrict__ x, long long n, int* bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) *bad = 1;
+}
+
+bool all_finite(const double* x, long long n, cudaStream_t s) {
+  if (n <= 0) return true;
+  int* bad = dalloc<int>(1, s);
+  CLAIR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  finite_kernel<<<grid_for(n), 256, 0, s>>>(x, n, bad); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int h = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  dfree(bad, s);
+  return h == 0;
+}
+
+// ------------------------------------------------------------------------------------
+// Input validation of a caller's CSR: rowptr[0] = 0, nondecreasing, rowptr[rows] = nnz,
+// columns in [0, cols) and strictly increasing within each row.
+// ------------------------------------------------------------------------------------
+__global__ void validate_rows(const int* __restrict__ rowptr, const int* __restrict__ col, int rows,
+                              int cols, int nnz, int* __restrict__ bad) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const int b = rowptr[r], e = rowptr[r + 1];
+  if ((r == 0 && b != 0) || e < b || b < 0 || e > nnz || (r == rows - 1 && e != nnz)) {
+    atomicAdd(bad, 1);
+    return;
+  }
+  int prev = -1;
+  for (int k = b; k < e; ++k) {
+    const int c = col[k];
+    if (c < 0 || c >= cols || c <= prev) {
+      atomicAdd(bad, 1);
+      return;
+    }
+    prev = c;
+  }
+}
+
+__global__ void validate_flags(const signed char* __restrict__ f, int n, int* __restrict__ bad) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && f[i] != 0 && f[i] != 1) atomicAdd(bad, 1);
+}
+
+void validate_csr(const int* rowptr, const int* col, int rows, int cols, int nnz, const char* what,
+                  cudaStream_t s) {
+  CLAIR_REQUIRE(rows >= 0 && nnz >= 0, CLAIR_ERR_ARG, "%s: negative size", what);
+  if (!rows) return;
+  int* bad = dalloc<int>(1, s);
+  CLAIR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  int h_rp[2] = {0, 0};
+  CLAIR_CUDA(cudaMemcpyAsync(&h_rp[0], rowptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaMemcpyAsync(&h_rp[1], rowptr + rows, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  if (h_rp[0] == 0 && h_rp[1] == nnz) {
+    validate_rows<<<ceil_div(rows, 256), 256, 0, s>>>(rowptr, col, rows, cols, nnz, bad); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+  }
+  int h = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  dfree(bad, s);
+  CLAIR_REQUIRE(h_rp[0] == 0 && h_rp[1] == nnz, CLAIR_ERR_ARG,
+                "%s: rowptr[0]=%d rowptr[rows]=%d, expected 0 and %d", what, h_rp[0], h_rp[1], nnz);
+  CLAIR_REQUIRE(h == 0, CLAIR_ERR_ARG,
+                "%s: %d rows with bad row pointers or unsorted/out-of-range columns", what, h);
+}
+
+void validate_cf(const signed char* cf, int n, cudaStream_t s) {
+  if (!n) return;
+  int* bad = dalloc<int>(1, s);
+  CLAIR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  validate_flags<<<ceil_div(n, 256), 256, 0, s>>>(cf, n, bad); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int h = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  dfree(bad, s);
+  CLAIR_REQUIRE(h == 0, CLAIR_ERR_ARG, "cf has %d entries other than 0/1", h);
+}
+
+// ------------------------------------------------------------------------------------
+// SpGEMM C = A B (Gustavson).  One warp per row of A; the row's entries k are taken in
+// stored (ascending column) order and, for each k, the lanes add a_ik * b_kj for the
+// distinct j of row k into a shared-memory hash table.  Every output entry therefore
+// sums its products in increasing k, with separate multiply and add (no contraction),
+// independent of scheduling.  Rows whose product count exceeds the small table go to a
+// one-warp-per-block path with a large dynamic table.
+// ------------------------------------------------------------------------------------
+constexpr int SG_SMALL = 1024;        // slots per warp (small path)
+constexpr int SG_WARPS = 4;           // warps per block (small path)
+constexpr int SG_LARGE = 16384;       // slots (large path)
+
+__device__ __forceinline__ int sg_hash(int key, int cap) {
+  return (int)(((unsigned)key * 2654435761u) & (unsigned)(cap - 1));
+}
+
+// Inserts key; returns slot (or -1 if the table is full).
+__device__ __forceinline__ int sg_insert(int* keys, int cap, int key, bool* is_new) {
+  int h = sg_hash(key, cap);
+  for (int probe = 0; probe < cap; ++probe) {
+    int prev = atomicCAS(&keys[h], -1, key);
+    if (prev == -1) {
+      *is_new = true;
+      return h;
+    }
+    if (prev == key) {
+      *is_new = false;
+      return h;
+    }
+    h = (h + 1) & (cap - 1);
+  }
+  return -1;
+}
+
+__global__ void spgemm_upper(const int* __restrict__ Arp, const int* __restrict__ Acol, int rows,
+                             const int* __restrict__ Brp, int* __restrict__ ub) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  long long u = 0;
+  for (int e = Arp[r]; e < Arp[r + 1]; ++e) u += Brp[Acol[e] + 1] - Brp[Acol[e]];
+  ub[r] = (int)(u < 0x7fffffffLL ? u : 0x7fffffffLL);
+}
+
+// One warp processes row r: NUMERIC=false counts distinct columns, NUMERIC=true writes
+// the sorted row.  keys/vals: the warp's table of `cap` slots.
+template <bool NUMERIC>
+__device__ void spgemm_row(int r, const int* __restrict__ Arp, const int* __restrict__ Acol,
+                           const double* __restrict__ Aval, const int* __restrict__ Brp,
+                           const int* __restrict__ Bcol, const double* __restrict__ Bval, int* keys,
+                           double* vals, int cap, int* __restrict__ count,
+                           const int* __restrict__ Crp, int* __restrict__ Ccol,
+                           double* __restrict__ Cval, int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  for (int s = lane; s < cap; s += 32) {
+    keys[s] = -1;
+    if (NUMERIC) vals[s] = 0.0;
+  }
+  __syncwarp();
+  int mine = 0;
+  for (int ea = Arp[r]; ea < Arp[r + 1]; ++ea) {
+    const int k = Acol[ea];
+    const double a = NUMERIC ? Aval[ea] : 0.0;
+    for (int eb = Brp[k] + lane; eb < Brp[k + 1]; eb += 32) {
+      bool is_new;
+      int slot = sg_insert(keys, cap, Bcol[eb], &is_new);
+      if (slot < 0) {
+        atomicExch(err, 1);
+        continue;
+      }
+      if (is_new) ++mine;
+      if (NUMERIC) vals[slot] = __dadd_rn(vals[slot], __dmul_rn(a, Bval[eb]));
+    }
+    __syncwarp();
+  }
+  if (!NUMERIC) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0) count[r] = mine;
+    return;
+  }
+  // write the occupied slots in ascending key order: rank = #occupied keys below
+  const int base = Crp[r];
+  for (int s = lane; s < cap; s += 32) {
+    const int key = keys[s];
+    if (key < 0) continue;
+    int rank = 0;
+    for (int t = 0; t < cap; ++t) rank += (keys[t] >= 0 && keys[t] < key);
+    Ccol[base + rank] = key;
+    Cval[base + rank] = vals[s];
+  }
+}
+
+template <bool NUMERIC>
+__global__ void __launch_bounds__(32 * SG_WARPS)
+spgemm_small(const int* __restrict__ Arp, const int* __restrict__ Acol,
+             const double* __restrict__ Aval, int rows, const int* __restrict__ Brp,
+             const int* __restrict__ Bcol, const double* __restrict__ Bval,
+             const int* __restrict__ ub, int* __restrict__ count, const int* __restrict__ Crp,
+             int* __restrict__ Ccol, double* __restrict__ Cval, int* __restrict__ err) {
+  __shared__ int keys[SG_WARPS][SG_SMALL];
+  __shared__ double vals[NUMERIC ? SG_WARPS : 1][NUMERIC ? SG_SMALL : 1];
+  const int w = threadIdx.x >> 5;
+  const int r = blockIdx.x * SG_WARPS + w;
+  if (r >= rows || ub[r] > SG_SMALL / 2) return;
+  spgemm_row<NUMERIC>(r, Arp, Acol, Aval, Brp, Bcol, Bval, keys[w], NUMERIC ? vals[w] : nullptr,
+                      SG_SMALL, count, Crp, Ccol, Cval, err);
+}
+
+template <bool NUMERIC>
+__global__ void __launch_bounds__(32)
+spgemm_large(const int* __restrict__ Arp, const int* __restrict__ Acol,
+             const double* __restrict__ Aval, const int* __restrict__ big_rows,
+             const int* __restrict__ Brp, const int* __restrict__ Bcol,
+             const double* __restrict__ Bval, int* __restrict__ count,
+             const int* __restrict__ Crp, int* __restrict__ Ccol, double* __restrict__ Cval,
+             int* __restrict__ err) {
+  extern __shared__ unsigned char smem[];
+  double* vals = reinterpret_cast<double*>(smem);
+  int* keys = reinterpret_cast<int*>(smem + (NUMERIC ? sizeof(double) * SG_LARGE : 0));
+  const int r = big_rows[blockIdx.x];
+  spgemm_row<NUMERIC>(r, Arp, Acol, Aval, Brp, Bcol, Bval, keys, NUMERIC ? vals : nullptr,
+                      SG_LARGE, count, Crp, Ccol, Cval, err);
+}
+
+__global__ void collect_big(const int* __restrict__ ub, int rows, int limit, int* __restrict__ list,
+                            int* __restrict__ cnt) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < rows && ub[r] > limit) list[atomicAdd(cnt, 1)] = r;
+}
+
+__global__ void count_nonzero(const int* __restrict__ rowptr, const double* __restrict__ val, int rows,
+                              int* __restrict__ cnt) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  int c = 0;
+  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) c += val[e] != 0.0;
+  cnt[r] = c;
+}
+
+__global__ void copy_nonzero(const int* __restrict__ rowptr, const int* __restrict__ col,
+                             const double* __restrict__ val, int rows, const int* __restrict__ out_rp,
+                             int* __restrict__ out_col, double* __restrict__ out_val) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  int o = out_rp[r];
+  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e)
+    if (val[e] != 0.0) {
+      out_col[o] = col[e];
+      out_val[o] = val[e];
+      ++o;
+    }
+}
+
+void drop_zeros(Csr& C, cudaStream_t s) {
+  const int rows = C.rows;
+  int* cnt = dalloc<int>(rows + 1, s);
+  if (rows) count_nonzero<<<ceil_div(rows, 256), 256, 0, s>>>(C.rowptr, C.val, rows, cnt); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int* rp = dalloc<int>(rows + 1, s);
+  const int nnz = (int)exclusive_scan(cnt, rp, rows, s, true);
+  if (nnz == C.nnz) {
+    dfree(cnt, s);
+    dfree(rp, s);
+    return;
+  }
+  int* col = dalloc<int>(nnz, s);
+  double* val = dalloc<double>(nnz, s);
+  if (rows) copy_nonzero<<<ceil_div(rows, 256), 256, 0, s>>>(C.rowptr, C.col, C.val, rows, rp, col, val); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  dfree(cnt, s);
+  dfree(C.rowptr, s);
+  dfree(C.col, s);
+  dfree(C.val, s);
+  C.rowptr = rp;
+  C.col = col;
+  C.val = val;
+  C.nnz = nnz;
+}
+
+void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
+  C.rows = A.rows;
+  C.cols = B.cols;
+  const int rows = A.rows;
+  int* ub = dalloc<int>(rows, s);
+  int* count = dalloc<int>(rows + 1, s);
+  int* err = dalloc<int>(2, s);
+  int* big = dalloc<int>(rows, s);
+  CLAIR_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
+  if (rows) {
+    spgemm_upper<<<ceil_div(rows, 256), 256, 0, s>>>(A.rowptr, A.col, rows, B.rowptr, ub); ::clair::count_launch();
+    collect_big<<<ceil_div(rows, 256), 256, 0, s>>>(ub, rows, SG_SMALL / 2, big, err + 1); ::clair::count_launch();
+  }
+  CLAIR_LAUNCHED();
+  int nbig = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&nbig, err + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  const size_t large_sym = sizeof(int) * SG_LARGE;
+  const size_t large_num = (sizeof(int) + sizeof(double)) * SG_LARGE;
+  static bool attr_set = false;
+  if (!attr_set) {
+    CLAIR_CUDA(cudaFuncSetAttribute(spgemm_large<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)large_sym));
+    CLAIR_CUDA(cudaFuncSetAttribute(spgemm_large<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)large_num));
+    attr_set = true;
+  }
+  const int grid_small = ceil_div(rows, SG_WARPS);
+  if (rows)
+    spgemm_small<false><<<grid_small, 32 * SG_WARPS, 0, s>>>(A.rowptr, A.col, A.val, rows, B.rowptr,
+                                                            B.col, B.val, ub, count, nullptr,
+                                                            nullptr, nullptr, err); ::clair::count_launch();
+  if (nbig)
+    spgemm_large<false><<<nbig, 32, large_sym, s>>>(A.rowptr, A.col, A.val, big, B.rowptr, B.col,
+                                                    B.val, count, nullptr, nullptr, nullptr, err); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  C.rowptr = dalloc<int>(rows + 1, s);
+  C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true);
+  C.col = dalloc<int>(C.nnz, s);
+  C.val = dalloc<double>(C.nnz, s);
+  if (rows)
+    spgemm_small<true><<<grid_small, 32 * SG_WARPS, 0, s>>>(A.rowptr, A.col, A.val, rows, B.rowptr,
+                                                           B.col, B.val, ub, count, C.rowptr, C.col,
+                                                           C.val, err); ::clair::count_launch();
+  if (nbig)
+    spgemm_large<true><<<nbig, 32, large_num, s>>>(A.rowptr, A.col, A.val, big, B.rowptr, B.col,
+                                                   B.val, count, C.rowptr, C.col, C.val, err); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int h_err = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  dfree(ub, s);
+  dfree(count, s);
+  dfree(err, s);
+  dfree(big, s);
+  CLAIR_REQUIRE(h_err == 0, CLAIR_ERR_CAPACITY, "SpGEMM row exceeds %d distinct columns", SG_LARGE);
+}
+
+}  // namespace clair
