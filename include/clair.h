@@ -169,6 +169,37 @@ clair_status clair_local_weights(int n, const int* Ahat_rowptr, const int* Ahat_
                                  int precision, double* Z_val, void* stream,
                                  int64_t* singular_out, int64_t* empty_out);
 
+/* Size of the one static device scratch array used by clair_local_weights_noalloc. */
+#define CLAIR_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* clair_local_weights without any device memory allocation.  The paper has no
+ * counterpart: this is a deployment variant of the same computation, with the same
+ * arguments, results (bit for bit) and error codes as clair_local_weights.
+ *
+ * It exists for callers that cannot let a library allocate device memory while they run:
+ * applications whose device memory is entirely reserved up front by their own pool or by
+ * a framework's caching allocator (an extra cudaMalloc would either fail or bypass the
+ * pool's accounting), and latency-critical loops that cannot afford cudaMalloc/cudaFree,
+ * which may synchronise the device and take unbounded time.  The caller still provides
+ * every input and output buffer.
+ *
+ * Temporaries come from one file-scope device array of CLAIR_NOALLOC_SCRATCH_BYTES
+ * (32 MiB).  Every GPU that loads the library keeps that array until the process exits.
+ * A call needs about 16 n + 28 nc + 16 nnz(Z) bytes plus 256-byte alignment per piece;
+ * when that exceeds the limit the call returns CLAIR_ERR_CAPACITY, names the sizes, and
+ * leaves Z_val untouched (use clair_local_weights for larger problems).
+ * The first call on a device looks up the array's device address with that device
+ * current; make that first call before starting any stream capture on the device.
+ * All calls share the one array and it keeps the last call's contents (every counter is
+ * cleared at the start of a call): calls that overlap on the GPU, from other streams or
+ * other host threads, race on it and corrupt each other's results, so serialise them.
+ * The call synchronises `stream`. */
+clair_status clair_local_weights_noalloc(int n, const int* Ahat_rowptr, const int* Ahat_col,
+                                         const double* Ahat_val, const signed char* cf, int nc,
+                                         const int* Z_rowptr, const int* Z_col, const double* B,
+                                         int precision, double* Z_val, void* stream,
+                                         int64_t* singular_out, int64_t* empty_out);
+
 /* One-line description of the last error on the calling thread ("" if none). */
 const char* clair_last_error(void);
 

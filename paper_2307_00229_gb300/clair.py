@@ -102,6 +102,8 @@ _SIGNATURES = {
                               ctypes.POINTER(_P), _PD]),
     "clair_free": (_I, [_P]),
     "clair_local_weights": (_I, [_I, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _PI64, _PI64]),
+    "clair_local_weights_noalloc": (_I, [_I, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _PI64,
+                                         _PI64]),
     "clair_last_error": (ctypes.c_char_p, []),
     "clair_kernel_launches": (ctypes.c_int64, []),
 }
@@ -240,6 +242,23 @@ def clair_local_weights(Ahat_rowptr, Ahat_col, Ahat_val, cf, nc: int, Z_rowptr, 
     sing, empty = ctypes.c_int64(0), ctypes.c_int64(0)
     n = Ahat_rowptr.numel() - 1
     st = load().clair_local_weights(
+        n, _dptr(Ahat_rowptr, torch.int32), _dptr(Ahat_col, torch.int32), _dptr(Ahat_val, torch.float64),
+        _dptr(cf, torch.int8), nc, _dptr(Z_rowptr, torch.int32), _dptr(Z_col, torch.int32),
+        _dptr(B, torch.float64), precision, _dptr(Z_val, torch.float64), _stream(stream),
+        ctypes.byref(sing), ctypes.byref(empty))
+    if st != CLAIR_OK and (st != CLAIR_ERR_SINGULAR_BLOCK or raise_singular):
+        _check(st)
+    return st, sing.value, empty.value
+
+
+def clair_local_weights_noalloc(Ahat_rowptr, Ahat_col, Ahat_val, cf, nc: int, Z_rowptr, Z_col, B,
+                                precision: int, Z_val, stream=None, raise_singular: bool = True):
+    """Same as ``clair_local_weights`` but the library allocates no device memory (its
+    temporaries live in one fixed static device array).  Returns ``(status, singular
+    blocks, skipped F-points)``."""
+    sing, empty = ctypes.c_int64(0), ctypes.c_int64(0)
+    n = Ahat_rowptr.numel() - 1
+    st = load().clair_local_weights_noalloc(
         n, _dptr(Ahat_rowptr, torch.int32), _dptr(Ahat_col, torch.int32), _dptr(Ahat_val, torch.float64),
         _dptr(cf, torch.int8), nc, _dptr(Z_rowptr, torch.int32), _dptr(Z_col, torch.int32),
         _dptr(B, torch.float64), precision, _dptr(Z_val, torch.float64), _stream(stream),

@@ -18,6 +18,7 @@
 // Pivoting is partial (largest |entry| among rows not yet used, lowest row on ties),
 // done implicitly by marking rows instead of swapping them.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -492,4 +493,197 @@ void transfer_weights(const Csr& Ahat, const signed char* cf, const int* cpts, C
     Zt.release(s);
 }
 
+// ======================================================================================
+// The same computation with every temporary carved from one static device array, for
+// callers that must not allocate device memory (see clair_local_weights_noalloc).
+// ======================================================================================
+int scan_ws_blocks(int n);
+long long exclusive_scan_ws(const int* in, int* out, int n, cudaStream_t s, bool want_total,
+                            long long* sums, int* ovf);
+void csr_transpose_ws(const Csr& A, Csr& At, int* perm, int* cnt, long long* sums, int* ovf,
+                      cudaStream_t s);
+void validate_csr_ws(const int* rowptr, const int* col, int rows, int cols, int nnz,
+                     const char* what, int* bad, cudaStream_t s);
+void validate_cf_ws(const signed char* cf, int n, int* bad, cudaStream_t s);
+const char* last_error();
+void clear_error();
+
+// The scratch array.  Host code only ever sees a host-side stand-in for this name; its
+// device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CLAIR_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_scratch_mutex;
+static void* g_scratch_address[256] = {};
+
+// Device address of the scratch array on the current device (looked up on first use).
+static unsigned char* scratch_on_current_device() {
+  int dev = -1;
+  CLAIR_CUDA(cudaGetDevice(&dev));
+  CLAIR_REQUIRE(dev >= 0 && dev < 256, CLAIR_ERR_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_address[dev]) {
+    void* p = nullptr;
+    CLAIR_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    CLAIR_REQUIRE(p != nullptr, CLAIR_ERR_CUDA, "no device address for the scratch array");
+    g_scratch_address[dev] = p;
+  }
+  return static_cast<unsigned char*>(g_scratch_address[dev]);
+}
+
+// Bump allocation of 256-byte aligned pieces; with base == nullptr it only measures.
+struct ScratchCursor {
+  unsigned char* base = nullptr;
+  size_t used = 0;
+  template <class T>
+  T* take(size_t count) {
+    const size_t bytes = ((count ? count : 1) * sizeof(T) + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + used) : nullptr;
+    used += bytes;
+    return p;
+  }
+};
+
+struct NoallocBuffers {
+  int *bad, *flag, *pre, *ovf, *cpts, *lists, *counts, *zt_rowptr, *zt_col, *perm, *cnt;
+  long long* sums;
+  unsigned long long *work, *nempty;
+  double *zt_val, *Bc;
+};
+
+static void carve(ScratchCursor& c, int n, int nc, int nnzZ, NoallocBuffers& b) {
+  b.bad = c.take<int>(1);
+  b.ovf = c.take<int>(1);
+  b.sums = c.take<long long>(scan_ws_blocks(n) + 1);
+  b.flag = c.take<int>(n);
+  b.pre = c.take<int>((size_t)n + 1);
+  b.cpts = c.take<int>(nc);
+  b.lists = c.take<int>((size_t)LS_BUCKETS * (nc > 0 ? nc : 1));
+  b.counts = c.take<int>(LS_BUCKETS + 1);
+  b.work = c.take<unsigned long long>(5);
+  b.zt_rowptr = c.take<int>((size_t)n + 1);
+  b.zt_col = c.take<int>(nnzZ);
+  b.zt_val = c.take<double>(nnzZ);
+  b.perm = c.take<int>(nnzZ);
+  b.cnt = c.take<int>((size_t)n + 1);
+  b.Bc = c.take<double>(nc);
+  b.nempty = c.take<unsigned long long>(1);
+}
+
+static size_t noalloc_bytes(int n, int nc, int nnzZ) {
+  ScratchCursor c;
+  NoallocBuffers b;
+  carve(c, n, nc, nnzZ, b);
+  return c.used;
+}
+
+static void local_weights_noalloc(int n, const Csr& Ahat, const signed char* cf, int nc, Csr& Z,
+                                  const double* B, int precision, const NoallocBuffers& b,
+                                  LocalStats& st, cudaStream_t s) {
+  validate_csr_ws(Ahat.rowptr, Ahat.col, n, n, Ahat.nnz, "Ahat", b.bad, s);
+  validate_cf_ws(cf, n, b.bad, s);
+  validate_csr_ws(Z.rowptr, Z.col, nc, n, Z.nnz, "Z", b.bad, s);
+  // coarse points
+  cf_to_int<<<ceil_div(n, 256), 256, 0, s>>>(cf, n, b.flag); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  const int nc2 = (int)exclusive_scan_ws(b.flag, b.pre, n, s, true, b.sums, b.ovf);
+  CLAIR_REQUIRE(nc2 == nc, CLAIR_ERR_ARG, "nc=%d but cf has %d C-points", nc, nc2);
+  coarse_of<<<ceil_div(n, 256), 256, 0, s>>>(cf, b.pre, n, b.cpts); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  // bucketed local solves (counters start at zero on every call)
+  CLAIR_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(int) * (LS_BUCKETS + 1), s));
+  CLAIR_CUDA(cudaMemsetAsync(b.work, 0, 5 * sizeof(unsigned long long), s));
+  if (nc) bucket_rows<<<ceil_div(nc, 256), 256, 0, s>>>(Z.rowptr, nc, b.lists, b.counts, Z.val, Z.col,
+                                                        b.cpts, Ahat.rowptr, b.counts + LS_BUCKETS,
+                                                        b.work + 1); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int counts_h[LS_BUCKETS + 1];
+  CLAIR_CUDA(cudaMemcpyAsync(counts_h, b.counts, sizeof(counts_h), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  CLAIR_REQUIRE(counts_h[LS_BUCKETS] == 0, CLAIR_ERR_CAPACITY,
+                "%d local systems larger than 128 unknowns", counts_h[LS_BUCKETS]);
+  if (precision == CLAIR_MIXED)
+    launch_solves<float>(Ahat, Z.rowptr, Z.col, b.cpts, b.lists, counts_h, nc, Z.val, b.work, s);
+  else
+    launch_solves<double>(Ahat, Z.rowptr, Z.col, b.cpts, b.lists, counts_h, nc, Z.val, b.work, s);
+  // column view of the weights, projection, values back into the row view
+  Csr Zt;
+  Zt.rowptr = b.zt_rowptr;
+  Zt.col = b.zt_col;
+  Zt.val = b.zt_val;
+  csr_transpose_ws(Z, Zt, b.perm, b.cnt, b.sums, b.ovf, s);
+  gather(B, b.cpts, b.Bc, nc, s);
+  CLAIR_CUDA(cudaMemsetAsync(b.nempty, 0, sizeof(unsigned long long), s));
+  if (Zt.rows) {
+    constexpr int W = 8;
+    project_rows<W><<<ceil_div((long long)Zt.rows * W, 256), 256, 0, s>>>(
+        Zt.rowptr, Zt.col, Zt.val, Zt.rows, cf, b.Bc, B, b.nempty); ::clair::count_launch();
+  }
+  CLAIR_LAUNCHED();
+  scatter_vals(Zt.val, b.perm, Z.val, Z.nnz, s);
+  unsigned long long h[2] = {0, 0};
+  CLAIR_CUDA(cudaMemcpyAsync(&h[0], b.work, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaMemcpyAsync(&h[1], b.nempty, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  st.singular += (long long)h[0];
+  st.empty += (long long)h[1];
+}
+
 }  // namespace clair
+
+extern "C" clair_status clair_local_weights_noalloc(
+    int n, const int* Ahat_rowptr, const int* Ahat_col, const double* Ahat_val,
+    const signed char* cf, int nc, const int* Z_rowptr, const int* Z_col, const double* B,
+    int precision, double* Z_val, void* stream, int64_t* singular_out, int64_t* empty_out) {
+  using namespace clair;
+  clear_error();
+  try {
+    CLAIR_REQUIRE(Ahat_rowptr && Ahat_col && Ahat_val && cf && Z_rowptr && Z_col && B && Z_val,
+                  CLAIR_ERR_ARG, "clair_local_weights_noalloc: null pointer");
+    CLAIR_REQUIRE(n > 0 && nc >= 0 && nc <= n, CLAIR_ERR_ARG,
+                  "clair_local_weights_noalloc: bad sizes n=%d nc=%d", n, nc);
+    CLAIR_REQUIRE(precision == CLAIR_FP64 || precision == CLAIR_MIXED, CLAIR_ERR_ARG,
+                  "unknown precision");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int nnzA = 0, nnzZ = 0;
+    CLAIR_CUDA(cudaMemcpyAsync(&nnzA, Ahat_rowptr + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaMemcpyAsync(&nnzZ, Z_rowptr + nc, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    CLAIR_REQUIRE(nnzA >= 0 && nnzZ >= 0, CLAIR_ERR_ARG, "negative nnz in a row pointer");
+    const size_t need = noalloc_bytes(n, nc, nnzZ);
+    CLAIR_REQUIRE(need <= (size_t)CLAIR_NOALLOC_SCRATCH_BYTES, CLAIR_ERR_CAPACITY,
+                  "clair_local_weights_noalloc needs %zu bytes of scratch for n=%d, nc=%d, "
+                  "nnz(Z)=%d; its fixed limit is %zu bytes (use clair_local_weights)",
+                  need, n, nc, nnzZ, (size_t)CLAIR_NOALLOC_SCRATCH_BYTES);
+    ScratchCursor cur;
+    cur.base = scratch_on_current_device();
+    NoallocBuffers buf;
+    carve(cur, n, nc, nnzZ, buf);
+    Csr Ahat;
+    Ahat.rows = Ahat.cols = n;
+    Ahat.nnz = nnzA;
+    Ahat.rowptr = const_cast<int*>(Ahat_rowptr);
+    Ahat.col = const_cast<int*>(Ahat_col);
+    Ahat.val = const_cast<double*>(Ahat_val);
+    Csr Z;
+    Z.rows = nc;
+    Z.cols = n;
+    Z.nnz = nnzZ;
+    Z.rowptr = const_cast<int*>(Z_rowptr);
+    Z.col = const_cast<int*>(Z_col);
+    Z.val = Z_val;
+    LocalStats st;
+    local_weights_noalloc(n, Ahat, cf, nc, Z, B, precision, buf, st, s);
+    if (singular_out) *singular_out = st.singular;
+    if (empty_out) *empty_out = st.empty;
+    if (st.singular) {
+      set_error("%lld local blocks had a zero pivot", st.singular);
+      return CLAIR_ERR_SINGULAR_BLOCK;
+    }
+  } catch (const Error& e) {
+    return e.st;
+  } catch (...) {
+    set_error("unexpected host exception");
+    return CLAIR_ERR_CUDA;
+  }
+  return CLAIR_OK;
+}

@@ -830,4 +830,80 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   CLAIR_REQUIRE(h_err == 0, CLAIR_ERR_CAPACITY, "SpGEMM row exceeds %d distinct columns", SG_LARGE);
 }
 
+// ------------------------------------------------------------------------------------
+// Variants that take every temporary from a caller-provided workspace instead of
+// allocating it (for the entry point that must not allocate device memory).
+// ------------------------------------------------------------------------------------
+int scan_ws_blocks(int n) { return std::max(1, ceil_div(n, SCAN_TILE)); }
+
+long long exclusive_scan_ws(const int* in, int* out, int n, cudaStream_t s, bool want_total,
+                            long long* sums, int* ovf) {
+  const int nb = scan_ws_blocks(n);
+  CLAIR_REQUIRE(nb <= SCAN_TILE, CLAIR_ERR_CAPACITY, "scan of %d items exceeds capacity", n);
+  CLAIR_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+  scan_block_sums<<<nb, SCAN_THREADS, 0, s>>>(in, n, sums); ::clair::count_launch();
+  scan_sums<<<1, SCAN_THREADS, 0, s>>>(sums, nb); ::clair::count_launch();
+  scan_apply<<<nb, SCAN_THREADS, 0, s>>>(in, n, sums, out, ovf); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  long long total = 0;
+  if (want_total) {
+    int total32 = 0, h_ovf = 0;
+    CLAIR_CUDA(cudaMemcpyAsync(&total32, out + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaMemcpyAsync(&h_ovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    CLAIR_REQUIRE(!h_ovf, CLAIR_ERR_CAPACITY, "scan total exceeds int32");
+    total = total32;
+  }
+  return total;
+}
+
+// At.rowptr (A.cols + 1), At.col and At.val (A.nnz each, val optional) are caller buffers;
+// perm (A.nnz), cnt (A.cols + 1), sums (scan_ws_blocks(A.cols) + 1) and ovf are workspace.
+void csr_transpose_ws(const Csr& A, Csr& At, int* perm, int* cnt, long long* sums, int* ovf,
+                      cudaStream_t s) {
+  At.rows = A.cols;
+  At.cols = A.rows;
+  At.nnz = A.nnz;
+  CLAIR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (A.cols + 1), s));
+  if (A.nnz) count_cols<<<grid_for(A.nnz), 256, 0, s>>>(A.col, A.nnz, cnt); ::clair::count_launch();
+  exclusive_scan_ws(cnt, At.rowptr, A.cols, s, false, sums, ovf);
+  CLAIR_CUDA(cudaMemcpyAsync(cnt, At.rowptr, sizeof(int) * A.cols, cudaMemcpyDeviceToDevice, s));
+  if (A.rows) transpose_fill<<<ceil_div(A.rows, 256), 256, 0, s>>>(A.rowptr, A.col, A.rows, cnt,
+                                                                     At.col, perm); ::clair::count_launch();
+  if (At.rows) sort_segments<<<ceil_div(At.rows, 128), 128, 0, s>>>(At.rowptr, At.rows, At.col, perm); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  if (A.val && At.val) gather(A.val, perm, At.val, A.nnz, s);
+}
+
+void validate_csr_ws(const int* rowptr, const int* col, int rows, int cols, int nnz,
+                     const char* what, int* bad, cudaStream_t s) {
+  CLAIR_REQUIRE(rows >= 0 && nnz >= 0, CLAIR_ERR_ARG, "%s: negative size", what);
+  if (!rows) return;
+  CLAIR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  int h_rp[2] = {0, 0};
+  CLAIR_CUDA(cudaMemcpyAsync(&h_rp[0], rowptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaMemcpyAsync(&h_rp[1], rowptr + rows, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  CLAIR_REQUIRE(h_rp[0] == 0 && h_rp[1] == nnz, CLAIR_ERR_ARG,
+                "%s: rowptr[0]=%d rowptr[rows]=%d, expected 0 and %d", what, h_rp[0], h_rp[1], nnz);
+  validate_rows<<<ceil_div(rows, 256), 256, 0, s>>>(rowptr, col, rows, cols, nnz, bad); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int h = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  CLAIR_REQUIRE(h == 0, CLAIR_ERR_ARG,
+                "%s: %d rows with bad row pointers or unsorted/out-of-range columns", what, h);
+}
+
+void validate_cf_ws(const signed char* cf, int n, int* bad, cudaStream_t s) {
+  if (!n) return;
+  CLAIR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  validate_flags<<<ceil_div(n, 256), 256, 0, s>>>(cf, n, bad); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int h = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  CLAIR_REQUIRE(h == 0, CLAIR_ERR_ARG, "cf has %d entries other than 0/1", h);
+}
+
 }  // namespace clair
