@@ -627,24 +627,17 @@ __device__ __forceinline__ int sg_insert(int* keys, int cap, int key, bool* is_n
   return -1;
 }
 
-__global__ void spgemm_upper(const int* __restrict__ Arp, const int* __restrict__ Acol, int rows,
-                             const int* __restrict__ Brp, int* __restrict__ ub) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= rows) return;
-  long long u = 0;
-  for (int e = Arp[r]; e < Arp[r + 1]; ++e) u += Brp[Acol[e] + 1] - Brp[Acol[e]];
-  ub[r] = (int)(u < 0x7fffffffLL ? u : 0x7fffffffLL);
-}
-
-// One warp processes row r: NUMERIC=false counts distinct columns, NUMERIC=true writes
-// the sorted row.  keys/vals: the warp's table of `cap` slots.
+// One warp processes row r.  NUMERIC = false: count[r] = number of distinct columns, or
+// -1 if they do not fit the table (the row is then redone with a larger one).
+// NUMERIC = true (the table holds at least twice the row's count): writes the row sorted
+// by column.  keys/vals: the warp's table of `cap` slots.
 template <bool NUMERIC>
 __device__ void spgemm_row(int r, const int* __restrict__ Arp, const int* __restrict__ Acol,
                            const double* __restrict__ Aval, const int* __restrict__ Brp,
                            const int* __restrict__ Bcol, const double* __restrict__ Bval, int* keys,
                            double* vals, int cap, int* __restrict__ count,
                            const int* __restrict__ Crp, int* __restrict__ Ccol,
-                           double* __restrict__ Cval, int* __restrict__ err) {
+                           double* __restrict__ Cval) {
   const int lane = threadIdx.x & 31;
   for (int s = lane; s < cap; s += 32) {
     keys[s] = -1;
@@ -652,75 +645,97 @@ __device__ void spgemm_row(int r, const int* __restrict__ Arp, const int* __rest
   }
   __syncwarp();
   int mine = 0;
+  bool full = false;
   for (int ea = Arp[r]; ea < Arp[r + 1]; ++ea) {
     const int k = Acol[ea];
     const double a = NUMERIC ? Aval[ea] : 0.0;
     for (int eb = Brp[k] + lane; eb < Brp[k + 1]; eb += 32) {
       bool is_new;
-      int slot = sg_insert(keys, cap, Bcol[eb], &is_new);
+      const int slot = sg_insert(keys, cap, Bcol[eb], &is_new);
       if (slot < 0) {
-        atomicExch(err, 1);
-        continue;
+        full = true;
+        break;
       }
       if (is_new) ++mine;
       if (NUMERIC) vals[slot] = __dadd_rn(vals[slot], __dmul_rn(a, Bval[eb]));
     }
-    __syncwarp();
+    if (__any_sync(0xffffffffu, full)) break;  // uniform across the warp
   }
   if (!NUMERIC) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-    if (lane == 0) count[r] = mine;
+    if (lane == 0) count[r] = __any_sync(0xffffffffu, full) ? -1 : mine;
     return;
   }
-  // write the occupied slots in ascending key order: rank = #occupied keys below
+  // compact the occupied slots to the front (each 32-slot chunk is read before any of
+  // its positions is written), then place every entry at its rank among the row's keys
+  __syncwarp();
+  int total = 0;
+  for (int c = 0; c < cap; c += 32) {
+    const int key = keys[c + lane];
+    const double v = vals[c + lane];
+    const unsigned occ = __ballot_sync(0xffffffffu, key >= 0);
+    __syncwarp();
+    if (key >= 0) {
+      const int dst = total + __popc(occ & ((1u << lane) - 1u));
+      keys[dst] = key;
+      vals[dst] = v;
+    }
+    total += __popc(occ);
+    __syncwarp();
+  }
   const int base = Crp[r];
-  for (int s = lane; s < cap; s += 32) {
-    const int key = keys[s];
-    if (key < 0) continue;
+  for (int t = lane; t < total; t += 32) {
+    const int key = keys[t];
     int rank = 0;
-    for (int t = 0; t < cap; ++t) rank += (keys[t] >= 0 && keys[t] < key);
+    for (int u = 0; u < total; ++u) rank += keys[u] < key;
     Ccol[base + rank] = key;
-    Cval[base + rank] = vals[s];
+    Cval[base + rank] = vals[t];
   }
 }
 
+// Small table, one warp per row.  Symbolic: every row.  Numeric: rows whose count fits
+// half of the table.
 template <bool NUMERIC>
 __global__ void __launch_bounds__(32 * SG_WARPS)
 spgemm_small(const int* __restrict__ Arp, const int* __restrict__ Acol,
              const double* __restrict__ Aval, int rows, const int* __restrict__ Brp,
              const int* __restrict__ Bcol, const double* __restrict__ Bval,
-             const int* __restrict__ ub, int* __restrict__ count, const int* __restrict__ Crp,
-             int* __restrict__ Ccol, double* __restrict__ Cval, int* __restrict__ err) {
+             int* __restrict__ count, const int* __restrict__ Crp, int* __restrict__ Ccol,
+             double* __restrict__ Cval) {
   __shared__ int keys[SG_WARPS][SG_SMALL];
   __shared__ double vals[NUMERIC ? SG_WARPS : 1][NUMERIC ? SG_SMALL : 1];
   const int w = threadIdx.x >> 5;
   const int r = blockIdx.x * SG_WARPS + w;
-  if (r >= rows || ub[r] > SG_SMALL / 2) return;
+  if (r >= rows) return;  // warp-uniform
+  if (NUMERIC && (Crp[r + 1] - Crp[r]) > SG_SMALL / 2) return;
   spgemm_row<NUMERIC>(r, Arp, Acol, Aval, Brp, Bcol, Bval, keys[w], NUMERIC ? vals[w] : nullptr,
-                      SG_SMALL, count, Crp, Ccol, Cval, err);
+                      SG_SMALL, count, Crp, Ccol, Cval);
 }
 
+// Large dynamic table, one warp per listed row.
 template <bool NUMERIC>
 __global__ void __launch_bounds__(32)
 spgemm_large(const int* __restrict__ Arp, const int* __restrict__ Acol,
-             const double* __restrict__ Aval, const int* __restrict__ big_rows,
+             const double* __restrict__ Aval, const int* __restrict__ list,
              const int* __restrict__ Brp, const int* __restrict__ Bcol,
              const double* __restrict__ Bval, int* __restrict__ count,
-             const int* __restrict__ Crp, int* __restrict__ Ccol, double* __restrict__ Cval,
-             int* __restrict__ err) {
+             const int* __restrict__ Crp, int* __restrict__ Ccol, double* __restrict__ Cval) {
   extern __shared__ unsigned char smem[];
   double* vals = reinterpret_cast<double*>(smem);
   int* keys = reinterpret_cast<int*>(smem + (NUMERIC ? sizeof(double) * SG_LARGE : 0));
-  const int r = big_rows[blockIdx.x];
+  const int r = list[blockIdx.x];
   spgemm_row<NUMERIC>(r, Arp, Acol, Aval, Brp, Bcol, Bval, keys, NUMERIC ? vals : nullptr,
-                      SG_LARGE, count, Crp, Ccol, Cval, err);
+                      SG_LARGE, count, Crp, Ccol, Cval);
 }
 
-__global__ void collect_big(const int* __restrict__ ub, int rows, int limit, int* __restrict__ list,
-                            int* __restrict__ cnt) {
+// list the rows with count == -1 (mode 0) or with more than `limit` entries (mode 1)
+__global__ void spgemm_collect(const int* __restrict__ count, const int* __restrict__ Crp, int rows,
+                               int mode, int limit, int* __restrict__ list, int* __restrict__ n) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < rows && ub[r] > limit) list[atomicAdd(cnt, 1)] = r;
+  if (r >= rows) return;
+  const bool take = mode == 0 ? count[r] < 0 : (Crp[r + 1] - Crp[r]) > limit;
+  if (take) list[atomicAdd(n, 1)] = r;
 }
 
 __global__ void count_nonzero(const int* __restrict__ rowptr, const double* __restrict__ val, int rows,
@@ -776,19 +791,10 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   C.rows = A.rows;
   C.cols = B.cols;
   const int rows = A.rows;
-  int* ub = dalloc<int>(rows, s);
   int* count = dalloc<int>(rows + 1, s);
-  int* err = dalloc<int>(2, s);
-  int* big = dalloc<int>(rows, s);
-  CLAIR_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
-  if (rows) {
-    spgemm_upper<<<ceil_div(rows, 256), 256, 0, s>>>(A.rowptr, A.col, rows, B.rowptr, ub); ::clair::count_launch();
-    collect_big<<<ceil_div(rows, 256), 256, 0, s>>>(ub, rows, SG_SMALL / 2, big, err + 1); ::clair::count_launch();
-  }
-  CLAIR_LAUNCHED();
-  int nbig = 0;
-  CLAIR_CUDA(cudaMemcpyAsync(&nbig, err + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CLAIR_CUDA(cudaStreamSynchronize(s));
+  int* list = dalloc<int>(rows, s);
+  int* nlist = dalloc<int>(2, s);
+  CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 2 * sizeof(int), s));
   const size_t large_sym = sizeof(int) * SG_LARGE;
   const size_t large_num = (sizeof(int) + sizeof(double)) * SG_LARGE;
   static bool attr_set = false;
@@ -800,34 +806,57 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
     attr_set = true;
   }
   const int grid_small = ceil_div(rows, SG_WARPS);
-  if (rows)
+  const int g = ceil_div(rows, 256);
+  // symbolic: small tables for every row, large tables for the rows that overflowed
+  if (rows) {
     spgemm_small<false><<<grid_small, 32 * SG_WARPS, 0, s>>>(A.rowptr, A.col, A.val, rows, B.rowptr,
-                                                            B.col, B.val, ub, count, nullptr,
-                                                            nullptr, nullptr, err); ::clair::count_launch();
-  if (nbig)
-    spgemm_large<false><<<nbig, 32, large_sym, s>>>(A.rowptr, A.col, A.val, big, B.rowptr, B.col,
-                                                    B.val, count, nullptr, nullptr, nullptr, err); ::clair::count_launch();
+                                                            B.col, B.val, count, nullptr, nullptr,
+                                                            nullptr); ::clair::count_launch();
+    spgemm_collect<<<g, 256, 0, s>>>(count, nullptr, rows, 0, 0, list, nlist); ::clair::count_launch();
+  }
   CLAIR_LAUNCHED();
+  int h_n[2] = {0, 0};
+  CLAIR_CUDA(cudaMemcpyAsync(h_n, nlist, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  if (h_n[0]) {
+    spgemm_large<false><<<h_n[0], 32, large_sym, s>>>(A.rowptr, A.col, A.val, list, B.rowptr, B.col,
+                                                      B.val, count, nullptr, nullptr, nullptr); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+    CLAIR_CUDA(cudaMemsetAsync(nlist, 0, sizeof(int), s));
+    spgemm_collect<<<g, 256, 0, s>>>(count, nullptr, rows, 0, 0, list, nlist); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+    int still = 0;
+    CLAIR_CUDA(cudaMemcpyAsync(&still, nlist, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    if (still) {
+      dfree(count, s);
+      dfree(list, s);
+      dfree(nlist, s);
+      CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "SpGEMM: %d rows exceed %d distinct columns", still,
+                    SG_LARGE);
+    }
+  }
   C.rowptr = dalloc<int>(rows + 1, s);
   C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true);
   C.col = dalloc<int>(C.nnz, s);
   C.val = dalloc<double>(C.nnz, s);
-  if (rows)
+  // numeric: rows up to half a small table there, the others in large tables
+  if (rows) {
     spgemm_small<true><<<grid_small, 32 * SG_WARPS, 0, s>>>(A.rowptr, A.col, A.val, rows, B.rowptr,
-                                                           B.col, B.val, ub, count, C.rowptr, C.col,
-                                                           C.val, err); ::clair::count_launch();
-  if (nbig)
-    spgemm_large<true><<<nbig, 32, large_num, s>>>(A.rowptr, A.col, A.val, big, B.rowptr, B.col,
-                                                   B.val, count, C.rowptr, C.col, C.val, err); ::clair::count_launch();
+                                                           B.col, B.val, count, C.rowptr, C.col,
+                                                           C.val); ::clair::count_launch();
+    spgemm_collect<<<g, 256, 0, s>>>(count, C.rowptr, rows, 1, SG_SMALL / 2, list, nlist + 1); ::clair::count_launch();
+  }
   CLAIR_LAUNCHED();
-  int h_err = 0;
-  CLAIR_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaMemcpyAsync(&h_n[1], nlist + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   CLAIR_CUDA(cudaStreamSynchronize(s));
-  dfree(ub, s);
+  if (h_n[1])
+    spgemm_large<true><<<h_n[1], 32, large_num, s>>>(A.rowptr, A.col, A.val, list, B.rowptr, B.col,
+                                                     B.val, count, C.rowptr, C.col, C.val); ::clair::count_launch();
+  CLAIR_LAUNCHED();
   dfree(count, s);
-  dfree(err, s);
-  dfree(big, s);
-  CLAIR_REQUIRE(h_err == 0, CLAIR_ERR_CAPACITY, "SpGEMM row exceeds %d distinct columns", SG_LARGE);
+  dfree(list, s);
+  dfree(nlist, s);
 }
 
 // ------------------------------------------------------------------------------------
