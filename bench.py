@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--nside", type=int, default=1024)
     ap.add_argument("--eps", type=float, default=1e-2)
     ap.add_argument("--degree", type=int, default=2)
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 steps (0: skip that arm)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-nside", type=int, default=128)
     return ap.parse_args()
@@ -253,8 +254,8 @@ def run_clair(args):
     sampler = ClockSampler(gpu_index)
     mixed = timed(cl.CLAIR_MIXED, args.steps, args.warmup)
     clocks = sampler.stop()
-    fp64 = timed(cl.CLAIR_FP64, args.fp64_steps, 1)
-    e2e = timed(cl.CLAIR_MIXED, max(1, min(args.steps, 3)), 1, e2e=True)
+    fp64 = timed(cl.CLAIR_FP64, args.fp64_steps, 1) if args.fp64_steps > 0 else None
+    e2e = None if args.no_e2e else timed(cl.CLAIR_MIXED, max(1, min(args.steps, 3)), 1, e2e=True)
 
     st = mixed["stats"]
     rows = int(st.r_rows)
@@ -296,13 +297,15 @@ def run_clair(args):
         "operator_complexity": st.operator_complexity,
         "setup_rows_per_s": rows / (st.setup_ms / 1e3),
         "phases_ms": phases,
-        "fp64": {"ms_per_step": fp64["ms"], "iterations": fp64["its"][-1], "relres": fp64["rel"][-1],
-                 "setup_ms": fp64["stats"].setup_ms, "value": world * rows / (fp64["ms"] / 1e3),
-                 "local_solve_ms": fp64["stats"].phase_ms[4]},
-        "mixed_speedup_vs_fp64": fp64["ms"] / mixed["ms"],
-        "e2e": {"value": world * rows / (e2e["ms"] / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
-                "ms_per_step": e2e["ms"]},
+        "fp64": None if fp64 is None else {
+            "ms_per_step": fp64["ms"], "iterations": fp64["its"][-1], "relres": fp64["rel"][-1],
+            "setup_ms": fp64["stats"].setup_ms, "value": world * rows / (fp64["ms"] / 1e3),
+            "local_solve_ms": fp64["stats"].phase_ms[4]},
+        "mixed_speedup_vs_fp64": None if fp64 is None else fp64["ms"] / mixed["ms"],
+        "e2e": None if e2e is None else {
+            "value": world * rows / (e2e["ms"] / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+            "ms_per_step": e2e["ms"]},
         "roofline": dominant, "roofline_other": other,
         "gpu_launches": mixed["launches"],
         "clocks": clocks,

@@ -43,11 +43,16 @@ struct Error {
 // ------------------------------------------------------------------------------------
 // Stream-ordered device buffers.
 // ------------------------------------------------------------------------------------
+// The library's own stream-ordered pool on the current device.  It keeps freed memory
+// for reuse (release threshold = unlimited) instead of returning it to the driver at every
+// synchronisation, so repeated setups do not re-map their temporaries.
+cudaMemPool_t library_pool();
+
 template <class T>
 T* dalloc(size_t count, cudaStream_t s) {
   void* p = nullptr;
   if (count == 0) count = 1;
-  CLAIR_CUDA(cudaMallocAsync(&p, count * sizeof(T), s));
+  CLAIR_CUDA(cudaMallocFromPoolAsync(&p, count * sizeof(T), library_pool(), s));
   return static_cast<T*>(p);
 }
 

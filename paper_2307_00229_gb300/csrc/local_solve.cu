@@ -299,30 +299,45 @@ __global__ void bucket_rows(const int* __restrict__ Zrp, int nc, int* __restrict
                             const int* __restrict__ Zcol, const int* __restrict__ cpts,
                             const int* __restrict__ Arp, int* __restrict__ too_big,
                             unsigned long long* __restrict__ work) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nc) return;
-  const int T = Zrp[r + 1] - Zrp[r] - 1;
-  if (T <= 0) {
-    if (T == 0) Zval[Zrp[r]] = 1.0;  // only the identity entry
-    return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int T = r < nc ? Zrp[r + 1] - Zrp[r] - 1 : -1;
+  if (T == 0) Zval[Zrp[r]] = 1.0;  // only the identity entry
+  const int b = T > 0 ? ls_bucket(T) : -1;
+  if (b >= 5) atomicAdd(too_big, 1);
+  unsigned long long t3 = 0, t2 = 0, t1 = 0, g = 0;
+  // one atomic per bucket and warp: lanes of the same bucket share a block of positions
+  const int key = (b >= 0 && b < 5) ? b : -1;
+  const unsigned grp = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(grp) - 1;
+  int base = 0;
+  if (lane == leader && key >= 0) base = atomicAdd(&counts[key], __popc(grp));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (key >= 0) {
+    const int pos = base + __popc(grp & ((1u << lane) - 1u));
+    lists[(long long)b * nc + pos] = r;
+    for (int e = Zrp[r]; e < Zrp[r + 1]; ++e) {
+      const int l = Zcol[e];
+      if (l != cpts[r]) g += (unsigned long long)(Arp[l + 1] - Arp[l]);
+    }
+    t1 = (unsigned long long)T;
+    t2 = t1 * t1;
+    t3 = t2 * t1;
   }
-  const int b = ls_bucket(T);
-  if (b >= 5) {
-    atomicAdd(too_big, 1);
-    return;
+  // one atomic per warp for the work counters
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    t3 += __shfl_xor_sync(0xffffffffu, t3, o);
+    t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+    g += __shfl_xor_sync(0xffffffffu, g, o);
   }
-  const int pos = atomicAdd(&counts[b], 1);
-  lists[(long long)b * nc + pos] = r;
-  unsigned long long g = 0;
-  for (int e = Zrp[r]; e < Zrp[r + 1]; ++e) {
-    const int l = Zcol[e];
-    if (l != cpts[r]) g += (unsigned long long)(Arp[l + 1] - Arp[l]);
+  if (lane == 0 && (t1 | g)) {
+    atomicAdd(&work[0], t3);
+    atomicAdd(&work[1], t2);
+    atomicAdd(&work[2], t1);
+    atomicAdd(&work[3], g);
   }
-  const unsigned long long t = (unsigned long long)T;
-  atomicAdd(&work[0], t * t * t);
-  atomicAdd(&work[1], t * t);
-  atomicAdd(&work[2], t);
-  atomicAdd(&work[3], g);
 }
 
 // Projection on the transposed weights: rows are fine points j, entries (j, coarse i).
@@ -455,7 +470,7 @@ void project_constraint(Csr& Wt, const signed char* cf, const double* Bc, const 
   unsigned long long* nempty = dalloc<unsigned long long>(1, s);
   CLAIR_CUDA(cudaMemsetAsync(nempty, 0, sizeof(unsigned long long), s));
   if (Wt.rows) {
-    constexpr int W = 8;
+    constexpr int W = 1;  // FP64: one thread per row
     project_rows<W><<<ceil_div((long long)Wt.rows * W, 256), 256, 0, s>>>(
         Wt.rowptr, Wt.col, Wt.val, Wt.rows, cf, Bc, B, nempty); ::clair::count_launch();
   }

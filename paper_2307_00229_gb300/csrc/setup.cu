@@ -308,7 +308,10 @@ __global__ void jacobi_first(const T* __restrict__ dinv, int rows, const signed 
     x[r] = cf[r] == which ? omega * dinv[r] * b[r] : T(0);
 }
 
-static int lanes_of(const Csr& A) {
+// One thread per row for FP64 (an FP64 warp instruction costs ~16 SM cycles whatever the
+// number of active lanes); for FP32, W lanes per row, W >= the mean row length.
+static int lanes_of(const Csr& A, bool fp64) {
+  if (fp64) return 1;
   double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
   int w = 2;
   while (w < 32 && w < avg) w <<= 1;
@@ -317,6 +320,7 @@ static int lanes_of(const Csr& A) {
 
 #define CLAIR_DISPATCH_W2(W, ...)                            \
   switch (W) {                                               \
+    case 1: { constexpr int WW = 1; __VA_ARGS__; ::clair::count_launch(); } break;   \
     case 2: { constexpr int WW = 2; __VA_ARGS__; ::clair::count_launch(); } break;   \
     case 4: { constexpr int WW = 4; __VA_ARGS__; ::clair::count_launch(); } break;   \
     case 8: { constexpr int WW = 8; __VA_ARGS__; ::clair::count_launch(); } break;   \
@@ -328,7 +332,7 @@ template <class T>
 void jacobi(const Csr& A, const T* vals, const T* dinv, const signed char* cf, int which, T omega,
             const T* b, const T* xin, T* xout, cudaStream_t s) {
   if (!A.rows) return;
-  const int W = lanes_of(A);
+  const int W = lanes_of(A, sizeof(T) == 8);
   const int blocks = ceil_div((long long)A.rows * W, 256);
   CLAIR_DISPATCH_W2(W, (jacobi_kernel<WW, T><<<blocks, 256, 0, s>>>(A.rowptr, A.col, vals, dinv,
                                                                     A.rows, cf, which, omega, b,
@@ -399,12 +403,176 @@ __global__ void scale_vec(const double* __restrict__ w, double* __restrict__ v, 
     v[i] = w[i] * f;
 }
 
-__global__ void ritz_kernel(double* __restrict__ H, int ldh, int m, const int* __restrict__ steps,
-                            double* __restrict__ omega) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+struct WarpSync {
+  __device__ void operator()() const { __syncwarp(); }
+};
+
+// One warp: the leading k x k block of H (k <= 60) is copied to shared memory and the
+// Francis iteration runs there with the reflector updates split among the lanes.
+__global__ void __launch_bounds__(32) ritz_kernel(const double* __restrict__ H, int ldh, int m,
+                                                  const int* __restrict__ steps,
+                                                  double* __restrict__ omega) {
+  __shared__ double Hs[60 * 60];
+  const int lane = threadIdx.x;
   const int k = *steps < 0 ? m : *steps;
-  const double rho = hessenberg_spectral_radius(H, ldh, k);
-  *omega = rho > 0.0 ? 1.0 / rho : 1.0;
+  for (int idx = lane; idx < k * k; idx += 32) Hs[idx] = H[(idx % k) + (long long)(idx / k) * ldh];
+  __syncwarp();
+  const double rho = hessenberg_spectral_radius_lanes(Hs, k, k, lane, 32, WarpSync{});
+  if (lane == 0) *omega = rho > 0.0 ? 1.0 / rho : 1.0;
+}
+
+// ---- fused Arnoldi step (m <= AR_MAXV): six launches per step ---------------------------
+// K1  v_j = w_prev * scale (stored for j > 0), w = D^-1 A v_j, partial dots of w with
+//     v_0..v_j and with itself                       -> finalize: h1, ||w||^2 before CGS
+// K3  w -= V h1, partial dots of the new w with v_0..v_j -> finalize: h2
+// K5  w -= V h2, partial ||w||^2                      -> finalize: H column, breakdown, 1/||w||
+// The partial sums are per block in a fixed grid-stride order and the finalize kernel adds
+// them in block order, so the result does not depend on scheduling.
+constexpr int AR_MAXV = 15;
+constexpr int AR_THREADS = 256;
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_to_partial(double (&acc)[NV], int nv,
+                                                        double* __restrict__ partial) {
+  __shared__ double sh[NV][AR_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double t = warp_sum(acc[v]);
+    if (lane == 0) sh[v][wid] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    for (int k = 0; k < AR_THREADS / 32; ++k) t += sh[threadIdx.x][k];
+    partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(AR_THREADS)
+arnoldi_k1(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ av,
+           const double* __restrict__ dinv, int n, double* __restrict__ V, int j,
+           const double* __restrict__ wprev, const double* __restrict__ scale_dev,
+           double* __restrict__ w, double* __restrict__ partial) {
+  constexpr int GPW = 32 / W;
+  const double sc = *scale_dev;
+  double acc[AR_MAXV + 2];
+#pragma unroll
+  for (int v = 0; v < AR_MAXV + 2; ++v) acc[v] = 0.0;
+  const int lane = threadIdx.x & 31, sub = lane % W, grp = lane / W;
+  const long long warp = (blockIdx.x * (long long)AR_THREADS + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * AR_THREADS) >> 5;
+  for (long long base = warp * GPW; base < n; base += nwarps * GPW) {  // warp-uniform trips
+    const long long i = base + grp;
+    double s = 0.0;
+    if (i < n)
+      for (int e = rp[i] + sub; e < rp[i + 1]; e += W) s += av[e] * wprev[ci[e]];
+    s = group_sum<W>(s);
+    if (sub == 0 && i < n) {
+      const double wi = dinv[i] * (sc * s);
+      const double vj = wprev[i] * sc;
+      w[i] = wi;
+      if (j > 0) V[(long long)j * n + i] = vj;
+      // every accumulator index is static: slot k <= j holds <v_k, w>, slot AR_MAXV + 1
+      // holds <w, w>
+#pragma unroll
+      for (int k = 0; k < AR_MAXV; ++k)
+        if (k <= j) acc[k] += (k < j ? V[(long long)k * n + i] : vj) * wi;
+      acc[AR_MAXV + 1] += wi * wi;
+    }
+  }
+  block_reduce_to_partial<AR_MAXV + 2>(acc, AR_MAXV + 2, partial);
+}
+
+// w -= V[:, 0..j] h; if DOTS, partial dots of the new w with v_0..v_j, else partial ||w||^2
+template <bool DOTS>
+__global__ void __launch_bounds__(AR_THREADS)
+arnoldi_cgs(const double* __restrict__ V, int j, int n, const double* __restrict__ h,
+            double* __restrict__ w, double* __restrict__ partial) {
+  double acc[AR_MAXV + 1];
+#pragma unroll
+  for (int v = 0; v < AR_MAXV + 1; ++v) acc[v] = 0.0;
+  double hk[AR_MAXV];
+#pragma unroll
+  for (int k = 0; k < AR_MAXV; ++k) hk[k] = k <= j ? h[k] : 0.0;
+  for (long long i = blockIdx.x * (long long)AR_THREADS + threadIdx.x; i < n;
+       i += (long long)gridDim.x * AR_THREADS) {
+    double vk[AR_MAXV];
+    double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < AR_MAXV; ++k) {
+      vk[k] = k <= j ? V[(long long)k * n + i] : 0.0;
+      if (k <= j) wi = fma(-hk[k], vk[k], wi);
+    }
+    w[i] = wi;
+    if (DOTS) {
+#pragma unroll
+      for (int k = 0; k < AR_MAXV; ++k)
+        if (k <= j) acc[k] += vk[k] * wi;
+    } else {
+      acc[0] += wi * wi;
+    }
+  }
+  block_reduce_to_partial<AR_MAXV + 1>(acc, DOTS ? j + 1 : 1, partial);
+}
+
+// Adds the partials of nv values in block order.  mode 0: h1 = out[0..j], w0n2 = out[j+1];
+// mode 1: h2 = out[0..j]; mode 2: ||w||^2 = out[0], then the H column, breakdown test and
+// the scale 1/||w|| of the next basis vector (0 after a breakdown).
+__global__ void __launch_bounds__(512)
+arnoldi_finalize(const double* __restrict__ partial, int nb, int nv, int mode, int j,
+                 double* __restrict__ h1, double* __restrict__ h2, double* __restrict__ sc,
+                 double* __restrict__ H, int ldh, int* __restrict__ steps) {
+  __shared__ double out[AR_MAXV + 2];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int v = wid; v < nv; v += 16) {
+    double t = 0.0;
+    for (int b = lane; b < nb; b += 32) t += partial[(long long)v * nb + b];
+    t = warp_sum(t);
+    if (lane == 0) out[v] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  // sc: [0] ||w||^2 before orthogonalisation, [1] scale of the next basis vector
+  if (mode == 0) {
+    for (int k = 0; k <= j; ++k) h1[k] = out[k];
+    sc[0] = out[AR_MAXV + 1];
+  } else if (mode == 1) {
+    for (int k = 0; k <= j; ++k) h2[k] = out[k];
+  } else {
+    const bool active = *steps < 0;
+    for (int i = 0; i <= j; ++i) H[i + (long long)j * ldh] = active ? h1[i] + h2[i] : 0.0;
+    const double hn = sqrt(out[0]);
+    H[j + 1 + (long long)j * ldh] = active ? hn : 0.0;
+    if (active && hn <= 1e-10 * sqrt(sc[0])) *steps = j + 1;
+    sc[1] = (active && hn > 0.0) ? 1.0 / hn : 0.0;
+  }
+}
+
+// wbuf[0], wbuf[1]: the new w of step j lives in wbuf[j & 1] while K1 gathers v_j from the
+// previous step's w in the other buffer.
+static void arnoldi_fused_steps(const Csr& A, const double* dinv, int m, double* V,
+                                double* const wbuf[2], double* H, int ldh, double* h1, double* h2,
+                                double* sc, const double* one, int* steps, double* partial,
+                                cudaStream_t s) {
+  const int n = A.rows;
+  const int nb = partial_blocks();
+  const int W = lanes_of(A, true);  // FP64: one thread per row
+  for (int j = 0; j < m; ++j) {
+    // the previous w (scaled by sc[1]) becomes v_j; v_0 is already normalised
+    double* w = wbuf[j & 1];
+    const double* wprev = j == 0 ? V : wbuf[(j + 1) & 1];
+    const double* scale = j == 0 ? one : sc + 1;
+    CLAIR_DISPATCH_W2(W, (arnoldi_k1<WW><<<nb, AR_THREADS, 0, s>>>(A.rowptr, A.col, A.val, dinv, n,
+                                                                  V, j, wprev, scale, w, partial)));
+    arnoldi_finalize<<<1, 512, 0, s>>>(partial, nb, AR_MAXV + 2, 0, j, h1, h2, sc, H, ldh, steps); ::clair::count_launch();
+    arnoldi_cgs<true><<<nb, AR_THREADS, 0, s>>>(V, j, n, h1, w, partial); ::clair::count_launch();
+    arnoldi_finalize<<<1, 512, 0, s>>>(partial, nb, j + 1, 1, j, h1, h2, sc, H, ldh, steps); ::clair::count_launch();
+    arnoldi_cgs<false><<<nb, AR_THREADS, 0, s>>>(V, j, n, h2, w, partial); ::clair::count_launch();
+    arnoldi_finalize<<<1, 512, 0, s>>>(partial, nb, 1, 2, j, h1, h2, sc, H, ldh, steps); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+  }
 }
 
 // omega = 1 / rho(D^-1 A) (device scalar *omega_dev); returns it on the host.
@@ -423,7 +591,7 @@ double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed
   double* w0n2 = sc + 129;
   double* inv = sc + 130;
   int* steps = dalloc<int>(1, s);
-  double* partial = dalloc<double>((size_t)partial_blocks() * (m + 2), s);
+  double* partial = dalloc<double>((size_t)partial_blocks() * (std::max(m, AR_MAXV) + 2), s);
   const int grid = std::min(ceil_div(n, 256), 32 * sm_count());
   CLAIR_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * ldh * m, s));
   const int minus1 = -1;
@@ -432,7 +600,16 @@ double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed
   multi_dot(V, 1, V, n, wn2, partial, s);
   scale_by_inv_sqrt<<<grid, 256, 0, s>>>(V, n, wn2); ::clair::count_launch();
   CLAIR_LAUNCHED();
-  for (int j = 0; j < m; ++j) {
+  if (m <= AR_MAXV) {
+    // sc layout for the fused steps: [w0n2, next scale]; `one` = 1.0 scales v_0
+    const double h_one = 1.0;
+    CLAIR_CUDA(cudaMemcpyAsync(sc + 131, &h_one, sizeof(double), cudaMemcpyHostToDevice, s));
+    double* w2 = dalloc<double>(n, s);
+    double* const wbuf[2] = {w, w2};
+    arnoldi_fused_steps(A, dinv, m, V, wbuf, H, ldh, h1, h2, sc + 128, sc + 131, steps, partial, s);
+    dfree(w2, s);
+  }
+  for (int j = 0; j < m && m > AR_MAXV; ++j) {
     double* vj = V + (size_t)j * n;
     spmv(A, vj, w, 1.0, 0.0, s);
     dinv_scale<<<grid, 256, 0, s>>>(w, dinv, n); ::clair::count_launch();

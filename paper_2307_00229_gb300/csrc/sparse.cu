@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -37,6 +38,27 @@ int sm_count() {
 }
 
 int partial_blocks() { return 2 * sm_count(); }
+
+cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[256] = {};
+  int dev = 0;
+  CLAIR_CUDA(cudaGetDevice(&dev));
+  CLAIR_REQUIRE(dev >= 0 && dev < 256, CLAIR_ERR_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    CLAIR_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = ~0ull;
+    CLAIR_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -241,6 +263,23 @@ __global__ void sort_segments(const int* __restrict__ rowptr, int rows, int* __r
   }
 }
 
+// One warp per segment: every entry goes to its rank among the segment's (distinct) keys.
+__global__ void sort_segments_warp(const int* __restrict__ rowptr, int rows,
+                                   const int* __restrict__ key, const int* __restrict__ perm,
+                                   int* __restrict__ key_out, int* __restrict__ perm_out) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= rows) return;  // warp-uniform
+  const int b = rowptr[w], L = rowptr[w + 1] - b;
+  for (int t = lane; t < L; t += 32) {
+    const int k = key[b + t];
+    int rank = 0;
+    for (int u = 0; u < L; ++u) rank += key[b + u] < k;
+    key_out[b + rank] = k;
+    perm_out[b + rank] = perm[b + t];
+  }
+}
+
 __global__ void gather_kernel(const double* __restrict__ x, const int* __restrict__ idx,
                               double* __restrict__ y, int n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -285,12 +324,17 @@ void csr_transpose(const Csr& A, Csr& At, int** perm_out, cudaStream_t s) {
   At.rowptr = dalloc<int>(A.cols + 1, s);
   exclusive_scan(cnt, At.rowptr, A.cols, s, false);
   CLAIR_CUDA(cudaMemcpyAsync(cnt, At.rowptr, sizeof(int) * A.cols, cudaMemcpyDeviceToDevice, s));
+  int* col_fill = dalloc<int>(A.nnz, s);
+  int* perm_fill = dalloc<int>(A.nnz, s);
   At.col = dalloc<int>(A.nnz, s);
   int* perm = dalloc<int>(A.nnz, s);
   if (A.rows) transpose_fill<<<ceil_div(A.rows, 256), 256, 0, s>>>(A.rowptr, A.col, A.rows, cnt,
-                                                                     At.col, perm); ::clair::count_launch();
-  if (At.rows) sort_segments<<<ceil_div(At.rows, 128), 128, 0, s>>>(At.rowptr, At.rows, At.col, perm); ::clair::count_launch();
+                                                                     col_fill, perm_fill); ::clair::count_launch();
+  if (At.rows) sort_segments_warp<<<ceil_div((long long)At.rows * 32, 256), 256, 0, s>>>(
+      At.rowptr, At.rows, col_fill, perm_fill, At.col, perm); ::clair::count_launch();
   CLAIR_LAUNCHED();
+  dfree(col_fill, s);
+  dfree(perm_fill, s);
   if (A.val) {
     At.val = dalloc<double>(A.nnz, s);
     gather(A.val, perm, At.val, A.nnz, s);
@@ -303,9 +347,13 @@ void csr_transpose(const Csr& A, Csr& At, int** perm_out, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------------------
-// Row kernels with W lanes per row.
+// Row kernels with W lanes per row.  FP64 kernels use one thread per row: on this GPU an
+// FP64 warp instruction costs the SM's FP64 unit about 16 cycles however few lanes are
+// active, so sub-warp groups (idle lanes, shuffle-add trees) waste most of it.  FP32
+// kernels use W lanes per row, W the power of two at or above the mean row length.
 // ------------------------------------------------------------------------------------
-static int lanes_for(const Csr& A) {
+static int lanes_for(const Csr& A, bool fp64) {
+  if (fp64) return 1;
   double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
   int w = 2;
   while (w < 32 && w < avg) w <<= 1;
@@ -329,6 +377,7 @@ __global__ void rowmax_kernel(const int* __restrict__ rowptr, const int* __restr
 
 #define CLAIR_DISPATCH_W(W, ...)             \
   switch (W) {                               \
+    case 1: { constexpr int WW = 1; __VA_ARGS__; ::clair::count_launch(); } break;   \
     case 2: { constexpr int WW = 2; __VA_ARGS__; ::clair::count_launch(); } break;   \
     case 4: { constexpr int WW = 4; __VA_ARGS__; ::clair::count_launch(); } break;   \
     case 8: { constexpr int WW = 8; __VA_ARGS__; ::clair::count_launch(); } break;   \
@@ -338,7 +387,7 @@ __global__ void rowmax_kernel(const int* __restrict__ rowptr, const int* __restr
 
 void row_max_offdiag(const Csr& A, double* out, cudaStream_t s) {
   if (!A.rows) return;
-  int W = lanes_for(A);
+  int W = lanes_for(A, true);
   long long threads = (long long)A.rows * W;
   int blocks = ceil_div(threads, 256);
   CLAIR_DISPATCH_W(W, rowmax_kernel<WW><<<blocks, 256, 0, s>>>(A.rowptr, A.col, A.val, A.rows, out));
@@ -368,7 +417,7 @@ template <class T, bool RESID>
 static void spmv_launch(const Csr& A, const T* vals, const T* x, const T* b, T* y, T alpha, T beta,
                         cudaStream_t s) {
   if (!A.rows) return;
-  int W = lanes_for(A);
+  int W = lanes_for(A, sizeof(T) == 8);
   long long threads = (long long)A.rows * W;
   int blocks = ceil_div(threads, 256);
   CLAIR_DISPATCH_W(W, (spmv_kernel<WW, T, RESID><<<blocks, 256, 0, s>>>(A.rowptr, A.col, vals, A.rows,
