@@ -192,8 +192,8 @@ enum Phase {
 
 class PhaseClock {
  public:
-  void begin(int ph, cudaStream_t s);
-  void end(cudaStream_t s);
+  int begin(int ph, cudaStream_t s);    // returns the mark to close
+  void end(int mark, cudaStream_t s);
   void collect(double* ms_out);  // synchronises; adds elapsed ms per phase; clears
   ~PhaseClock();
 
@@ -208,14 +208,15 @@ class PhaseClock {
 PhaseClock* active_clock();
 void set_active_clock(PhaseClock* c);
 
-struct ClockScope {  // times a block of host code's launches into one phase
+struct ClockScope {  // times the launches a block of host code makes on `s` as one phase
   ClockScope(int ph, cudaStream_t s) : s_(s) {
-    if (active_clock()) active_clock()->begin(ph, s);
+    if (active_clock()) mark_ = active_clock()->begin(ph, s);
   }
   ~ClockScope() {
-    if (active_clock()) active_clock()->end(s_);
+    if (active_clock() && mark_ >= 0) active_clock()->end(mark_, s_);
   }
   cudaStream_t s_;
+  int mark_ = -1;
 };
 
 }  // namespace clair

@@ -20,7 +20,13 @@ void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf
                    int nc, int n, int degree, Csr& Z, cudaStream_t s);
 template <class T>
 void jacobi(const Csr& A, const T* vals, const T* dinv, const signed char* cf, int which, T omega,
-            const T* b, const T* xin, T* xout, cudaStream_t s);
+            const T* b, const T* xin, T* xout, cudaStream_t s, const T* omega_dev = nullptr);
+void smooth_modes(const Csr& M, const double* dinv, const signed char* cf, const double* omega_dev,
+                  int sweeps, double* Bv, double* tmp, cudaStream_t s);
+void transfer_solve(const Csr& Ahat, const int* cpts, Csr& Z, int precision, LocalStats& st,
+                    cudaStream_t s);
+void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const double* B,
+                      LocalStats& st, Csr* keep_t, cudaStream_t s);
 template <class T>
 void jacobi_from_zero(int rows, const T* dinv, const signed char* cf, int which, T omega,
                       const T* b, T* x, cudaStream_t s);
@@ -145,6 +151,23 @@ __global__ void inject(const double* __restrict__ x, const int* __restrict__ cpt
   if (i < nc) y[i] = x[cpts[i]];
 }
 
+// A second stream and the fork/join events of one setup (released on scope exit).
+struct SideStream {
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  SideStream() {
+    CLAIR_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    CLAIR_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CLAIR_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+  }
+  ~SideStream() {
+    if (s2) cudaStreamSynchronize(s2);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (s2) cudaStreamDestroy(s2);
+  }
+};
+
 // Builds the hierarchy from the fine operator (already copied into h->lv[0].A).
 static void setup_levels(clair_hierarchy* h, const double* B0) {
   cudaStream_t s = h->stream;
@@ -156,7 +179,8 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
     CLAIR_CUDA(cudaMemcpyAsync(L0.B_P, B0, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, s));
     CLAIR_CUDA(cudaMemcpyAsync(L0.B_R, B0, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, s));
   }
-  double* omega_dev = dalloc<double>(1, s);
+  SideStream ss;
+  double* omega_dev = dalloc<double>(p.max_levels, s);  // one weight per level, on the device
   for (int k = 0;; ++k) {
     Level& L = h->lv[k];
     const int n = L.n;
@@ -194,26 +218,23 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
       dfree(sAt, s);
       break;
     }
-    // relaxation weight and smoothed modes (zero right-hand side), A for P, A^T for R
+    // Fork.  Stream s2: relaxation weight (Arnoldi), then the mode vectors smoothed with
+    // zero right-hand side (A for P, A^T for R), the weight read on the device.  Stream s:
+    // patterns and local lAIR solves, which need neither.  Join before the projection.
+    CLAIR_CUDA(cudaEventRecord(ss.fork, s));
+    CLAIR_CUDA(cudaStreamWaitEvent(ss.s2, ss.fork, 0));
     {
-      ClockScope clk(PH_WEIGHT, s);
-      L.omega = arnoldi_weight(L.A, L.dinv, p.arnoldi_iters, p.seed + (uint64_t)k, omega_dev, s);
+      ClockScope clk(PH_WEIGHT, ss.s2);
+      arnoldi_weight(L.A, L.dinv, p.arnoldi_iters, p.seed + (uint64_t)k, omega_dev + k, ss.s2);
     }
     {
-      ClockScope clk(PH_SMOOTH, s);
-      double* tmp = dalloc<double>(n, s);
-      for (int side = 0; side < 2; ++side) {
-        const Csr& M = side == 0 ? L.A : At;
-        double* Bv = side == 0 ? L.B_P : L.B_R;
-        for (int it = 0; it < p.b_smooth_iters; ++it) {
-          jacobi<double>(M, M.val, L.dinv, L.cf, 1, L.omega, nullptr, Bv, tmp, s);
-          jacobi<double>(M, M.val, L.dinv, L.cf, 0, L.omega, nullptr, tmp, Bv, s);
-          jacobi<double>(M, M.val, L.dinv, L.cf, 0, L.omega, nullptr, Bv, tmp, s);
-          CLAIR_CUDA(cudaMemcpyAsync(Bv, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        }
-      }
-      dfree(tmp, s);
+      ClockScope clk(PH_SMOOTH, ss.s2);
+      double* tmp = dalloc<double>(n, ss.s2);
+      smooth_modes(L.A, L.dinv, L.cf, omega_dev + k, p.b_smooth_iters, L.B_P, tmp, ss.s2);
+      smooth_modes(At, L.dinv, L.cf, omega_dev + k, p.b_smooth_iters, L.B_R, tmp, ss.s2);
+      dfree(tmp, ss.s2);
     }
+    CLAIR_CUDA(cudaEventRecord(ss.join, ss.s2));
     // interpolation-strength masks for the two patterns
     // R: Algorithm 1 on A^T, walked on A, S(A^T) uses the row maxima of A^T
     // P: Algorithm 1 on A,   walked on A^T, S(A) uses the row maxima of A
@@ -227,8 +248,11 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
       build_pattern(L.A, sR, L.cf, L.cpts, L.nc, n, p.degree, L.R, s);
       build_pattern(At, sP, L.cf, L.cpts, L.nc, n, p.degree, Pt, s);
     }
-    transfer_weights(At, L.cf, L.cpts, L.R, L.B_R, p.precision, h->st, nullptr, s);
-    transfer_weights(L.A, L.cf, L.cpts, Pt, L.B_P, p.precision, h->st, &L.P, s);
+    transfer_solve(At, L.cpts, L.R, p.precision, h->st, s);
+    transfer_solve(L.A, L.cpts, Pt, p.precision, h->st, s);
+    CLAIR_CUDA(cudaStreamWaitEvent(s, ss.join, 0));
+    transfer_project(L.cf, L.cpts, L.R, L.B_R, h->st, nullptr, s);
+    transfer_project(L.cf, L.cpts, Pt, L.B_P, h->st, &L.P, s);
     Pt.release(s);
     dfree(rmaxA, s);
     dfree(rmaxAt, s);
@@ -253,6 +277,14 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
     }
     CLAIR_LAUNCHED();
     h->lv.push_back(C);
+  }
+  {
+    std::vector<double> om(p.max_levels, 1.0);
+    CLAIR_CUDA(cudaMemcpyAsync(om.data(), omega_dev, sizeof(double) * p.max_levels,
+                               cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    for (size_t k = 0; k < h->lv.size(); ++k)
+      if (h->lv[k].nc) h->lv[k].omega = om[k];
   }
   dfree(omega_dev, s);
   // coarsest level: dense inverse; float copies and work vectors everywhere

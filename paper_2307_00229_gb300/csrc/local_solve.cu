@@ -486,12 +486,27 @@ void project_constraint(Csr& Wt, const signed char* cf, const double* Bc, const 
 // projection.  On return Z.val holds the projected weights (row = coarse point) and, if
 // keep_t is set, Zt receives the transposed operator (rows = fine points) with the same
 // projected values.
+void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const double* B,
+                      LocalStats& st, Csr* keep_t, cudaStream_t s);
+
+// First half: the local lAIR solves into Z.val (no mode vector needed).
+void transfer_solve(const Csr& Ahat, const int* cpts, Csr& Z, int precision, LocalStats& st,
+                    cudaStream_t s) {
+  if (!Z.val) Z.val = dalloc<double>(Z.nnz, s);
+  local_solves(Ahat, Z.rowptr, Z.col, cpts, Z.rows, precision, Z.val, st, s);
+}
+
 void transfer_weights(const Csr& Ahat, const signed char* cf, const int* cpts, Csr& Z,
                       const double* B, int precision, LocalStats& st, Csr* keep_t,
                       cudaStream_t s) {
+  transfer_solve(Ahat, cpts, Z, precision, st, s);
+  transfer_project(cf, cpts, Z, B, st, keep_t, s);
+}
+
+// Second half: projection onto the mode constraint (needs the smoothed mode vector B).
+void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const double* B,
+                      LocalStats& st, Csr* keep_t, cudaStream_t s) {
   const int nc = Z.rows;
-  if (!Z.val) Z.val = dalloc<double>(Z.nnz, s);
-  local_solves(Ahat, Z.rowptr, Z.col, cpts, nc, precision, Z.val, st, s);
   ClockScope clk(PH_PROJECT, s);
   Csr Zt;
   int* perm = nullptr;

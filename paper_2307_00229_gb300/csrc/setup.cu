@@ -284,7 +284,8 @@ __global__ void jacobi_kernel(const int* __restrict__ rowptr, const int* __restr
                               const T* __restrict__ val, const T* __restrict__ dinv, int rows,
                               const signed char* __restrict__ cf, int which, T omega,
                               const T* __restrict__ b, const T* __restrict__ xin,
-                              T* __restrict__ xout) {
+                              T* __restrict__ xout, const T* __restrict__ omega_dev) {
+  if (omega_dev) omega = *omega_dev;  // weight produced on the device by the Arnoldi step
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int r = (int)(t / W), lane = (int)(t % W);
   const bool ok = r < rows;
@@ -330,19 +331,32 @@ static int lanes_of(const Csr& A, bool fp64) {
 
 template <class T>
 void jacobi(const Csr& A, const T* vals, const T* dinv, const signed char* cf, int which, T omega,
-            const T* b, const T* xin, T* xout, cudaStream_t s) {
+            const T* b, const T* xin, T* xout, cudaStream_t s, const T* omega_dev = nullptr) {
   if (!A.rows) return;
   const int W = lanes_of(A, sizeof(T) == 8);
   const int blocks = ceil_div((long long)A.rows * W, 256);
   CLAIR_DISPATCH_W2(W, (jacobi_kernel<WW, T><<<blocks, 256, 0, s>>>(A.rowptr, A.col, vals, dinv,
                                                                     A.rows, cf, which, omega, b,
-                                                                    xin, xout)));
+                                                                    xin, xout, omega_dev)));
   CLAIR_LAUNCHED();
 }
+
+// Mode-vector smoothing B <- CFF^sweeps(B) with a zero right-hand side and the weight
+// read from device memory (so it can follow the Arnoldi step without a host round trip).
+void smooth_modes(const Csr& M, const double* dinv, const signed char* cf, const double* omega_dev,
+                  int sweeps, double* Bv, double* tmp, cudaStream_t s) {
+  for (int it = 0; it < sweeps; ++it) {
+    jacobi<double>(M, M.val, dinv, cf, 1, 1.0, nullptr, Bv, tmp, s, omega_dev);
+    jacobi<double>(M, M.val, dinv, cf, 0, 1.0, nullptr, tmp, Bv, s, omega_dev);
+    jacobi<double>(M, M.val, dinv, cf, 0, 1.0, nullptr, Bv, tmp, s, omega_dev);
+    CLAIR_CUDA(cudaMemcpyAsync(Bv, tmp, sizeof(double) * M.rows, cudaMemcpyDeviceToDevice, s));
+  }
+}
 template void jacobi<double>(const Csr&, const double*, const double*, const signed char*, int,
-                             double, const double*, const double*, double*, cudaStream_t);
+                             double, const double*, const double*, double*, cudaStream_t,
+                             const double*);
 template void jacobi<float>(const Csr&, const float*, const float*, const signed char*, int, float,
-                            const float*, const float*, float*, cudaStream_t);
+                            const float*, const float*, float*, cudaStream_t, const float*);
 
 template <class T>
 void jacobi_from_zero(int rows, const T* dinv, const signed char* cf, int which, T omega,
@@ -575,7 +589,7 @@ static void arnoldi_fused_steps(const Csr& A, const double* dinv, int m, double*
   }
 }
 
-// omega = 1 / rho(D^-1 A) (device scalar *omega_dev); returns it on the host.
+// Enqueues omega = 1 / rho(D^-1 A) into the device scalar *omega_dev (no host sync).
 double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed,
                       double* omega_dev, cudaStream_t s) {
   const int n = A.rows;
@@ -626,16 +640,13 @@ double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed
   }
   ritz_kernel<<<1, 32, 0, s>>>(H, ldh, m, steps, omega_dev); ::clair::count_launch();
   CLAIR_LAUNCHED();
-  double om = 1.0;
-  CLAIR_CUDA(cudaMemcpyAsync(&om, omega_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CLAIR_CUDA(cudaStreamSynchronize(s));
   dfree(V, s);
   dfree(w, s);
   dfree(H, s);
   dfree(sc, s);
   dfree(steps, s);
   dfree(partial, s);
-  return om;
+  return 0.0;  // the weight is in *omega_dev once the stream reaches this point
 }
 
 // ------------------------------------------------------------------------------------

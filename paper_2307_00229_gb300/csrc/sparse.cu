@@ -68,7 +68,7 @@ static thread_local PhaseClock* g_clock = nullptr;
 PhaseClock* active_clock() { return g_clock; }
 void set_active_clock(PhaseClock* c) { g_clock = c; }
 
-void PhaseClock::begin(int ph, cudaStream_t s) {
+int PhaseClock::begin(int ph, cudaStream_t s) {
   if (n_ == cap_) {
     int cap = cap_ ? 2 * cap_ : 64;
     Mark* m = new Mark[cap];
@@ -82,14 +82,15 @@ void PhaseClock::begin(int ph, cudaStream_t s) {
   cudaEventCreate(&m.a);
   cudaEventCreate(&m.b);
   cudaEventRecord(m.a, s);
+  return n_ - 1;
 }
 
-void PhaseClock::end(cudaStream_t s) {
-  if (n_) cudaEventRecord(marks_[n_ - 1].b, s);
+void PhaseClock::end(int mark, cudaStream_t s) {
+  if (mark >= 0 && mark < n_) cudaEventRecord(marks_[mark].b, s);
 }
 
 void PhaseClock::collect(double* ms_out) {
-  if (n_) cudaEventSynchronize(marks_[n_ - 1].b);
+  for (int i = 0; i < n_; ++i) cudaEventSynchronize(marks_[i].b);
   for (int i = 0; i < n_; ++i) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, marks_[i].a, marks_[i].b) == cudaSuccess) ms_out[marks_[i].ph] += ms;
