@@ -59,6 +59,8 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
              unsigned long long* __restrict__ nsingular) {
   constexpr int GPW = 32 / G;
   __shared__ int zl[LS_WARPS * GPW][G];
+  __shared__ int pre[LS_WARPS * GPW][G + 1];
+  __shared__ Real rhs_s[LS_WARPS * GPW][G];
   __shared__ Real tile[LS_WARPS * GPW][G][G + 1];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -89,26 +91,44 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
   zl[gib][p] = fcol;
   __syncwarp();
 
-  // gather row p of the local matrix (row l_p of Ahat restricted to the pattern) and
-  // the right-hand side -Ahat[l_p, i]
-  Real rhs = 0;
+  // Gather the local matrix (row p = row l_p of Ahat restricted to the pattern) and the
+  // right-hand side -Ahat[l_p, i].  The rows' entries are flattened (a group scan of the
+  // row lengths) and spread over all G lanes so their loads are independent.
 #pragma unroll
   for (int q = 0; q < G; ++q) tile[gib][p][q] = Real(0);
-  if (live && p < T) {
-    for (int e = Arp[fcol]; e < Arp[fcol + 1]; ++e) {
-      const int c = Acol[e];
-      if (c == i) {
-        rhs = Real(-Aval[e]);
-      } else {
-        const int q = find_sorted(zl[gib], T, c);
-        if (q >= 0) tile[gib][p][q] = Real(Aval[e]);
-      }
+  rhs_s[gib][p] = Real(0);
+  const int row0 = (live && p < T) ? Arp[fcol] : 0;
+  int rlen = (live && p < T) ? Arp[fcol + 1] - row0 : 0;
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, rlen, o, G);
+    if (p >= o) rlen += t;
+  }
+  pre[gib][p + 1] = rlen;  // inclusive prefix
+  if (p == 0) pre[gib][0] = 0;
+  __syncwarp();
+  const int total = pre[gib][G];
+  for (int t = p; t < total; t += G) {
+    int lo = 0, hi = G;  // row r with pre[r] <= t < pre[r + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pre[gib][mid] <= t) lo = mid; else hi = mid;
+    }
+    const int e = Arp[zl[gib][lo]] + (t - pre[gib][lo]);
+    const int c = Acol[e];
+    if (c == i) {
+      rhs_s[gib][lo] = Real(-Aval[e]);
+    } else {
+      const int q = find_sorted(zl[gib], T, c);
+      if (q >= 0) tile[gib][lo][q] = Real(Aval[e]);
     }
   }
+  __syncwarp();
+  (void)row0;
   Real a[G];
 #pragma unroll
   for (int q = 0; q < G; ++q) a[q] = tile[gib][p][q];
-  Real b = rhs;
+  Real b = rhs_s[gib][p];
 
   // elimination with implicit partial pivoting
   bool done = !(live && p < T);
@@ -210,16 +230,35 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
   for (int q = 0; q < TMAX; ++q) row[q] = Real(0);
   rhs[t] = Real(0);
   __syncthreads();
-  if (t < T) {
-    const int l = zl[t];
-    for (int e = Arp[l]; e < Arp[l + 1]; ++e) {
-      const int c = Acol[e];
-      if (c == i) {
-        rhs[t] = Real(-Aval[e]);
-      } else {
-        const int q = find_sorted(zl, T, c);
-        if (q >= 0) row[q] = Real(Aval[e]);
-      }
+  // flattened gather: block scan of the row lengths, then all threads over the entries
+  __shared__ int pre[TMAX + 1];
+  __shared__ int wsum[TMAX / 32];
+  int rlen = t < T ? Arp[zl[t] + 1] - Arp[zl[t]] : 0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, rlen, o);
+    if (lane >= o) rlen += v;
+  }
+  if (lane == 31) wsum[wid] = rlen;
+  __syncthreads();
+  for (int w = 0; w < wid; ++w) rlen += wsum[w];
+  pre[t + 1] = rlen;
+  if (t == 0) pre[0] = 0;
+  __syncthreads();
+  const int total = pre[TMAX];
+  for (int f = t; f < total; f += TMAX) {
+    int lo = 0, hi = TMAX;  // row r with pre[r] <= f < pre[r + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pre[mid] <= f) lo = mid; else hi = mid;
+    }
+    const int e = Arp[zl[lo]] + (f - pre[lo]);
+    const int c = Acol[e];
+    if (c == i) {
+      rhs[lo] = Real(-Aval[e]);
+    } else {
+      const int q = find_sorted(zl, T, c);
+      if (q >= 0) tile[lo * PITCH + q] = Real(Aval[e]);
     }
   }
   bool done = t >= T;

@@ -651,8 +651,6 @@ void validate_cf(const signed char* cf, int n, cudaStream_t s) {
 // independent of scheduling.  Rows whose product count exceeds the small table go to a
 // one-warp-per-block path with a large dynamic table.
 // ------------------------------------------------------------------------------------
-constexpr int SG_SMALL = 1024;        // slots per warp (small path)
-constexpr int SG_WARPS = 4;           // warps per block (small path)
 constexpr int SG_LARGE = 16384;       // slots (large path)
 
 __device__ __forceinline__ int sg_hash(int key, int cap) {
@@ -744,26 +742,161 @@ __device__ void spgemm_row(int r, const int* __restrict__ Arp, const int* __rest
   }
 }
 
-// Small table, one warp per row.  Symbolic: every row.  Numeric: rows whose count fits
-// half of the table.
-template <bool NUMERIC>
-__global__ void __launch_bounds__(32 * SG_WARPS)
-spgemm_small(const int* __restrict__ Arp, const int* __restrict__ Acol,
-             const double* __restrict__ Aval, int rows, const int* __restrict__ Brp,
-             const int* __restrict__ Bcol, const double* __restrict__ Bval,
-             int* __restrict__ count, const int* __restrict__ Crp, int* __restrict__ Ccol,
-             double* __restrict__ Cval) {
-  __shared__ int keys[SG_WARPS][SG_SMALL];
-  __shared__ double vals[NUMERIC ? SG_WARPS : 1][NUMERIC ? SG_SMALL : 1];
-  const int w = threadIdx.x >> 5;
-  const int r = blockIdx.x * SG_WARPS + w;
-  if (r >= rows) return;  // warp-uniform
-  if (NUMERIC && (Crp[r + 1] - Crp[r]) > SG_SMALL / 2) return;
-  spgemm_row<NUMERIC>(r, Arp, Acol, Aval, Brp, Bcol, Bval, keys[w], NUMERIC ? vals[w] : nullptr,
-                      SG_SMALL, count, Crp, Ccol, Cval);
+// The same row product with all 32 lanes on the row's flattened product list: product p
+// (k-major order: entry ea of A's row, then the entries of B's row Acol[ea]) is found from
+// a warp-scanned prefix of the B-row lengths.  Products are taken 32 at a time; within a
+// chunk, lanes whose products share a column are combined by the lowest such lane in lane
+// order before one add into the table, so every sum has a fixed order.  The row uses a
+// table of rcap <= CAP slots sized from its product count (symbolic) or its exact
+// output count (numeric), so clearing and compacting cost what the row needs.
+// Tiers: CAP 512 / prefix 512 with four warps per block for the bulk of the rows, CAP
+// 4096 / prefix 2048 with one warp per block, then the sequential large table above.
+constexpr int SG_CAP1 = 512, SG_PRE1 = 512, SG_WARPS1 = 4;
+constexpr int SG_CAP2 = 4096, SG_PRE2 = 2048;
+
+__device__ __forceinline__ int sg_pow2_at_least(int v, int lo, int hi) {
+  int c = lo;
+  while (c < v && c < hi) c <<= 1;
+  return c;
 }
 
-// Large dynamic table, one warp per listed row.
+template <bool NUMERIC, int CAP, int PCAP>
+__device__ void spgemm_row_flat(int r, const int* __restrict__ Arp, const int* __restrict__ Acol,
+                                const double* __restrict__ Aval, const int* __restrict__ Brp,
+                                const int* __restrict__ Bcol, const double* __restrict__ Bval,
+                                int* keys, double* vals, int* prefix, double* stage,
+                                int* __restrict__ count, const int* __restrict__ Crp,
+                                int* __restrict__ Ccol, double* __restrict__ Cval) {
+  const int lane = threadIdx.x & 31;
+  const int a0 = Arp[r], nA = Arp[r + 1] - a0;  // nA <= PCAP (checked by the caller)
+  // prefix[t] = number of products of A entries 0..t-1
+  int base = 0;
+  for (int c = 0; c < nA; c += 32) {
+    int len = 0;
+    if (c + lane < nA) {
+      const int k = Acol[a0 + c + lane];
+      len = Brp[k + 1] - Brp[k];
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (c + lane < nA) prefix[c + lane + 1] = base + incl;
+    base += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) prefix[0] = 0;
+  const int total = base;
+  const int rcap = sg_pow2_at_least(2 * (NUMERIC ? (Crp[r + 1] - Crp[r]) : total), 32, CAP);
+  for (int s = lane; s < rcap; s += 32) {
+    keys[s] = -1;
+    if (NUMERIC) vals[s] = 0.0;
+  }
+  __syncwarp();
+  int mine = 0;
+  bool full = false;
+  for (int p0 = 0; p0 < total; p0 += 32) {
+    const int p = p0 + lane;
+    int slot = -1;
+    double prod = 0.0;
+    if (p < total) {
+      int lo = 0, hi = nA;  // largest t with prefix[t] <= p
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= p) lo = mid; else hi = mid;
+      }
+      const int ea = a0 + lo;
+      const int k = Acol[ea];
+      const int eb = Brp[k] + (p - prefix[lo]);
+      bool is_new = false;
+      slot = sg_insert(keys, rcap, Bcol[eb], &is_new);
+      if (slot < 0) full = true;
+      if (is_new) ++mine;
+      if (NUMERIC) prod = __dmul_rn(Aval[ea], Bval[eb]);
+    }
+    if (__any_sync(0xffffffffu, full)) break;
+    if (NUMERIC) {
+      stage[lane] = prod;
+      const unsigned grp = __match_any_sync(0xffffffffu, slot);
+      __syncwarp();
+      if (slot >= 0 && lane == __ffs(grp) - 1) {
+        double sum = prod;
+        for (unsigned g = grp & (grp - 1); g; g &= g - 1) sum = __dadd_rn(sum, stage[__ffs(g) - 1]);
+        vals[slot] = __dadd_rn(vals[slot], sum);
+      }
+      __syncwarp();
+    }
+  }
+  if (!NUMERIC) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0) count[r] = __any_sync(0xffffffffu, full) ? -1 : mine;
+    return;
+  }
+  __syncwarp();
+  int ntot = 0;
+  for (int c = 0; c < rcap; c += 32) {
+    const int key = keys[c + lane];
+    const double v = vals[c + lane];
+    const unsigned occ = __ballot_sync(0xffffffffu, key >= 0);
+    __syncwarp();
+    if (key >= 0) {
+      const int dst = ntot + __popc(occ & ((1u << lane) - 1u));
+      keys[dst] = key;
+      vals[dst] = v;
+    }
+    ntot += __popc(occ);
+    __syncwarp();
+  }
+  const int obase = Crp[r];
+  for (int t = lane; t < ntot; t += 32) {
+    const int key = keys[t];
+    int rank = 0;
+    for (int u = 0; u < ntot; ++u) rank += keys[u] < key;
+    Ccol[obase + rank] = key;
+    Cval[obase + rank] = vals[t];
+  }
+}
+
+// shared memory of one warp of a flat tier: stage, (vals), keys, prefix
+__host__ __device__ constexpr size_t sg_warp_bytes(bool numeric, int cap, int pcap) {
+  return sizeof(double) * 32 + (numeric ? sizeof(double) * cap : 0) + sizeof(int) * cap +
+         sizeof(int) * (pcap + 8);
+}
+
+// One warp per row, rows 0..nrows-1 or list[0..nrows-1].  Symbolic: rows whose A row is
+// longer than PCAP get count -1 (next tier).  Numeric: rows whose output count exceeds
+// CAP/2 or whose A row exceeds PCAP are left to the next tier.
+template <bool NUMERIC, int CAP, int PCAP, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS)
+spgemm_flat(const int* __restrict__ Arp, const int* __restrict__ Acol,
+            const double* __restrict__ Aval, const int* __restrict__ list, int nrows,
+            const int* __restrict__ Brp, const int* __restrict__ Bcol,
+            const double* __restrict__ Bval, int* __restrict__ count, const int* __restrict__ Crp,
+            int* __restrict__ Ccol, double* __restrict__ Cval) {
+  extern __shared__ __align__(16) unsigned char sg_smem[];
+  const int w = threadIdx.x >> 5;
+  unsigned char* mine = sg_smem + (size_t)w * sg_warp_bytes(NUMERIC, CAP, PCAP);
+  double* stage = reinterpret_cast<double*>(mine);
+  double* vals = NUMERIC ? stage + 32 : nullptr;
+  int* keys = reinterpret_cast<int*>(mine + sizeof(double) * 32 +
+                                     (NUMERIC ? sizeof(double) * CAP : 0));
+  int* prefix = keys + CAP;
+  const int idx = blockIdx.x * WARPS + w;
+  if (idx >= nrows) return;  // warp-uniform
+  const int r = list ? list[idx] : idx;
+  const bool long_row = (Arp[r + 1] - Arp[r]) > PCAP;
+  if (!NUMERIC && long_row) {
+    if ((threadIdx.x & 31) == 0) count[r] = -1;
+    return;
+  }
+  if (NUMERIC && ((Crp[r + 1] - Crp[r]) > CAP / 2 || long_row)) return;
+  spgemm_row_flat<NUMERIC, CAP, PCAP>(r, Arp, Acol, Aval, Brp, Bcol, Bval, keys, vals, prefix,
+                                      stage, count, Crp, Ccol, Cval);
+}
+
+// Large dynamic table, one warp per listed row (sequential over the A row's entries).
 template <bool NUMERIC>
 __global__ void __launch_bounds__(32)
 spgemm_large(const int* __restrict__ Arp, const int* __restrict__ Acol,
@@ -779,12 +912,18 @@ spgemm_large(const int* __restrict__ Arp, const int* __restrict__ Acol,
                       SG_LARGE, count, Crp, Ccol, Cval);
 }
 
-// list the rows with count == -1 (mode 0) or with more than `limit` entries (mode 1)
-__global__ void spgemm_collect(const int* __restrict__ count, const int* __restrict__ Crp, int rows,
-                               int mode, int limit, int* __restrict__ list, int* __restrict__ n) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= rows) return;
-  const bool take = mode == 0 ? count[r] < 0 : (Crp[r + 1] - Crp[r]) > limit;
+// Lists (from `src` rows, or all rows when src == nullptr) the rows with count == -1
+// (mode 0) or, mode 1, the rows a numeric tier left out: more than `lim_cnt` output
+// entries or more than `lim_nA` A entries.
+__global__ void spgemm_collect(const int* __restrict__ count, const int* __restrict__ Crp,
+                               const int* __restrict__ Arp, const int* __restrict__ src,
+                               int nsrc, int mode, int lim_cnt, int lim_nA,
+                               int* __restrict__ list, int* __restrict__ n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nsrc) return;
+  const int r = src ? src[t] : t;
+  const bool take = mode == 0 ? count[r] < 0
+                              : ((Crp[r + 1] - Crp[r]) > lim_cnt || (Arp[r + 1] - Arp[r]) > lim_nA);
   if (take) list[atomicAdd(n, 1)] = r;
 }
 
@@ -842,70 +981,103 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   C.cols = B.cols;
   const int rows = A.rows;
   int* count = dalloc<int>(rows + 1, s);
-  int* list = dalloc<int>(rows, s);
-  int* nlist = dalloc<int>(2, s);
-  CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 2 * sizeof(int), s));
-  const size_t large_sym = sizeof(int) * SG_LARGE;
-  const size_t large_num = (sizeof(int) + sizeof(double)) * SG_LARGE;
+  int* list1 = dalloc<int>(rows, s);
+  int* list2 = dalloc<int>(rows, s);
+  int* nlist = dalloc<int>(4, s);
+  CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 4 * sizeof(int), s));
+  const size_t t1_sym = SG_WARPS1 * sg_warp_bytes(false, SG_CAP1, SG_PRE1);
+  const size_t t1_num = SG_WARPS1 * sg_warp_bytes(true, SG_CAP1, SG_PRE1);
+  const size_t t2_sym = sg_warp_bytes(false, SG_CAP2, SG_PRE2);
+  const size_t t2_num = sg_warp_bytes(true, SG_CAP2, SG_PRE2);
+  const size_t t3_sym = sizeof(int) * SG_LARGE;
+  const size_t t3_num = (sizeof(int) + sizeof(double)) * SG_LARGE;
+  auto t1s = spgemm_flat<false, SG_CAP1, SG_PRE1, SG_WARPS1>;
+  auto t1n = spgemm_flat<true, SG_CAP1, SG_PRE1, SG_WARPS1>;
+  auto t2s = spgemm_flat<false, SG_CAP2, SG_PRE2, 1>;
+  auto t2n = spgemm_flat<true, SG_CAP2, SG_PRE2, 1>;
   static bool attr_set = false;
   if (!attr_set) {
+    CLAIR_CUDA(cudaFuncSetAttribute(t1s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t1_sym));
+    CLAIR_CUDA(cudaFuncSetAttribute(t1n, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t1_num));
+    CLAIR_CUDA(cudaFuncSetAttribute(t2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t2_sym));
+    CLAIR_CUDA(cudaFuncSetAttribute(t2n, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t2_num));
     CLAIR_CUDA(cudaFuncSetAttribute(spgemm_large<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)large_sym));
+                                    (int)t3_sym));
     CLAIR_CUDA(cudaFuncSetAttribute(spgemm_large<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)large_num));
+                                    (int)t3_num));
     attr_set = true;
   }
-  const int grid_small = ceil_div(rows, SG_WARPS);
-  const int g = ceil_div(rows, 256);
-  // symbolic: small tables for every row, large tables for the rows that overflowed
+  auto read_count = [&](int* dev) {
+    int h = 0;
+    CLAIR_CUDA(cudaMemcpyAsync(&h, dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    return h;
+  };
+  // ---- symbolic: tier 1 for every row, then the rows it could not hold ----
   if (rows) {
-    spgemm_small<false><<<grid_small, 32 * SG_WARPS, 0, s>>>(A.rowptr, A.col, A.val, rows, B.rowptr,
-                                                            B.col, B.val, count, nullptr, nullptr,
-                                                            nullptr); ::clair::count_launch();
-    spgemm_collect<<<g, 256, 0, s>>>(count, nullptr, rows, 0, 0, list, nlist); ::clair::count_launch();
+    t1s<<<ceil_div(rows, SG_WARPS1), 32 * SG_WARPS1, t1_sym, s>>>(
+        A.rowptr, A.col, A.val, nullptr, rows, B.rowptr, B.col, B.val, count, nullptr, nullptr,
+        nullptr); ::clair::count_launch();
+    spgemm_collect<<<ceil_div(rows, 256), 256, 0, s>>>(count, nullptr, A.rowptr, nullptr, rows, 0,
+                                                       0, 0, list1, nlist); ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
-  int h_n[2] = {0, 0};
-  CLAIR_CUDA(cudaMemcpyAsync(h_n, nlist, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CLAIR_CUDA(cudaStreamSynchronize(s));
-  if (h_n[0]) {
-    spgemm_large<false><<<h_n[0], 32, large_sym, s>>>(A.rowptr, A.col, A.val, list, B.rowptr, B.col,
-                                                      B.val, count, nullptr, nullptr, nullptr); ::clair::count_launch();
+  const int n1 = rows ? read_count(nlist) : 0;
+  if (n1) {
+    t2s<<<n1, 32, t2_sym, s>>>(A.rowptr, A.col, A.val, list1, n1, B.rowptr, B.col, B.val, count,
+                               nullptr, nullptr, nullptr); ::clair::count_launch();
+    spgemm_collect<<<ceil_div(n1, 256), 256, 0, s>>>(count, nullptr, A.rowptr, list1, n1, 0, 0, 0,
+                                                     list2, nlist + 1); ::clair::count_launch();
     CLAIR_LAUNCHED();
-    CLAIR_CUDA(cudaMemsetAsync(nlist, 0, sizeof(int), s));
-    spgemm_collect<<<g, 256, 0, s>>>(count, nullptr, rows, 0, 0, list, nlist); ::clair::count_launch();
-    CLAIR_LAUNCHED();
-    int still = 0;
-    CLAIR_CUDA(cudaMemcpyAsync(&still, nlist, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CLAIR_CUDA(cudaStreamSynchronize(s));
-    if (still) {
-      dfree(count, s);
-      dfree(list, s);
-      dfree(nlist, s);
-      CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "SpGEMM: %d rows exceed %d distinct columns", still,
-                    SG_LARGE);
+    const int n2 = read_count(nlist + 1);
+    if (n2) {
+      spgemm_large<false><<<n2, 32, t3_sym, s>>>(A.rowptr, A.col, A.val, list2, B.rowptr, B.col,
+                                                 B.val, count, nullptr, nullptr, nullptr); ::clair::count_launch();
+      CLAIR_CUDA(cudaMemsetAsync(nlist + 2, 0, sizeof(int), s));
+      spgemm_collect<<<ceil_div(n2, 256), 256, 0, s>>>(count, nullptr, A.rowptr, list2, n2, 0, 0, 0,
+                                                       list1, nlist + 2); ::clair::count_launch();
+      CLAIR_LAUNCHED();
+      const int still = read_count(nlist + 2);
+      if (still) {
+        dfree(count, s);
+        dfree(list1, s);
+        dfree(list2, s);
+        dfree(nlist, s);
+        CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "SpGEMM: %d rows exceed %d distinct columns",
+                      still, SG_LARGE);
+      }
     }
   }
   C.rowptr = dalloc<int>(rows + 1, s);
   C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true);
   C.col = dalloc<int>(C.nnz, s);
   C.val = dalloc<double>(C.nnz, s);
-  // numeric: rows up to half a small table there, the others in large tables
+  // ---- numeric: each row in the first tier that holds it ----
+  CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 4 * sizeof(int), s));
   if (rows) {
-    spgemm_small<true><<<grid_small, 32 * SG_WARPS, 0, s>>>(A.rowptr, A.col, A.val, rows, B.rowptr,
-                                                           B.col, B.val, count, C.rowptr, C.col,
-                                                           C.val); ::clair::count_launch();
-    spgemm_collect<<<g, 256, 0, s>>>(count, C.rowptr, rows, 1, SG_SMALL / 2, list, nlist + 1); ::clair::count_launch();
+    t1n<<<ceil_div(rows, SG_WARPS1), 32 * SG_WARPS1, t1_num, s>>>(
+        A.rowptr, A.col, A.val, nullptr, rows, B.rowptr, B.col, B.val, count, C.rowptr, C.col,
+        C.val); ::clair::count_launch();
+    spgemm_collect<<<ceil_div(rows, 256), 256, 0, s>>>(count, C.rowptr, A.rowptr, nullptr, rows, 1,
+                                                       SG_CAP1 / 2, SG_PRE1, list1, nlist); ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
-  CLAIR_CUDA(cudaMemcpyAsync(&h_n[1], nlist + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CLAIR_CUDA(cudaStreamSynchronize(s));
-  if (h_n[1])
-    spgemm_large<true><<<h_n[1], 32, large_num, s>>>(A.rowptr, A.col, A.val, list, B.rowptr, B.col,
-                                                     B.val, count, C.rowptr, C.col, C.val); ::clair::count_launch();
+  const int m1 = rows ? read_count(nlist) : 0;
+  if (m1) {
+    t2n<<<m1, 32, t2_num, s>>>(A.rowptr, A.col, A.val, list1, m1, B.rowptr, B.col, B.val, count,
+                               C.rowptr, C.col, C.val); ::clair::count_launch();
+    spgemm_collect<<<ceil_div(m1, 256), 256, 0, s>>>(count, C.rowptr, A.rowptr, list1, m1, 1,
+                                                     SG_CAP2 / 2, SG_PRE2, list2, nlist + 1); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+    const int m2 = read_count(nlist + 1);
+    if (m2)
+      spgemm_large<true><<<m2, 32, t3_num, s>>>(A.rowptr, A.col, A.val, list2, B.rowptr, B.col,
+                                                B.val, count, C.rowptr, C.col, C.val); ::clair::count_launch();
+  }
   CLAIR_LAUNCHED();
   dfree(count, s);
-  dfree(list, s);
+  dfree(list1, s);
+  dfree(list2, s);
   dfree(nlist, s);
 }
 
