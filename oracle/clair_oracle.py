@@ -351,9 +351,14 @@ def _row_least_squares(Bc_J: np.ndarray, target: np.ndarray) -> np.ndarray:
 
 
 def clair_algorithm1(Ahat, cf: np.ndarray, B: np.ndarray, Wpat: sp.csc_matrix,
-                     params: Params) -> sp.csc_matrix:
+                     params: Params, cpts: np.ndarray | None = None) -> sp.csc_matrix:
     """Algorithm 1 of the paper on operator ``Ahat``: returns the F-rows ``W`` (n x n_c,
     zero on C rows) of ``P = [W; I]`` obeying the pattern ``Wpat``.
+
+    ``cpts`` (default: all C-points of ``cf`` in increasing order) names the C-point of each
+    column of ``Wpat``; passing a subset of columns runs the algorithm on those columns
+    only, which is exact for every F row whose pattern row lies inside the subset (every
+    step of the algorithm is local to a column block or to an F row).
 
     Steps, in the paper's order:
       * tentative ``w_t`` from ``[-A_fc, I]`` on the pattern;
@@ -367,12 +372,14 @@ def clair_algorithm1(Ahat, cf: np.ndarray, B: np.ndarray, Wpat: sp.csc_matrix,
     """
     Ahat = csr_of(Ahat)
     n = Ahat.shape[0]
-    cpts = np.flatnonzero(cf == C_PT)
+    if cpts is None:
+        cpts = np.flatnonzero(cf == C_PT)
     nc = cpts.size
     B = B.reshape(n, -1)
     Bc = B[cpts]
     Wpat = Wpat.tocsc()
     Wpat.sort_indices()
+    assert Wpat.shape[1] == nc
 
     def block(rows, cols):
         """Dense ``Ahat[rows, cols]`` (``cols`` sorted ascending)."""

@@ -80,6 +80,10 @@ struct clair_hierarchy {
   double setup_ms = 0.0;
   double phase_ms[clair::PH_COUNT] = {};   // setup, per phase
   double solve_ms[clair::PH_COUNT] = {};   // last solve, per phase
+  cudaGraphExec_t cycle_exec = nullptr;     // captured fine-level V(1,1) cycle
+  long long cycle_kernels = 0;              // kernels in that graph
+  double* vin = nullptr;                    // its fixed input and output vectors
+  double* zout = nullptr;
 };
 
 namespace clair {
@@ -142,6 +146,10 @@ static void release_all(clair_hierarchy* h) {
   dfree(k.scal, s);
   dfree(k.partial, s);
   if (k.host) cudaFreeHost(k.host);
+  if (h->cycle_exec) cudaGraphExecDestroy(h->cycle_exec);
+  h->cycle_exec = nullptr;
+  dfree(h->vin, s);
+  dfree(h->zout, s);
   k.host = nullptr;
 }
 
@@ -396,8 +404,8 @@ static void vcycle_level(clair_hierarchy* h, int k) {
   CLAIR_CUDA(cudaMemcpyAsync(x, y, sizeof(T) * L.n, cudaMemcpyDeviceToDevice, s));
 }
 
-// z = M^-1 v on level k (float64 in and out).
-static void apply_precond(clair_hierarchy* h, int k, const double* v, double* z) {
+// z = M^-1 v on level k (float64 in and out), launching every kernel.
+static void apply_precond_direct(clair_hierarchy* h, int k, const double* v, double* z) {
   cudaStream_t s = h->stream;
   Level& L = h->lv[k];
   if (h->p.precision == CLAIR_MIXED) {
@@ -409,6 +417,49 @@ static void apply_precond(clair_hierarchy* h, int k, const double* v, double* z)
     vcycle_level<double>(h, k);
     CLAIR_CUDA(cudaMemcpyAsync(z, L.x64, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
   }
+}
+
+// The fine-level cycle is a fixed sequence of about ten kernels per level; it is captured
+// once into a CUDA graph with fixed input / output buffers (h->vin, h->zout) and replayed,
+// so each FGMRES iteration pays one graph launch instead of every kernel launch.
+static void build_cycle_graph(clair_hierarchy* h) {
+  cudaStream_t cs;
+  CLAIR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t keep = h->stream;
+  h->stream = cs;
+  const long long before = launch_count();
+  cudaGraph_t g = nullptr;
+  try {
+    CLAIR_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    apply_precond_direct(h, 0, h->vin, h->zout);
+    CLAIR_CUDA(cudaStreamEndCapture(cs, &g));
+    CLAIR_CUDA(cudaGraphInstantiate(&h->cycle_exec, g, 0));
+  } catch (...) {
+    cudaGraph_t dummy;
+    cudaStreamEndCapture(cs, &dummy);
+    if (g) cudaGraphDestroy(g);
+    h->stream = keep;
+    cudaStreamDestroy(cs);
+    throw;
+  }
+  h->cycle_kernels = launch_count() - before;
+  cudaGraphDestroy(g);
+  h->stream = keep;
+  cudaStreamDestroy(cs);
+}
+
+// z = M^-1 v on level k; the fine level replays the captured cycle.
+static void apply_precond(clair_hierarchy* h, int k, const double* v, double* z) {
+  if (k != 0 || !h->cycle_exec) {
+    apply_precond_direct(h, k, v, z);
+    return;
+  }
+  cudaStream_t s = h->stream;
+  const size_t bytes = sizeof(double) * h->lv[0].n;
+  CLAIR_CUDA(cudaMemcpyAsync(h->vin, v, bytes, cudaMemcpyDeviceToDevice, s));
+  CLAIR_CUDA(cudaGraphLaunch(h->cycle_exec, s));
+  for (long long i = 0; i < h->cycle_kernels; ++i) count_launch();
+  CLAIR_CUDA(cudaMemcpyAsync(z, h->zout, bytes, cudaMemcpyDeviceToDevice, s));
 }
 
 // --- FGMRES -----------------------------------------------------------------------------
@@ -658,6 +709,10 @@ clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, cons
     setup_levels(h, B);
     alloc_krylov(h);
     set_active_clock(nullptr);
+    h->vin = dalloc<double>(n, s);
+    h->zout = dalloc<double>(n, s);
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    build_cycle_graph(h);
     clock.collect(h->phase_ms);
     CLAIR_CUDA(cudaEventRecord(e1, s));
     CLAIR_CUDA(cudaEventSynchronize(e1));

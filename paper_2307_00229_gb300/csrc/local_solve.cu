@@ -25,9 +25,12 @@
 
 namespace clair {
 
-constexpr int LS_BUCKETS = 6;                     // T in [1,8], (8,16], (16,32], (32,64], (64,128], (128,256]
+// Solvable buckets: T in [1,8], (8,16], (16,32], (32,64], (64,128], (128,512]; bucket 6
+// counts systems larger than LS_TBIG (refused).
+constexpr int LS_BUCKETS = 6;
+constexpr int LS_TBIG = 512;
 __host__ __device__ inline int ls_bucket(int T) {
-  return T <= 8 ? 0 : T <= 16 ? 1 : T <= 32 ? 2 : T <= 64 ? 3 : T <= 128 ? 4 : 5;
+  return T <= 8 ? 0 : T <= 16 ? 1 : T <= 32 ? 2 : T <= 64 ? 3 : T <= 128 ? 4 : T <= LS_TBIG ? 5 : 6;
 }
 
 // Position of column c in the sorted list z[0..T-1], or -1.
@@ -329,6 +332,137 @@ static size_t cta_smem() {
 }
 
 // ------------------------------------------------------------------------------------
+// Large systems (128 < T <= 512, rare: long rows on coarse levels of advective problems):
+// one block of 256 threads per system, the matrix in a global scratch tile (row-major,
+// leading dimension `pitch`), thread t owning rows t, t+256, ...; same implicit partial
+// pivoting as above.
+// ------------------------------------------------------------------------------------
+constexpr int LB_THREADS = 256;
+
+template <class Real>
+__global__ void __launch_bounds__(LB_THREADS)
+lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
+           const double* __restrict__ Aval, const int* __restrict__ Zrp,
+           const int* __restrict__ Zcol, const int* __restrict__ cpts,
+           const int* __restrict__ work, double* __restrict__ Zval,
+           unsigned long long* __restrict__ nsingular, Real* __restrict__ scratch, int pitch) {
+  __shared__ int zl[LS_TBIG];
+  __shared__ int stepof[LS_TBIG];
+  __shared__ int steprow[LS_TBIG];
+  __shared__ Real rhs[LS_TBIG];
+  __shared__ Real xs[LS_TBIG];
+  __shared__ Real red_v[LB_THREADS / 32];
+  __shared__ int red_w[LB_THREADS / 32];
+  __shared__ int s_piv, s_d, s_sing;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int r = work[blockIdx.x];
+  const int i = cpts[r];
+  const int base = Zrp[r];
+  const int len = Zrp[r + 1] - base;
+  const int T = len - 1;
+  Real* M = scratch + (size_t)blockIdx.x * pitch * pitch;
+  if (t == 0) {
+    s_d = T;
+    s_sing = 0;
+  }
+  __syncthreads();
+  for (int q = t; q < len; q += LB_THREADS)
+    if (Zcol[base + q] == i) s_d = q;
+  __syncthreads();
+  const int d = s_d;
+  for (int p = t; p < T; p += LB_THREADS) {
+    zl[p] = Zcol[base + p + (p >= d ? 1 : 0)];
+    rhs[p] = Real(0);
+    stepof[p] = -1;
+    for (int q = 0; q < T; ++q) M[(size_t)p * pitch + q] = Real(0);
+  }
+  __syncthreads();
+  for (int p = t; p < T; p += LB_THREADS) {
+    const int l = zl[p];
+    for (int e = Arp[l]; e < Arp[l + 1]; ++e) {
+      const int c = Acol[e];
+      if (c == i) {
+        rhs[p] = Real(-Aval[e]);
+      } else {
+        const int q = find_sorted(zl, T, c);
+        if (q >= 0) M[(size_t)p * pitch + q] = Real(Aval[e]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < T; ++k) {
+    Real v = Real(-1);
+    int who = T;
+    for (int p = t; p < T; p += LB_THREADS)
+      if (stepof[p] < 0) {
+        const Real a = M[(size_t)p * pitch + k];
+        const Real m = a < 0 ? -a : a;
+        if (m > v) {  // rows visited in increasing order: ties keep the lowest row
+          v = m;
+          who = p;
+        }
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const Real v2 = __shfl_xor_sync(0xffffffffu, v, o);
+      const int w2 = __shfl_xor_sync(0xffffffffu, who, o);
+      if (v2 > v || (v2 == v && w2 < who)) {
+        v = v2;
+        who = w2;
+      }
+    }
+    if (lane == 0) {
+      red_v[wid] = v;
+      red_w[wid] = who;
+    }
+    __syncthreads();
+    if (t == 0) {
+      Real bv = red_v[0];
+      int bw = red_w[0];
+      for (int w = 1; w < LB_THREADS / 32; ++w)
+        if (red_v[w] > bv || (red_v[w] == bv && red_w[w] < bw)) {
+          bv = red_v[w];
+          bw = red_w[w];
+        }
+      s_piv = bw;
+      steprow[k] = bw;
+      stepof[bw] = k;
+      if (!(bv > Real(0))) s_sing = 1;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    const Real* prow = M + (size_t)piv * pitch;
+    const Real pk = prow[k];
+    for (int p = t; p < T; p += LB_THREADS)
+      if (stepof[p] < 0 && pk != Real(0)) {
+        Real* row = M + (size_t)p * pitch;
+        const Real l = row[k] / pk;
+        for (int j = k + 1; j < T; ++j) row[j] -= l * prow[j];
+        rhs[p] -= l * rhs[piv];
+      }
+    __syncthreads();
+  }
+  for (int k = T - 1; k >= 0; --k) {
+    const int own = steprow[k];
+    if (t == 0) {
+      const Real dk = M[(size_t)own * pitch + k];
+      xs[k] = dk != Real(0) ? rhs[own] / dk : Real(0);
+    }
+    __syncthreads();
+    const Real xk = xs[k];
+    for (int p = t; p < T; p += LB_THREADS)
+      if (stepof[p] < k) rhs[p] -= M[(size_t)p * pitch + k] * xk;
+    __syncthreads();
+  }
+  const bool sing = s_sing != 0;
+  for (int p = t; p < T; p += LB_THREADS) Zval[base + p + (p >= d ? 1 : 0)] = sing ? 0.0 : (double)xs[p];
+  if (t == 0) {
+    Zval[base + d] = 1.0;
+    if (sing) atomicAdd(nsingular, 1ull);
+  }
+}
+
+// ------------------------------------------------------------------------------------
 // Bucketing and the projection.
 // ------------------------------------------------------------------------------------
 // work[0..2] = sum T^3, T^2, T; work[3] = A entries gathered (row lengths of the pattern's
@@ -342,10 +476,11 @@ __global__ void bucket_rows(const int* __restrict__ Zrp, int nc, int* __restrict
   const int T = r < nc ? Zrp[r + 1] - Zrp[r] - 1 : -1;
   if (T == 0) Zval[Zrp[r]] = 1.0;  // only the identity entry
   const int b = T > 0 ? ls_bucket(T) : -1;
-  if (b >= 5) atomicAdd(too_big, 1);
+  if (b >= LS_BUCKETS) atomicAdd(too_big, 1);
+  if (b == LS_BUCKETS - 1) atomicMax(too_big + 1, T);  // largest T of the big bucket
   unsigned long long t3 = 0, t2 = 0, t1 = 0, g = 0;
   // one atomic per bucket and warp: lanes of the same bucket share a block of positions
-  const int key = (b >= 0 && b < 5) ? b : -1;
+  const int key = (b >= 0 && b < LS_BUCKETS) ? b : -1;
   const unsigned grp = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(grp) - 1;
@@ -437,7 +572,8 @@ int coarse_points(const signed char* cf, int n, int** cpts_out, cudaStream_t s) 
 template <class Real>
 static void launch_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* cpts,
                           const int* lists, const int* counts_h, int nc, double* Zval,
-                          unsigned long long* nsing, cudaStream_t s) {
+                          unsigned long long* nsing, cudaStream_t s, Real* big_scratch = nullptr,
+                          int big_pitch = 0, int big_chunk = 0) {
   static bool attr = false;
   if (!attr) {
     CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -462,32 +598,68 @@ static void launch_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, cons
   if (counts_h[4])
     lsolve_cta<Real, 128><<<counts_h[4], 128, cta_smem<Real, 128>(), s>>>(
         Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts, lists + 4LL * nc, Zval, nsing); ::clair::count_launch();
+  if (counts_h[5]) {
+    CLAIR_REQUIRE(big_scratch && big_chunk > 0, CLAIR_ERR_CAPACITY,
+                  "%d local systems larger than 128 unknowns (this entry point solves T <= 128)",
+                  counts_h[5]);
+    for (int off = 0; off < counts_h[5]; off += big_chunk) {
+      const int cnt = std::min(big_chunk, counts_h[5] - off);
+      lsolve_big<Real><<<cnt, LB_THREADS, 0, s>>>(Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts,
+                                                 lists + 5LL * nc + off, Zval, nsing, big_scratch,
+                                                 big_pitch); ::clair::count_launch();
+    }
+  }
   CLAIR_LAUNCHED();
+}
+
+// Scratch for the large-system bucket: `chunk` tiles of pitch x pitch values, at most
+// 256 MiB, pitch = the bucket's largest T.
+template <class Real>
+static Real* big_tiles(const int* counts_h, int& pitch, int& chunk, cudaStream_t s) {
+  pitch = 0;
+  chunk = 0;
+  if (!counts_h[5]) return nullptr;
+  pitch = counts_h[LS_BUCKETS + 1];
+  const size_t tile = (size_t)pitch * pitch * sizeof(Real);
+  chunk = (int)std::max<size_t>(1, std::min<size_t>(counts_h[5], (256ull << 20) / tile));
+  return dalloc<Real>((size_t)chunk * pitch * pitch, s);
 }
 
 // Local lAIR solves for all coarse rows of the pattern Z (nc x n), values into Zval.
 void local_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* cpts, int nc,
                   int precision, double* Zval, LocalStats& st, cudaStream_t s) {
   int* lists = dalloc<int>((long long)LS_BUCKETS * std::max(nc, 1), s);
-  int* counts = dalloc<int>(LS_BUCKETS + 1, s);
+  int* counts = dalloc<int>(LS_BUCKETS + 2, s);
   unsigned long long* nsing = dalloc<unsigned long long>(5, s);  // [0] singular, [1..4] work
-  CLAIR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * (LS_BUCKETS + 1), s));
+  CLAIR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * (LS_BUCKETS + 2), s));
   CLAIR_CUDA(cudaMemsetAsync(nsing, 0, 5 * sizeof(unsigned long long), s));
   if (nc) bucket_rows<<<ceil_div(nc, 256), 256, 0, s>>>(Zrp, nc, lists, counts, Zval, Zcol, cpts,
                                                         Ahat.rowptr, counts + LS_BUCKETS,
                                                         nsing + 1); ::clair::count_launch();
   CLAIR_LAUNCHED();
-  int counts_h[LS_BUCKETS + 1];
+  int counts_h[LS_BUCKETS + 2];
   CLAIR_CUDA(cudaMemcpyAsync(counts_h, counts, sizeof(counts_h), cudaMemcpyDeviceToHost, s));
   CLAIR_CUDA(cudaStreamSynchronize(s));
   CLAIR_REQUIRE(counts_h[LS_BUCKETS] == 0, CLAIR_ERR_CAPACITY,
-                "%d local systems larger than 128 unknowns", counts_h[LS_BUCKETS]);
+                "%d local systems larger than %d unknowns", counts_h[LS_BUCKETS], LS_TBIG);
   {
     ClockScope clk(PH_LSOLVE, s);
     if (precision == CLAIR_MIXED)
-      launch_solves<float>(Ahat, Zrp, Zcol, cpts, lists, counts_h, nc, Zval, nsing, s);
+    {
+      int pitch, chunk;
+      float* tiles = big_tiles<float>(counts_h, pitch, chunk, s);
+      launch_solves<float>(Ahat, Zrp, Zcol, cpts, lists, counts_h, nc, Zval, nsing, s, tiles, pitch,
+                           chunk);
+      dfree(tiles, s);
+    }
     else
-      launch_solves<double>(Ahat, Zrp, Zcol, cpts, lists, counts_h, nc, Zval, nsing, s);
+    {
+      int pitch, chunk;
+      double* tiles = big_tiles<double>(counts_h, pitch, chunk, s);
+      launch_solves<double>(Ahat, Zrp, Zcol, cpts, lists, counts_h, nc, Zval, nsing, s, tiles, pitch,
+                            chunk);
+      dfree(tiles, s);
+    }
   }
   unsigned long long h[5] = {0, 0, 0, 0, 0};
   CLAIR_CUDA(cudaMemcpyAsync(h, nsing, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -627,7 +799,7 @@ static void carve(ScratchCursor& c, int n, int nc, int nnzZ, NoallocBuffers& b) 
   b.pre = c.take<int>((size_t)n + 1);
   b.cpts = c.take<int>(nc);
   b.lists = c.take<int>((size_t)LS_BUCKETS * (nc > 0 ? nc : 1));
-  b.counts = c.take<int>(LS_BUCKETS + 1);
+  b.counts = c.take<int>(LS_BUCKETS + 2);
   b.work = c.take<unsigned long long>(5);
   b.zt_rowptr = c.take<int>((size_t)n + 1);
   b.zt_col = c.take<int>(nnzZ);
@@ -659,17 +831,17 @@ static void local_weights_noalloc(int n, const Csr& Ahat, const signed char* cf,
   coarse_of<<<ceil_div(n, 256), 256, 0, s>>>(cf, b.pre, n, b.cpts); ::clair::count_launch();
   CLAIR_LAUNCHED();
   // bucketed local solves (counters start at zero on every call)
-  CLAIR_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(int) * (LS_BUCKETS + 1), s));
+  CLAIR_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(int) * (LS_BUCKETS + 2), s));
   CLAIR_CUDA(cudaMemsetAsync(b.work, 0, 5 * sizeof(unsigned long long), s));
   if (nc) bucket_rows<<<ceil_div(nc, 256), 256, 0, s>>>(Z.rowptr, nc, b.lists, b.counts, Z.val, Z.col,
                                                         b.cpts, Ahat.rowptr, b.counts + LS_BUCKETS,
                                                         b.work + 1); ::clair::count_launch();
   CLAIR_LAUNCHED();
-  int counts_h[LS_BUCKETS + 1];
+  int counts_h[LS_BUCKETS + 2];
   CLAIR_CUDA(cudaMemcpyAsync(counts_h, b.counts, sizeof(counts_h), cudaMemcpyDeviceToHost, s));
   CLAIR_CUDA(cudaStreamSynchronize(s));
   CLAIR_REQUIRE(counts_h[LS_BUCKETS] == 0, CLAIR_ERR_CAPACITY,
-                "%d local systems larger than 128 unknowns", counts_h[LS_BUCKETS]);
+                "%d local systems larger than %d unknowns", counts_h[LS_BUCKETS], LS_TBIG);
   if (precision == CLAIR_MIXED)
     launch_solves<float>(Ahat, Z.rowptr, Z.col, b.cpts, b.lists, counts_h, nc, Z.val, b.work, s);
   else

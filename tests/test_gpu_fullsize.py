@@ -1,0 +1,173 @@
+"""GPU parity at the full 1024^2 size of the bench workload, in the bench's configuration.
+
+* Bench workload (eps 1e-2, m 2), FP64 and MIXED setups: the level-0 splitting is
+  compared in full (bit-exact), the relaxation weight and both smoothed mode vectors in
+  full, and the R and P weights on a seeded sample of coarse points.  The oracle computes
+  the sampled weights exactly by running Algorithm 1 on the columns that touch the
+  sample's F rows (every step of the algorithm is local to a column block or an F row).
+* The other eps and m variants of the workload: properties that hold at any size (the
+  mode constraint on every F column / row, the splitting invariant, convergence of both
+  precisions to the 1e-8 true residual with iteration counts within one).
+Tolerances as in test_gpu_parity.py.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 2e-5
+OMEGA_TOL = 1e-8
+NSAMPLE = 160
+
+
+@pytest.fixture(scope="module")
+def cl():
+    import torch
+    from paper_2307_00229_gb300 import clair
+    clair.load()
+    torch.cuda.init()
+    return clair
+
+
+def dev(a, dtype):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def setup_gpu(cl, prob, precision, degree=2):
+    import torch
+    p = cl.clair_params_default()
+    p.precision = precision
+    p.degree = degree
+    A = prob.A
+    h = cl.clair_setup(dev(A.rowptr, torch.int32), dev(A.col, torch.int32),
+                       dev(A.val, torch.float64), dev(prob.B, torch.float64), p)
+    return h
+
+
+def level0(cl, h):
+    import torch
+    torch.cuda.synchronize()
+    v = cl.clair_level_view(h, 0)
+    out = {k: (x.cpu().numpy() if hasattr(x, "cpu") else x) for k, x in v.items()}
+    n, nc = out["n"], out["nc"]
+    out["R"] = sp.csr_matrix((out["R_val"], out["R_col"], out["R_rowptr"]), shape=(nc, n))
+    out["P"] = sp.csr_matrix((out["P_val"], out["P_col"], out["P_rowptr"]), shape=(n, nc))
+    return out
+
+
+@pytest.fixture(scope="module")
+def bench_oracle():
+    """Level-0 oracle quantities of the bench workload (1024^2, eps 1e-2, m 2)."""
+    prob = workloads.config2()
+    A = O.csr_of(prob.A)
+    At = A.T.tocsr()
+    At.sort_indices()
+    p = O.Params()
+    cf = O.split_fc(A, p.theta_coarsen)
+    omega = 1.0 / O.arnoldi_rho(A, p.arnoldi_iters, p.seed)
+    B = prob.B.reshape(-1, 1)
+    B_P = O.smooth_modes(A, B, cf, omega, p.b_smooth_iters)[:, 0]
+    B_R = O.smooth_modes(At, B, cf, omega, p.b_smooth_iters)[:, 0]
+    pats = {}
+    for side, Ahat in (("R", At), ("P", A)):
+        S = O.strength(Ahat, p.theta_interp)
+        pats[side] = O.clair_pattern(S, O.base_pattern(S, cf, "FC"), cf, p.degree)
+    rng = np.random.default_rng(2024)
+    nc = int(cf.sum())
+    sample = np.sort(rng.choice(nc, NSAMPLE, replace=False))
+    return {"prob": prob, "A": A, "At": At, "cf": cf, "omega": omega, "B_P": B_P, "B_R": B_R,
+            "pats": pats, "sample": sample}
+
+
+def sampled_columns(Ahat, cf, B, Wpat, sample):
+    """Exact Algorithm 1 weights of the sampled columns: {column: (rows, values)}."""
+    cpts = np.flatnonzero(cf)
+    Wc = Wpat.tocsc()
+    Wr = Wpat.tocsr()
+    rows = np.unique(np.concatenate([Wc.indices[Wc.indptr[i]:Wc.indptr[i + 1]] for i in sample]))
+    cols = np.unique(np.concatenate([Wr.indices[Wr.indptr[j]:Wr.indptr[j + 1]] for j in rows]))
+    W = O.clair_algorithm1(Ahat, cf, B, Wc[:, cols], O.Params(), cpts=cpts[cols]).tocsc()
+    pos = {c: k for k, c in enumerate(cols)}
+    out = {}
+    for i in sample:
+        k = pos[i]
+        out[i] = (W.indices[W.indptr[k]:W.indptr[k + 1]], W.data[W.indptr[k]:W.indptr[k + 1]])
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bench_workload_level0_matches_oracle(cl, bench_oracle, precision):
+    o = bench_oracle
+    h = setup_gpu(cl, o["prob"], precision)
+    try:
+        g = level0(cl, h)
+    finally:
+        cl.clair_free(h)
+    assert np.array_equal(g["cf"], o["cf"]), "splitting differs at full size"
+    dom = abs(g["omega"] - o["omega"]) / o["omega"]
+    assert dom <= OMEGA_TOL, dom
+    tol = FP64_TOL + 100 * dom
+    for key in ("B_P", "B_R"):
+        assert np.abs(g[key] - o[key]).max() <= tol * np.abs(o[key]).max(), key
+    wtol = tol if precision == 0 else FP32_TOL
+    cpts = np.flatnonzero(o["cf"])
+    Pt = g["P"].T.tocsr()
+    for side, Ahat, Bv, Z in (("R", o["At"], o["B_R"], g["R"]), ("P", o["A"], o["B_P"], Pt)):
+        ref = sampled_columns(Ahat, o["cf"], Bv, o["pats"][side], o["sample"])
+        worst = 0.0
+        for i, (rows, vals) in ref.items():
+            s, e = Z.indptr[i], Z.indptr[i + 1]
+            cols, gv = Z.indices[s:e], Z.data[s:e]
+            keep = cols != cpts[i]
+            assert np.array_equal(cols[keep], rows), (side, i)
+            assert gv[~keep].tolist() == [1.0]
+            if vals.size:
+                worst = max(worst, np.abs(gv[keep] - vals).max() / np.abs(vals).max())
+        assert worst <= wtol, (side, worst)
+
+
+VARIANTS = [(0.0, 2), (1e-4, 2), (1.0, 2), (1e-2, 1), (0.0, 1)]
+
+
+@pytest.mark.parametrize("eps,degree", VARIANTS)
+def test_full_size_properties(cl, eps, degree):
+    import torch
+    prob = workloads.config2(eps=eps, degree=degree)
+    A = O.csr_of(prob.A)
+    its = {}
+    for precision in (0, 1):
+        h = setup_gpu(cl, prob, precision, degree)
+        try:
+            g = level0(cl, h)
+            f = dev(prob.f, torch.float64)
+            u = torch.zeros_like(f)
+            st, it, rel = cl.clair_solve(h, f, u)
+            uh = u.cpu().numpy()
+        finally:
+            cl.clair_free(h)
+        assert np.linalg.norm(prob.f - A @ uh) <= 1e-8 * np.linalg.norm(prob.f)
+        its[precision] = it
+        cf = g["cf"].astype(bool)
+        cpts = np.flatnonzero(cf)
+        # the mode constraint: sum_i R_ij B_c(i) = B(j), sum_i P_ji B_c(i) = B(j) on F
+        for key, M in (("B_R", g["R"].T.tocsr()), ("B_P", g["P"])):
+            Bv = g[key]
+            lhs = M @ Bv[cpts]
+            Fj = ~cf & (np.diff(M.indptr) > 0)
+            nz = np.asarray(abs(M) @ np.abs(Bv[cpts])).ravel() > 0
+            sel = Fj & nz
+            np.testing.assert_allclose(lhs[sel], Bv[sel], rtol=1e-12, atol=1e-300)
+        # splitting invariant: every F-point with a strong dependence depends on a C-point
+        S = O.strength(A, 0.25)
+        has = np.diff(S.indptr) > 0
+        dep_c = (S @ cf.astype(np.float64)) > 0
+        assert not np.any(~cf & has & ~dep_c)
+    assert abs(its[0] - its[1]) <= 1, its

@@ -496,3 +496,27 @@ def test_workload_generators():
     # splitmix64 reference values (sequential generator seeded with 0)
     z = workloads.splitmix64(0, 3)
     assert [hex(int(v)) for v in z] == ["0xe220a8397b1dcdaf", "0x6e789e6aa1b965f4", "0x6c45d188009454f"]
+
+
+def test_algorithm1_on_column_subset_matches_full_run():
+    """Running Algorithm 1 on the columns that touch a sample's F rows reproduces the full
+    run on the sampled columns (used by the full-size GPU parity test)."""
+    A = small_problem(10, eps=1e-2)
+    At = A.T.tocsr()
+    cf = O.split_fc(A, 0.25)
+    B = 0.5 + workloads.uniform01(13, A.shape[0])
+    S = O.strength(At, 0.05)
+    Wpat = O.clair_pattern(S, O.base_pattern(S, cf, "FC"), cf, 2).tocsc()
+    full = O.clair_algorithm1(At, cf, B, Wpat, O.Params()).tocsc()
+    cpts = np.flatnonzero(cf)
+    Wr = Wpat.tocsr()
+    sample = np.array([1, 5, 9, 17])
+    rows = np.unique(np.concatenate([Wpat.indices[Wpat.indptr[i]:Wpat.indptr[i + 1]] for i in sample]))
+    cols = np.unique(np.concatenate([Wr.indices[Wr.indptr[j]:Wr.indptr[j + 1]] for j in rows]))
+    sub = O.clair_algorithm1(At, cf, B, Wpat[:, cols], O.Params(), cpts=cpts[cols]).tocsc()
+    for i in sample:
+        k = int(np.searchsorted(cols, i))
+        np.testing.assert_array_equal(sub.indices[sub.indptr[k]:sub.indptr[k + 1]],
+                                      full.indices[full.indptr[i]:full.indptr[i + 1]])
+        np.testing.assert_allclose(sub.data[sub.indptr[k]:sub.indptr[k + 1]],
+                                   full.data[full.indptr[i]:full.indptr[i + 1]], rtol=1e-13, atol=1e-15)
