@@ -712,7 +712,8 @@ __device__ void spgemm_row(int r, const int* __restrict__ Arp, const int* __rest
   if (!NUMERIC) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-    if (lane == 0) count[r] = __any_sync(0xffffffffu, full) ? -1 : mine;
+    const bool overflow = __any_sync(0xffffffffu, full);  // all lanes vote
+    if (lane == 0) count[r] = overflow ? -1 : mine;
     return;
   }
   // compact the occupied slots to the front (each 32-slot chunk is read before any of
@@ -831,7 +832,8 @@ __device__ void spgemm_row_flat(int r, const int* __restrict__ Arp, const int* _
   if (!NUMERIC) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-    if (lane == 0) count[r] = __any_sync(0xffffffffu, full) ? -1 : mine;
+    const bool overflow = __any_sync(0xffffffffu, full);  // all lanes vote
+    if (lane == 0) count[r] = overflow ? -1 : mine;
     return;
   }
   __syncwarp();

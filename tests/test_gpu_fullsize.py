@@ -7,7 +7,8 @@
   sample's F rows (every step of the algorithm is local to a column block or an F row).
 * The other eps and m variants of the workload: properties that hold at any size (the
   mode constraint on every F column / row, the splitting invariant, convergence of both
-  precisions to the 1e-8 true residual with iteration counts within one).
+  precisions to the 1e-8 true residual with iteration counts within one), and every
+  coarse operator equal to the Galerkin product of its level's R, A and P.
 Tolerances as in test_gpu_parity.py.
 """
 import math
@@ -52,15 +53,39 @@ def setup_gpu(cl, prob, precision, degree=2):
     return h
 
 
-def level0(cl, h):
+def level0(cl, h, k=0):
     import torch
     torch.cuda.synchronize()
-    v = cl.clair_level_view(h, 0)
+    v = cl.clair_level_view(h, k)
     out = {k: (x.cpu().numpy() if hasattr(x, "cpu") else x) for k, x in v.items()}
     n, nc = out["n"], out["nc"]
-    out["R"] = sp.csr_matrix((out["R_val"], out["R_col"], out["R_rowptr"]), shape=(nc, n))
-    out["P"] = sp.csr_matrix((out["P_val"], out["P_col"], out["P_rowptr"]), shape=(n, nc))
+    out["A"] = sp.csr_matrix((out["A_val"], out["A_col"], out["A_rowptr"]), shape=(n, n))
+    if nc:
+        out["R"] = sp.csr_matrix((out["R_val"], out["R_col"], out["R_rowptr"]), shape=(nc, n))
+        out["P"] = sp.csr_matrix((out["P_val"], out["P_col"], out["P_rowptr"]), shape=(n, nc))
     return out
+
+
+def check_galerkin(cl, h):
+    """Every coarse operator is the Galerkin product of its level (Section 2): (R A) P
+    entry by entry to rounding, relative to the row's largest entry.  An entry whose
+    products cancel may sum to an exact zero (dropped) in one summation order and to a
+    rounding-size value in another, so the comparison runs over the union of both
+    sparsity patterns and the patterns may differ only in such entries.  At full size the
+    coarse rows are long enough to reach every tier of the sparse product."""
+    nlev = cl.clair_stats(h).levels
+    prev = level0(cl, h, 0)
+    for k in range(1, nlev):
+        cur = level0(cl, h, k)
+        ref = ((prev["R"] @ prev["A"]) @ prev["P"]).tocsr()
+        ref.eliminate_zeros()
+        Ac = cur["A"]
+        assert Ac.shape == ref.shape, k
+        assert abs(Ac.nnz - ref.nnz) <= 1e-4 * ref.nnz, (k, Ac.nnz, ref.nnz)
+        D = (Ac - ref).tocoo()
+        scale = np.abs(ref).max(axis=1).toarray().ravel()
+        assert np.all(np.abs(D.data) <= 1e-12 * scale[D.row]), k
+        prev = cur
 
 
 @pytest.fixture(scope="module")
@@ -147,6 +172,7 @@ def test_full_size_properties(cl, eps, degree):
         h = setup_gpu(cl, prob, precision, degree)
         try:
             g = level0(cl, h)
+            check_galerkin(cl, h)
             f = dev(prob.f, torch.float64)
             u = torch.zeros_like(f)
             st, it, rel = cl.clair_solve(h, f, u)
