@@ -11,3 +11,4 @@ the passage it follows.  The only module both sides use is ``workloads`` (seeded
 generators, which hold none of the method's arithmetic).
 """
 from .clair_oracle import *  # noqa: F401,F403
+from . import adjoint  # noqa: F401
