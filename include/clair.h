@@ -202,6 +202,54 @@ clair_status clair_local_weights_noalloc(int n, const int* Ahat_rowptr, const in
                                          int precision, double* Z_val, void* stream,
                                          int64_t* singular_out, int64_t* empty_out);
 
+/* ---- Adjoint path: gradients of a loss of the solutions -----------------------------
+ * The paper solves A u = f (Section 1).  For a loss L(u_1..u_k) of several solutions, the
+ * implicit-function theorem gives A^T lam_r = dL/du_r and dL/da_ij = -sum_r lam_r[i] u_r[j]
+ * on the stored entries of A.  The adjoint operator A^T is nonsymmetric like A and gets
+ * its own CLAIR hierarchy (R from A, P from A^T: Section 3.1.3 run on A^T). */
+
+/* Hierarchy for A^T: transposes the fine operator of `fwd` on the device and runs
+ * clair_setup on it with fwd's parameters and fwd's (unsmoothed) mode vector.
+ *   fwd : a hierarchy from clair_setup (not modified)
+ *   adj : receives the new hierarchy (owned by the caller, release with clair_free);
+ *         *adj = NULL on failure
+ * Same errors as clair_setup; synchronises `stream`. */
+clair_status clair_setup_adjoint(clair_h fwd, void* stream, clair_h* adj);
+
+/* Operator gradient sampled on the sparsity of A:
+ *   dA[e] = -sum_{r=0}^{nrhs-1} lambda[r*n + row(e)] * u[r*n + col(e)]
+ * for every stored entry e of A in its CSR order (sum in increasing r, float64).
+ *   n, nnz, rowptr, col : device CSR pattern of A (validated)
+ *   lambda, u           : device float64 [nrhs * n], RHS-major (vector r contiguous):
+ *                         the adjoint and state solutions
+ *   dA                  : device float64 [nnz], written
+ * CLAIR_ERR_ARG on null pointers, bad sizes or an invalid pattern. Asynchronous after
+ * validation (which synchronises `stream` once). */
+clair_status clair_sddmm_grad(int n, int nnz, const int* rowptr, const int* col, int nrhs,
+                              const double* lambda, const double* u, double* dA, void* stream);
+
+/* Chain rule from the entries of the 5-point first-order upwind finite-difference operator
+ * of the Section 4.2 advection-diffusion problem (Eq. 4.1) to its per-node fields. The
+ * grid is nside x nside interior nodes (x fastest) with spacing h and Dirichlet values
+ * eliminated. The interior face between nodes k and Q carries
+ * e_f = 2 e_k e_Q / (e_k + e_Q) (a boundary face carries e_k). Row k holds
+ * sum_f e_f/h^2 + (|vx_k| + |vy_k|)/h on the diagonal, -e_f/h^2 on each neighbour, and
+ * -max(vx_k,0)/h west, -max(-vx_k,0)/h east, -max(vy_k,0)/h south, -max(-vy_k,0)/h
+ * north.
+ *   eps, vx, vy          : device float64 [nside^2], the fields A was assembled from
+ *   rowptr, col, nnz, dA : device CSR pattern of A and dL/da on it (e.g. from
+ *                          clair_sddmm_grad)
+ *   deps, dvx, dvy       : device float64 [nside^2], written: dL/d eps_k, dL/d vx_k,
+ *                          dL/d vy_k. The derivative of |v| is taken as sign(v), 0 at
+ *                          v = 0, where the upwind operator is not differentiable. Entries
+ *                          not stored in A contribute nothing.
+ * CLAIR_ERR_ARG on null pointers, bad sizes, an invalid pattern or a column outside the
+ * 5-point stencil. Synchronises `stream`. */
+clair_status clair_advdiff2d_param_grad(int nside, double h, const double* eps, const double* vx,
+                                        const double* vy, const int* rowptr, const int* col,
+                                        int nnz, const double* dA, double* deps, double* dvx,
+                                        double* dvy, void* stream);
+
 /* One-line description of the last error on the calling thread ("" if none). */
 const char* clair_last_error(void);
 

@@ -104,6 +104,10 @@ _SIGNATURES = {
     "clair_local_weights": (_I, [_I, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _PI64, _PI64]),
     "clair_local_weights_noalloc": (_I, [_I, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _PI64,
                                          _PI64]),
+    "clair_setup_adjoint": (_I, [_P, _P, ctypes.POINTER(_P)]),
+    "clair_sddmm_grad": (_I, [_I, _I, _P, _P, _I, _P, _P, _P, _P]),
+    "clair_advdiff2d_param_grad": (_I, [_I, ctypes.c_double, _P, _P, _P, _P, _P, _I, _P, _P, _P,
+                                        _P, _P]),
     "clair_last_error": (ctypes.c_char_p, []),
     "clair_kernel_launches": (ctypes.c_int64, []),
 }
@@ -266,3 +270,85 @@ def clair_local_weights_noalloc(Ahat_rowptr, Ahat_col, Ahat_val, cf, nc: int, Z_
     if st != CLAIR_OK and (st != CLAIR_ERR_SINGULAR_BLOCK or raise_singular):
         _check(st)
     return st, sing.value, empty.value
+
+
+# ---- adjoint path -------------------------------------------------------------------------
+
+def clair_setup_adjoint(h, stream=None) -> ctypes.c_void_p:
+    """Hierarchy for A^T of the hierarchy ``h`` (same parameters and mode vector)."""
+    adj = ctypes.c_void_p()
+    _check(load().clair_setup_adjoint(h, _stream(stream), ctypes.byref(adj)))
+    return adj
+
+
+def clair_sddmm_grad(rowptr, col, lam, u, dA, stream=None):
+    """``dA[e] = -sum_r lam[r, row(e)] u[r, col(e)]`` on A's pattern; lam, u: (nrhs, n)."""
+    n = rowptr.numel() - 1
+    if lam.shape != u.shape or lam.dim() != 2 or lam.shape[1] != n or dA.numel() != col.numel():
+        raise ValueError("clair_sddmm_grad: lam and u must be (nrhs, n) and dA must be (nnz,)")
+    _check(load().clair_sddmm_grad(n, col.numel(), _dptr(rowptr, torch.int32), _dptr(col, torch.int32),
+                                   lam.shape[0], _dptr(lam, torch.float64), _dptr(u, torch.float64),
+                                   _dptr(dA, torch.float64), _stream(stream)))
+
+
+def clair_advdiff2d_param_grad(nside: int, h: float, eps, vx, vy, rowptr, col, dA, stream=None):
+    """Chain rule of the 5-point upwind operator: returns ``(deps, dvx, dvy)`` per node."""
+    deps, dvx, dvy = (torch.empty(nside * nside, dtype=torch.float64, device="cuda") for _ in range(3))
+    _check(load().clair_advdiff2d_param_grad(
+        nside, float(h), _dptr(eps, torch.float64), _dptr(vx, torch.float64), _dptr(vy, torch.float64),
+        _dptr(rowptr, torch.int32), _dptr(col, torch.int32), col.numel(), _dptr(dA, torch.float64),
+        _dptr(deps, torch.float64), _dptr(dvx, torch.float64), _dptr(dvy, torch.float64),
+        _stream(stream)))
+    return deps, dvx, dvy
+
+
+class Hierarchy:
+    """Owns a library hierarchy handle and frees it with the object."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.clair_free(self.handle)
+            self.handle = None
+
+
+class ClairSolve(torch.autograd.Function):
+    """``U[r] = A(val)^{-1} F[r]`` for every row of F with CLAIR-preconditioned FGMRES,
+    differentiable in the values of A and in F.
+
+    Backward builds the hierarchy of A^T (clair_setup_adjoint), solves
+    ``A^T Lam[r] = dL/dU[r]`` and returns ``dL/dval = -sum_r Lam[r, row] U[r, col]``
+    (clair_sddmm_grad) and ``dL/dF = Lam``.  Every step runs in the CUDA library; this
+    class only moves pointers.
+
+    Arguments: ``val`` (nnz,) float64; ``F`` (nrhs, n) float64; ``rowptr``/``col`` int32
+    CSR pattern; ``B`` (n,) float64 mode vector; ``params`` a ``clair_params`` or None.
+    """
+
+    @staticmethod
+    def forward(ctx, val, F, rowptr, col, B, params):
+        F = F.detach().contiguous()
+        fwd = Hierarchy(clair_setup(rowptr, col, val.detach().contiguous(), B, params))
+        U = torch.zeros_like(F)
+        for r in range(F.shape[0]):
+            clair_solve(fwd.handle, F[r], U[r])
+        ctx.fwd = fwd
+        ctx.pattern = (rowptr, col)
+        ctx.save_for_backward(U)
+        return U
+
+    @staticmethod
+    def backward(ctx, gU):
+        (U,) = ctx.saved_tensors
+        rowptr, col = ctx.pattern
+        adj = Hierarchy(clair_setup_adjoint(ctx.fwd.handle))
+        gU = gU.detach().contiguous()
+        Lam = torch.zeros_like(gU)
+        for r in range(gU.shape[0]):
+            clair_solve(adj.handle, gU[r], Lam[r])
+        dval = torch.empty(col.numel(), dtype=torch.float64, device=U.device)
+        clair_sddmm_grad(rowptr, col, Lam, U, dval)
+        del adj
+        return dval, Lam, None, None, None, None

@@ -16,6 +16,7 @@ namespace clair {
 // per host thread.
 // ------------------------------------------------------------------------------------
 void set_error(const char* fmt, ...);
+void clear_error();
 
 struct Error {
   clair_status st;
@@ -78,6 +79,22 @@ struct Csr {
 };
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Body of every C-ABI entry point: host exceptions become status codes and the message
+// stays readable through clair_last_error().
+#define CLAIR_API_BEGIN \
+  ::clair::clear_error(); \
+  try {
+#define CLAIR_API_END                                    \
+  }                                                      \
+  catch (const ::clair::Error& e) {                      \
+    return e.st;                                         \
+  }                                                      \
+  catch (...) {                                          \
+    ::clair::set_error("unexpected host exception");     \
+    return CLAIR_ERR_CUDA;                               \
+  }                                                      \
+  return CLAIR_OK;
 
 // Number of SMs of the current device (cached per process).
 int sm_count();

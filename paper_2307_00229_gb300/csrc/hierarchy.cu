@@ -84,6 +84,7 @@ struct clair_hierarchy {
   long long cycle_kernels = 0;              // kernels in that graph
   double* vin = nullptr;                    // its fixed input and output vectors
   double* zout = nullptr;
+  double* B0 = nullptr;                     // the caller's mode vector, unsmoothed
 };
 
 namespace clair {
@@ -150,6 +151,7 @@ static void release_all(clair_hierarchy* h) {
   h->cycle_exec = nullptr;
   dfree(h->vin, s);
   dfree(h->zout, s);
+  dfree(h->B0, s);
   k.host = nullptr;
 }
 
@@ -618,20 +620,6 @@ static clair_status fgmres(clair_hierarchy* h, const double* f, double* u, int* 
 // =======================================================================================
 using namespace clair;
 
-#define CLAIR_API_BEGIN \
-  clear_error();        \
-  try {
-#define CLAIR_API_END                                    \
-  }                                                      \
-  catch (const Error& e) {                               \
-    return e.st;                                         \
-  }                                                      \
-  catch (...) {                                          \
-    set_error("unexpected host exception");              \
-    return CLAIR_ERR_CUDA;                               \
-  }                                                      \
-  return CLAIR_OK;
-
 extern "C" {
 
 clair_status clair_params_default(clair_params* p) {
@@ -704,6 +692,8 @@ clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, cons
     validate_csr(rowptr, col, n, n, nnz, "A", s);
     CLAIR_REQUIRE(all_finite(val, nnz, s), CLAIR_ERR_NONFINITE, "A has nonfinite values");
     CLAIR_REQUIRE(all_finite(B, n, s), CLAIR_ERR_NONFINITE, "B has nonfinite values");
+    h->B0 = dalloc<double>(n, s);
+    CLAIR_CUDA(cudaMemcpyAsync(h->B0, B, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     PhaseClock clock;
     set_active_clock(&clock);
     setup_levels(h, B);
@@ -728,6 +718,27 @@ clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, cons
     throw;
   }
   *out = h;
+  CLAIR_API_END
+}
+
+clair_status clair_setup_adjoint(clair_h fwd, void* stream, clair_h* adj) {
+  if (adj) *adj = nullptr;
+  CLAIR_API_BEGIN
+  CLAIR_REQUIRE(fwd && adj, CLAIR_ERR_ARG, "clair_setup_adjoint: null pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Csr& A = fwd->lv[0].A;
+  Csr At;
+  csr_transpose(A, At, nullptr, s);
+  clair_status st;
+  try {
+    st = clair_setup(A.rows, A.nnz, At.rowptr, At.col, At.val, fwd->B0, &fwd->p, stream, adj);
+  } catch (...) {
+    At.release(s);
+    throw;
+  }
+  At.release(s);
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  return st;
   CLAIR_API_END
 }
 
