@@ -50,7 +50,11 @@ typedef struct {
   double theta_coarsen;   /* strength threshold for the C/F splitting */
   double theta_interp;    /* strength threshold for the transfer patterns */
   int degree;             /* sparsity pattern degree m of Algorithm 1 (1 or 2) */
-  int coarsen;            /* CLAIR_COARSEN_FC or CLAIR_COARSEN_AGG */
+  int coarsen;            /* CLAIR_COARSEN_FC (C/F splitting, the Ruge-Stueben first pass
+                             read as a parallel independent set) or CLAIR_COARSEN_AGG
+                             (aggregation: roots of a distance-two independent set are the
+                             C-points, Algorithm 1's base pattern T is the aggregation
+                             operator; Section 3.1.3 and its footnote) */
   int b_smooth_iters;     /* CFF sweeps applied to the mode vector on each level */
   int arnoldi_iters;      /* Arnoldi steps for rho(D^-1 A) */
   int post_weighted;      /* 1: post-smoothing uses the weight too; 0: weight 1 */

@@ -16,8 +16,13 @@ void strength(const Csr& M, const double* thr, double theta, int mode, unsigned 
               cudaStream_t s);
 void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsigned char* sAt,
               signed char* cf, cudaStream_t s);
+void aggregate(const Csr& A, const Csr& At, const unsigned char* sA, const unsigned char* sAt,
+               signed char* cf, int* agg, cudaStream_t s);
+void aggregate_members(const int* agg, int n, int nc, int** rp_out, int** members_out,
+                       cudaStream_t s);
 void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf, const int* cpts,
-                   int nc, int n, int degree, Csr& Z, cudaStream_t s);
+                   int nc, int n, int degree, const int* Mrp, const int* Mcol, Csr& Z,
+                   cudaStream_t s);
 template <class T>
 void jacobi(const Csr& A, const T* vals, const T* dinv, const signed char* cf, int which, T omega,
             const T* b, const T* xin, T* xout, cudaStream_t s, const T* omega_dev = nullptr);
@@ -199,6 +204,7 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
     if (n <= p.coarse_max || k + 1 >= p.max_levels) break;
 
     Csr At;
+    int* agg = nullptr;                           // aggregate of each point (Agg coarsening)
     double* rmaxA = dalloc<double>(n, s);
     double* rmaxAt = dalloc<double>(n, s);
     unsigned char* sA = dalloc<unsigned char>(L.A.nnz, s);
@@ -212,12 +218,16 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
       strength(L.A, rmaxA, p.theta_coarsen, 0, sA, s);
       strength(At, rmaxA, p.theta_coarsen, 1, sAt, s);
       L.cf = dalloc<signed char>(n, s);
-      CLAIR_REQUIRE(p.coarsen == CLAIR_COARSEN_FC, CLAIR_ERR_UNSUPPORTED,
-                    "aggregation coarsening is not built yet");
-      split_fc(L.A, At, sA, sAt, L.cf, s);
+      if (p.coarsen == CLAIR_COARSEN_AGG) {
+        agg = dalloc<int>(n, s);
+        aggregate(L.A, At, sA, sAt, L.cf, agg, s);
+      } else {
+        split_fc(L.A, At, sA, sAt, L.cf, s);
+      }
       L.nc = coarse_points(L.cf, n, &L.cpts, s);
     }
     if (L.nc == 0 || L.nc == n) {
+      dfree(agg, s);
       dfree(L.cf, s);
       dfree(L.cpts, s);
       L.nc = 0;
@@ -255,8 +265,14 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
       ClockScope clk(PH_PATTERN, s);
       strength(L.A, rmaxAt, p.theta_interp, 1, sR, s);
       strength(At, rmaxA, p.theta_interp, 1, sP, s);
-      build_pattern(L.A, sR, L.cf, L.cpts, L.nc, n, p.degree, L.R, s);
-      build_pattern(At, sP, L.cf, L.cpts, L.nc, n, p.degree, Pt, s);
+      int* Mrp = nullptr;
+      int* Mcol = nullptr;
+      if (agg) aggregate_members(agg, n, L.nc, &Mrp, &Mcol, s);
+      build_pattern(L.A, sR, L.cf, L.cpts, L.nc, n, p.degree, Mrp, Mcol, L.R, s);
+      build_pattern(At, sP, L.cf, L.cpts, L.nc, n, p.degree, Mrp, Mcol, Pt, s);
+      dfree(Mrp, s);
+      dfree(Mcol, s);
+      dfree(agg, s);
     }
     transfer_solve(At, L.cpts, L.R, p.precision, h->st, s);
     transfer_solve(L.A, L.cpts, Pt, p.precision, h->st, s);
@@ -667,6 +683,8 @@ clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, cons
   CLAIR_REQUIRE(p.arnoldi_iters >= 1 && p.arnoldi_iters <= 60, CLAIR_ERR_ARG,
                 "arnoldi_iters in [1, 60]");
   CLAIR_REQUIRE(p.degree == 1 || p.degree == 2, CLAIR_ERR_UNSUPPORTED, "degree must be 1 or 2");
+  CLAIR_REQUIRE(p.coarsen == CLAIR_COARSEN_FC || p.coarsen == CLAIR_COARSEN_AGG, CLAIR_ERR_ARG,
+                "unknown coarsening type %d", p.coarsen);
   CLAIR_REQUIRE(p.b_smooth_iters >= 0 && p.gmres_maxit >= 1 && p.rtol > 0.0, CLAIR_ERR_ARG,
                 "bad iteration counts or rtol");
   clair_hierarchy* h = new clair_hierarchy();

@@ -8,6 +8,7 @@
 //    double-shift QR for the Ritz values,
 //  * weighted Jacobi on the C or F subset (CFF / FFC, Section 4; also smooths B),
 //  * the dense inverse of the coarsest operator.
+#include <limits.h>
 #include <math.h>
 
 #include <algorithm>
@@ -163,6 +164,251 @@ void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsign
 }
 
 // ------------------------------------------------------------------------------------
+// Aggregation ("Agg" coarsening): roots form a distance-two independent set of the
+// symmetrised strength graph G (neighbours of i: strong entries of row i of A and of row
+// i of A^T), chosen in rounds by the largest key (lambda_i, lowbias32(i)) among the
+// undecided points within distance two; every point within distance two of a new root
+// is decided.  Points without G-neighbours stay out of every aggregate.  A point next
+// to a root joins it (roots are at least three apart, so it is unique); every other
+// point joins the adjacent aggregate of lowest index.  Roots become the C-points,
+// numbered in increasing point index.
+// ------------------------------------------------------------------------------------
+int coarse_points(const signed char* cf, int n, int** cpts_out, cudaStream_t s);
+
+struct GraphG {
+  const int* Arp;
+  const int* Acol;
+  const unsigned char* sA;
+  const int* Atrp;
+  const int* Atcol;
+  const unsigned char* sAt;
+};
+
+__global__ void agg_init(GraphG g, int n, unsigned long long* __restrict__ key,
+                         signed char* __restrict__ und, signed char* __restrict__ iso,
+                         signed char* __restrict__ root) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned lam = 0;
+  for (int e = g.Atrp[i]; e < g.Atrp[i + 1]; ++e) lam += g.sAt[e];
+  bool has = lam > 0;
+  for (int e = g.Arp[i]; e < g.Arp[i + 1] && !has; ++e) has = g.sA[e] != 0;
+  key[i] = ((unsigned long long)lam << 32) | lowbias32((uint32_t)i);
+  und[i] = has ? 1 : 0;
+  iso[i] = has ? 0 : 1;
+  root[i] = 0;
+}
+
+// m1_i = max over i and its G-neighbours of (undecided ? key : 0)
+__global__ void agg_max1(GraphG g, int n, const unsigned long long* __restrict__ key,
+                         const signed char* __restrict__ und, unsigned long long* __restrict__ m1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long m = und[i] ? key[i] : 0ull;
+  for (int e = g.Arp[i]; e < g.Arp[i + 1]; ++e)
+    if (g.sA[e]) {
+      const int j = g.Acol[e];
+      if (und[j] && key[j] > m) m = key[j];
+    }
+  for (int e = g.Atrp[i]; e < g.Atrp[i + 1]; ++e)
+    if (g.sAt[e]) {
+      const int j = g.Atcol[e];
+      if (und[j] && key[j] > m) m = key[j];
+    }
+  m1[i] = m;
+}
+
+// m2_i = max(m1 over i and its G-neighbours); an undecided point with key == m2 is a root
+__global__ void agg_max2(GraphG g, int n, const unsigned long long* __restrict__ key,
+                         const signed char* __restrict__ und,
+                         const unsigned long long* __restrict__ m1,
+                         signed char* __restrict__ newr, signed char* __restrict__ root) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long m = m1[i];
+  for (int e = g.Arp[i]; e < g.Arp[i + 1]; ++e)
+    if (g.sA[e] && m1[g.Acol[e]] > m) m = m1[g.Acol[e]];
+  for (int e = g.Atrp[i]; e < g.Atrp[i + 1]; ++e)
+    if (g.sAt[e] && m1[g.Atcol[e]] > m) m = m1[g.Atcol[e]];
+  const bool r = und[i] && key[i] == m;
+  newr[i] = r ? 1 : 0;
+  if (r) root[i] = 1;
+}
+
+// out_i = 1 if some G-neighbour of i has in_j != 0
+__global__ void agg_near(GraphG g, int n, const signed char* __restrict__ in,
+                         signed char* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool hit = false;
+  for (int e = g.Arp[i]; e < g.Arp[i + 1] && !hit; ++e) hit = g.sA[e] && in[g.Acol[e]];
+  for (int e = g.Atrp[i]; e < g.Atrp[i + 1] && !hit; ++e) hit = g.sAt[e] && in[g.Atcol[e]];
+  out[i] = hit ? 1 : 0;
+}
+
+// decides every point within distance two of a new root; counts the undecided rest
+__global__ void agg_decide(GraphG g, int n, const signed char* __restrict__ newr,
+                           const signed char* __restrict__ near1, signed char* __restrict__ und,
+                           int* __restrict__ remaining) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !und[i]) return;
+  bool hit = newr[i] || near1[i];
+  for (int e = g.Arp[i]; e < g.Arp[i + 1] && !hit; ++e) hit = g.sA[e] && near1[g.Acol[e]];
+  for (int e = g.Atrp[i]; e < g.Atrp[i + 1] && !hit; ++e) hit = g.sAt[e] && near1[g.Atcol[e]];
+  if (hit)
+    und[i] = 0;
+  else
+    atomicAdd(remaining, 1);
+}
+
+__global__ void agg_root_index(const int* __restrict__ cpts, int nc, int* __restrict__ cidx) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nc) cidx[cpts[r]] = r;
+}
+
+// first_j: the root's own index, the unique adjacent root's index, or -1
+__global__ void agg_first(GraphG g, int n, const signed char* __restrict__ root,
+                          const signed char* __restrict__ iso, const int* __restrict__ cidx,
+                          int* __restrict__ first, int* __restrict__ err) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  if (root[j]) {
+    first[j] = cidx[j];
+    return;
+  }
+  int found = -1;
+  if (!iso[j]) {
+    for (int e = g.Arp[j]; e < g.Arp[j + 1]; ++e)
+      if (g.sA[e] && root[g.Acol[e]]) {
+        const int r = g.Acol[e];
+        if (found >= 0 && found != r) atomicAdd(err, 1);
+        found = r;
+      }
+    for (int e = g.Atrp[j]; e < g.Atrp[j + 1]; ++e)
+      if (g.sAt[e] && root[g.Atcol[e]]) {
+        const int r = g.Atcol[e];
+        if (found >= 0 && found != r) atomicAdd(err, 1);
+        found = r;
+      }
+  }
+  first[j] = found >= 0 ? cidx[found] : -1;
+}
+
+// remaining points: the lowest aggregate index among their G-neighbours' first choices
+__global__ void agg_final(GraphG g, int n, const signed char* __restrict__ iso,
+                          const int* __restrict__ first, int* __restrict__ agg,
+                          int* __restrict__ err) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int a = first[j];
+  if (a < 0 && !iso[j]) {
+    int best = INT_MAX;
+    for (int e = g.Arp[j]; e < g.Arp[j + 1]; ++e)
+      if (g.sA[e] && first[g.Acol[e]] >= 0) best = min(best, first[g.Acol[e]]);
+    for (int e = g.Atrp[j]; e < g.Atrp[j + 1]; ++e)
+      if (g.sAt[e] && first[g.Atcol[e]] >= 0) best = min(best, first[g.Atcol[e]]);
+    if (best == INT_MAX) atomicAdd(err, 1);
+    a = best == INT_MAX ? -1 : best;
+  }
+  agg[j] = a;
+}
+
+__global__ void agg_to_cf(int n, const signed char* __restrict__ root, signed char* __restrict__ cf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) cf[i] = root[i];
+}
+
+void aggregate(const Csr& A, const Csr& At, const unsigned char* sA, const unsigned char* sAt,
+               signed char* cf, int* agg, cudaStream_t s) {
+  const int n = A.rows;
+  if (!n) return;
+  const GraphG g{A.rowptr, A.col, sA, At.rowptr, At.col, sAt};
+  unsigned long long* key = dalloc<unsigned long long>(n, s);
+  unsigned long long* m1 = dalloc<unsigned long long>(n, s);
+  signed char* und = dalloc<signed char>(n, s);
+  signed char* iso = dalloc<signed char>(n, s);
+  signed char* root = dalloc<signed char>(n, s);
+  signed char* newr = dalloc<signed char>(n, s);
+  signed char* near1 = dalloc<signed char>(n, s);
+  int* remaining = dalloc<int>(2, s);
+  const int gr = ceil_div(n, 256);
+  agg_init<<<gr, 256, 0, s>>>(g, n, key, und, iso, root); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  for (int round = 0;; ++round) {
+    CLAIR_REQUIRE(round < 10000, CLAIR_ERR_CAPACITY, "aggregation did not terminate");
+    CLAIR_CUDA(cudaMemsetAsync(remaining, 0, sizeof(int), s));
+    agg_max1<<<gr, 256, 0, s>>>(g, n, key, und, m1); ::clair::count_launch();
+    agg_max2<<<gr, 256, 0, s>>>(g, n, key, und, m1, newr, root); ::clair::count_launch();
+    agg_near<<<gr, 256, 0, s>>>(g, n, newr, near1); ::clair::count_launch();
+    agg_decide<<<gr, 256, 0, s>>>(g, n, newr, near1, und, remaining); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+    int h = 0;
+    CLAIR_CUDA(cudaMemcpyAsync(&h, remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    if (h == 0) break;
+  }
+  agg_to_cf<<<gr, 256, 0, s>>>(n, root, cf); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int* cpts = nullptr;
+  const int nc = coarse_points(cf, n, &cpts, s);
+  int* cidx = dalloc<int>(n, s);
+  int* first = dalloc<int>(n, s);
+  int* err = remaining + 1;
+  CLAIR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  if (nc) {
+    agg_root_index<<<ceil_div(nc, 256), 256, 0, s>>>(cpts, nc, cidx); ::clair::count_launch();
+  }
+  agg_first<<<gr, 256, 0, s>>>(g, n, root, iso, cidx, first, err); ::clair::count_launch();
+  agg_final<<<gr, 256, 0, s>>>(g, n, iso, first, agg, err); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int h = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  dfree(key, s);
+  dfree(m1, s);
+  dfree(und, s);
+  dfree(iso, s);
+  dfree(root, s);
+  dfree(newr, s);
+  dfree(near1, s);
+  dfree(remaining, s);
+  dfree(cpts, s);
+  dfree(cidx, s);
+  dfree(first, s);
+  CLAIR_REQUIRE(h == 0, CLAIR_ERR_ARG, "aggregation: %d points without a unique root or aggregate", h);
+}
+
+// Members of every aggregate as a CSR (nc rows; order within a row is irrelevant: the
+// pattern is a set).
+__global__ void agg_count(const int* __restrict__ agg, int n, int* __restrict__ cnt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n && agg[j] >= 0) atomicAdd(&cnt[agg[j]], 1);
+}
+
+__global__ void agg_fill(const int* __restrict__ agg, int n, const int* __restrict__ rp,
+                         int* __restrict__ cursor, int* __restrict__ members) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n && agg[j] >= 0) members[rp[agg[j]] + atomicAdd(&cursor[agg[j]], 1)] = j;
+}
+
+void aggregate_members(const int* agg, int n, int nc, int** rp_out, int** members_out,
+                       cudaStream_t s) {
+  int* cnt = dalloc<int>(nc + 1, s);
+  CLAIR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (nc + 1), s));
+  if (n) agg_count<<<ceil_div(n, 256), 256, 0, s>>>(agg, n, cnt); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  int* rp = dalloc<int>(nc + 1, s);
+  const int total = (int)exclusive_scan(cnt, rp, nc, s, true);
+  int* members = dalloc<int>(std::max(total, 1), s);
+  CLAIR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (nc + 1), s));
+  if (n) agg_fill<<<ceil_div(n, 256), 256, 0, s>>>(agg, n, rp, cnt, members); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  dfree(cnt, s);
+  *rp_out = rp;
+  *members_out = members;
+}
+
+// ------------------------------------------------------------------------------------
 // Pattern of Algorithm 1 for the operator Ahat, walked on Ahat^T (= Wm): the column of
 // coarse point i collects the F-points j with S_ji (row i of Wm, strong in the column-
 // relative sense) and, for m = 2, the F-points j with S_jk for such an F-point k.  The C
@@ -191,11 +437,12 @@ __device__ __forceinline__ void pt_insert(int* keys, int key, int* fresh, int* e
   atomicExch(err, 1);
 }
 
-template <bool COUNT>
+template <bool COUNT, bool AGG>
 __global__ void __launch_bounds__(32 * PT_WARPS)
 pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
                const unsigned char* __restrict__ sW, const signed char* __restrict__ cf,
-               const int* __restrict__ cpts, int nc, int degree, int* __restrict__ count,
+               const int* __restrict__ cpts, int nc, int degree, const int* __restrict__ Mrp,
+               const int* __restrict__ Mcol, int* __restrict__ count,
                const int* __restrict__ Zrp, int* __restrict__ Zcol, int* __restrict__ err) {
   __shared__ int keys[PT_WARPS][PT_CAP];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -207,15 +454,30 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
   const int i = cpts[r];
   int fresh = 0;
   if (lane == 0) pt_insert(K, i, &fresh, err);
-  for (int e = Wrp[i] + lane; e < Wrp[i + 1]; e += 32)
-    if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], &fresh, err);
-  if (degree >= 2) {
-    // second hop from every first-hop F-point, one first-hop point at a time
-    for (int e1 = Wrp[i]; e1 < Wrp[i + 1]; ++e1) {
-      const int k = Wcol[e1];
-      if (!sW[e1] || cf[k]) continue;
-      for (int e = Wrp[k] + lane; e < Wrp[k + 1]; e += 32)
-        if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], &fresh, err);
+  if (!AGG) {
+    // T column i = i and the F-points j with S_ji
+    for (int e = Wrp[i] + lane; e < Wrp[i + 1]; e += 32)
+      if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], &fresh, err);
+    if (degree >= 2) {
+      // second hop from every first-hop F-point, one first-hop point at a time
+      for (int e1 = Wrp[i]; e1 < Wrp[i + 1]; ++e1) {
+        const int k = Wcol[e1];
+        if (!sW[e1] || cf[k]) continue;
+        for (int e = Wrp[k] + lane; e < Wrp[k + 1]; e += 32)
+          if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], &fresh, err);
+      }
+    }
+  } else {
+    // T column i = the members of aggregate r (its root i included)
+    for (int m = Mrp[r] + lane; m < Mrp[r + 1]; m += 32)
+      if (!cf[Mcol[m]]) pt_insert(K, Mcol[m], &fresh, err);
+    if (degree >= 2) {
+      // second hop: F-points j with S_jk for every member k
+      for (int m = Mrp[r]; m < Mrp[r + 1]; ++m) {
+        const int k = Mcol[m];
+        for (int e = Wrp[k] + lane; e < Wrp[k + 1]; e += 32)
+          if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], &fresh, err);
+      }
     }
   }
   __syncwarp();
@@ -247,7 +509,8 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
 // Builds the pattern CSR Z (nc rows) for Algorithm 1 on Ahat, walking Wm = Ahat^T with
 // its strength mask sW.
 void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf, const int* cpts,
-                   int nc, int n, int degree, Csr& Z, cudaStream_t s) {
+                   int nc, int n, int degree, const int* Mrp, const int* Mcol, Csr& Z,
+                   cudaStream_t s) {
   CLAIR_REQUIRE(degree == 1 || degree == 2, CLAIR_ERR_UNSUPPORTED,
                 "pattern degree %d not supported (1 or 2)", degree);
   Z.rows = nc;
@@ -256,16 +519,33 @@ void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf
   int* err = dalloc<int>(1, s);
   CLAIR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   const int g = ceil_div(nc, PT_WARPS);
-  if (nc)
-    pattern_kernel<true><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc, degree,
-                                                     count, nullptr, nullptr, err); ::clair::count_launch();
+  const bool agg = Mrp != nullptr;
+  if (nc) {
+    if (agg)
+      pattern_kernel<true, true><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
+                                                             degree, Mrp, Mcol, count, nullptr,
+                                                             nullptr, err);
+    else
+      pattern_kernel<true, false><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
+                                                              degree, nullptr, nullptr, count,
+                                                              nullptr, nullptr, err);
+    ::clair::count_launch();
+  }
   CLAIR_LAUNCHED();
   Z.rowptr = dalloc<int>(nc + 1, s);
   Z.nnz = (int)exclusive_scan(count, Z.rowptr, nc, s, true);
   Z.col = dalloc<int>(Z.nnz, s);
-  if (nc)
-    pattern_kernel<false><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc, degree,
-                                                      nullptr, Z.rowptr, Z.col, err); ::clair::count_launch();
+  if (nc) {
+    if (agg)
+      pattern_kernel<false, true><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
+                                                              degree, Mrp, Mcol, nullptr, Z.rowptr,
+                                                              Z.col, err);
+    else
+      pattern_kernel<false, false><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts,
+                                                               nc, degree, nullptr, nullptr,
+                                                               nullptr, Z.rowptr, Z.col, err);
+    ::clair::count_launch();
+  }
   CLAIR_LAUNCHED();
   int h = 0;
   CLAIR_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -80,20 +80,31 @@ def rowwise_err(G, Oref):
     return worst
 
 
-SMALL_CASES = [("cfg1", None), ("eps0", 0.0), ("eps1e-4", 1e-4), ("eps1", 1.0)]
+SMALL_CASES = [("cfg1", None), ("eps0", 0.0), ("eps1e-4", 1e-4), ("eps1", 1.0),
+               ("agg2d", 1e-2), ("agg3d16", 1e-3), ("agg3d20", 1e-3)]
 
 
 def small_problem(tag, eps):
     if tag == "cfg1":
         return workloads.config1()
+    if tag.startswith("agg3d"):
+        return workloads.config3(int(tag[5:]))      # recirculating 3D flow, nside^3 nodes
     return workloads.constdir_2d(48, math.pi / 6, eps, seed=1, degree=2, name=tag)
+
+
+def oracle_params(tag):
+    return O.Params(coarsen="AGG") if tag.startswith("agg") else O.Params()
+
+
+def gpu_coarsen(tag):
+    return 1 if tag.startswith("agg") else 0
 
 
 @pytest.mark.parametrize("tag,eps", SMALL_CASES)
 def test_hierarchy_matches_oracle_fp64(cl, tag, eps):
     prob = small_problem(tag, eps)
-    H = O.build_hierarchy(prob.A, prob.B, O.Params())
-    h = gpu_setup(cl, prob)
+    H = O.build_hierarchy(prob.A, prob.B, oracle_params(tag))
+    h = gpu_setup(cl, prob, coarsen=gpu_coarsen(tag))
     try:
         G = host_levels(cl, h)
         assert len(G) == len(H.levels)
@@ -133,10 +144,10 @@ def test_hierarchy_matches_oracle_fp64(cl, tag, eps):
 def test_solve_matches_oracle(cl, tag, eps, precision):
     import torch
     prob = small_problem(tag, eps)
-    H = O.build_hierarchy(prob.A, prob.B, O.Params())
+    H = O.build_hierarchy(prob.A, prob.B, oracle_params(tag))
     A = O.csr_of(prob.A)
     x_o, its_o, _ = O.fgmres(A, prob.f, lambda v: O.vcycle(H, v), 50, 1e-8, 200)
-    h = gpu_setup(cl, prob, precision)
+    h = gpu_setup(cl, prob, precision, coarsen=gpu_coarsen(tag))
     try:
         f = dev(prob.f, torch.float64)
         u = torch.zeros_like(f)
