@@ -34,7 +34,7 @@ typedef enum {
   CLAIR_ERR_SINGULAR_BLOCK = 3, /* a local block had a zero pivot (its weights are set to 0) */
   CLAIR_ERR_NONFINITE = 4,      /* NaN or Inf in an input or a result */
   CLAIR_ERR_NOT_CONVERGED = 5,  /* FGMRES stopped at gmres_maxit above rtol */
-  CLAIR_ERR_CAPACITY = 6,       /* a size exceeded a kernel limit (e.g. local system > 512) */
+  CLAIR_ERR_CAPACITY = 6,       /* a size exceeded a kernel limit (e.g. local system > 4096) */
   CLAIR_ERR_UNSUPPORTED = 7     /* a parameter combination this build does not implement */
 } clair_status;
 
@@ -160,7 +160,7 @@ clair_status clair_free(clair_h h);
  *   cf                     : device int8 [n] splitting
  *   nc, Z_rowptr, Z_col    : device CSR pattern (nc x n), rows = coarse points, columns
  *                            sorted, each row containing its own C-point column (identity)
- *                            and the F-points of its local system (at most 512 of them)
+ *                            and the F-points of its local system (at most 4096 of them)
  *   B                      : device float64 [n] mode vector on the fine points
  *   precision              : CLAIR_FP64 (float64 local solves) or CLAIR_MIXED (float32)
  *   Z_val                  : device float64 [nnz] output weights (1 at identity entries)

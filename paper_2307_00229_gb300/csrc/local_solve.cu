@@ -25,10 +25,10 @@
 
 namespace clair {
 
-// Solvable buckets: T in [1,8], (8,16], (16,32], (32,64], (64,128], (128,512]; bucket 6
+// Solvable buckets: T in [1,8], (8,16], (16,32], (32,64], (64,128], (128,4096]; bucket 6
 // counts systems larger than LS_TBIG (refused).
 constexpr int LS_BUCKETS = 6;
-constexpr int LS_TBIG = 512;
+constexpr int LS_TBIG = 4096;
 __host__ __device__ inline int ls_bucket(int T) {
   return T <= 8 ? 0 : T <= 16 ? 1 : T <= 32 ? 2 : T <= 64 ? 3 : T <= 128 ? 4 : T <= LS_TBIG ? 5 : 6;
 }
@@ -332,12 +332,18 @@ static size_t cta_smem() {
 }
 
 // ------------------------------------------------------------------------------------
-// Large systems (128 < T <= 512, rare: long rows on coarse levels of advective problems):
-// one block of 256 threads per system, the matrix in a global scratch tile (row-major,
-// leading dimension `pitch`), thread t owning rows t, t+256, ...; same implicit partial
-// pivoting as above.
+// Large systems (128 < T <= LS_TBIG, rare: long rows on coarse levels): one block of 256
+// threads per system, the matrix in a global scratch tile stored column-major (leading
+// dimension `pitch`) so that the threads, which own rows t, t+256, ..., touch consecutive
+// addresses in every column; same implicit partial pivoting as above.  The per-system
+// index and vector arrays live in dynamic shared memory sized for `pitch` unknowns.
 // ------------------------------------------------------------------------------------
 constexpr int LB_THREADS = 256;
+
+template <class Real>
+__host__ __device__ constexpr size_t big_smem(int pitch) {
+  return (size_t)pitch * (3 * sizeof(int) + 2 * sizeof(Real)) + 2 * sizeof(Real);
+}
 
 template <class Real>
 __global__ void __launch_bounds__(LB_THREADS)
@@ -346,11 +352,12 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
            const int* __restrict__ Zcol, const int* __restrict__ cpts,
            const int* __restrict__ work, double* __restrict__ Zval,
            unsigned long long* __restrict__ nsingular, Real* __restrict__ scratch, int pitch) {
-  __shared__ int zl[LS_TBIG];
-  __shared__ int stepof[LS_TBIG];
-  __shared__ int steprow[LS_TBIG];
-  __shared__ Real rhs[LS_TBIG];
-  __shared__ Real xs[LS_TBIG];
+  extern __shared__ __align__(16) unsigned char lb_smem[];
+  Real* rhs = reinterpret_cast<Real*>(lb_smem);
+  Real* xs = rhs + pitch;
+  int* zl = reinterpret_cast<int*>(xs + pitch);
+  int* stepof = zl + pitch;
+  int* steprow = stepof + pitch;
   __shared__ Real red_v[LB_THREADS / 32];
   __shared__ int red_w[LB_THREADS / 32];
   __shared__ int s_piv, s_d, s_sing;
@@ -359,8 +366,8 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
   const int i = cpts[r];
   const int base = Zrp[r];
   const int len = Zrp[r + 1] - base;
-  const int T = len - 1;
-  Real* M = scratch + (size_t)blockIdx.x * pitch * pitch;
+  const int T = len - 1;  // T <= pitch (pitch = the largest T of the launch)
+  Real* M = scratch + (size_t)blockIdx.x * pitch * pitch;  // M(p, q) at M[q * pitch + p]
   if (t == 0) {
     s_d = T;
     s_sing = 0;
@@ -374,8 +381,9 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
     zl[p] = Zcol[base + p + (p >= d ? 1 : 0)];
     rhs[p] = Real(0);
     stepof[p] = -1;
-    for (int q = 0; q < T; ++q) M[(size_t)p * pitch + q] = Real(0);
   }
+  for (int q = 0; q < T; ++q)
+    for (int p = t; p < T; p += LB_THREADS) M[(size_t)q * pitch + p] = Real(0);
   __syncthreads();
   for (int p = t; p < T; p += LB_THREADS) {
     const int l = zl[p];
@@ -385,17 +393,18 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
         rhs[p] = Real(-Aval[e]);
       } else {
         const int q = find_sorted(zl, T, c);
-        if (q >= 0) M[(size_t)p * pitch + q] = Real(Aval[e]);
+        if (q >= 0) M[(size_t)q * pitch + p] = Real(Aval[e]);
       }
     }
   }
   __syncthreads();
   for (int k = 0; k < T; ++k) {
+    const Real* colk = M + (size_t)k * pitch;
     Real v = Real(-1);
     int who = T;
     for (int p = t; p < T; p += LB_THREADS)
       if (stepof[p] < 0) {
-        const Real a = M[(size_t)p * pitch + k];
+        const Real a = colk[p];
         const Real m = a < 0 ? -a : a;
         if (m > v) {  // rows visited in increasing order: ties keep the lowest row
           v = m;
@@ -431,27 +440,29 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
     }
     __syncthreads();
     const int piv = s_piv;
-    const Real* prow = M + (size_t)piv * pitch;
-    const Real pk = prow[k];
+    const Real pk = colk[piv];
     for (int p = t; p < T; p += LB_THREADS)
       if (stepof[p] < 0 && pk != Real(0)) {
-        Real* row = M + (size_t)p * pitch;
-        const Real l = row[k] / pk;
-        for (int j = k + 1; j < T; ++j) row[j] -= l * prow[j];
+        const Real l = colk[p] / pk;
+        for (int j = k + 1; j < T; ++j) {
+          Real* colj = M + (size_t)j * pitch;
+          colj[p] -= l * colj[piv];
+        }
         rhs[p] -= l * rhs[piv];
       }
     __syncthreads();
   }
   for (int k = T - 1; k >= 0; --k) {
     const int own = steprow[k];
+    const Real* colk = M + (size_t)k * pitch;
     if (t == 0) {
-      const Real dk = M[(size_t)own * pitch + k];
+      const Real dk = colk[own];
       xs[k] = dk != Real(0) ? rhs[own] / dk : Real(0);
     }
     __syncthreads();
     const Real xk = xs[k];
     for (int p = t; p < T; p += LB_THREADS)
-      if (stepof[p] < k) rhs[p] -= M[(size_t)p * pitch + k] * xk;
+      if (stepof[p] < k) rhs[p] -= colk[p] * xk;
     __syncthreads();
   }
   const bool sing = s_sing != 0;
@@ -580,6 +591,8 @@ static void launch_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, cons
                                     (int)cta_smem<Real, 64>()));
     CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)cta_smem<Real, 128>()));
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_big<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)big_smem<Real>(LS_TBIG)));
     attr = true;
   }
   const int per_block[3] = {LS_WARPS * 4, LS_WARPS * 2, LS_WARPS};
@@ -604,7 +617,8 @@ static void launch_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, cons
                   counts_h[5]);
     for (int off = 0; off < counts_h[5]; off += big_chunk) {
       const int cnt = std::min(big_chunk, counts_h[5] - off);
-      lsolve_big<Real><<<cnt, LB_THREADS, 0, s>>>(Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts,
+      lsolve_big<Real><<<cnt, LB_THREADS, big_smem<Real>(big_pitch), s>>>(
+          Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts,
                                                  lists + 5LL * nc + off, Zval, nsing, big_scratch,
                                                  big_pitch); ::clair::count_launch();
     }

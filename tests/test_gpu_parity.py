@@ -202,9 +202,12 @@ def test_vcycle_matches_oracle(cl, precision):
 EDGE_T = [1, 2, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 100, 127, 128]
 
 
-def crafted_case(nside=26, eps=1.0, seed=5):
+EDGE_T_BIG = [129, 200, 511, 512, 513, 700, 1000]
+
+
+def crafted_case(nside=26, eps=1.0, seed=5, sizes=EDGE_T):
     """C-points on a sparse lattice; pattern of C-point number r = the T_r F-points
-    nearest to it (Chebyshev distance, then index), T_r cycling through EDGE_T, with a
+    nearest to it (Chebyshev distance, then index), T_r cycling through `sizes`, with a
     few empty patterns."""
     A = O.csr_of(workloads.advdiff_2d(nside, 0.3, 0.7, eps))
     n = A.shape[0]
@@ -214,7 +217,7 @@ def crafted_case(nside=26, eps=1.0, seed=5):
     F = np.flatnonzero(cf == 0)
     rows, cols = [], []
     for r, c in enumerate(cpts):
-        T = 0 if r % 11 == 10 else EDGE_T[r % len(EDGE_T)]
+        T = 0 if r % 11 == 10 else sizes[r % len(sizes)]
         d = np.maximum(np.abs(ix[F] - ix[c]), np.abs(iy[F] - iy[c]))
         order = np.lexsort((F, d))[:T]
         sel = np.sort(F[order])
@@ -238,10 +241,12 @@ def pattern_rows_with_identity(Wpat, cpts):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("eps", [1.0, 1e-3])
-def test_local_weights_every_bucket(cl, precision, eps):
+@pytest.mark.parametrize("eps,big", [(1.0, False), (1e-3, False), (1.0, True)])
+def test_local_weights_every_bucket(cl, precision, eps, big):
+    """Every bucket edge of the batched local solves, and (big) the large-system path
+    up to T = 1000 (one 256-thread block per system, column-major global tile)."""
     import torch
-    A, cf, cpts, Wpat, B = crafted_case(eps=eps)
+    A, cf, cpts, Wpat, B = crafted_case(nside=48, eps=eps, sizes=EDGE_T_BIG) if big else crafted_case(eps=eps)
     n = A.shape[0]
     W = O.clair_algorithm1(A, cf, B, Wpat, O.Params()).tocsc()
     zrp, zcol = pattern_rows_with_identity(Wpat, cpts)
@@ -256,7 +261,9 @@ def test_local_weights_every_bucket(cl, precision, eps):
     ref = (W.T + ident).tocsr()
     ref.sort_indices()
     err = rowwise_err(got, ref)
-    assert err <= (FP64_TOL if precision == 0 else FP32_TOL), err
+    # FP32 elimination error grows with T (~T u32 for these well-conditioned blocks)
+    tol = FP64_TOL if precision == 0 else (FP32_TOL if not big else 1e-4)
+    assert err <= tol, err
     # the constraint itself: sum_i w_ji B_c(i) = B_j on every F column with a pattern
     cols_hit = np.unique(Wpat.indices)
     s = np.asarray((sp.diags(B[cpts]) @ got).sum(axis=0)).ravel()
