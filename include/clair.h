@@ -206,6 +206,43 @@ clair_status clair_local_weights_noalloc(int n, const int* Ahat_rowptr, const in
                                          int precision, double* Z_val, void* stream,
                                          int64_t* singular_out, int64_t* empty_out);
 
+/* ---- Batches of independent problems ----------------------------------------------
+ * Many instances A_i u_i = f_i (not in the paper; its method applied to each instance)
+ * set up and solved together as one block-diagonal operator, so every step of the setup
+ * (strength, splitting, patterns, the bucketed local solves of Algorithm 1, the
+ * projection, the Galerkin product) and every V-cycle kernel is one launch for the whole
+ * batch.  Each instance's hierarchy equals the one clair_setup builds for it alone (up
+ * to the summation order of its relaxation weight): splitting keys use instance-local
+ * indices, each instance gets its own Arnoldi weight (Section 4) from its own start
+ * vector, and an instance that reaches n_i <= coarse_max (or max_levels, or a splitting
+ * with no C- or no F-point) is frozen: identity transfers and zero relaxation weight
+ * until the batch's coarsest level, where each instance's diagonal block is inverted. */
+
+/* Setup of a batch: A is the block-diagonal CSR of all instances, instance i owning rows
+ * and columns offsets_host[i] .. offsets_host[i+1]-1.
+ *   ninst, offsets_host : host int [ninst + 1], offsets_host[0] = 0, offsets_host[ninst]
+ *                         = n, strictly increasing
+ *   other arguments     : as clair_setup (B concatenated over the instances)
+ * CLAIR_ERR_ARG if an entry couples two instances or the offsets are invalid;
+ * CLAIR_ERR_UNSUPPORTED if arnoldi_iters > 15.  clair_solve on the result solves all
+ * instances at once (one FGMRES on the block-diagonal system, absolute tolerance
+ * rtol * min_i ||f_i||, so every instance reaches rtol relative to its own ||f_i||;
+ * *relres reports the worst instance). */
+clair_status clair_setup_batched(int ninst, const int* offsets_host, int n, int nnz,
+                                 const int* rowptr, const int* col, const double* val,
+                                 const double* B, const clair_params* p, void* stream,
+                                 clair_h* out);
+
+/* Per-instance view of level `level` of a hierarchy (a single-problem hierarchy reports
+ * one instance).  Output pointers are host arrays and may be NULL:
+ *   ninst        : number of instances
+ *   offsets_host : int [ninst + 1], the instances' row ranges on this level
+ *   omega_host   : double [ninst], relaxation weight of each instance on this level
+ *   frozen_host  : int8 [ninst], 1 where the instance is frozen (its coarsest level was
+ *                  reached) on this level */
+clair_status clair_batch_view(clair_h h, int level, int* ninst, int* offsets_host,
+                              double* omega_host, signed char* frozen_host);
+
 /* ---- Adjoint path: gradients of a loss of the solutions -----------------------------
  * The paper solves A u = f (Section 1).  For a loss L(u_1..u_k) of several solutions, the
  * implicit-function theorem gives A^T lam_r = dL/du_r and dL/da_ij = -sum_r lam_r[i] u_r[j]

@@ -104,6 +104,9 @@ _SIGNATURES = {
     "clair_local_weights": (_I, [_I, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _PI64, _PI64]),
     "clair_local_weights_noalloc": (_I, [_I, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _PI64,
                                          _PI64]),
+    "clair_setup_batched": (_I, [_I, _P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(clair_params), _P,
+                                 ctypes.POINTER(_P)]),
+    "clair_batch_view": (_I, [_P, _I, _PI, _P, _P, _P]),
     "clair_setup_adjoint": (_I, [_P, _P, ctypes.POINTER(_P)]),
     "clair_sddmm_grad": (_I, [_I, _I, _P, _P, _I, _P, _P, _P, _P]),
     "clair_advdiff2d_param_grad": (_I, [_I, ctypes.c_double, _P, _P, _P, _P, _P, _I, _P, _P, _P,
@@ -174,6 +177,32 @@ def clair_setup(rowptr, col, val, B, params: clair_params | None = None, stream=
                               ctypes.byref(params) if params is not None else None,
                               _stream(stream), ctypes.byref(h)))
     return h
+
+
+def clair_setup_batched(offsets, rowptr, col, val, B, params: clair_params | None = None,
+                        stream=None) -> ctypes.c_void_p:
+    """Setup of a batch: block-diagonal CSR, instance i owning rows offsets[i]..offsets[i+1]-1."""
+    off = (ctypes.c_int * len(offsets))(*[int(x) for x in offsets])
+    n = rowptr.numel() - 1
+    h = ctypes.c_void_p()
+    _check(load().clair_setup_batched(len(offsets) - 1, off, n, col.numel(), _dptr(rowptr, torch.int32),
+                                      _dptr(col, torch.int32), _dptr(val, torch.float64),
+                                      _dptr(B, torch.float64),
+                                      ctypes.byref(params) if params is not None else None,
+                                      _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def clair_batch_view(h, level: int) -> dict:
+    """Per-instance row ranges, weights and frozen flags of level ``level`` (host lists)."""
+    ninst = ctypes.c_int()
+    _check(load().clair_batch_view(h, level, ctypes.byref(ninst), None, None, None))
+    k = ninst.value
+    off = (ctypes.c_int * (k + 1))()
+    om = (ctypes.c_double * k)()
+    fz = (ctypes.c_int8 * k)()
+    _check(load().clair_batch_view(h, level, ctypes.byref(ninst), off, om, fz))
+    return {"ninst": k, "offsets": list(off), "omega": list(om), "frozen": [int(x) for x in fz]}
 
 
 def clair_solve(h, f, u, stream=None, raise_not_converged: bool = True):

@@ -15,9 +15,9 @@ namespace clair {
 void strength(const Csr& M, const double* thr, double theta, int mode, unsigned char* mask,
               cudaStream_t s);
 void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsigned char* sAt,
-              signed char* cf, cudaStream_t s);
+              const int* lbase, signed char* cf, cudaStream_t s);
 void aggregate(const Csr& A, const Csr& At, const unsigned char* sA, const unsigned char* sAt,
-               signed char* cf, int* agg, cudaStream_t s);
+               const int* lbase, signed char* cf, int* agg, cudaStream_t s);
 void aggregate_members(const int* agg, int n, int nc, int** rp_out, int** members_out,
                        cudaStream_t s);
 void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf, const int* cpts,
@@ -37,9 +37,13 @@ void jacobi_from_zero(int rows, const T* dinv, const signed char* cf, int which,
                       const T* b, T* x, cudaStream_t s);
 double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed,
                       double* omega_dev, cudaStream_t s);
-void dense_inverse(const Csr& A, double* Inv, cudaStream_t s);
+void arnoldi_weight_batched(const Csr& A, const double* dinv, int iters, uint64_t seed,
+                            const std::vector<int>& off, double* omega_dev, cudaStream_t s);
+void dense_inverse(const Csr& A, const std::vector<int>& off, double* Inv, int** d_off,
+                   long long** d_ioff, cudaStream_t s);
 template <class T>
-void coarse_apply(const T* Inv, int n, const T* b, T* x, cudaStream_t s);
+void coarse_apply(const T* Inv, const int* d_off, const long long* d_ioff, int nblk, int n,
+                  const T* b, T* x, cudaStream_t s);
 int coarse_points(const signed char* cf, int n, int** cpts_out, cudaStream_t s);
 void transfer_weights(const Csr& Ahat, const signed char* cf, const int* cpts, Csr& Z,
                       const double* B, int precision, LocalStats& st, Csr* keep_t,
@@ -58,6 +62,16 @@ struct Level {
   double omega = 1.0;
   double* B_P = nullptr;
   double* B_R = nullptr;
+  // batch (block-diagonal instances): host row offsets of the instances on this level,
+  // instance and instance base of every row, weights and frozen flags per instance, and
+  // the relaxation weights folded into D^-1 per row (pre and post smoothing)
+  std::vector<int> off;
+  int* inst = nullptr;
+  int* lbase = nullptr;
+  std::vector<double> omega_inst;
+  std::vector<char> frozen;
+  double *wpre64 = nullptr, *wpost64 = nullptr;
+  float *wpre32 = nullptr, *wpost32 = nullptr;
   // cycle work vectors
   double *b64 = nullptr, *x64 = nullptr, *y64 = nullptr, *r64 = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *y32 = nullptr, *r32 = nullptr;
@@ -90,6 +104,10 @@ struct clair_hierarchy {
   double* vin = nullptr;                    // its fixed input and output vectors
   double* zout = nullptr;
   double* B0 = nullptr;                     // the caller's mode vector, unsmoothed
+  int ninst = 1;                            // instances of a block-diagonal batch
+  int* coarse_off = nullptr;                // coarsest diagonal blocks (device offsets)
+  long long* coarse_ioff = nullptr;         // and their inverses' offsets in Inv
+  int coarse_nblk = 1;
 };
 
 namespace clair {
@@ -121,6 +139,12 @@ static void release_level(Level& L, cudaStream_t s) {
   dfree(L.cpts, s);
   dfree(L.B_P, s);
   dfree(L.B_R, s);
+  dfree(L.inst, s);
+  dfree(L.lbase, s);
+  dfree(L.wpre64, s);
+  dfree(L.wpost64, s);
+  dfree(L.wpre32, s);
+  dfree(L.wpost32, s);
   dfree(L.b64, s);
   dfree(L.x64, s);
   dfree(L.y64, s);
@@ -137,6 +161,8 @@ static void release_all(clair_hierarchy* h) {
   h->lv.clear();
   dfree(h->Inv, s);
   dfree(h->Inv32, s);
+  dfree(h->coarse_off, s);
+  dfree(h->coarse_ioff, s);
   Krylov& k = h->kr;
   dfree(k.V, s);
   dfree(k.Z, s);
@@ -166,6 +192,161 @@ __global__ void inject(const double* __restrict__ x, const int* __restrict__ cpt
   if (i < nc) y[i] = x[cpts[i]];
 }
 
+
+// ---- batch of independent instances (block-diagonal operator) ------------------------
+// Rows off[i] .. off[i+1]-1 of every level belong to instance i (coarse points are
+// numbered in fine order, so the ranges stay contiguous).  An instance that reaches its
+// coarsest size is frozen: all its points become C-points (identity transfers, no
+// F-points) and its relaxation weights are zero, so it passes unchanged to the batch's
+// coarsest level, where its diagonal block is inverted.
+__global__ void row_instance(const int* __restrict__ off, int ninst, int n, int* __restrict__ inst,
+                             int* __restrict__ lbase) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int lo = 0, hi = ninst;  // largest i with off[i] <= r
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= r) lo = mid; else hi = mid;
+  }
+  inst[r] = lo;
+  lbase[r] = off[lo];
+}
+
+// cnt[i] = number of C-points of instance i (one block per instance)
+__global__ void count_c_instances(const signed char* __restrict__ cf, const int* __restrict__ off,
+                                  int* __restrict__ cnt) {
+  __shared__ int part[8];
+  const int i = blockIdx.x;
+  int c = 0;
+  for (int r = off[i] + threadIdx.x; r < off[i + 1]; r += blockDim.x) c += cf[r] == 1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    cnt[i] = t;
+  }
+}
+
+__global__ void freeze_rows(const int* __restrict__ inst, const char* __restrict__ frozen, int n,
+                            signed char* __restrict__ cf) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n && frozen[inst[r]]) cf[r] = 1;
+}
+
+__global__ void point_to_coarse(const int* __restrict__ cpts, int nc, int* __restrict__ cidx) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nc) cidx[cpts[r]] = r;
+}
+
+// aggregate index after freezing renumbered the C-points: the old root's new coarse
+// index; frozen instances keep no aggregates
+__global__ void remap_aggregates(const int* __restrict__ inst, const char* __restrict__ frozen,
+                                 const int* __restrict__ old_cpts, const int* __restrict__ cidx,
+                                 int n, int* __restrict__ agg) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int a = agg[j];
+  agg[j] = (a < 0 || frozen[inst[j]]) ? -1 : cidx[old_cpts[a]];
+}
+
+// out[r] = weight of r's instance times dinv[r] (the weight folded into D^-1)
+template <class T>
+__global__ void instance_weights(const int* __restrict__ inst, const double* __restrict__ w,
+                                 const T* __restrict__ dinv, int n, T* __restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) out[r] = (T)w[inst[r]] * dinv[r];
+}
+
+__global__ void check_block_diagonal(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                     const int* __restrict__ inst, const int* __restrict__ off,
+                                     int n, int* __restrict__ bad) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int lo = off[inst[r]], hi = off[inst[r] + 1];
+  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e)
+    if (col[e] < lo || col[e] >= hi) {
+      atomicAdd(bad, 1);
+      return;
+    }
+}
+
+// out[i] = sum of x^2 over instance i's rows (one block of 256 per instance, fixed order)
+__global__ void instance_sumsq(const double* __restrict__ x, const int* __restrict__ off,
+                               double* __restrict__ out) {
+  __shared__ double part[8];
+  const int i = blockIdx.x;
+  double a = 0.0;
+  for (int r = off[i] + threadIdx.x; r < off[i + 1]; r += blockDim.x) a += x[r] * x[r];
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    out[i] = t;
+  }
+}
+
+// device copies of a level's instance map
+static void level_instances(Level& L, cudaStream_t s) {
+  const int ninst = (int)L.off.size() - 1;
+  int* d_off = dalloc<int>(ninst + 1, s);
+  CLAIR_CUDA(cudaMemcpyAsync(d_off, L.off.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice, s));
+  L.inst = dalloc<int>(L.n, s);
+  L.lbase = dalloc<int>(L.n, s);
+  if (L.n) {
+    row_instance<<<ceil_div(L.n, 256), 256, 0, s>>>(d_off, ninst, L.n, L.inst, L.lbase); ::clair::count_launch();
+  }
+  CLAIR_LAUNCHED();
+  dfree(d_off, s);
+}
+
+// per-instance C counts of a level (host)
+static std::vector<int> c_counts(const Level& L, const signed char* cf, cudaStream_t s) {
+  const int ninst = (int)L.off.size() - 1;
+  int* d_off = dalloc<int>(ninst + 1, s);
+  int* d_cnt = dalloc<int>(ninst, s);
+  CLAIR_CUDA(cudaMemcpyAsync(d_off, L.off.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice, s));
+  count_c_instances<<<ninst, 256, 0, s>>>(cf, d_off, d_cnt); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  std::vector<int> cnt(ninst);
+  CLAIR_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * ninst, cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  dfree(d_off, s);
+  dfree(d_cnt, s);
+  return cnt;
+}
+
+// weights folded into D^-1 for the cycle: pre = omega_i, post = 1 (or omega_i when
+// post_weighted), both 0 for a frozen instance
+static void batch_cycle_weights(Level& L, bool post_weighted, cudaStream_t s) {
+  const int ninst = (int)L.off.size() - 1;
+  std::vector<double> w(2 * ninst);
+  for (int i = 0; i < ninst; ++i) {
+    const bool fz = L.frozen[i] != 0;
+    w[i] = fz ? 0.0 : L.omega_inst[i];
+    w[ninst + i] = fz ? 0.0 : (post_weighted ? L.omega_inst[i] : 1.0);
+  }
+  double* dw = dalloc<double>(2 * ninst, s);
+  CLAIR_CUDA(cudaMemcpyAsync(dw, w.data(), sizeof(double) * 2 * ninst, cudaMemcpyHostToDevice, s));
+  L.wpre64 = dalloc<double>(L.n, s);
+  L.wpost64 = dalloc<double>(L.n, s);
+  L.wpre32 = dalloc<float>(L.n, s);
+  L.wpost32 = dalloc<float>(L.n, s);
+  const int g = ceil_div(L.n, 256);
+  if (L.n) {
+    instance_weights<double><<<g, 256, 0, s>>>(L.inst, dw, L.dinv, L.n, L.wpre64); ::clair::count_launch();
+    instance_weights<double><<<g, 256, 0, s>>>(L.inst, dw + ninst, L.dinv, L.n, L.wpost64); ::clair::count_launch();
+    instance_weights<float><<<g, 256, 0, s>>>(L.inst, dw, L.dinv32, L.n, L.wpre32); ::clair::count_launch();
+    instance_weights<float><<<g, 256, 0, s>>>(L.inst, dw + ninst, L.dinv32, L.n, L.wpost32); ::clair::count_launch();
+  }
+  CLAIR_LAUNCHED();
+  dfree(dw, s);
+}
+
 // A second stream and the fork/join events of one setup (released on scope exit).
 struct SideStream {
   cudaStream_t s2 = nullptr;
@@ -187,6 +368,8 @@ struct SideStream {
 static void setup_levels(clair_hierarchy* h, const double* B0) {
   cudaStream_t s = h->stream;
   const clair_params& p = h->p;
+  const bool batch = h->ninst > 1;
+  const int ninst = h->ninst;
   {
     Level& L0 = h->lv[0];
     L0.B_P = dalloc<double>(L0.n, s);
@@ -195,13 +378,27 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
     CLAIR_CUDA(cudaMemcpyAsync(L0.B_R, B0, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, s));
   }
   SideStream ss;
-  double* omega_dev = dalloc<double>(p.max_levels, s);  // one weight per level, on the device
+  // one weight per level (per level and instance for a batch), on the device
+  double* omega_dev = dalloc<double>((size_t)p.max_levels * ninst, s);
   for (int k = 0;; ++k) {
     Level& L = h->lv[k];
     const int n = L.n;
     L.dinv = dalloc<double>(n, s);
     inverse_diagonal(L.A, L.dinv, s);
-    if (n <= p.coarse_max || k + 1 >= p.max_levels) break;
+    if (!batch) {
+      if (n <= p.coarse_max || k + 1 >= p.max_levels) break;
+    } else {
+      // an instance at its coarsest size (or the level cap) freezes; all frozen: stop
+      level_instances(L, s);
+      if (L.frozen.empty()) L.frozen.assign(ninst, 0);
+      bool all = true;
+      for (int i = 0; i < ninst; ++i) {
+        const int ni = L.off[i + 1] - L.off[i];
+        if (ni <= p.coarse_max || k + 1 >= p.max_levels) L.frozen[i] = 1;
+        all = all && L.frozen[i];
+      }
+      if (all) break;
+    }
 
     Csr At;
     int* agg = nullptr;                           // aggregate of each point (Agg coarsening)
@@ -209,6 +406,7 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
     double* rmaxAt = dalloc<double>(n, s);
     unsigned char* sA = dalloc<unsigned char>(L.A.nnz, s);
     unsigned char* sAt = dalloc<unsigned char>(L.A.nnz, s);
+    std::vector<int> cnt;                         // C-points per instance (batch)
     {
       ClockScope clk(PH_SPLIT, s);
       csr_transpose(L.A, At, nullptr, s);
@@ -220,11 +418,44 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
       L.cf = dalloc<signed char>(n, s);
       if (p.coarsen == CLAIR_COARSEN_AGG) {
         agg = dalloc<int>(n, s);
-        aggregate(L.A, At, sA, sAt, L.cf, agg, s);
+        aggregate(L.A, At, sA, sAt, L.lbase, L.cf, agg, s);
       } else {
-        split_fc(L.A, At, sA, sAt, L.cf, s);
+        split_fc(L.A, At, sA, sAt, L.lbase, L.cf, s);
       }
       L.nc = coarse_points(L.cf, n, &L.cpts, s);
+      if (batch) {
+        // an instance whose splitting leaves no C-point or no F-point ends there
+        cnt = c_counts(L, L.cf, s);
+        bool all = true, changed = false;
+        for (int i = 0; i < ninst; ++i) {
+          const int ni = L.off[i + 1] - L.off[i];
+          if (!L.frozen[i] && (cnt[i] == 0 || cnt[i] == ni)) L.frozen[i] = 1;
+          all = all && L.frozen[i];
+          if (L.frozen[i] && cnt[i] != ni) changed = true;
+        }
+        if (all) {
+          L.nc = 0;  // this level is the batch's coarsest
+        } else if (changed) {
+          char* dfz = dalloc<char>(ninst, s);
+          CLAIR_CUDA(cudaMemcpyAsync(dfz, L.frozen.data(), ninst, cudaMemcpyHostToDevice, s));
+          freeze_rows<<<ceil_div(n, 256), 256, 0, s>>>(L.inst, dfz, n, L.cf); ::clair::count_launch();
+          CLAIR_LAUNCHED();
+          int* old_cpts = L.cpts;
+          L.cpts = nullptr;
+          L.nc = coarse_points(L.cf, n, &L.cpts, s);
+          if (agg) {
+            int* cidx = dalloc<int>(n, s);
+            point_to_coarse<<<ceil_div(L.nc, 256), 256, 0, s>>>(L.cpts, L.nc, cidx); ::clair::count_launch();
+            remap_aggregates<<<ceil_div(n, 256), 256, 0, s>>>(L.inst, dfz, old_cpts, cidx, n, agg); ::clair::count_launch();
+            CLAIR_LAUNCHED();
+            dfree(cidx, s);
+          }
+          dfree(old_cpts, s);
+          dfree(dfz, s);
+          for (int i = 0; i < ninst; ++i)
+            if (L.frozen[i]) cnt[i] = L.off[i + 1] - L.off[i];
+        }
+      }
     }
     if (L.nc == 0 || L.nc == n) {
       dfree(agg, s);
@@ -243,15 +474,30 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
     // patterns and local lAIR solves, which need neither.  Join before the projection.
     CLAIR_CUDA(cudaEventRecord(ss.fork, s));
     CLAIR_CUDA(cudaStreamWaitEvent(ss.s2, ss.fork, 0));
+    double* om_k = omega_dev + (size_t)k * ninst;
     {
       ClockScope clk(PH_WEIGHT, ss.s2);
-      arnoldi_weight(L.A, L.dinv, p.arnoldi_iters, p.seed + (uint64_t)k, omega_dev + k, ss.s2);
+      if (batch)
+        arnoldi_weight_batched(L.A, L.dinv, p.arnoldi_iters, p.seed + (uint64_t)k, L.off, om_k,
+                               ss.s2);
+      else
+        arnoldi_weight(L.A, L.dinv, p.arnoldi_iters, p.seed + (uint64_t)k, om_k, ss.s2);
     }
     {
       ClockScope clk(PH_SMOOTH, ss.s2);
       double* tmp = dalloc<double>(n, ss.s2);
-      smooth_modes(L.A, L.dinv, L.cf, omega_dev + k, p.b_smooth_iters, L.B_P, tmp, ss.s2);
-      smooth_modes(At, L.dinv, L.cf, omega_dev + k, p.b_smooth_iters, L.B_R, tmp, ss.s2);
+      if (batch) {
+        // each instance's weight folded into D^-1, unit scalar weight
+        double* wd = dalloc<double>(n, ss.s2);
+        instance_weights<double><<<ceil_div(n, 256), 256, 0, ss.s2>>>(L.inst, om_k, L.dinv, n, wd); ::clair::count_launch();
+        CLAIR_LAUNCHED();
+        smooth_modes(L.A, wd, L.cf, nullptr, p.b_smooth_iters, L.B_P, tmp, ss.s2);
+        smooth_modes(At, wd, L.cf, nullptr, p.b_smooth_iters, L.B_R, tmp, ss.s2);
+        dfree(wd, ss.s2);
+      } else {
+        smooth_modes(L.A, L.dinv, L.cf, om_k, p.b_smooth_iters, L.B_P, tmp, ss.s2);
+        smooth_modes(At, L.dinv, L.cf, om_k, p.b_smooth_iters, L.B_R, tmp, ss.s2);
+      }
       dfree(tmp, ss.s2);
     }
     CLAIR_CUDA(cudaEventRecord(ss.join, ss.s2));
@@ -302,32 +548,50 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
       inject<<<ceil_div(C.n, 256), 256, 0, s>>>(L.B_R, L.cpts, C.n, C.B_R); ::clair::count_launch();
     }
     CLAIR_LAUNCHED();
+    if (batch) {
+      C.off.assign(ninst + 1, 0);
+      for (int i = 0; i < ninst; ++i) C.off[i + 1] = C.off[i] + cnt[i];
+      C.frozen = L.frozen;
+    }
     h->lv.push_back(C);
   }
   {
-    std::vector<double> om(p.max_levels, 1.0);
-    CLAIR_CUDA(cudaMemcpyAsync(om.data(), omega_dev, sizeof(double) * p.max_levels,
+    std::vector<double> om((size_t)p.max_levels * ninst, 1.0);
+    CLAIR_CUDA(cudaMemcpyAsync(om.data(), omega_dev, sizeof(double) * om.size(),
                                cudaMemcpyDeviceToHost, s));
     CLAIR_CUDA(cudaStreamSynchronize(s));
-    for (size_t k = 0; k < h->lv.size(); ++k)
-      if (h->lv[k].nc) h->lv[k].omega = om[k];
+    for (size_t k = 0; k < h->lv.size(); ++k) {
+      Level& L = h->lv[k];
+      if (!L.nc) continue;
+      L.omega = om[k * ninst];
+      if (batch) L.omega_inst.assign(om.begin() + k * ninst, om.begin() + (k + 1) * ninst);
+    }
   }
   dfree(omega_dev, s);
   // coarsest level: dense inverse; float copies and work vectors everywhere
   ClockScope clk(PH_COARSE, s);
   Level& last = h->lv.back();
   h->nL = last.n;
-  CLAIR_REQUIRE(h->nL <= 1024, CLAIR_ERR_CAPACITY,
-                "coarsest level has %d unknowns (> 1024): raise max_levels", h->nL);
-  h->Inv = dalloc<double>((size_t)h->nL * h->nL, s);
-  dense_inverse(last.A, h->Inv, s);
-  to_float_copy(h->Inv, &h->Inv32, (long long)h->nL * h->nL, s);
+  // coarsest level: one dense block, or each instance's diagonal block of a batch
+  std::vector<int> blocks = batch ? last.off : std::vector<int>{0, last.n};
+  long long inv_size = 0;
+  for (size_t i = 0; i + 1 < blocks.size(); ++i) {
+    const long long ni = blocks[i + 1] - blocks[i];
+    CLAIR_REQUIRE(ni <= 1024, CLAIR_ERR_CAPACITY,
+                  "coarsest level has a block of %lld unknowns (> 1024): raise max_levels", ni);
+    inv_size += ni * ni;
+  }
+  h->coarse_nblk = (int)blocks.size() - 1;
+  h->Inv = dalloc<double>(std::max<long long>(inv_size, 1), s);
+  dense_inverse(last.A, blocks, h->Inv, &h->coarse_off, &h->coarse_ioff, s);
+  to_float_copy(h->Inv, &h->Inv32, std::max<long long>(inv_size, 1), s);
   for (auto& L : h->lv) {
     to_float_copy(L.A.val, &L.A.val32, L.A.nnz, s);
     to_float_copy(L.dinv, &L.dinv32, L.n, s);
     if (L.nc) {
       to_float_copy(L.R.val, &L.R.val32, L.R.nnz, s);
       to_float_copy(L.P.val, &L.P.val32, L.P.nnz, s);
+      if (batch) batch_cycle_weights(L, p.post_weighted != 0, s);
     }
     alloc_cycle(L, s);
   }
@@ -342,6 +606,8 @@ struct Vec {
   static T* r(Level& L);
   static const T* aval(const Csr& M);
   static const T* dinv(const Level& L);
+  static const T* wpre(const Level& L);
+  static const T* wpost(const Level& L);
 };
 template <>
 struct Vec<double> {
@@ -351,6 +617,8 @@ struct Vec<double> {
   static double* r(Level& L) { return L.r64; }
   static const double* aval(const Csr& M) { return M.val; }
   static const double* dinv(const Level& L) { return L.dinv; }
+  static const double* wpre(const Level& L) { return L.wpre64; }
+  static const double* wpost(const Level& L) { return L.wpost64; }
 };
 template <>
 struct Vec<float> {
@@ -360,6 +628,8 @@ struct Vec<float> {
   static float* r(Level& L) { return L.r32; }
   static const float* aval(const Csr& M) { return M.val32; }
   static const float* dinv(const Level& L) { return L.dinv32; }
+  static const float* wpre(const Level& L) { return L.wpre32; }
+  static const float* wpost(const Level& L) { return L.wpost32; }
 };
 
 template <class T>
@@ -397,13 +667,16 @@ static void vcycle_level(clair_hierarchy* h, int k) {
       Inv = reinterpret_cast<const T*>(h->Inv);
     else
       Inv = reinterpret_cast<const T*>(h->Inv32);
-    coarse_apply<T>(Inv, L.n, b, x, s);
+    coarse_apply<T>(Inv, h->coarse_off, h->coarse_ioff, h->coarse_nblk, L.n, b, x, s);
     return;
   }
   const T* av = Vec<T>::aval(L.A);
-  const T* dv = Vec<T>::dinv(L);
-  const T w = (T)L.omega;
-  const T wpost = h->p.post_weighted ? w : T(1);
+  // a batch folds each instance's weight into D^-1 (0 for frozen instances)
+  const bool batch = h->ninst > 1;
+  const T* dv = batch ? Vec<T>::wpre(L) : Vec<T>::dinv(L);
+  const T* dvpost = batch ? Vec<T>::wpost(L) : Vec<T>::dinv(L);
+  const T w = batch ? T(1) : (T)L.omega;
+  const T wpost = batch ? T(1) : (h->p.post_weighted ? w : T(1));
   // CFF pre-smoothing from x = 0
   jacobi_from_zero<T>(L.n, dv, L.cf, 1, w, b, x, s);
   jacobi<T>(L.A, av, dv, L.cf, 0, w, b, x, y, s);
@@ -416,9 +689,9 @@ static void vcycle_level(clair_hierarchy* h, int k) {
   vcycle_level<T>(h, k + 1);
   spmv_t<T>(L.P, Vec<T>::x(C), x, T(1), T(1), s);
   // FFC post-smoothing
-  jacobi<T>(L.A, av, dv, L.cf, 0, wpost, b, x, y, s);
-  jacobi<T>(L.A, av, dv, L.cf, 0, wpost, b, y, x, s);
-  jacobi<T>(L.A, av, dv, L.cf, 1, wpost, b, x, y, s);
+  jacobi<T>(L.A, av, dvpost, L.cf, 0, wpost, b, x, y, s);
+  jacobi<T>(L.A, av, dvpost, L.cf, 0, wpost, b, y, x, s);
+  jacobi<T>(L.A, av, dvpost, L.cf, 1, wpost, b, x, y, s);
   CLAIR_CUDA(cudaMemcpyAsync(x, y, sizeof(T) * L.n, cudaMemcpyDeviceToDevice, s));
 }
 
@@ -567,6 +840,28 @@ static double read_scalar(clair_hierarchy* h, const double* dev) {
   return h->kr.host[0];
 }
 
+// ||x_i|| for every instance of a batch (host)
+static std::vector<double> instance_norms(clair_hierarchy* h, const double* x) {
+  cudaStream_t s = h->stream;
+  const std::vector<int>& off = h->lv[0].off;
+  const int ninst = (int)off.size() - 1;
+  int* d_off = dalloc<int>(ninst + 1, s);
+  double* d_out = dalloc<double>(ninst, s);
+  CLAIR_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice, s));
+  instance_sumsq<<<ninst, 256, 0, s>>>(x, d_off, d_out); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  std::vector<double> out(ninst);
+  CLAIR_CUDA(cudaMemcpyAsync(out.data(), d_out, sizeof(double) * ninst, cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  dfree(d_off, s);
+  dfree(d_out, s);
+  for (double& v : out) v = sqrt(v);
+  return out;
+}
+
+// A batch is solved as one block-diagonal system: the absolute tolerance is rtol times the
+// smallest instance right-hand-side norm, so every instance's residual (bounded by the
+// global one) is within rtol of its own ||f_i||.
 static clair_status fgmres(clair_hierarchy* h, const double* f, double* u, int* iters_out,
                            double* relres_out) {
   cudaStream_t s = h->stream;
@@ -583,7 +878,15 @@ static clair_status fgmres(clair_hierarchy* h, const double* f, double* u, int* 
     if (relres_out) *relres_out = 0.0;
     return CLAIR_OK;
   }
-  const double tol = h->p.rtol * fnorm;
+  double tol = h->p.rtol * fnorm;
+  std::vector<double> fi;
+  if (h->ninst > 1) {
+    fi = instance_norms(h, f);
+    double fmin = fnorm;
+    for (double v : fi)
+      if (v > 0.0) fmin = std::min(fmin, v);
+    tol = h->p.rtol * fmin;
+  }
   residual(L0.A, f, u, k.r, s);
   multi_dot(k.r, 1, k.r, n, k.scal + 1, k.partial, s);
   double beta = sqrt(read_scalar(h, k.scal + 1));
@@ -624,8 +927,15 @@ static clair_status fgmres(clair_hierarchy* h, const double* f, double* u, int* 
     beta = sqrt(read_scalar(h, k.scal + 1));
     CLAIR_REQUIRE(isfinite(beta), CLAIR_ERR_NONFINITE, "nonfinite residual");
   }
+  double rel = beta / fnorm;
+  if (h->ninst > 1) {  // the worst instance
+    const std::vector<double> ri = instance_norms(h, k.r);
+    rel = 0.0;
+    for (size_t i = 0; i < ri.size(); ++i)
+      rel = std::max(rel, fi[i] > 0.0 ? ri[i] / fi[i] : ri[i]);
+  }
   if (iters_out) *iters_out = its;
-  if (relres_out) *relres_out = beta / fnorm;
+  if (relres_out) *relres_out = rel;
   return beta <= tol ? CLAIR_OK : CLAIR_ERR_NOT_CONVERGED;
 }
 
@@ -662,8 +972,10 @@ clair_status clair_params_default(clair_params* p) {
 
 const char* clair_last_error(void) { return last_error(); }
 
-clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, const double* val,
-                         const double* B, const clair_params* pin, void* stream, clair_h* out) {
+static clair_status setup_common(int ninst, const int* offsets_host, int n, int nnz,
+                                 const int* rowptr, const int* col, const double* val,
+                                 const double* B, const clair_params* pin, void* stream,
+                                 clair_h* out) {
   if (out) *out = nullptr;
   CLAIR_API_BEGIN
   CLAIR_REQUIRE(out && rowptr && col && val && B, CLAIR_ERR_ARG, "clair_setup: null pointer");
@@ -687,8 +999,21 @@ clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, cons
                 "unknown coarsening type %d", p.coarsen);
   CLAIR_REQUIRE(p.b_smooth_iters >= 0 && p.gmres_maxit >= 1 && p.rtol > 0.0, CLAIR_ERR_ARG,
                 "bad iteration counts or rtol");
+  std::vector<int> off{0, n};
+  if (ninst > 1) {
+    CLAIR_REQUIRE(offsets_host, CLAIR_ERR_ARG, "clair_setup_batched: null offsets");
+    off.assign(offsets_host, offsets_host + ninst + 1);
+    CLAIR_REQUIRE(off[0] == 0 && off[ninst] == n, CLAIR_ERR_ARG,
+                  "clair_setup_batched: offsets must run from 0 to n");
+    for (int i = 0; i < ninst; ++i)
+      CLAIR_REQUIRE(off[i + 1] > off[i], CLAIR_ERR_ARG,
+                    "clair_setup_batched: instance %d is empty or offsets decrease", i);
+    CLAIR_REQUIRE(p.arnoldi_iters <= 15, CLAIR_ERR_UNSUPPORTED,
+                  "clair_setup_batched: arnoldi_iters must be <= 15");
+  }
   clair_hierarchy* h = new clair_hierarchy();
   h->p = p;
+  h->ninst = std::max(ninst, 1);
   h->stream = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   try {
@@ -698,6 +1023,7 @@ clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, cons
     CLAIR_CUDA(cudaEventRecord(e0, s));
     Level L0;
     L0.n = n;
+    if (h->ninst > 1) L0.off = off;
     L0.A.rows = L0.A.cols = n;
     L0.A.nnz = nnz;
     L0.A.rowptr = dalloc<int>(n + 1, s);
@@ -708,6 +1034,27 @@ clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, cons
     CLAIR_CUDA(cudaMemcpyAsync(L0.A.col, col, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, s));
     CLAIR_CUDA(cudaMemcpyAsync(L0.A.val, val, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
     validate_csr(rowptr, col, n, n, nnz, "A", s);
+    if (h->ninst > 1) {  // no entry may couple two instances
+      int* d_off = dalloc<int>(h->ninst + 1, s);
+      int* inst = dalloc<int>(n, s);
+      int* base = dalloc<int>(n, s);
+      int* bad = dalloc<int>(1, s);
+      CLAIR_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (h->ninst + 1),
+                                 cudaMemcpyHostToDevice, s));
+      CLAIR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+      row_instance<<<ceil_div(n, 256), 256, 0, s>>>(d_off, h->ninst, n, inst, base); ::clair::count_launch();
+      check_block_diagonal<<<ceil_div(n, 256), 256, 0, s>>>(rowptr, col, inst, d_off, n, bad); ::clair::count_launch();
+      CLAIR_LAUNCHED();
+      int hb = 0;
+      CLAIR_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CLAIR_CUDA(cudaStreamSynchronize(s));
+      dfree(d_off, s);
+      dfree(inst, s);
+      dfree(base, s);
+      dfree(bad, s);
+      CLAIR_REQUIRE(hb == 0, CLAIR_ERR_ARG,
+                    "clair_setup_batched: %d rows couple two instances (not block-diagonal)", hb);
+    }
     CLAIR_REQUIRE(all_finite(val, nnz, s), CLAIR_ERR_NONFINITE, "A has nonfinite values");
     CLAIR_REQUIRE(all_finite(B, n, s), CLAIR_ERR_NONFINITE, "B has nonfinite values");
     h->B0 = dalloc<double>(n, s);
@@ -739,6 +1086,43 @@ clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, cons
   CLAIR_API_END
 }
 
+clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, const double* val,
+                         const double* B, const clair_params* p, void* stream, clair_h* out) {
+  return setup_common(1, nullptr, n, nnz, rowptr, col, val, B, p, stream, out);
+}
+
+clair_status clair_setup_batched(int ninst, const int* offsets_host, int n, int nnz,
+                                 const int* rowptr, const int* col, const double* val,
+                                 const double* B, const clair_params* p, void* stream,
+                                 clair_h* out) {
+  if (out) *out = nullptr;
+  if (ninst < 1) {
+    set_error("clair_setup_batched: ninst must be >= 1");
+    return CLAIR_ERR_ARG;
+  }
+  return setup_common(ninst, offsets_host, n, nnz, rowptr, col, val, B, p, stream, out);
+}
+
+clair_status clair_batch_view(clair_h h, int level, int* ninst, int* offsets_host,
+                              double* omega_host, signed char* frozen_host) {
+  CLAIR_API_BEGIN
+  CLAIR_REQUIRE(h && ninst, CLAIR_ERR_ARG, "clair_batch_view: null pointer");
+  CLAIR_REQUIRE(level >= 0 && level < (int)h->lv.size(), CLAIR_ERR_ARG, "bad level %d", level);
+  const Level& L = h->lv[level];
+  *ninst = h->ninst;
+  for (int i = 0; i < h->ninst; ++i) {
+    if (offsets_host) {
+      offsets_host[i] = h->ninst > 1 ? L.off[i] : 0;
+      offsets_host[i + 1] = h->ninst > 1 ? L.off[i + 1] : L.n;
+    }
+    if (omega_host)
+      omega_host[i] = (h->ninst > 1 && !L.omega_inst.empty()) ? L.omega_inst[i] : L.omega;
+    if (frozen_host)
+      frozen_host[i] = (h->ninst > 1 && !L.frozen.empty()) ? L.frozen[i] : (L.nc ? 0 : 1);
+  }
+  CLAIR_API_END
+}
+
 clair_status clair_setup_adjoint(clair_h fwd, void* stream, clair_h* adj) {
   if (adj) *adj = nullptr;
   CLAIR_API_BEGIN
@@ -749,7 +1133,8 @@ clair_status clair_setup_adjoint(clair_h fwd, void* stream, clair_h* adj) {
   csr_transpose(A, At, nullptr, s);
   clair_status st;
   try {
-    st = clair_setup(A.rows, A.nnz, At.rowptr, At.col, At.val, fwd->B0, &fwd->p, stream, adj);
+    st = setup_common(fwd->ninst, fwd->ninst > 1 ? fwd->lv[0].off.data() : nullptr, A.rows, A.nnz,
+                      At.rowptr, At.col, At.val, fwd->B0, &fwd->p, stream, adj);
   } catch (...) {
     At.release(s);
     throw;

@@ -54,13 +54,14 @@ void strength(const Csr& M, const double* thr, double theta, int mode, unsigned 
 enum : signed char { ST_U = 0, ST_C = 1, ST_F = 2 };
 
 __global__ void pmis_init(const int* __restrict__ Atrp, const unsigned char* __restrict__ sAt,
-                          int n, unsigned long long* __restrict__ key,
+                          int n, const int* __restrict__ lbase, unsigned long long* __restrict__ key,
                           signed char* __restrict__ state, int* __restrict__ mark) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   unsigned lam = 0;
   for (int e = Atrp[i]; e < Atrp[i + 1]; ++e) lam += sAt[e];
-  key[i] = ((unsigned long long)lam << 32) | lowbias32((uint32_t)i);
+  // the hash takes the index within the point's instance (a batch is block-diagonal)
+  key[i] = ((unsigned long long)lam << 32) | lowbias32((uint32_t)(i - (lbase ? lbase[i] : 0)));
   state[i] = lam == 0 ? ST_F : ST_U;
   mark[i] = -1;
 }
@@ -132,7 +133,7 @@ __global__ void pmis_finish(int n, const int* __restrict__ mark, const signed ch
 }
 
 void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsigned char* sAt,
-              signed char* cf, cudaStream_t s) {
+              const int* lbase, signed char* cf, cudaStream_t s) {
   const int n = A.rows;
   if (!n) return;
   unsigned long long* key = dalloc<unsigned long long>(n, s);
@@ -140,7 +141,7 @@ void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsign
   int* mark = dalloc<int>(n, s);
   int* remaining = dalloc<int>(1, s);
   const int g = ceil_div(n, 256);
-  pmis_init<<<g, 256, 0, s>>>(At.rowptr, sAt, n, key, state, mark); ::clair::count_launch();
+  pmis_init<<<g, 256, 0, s>>>(At.rowptr, sAt, n, lbase, key, state, mark); ::clair::count_launch();
   CLAIR_LAUNCHED();
   for (int round = 0;; ++round) {
     CLAIR_REQUIRE(round < 10000, CLAIR_ERR_CAPACITY, "C/F splitting did not terminate");
@@ -184,16 +185,16 @@ struct GraphG {
   const unsigned char* sAt;
 };
 
-__global__ void agg_init(GraphG g, int n, unsigned long long* __restrict__ key,
-                         signed char* __restrict__ und, signed char* __restrict__ iso,
-                         signed char* __restrict__ root) {
+__global__ void agg_init(GraphG g, int n, const int* __restrict__ lbase,
+                         unsigned long long* __restrict__ key, signed char* __restrict__ und,
+                         signed char* __restrict__ iso, signed char* __restrict__ root) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   unsigned lam = 0;
   for (int e = g.Atrp[i]; e < g.Atrp[i + 1]; ++e) lam += g.sAt[e];
   bool has = lam > 0;
   for (int e = g.Arp[i]; e < g.Arp[i + 1] && !has; ++e) has = g.sA[e] != 0;
-  key[i] = ((unsigned long long)lam << 32) | lowbias32((uint32_t)i);
+  key[i] = ((unsigned long long)lam << 32) | lowbias32((uint32_t)(i - (lbase ? lbase[i] : 0)));
   und[i] = has ? 1 : 0;
   iso[i] = has ? 0 : 1;
   root[i] = 0;
@@ -319,7 +320,7 @@ __global__ void agg_to_cf(int n, const signed char* __restrict__ root, signed ch
 }
 
 void aggregate(const Csr& A, const Csr& At, const unsigned char* sA, const unsigned char* sAt,
-               signed char* cf, int* agg, cudaStream_t s) {
+               const int* lbase, signed char* cf, int* agg, cudaStream_t s) {
   const int n = A.rows;
   if (!n) return;
   const GraphG g{A.rowptr, A.col, sA, At.rowptr, At.col, sAt};
@@ -332,7 +333,7 @@ void aggregate(const Csr& A, const Csr& At, const unsigned char* sA, const unsig
   signed char* near1 = dalloc<signed char>(n, s);
   int* remaining = dalloc<int>(2, s);
   const int gr = ceil_div(n, 256);
-  agg_init<<<gr, 256, 0, s>>>(g, n, key, und, iso, root); ::clair::count_launch();
+  agg_init<<<gr, 256, 0, s>>>(g, n, lbase, key, und, iso, root); ::clair::count_launch();
   CLAIR_LAUNCHED();
   for (int round = 0;; ++round) {
     CLAIR_REQUIRE(round < 10000, CLAIR_ERR_CAPACITY, "aggregation did not terminate");
@@ -869,6 +870,241 @@ static void arnoldi_fused_steps(const Csr& A, const double* dinv, int m, double*
   }
 }
 
+// ---- segmented Arnoldi: one independent run per instance of a block-diagonal batch ----
+// Block b of every launch owns rows [lo[b], hi[b]) of instance inst[b]; an instance's
+// blocks are consecutive (first bfirst[i], count bcount[i]) and its finalize adds their
+// partial sums in block order, so every instance's weight is deterministic and equals a
+// run on that instance alone up to the summation order.  The start vector of instance i
+// is draw (row - off[i]) of the stream seeded with `seed`, as in a run on the instance.
+struct SegBlocks {
+  const int* lo;
+  const int* hi;
+  const int* inst;
+};
+constexpr int SEG_HS = AR_MAXV + 1;  // per-instance stride of h1 / h2
+
+__global__ void seg_start(double* __restrict__ v, SegBlocks sb, const int* __restrict__ off,
+                          uint64_t seed, double* __restrict__ partial) {
+  const int b = blockIdx.x;
+  const int lo = sb.lo[b], hi = sb.hi[b], base = off[sb.inst[b]];
+  double acc[1] = {0.0};
+  for (int i = lo + threadIdx.x; i < hi; i += AR_THREADS) {
+    const double x = splitmix_pm1(seed, (uint64_t)(i - base));
+    v[i] = x;
+    acc[0] += x * x;
+  }
+  block_reduce_to_partial<1>(acc, 1, partial);
+}
+
+template <int W>
+__global__ void __launch_bounds__(AR_THREADS)
+seg_k1(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ av,
+       const double* __restrict__ dinv, int n, double* __restrict__ V, int j,
+       const double* __restrict__ wprev, const double* __restrict__ sc, int use_scale,
+       double* __restrict__ w, double* __restrict__ partial, SegBlocks sb) {
+  constexpr int GPW = 32 / W;
+  const int b = blockIdx.x;
+  const int lo = sb.lo[b], hi = sb.hi[b];
+  const double scl = use_scale ? sc[2 * sb.inst[b] + 1] : 1.0;
+  double acc[AR_MAXV + 2];
+#pragma unroll
+  for (int v = 0; v < AR_MAXV + 2; ++v) acc[v] = 0.0;
+  const int lane = threadIdx.x & 31, sub = lane % W, grp = lane / W;
+  const int warp = threadIdx.x >> 5;
+  for (int base = lo + warp * GPW; base < hi; base += (AR_THREADS / 32) * GPW) {  // warp-uniform
+    const int i = base + grp;
+    double s = 0.0;
+    if (i < hi)
+      for (int e = rp[i] + sub; e < rp[i + 1]; e += W) s += av[e] * wprev[ci[e]];
+    s = group_sum<W>(s);
+    if (sub == 0 && i < hi) {
+      const double wi = dinv[i] * (scl * s);
+      const double vj = wprev[i] * scl;
+      w[i] = wi;
+      if (j > 0) V[(long long)j * n + i] = vj;
+#pragma unroll
+      for (int k = 0; k < AR_MAXV; ++k)
+        if (k <= j) acc[k] += (k < j ? V[(long long)k * n + i] : vj) * wi;
+      acc[AR_MAXV + 1] += wi * wi;
+    }
+  }
+  block_reduce_to_partial<AR_MAXV + 2>(acc, AR_MAXV + 2, partial);
+}
+
+template <bool DOTS>
+__global__ void __launch_bounds__(AR_THREADS)
+seg_cgs(const double* __restrict__ V, int j, int n, const double* __restrict__ h,
+        double* __restrict__ w, double* __restrict__ partial, SegBlocks sb) {
+  const int b = blockIdx.x;
+  const int lo = sb.lo[b], hi = sb.hi[b];
+  const double* hi_ = h + (long long)SEG_HS * sb.inst[b];
+  double acc[AR_MAXV + 1];
+#pragma unroll
+  for (int v = 0; v < AR_MAXV + 1; ++v) acc[v] = 0.0;
+  double hk[AR_MAXV];
+#pragma unroll
+  for (int k = 0; k < AR_MAXV; ++k) hk[k] = k <= j ? hi_[k] : 0.0;
+  for (int i = lo + threadIdx.x; i < hi; i += AR_THREADS) {
+    double vk[AR_MAXV];
+    double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < AR_MAXV; ++k) {
+      vk[k] = k <= j ? V[(long long)k * n + i] : 0.0;
+      if (k <= j) wi = fma(-hk[k], vk[k], wi);
+    }
+    w[i] = wi;
+    if (DOTS) {
+#pragma unroll
+      for (int k = 0; k < AR_MAXV; ++k)
+        if (k <= j) acc[k] += vk[k] * wi;
+    } else {
+      acc[0] += wi * wi;
+    }
+  }
+  block_reduce_to_partial<AR_MAXV + 1>(acc, DOTS ? j + 1 : 1, partial);
+}
+
+// One block per instance: adds its blocks' partials in block order.  mode 0: h1, ||w||^2
+// before orthogonalisation; 1: h2; 2: H column, breakdown test, next scale; 3: scale of
+// the start vector (1/||v_0||), stored as the next scale.
+__global__ void __launch_bounds__(512)
+seg_finalize(const double* __restrict__ partial, int nb, int nv, int mode, int j,
+             const int* __restrict__ bfirst, const int* __restrict__ bcount,
+             double* __restrict__ h1, double* __restrict__ h2, double* __restrict__ sc,
+             double* __restrict__ H, int ldh, int m, int* __restrict__ steps) {
+  __shared__ double out[AR_MAXV + 2];
+  const int inst = blockIdx.x;
+  const int b0 = bfirst[inst], b1 = b0 + bcount[inst];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int v = wid; v < nv; v += 16) {
+    double t = 0.0;
+    for (int b = b0 + lane; b < b1; b += 32) t += partial[(long long)v * nb + b];
+    t = warp_sum(t);
+    if (lane == 0) out[v] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double* h1i = h1 + (long long)SEG_HS * inst;
+  double* h2i = h2 + (long long)SEG_HS * inst;
+  double* sci = sc + 2 * inst;
+  double* Hi = H + (long long)inst * ldh * m;
+  if (mode == 0) {
+    for (int k = 0; k <= j; ++k) h1i[k] = out[k];
+    sci[0] = out[AR_MAXV + 1];
+  } else if (mode == 1) {
+    for (int k = 0; k <= j; ++k) h2i[k] = out[k];
+  } else if (mode == 2) {
+    const bool active = steps[inst] < 0;
+    for (int i = 0; i <= j; ++i) Hi[i + (long long)j * ldh] = active ? h1i[i] + h2i[i] : 0.0;
+    const double hn = sqrt(out[0]);
+    Hi[j + 1 + (long long)j * ldh] = active ? hn : 0.0;
+    if (active && hn <= 1e-10 * sqrt(sci[0])) steps[inst] = j + 1;
+    sci[1] = (active && hn > 0.0) ? 1.0 / hn : 0.0;
+  } else {
+    sci[1] = out[0] > 0.0 ? 1.0 / sqrt(out[0]) : 0.0;
+  }
+}
+
+__global__ void seg_scale_start(double* __restrict__ v, SegBlocks sb, const double* __restrict__ sc) {
+  const int b = blockIdx.x;
+  const double f = sc[2 * sb.inst[b] + 1];
+  for (int i = sb.lo[b] + threadIdx.x; i < sb.hi[b]; i += blockDim.x) v[i] *= f;
+}
+
+__global__ void __launch_bounds__(32) seg_ritz(const double* __restrict__ H, int ldh, int m,
+                                               const int* __restrict__ steps,
+                                               double* __restrict__ omega) {
+  __shared__ double Hs[AR_MAXV * AR_MAXV];
+  const int inst = blockIdx.x, lane = threadIdx.x;
+  const double* Hi = H + (long long)inst * ldh * m;
+  const int k = steps[inst] < 0 ? m : steps[inst];
+  for (int idx = lane; idx < k * k; idx += 32) Hs[idx] = Hi[(idx % k) + (long long)(idx / k) * ldh];
+  __syncwarp();
+  const double rho = hessenberg_spectral_radius_lanes(Hs, k, k, lane, 32, WarpSync{});
+  if (lane == 0) omega[inst] = rho > 0.0 ? 1.0 / rho : 1.0;
+}
+
+// Enqueues omega_i = 1 / rho(D_i^-1 A_i) for every diagonal block i of A (rows off[i] ..
+// off[i+1]-1, host offsets) into omega_dev[i].  iters <= 15.
+void arnoldi_weight_batched(const Csr& A, const double* dinv, int iters, uint64_t seed,
+                            const std::vector<int>& off, double* omega_dev, cudaStream_t s) {
+  const int n = A.rows;
+  const int ninst = (int)off.size() - 1;
+  const int m = std::max(1, std::min(iters, AR_MAXV));
+  const int ldh = m + 1;
+  // blocks per instance in proportion to its rows (at least one)
+  const int target = partial_blocks();
+  std::vector<int> lo, hi, inst, bfirst(ninst), bcount(ninst);
+  for (int i = 0; i < ninst; ++i) {
+    const int ni = off[i + 1] - off[i];
+    const int nb = std::max(1, std::min(ceil_div(ni, AR_THREADS),
+                                        (int)((long long)target * ni / std::max(n, 1))));
+    bfirst[i] = (int)lo.size();
+    bcount[i] = nb;
+    for (int b = 0; b < nb; ++b) {
+      lo.push_back(off[i] + (int)((long long)ni * b / nb));
+      hi.push_back(off[i] + (int)((long long)ni * (b + 1) / nb));
+      inst.push_back(i);
+    }
+  }
+  const int nb = (int)lo.size();
+  std::vector<int> pack;
+  for (const std::vector<int>* v : {(const std::vector<int>*)&lo, (const std::vector<int>*)&hi,
+                                    (const std::vector<int>*)&inst, (const std::vector<int>*)&bfirst,
+                                    (const std::vector<int>*)&bcount, &off})
+    pack.insert(pack.end(), v->begin(), v->end());
+  int* dpack = dalloc<int>(pack.size(), s);
+  CLAIR_CUDA(cudaMemcpyAsync(dpack, pack.data(), sizeof(int) * pack.size(), cudaMemcpyHostToDevice, s));
+  const SegBlocks sb{dpack, dpack + nb, dpack + 2 * nb};
+  const int* d_bfirst = dpack + 3 * nb;
+  const int* d_bcount = d_bfirst + ninst;
+  const int* d_off = d_bcount + ninst;
+  double* V = dalloc<double>((size_t)(m + 1) * n, s);
+  double* w0 = dalloc<double>(n, s);
+  double* w1 = dalloc<double>(n, s);
+  double* H = dalloc<double>((size_t)ninst * ldh * m, s);
+  double* h1 = dalloc<double>((size_t)ninst * SEG_HS, s);
+  double* h2 = dalloc<double>((size_t)ninst * SEG_HS, s);
+  double* sc = dalloc<double>((size_t)ninst * 2, s);
+  int* steps = dalloc<int>(ninst, s);
+  double* partial = dalloc<double>((size_t)nb * (AR_MAXV + 2), s);
+  CLAIR_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * ninst * ldh * m, s));
+  CLAIR_CUDA(cudaMemsetAsync(steps, 0xff, sizeof(int) * ninst, s));  // -1: no breakdown
+  seg_start<<<nb, AR_THREADS, 0, s>>>(V, sb, d_off, seed, partial); ::clair::count_launch();
+  seg_finalize<<<ninst, 512, 0, s>>>(partial, nb, 1, 3, 0, d_bfirst, d_bcount, h1, h2, sc, H, ldh,
+                                     m, steps); ::clair::count_launch();
+  seg_scale_start<<<nb, AR_THREADS, 0, s>>>(V, sb, sc); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  double* const wbuf[2] = {w0, w1};
+  for (int j = 0; j < m; ++j) {
+    double* w = wbuf[j & 1];
+    const double* wprev = j == 0 ? V : wbuf[(j + 1) & 1];
+    seg_k1<1><<<nb, AR_THREADS, 0, s>>>(A.rowptr, A.col, A.val, dinv, n, V, j, wprev, sc, j > 0, w,
+                                        partial, sb); ::clair::count_launch();
+    seg_finalize<<<ninst, 512, 0, s>>>(partial, nb, AR_MAXV + 2, 0, j, d_bfirst, d_bcount, h1, h2,
+                                       sc, H, ldh, m, steps); ::clair::count_launch();
+    seg_cgs<true><<<nb, AR_THREADS, 0, s>>>(V, j, n, h1, w, partial, sb); ::clair::count_launch();
+    seg_finalize<<<ninst, 512, 0, s>>>(partial, nb, j + 1, 1, j, d_bfirst, d_bcount, h1, h2, sc, H,
+                                       ldh, m, steps); ::clair::count_launch();
+    seg_cgs<false><<<nb, AR_THREADS, 0, s>>>(V, j, n, h2, w, partial, sb); ::clair::count_launch();
+    seg_finalize<<<ninst, 512, 0, s>>>(partial, nb, 1, 2, j, d_bfirst, d_bcount, h1, h2, sc, H, ldh,
+                                       m, steps); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+  }
+  seg_ritz<<<ninst, 32, 0, s>>>(H, ldh, m, steps, omega_dev); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  dfree(V, s);
+  dfree(w0, s);
+  dfree(w1, s);
+  dfree(H, s);
+  dfree(h1, s);
+  dfree(h2, s);
+  dfree(sc, s);
+  dfree(partial, s);
+  dfree(steps, s);
+  dfree(dpack, s);
+}
+
 // Enqueues omega = 1 / rho(D^-1 A) into the device scalar *omega_dev (no host sync).
 double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed,
                       double* omega_dev, cudaStream_t s) {
@@ -933,79 +1169,105 @@ double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed
 // Coarsest level: dense inverse by Gauss-Jordan elimination with partial pivoting (one
 // block; n <= a few hundred).  M is n x n column-major in global memory, overwritten.
 // ------------------------------------------------------------------------------------
-__global__ void csr_to_dense(const int* __restrict__ rowptr, const int* __restrict__ col,
-                             const double* __restrict__ val, int n, double* __restrict__ M) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  for (int c = 0; c < n; ++c) M[r + (long long)c * n] = 0.0;
-  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) M[r + (long long)col[e] * n] = val[e];
+// Dense inverses of the diagonal blocks of the coarsest operator: block i holds rows and
+// columns off[i] .. off[i+1]-1 (one block when the hierarchy is not a batch) and is stored
+// column-major at Inv + ioff[i], ioff[i] = sum_{j<i} n_j^2.  One CUDA block per diagonal
+// block: Gauss-Jordan with partial pivoting.
+__global__ void csr_to_dense_blocks(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                    const double* __restrict__ val, const int* __restrict__ off,
+                                    const long long* __restrict__ ioff, double* __restrict__ M) {
+  const int i = blockIdx.x;
+  const int r0 = off[i], nb = off[i + 1] - r0;
+  double* Mi = M + ioff[i];
+  for (long long idx = threadIdx.x; idx < (long long)nb * nb; idx += blockDim.x) Mi[idx] = 0.0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < nb; r += blockDim.x)
+    for (int e = rowptr[r0 + r]; e < rowptr[r0 + r + 1]; ++e)
+      Mi[r + (long long)(col[e] - r0) * nb] = val[e];
 }
 
-__global__ void gauss_jordan(double* __restrict__ M, double* __restrict__ Inv, int n,
-                             int* __restrict__ singular) {
+__global__ void gauss_jordan_blocks(double* __restrict__ M, double* __restrict__ Inv,
+                                    const int* __restrict__ off, const long long* __restrict__ ioff,
+                                    int* __restrict__ singular) {
   // Inv starts as identity; row operations on [M | Inv].
   __shared__ int s_piv;
   __shared__ double s_pv;
+  const int blk = blockIdx.x;
+  const int n = off[blk + 1] - off[blk];
+  double* Mb = M + ioff[blk];
+  double* Ib = Inv + ioff[blk];
   const int t = threadIdx.x, nt = blockDim.x;
-  for (int idx = t; idx < n * n; idx += nt) Inv[idx] = (idx % n == idx / n) ? 1.0 : 0.0;
+  for (int idx = t; idx < n * n; idx += nt) Ib[idx] = (idx % n == idx / n) ? 1.0 : 0.0;
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     if (t == 0) {
       int p = k;
-      double best = fabs(M[k + (long long)k * n]);
+      double best = fabs(Mb[k + (long long)k * n]);
       for (int r = k + 1; r < n; ++r) {
-        const double v = fabs(M[r + (long long)k * n]);
+        const double v = fabs(Mb[r + (long long)k * n]);
         if (v > best) {
           best = v;
           p = r;
         }
       }
       s_piv = p;
-      s_pv = M[p + (long long)k * n];
+      s_pv = Mb[p + (long long)k * n];
       if (best == 0.0) *singular = 1;
     }
     __syncthreads();
     const int p = s_piv;
     if (p != k)
       for (int c = t; c < n; c += nt) {
-        double a = M[k + (long long)c * n];
-        M[k + (long long)c * n] = M[p + (long long)c * n];
-        M[p + (long long)c * n] = a;
-        double b = Inv[k + (long long)c * n];
-        Inv[k + (long long)c * n] = Inv[p + (long long)c * n];
-        Inv[p + (long long)c * n] = b;
+        double a = Mb[k + (long long)c * n];
+        Mb[k + (long long)c * n] = Mb[p + (long long)c * n];
+        Mb[p + (long long)c * n] = a;
+        double b = Ib[k + (long long)c * n];
+        Ib[k + (long long)c * n] = Ib[p + (long long)c * n];
+        Ib[p + (long long)c * n] = b;
       }
     __syncthreads();
     const double pv = s_pv;
     for (int c = t; c < n; c += nt) {
       if (pv != 0.0) {
-        M[k + (long long)c * n] /= pv;
-        Inv[k + (long long)c * n] /= pv;
+        Mb[k + (long long)c * n] /= pv;
+        Ib[k + (long long)c * n] /= pv;
       }
     }
     __syncthreads();
     // eliminate column k from every other row (rows split over threads)
     for (int r = t; r < n; r += nt) {
       if (r == k) continue;
-      const double f = M[r + (long long)k * n];
+      const double f = Mb[r + (long long)k * n];
       if (f == 0.0) continue;
       for (int c = 0; c < n; ++c) {
-        M[r + (long long)c * n] -= f * M[k + (long long)c * n];
-        Inv[r + (long long)c * n] -= f * Inv[k + (long long)c * n];
+        Mb[r + (long long)c * n] -= f * Mb[k + (long long)c * n];
+        Ib[r + (long long)c * n] -= f * Ib[k + (long long)c * n];
       }
     }
     __syncthreads();
   }
 }
 
-void dense_inverse(const Csr& A, double* Inv, cudaStream_t s) {
-  const int n = A.rows;
-  double* M = dalloc<double>((size_t)n * n, s);
+// d_off / d_ioff receive device copies of the block offsets (caller frees them).
+void dense_inverse(const Csr& A, const std::vector<int>& off, double* Inv, int** d_off,
+                   long long** d_ioff, cudaStream_t s) {
+  const int nblk = (int)off.size() - 1;
+  std::vector<long long> ioff(nblk + 1, 0);
+  for (int i = 0; i < nblk; ++i) {
+    const long long ni = off[i + 1] - off[i];
+    ioff[i + 1] = ioff[i] + ni * ni;
+  }
+  *d_off = dalloc<int>(nblk + 1, s);
+  *d_ioff = dalloc<long long>(nblk + 1, s);
+  CLAIR_CUDA(cudaMemcpyAsync(*d_off, off.data(), sizeof(int) * (nblk + 1), cudaMemcpyHostToDevice, s));
+  CLAIR_CUDA(cudaMemcpyAsync(*d_ioff, ioff.data(), sizeof(long long) * (nblk + 1),
+                             cudaMemcpyHostToDevice, s));
+  double* M = dalloc<double>(std::max<long long>(ioff[nblk], 1), s);
   int* sing = dalloc<int>(1, s);
   CLAIR_CUDA(cudaMemsetAsync(sing, 0, sizeof(int), s));
-  if (n) {
-    csr_to_dense<<<ceil_div(n, 128), 128, 0, s>>>(A.rowptr, A.col, A.val, n, M); ::clair::count_launch();
-    gauss_jordan<<<1, 256, 0, s>>>(M, Inv, n, sing); ::clair::count_launch();
+  if (A.rows) {
+    csr_to_dense_blocks<<<nblk, 256, 0, s>>>(A.rowptr, A.col, A.val, *d_off, *d_ioff, M); ::clair::count_launch();
+    gauss_jordan_blocks<<<nblk, 256, 0, s>>>(M, Inv, *d_off, *d_ioff, sing); ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
   int h = 0;
@@ -1016,24 +1278,34 @@ void dense_inverse(const Csr& A, double* Inv, cudaStream_t s) {
   CLAIR_REQUIRE(h == 0, CLAIR_ERR_SINGULAR_BLOCK, "coarsest operator is singular");
 }
 
-// x = Inv b for a dense n x n column-major Inv (one block).
+// x = Inv b blockwise (row r of block i: sum over the block's columns).
 template <class T>
-__global__ void dense_gemv(const T* __restrict__ Inv, int n, const T* __restrict__ b,
-                           T* __restrict__ x) {
+__global__ void dense_gemv_blocks(const T* __restrict__ Inv, const int* __restrict__ off,
+                                  const long long* __restrict__ ioff, int nblk, int n,
+                                  const T* __restrict__ b, T* __restrict__ x) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    int lo = 0, hi = nblk;  // block holding row r: largest i with off[i] <= r
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (off[mid] <= r) lo = mid; else hi = mid;
+    }
+    const int r0 = off[lo], nb = off[lo + 1] - r0;
+    const T* Ib = Inv + ioff[lo];
     T acc = 0;
-    for (int c = 0; c < n; ++c) acc += Inv[r + (long long)c * n] * b[c];
+    for (int c = 0; c < nb; ++c) acc += Ib[(r - r0) + (long long)c * nb] * b[r0 + c];
     x[r] = acc;
   }
 }
-
 template <class T>
-void coarse_apply(const T* Inv, int n, const T* b, T* x, cudaStream_t s) {
+void coarse_apply(const T* Inv, const int* d_off, const long long* d_ioff, int nblk, int n,
+                  const T* b, T* x, cudaStream_t s) {
   if (!n) return;
-  dense_gemv<T><<<ceil_div(n, 128), 128, 0, s>>>(Inv, n, b, x); ::clair::count_launch();
+  dense_gemv_blocks<T><<<ceil_div(n, 128), 128, 0, s>>>(Inv, d_off, d_ioff, nblk, n, b, x); ::clair::count_launch();
   CLAIR_LAUNCHED();
 }
-template void coarse_apply<double>(const double*, int, const double*, double*, cudaStream_t);
-template void coarse_apply<float>(const float*, int, const float*, float*, cudaStream_t);
+template void coarse_apply<double>(const double*, const int*, const long long*, int, int,
+                                   const double*, double*, cudaStream_t);
+template void coarse_apply<float>(const float*, const int*, const long long*, int, int,
+                                  const float*, float*, cudaStream_t);
 
 }  // namespace clair

@@ -252,6 +252,25 @@ def config4(count: int = 64, seed: int = 3, max_side: int | None = None) -> list
     return probs
 
 
+def block_diagonal(mats) -> tuple[CSR, np.ndarray]:
+    """Stacks square CSR operators into one block-diagonal CSR; returns it and the row
+    offsets of the blocks (length len(mats) + 1)."""
+    offs = np.zeros(len(mats) + 1, dtype=np.int64)
+    for i, M in enumerate(mats):
+        offs[i + 1] = offs[i] + M.n
+    rowptr = [np.zeros(1, dtype=np.int64)]
+    cols, vals = [], []
+    base_nnz = 0
+    for i, M in enumerate(mats):
+        rowptr.append(M.rowptr[1:].astype(np.int64) + base_nnz)
+        cols.append(M.col.astype(np.int64) + offs[i])
+        vals.append(M.val)
+        base_nnz += M.nnz
+    A = CSR(int(offs[-1]), np.concatenate(rowptr).astype(np.int32),
+            np.concatenate(cols).astype(np.int32), np.concatenate(vals))
+    return A, offs
+
+
 def config5_fields(nside: int = 512, seed: int = 4):
     """Per-node eps = 10^(-3 + N(0, 0.5)) and velocity from psi = sin(pi x) sin(pi y)."""
     n = nside * nside
