@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-nside", type=int, default=128)
+    ap.add_argument("--workload", choices=["advdiff1024", "batch64", "adjoint512", "recirc3d"],
+                    default="advdiff1024",
+                    help="advdiff1024: the headline line (default).  The others time the "
+                         "many-instance batch (64 instances, sides 64-512), the adjoint "
+                         "gradient (512^2 variable eps, 8 RHS) and the 128^3 recirculating "
+                         "aggregation setup, each on its own JSON line")
     return ap.parse_args()
 
 
@@ -376,10 +382,189 @@ def run_reference(args):
     }), flush=True)
 
 
+# ----------------------------------------------------------------------------------------
+# Other workloads (one JSON line each; not the headline)
+# ----------------------------------------------------------------------------------------
+def _events_ms(fn, steps, warmup, flush):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    times, out = [], None
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.mean(times), times, out
+
+
+def _line(metric, value, unit, hib, ms, times, args, workload, extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": hib, "scaling": "weak",
+         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+         "config": dict(workload, l2="flushed (256 MiB write) before each step")}
+    d.update(extra)
+    d["step_times_ms"] = times
+    print(json.dumps(d), flush=True)
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2307_00229_gb300 import clair as cl
+    cl.load()
+    probs = workloads.config4()
+    A, offs = workloads.block_diagonal([pr.A for pr in probs])
+    f = np.concatenate([pr.f for pr in probs])
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    rowptr, col, val = t(A.rowptr, torch.int32), t(A.col, torch.int32), t(A.val, torch.float64)
+    B, fd = t(np.ones(A.n), torch.float64), t(f, torch.float64)
+    u = torch.zeros_like(fd)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    res = {}
+    for name, prec, steps in (("mixed", cl.CLAIR_MIXED, args.steps), ("fp64", cl.CLAIR_FP64, max(1, args.fp64_steps))):
+        p = cl.clair_params_default()
+        p.precision = prec
+
+        def step():
+            h = cl.clair_setup_batched(offs.tolist(), rowptr, col, val, B, p)
+            u.zero_()
+            st, its, rel = cl.clair_solve(h, fd, u, raise_not_converged=False)
+            s_ = cl.clair_stats(h)
+            cl.clair_free(h)
+            return st, its, rel, s_
+        l0 = cl.clair_kernel_launches()
+        ms, times, (st, its, rel, sts) = _events_ms(step, steps, args.warmup, flush)
+        res[name] = {"ms": ms, "times": times, "its": its, "rel": rel, "status": st,
+                     "setup_ms": sts.setup_ms, "rows": int(sts.r_rows), "levels": sts.levels,
+                     "launches": (cl.clair_kernel_launches() - l0) // (steps + args.warmup),
+                     "phases_ms": {n_: sts.phase_ms[i] for i, n_ in enumerate(cl.PHASES[:8])},
+                     "solve_phases_ms": {n_: sts.solve_phase_ms[i] for i, n_ in enumerate(cl.PHASES) if i >= 8}}
+    # the same instances one after another (setup + solve each), for comparison
+    p = cl.clair_params_default()
+    p.precision = cl.CLAIR_MIXED
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    seq_rows = 0
+    for i, pr in enumerate(probs):
+        lo, hi = int(offs[i]), int(offs[i + 1])
+        h = cl.clair_setup(t(pr.A.rowptr, torch.int32), t(pr.A.col, torch.int32),
+                           t(pr.A.val, torch.float64), B[lo:hi].contiguous(), p)
+        ui = torch.zeros(hi - lo, dtype=torch.float64, device="cuda")
+        cl.clair_solve(h, fd[lo:hi].contiguous(), ui, raise_not_converged=False)
+        seq_rows += int(cl.clair_stats(h).r_rows)
+        cl.clair_free(h)
+    e1.record()
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    m = res["mixed"]
+    _line("R rows/s in setup; time-to-1e-8 rel residual of all instances (one batched setup + solve)",
+          m["rows"] / (m["ms"] / 1e3), "R rows/s", True, m["ms"], m["times"], args,
+          {"workload": "batch64_advdiff2d", "instances": len(probs), "n_total": A.n, "nnz_total": A.nnz,
+           "sides": [pr.meta["nside"] for pr in probs], "coarsen": "FC", "degree": 2,
+           "precision": "mixed (FP32 local solves and V-cycle, FP64 FGMRES)"},
+          {"iterations": m["its"], "worst_instance_relres": m["rel"], "status": m["status"],
+           "setup_ms": m["setup_ms"], "r_rows": m["rows"], "levels": m["levels"],
+           "phases_ms": m["phases_ms"], "solve_phases_ms": m["solve_phases_ms"],
+           "gpu_launches": m["launches"],
+           "fp64": {k: res["fp64"][k] for k in ("ms", "its", "rel", "setup_ms", "status")},
+           "sequential_instances_ms": seq_ms, "sequential_r_rows": seq_rows})
+
+
+def run_adjoint(args):
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2307_00229_gb300 import clair as cl
+    cl.load()
+    prob = workloads.config5()
+    A, m = prob.A, prob.meta
+    nside = m["nside"]
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    rowptr, col, val0 = t(A.rowptr, torch.int32), t(A.col, torch.int32), t(A.val, torch.float64)
+    F0, T = t(prob.f, torch.float64), t(m["u_target"], torch.float64)
+    eps, vx, vy = t(m["eps_field"], torch.float64), t(m["vx"], torch.float64), t(m["vy"], torch.float64)
+    B = t(np.ones(A.n), torch.float64)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, prec in (("mixed", cl.CLAIR_MIXED), ("fp64", cl.CLAIR_FP64)):
+        p = cl.clair_params_default()
+        p.precision = prec
+
+        def step():
+            val = val0.clone().requires_grad_(True)
+            U = cl.ClairSolve.apply(val, F0, rowptr, col, B, p)
+            loss = ((U - T) ** 2).sum()
+            loss.backward()
+            return cl.clair_advdiff2d_param_grad(nside, 1.0 / (nside + 1), eps, vx, vy, rowptr, col, val.grad)
+        ms, times, g = _events_ms(step, args.steps if name == "mixed" else max(1, args.fp64_steps),
+                                  args.warmup, flush)
+        out[name] = {"ms": ms, "times": times}
+    _line("adjoint gradient time: forward setup + 8 solves, adjoint setup + 8 solves, "
+          "sampled outer product, field chain rule", out["mixed"]["ms"], "ms", False,
+          out["mixed"]["ms"], out["mixed"]["times"], args,
+          {"workload": f"varcoef2d_{nside}_8rhs", "n": A.n, "nnz": A.nnz, "nrhs": 8,
+           "precision": "mixed (FP32 local solves and V-cycle, FP64 FGMRES)"},
+          {"fp64": out["fp64"]})
+
+
+def run_recirc3d(args):
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2307_00229_gb300 import clair as cl
+    cl.load()
+    prob = workloads.config3()
+    A = prob.A
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    args_ = (t(A.rowptr, torch.int32), t(A.col, torch.int32), t(A.val, torch.float64),
+             t(prob.B, torch.float64))
+    f = t(prob.f, torch.float64)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    p = cl.clair_params_default()
+    p.precision = cl.CLAIR_MIXED
+    p.coarsen = cl.CLAIR_COARSEN_AGG
+
+    def setup_only():
+        h = cl.clair_setup(*args_, p)
+        s_ = cl.clair_stats(h)
+        cl.clair_free(h)
+        return s_
+    ms, times, sts = _events_ms(setup_only, args.steps, args.warmup, flush)
+    h = cl.clair_setup(*args_, p)
+    u = torch.zeros_like(f)
+    st, its, rel = cl.clair_solve(h, f, u, raise_not_converged=False)
+    cl.clair_free(h)
+    _line("R rows/s in setup (aggregation coarsening)", int(sts.r_rows) / (ms / 1e3), "R rows/s", True,
+          ms, times, args, {"workload": "recirc3d_128", "n": A.n, "nnz": A.nnz, "coarsen": "AGG",
+                            "degree": 2, "eps": 1e-3, "precision": "mixed"},
+          {"r_rows": int(sts.r_rows), "levels": sts.levels, "operator_complexity": sts.operator_complexity,
+           "phases_ms": {n_: sts.phase_ms[i] for i, n_ in enumerate(cl.PHASES[:8])},
+           "solve": {"status": st, "iterations": its, "relres": rel,
+                     "note": "the paper's aggregation variant did not converge at alpha <= 1e-3 either"}})
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
+    elif args.workload == "adjoint512":
+        run_adjoint(args)
+    elif args.workload == "recirc3d":
+        run_recirc3d(args)
     else:
         run_clair(args)
 

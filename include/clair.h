@@ -93,6 +93,9 @@ typedef struct {
   double lsolve_flops;        /* sum over local systems of (2/3) T^3 + 2 T^2 */
   double lsolve_min_bytes;    /* 12 nnz(A_k) per side (A read once) + 12 nnz(R_k) + 12 nnz(P_k) */
   int64_t lsolve_gathered;    /* A entries read by the local gathers, repeats included */
+  int64_t fp64_cycle_from;    /* last clair_solve in CLAIR_MIXED: iteration from which the
+                                 FP64 cycle took over (a restart cycle ended unconverged or
+                                 produced a nonfinite estimate), -1 if it never did */
 } clair_stats_t;
 
 /* Kernel launches issued by this library in this process so far (monotonic counter). */
@@ -117,6 +120,10 @@ clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col,
 /* Solve A u = f (hot path, part 2): right-preconditioned FGMRES(gmres_restart) in float64
  * with one V(1,1) cycle (CFF pre, FFC post, Section 4) per iteration, FP32 cycle in
  * CLAIR_MIXED mode.  Stops on the true float64 residual (restart = iterative refinement).
+ * In CLAIR_MIXED mode a restart cycle that uses all gmres_restart iterations without
+ * converging, or a nonfinite residual estimate, switches the rest of the solve to the
+ * FP64 cycle of the same hierarchy (flexible GMRES admits the change; see
+ * clair_stats_t.fp64_cycle_from).
  *   f     : device float64 [n]
  *   u     : device float64 [n]; input initial guess, output solution
  *   iters, relres : host outputs (iterations done, final ||f - A u|| / ||f||); may be NULL

@@ -75,6 +75,7 @@ class clair_stats_t(ctypes.Structure):
         ("lsolve_flops", ctypes.c_double),
         ("lsolve_min_bytes", ctypes.c_double),
         ("lsolve_gathered", ctypes.c_int64),
+        ("fp64_cycle_from", ctypes.c_int64),
     ]
 
 

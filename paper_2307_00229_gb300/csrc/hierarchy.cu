@@ -108,6 +108,8 @@ struct clair_hierarchy {
   int* coarse_off = nullptr;                // coarsest diagonal blocks (device offsets)
   long long* coarse_ioff = nullptr;         // and their inverses' offsets in Inv
   int coarse_nblk = 1;
+  bool cycle_fp64 = false;                  // MIXED solve fell back to the FP64 cycle
+  int fp64_from = -1;                       // iteration of that fallback (-1: none)
 };
 
 namespace clair {
@@ -699,7 +701,7 @@ static void vcycle_level(clair_hierarchy* h, int k) {
 static void apply_precond_direct(clair_hierarchy* h, int k, const double* v, double* z) {
   cudaStream_t s = h->stream;
   Level& L = h->lv[k];
-  if (h->p.precision == CLAIR_MIXED) {
+  if (h->p.precision == CLAIR_MIXED && !h->cycle_fp64) {
     to_float(v, L.b32, L.n, s);
     vcycle_level<float>(h, k);
     to_double(L.x32, z, L.n, s);
@@ -741,7 +743,7 @@ static void build_cycle_graph(clair_hierarchy* h) {
 
 // z = M^-1 v on level k; the fine level replays the captured cycle.
 static void apply_precond(clair_hierarchy* h, int k, const double* v, double* z) {
-  if (k != 0 || !h->cycle_exec) {
+  if (k != 0 || !h->cycle_exec || h->cycle_fp64) {
     apply_precond_direct(h, k, v, z);
     return;
   }
@@ -891,11 +893,24 @@ static clair_status fgmres(clair_hierarchy* h, const double* f, double* u, int* 
   multi_dot(k.r, 1, k.r, n, k.scal + 1, k.partial, s);
   double beta = sqrt(read_scalar(h, k.scal + 1));
   CLAIR_REQUIRE(isfinite(beta), CLAIR_ERR_NONFINITE, "nonfinite initial residual");
+  // MIXED: the FP32 cycle carries ~7 digits; where the hierarchy's weights span more than
+  // that (near-pure advection after mode smoothing) it stops reducing the residual.  A
+  // restart cycle that ends unconverged, or a nonfinite estimate (that cycle is
+  // discarded), switches the rest of the solve to the FP64 cycle on the same hierarchy.
+  h->cycle_fp64 = false;
+  h->fp64_from = -1;
+  const bool mixed = h->p.precision == CLAIR_MIXED;
+  // a MIXED cycle that gains less than 2x in the residual estimate over 10 iterations has
+  // stalled: its directions are kept (it is still a valid flexible preconditioner) and
+  // the following cycles use FP64
+  constexpr int kStallWindow = 10;
+  std::vector<double> est_hist;
   while (beta > tol && its < h->p.gmres_maxit) {
     gmres_start<<<1, 32, 0, s>>>(k.g, m, k.scal, k.scal + 3); ::clair::count_launch();
     scale_into<<<grid, 256, 0, s>>>(k.r, k.V, n, k.scal + 3); ::clair::count_launch();
     CLAIR_LAUNCHED();
     int jend = 0;
+    bool discarded = false, stalled = false;
     for (int j = 0; j < m; ++j) {
       double* vj = k.V + (size_t)j * n;
       double* zj = k.Z + (size_t)j * n;
@@ -916,16 +931,35 @@ static clair_status fgmres(clair_hierarchy* h, const double* f, double* u, int* 
       ++its;
       jend = j + 1;
       const double est = read_scalar(h, k.scal + 4);
+      if (!isfinite(est) && mixed && !h->cycle_fp64) {
+        jend = 0;  // discard this cycle's directions
+        discarded = true;
+        break;
+      }
       CLAIR_REQUIRE(isfinite(est), CLAIR_ERR_NONFINITE, "nonfinite residual estimate");
       if (est <= tol || its >= h->p.gmres_maxit) break;
+      est_hist.push_back(est);
+      if (mixed && !h->cycle_fp64 && j + 1 >= kStallWindow &&
+          est > 0.5 * est_hist[est_hist.size() - kStallWindow]) {
+        stalled = true;
+        break;
+      }
     }
-    gmres_backsolve<<<1, 32, 0, s>>>(k.H, m + 1, jend, k.g, k.y); ::clair::count_launch();
-    CLAIR_LAUNCHED();
-    multi_axpy(k.Z, jend, k.y, u, n, s);
+    if (jend > 0) {
+      gmres_backsolve<<<1, 32, 0, s>>>(k.H, m + 1, jend, k.g, k.y); ::clair::count_launch();
+      CLAIR_LAUNCHED();
+      multi_axpy(k.Z, jend, k.y, u, n, s);
+    }
     residual(L0.A, f, u, k.r, s);
     multi_dot(k.r, 1, k.r, n, k.scal + 1, k.partial, s);
     beta = sqrt(read_scalar(h, k.scal + 1));
     CLAIR_REQUIRE(isfinite(beta), CLAIR_ERR_NONFINITE, "nonfinite residual");
+    // (a cycle that stopped on its estimate but not on the true residual is iterative
+    // refinement, and stays in FP32)
+    if (beta > tol && mixed && !h->cycle_fp64 && (discarded || stalled || jend == m)) {
+      h->cycle_fp64 = true;
+      h->fp64_from = its;
+    }
   }
   double rel = beta / fnorm;
   if (h->ninst > 1) {  // the worst instance
@@ -1218,6 +1252,7 @@ clair_status clair_stats(clair_h h, clair_stats_t* o) {
     if (L.nc) minb += 2.0 * 12.0 * L.A.nnz + 12.0 * (double)L.R.nnz + 12.0 * (double)L.P.nnz;
   o->lsolve_min_bytes = minb;
   o->lsolve_gathered = h->st.gathered;
+  o->fp64_cycle_from = h->fp64_from;
   CLAIR_API_END
 }
 

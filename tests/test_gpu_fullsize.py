@@ -165,14 +165,16 @@ def test_bench_workload_level0_matches_oracle(cl, bench_oracle, precision):
 # the smoothed mode vector toward zero by about (1 - omega)^5 per level (the inflow
 # boundary holds u = 0), so coarse-level B spans ~20 decades and the projected weights
 # reach ~1e13 (oracle, 256^2, eps 0: min B 1e-21 on level 5).  An FP32 V-cycle cannot
-# carry that range and FP64 convergence degrades; those runs are held to the invariants
-# only.  With B = 1 unsmoothed the same hierarchies converge in both precisions.
+# carry that range: MIXED solves there switch to the FP64 cycle when the FP32 cycle
+# stalls (clair_stats_t.fp64_cycle_from), and FP64 itself does not reach 1e-8 within
+# gmres_maxit for eps = 0, m = 2.  With B = 1 unsmoothed the same hierarchies converge in
+# both precisions.
 VARIANTS = [
     (1e-2, 1, 5, (0, 1)),
     (1.0, 2, 5, (0, 1)),
-    (1e-4, 2, 5, (0,)),
-    (0.0, 1, 5, (0,)),
-    (0.0, 2, 5, ()),
+    (1e-4, 2, 5, (0, 1)),
+    (0.0, 1, 5, (0, 1)),
+    (0.0, 2, 5, (1,)),
     (0.0, 2, 0, (0, 1)),
     (0.0, 1, 0, (0, 1)),
 ]
@@ -183,7 +185,7 @@ def test_full_size_properties(cl, eps, degree, sweeps, converge):
     import torch
     prob = workloads.config2(eps=eps, degree=degree)
     A = O.csr_of(prob.A)
-    its = {}
+    its, fell_back = {}, {}
     for precision in (0, 1):
         h = setup_gpu(cl, prob, precision, degree, sweeps)
         try:
@@ -196,6 +198,7 @@ def test_full_size_properties(cl, eps, degree, sweeps, converge):
                 uh = u.cpu().numpy()
                 assert np.linalg.norm(prob.f - A @ uh) <= 1e-8 * np.linalg.norm(prob.f)
                 its[precision] = it
+                fell_back[precision] = cl.clair_stats(h).fp64_cycle_from >= 0
         finally:
             cl.clair_free(h)
         cf = g["cf"].astype(bool)
@@ -213,5 +216,5 @@ def test_full_size_properties(cl, eps, degree, sweeps, converge):
         has = np.diff(S.indptr) > 0
         dep_c = (S @ cf.astype(np.float64)) > 0
         assert not np.any(~cf & has & ~dep_c)
-    if len(its) == 2:
+    if len(its) == 2 and not fell_back[1]:
         assert abs(its[0] - its[1]) <= 1, its
