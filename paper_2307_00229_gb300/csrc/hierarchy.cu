@@ -35,10 +35,14 @@ void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const doub
 template <class T>
 void jacobi_from_zero(int rows, const T* dinv, const signed char* cf, int which, T omega,
                       const T* b, T* x, cudaStream_t s);
+struct RitzHost;
+RitzHost* ritz_host_alloc(int ninst);
+void ritz_host_free(RitzHost* r);
 double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed,
-                      double* omega_dev, cudaStream_t s);
+                      double* omega_dev, RitzHost* rh, cudaStream_t s);
 void arnoldi_weight_batched(const Csr& A, const double* dinv, int iters, uint64_t seed,
-                            const std::vector<int>& off, double* omega_dev, cudaStream_t s);
+                            const std::vector<int>& off, double* omega_dev, RitzHost* rh,
+                            cudaStream_t s);
 void dense_inverse(const Csr& A, const std::vector<int>& off, double* Inv, int** d_off,
                    long long** d_ioff, cudaStream_t s);
 template <class T>
@@ -352,15 +356,17 @@ static void batch_cycle_weights(Level& L, bool post_weighted, cudaStream_t s) {
 // A second stream and the fork/join events of one setup (released on scope exit).
 struct SideStream {
   cudaStream_t s2 = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t fork = nullptr, split = nullptr, join = nullptr;
   SideStream() {
     CLAIR_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
     CLAIR_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CLAIR_CUDA(cudaEventCreateWithFlags(&split, cudaEventDisableTiming));
     CLAIR_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
   }
   ~SideStream() {
     if (s2) cudaStreamSynchronize(s2);
     if (fork) cudaEventDestroy(fork);
+    if (split) cudaEventDestroy(split);
     if (join) cudaEventDestroy(join);
     if (s2) cudaStreamDestroy(s2);
   }
@@ -379,6 +385,16 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
     CLAIR_CUDA(cudaMemcpyAsync(L0.B_P, B0, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, s));
     CLAIR_CUDA(cudaMemcpyAsync(L0.B_R, B0, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, s));
   }
+  // pinned buffers of the host Ritz steps; declared before the side stream so that the
+  // stream (whose destructor waits for it) is gone before they are released
+  struct RitzList {
+    std::vector<RitzHost*> v;
+    void push_back(RitzHost* r) { v.push_back(r); }
+    RitzHost* back() { return v.back(); }
+    ~RitzList() {
+      for (RitzHost* r : v) ritz_host_free(r);
+    }
+  } ritz;
   SideStream ss;
   // one weight per level (per level and instance for a batch), on the device
   double* omega_dev = dalloc<double>((size_t)p.max_levels * ninst, s);
@@ -400,6 +416,24 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
         all = all && L.frozen[i];
       }
       if (all) break;
+    }
+    // Fork.  Stream s2: relaxation weight (Arnoldi on D^-1 A needs neither the splitting
+    // nor A^T, so it starts now), then, once the splitting is known, the mode vectors
+    // smoothed with zero right-hand side (A for P, A^T for R), the weight read on the
+    // device.  Stream s: splitting, patterns and local lAIR solves.  Join before the
+    // projection.
+    CLAIR_CUDA(cudaEventRecord(ss.fork, s));
+    CLAIR_CUDA(cudaStreamWaitEvent(ss.s2, ss.fork, 0));
+    double* om_k = omega_dev + (size_t)k * ninst;
+    {
+      ClockScope clk(PH_WEIGHT, ss.s2);
+      ritz.push_back(ritz_host_alloc(ninst));
+      if (batch)
+        arnoldi_weight_batched(L.A, L.dinv, p.arnoldi_iters, p.seed + (uint64_t)k, L.off, om_k,
+                               ritz.back(), ss.s2);
+      else
+        arnoldi_weight(L.A, L.dinv, p.arnoldi_iters, p.seed + (uint64_t)k, om_k, ritz.back(),
+                       ss.s2);
     }
 
     Csr At;
@@ -471,20 +505,8 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
       dfree(sAt, s);
       break;
     }
-    // Fork.  Stream s2: relaxation weight (Arnoldi), then the mode vectors smoothed with
-    // zero right-hand side (A for P, A^T for R), the weight read on the device.  Stream s:
-    // patterns and local lAIR solves, which need neither.  Join before the projection.
-    CLAIR_CUDA(cudaEventRecord(ss.fork, s));
-    CLAIR_CUDA(cudaStreamWaitEvent(ss.s2, ss.fork, 0));
-    double* om_k = omega_dev + (size_t)k * ninst;
-    {
-      ClockScope clk(PH_WEIGHT, ss.s2);
-      if (batch)
-        arnoldi_weight_batched(L.A, L.dinv, p.arnoldi_iters, p.seed + (uint64_t)k, L.off, om_k,
-                               ss.s2);
-      else
-        arnoldi_weight(L.A, L.dinv, p.arnoldi_iters, p.seed + (uint64_t)k, om_k, ss.s2);
-    }
+    CLAIR_CUDA(cudaEventRecord(ss.split, s));
+    CLAIR_CUDA(cudaStreamWaitEvent(ss.s2, ss.split, 0));
     {
       ClockScope clk(PH_SMOOTH, ss.s2);
       double* tmp = dalloc<double>(n, ss.s2);
@@ -557,6 +579,10 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
     }
     h->lv.push_back(C);
   }
+  // the last level's weight chain may still run on s2 (a level that turned out to be the
+  // coarsest after its splitting)
+  CLAIR_CUDA(cudaEventRecord(ss.join, ss.s2));
+  CLAIR_CUDA(cudaStreamWaitEvent(s, ss.join, 0));
   {
     std::vector<double> om((size_t)p.max_levels * ninst, 1.0);
     CLAIR_CUDA(cudaMemcpyAsync(om.data(), omega_dev, sizeof(double) * om.size(),

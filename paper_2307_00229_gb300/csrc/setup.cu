@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <new>
 #include <vector>
 
 #include "common.cuh"
@@ -870,6 +871,66 @@ static void arnoldi_fused_steps(const Csr& A, const double* dinv, int m, double*
   }
 }
 
+// ---- Ritz values on the host --------------------------------------------------------
+// The 15 x 15 Hessenberg QR is a chain of dependent FP64 operations (about 0.5 ms on one
+// warp at 64-cycle FP64 latency, tens of microseconds on a host core).  The Hessenberg
+// matrices are copied to pinned host memory, a stream callback computes the weights and
+// the next copy puts them back on the device, all in stream order.
+struct RitzHost {
+  int ldh = 0, m = 0, ninst = 0;
+  double* H = nullptr;      // ninst x ldh x m, pinned
+  int* steps = nullptr;     // ninst, pinned
+  double* omega = nullptr;  // ninst, pinned
+};
+
+static void CUDART_CB ritz_on_host(void* data) {
+  RitzHost* r = static_cast<RitzHost*>(data);
+  double Hs[AR_MAXV * AR_MAXV];
+  for (int i = 0; i < r->ninst; ++i) {
+    const double* Hi = r->H + (size_t)i * r->ldh * r->m;
+    const int k = r->steps[i] < 0 ? r->m : r->steps[i];
+    for (int c = 0; c < k; ++c)
+      for (int q = 0; q < k; ++q) Hs[q + c * k] = Hi[q + (size_t)c * r->ldh];
+    const double rho = hessenberg_spectral_radius(Hs, k, k);
+    r->omega[i] = rho > 0.0 ? 1.0 / rho : 1.0;
+  }
+}
+
+// Pinned buffers for one Arnoldi run's Ritz step (released by the caller after the
+// stream has passed the run).
+RitzHost* ritz_host_alloc(int ninst) {
+  RitzHost* r = nullptr;
+  CLAIR_CUDA(cudaHostAlloc(&r, sizeof(RitzHost), cudaHostAllocDefault));
+  new (r) RitzHost();
+  r->ninst = ninst;
+  const int ldh = AR_MAXV + 1;
+  CLAIR_CUDA(cudaHostAlloc(&r->H, sizeof(double) * ninst * ldh * AR_MAXV, cudaHostAllocDefault));
+  CLAIR_CUDA(cudaHostAlloc(&r->steps, sizeof(int) * ninst, cudaHostAllocDefault));
+  CLAIR_CUDA(cudaHostAlloc(&r->omega, sizeof(double) * ninst, cudaHostAllocDefault));
+  return r;
+}
+
+void ritz_host_free(RitzHost* r) {
+  if (!r) return;
+  cudaFreeHost(r->H);
+  cudaFreeHost(r->steps);
+  cudaFreeHost(r->omega);
+  cudaFreeHost(r);
+}
+
+// Enqueues: H, steps -> host; the callback; weights -> omega_dev.
+static void ritz_via_host(const double* H, int ldh, int m, const int* steps, int ninst,
+                          double* omega_dev, RitzHost* r, cudaStream_t s) {
+  CLAIR_REQUIRE(m <= AR_MAXV && r && r->ninst >= ninst, CLAIR_ERR_ARG, "host Ritz step misuse");
+  r->ldh = ldh;
+  r->m = m;
+  r->ninst = ninst;
+  CLAIR_CUDA(cudaMemcpyAsync(r->H, H, sizeof(double) * ninst * ldh * m, cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaMemcpyAsync(r->steps, steps, sizeof(int) * ninst, cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaLaunchHostFunc(s, ritz_on_host, r));
+  CLAIR_CUDA(cudaMemcpyAsync(omega_dev, r->omega, sizeof(double) * ninst, cudaMemcpyHostToDevice, s));
+}
+
 // ---- segmented Arnoldi: one independent run per instance of a block-diagonal batch ----
 // Block b of every launch owns rows [lo[b], hi[b]) of instance inst[b]; an instance's
 // blocks are consecutive (first bfirst[i], count bcount[i]) and its finalize adds their
@@ -1027,7 +1088,8 @@ __global__ void __launch_bounds__(32) seg_ritz(const double* __restrict__ H, int
 // Enqueues omega_i = 1 / rho(D_i^-1 A_i) for every diagonal block i of A (rows off[i] ..
 // off[i+1]-1, host offsets) into omega_dev[i].  iters <= 15.
 void arnoldi_weight_batched(const Csr& A, const double* dinv, int iters, uint64_t seed,
-                            const std::vector<int>& off, double* omega_dev, cudaStream_t s) {
+                            const std::vector<int>& off, double* omega_dev, RitzHost* rh,
+                            cudaStream_t s) {
   const int n = A.rows;
   const int ninst = (int)off.size() - 1;
   const int m = std::max(1, std::min(iters, AR_MAXV));
@@ -1091,8 +1153,12 @@ void arnoldi_weight_batched(const Csr& A, const double* dinv, int iters, uint64_
                                        m, steps); ::clair::count_launch();
     CLAIR_LAUNCHED();
   }
-  seg_ritz<<<ninst, 32, 0, s>>>(H, ldh, m, steps, omega_dev); ::clair::count_launch();
-  CLAIR_LAUNCHED();
+  if (rh) {
+    ritz_via_host(H, ldh, m, steps, ninst, omega_dev, rh, s);
+  } else {
+    seg_ritz<<<ninst, 32, 0, s>>>(H, ldh, m, steps, omega_dev); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+  }
   dfree(V, s);
   dfree(w0, s);
   dfree(w1, s);
@@ -1107,7 +1173,7 @@ void arnoldi_weight_batched(const Csr& A, const double* dinv, int iters, uint64_
 
 // Enqueues omega = 1 / rho(D^-1 A) into the device scalar *omega_dev (no host sync).
 double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed,
-                      double* omega_dev, cudaStream_t s) {
+                      double* omega_dev, RitzHost* rh, cudaStream_t s) {
   const int n = A.rows;
   const int m = std::max(1, std::min(iters, n));
   const int ldh = m + 1;
@@ -1154,8 +1220,12 @@ double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed
     scale_vec<<<grid, 256, 0, s>>>(w, V + (size_t)(j + 1) * n, n, inv); ::clair::count_launch();
     CLAIR_LAUNCHED();
   }
-  ritz_kernel<<<1, 32, 0, s>>>(H, ldh, m, steps, omega_dev); ::clair::count_launch();
-  CLAIR_LAUNCHED();
+  if (rh && m <= AR_MAXV) {
+    ritz_via_host(H, ldh, m, steps, 1, omega_dev, rh, s);
+  } else {
+    ritz_kernel<<<1, 32, 0, s>>>(H, ldh, m, steps, omega_dev); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+  }
   dfree(V, s);
   dfree(w, s);
   dfree(H, s);
