@@ -591,11 +591,18 @@ __global__ void jacobi_first(const T* __restrict__ dinv, int rows, const signed 
     x[r] = cf[r] == which ? omega * dinv[r] * b[r] : T(0);
 }
 
-// One thread per row for FP64 (an FP64 warp instruction costs ~16 SM cycles whatever the
-// number of active lanes); for FP32, W lanes per row, W >= the mean row length.
+// FP64 short rows one per thread (an FP64 warp instruction costs ~16 SM cycles whatever
+// the number of active lanes), long rows about four entries per lane (else one thread's
+// chain of dependent index and value loads); FP32: W lanes per row, W >= the mean row
+// length.
 static int lanes_of(const Csr& A, bool fp64) {
-  if (fp64) return 1;
   double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
+  if (fp64) {
+    if (avg <= 8.0) return 1;
+    int w = 2;
+    while (w < 32 && 4 * w < avg) w <<= 1;
+    return w;
+  }
   int w = 2;
   while (w < 32 && w < avg) w <<= 1;
   return w;
@@ -854,7 +861,7 @@ static void arnoldi_fused_steps(const Csr& A, const double* dinv, int m, double*
                                 cudaStream_t s) {
   const int n = A.rows;
   const int nb = partial_blocks();
-  const int W = lanes_of(A, true);  // FP64: one thread per row
+  const int W = lanes_of(A, true);
   for (int j = 0; j < m; ++j) {
     // the previous w (scaled by sc[1]) becomes v_j; v_0 is already normalised
     double* w = wbuf[j & 1];

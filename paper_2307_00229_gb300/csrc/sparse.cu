@@ -353,9 +353,18 @@ void csr_transpose(const Csr& A, Csr& At, int** perm_out, cudaStream_t s) {
 // active, so sub-warp groups (idle lanes, shuffle-add trees) waste most of it.  FP32
 // kernels use W lanes per row, W the power of two at or above the mean row length.
 // ------------------------------------------------------------------------------------
+// FP32: W >= the mean row length.  FP64: an FP64 warp instruction costs about the same
+// with 1 or 32 active lanes, so short rows run one per thread; long rows (coarse levels)
+// would then be one thread's chain of dependent index and value loads, so they get lanes
+// at about four entries per lane.
 static int lanes_for(const Csr& A, bool fp64) {
-  if (fp64) return 1;
   double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
+  if (fp64) {
+    if (avg <= 8.0) return 1;
+    int w = 2;
+    while (w < 32 && 4 * w < avg) w <<= 1;
+    return w;
+  }
   int w = 2;
   while (w < 32 && w < avg) w <<= 1;
   return w;
