@@ -115,6 +115,35 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
+// Sum over CSR entries e0 <= e < e1 of val[e] * x[col[e]], in increasing e (lane `lane`
+// of W takes every W-th entry).  With one lane per row the row's indices and values are
+// loaded eight at a time before their gathers, so a short row costs two dependent memory
+// round trips instead of two per entry; the order and the contraction (acc + v * x into
+// one fma) are the same either way.
+template <int W, class T, class X>
+__device__ __forceinline__ T csr_row_dot(const int* __restrict__ col, const T* __restrict__ val,
+                                         const X* __restrict__ x, int e0, int e1, int lane) {
+  T acc = 0;
+  if constexpr (W == 1) {
+    for (int eb = e0; eb < e1; eb += 8) {
+      int c[8];
+      T v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const bool in = eb + q < e1;
+        c[q] = in ? col[eb + q] : 0;
+        v[q] = in ? val[eb + q] : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (eb + q < e1) acc += v[q] * __ldg(&x[c[q]]);
+    }
+  } else {
+    for (int e = e0 + lane; e < e1; e += W) acc += val[e] * __ldg(&x[col[e]]);
+  }
+  return acc;
+}
+
 // splitmix64 (Steele, Lea & Flood 2014): draw i of the stream seeded with `seed`.
 __device__ __forceinline__ double splitmix_pm1(uint64_t seed, uint64_t i) {
   uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;

@@ -1350,6 +1350,7 @@ clair_status clair_local_weights(int n, const int* Ahat_rowptr, const int* Ahat_
   }
   Csr Ahat;
   Ahat.rows = Ahat.cols = n;
+  Ahat.nnz = nnzA;
   Ahat.rowptr = const_cast<int*>(Ahat_rowptr);
   Ahat.col = const_cast<int*>(Ahat_col);
   Ahat.val = const_cast<double*>(Ahat_val);

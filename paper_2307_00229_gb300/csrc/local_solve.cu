@@ -53,10 +53,10 @@ __device__ __forceinline__ int find_sorted(const int* z, int T, int c) {
 // ------------------------------------------------------------------------------------
 constexpr int LS_WARPS = 4;  // warps per block in the sub-warp path
 
-template <class Real, int G>
+template <class Real, class VT, int G>
 __global__ void __launch_bounds__(32 * LS_WARPS)
 lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
-             const double* __restrict__ Aval, const int* __restrict__ Zrp,
+             const VT* __restrict__ Aval, const int* __restrict__ Zrp,
              const int* __restrict__ Zcol, const int* __restrict__ cpts,
              const int* __restrict__ work, int nwork, double* __restrict__ Zval,
              unsigned long long* __restrict__ nsingular) {
@@ -195,10 +195,10 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
 // CTA path: one system per block of TMAX threads, T <= TMAX (64 or 128); the matrix
 // lives in shared memory, thread r owns row r.
 // ------------------------------------------------------------------------------------
-template <class Real, int TMAX>
+template <class Real, class VT, int TMAX>
 __global__ void __launch_bounds__(TMAX)
 lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
-           const double* __restrict__ Aval, const int* __restrict__ Zrp,
+           const VT* __restrict__ Aval, const int* __restrict__ Zrp,
            const int* __restrict__ Zcol, const int* __restrict__ cpts,
            const int* __restrict__ work, double* __restrict__ Zval,
            unsigned long long* __restrict__ nsingular) {
@@ -345,10 +345,10 @@ __host__ __device__ constexpr size_t big_smem(int pitch) {
   return (size_t)pitch * (3 * sizeof(int) + 2 * sizeof(Real)) + 2 * sizeof(Real);
 }
 
-template <class Real>
+template <class Real, class VT>
 __global__ void __launch_bounds__(LB_THREADS)
 lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
-           const double* __restrict__ Aval, const int* __restrict__ Zrp,
+           const VT* __restrict__ Aval, const int* __restrict__ Zrp,
            const int* __restrict__ Zcol, const int* __restrict__ cpts,
            const int* __restrict__ work, double* __restrict__ Zval,
            unsigned long long* __restrict__ nsingular, Real* __restrict__ scratch, int pitch) {
@@ -580,47 +580,51 @@ int coarse_points(const signed char* cf, int n, int** cpts_out, cudaStream_t s) 
   return nc;
 }
 
-template <class Real>
-static void launch_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* cpts,
-                          const int* lists, const int* counts_h, int nc, double* Zval,
-                          unsigned long long* nsing, cudaStream_t s, Real* big_scratch = nullptr,
-                          int big_pitch = 0, int big_chunk = 0) {
+// vals: Ahat's values in the gather's type (a float copy in MIXED mode, so each value is
+// converted once instead of once per local system it appears in; converting the copy
+// gives the same floats).
+template <class Real, class VT>
+static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const int* Zcol,
+                          const int* cpts, const int* lists, const int* counts_h, int nc,
+                          double* Zval, unsigned long long* nsing, cudaStream_t s,
+                          Real* big_scratch = nullptr, int big_pitch = 0, int big_chunk = 0) {
   static bool attr = false;
   if (!attr) {
-    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, VT, 64>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)cta_smem<Real, 64>()));
-    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, VT, 128>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)cta_smem<Real, 128>()));
-    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_big<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_big<Real, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)big_smem<Real>(LS_TBIG)));
     attr = true;
   }
   const int per_block[3] = {LS_WARPS * 4, LS_WARPS * 2, LS_WARPS};
   if (counts_h[0])
-    lsolve_group<Real, 8><<<ceil_div(counts_h[0], per_block[0]), 32 * LS_WARPS, 0, s>>>(
-        Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts, lists + 0LL * nc, counts_h[0], Zval, nsing); ::clair::count_launch();
+    lsolve_group<Real, VT, 8><<<ceil_div(counts_h[0], per_block[0]), 32 * LS_WARPS, 0, s>>>(
+        Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 0LL * nc, counts_h[0], Zval, nsing); ::clair::count_launch();
   if (counts_h[1])
-    lsolve_group<Real, 16><<<ceil_div(counts_h[1], per_block[1]), 32 * LS_WARPS, 0, s>>>(
-        Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts, lists + 1LL * nc, counts_h[1], Zval, nsing); ::clair::count_launch();
+    lsolve_group<Real, VT, 16><<<ceil_div(counts_h[1], per_block[1]), 32 * LS_WARPS, 0, s>>>(
+        Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 1LL * nc, counts_h[1], Zval, nsing); ::clair::count_launch();
   if (counts_h[2])
-    lsolve_group<Real, 32><<<ceil_div(counts_h[2], per_block[2]), 32 * LS_WARPS, 0, s>>>(
-        Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts, lists + 2LL * nc, counts_h[2], Zval, nsing); ::clair::count_launch();
+    lsolve_group<Real, VT, 32><<<ceil_div(counts_h[2], per_block[2]), 32 * LS_WARPS, 0, s>>>(
+        Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 2LL * nc, counts_h[2], Zval, nsing); ::clair::count_launch();
   if (counts_h[3])
-    lsolve_cta<Real, 64><<<counts_h[3], 64, cta_smem<Real, 64>(), s>>>(
-        Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts, lists + 3LL * nc, Zval, nsing); ::clair::count_launch();
+    lsolve_cta<Real, VT, 64><<<counts_h[3], 64, cta_smem<Real, 64>(), s>>>(
+        Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 3LL * nc, Zval, nsing); ::clair::count_launch();
   if (counts_h[4])
-    lsolve_cta<Real, 128><<<counts_h[4], 128, cta_smem<Real, 128>(), s>>>(
-        Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts, lists + 4LL * nc, Zval, nsing); ::clair::count_launch();
+    lsolve_cta<Real, VT, 128><<<counts_h[4], 128, cta_smem<Real, 128>(), s>>>(
+        Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 4LL * nc, Zval, nsing); ::clair::count_launch();
   if (counts_h[5]) {
     CLAIR_REQUIRE(big_scratch && big_chunk > 0, CLAIR_ERR_CAPACITY,
                   "%d local systems larger than 128 unknowns (this entry point solves T <= 128)",
                   counts_h[5]);
     for (int off = 0; off < counts_h[5]; off += big_chunk) {
       const int cnt = std::min(big_chunk, counts_h[5] - off);
-      lsolve_big<Real><<<cnt, LB_THREADS, big_smem<Real>(big_pitch), s>>>(
-          Ahat.rowptr, Ahat.col, Ahat.val, Zrp, Zcol, cpts,
-                                                 lists + 5LL * nc + off, Zval, nsing, big_scratch,
-                                                 big_pitch); ::clair::count_launch();
+      lsolve_big<Real, VT><<<cnt, LB_THREADS, big_smem<Real>(big_pitch), s>>>(
+          Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 5LL * nc + off, Zval, nsing,
+          big_scratch, big_pitch); ::clair::count_launch();
     }
   }
   CLAIR_LAUNCHED();
@@ -662,16 +666,19 @@ void local_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* c
     {
       int pitch, chunk;
       float* tiles = big_tiles<float>(counts_h, pitch, chunk, s);
-      launch_solves<float>(Ahat, Zrp, Zcol, cpts, lists, counts_h, nc, Zval, nsing, s, tiles, pitch,
-                           chunk);
+      float* vals32 = dalloc<float>(std::max(Ahat.nnz, 1), s);
+      to_float(Ahat.val, vals32, Ahat.nnz, s);
+      launch_solves<float, float>(Ahat, vals32, Zrp, Zcol, cpts, lists, counts_h, nc, Zval, nsing,
+                                  s, tiles, pitch, chunk);
+      dfree(vals32, s);
       dfree(tiles, s);
     }
     else
     {
       int pitch, chunk;
       double* tiles = big_tiles<double>(counts_h, pitch, chunk, s);
-      launch_solves<double>(Ahat, Zrp, Zcol, cpts, lists, counts_h, nc, Zval, nsing, s, tiles, pitch,
-                            chunk);
+      launch_solves<double, double>(Ahat, Ahat.val, Zrp, Zcol, cpts, lists, counts_h, nc, Zval,
+                                    nsing, s, tiles, pitch, chunk);
       dfree(tiles, s);
     }
   }
@@ -857,9 +864,11 @@ static void local_weights_noalloc(int n, const Csr& Ahat, const signed char* cf,
   CLAIR_REQUIRE(counts_h[LS_BUCKETS] == 0, CLAIR_ERR_CAPACITY,
                 "%d local systems larger than %d unknowns", counts_h[LS_BUCKETS], LS_TBIG);
   if (precision == CLAIR_MIXED)
-    launch_solves<float>(Ahat, Z.rowptr, Z.col, b.cpts, b.lists, counts_h, nc, Z.val, b.work, s);
+    launch_solves<float, double>(Ahat, Ahat.val, Z.rowptr, Z.col, b.cpts, b.lists, counts_h, nc,
+                                 Z.val, b.work, s);
   else
-    launch_solves<double>(Ahat, Z.rowptr, Z.col, b.cpts, b.lists, counts_h, nc, Z.val, b.work, s);
+    launch_solves<double, double>(Ahat, Ahat.val, Z.rowptr, Z.col, b.cpts, b.lists, counts_h, nc,
+                                  Z.val, b.work, s);
   // column view of the weights, projection, values back into the row view
   Csr Zt;
   Zt.rowptr = b.zt_rowptr;

@@ -574,7 +574,7 @@ __global__ void jacobi_kernel(const int* __restrict__ rowptr, const int* __restr
   const bool act = ok && cf[r] == which;
   T acc = 0;
   if (act)
-    for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += W) acc += val[e] * __ldg(&xin[col[e]]);
+    acc = csr_row_dot<W>(col, val, xin, rowptr[r], rowptr[r + 1], lane);
   acc = group_sum<W>(acc);
   if (ok && lane == 0) {
     const T xr = xin[r];
@@ -724,13 +724,16 @@ __global__ void __launch_bounds__(32) ritz_kernel(const double* __restrict__ H, 
   if (lane == 0) *omega = rho > 0.0 ? 1.0 / rho : 1.0;
 }
 
-// ---- fused Arnoldi step (m <= AR_MAXV): six launches per step ---------------------------
-// K1  v_j = w_prev * scale (stored for j > 0), w = D^-1 A v_j, partial dots of w with
-//     v_0..v_j and with itself                       -> finalize: h1, ||w||^2 before CGS
-// K3  w -= V h1, partial dots of the new w with v_0..v_j -> finalize: h2
-// K5  w -= V h2, partial ||w||^2                      -> finalize: H column, breakdown, 1/||w||
-// The partial sums are per block in a fixed grid-stride order and the finalize kernel adds
-// them in block order, so the result does not depend on scheduling.
+// ---- fused Arnoldi step (m <= AR_MAXV): three launches per step -------------------------
+// K1  [sums K3's partials of the previous step: ||w||, its H column, breakdown, scale]
+//     v_j = w_prev * scale (stored for j > 0), w = D^-1 A v_j, partial dots of w with
+//     v_0..v_j and with itself
+// K2  [sums K1's partials: h1, ||w||^2 before CGS]  w -= V h1, partial dots with v_0..v_j
+// K3  [sums K2's partials: h2]                       w -= V h2, partial ||w||^2
+// Every block adds the previous kernel's per-block partials itself, in block order (block
+// 0 also stores the results), so no separate finalize launch sits between the steps and
+// the result does not depend on scheduling.  Consecutive kernels write alternate partial
+// buffers; steps_hist[t] is the breakdown state after step t-1 (-1: none).
 constexpr int AR_MAXV = 15;
 constexpr int AR_THREADS = 256;
 
@@ -752,14 +755,56 @@ __device__ __forceinline__ void block_reduce_to_partial(double (&acc)[NV], int n
   }
 }
 
+// Sums the previous kernel's partials (nv values, nb blocks) into out[0..nv-1], the same
+// order in every block: lanes over blocks, then the warp tree.
+__device__ __forceinline__ void sum_partials(const double* __restrict__ partial, int nb, int nv,
+                                             double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int v = wid; v < nv; v += AR_THREADS / 32) {
+    double t = 0.0;
+    for (int b = lane; b < nb; b += 32) t += partial[(long long)v * nb + b];
+    t = warp_sum(t);
+    if (lane == 0) out[v] = t;
+  }
+  __syncthreads();
+}
+
+struct ArnoldiState {
+  double* H;           // ldh x m, column-major
+  int ldh;
+  double* h1;          // h1 of the current step (AR_MAXV)
+  double* h2;          // h2 of the current step (AR_MAXV)
+  double* w0n2;        // ||w||^2 before orthogonalisation, current step
+  int* steps_hist;     // m + 1 entries, [0] = -1
+};
+
+// Finalize of step t-1 from ||w||^2 = hn2: H column, breakdown state; returns the scale of
+// the next basis vector (0 once broken down).  Block 0 stores; every block computes.
+__device__ __forceinline__ double arnoldi_close_step(const ArnoldiState& st, int t, double hn2) {
+  const bool active = st.steps_hist[t - 1] < 0;
+  const double hn = sqrt(hn2);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int j = t - 1;
+    for (int i = 0; i <= j; ++i) st.H[i + (long long)j * st.ldh] = active ? st.h1[i] + st.h2[i] : 0.0;
+    st.H[j + 1 + (long long)j * st.ldh] = active ? hn : 0.0;
+    st.steps_hist[t] = (active && hn <= 1e-10 * sqrt(*st.w0n2)) ? t : st.steps_hist[t - 1];
+  }
+  return (active && hn > 0.0) ? 1.0 / hn : 0.0;
+}
+
 template <int W>
 __global__ void __launch_bounds__(AR_THREADS)
 arnoldi_k1(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ av,
            const double* __restrict__ dinv, int n, double* __restrict__ V, int j,
-           const double* __restrict__ wprev, const double* __restrict__ scale_dev,
+           const double* __restrict__ wprev, ArnoldiState st, const double* __restrict__ pin,
            double* __restrict__ w, double* __restrict__ partial) {
+  __shared__ double red[1];
+  double sc = 1.0;  // v_0 is normalised already
+  if (j > 0) {
+    sum_partials(pin, gridDim.x, 1, red);
+    sc = arnoldi_close_step(st, j, red[0]);
+  }
   constexpr int GPW = 32 / W;
-  const double sc = *scale_dev;
   double acc[AR_MAXV + 2];
 #pragma unroll
   for (int v = 0; v < AR_MAXV + 2; ++v) acc[v] = 0.0;
@@ -770,7 +815,7 @@ arnoldi_k1(const int* __restrict__ rp, const int* __restrict__ ci, const double*
     const long long i = base + grp;
     double s = 0.0;
     if (i < n)
-      for (int e = rp[i] + sub; e < rp[i + 1]; e += W) s += av[e] * wprev[ci[e]];
+      s = csr_row_dot<W>(ci, av, wprev, rp[i], rp[i + 1], sub);
     s = group_sum<W>(s);
     if (sub == 0 && i < n) {
       const double wi = dinv[i] * (sc * s);
@@ -788,17 +833,31 @@ arnoldi_k1(const int* __restrict__ rp, const int* __restrict__ ci, const double*
   block_reduce_to_partial<AR_MAXV + 2>(acc, AR_MAXV + 2, partial);
 }
 
-// w -= V[:, 0..j] h; if DOTS, partial dots of the new w with v_0..v_j, else partial ||w||^2
-template <bool DOTS>
+// FIRST: h1 (and ||w||^2 before CGS) from K1's partials, w -= V h1, partial dots with
+// v_0..v_j.  Otherwise: h2 from the first pass's partials, w -= V h2, partial ||w||^2.
+template <bool FIRST>
 __global__ void __launch_bounds__(AR_THREADS)
-arnoldi_cgs(const double* __restrict__ V, int j, int n, const double* __restrict__ h,
-            double* __restrict__ w, double* __restrict__ partial) {
+arnoldi_cgs(const double* __restrict__ V, int j, int n, ArnoldiState st,
+            const double* __restrict__ pin, double* __restrict__ w, double* __restrict__ partial) {
+  __shared__ double hs[AR_MAXV + 2];
+  if (FIRST) {
+    // K1 wrote AR_MAXV + 2 values per block: <v_k, w> for k <= j, slot AR_MAXV + 1 <w, w>
+    sum_partials(pin, gridDim.x, AR_MAXV + 2, hs);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      for (int k = 0; k <= j; ++k) st.h1[k] = hs[k];
+      *st.w0n2 = hs[AR_MAXV + 1];
+    }
+  } else {
+    sum_partials(pin, gridDim.x, j + 1, hs);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+      for (int k = 0; k <= j; ++k) st.h2[k] = hs[k];
+  }
   double acc[AR_MAXV + 1];
 #pragma unroll
   for (int v = 0; v < AR_MAXV + 1; ++v) acc[v] = 0.0;
   double hk[AR_MAXV];
 #pragma unroll
-  for (int k = 0; k < AR_MAXV; ++k) hk[k] = k <= j ? h[k] : 0.0;
+  for (int k = 0; k < AR_MAXV; ++k) hk[k] = k <= j ? hs[k] : 0.0;
   for (long long i = blockIdx.x * (long long)AR_THREADS + threadIdx.x; i < n;
        i += (long long)gridDim.x * AR_THREADS) {
     double vk[AR_MAXV];
@@ -809,7 +868,7 @@ arnoldi_cgs(const double* __restrict__ V, int j, int n, const double* __restrict
       if (k <= j) wi = fma(-hk[k], vk[k], wi);
     }
     w[i] = wi;
-    if (DOTS) {
+    if (FIRST) {
 #pragma unroll
       for (int k = 0; k < AR_MAXV; ++k)
         if (k <= j) acc[k] += vk[k] * wi;
@@ -817,65 +876,41 @@ arnoldi_cgs(const double* __restrict__ V, int j, int n, const double* __restrict
       acc[0] += wi * wi;
     }
   }
-  block_reduce_to_partial<AR_MAXV + 1>(acc, DOTS ? j + 1 : 1, partial);
+  block_reduce_to_partial<AR_MAXV + 1>(acc, FIRST ? j + 1 : 1, partial);
 }
 
-// Adds the partials of nv values in block order.  mode 0: h1 = out[0..j], w0n2 = out[j+1];
-// mode 1: h2 = out[0..j]; mode 2: ||w||^2 = out[0], then the H column, breakdown test and
-// the scale 1/||w|| of the next basis vector (0 after a breakdown).
-__global__ void __launch_bounds__(512)
-arnoldi_finalize(const double* __restrict__ partial, int nb, int nv, int mode, int j,
-                 double* __restrict__ h1, double* __restrict__ h2, double* __restrict__ sc,
-                 double* __restrict__ H, int ldh, int* __restrict__ steps) {
-  __shared__ double out[AR_MAXV + 2];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int v = wid; v < nv; v += 16) {
-    double t = 0.0;
-    for (int b = lane; b < nb; b += 32) t += partial[(long long)v * nb + b];
-    t = warp_sum(t);
-    if (lane == 0) out[v] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  // sc: [0] ||w||^2 before orthogonalisation, [1] scale of the next basis vector
-  if (mode == 0) {
-    for (int k = 0; k <= j; ++k) h1[k] = out[k];
-    sc[0] = out[AR_MAXV + 1];
-  } else if (mode == 1) {
-    for (int k = 0; k <= j; ++k) h2[k] = out[k];
-  } else {
-    const bool active = *steps < 0;
-    for (int i = 0; i <= j; ++i) H[i + (long long)j * ldh] = active ? h1[i] + h2[i] : 0.0;
-    const double hn = sqrt(out[0]);
-    H[j + 1 + (long long)j * ldh] = active ? hn : 0.0;
-    if (active && hn <= 1e-10 * sqrt(sc[0])) *steps = j + 1;
-    sc[1] = (active && hn > 0.0) ? 1.0 / hn : 0.0;
-  }
+// The last step's finalize (one block).
+__global__ void __launch_bounds__(AR_THREADS)
+arnoldi_last(ArnoldiState st, int m, const double* __restrict__ pin, int nb) {
+  __shared__ double red[1];
+  sum_partials(pin, nb, 1, red);
+  arnoldi_close_step(st, m, red[0]);
 }
 
-// wbuf[0], wbuf[1]: the new w of step j lives in wbuf[j & 1] while K1 gathers v_j from the
-// previous step's w in the other buffer.
+// w of step j lives in wbuf[j & 1] while K1 gathers v_j from the previous step's w in the
+// other buffer; kernel t (3 per step) writes partial buffer t & 1 and reads the other.
 static void arnoldi_fused_steps(const Csr& A, const double* dinv, int m, double* V,
-                                double* const wbuf[2], double* H, int ldh, double* h1, double* h2,
-                                double* sc, const double* one, int* steps, double* partial,
-                                cudaStream_t s) {
+                                double* const wbuf[2], const ArnoldiState& st,
+                                double* const pbuf[2], cudaStream_t s) {
   const int n = A.rows;
   const int nb = partial_blocks();
   const int W = lanes_of(A, true);
+  int t = 0;
   for (int j = 0; j < m; ++j) {
-    // the previous w (scaled by sc[1]) becomes v_j; v_0 is already normalised
     double* w = wbuf[j & 1];
     const double* wprev = j == 0 ? V : wbuf[(j + 1) & 1];
-    const double* scale = j == 0 ? one : sc + 1;
     CLAIR_DISPATCH_W2(W, (arnoldi_k1<WW><<<nb, AR_THREADS, 0, s>>>(A.rowptr, A.col, A.val, dinv, n,
-                                                                  V, j, wprev, scale, w, partial)));
-    arnoldi_finalize<<<1, 512, 0, s>>>(partial, nb, AR_MAXV + 2, 0, j, h1, h2, sc, H, ldh, steps); ::clair::count_launch();
-    arnoldi_cgs<true><<<nb, AR_THREADS, 0, s>>>(V, j, n, h1, w, partial); ::clair::count_launch();
-    arnoldi_finalize<<<1, 512, 0, s>>>(partial, nb, j + 1, 1, j, h1, h2, sc, H, ldh, steps); ::clair::count_launch();
-    arnoldi_cgs<false><<<nb, AR_THREADS, 0, s>>>(V, j, n, h2, w, partial); ::clair::count_launch();
-    arnoldi_finalize<<<1, 512, 0, s>>>(partial, nb, 1, 2, j, h1, h2, sc, H, ldh, steps); ::clair::count_launch();
+                                                                  V, j, wprev, st, pbuf[(t + 1) & 1],
+                                                                  w, pbuf[t & 1])));
+    ++t;
+    arnoldi_cgs<true><<<nb, AR_THREADS, 0, s>>>(V, j, n, st, pbuf[(t + 1) & 1], w, pbuf[t & 1]); ::clair::count_launch();
+    ++t;
+    arnoldi_cgs<false><<<nb, AR_THREADS, 0, s>>>(V, j, n, st, pbuf[(t + 1) & 1], w, pbuf[t & 1]); ::clair::count_launch();
+    ++t;
     CLAIR_LAUNCHED();
   }
+  arnoldi_last<<<1, AR_THREADS, 0, s>>>(st, m, pbuf[(t + 1) & 1], nb); ::clair::count_launch();
+  CLAIR_LAUNCHED();
 }
 
 // ---- Ritz values on the host --------------------------------------------------------
@@ -983,7 +1018,7 @@ seg_k1(const int* __restrict__ rp, const int* __restrict__ ci, const double* __r
     const int i = base + grp;
     double s = 0.0;
     if (i < hi)
-      for (int e = rp[i] + sub; e < rp[i + 1]; e += W) s += av[e] * wprev[ci[e]];
+      s = csr_row_dot<W>(ci, av, wprev, rp[i], rp[i + 1], sub);
     s = group_sum<W>(s);
     if (sub == 0 && i < hi) {
       const double wi = dinv[i] * (scl * s);
@@ -1203,14 +1238,19 @@ double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed
   multi_dot(V, 1, V, n, wn2, partial, s);
   scale_by_inv_sqrt<<<grid, 256, 0, s>>>(V, n, wn2); ::clair::count_launch();
   CLAIR_LAUNCHED();
+  int* steps_hist = nullptr;
   if (m <= AR_MAXV) {
-    // sc layout for the fused steps: [w0n2, next scale]; `one` = 1.0 scales v_0
-    const double h_one = 1.0;
-    CLAIR_CUDA(cudaMemcpyAsync(sc + 131, &h_one, sizeof(double), cudaMemcpyHostToDevice, s));
     double* w2 = dalloc<double>(n, s);
+    double* p2 = dalloc<double>((size_t)partial_blocks() * (AR_MAXV + 2), s);
+    steps_hist = dalloc<int>(m + 1, s);
+    CLAIR_CUDA(cudaMemsetAsync(steps_hist, 0xff, sizeof(int) * (m + 1), s));  // -1
     double* const wbuf[2] = {w, w2};
-    arnoldi_fused_steps(A, dinv, m, V, wbuf, H, ldh, h1, h2, sc + 128, sc + 131, steps, partial, s);
+    double* const pbuf[2] = {partial, p2};
+    const ArnoldiState st{H, ldh, h1, h2, sc + 129, steps_hist};
+    arnoldi_fused_steps(A, dinv, m, V, wbuf, st, pbuf, s);
+    CLAIR_CUDA(cudaMemcpyAsync(steps, steps_hist + m, sizeof(int), cudaMemcpyDeviceToDevice, s));
     dfree(w2, s);
+    dfree(p2, s);
   }
   for (int j = 0; j < m && m > AR_MAXV; ++j) {
     double* vj = V + (size_t)j * n;
@@ -1238,6 +1278,7 @@ double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed
   dfree(H, s);
   dfree(sc, s);
   dfree(steps, s);
+  dfree(steps_hist, s);
   dfree(partial, s);
   return 0.0;  // the weight is in *omega_dev once the stream reaches this point
 }

@@ -413,7 +413,7 @@ __global__ void spmv_kernel(const int* __restrict__ rowptr, const int* __restric
   const bool ok = r < rows;  // no early exit: every lane takes part in the shuffles
   T acc = 0;
   if (ok)
-    for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += W) acc += val[e] * __ldg(&x[col[e]]);
+    acc = csr_row_dot<W>(col, val, x, rowptr[r], rowptr[r + 1], lane);
   acc = group_sum<W>(acc);
   if (ok && lane == 0) {
     if (RESID)
@@ -759,8 +759,11 @@ __device__ void spgemm_row(int r, const int* __restrict__ Arp, const int* __rest
 // order before one add into the table, so every sum has a fixed order.  The row uses a
 // table of rcap <= CAP slots sized from its product count (symbolic) or its exact
 // output count (numeric), so clearing and compacting cost what the row needs.
-// Tiers: CAP 512 / prefix 512 with four warps per block for the bulk of the rows, CAP
-// 4096 / prefix 2048 with one warp per block, then the sequential large table above.
+// Tiers: CAP 128 / prefix 128 with eight warps per block for the bulk of the rows (a small
+// table keeps eight warps' tables in 19 KB of shared memory, so occupancy is not limited
+// by it), CAP 512 / prefix 512 with four warps, CAP 4096 / prefix 2048 with one warp, then
+// the sequential large table above.
+constexpr int SG_CAP0 = 128, SG_PRE0 = 128, SG_WARPS0 = 8;
 constexpr int SG_CAP1 = 512, SG_PRE1 = 512, SG_WARPS1 = 4;
 constexpr int SG_CAP2 = 4096, SG_PRE2 = 2048;
 
@@ -883,9 +886,10 @@ template <bool NUMERIC, int CAP, int PCAP, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS)
 spgemm_flat(const int* __restrict__ Arp, const int* __restrict__ Acol,
             const double* __restrict__ Aval, const int* __restrict__ list, int nrows,
-            const int* __restrict__ Brp, const int* __restrict__ Bcol,
-            const double* __restrict__ Bval, int* __restrict__ count, const int* __restrict__ Crp,
-            int* __restrict__ Ccol, double* __restrict__ Cval) {
+            const int* __restrict__ dnrows, const int* __restrict__ Brp,
+            const int* __restrict__ Bcol, const double* __restrict__ Bval,
+            int* __restrict__ count, const int* __restrict__ Crp, int* __restrict__ Ccol,
+            double* __restrict__ Cval) {
   extern __shared__ __align__(16) unsigned char sg_smem[];
   const int w = threadIdx.x >> 5;
   unsigned char* mine = sg_smem + (size_t)w * sg_warp_bytes(NUMERIC, CAP, PCAP);
@@ -894,33 +898,40 @@ spgemm_flat(const int* __restrict__ Arp, const int* __restrict__ Acol,
   int* keys = reinterpret_cast<int*>(mine + sizeof(double) * 32 +
                                      (NUMERIC ? sizeof(double) * CAP : 0));
   int* prefix = keys + CAP;
-  const int idx = blockIdx.x * WARPS + w;
-  if (idx >= nrows) return;  // warp-uniform
-  const int r = list ? list[idx] : idx;
-  const bool long_row = (Arp[r + 1] - Arp[r]) > PCAP;
-  if (!NUMERIC && long_row) {
-    if ((threadIdx.x & 31) == 0) count[r] = -1;
-    return;
+  if (dnrows) nrows = *dnrows;  // rows listed by the previous tier, counted on the device
+  for (int idx = blockIdx.x * WARPS + w; idx < nrows; idx += gridDim.x * WARPS) {  // warp-uniform
+    const int r = list ? list[idx] : idx;
+    const bool long_row = (Arp[r + 1] - Arp[r]) > PCAP;
+    if (!NUMERIC && long_row) {
+      if ((threadIdx.x & 31) == 0) count[r] = -1;
+      continue;
+    }
+    if (NUMERIC && ((Crp[r + 1] - Crp[r]) > CAP / 2 || long_row)) continue;
+    spgemm_row_flat<NUMERIC, CAP, PCAP>(r, Arp, Acol, Aval, Brp, Bcol, Bval, keys, vals, prefix,
+                                        stage, count, Crp, Ccol, Cval);
+    __syncwarp();
   }
-  if (NUMERIC && ((Crp[r + 1] - Crp[r]) > CAP / 2 || long_row)) return;
-  spgemm_row_flat<NUMERIC, CAP, PCAP>(r, Arp, Acol, Aval, Brp, Bcol, Bval, keys, vals, prefix,
-                                      stage, count, Crp, Ccol, Cval);
 }
 
-// Large dynamic table, one warp per listed row (sequential over the A row's entries).
+// Large dynamic table, one warp per listed row (sequential over the A row's entries); the
+// list's length is read on the device.
 template <bool NUMERIC>
 __global__ void __launch_bounds__(32)
 spgemm_large(const int* __restrict__ Arp, const int* __restrict__ Acol,
              const double* __restrict__ Aval, const int* __restrict__ list,
-             const int* __restrict__ Brp, const int* __restrict__ Bcol,
-             const double* __restrict__ Bval, int* __restrict__ count,
-             const int* __restrict__ Crp, int* __restrict__ Ccol, double* __restrict__ Cval) {
+             const int* __restrict__ dnrows, const int* __restrict__ Brp,
+             const int* __restrict__ Bcol, const double* __restrict__ Bval,
+             int* __restrict__ count, const int* __restrict__ Crp, int* __restrict__ Ccol,
+             double* __restrict__ Cval) {
   extern __shared__ unsigned char smem[];
   double* vals = reinterpret_cast<double*>(smem);
   int* keys = reinterpret_cast<int*>(smem + (NUMERIC ? sizeof(double) * SG_LARGE : 0));
-  const int r = list[blockIdx.x];
-  spgemm_row<NUMERIC>(r, Arp, Acol, Aval, Brp, Bcol, Bval, keys, NUMERIC ? vals : nullptr,
-                      SG_LARGE, count, Crp, Ccol, Cval);
+  const int nrows = *dnrows;
+  for (int idx = blockIdx.x; idx < nrows; idx += gridDim.x) {
+    spgemm_row<NUMERIC>(list[idx], Arp, Acol, Aval, Brp, Bcol, Bval, keys,
+                        NUMERIC ? vals : nullptr, SG_LARGE, count, Crp, Ccol, Cval);
+    __syncwarp();
+  }
 }
 
 // Lists (from `src` rows, or all rows when src == nullptr) the rows with count == -1
@@ -928,14 +939,15 @@ spgemm_large(const int* __restrict__ Arp, const int* __restrict__ Acol,
 // entries or more than `lim_nA` A entries.
 __global__ void spgemm_collect(const int* __restrict__ count, const int* __restrict__ Crp,
                                const int* __restrict__ Arp, const int* __restrict__ src,
-                               int nsrc, int mode, int lim_cnt, int lim_nA,
-                               int* __restrict__ list, int* __restrict__ n) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nsrc) return;
-  const int r = src ? src[t] : t;
-  const bool take = mode == 0 ? count[r] < 0
-                              : ((Crp[r + 1] - Crp[r]) > lim_cnt || (Arp[r + 1] - Arp[r]) > lim_nA);
-  if (take) list[atomicAdd(n, 1)] = r;
+                               int nsrc, const int* __restrict__ dnsrc, int mode, int lim_cnt,
+                               int lim_nA, int* __restrict__ list, int* __restrict__ n) {
+  if (dnsrc) nsrc = *dnsrc;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nsrc; t += gridDim.x * blockDim.x) {
+    const int r = src ? src[t] : t;
+    const bool take = mode == 0 ? count[r] < 0
+                                : ((Crp[r + 1] - Crp[r]) > lim_cnt || (Arp[r + 1] - Arp[r]) > lim_nA);
+    if (take) list[atomicAdd(n, 1)] = r;
+  }
 }
 
 __global__ void count_nonzero(const int* __restrict__ rowptr, const double* __restrict__ val, int rows,
@@ -987,108 +999,127 @@ void drop_zeros(Csr& C, cudaStream_t s) {
   C.nnz = nnz;
 }
 
+// Tier 0 runs over every row; each later tier (and the large table) runs over the rows the
+// previous one listed, with a grid-stride loop over a count it reads on the device, so the
+// tiers follow one another without a host round trip.  The host reads back once, with the
+// output size (symbolic) and the rows no table could hold.
 void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   C.rows = A.rows;
   C.cols = B.cols;
   const int rows = A.rows;
   int* count = dalloc<int>(rows + 1, s);
-  int* list1 = dalloc<int>(rows, s);
-  int* list2 = dalloc<int>(rows, s);
-  int* nlist = dalloc<int>(4, s);
-  CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 4 * sizeof(int), s));
-  const size_t t1_sym = SG_WARPS1 * sg_warp_bytes(false, SG_CAP1, SG_PRE1);
-  const size_t t1_num = SG_WARPS1 * sg_warp_bytes(true, SG_CAP1, SG_PRE1);
-  const size_t t2_sym = sg_warp_bytes(false, SG_CAP2, SG_PRE2);
-  const size_t t2_num = sg_warp_bytes(true, SG_CAP2, SG_PRE2);
-  const size_t t3_sym = sizeof(int) * SG_LARGE;
-  const size_t t3_num = (sizeof(int) + sizeof(double)) * SG_LARGE;
-  auto t1s = spgemm_flat<false, SG_CAP1, SG_PRE1, SG_WARPS1>;
-  auto t1n = spgemm_flat<true, SG_CAP1, SG_PRE1, SG_WARPS1>;
-  auto t2s = spgemm_flat<false, SG_CAP2, SG_PRE2, 1>;
-  auto t2n = spgemm_flat<true, SG_CAP2, SG_PRE2, 1>;
+  int* lists[2] = {dalloc<int>(std::max(rows, 1), s), dalloc<int>(std::max(rows, 1), s)};
+  int* nlist = dalloc<int>(8, s);
+  struct Tier {
+    int cap, pcap, warps;
+    void (*sym)(const int*, const int*, const double*, const int*, int, const int*, const int*,
+                const int*, const double*, int*, const int*, int*, double*);
+    void (*num)(const int*, const int*, const double*, const int*, int, const int*, const int*,
+                const int*, const double*, int*, const int*, int*, double*);
+  };
+  const Tier tiers[3] = {
+      {SG_CAP0, SG_PRE0, SG_WARPS0, spgemm_flat<false, SG_CAP0, SG_PRE0, SG_WARPS0>,
+       spgemm_flat<true, SG_CAP0, SG_PRE0, SG_WARPS0>},
+      {SG_CAP1, SG_PRE1, SG_WARPS1, spgemm_flat<false, SG_CAP1, SG_PRE1, SG_WARPS1>,
+       spgemm_flat<true, SG_CAP1, SG_PRE1, SG_WARPS1>},
+      {SG_CAP2, SG_PRE2, 1, spgemm_flat<false, SG_CAP2, SG_PRE2, 1>,
+       spgemm_flat<true, SG_CAP2, SG_PRE2, 1>}};
+  const size_t large_sym = sizeof(int) * SG_LARGE;
+  const size_t large_num = (sizeof(int) + sizeof(double)) * SG_LARGE;
   static bool attr_set = false;
   if (!attr_set) {
-    CLAIR_CUDA(cudaFuncSetAttribute(t1s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t1_sym));
-    CLAIR_CUDA(cudaFuncSetAttribute(t1n, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t1_num));
-    CLAIR_CUDA(cudaFuncSetAttribute(t2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t2_sym));
-    CLAIR_CUDA(cudaFuncSetAttribute(t2n, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t2_num));
+    for (const Tier& t : tiers) {
+      CLAIR_CUDA(cudaFuncSetAttribute(t.sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(t.warps * sg_warp_bytes(false, t.cap, t.pcap))));
+      CLAIR_CUDA(cudaFuncSetAttribute(t.num, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(t.warps * sg_warp_bytes(true, t.cap, t.pcap))));
+    }
     CLAIR_CUDA(cudaFuncSetAttribute(spgemm_large<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)t3_sym));
+                                    (int)large_sym));
     CLAIR_CUDA(cudaFuncSetAttribute(spgemm_large<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)t3_num));
+                                    (int)large_num));
     attr_set = true;
   }
-  auto read_count = [&](int* dev) {
-    int h = 0;
-    CLAIR_CUDA(cudaMemcpyAsync(&h, dev, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CLAIR_CUDA(cudaStreamSynchronize(s));
-    return h;
+  const int sms = sm_count();
+  // grid of a tier over listed rows: enough warps to fill the GPU, never more than the rows
+  auto grid_for_list = [&](int warps_per_block, int blocks_per_sm) {
+    return std::max(1, std::min(ceil_div(rows, warps_per_block), sms * blocks_per_sm));
   };
-  // ---- symbolic: tier 1 for every row, then the rows it could not hold ----
-  if (rows) {
-    t1s<<<ceil_div(rows, SG_WARPS1), 32 * SG_WARPS1, t1_sym, s>>>(
-        A.rowptr, A.col, A.val, nullptr, rows, B.rowptr, B.col, B.val, count, nullptr, nullptr,
-        nullptr); ::clair::count_launch();
-    spgemm_collect<<<ceil_div(rows, 256), 256, 0, s>>>(count, nullptr, A.rowptr, nullptr, rows, 0,
-                                                       0, 0, list1, nlist); ::clair::count_launch();
-  }
-  CLAIR_LAUNCHED();
-  const int n1 = rows ? read_count(nlist) : 0;
-  if (n1) {
-    t2s<<<n1, 32, t2_sym, s>>>(A.rowptr, A.col, A.val, list1, n1, B.rowptr, B.col, B.val, count,
-                               nullptr, nullptr, nullptr); ::clair::count_launch();
-    spgemm_collect<<<ceil_div(n1, 256), 256, 0, s>>>(count, nullptr, A.rowptr, list1, n1, 0, 0, 0,
-                                                     list2, nlist + 1); ::clair::count_launch();
-    CLAIR_LAUNCHED();
-    const int n2 = read_count(nlist + 1);
-    if (n2) {
-      spgemm_large<false><<<n2, 32, t3_sym, s>>>(A.rowptr, A.col, A.val, list2, B.rowptr, B.col,
-                                                 B.val, count, nullptr, nullptr, nullptr); ::clair::count_launch();
-      CLAIR_CUDA(cudaMemsetAsync(nlist + 2, 0, sizeof(int), s));
-      spgemm_collect<<<ceil_div(n2, 256), 256, 0, s>>>(count, nullptr, A.rowptr, list2, n2, 0, 0, 0,
-                                                       list1, nlist + 2); ::clair::count_launch();
+  // ---- symbolic ----
+  CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 8 * sizeof(int), s));
+  {
+    const int* src = nullptr;
+    const int* dn = nullptr;
+    int cur = 0;
+    for (int t = 0; t < 4; ++t) {
+      if (t < 3) {
+        const Tier& T = tiers[t];
+        const size_t sm = T.warps * sg_warp_bytes(false, T.cap, T.pcap);
+        const int grid = t == 0 ? std::max(1, ceil_div(rows, T.warps)) : grid_for_list(T.warps, 8);
+        T.sym<<<grid, 32 * T.warps, sm, s>>>(A.rowptr, A.col, A.val, src, rows, dn, B.rowptr, B.col,
+                                            B.val, count, nullptr, nullptr, nullptr); ::clair::count_launch();
+      } else {
+        spgemm_large<false><<<std::max(1, std::min(rows, sms)), 32, large_sym, s>>>(
+            A.rowptr, A.col, A.val, src, dn, B.rowptr, B.col, B.val, count, nullptr, nullptr,
+            nullptr); ::clair::count_launch();
+      }
+      spgemm_collect<<<std::max(1, std::min(ceil_div(rows, 256), sms * 8)), 256, 0, s>>>(
+          count, nullptr, A.rowptr, src, rows, dn, 0, 0, 0, lists[cur], nlist + t); ::clair::count_launch();
       CLAIR_LAUNCHED();
-      const int still = read_count(nlist + 2);
-      if (still) {
-        dfree(count, s);
-        dfree(list1, s);
-        dfree(list2, s);
-        dfree(nlist, s);
-        CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "SpGEMM: %d rows exceed %d distinct columns",
-                      still, SG_LARGE);
+      src = lists[cur];
+      dn = nlist + t;
+      cur ^= 1;
+    }
+  }
+  // rows still unplaced after the large table: nlist[3]; the scan's read-back carries it
+  C.rowptr = dalloc<int>(rows + 1, s);
+  C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true);  // synchronises s
+  int still = 0;  // the stream is idle here: a short read
+  CLAIR_CUDA(cudaMemcpyAsync(&still, nlist + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  if (still) {
+    dfree(count, s);
+    dfree(lists[0], s);
+    dfree(lists[1], s);
+    dfree(nlist, s);
+    dfree(C.rowptr, s);
+    CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "SpGEMM: %d rows exceed %d distinct columns", still,
+                  SG_LARGE);
+  }
+  C.col = dalloc<int>(C.nnz, s);
+  C.val = dalloc<double>(C.nnz, s);
+  // ---- numeric: each row in the first tier that holds it (output count <= cap / 2, A row
+  // <= prefix capacity) ----
+  CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 8 * sizeof(int), s));
+  {
+    const int* src = nullptr;
+    const int* dn = nullptr;
+    int cur = 0;
+    for (int t = 0; t < 4; ++t) {
+      if (t < 3) {
+        const Tier& T = tiers[t];
+        const size_t sm = T.warps * sg_warp_bytes(true, T.cap, T.pcap);
+        const int grid = t == 0 ? std::max(1, ceil_div(rows, T.warps)) : grid_for_list(T.warps, 8);
+        T.num<<<grid, 32 * T.warps, sm, s>>>(A.rowptr, A.col, A.val, src, rows, dn, B.rowptr, B.col,
+                                            B.val, count, C.rowptr, C.col, C.val); ::clair::count_launch();
+        spgemm_collect<<<std::max(1, std::min(ceil_div(rows, 256), sms * 8)), 256, 0, s>>>(
+            count, C.rowptr, A.rowptr, src, rows, dn, 1, T.cap / 2, T.pcap, lists[cur],
+            nlist + t); ::clair::count_launch();
+        CLAIR_LAUNCHED();
+        src = lists[cur];
+        dn = nlist + t;
+        cur ^= 1;
+      } else {
+        spgemm_large<true><<<std::max(1, std::min(rows, sms)), 32, large_num, s>>>(
+            A.rowptr, A.col, A.val, src, dn, B.rowptr, B.col, B.val, count, C.rowptr, C.col,
+            C.val); ::clair::count_launch();
+        CLAIR_LAUNCHED();
       }
     }
   }
-  C.rowptr = dalloc<int>(rows + 1, s);
-  C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true);
-  C.col = dalloc<int>(C.nnz, s);
-  C.val = dalloc<double>(C.nnz, s);
-  // ---- numeric: each row in the first tier that holds it ----
-  CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 4 * sizeof(int), s));
-  if (rows) {
-    t1n<<<ceil_div(rows, SG_WARPS1), 32 * SG_WARPS1, t1_num, s>>>(
-        A.rowptr, A.col, A.val, nullptr, rows, B.rowptr, B.col, B.val, count, C.rowptr, C.col,
-        C.val); ::clair::count_launch();
-    spgemm_collect<<<ceil_div(rows, 256), 256, 0, s>>>(count, C.rowptr, A.rowptr, nullptr, rows, 1,
-                                                       SG_CAP1 / 2, SG_PRE1, list1, nlist); ::clair::count_launch();
-  }
-  CLAIR_LAUNCHED();
-  const int m1 = rows ? read_count(nlist) : 0;
-  if (m1) {
-    t2n<<<m1, 32, t2_num, s>>>(A.rowptr, A.col, A.val, list1, m1, B.rowptr, B.col, B.val, count,
-                               C.rowptr, C.col, C.val); ::clair::count_launch();
-    spgemm_collect<<<ceil_div(m1, 256), 256, 0, s>>>(count, C.rowptr, A.rowptr, list1, m1, 1,
-                                                     SG_CAP2 / 2, SG_PRE2, list2, nlist + 1); ::clair::count_launch();
-    CLAIR_LAUNCHED();
-    const int m2 = read_count(nlist + 1);
-    if (m2)
-      spgemm_large<true><<<m2, 32, t3_num, s>>>(A.rowptr, A.col, A.val, list2, B.rowptr, B.col,
-                                                B.val, count, C.rowptr, C.col, C.val); ::clair::count_launch();
-  }
-  CLAIR_LAUNCHED();
   dfree(count, s);
-  dfree(list1, s);
-  dfree(list2, s);
+  dfree(lists[0], s);
+  dfree(lists[1], s);
   dfree(nlist, s);
 }
 
