@@ -358,7 +358,11 @@ struct SideStream {
   cudaStream_t s2 = nullptr;
   cudaEvent_t fork = nullptr, split = nullptr, join = nullptr;
   SideStream() {
-    CLAIR_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    // the weight chain is the longer branch on the fine levels: its blocks go first, the
+    // splitting, patterns and local solves use the SMs it leaves
+    int lo = 0, hi = 0;
+    CLAIR_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CLAIR_CUDA(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi));
     CLAIR_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     CLAIR_CUDA(cudaEventCreateWithFlags(&split, cudaEventDisableTiming));
     CLAIR_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));

@@ -725,15 +725,15 @@ __global__ void __launch_bounds__(32) ritz_kernel(const double* __restrict__ H, 
 }
 
 // ---- fused Arnoldi step (m <= AR_MAXV): three launches per step -------------------------
-// K1  [sums K3's partials of the previous step: ||w||, its H column, breakdown, scale]
-//     v_j = w_prev * scale (stored for j > 0), w = D^-1 A v_j, partial dots of w with
-//     v_0..v_j and with itself
-// K2  [sums K1's partials: h1, ||w||^2 before CGS]  w -= V h1, partial dots with v_0..v_j
-// K3  [sums K2's partials: h2]                       w -= V h2, partial ||w||^2
-// Every block adds the previous kernel's per-block partials itself, in block order (block
-// 0 also stores the results), so no separate finalize launch sits between the steps and
-// the result does not depend on scheduling.  Consecutive kernels write alternate partial
-// buffers; steps_hist[t] is the breakdown state after step t-1 (-1: none).
+// K1  v_j = w_prev * scale (stored for j > 0), w = D^-1 A v_j, dots of w with v_0..v_j and
+//     with itself                              -> h1, ||w||^2 before CGS
+// K2  w -= V h1, dots of the new w with v_0..v_j  -> h2
+// K3  w -= V h2, ||w||^2                        -> H column, breakdown, scale of v_{j+1}
+// Each block writes its partial sums; the last block to arrive (atomic ticket) adds them
+// in block order and publishes the step's scalars, so the next kernel reads finished
+// values, no finalize launch sits between the kernels, the grid can fill the GPU, and the
+// result does not depend on scheduling.  steps_hist[t] is the breakdown state after step
+// t-1 (-1: none).
 constexpr int AR_MAXV = 15;
 constexpr int AR_THREADS = 256;
 
@@ -755,55 +755,49 @@ __device__ __forceinline__ void block_reduce_to_partial(double (&acc)[NV], int n
   }
 }
 
-// Sums the previous kernel's partials (nv values, nb blocks) into out[0..nv-1], the same
-// order in every block: lanes over blocks, then the warp tree.
-__device__ __forceinline__ void sum_partials(const double* __restrict__ partial, int nb, int nv,
-                                             double* out) {
+struct ArnoldiState {
+  double* H;            // ldh x m, column-major
+  int ldh;
+  double* h1;           // h1 of the current step (AR_MAXV)
+  double* h2;           // h2 of the current step (AR_MAXV)
+  double* w0n2;         // ||w||^2 before orthogonalisation, current step
+  double* scale;        // scale of the next basis vector
+  int* steps_hist;      // m + 1 entries, [0] = -1
+  unsigned* ticket;     // arrival counter (0 between kernels)
+};
+
+// After the block's partials are written: true in the block that arrives last.
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return is_last;
+}
+
+// In the last block: out[v] = sum over blocks of partial v, lanes over blocks then the
+// warp tree (reads bypass L1: the other blocks wrote them in this kernel).
+__device__ __forceinline__ void sum_partials(const double* partial, int nv, double* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nb = gridDim.x;
   for (int v = wid; v < nv; v += AR_THREADS / 32) {
     double t = 0.0;
-    for (int b = lane; b < nb; b += 32) t += partial[(long long)v * nb + b];
+    for (int b = lane; b < nb; b += 32) t += __ldcg(&partial[(long long)v * nb + b]);
     t = warp_sum(t);
     if (lane == 0) out[v] = t;
   }
   __syncthreads();
 }
 
-struct ArnoldiState {
-  double* H;           // ldh x m, column-major
-  int ldh;
-  double* h1;          // h1 of the current step (AR_MAXV)
-  double* h2;          // h2 of the current step (AR_MAXV)
-  double* w0n2;        // ||w||^2 before orthogonalisation, current step
-  int* steps_hist;     // m + 1 entries, [0] = -1
-};
-
-// Finalize of step t-1 from ||w||^2 = hn2: H column, breakdown state; returns the scale of
-// the next basis vector (0 once broken down).  Block 0 stores; every block computes.
-__device__ __forceinline__ double arnoldi_close_step(const ArnoldiState& st, int t, double hn2) {
-  const bool active = st.steps_hist[t - 1] < 0;
-  const double hn = sqrt(hn2);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const int j = t - 1;
-    for (int i = 0; i <= j; ++i) st.H[i + (long long)j * st.ldh] = active ? st.h1[i] + st.h2[i] : 0.0;
-    st.H[j + 1 + (long long)j * st.ldh] = active ? hn : 0.0;
-    st.steps_hist[t] = (active && hn <= 1e-10 * sqrt(*st.w0n2)) ? t : st.steps_hist[t - 1];
-  }
-  return (active && hn > 0.0) ? 1.0 / hn : 0.0;
-}
-
 template <int W>
 __global__ void __launch_bounds__(AR_THREADS)
 arnoldi_k1(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ av,
            const double* __restrict__ dinv, int n, double* __restrict__ V, int j,
-           const double* __restrict__ wprev, ArnoldiState st, const double* __restrict__ pin,
-           double* __restrict__ w, double* __restrict__ partial) {
-  __shared__ double red[1];
-  double sc = 1.0;  // v_0 is normalised already
-  if (j > 0) {
-    sum_partials(pin, gridDim.x, 1, red);
-    sc = arnoldi_close_step(st, j, red[0]);
-  }
+           const double* __restrict__ wprev, ArnoldiState st, double* __restrict__ w,
+           double* __restrict__ partial) {
+  __shared__ double hs[AR_MAXV + 2];
+  const double sc = j > 0 ? *st.scale : 1.0;  // v_0 is normalised already
   constexpr int GPW = 32 / W;
   double acc[AR_MAXV + 2];
 #pragma unroll
@@ -814,8 +808,7 @@ arnoldi_k1(const int* __restrict__ rp, const int* __restrict__ ci, const double*
   for (long long base = warp * GPW; base < n; base += nwarps * GPW) {  // warp-uniform trips
     const long long i = base + grp;
     double s = 0.0;
-    if (i < n)
-      s = csr_row_dot<W>(ci, av, wprev, rp[i], rp[i + 1], sub);
+    if (i < n) s = csr_row_dot<W>(ci, av, wprev, rp[i], rp[i + 1], sub);
     s = group_sum<W>(s);
     if (sub == 0 && i < n) {
       const double wi = dinv[i] * (sc * s);
@@ -831,33 +824,29 @@ arnoldi_k1(const int* __restrict__ rp, const int* __restrict__ ci, const double*
     }
   }
   block_reduce_to_partial<AR_MAXV + 2>(acc, AR_MAXV + 2, partial);
+  if (!last_block(st.ticket)) return;
+  sum_partials(partial, AR_MAXV + 2, hs);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k <= j; ++k) st.h1[k] = hs[k];
+    *st.w0n2 = hs[AR_MAXV + 1];
+    *st.ticket = 0u;
+  }
 }
 
-// FIRST: h1 (and ||w||^2 before CGS) from K1's partials, w -= V h1, partial dots with
-// v_0..v_j.  Otherwise: h2 from the first pass's partials, w -= V h2, partial ||w||^2.
+// FIRST: w -= V h1, dots of the new w with v_0..v_j -> h2.  Otherwise: w -= V h2,
+// ||w||^2 -> the step's H column, breakdown state and the scale of v_{j+1}.
 template <bool FIRST>
 __global__ void __launch_bounds__(AR_THREADS)
-arnoldi_cgs(const double* __restrict__ V, int j, int n, ArnoldiState st,
-            const double* __restrict__ pin, double* __restrict__ w, double* __restrict__ partial) {
-  __shared__ double hs[AR_MAXV + 2];
-  if (FIRST) {
-    // K1 wrote AR_MAXV + 2 values per block: <v_k, w> for k <= j, slot AR_MAXV + 1 <w, w>
-    sum_partials(pin, gridDim.x, AR_MAXV + 2, hs);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      for (int k = 0; k <= j; ++k) st.h1[k] = hs[k];
-      *st.w0n2 = hs[AR_MAXV + 1];
-    }
-  } else {
-    sum_partials(pin, gridDim.x, j + 1, hs);
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-      for (int k = 0; k <= j; ++k) st.h2[k] = hs[k];
-  }
+arnoldi_cgs(const double* __restrict__ V, int j, int n, ArnoldiState st, double* __restrict__ w,
+            double* __restrict__ partial) {
+  __shared__ double hs[AR_MAXV + 1];
+  const double* h = FIRST ? st.h1 : st.h2;
   double acc[AR_MAXV + 1];
 #pragma unroll
   for (int v = 0; v < AR_MAXV + 1; ++v) acc[v] = 0.0;
   double hk[AR_MAXV];
 #pragma unroll
-  for (int k = 0; k < AR_MAXV; ++k) hk[k] = k <= j ? hs[k] : 0.0;
+  for (int k = 0; k < AR_MAXV; ++k) hk[k] = k <= j ? h[k] : 0.0;
   for (long long i = blockIdx.x * (long long)AR_THREADS + threadIdx.x; i < n;
        i += (long long)gridDim.x * AR_THREADS) {
     double vk[AR_MAXV];
@@ -877,40 +866,40 @@ arnoldi_cgs(const double* __restrict__ V, int j, int n, ArnoldiState st,
     }
   }
   block_reduce_to_partial<AR_MAXV + 1>(acc, FIRST ? j + 1 : 1, partial);
-}
-
-// The last step's finalize (one block).
-__global__ void __launch_bounds__(AR_THREADS)
-arnoldi_last(ArnoldiState st, int m, const double* __restrict__ pin, int nb) {
-  __shared__ double red[1];
-  sum_partials(pin, nb, 1, red);
-  arnoldi_close_step(st, m, red[0]);
+  if (!last_block(st.ticket)) return;
+  sum_partials(partial, FIRST ? j + 1 : 1, hs);
+  if (threadIdx.x != 0) return;
+  if (FIRST) {
+    for (int k = 0; k <= j; ++k) st.h2[k] = hs[k];
+  } else {
+    // close step j: H column, breakdown test, scale of the next basis vector
+    const bool active = st.steps_hist[j] < 0;
+    const double hn = sqrt(hs[0]);
+    for (int i = 0; i <= j; ++i) st.H[i + (long long)j * st.ldh] = active ? st.h1[i] + st.h2[i] : 0.0;
+    st.H[j + 1 + (long long)j * st.ldh] = active ? hn : 0.0;
+    st.steps_hist[j + 1] = (active && hn <= 1e-10 * sqrt(*st.w0n2)) ? j + 1 : st.steps_hist[j];
+    *st.scale = (active && hn > 0.0) ? 1.0 / hn : 0.0;
+  }
+  *st.ticket = 0u;
 }
 
 // w of step j lives in wbuf[j & 1] while K1 gathers v_j from the previous step's w in the
-// other buffer; kernel t (3 per step) writes partial buffer t & 1 and reads the other.
+// other buffer.  nb blocks: up to four per SM (the register limit of these kernels), fewer
+// on small levels.
 static void arnoldi_fused_steps(const Csr& A, const double* dinv, int m, double* V,
-                                double* const wbuf[2], const ArnoldiState& st,
-                                double* const pbuf[2], cudaStream_t s) {
+                                double* const wbuf[2], const ArnoldiState& st, double* partial,
+                                int nb, cudaStream_t s) {
   const int n = A.rows;
-  const int nb = partial_blocks();
   const int W = lanes_of(A, true);
-  int t = 0;
   for (int j = 0; j < m; ++j) {
     double* w = wbuf[j & 1];
     const double* wprev = j == 0 ? V : wbuf[(j + 1) & 1];
     CLAIR_DISPATCH_W2(W, (arnoldi_k1<WW><<<nb, AR_THREADS, 0, s>>>(A.rowptr, A.col, A.val, dinv, n,
-                                                                  V, j, wprev, st, pbuf[(t + 1) & 1],
-                                                                  w, pbuf[t & 1])));
-    ++t;
-    arnoldi_cgs<true><<<nb, AR_THREADS, 0, s>>>(V, j, n, st, pbuf[(t + 1) & 1], w, pbuf[t & 1]); ::clair::count_launch();
-    ++t;
-    arnoldi_cgs<false><<<nb, AR_THREADS, 0, s>>>(V, j, n, st, pbuf[(t + 1) & 1], w, pbuf[t & 1]); ::clair::count_launch();
-    ++t;
+                                                                  V, j, wprev, st, w, partial)));
+    arnoldi_cgs<true><<<nb, AR_THREADS, 0, s>>>(V, j, n, st, w, partial); ::clair::count_launch();
+    arnoldi_cgs<false><<<nb, AR_THREADS, 0, s>>>(V, j, n, st, w, partial); ::clair::count_launch();
     CLAIR_LAUNCHED();
   }
-  arnoldi_last<<<1, AR_THREADS, 0, s>>>(st, m, pbuf[(t + 1) & 1], nb); ::clair::count_launch();
-  CLAIR_LAUNCHED();
 }
 
 // ---- Ritz values on the host --------------------------------------------------------
@@ -1240,17 +1229,21 @@ double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed
   CLAIR_LAUNCHED();
   int* steps_hist = nullptr;
   if (m <= AR_MAXV) {
+    const int W = lanes_of(A, true);
+    const int nb = std::max(1, std::min(4 * sm_count(), ceil_div((long long)n * W, AR_THREADS)));
     double* w2 = dalloc<double>(n, s);
-    double* p2 = dalloc<double>((size_t)partial_blocks() * (AR_MAXV + 2), s);
+    double* p2 = dalloc<double>((size_t)nb * (AR_MAXV + 2), s);
     steps_hist = dalloc<int>(m + 1, s);
+    unsigned* ticket = dalloc<unsigned>(1, s);
     CLAIR_CUDA(cudaMemsetAsync(steps_hist, 0xff, sizeof(int) * (m + 1), s));  // -1
+    CLAIR_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
     double* const wbuf[2] = {w, w2};
-    double* const pbuf[2] = {partial, p2};
-    const ArnoldiState st{H, ldh, h1, h2, sc + 129, steps_hist};
-    arnoldi_fused_steps(A, dinv, m, V, wbuf, st, pbuf, s);
+    const ArnoldiState st{H, ldh, h1, h2, sc + 129, sc + 131, steps_hist, ticket};
+    arnoldi_fused_steps(A, dinv, m, V, wbuf, st, p2, nb, s);
     CLAIR_CUDA(cudaMemcpyAsync(steps, steps_hist + m, sizeof(int), cudaMemcpyDeviceToDevice, s));
     dfree(w2, s);
     dfree(p2, s);
+    dfree(ticket, s);
   }
   for (int j = 0; j < m && m > AR_MAXV; ++j) {
     double* vj = V + (size_t)j * n;
