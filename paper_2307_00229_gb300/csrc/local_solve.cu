@@ -133,13 +133,16 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
   for (int q = 0; q < G; ++q) a[q] = tile[gib][p][q];
   Real b = rhs_s[gib][p];
 
-  // elimination with implicit partial pivoting
+  // elimination with implicit partial pivoting; steps and columns beyond the largest
+  // system of the warp are no-ops for every group, so the loops stop there (warp-uniform)
+  const int Tw = __reduce_max_sync(0xffffffffu, live ? T : 0);
   bool done = !(live && p < T);
   int mystep = -1;
   int pivlane[G];
   bool singular = false;
 #pragma unroll
   for (int k = 0; k < G; ++k) {
+    if (k >= Tw) break;
     Real v = done ? Real(-1) : (a[k] < 0 ? -a[k] : a[k]);
     int who = p;
 #pragma unroll
@@ -164,6 +167,7 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
     }
 #pragma unroll
     for (int j = k + 1; j < G; ++j) {
+      if (j >= Tw) break;
       const Real pj = __shfl_sync(0xffffffffu, a[j], who, G);
       a[j] -= l * pj;
     }
@@ -173,6 +177,7 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
   Real myx = 0;
 #pragma unroll
   for (int k = G - 1; k >= 0; --k) {
+    if (k >= Tw) continue;
     const int own = pivlane[k];
     Real xk = (p == own && a[k] != Real(0)) ? b / a[k] : Real(0);
     xk = __shfl_sync(0xffffffffu, xk, own, G);
