@@ -31,6 +31,10 @@ if ROOT not in sys.path:
 METRIC = "R rows/s in setup; time-to-1e-8 rel residual, mixed vs FP64 path, 1 GB300"
 UNIT = "R rows/s"
 PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# DRAM bytes (read + write) of the local-solve launches of one step of the default workload,
+# from the ncu capture summarised in profiles/launches_setup_solve_1024sq.md; None once those
+# kernels change without a new capture.
+LSOLVE_DRAM_BYTES_PER_STEP = 505_901_312
 
 
 def parse():
@@ -275,7 +279,10 @@ def run_clair(args):
     vcycle_ms = phases["vcycle"] / max(its, 1)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x 2 x max clock
     lsolve = {"bound": "alu", "achieved": st.lsolve_flops / (phases["local_solve"] * 1e-3) / 1e12,
-              "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,
+              "peak": fp32_peak, "unit": "TFLOP/s",
+              "traffic": LSOLVE_DRAM_BYTES_PER_STEP,
+              "traffic_scope": "per step, all local-solve launches (profiles/launches_setup_solve_1024sq.md)",
+              "algorithmic_bytes": st.lsolve_min_bytes,
               "kernel": "lsolve_group/lsolve_cta (FP32 batched local LU)",
               "share_of_step": phases["local_solve"] / mixed["ms"]}
     lsolve["frac"] = lsolve["achieved"] / lsolve["peak"]
