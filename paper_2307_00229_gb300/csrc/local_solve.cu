@@ -63,6 +63,7 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
   constexpr int GPW = 32 / G;
   __shared__ int zl[LS_WARPS * GPW][G];
   __shared__ int pre[LS_WARPS * GPW][G + 1];
+  __shared__ int rs[LS_WARPS * GPW][G];  // start of each pattern row in Ahat
   __shared__ Real rhs_s[LS_WARPS * GPW][G];
   __shared__ Real tile[LS_WARPS * GPW][G][G + 1];
   const int lane = threadIdx.x & 31;
@@ -102,6 +103,7 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
   rhs_s[gib][p] = Real(0);
   const int row0 = (live && p < T) ? Arp[fcol] : 0;
   int rlen = (live && p < T) ? Arp[fcol + 1] - row0 : 0;
+  rs[gib][p] = row0;
 #pragma unroll
   for (int o = 1; o < G; o <<= 1) {
     const int t = __shfl_up_sync(0xffffffffu, rlen, o, G);
@@ -111,13 +113,16 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
   if (p == 0) pre[gib][0] = 0;
   __syncwarp();
   const int total = pre[gib][G];
+  // entry indices come from shared memory, so the loads of different entries are
+  // independent (no global row-pointer load in front of each)
+#pragma unroll 4
   for (int t = p; t < total; t += G) {
     int lo = 0, hi = G;  // row r with pre[r] <= t < pre[r + 1]
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
       if (pre[gib][mid] <= t) lo = mid; else hi = mid;
     }
-    const int e = Arp[zl[gib][lo]] + (t - pre[gib][lo]);
+    const int e = rs[gib][lo] + (t - pre[gib][lo]);
     const int c = Acol[e];
     if (c == i) {
       rhs_s[gib][lo] = Real(-Aval[e]);
@@ -127,7 +132,6 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
     }
   }
   __syncwarp();
-  (void)row0;
   Real a[G];
 #pragma unroll
   for (int q = 0; q < G; ++q) a[q] = tile[gib][p][q];
@@ -241,7 +245,10 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
   // flattened gather: block scan of the row lengths, then all threads over the entries
   __shared__ int pre[TMAX + 1];
   __shared__ int wsum[TMAX / 32];
-  int rlen = t < T ? Arp[zl[t] + 1] - Arp[zl[t]] : 0;
+  __shared__ int rs[TMAX];  // start of each pattern row in Ahat
+  const int rstart = t < T ? Arp[zl[t]] : 0;
+  rs[t] = rstart;
+  int rlen = t < T ? Arp[zl[t] + 1] - rstart : 0;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int v = __shfl_up_sync(0xffffffffu, rlen, o);
@@ -254,13 +261,14 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
   if (t == 0) pre[0] = 0;
   __syncthreads();
   const int total = pre[TMAX];
+#pragma unroll 4
   for (int f = t; f < total; f += TMAX) {
     int lo = 0, hi = TMAX;  // row r with pre[r] <= f < pre[r + 1]
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
       if (pre[mid] <= f) lo = mid; else hi = mid;
     }
-    const int e = Arp[zl[lo]] + (f - pre[lo]);
+    const int e = rs[lo] + (f - pre[lo]);
     const int c = Acol[e];
     if (c == i) {
       rhs[lo] = Real(-Aval[e]);
