@@ -167,6 +167,25 @@ def level_summary(cl, h):
 
 
 # ----------------------------------------------------------------------------------------
+# Several GPUs: independent replicas (the path does not shard across GPUs on this system);
+# every rank runs the same workload, the job's time is the slowest rank's.
+# ----------------------------------------------------------------------------------------
+def slowest_rank_ms(ms, dist=None, device=None):
+    """Max over ranks of the per-step time (all-reduce MAX; the local value alone at N=1)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rows_per_s(rows_per_rank, world, ms):
+    """Whole-job throughput: every rank builds `rows_per_rank` R rows in `ms` (weak scaling)."""
+    return world * rows_per_rank / (ms / 1e3)
+
+
+# ----------------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------------
 def run_clair(args):
@@ -244,11 +263,7 @@ def run_clair(args):
         launches = cl.clair_kernel_launches() - launches0
         if dist:
             dist.barrier()
-        ms = statistics.mean(times)
-        if dist:
-            tt = torch.tensor([ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = slowest_rank_ms(statistics.mean(times), dist, dev)
         bytes_h2d = sum(x.numel() * x.element_size() for x in host.values()) if e2e else 0
         return {"ms": ms, "times": times, "its": its_l, "rel": rel_l, "stats": stats[0],
                 "levels": stats[1], "wall": wall, "launches": launches // max(steps, 1),
@@ -269,7 +284,7 @@ def run_clair(args):
 
     st = mixed["stats"]
     rows = int(st.r_rows)
-    value = world * rows / (mixed["ms"] / 1e3)
+    value = job_rows_per_s(rows, world, mixed["ms"])
     pk, pk_kind = peaks()
     phases = {name: st.phase_ms[i] for i, name in enumerate(cl.PHASES[:8])}
     phases.update({name: st.solve_phase_ms[i] for i, name in enumerate(cl.PHASES) if i >= 8})
@@ -312,11 +327,11 @@ def run_clair(args):
         "phases_ms": phases,
         "fp64": None if fp64 is None else {
             "ms_per_step": fp64["ms"], "iterations": fp64["its"][-1], "relres": fp64["rel"][-1],
-            "setup_ms": fp64["stats"].setup_ms, "value": world * rows / (fp64["ms"] / 1e3),
+            "setup_ms": fp64["stats"].setup_ms, "value": job_rows_per_s(rows, world, fp64["ms"]),
             "local_solve_ms": fp64["stats"].phase_ms[4]},
         "mixed_speedup_vs_fp64": None if fp64 is None else fp64["ms"] / mixed["ms"],
         "e2e": None if e2e is None else {
-            "value": world * rows / (e2e["ms"] / 1e3), "unit": UNIT,
+            "value": job_rows_per_s(rows, world, e2e["ms"]), "unit": UNIT,
             "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
             "ms_per_step": e2e["ms"]},
         "roofline": dominant, "roofline_other": other,
