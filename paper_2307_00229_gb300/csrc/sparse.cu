@@ -934,6 +934,191 @@ spgemm_large(const int* __restrict__ Arp, const int* __restrict__ Acol,
   }
 }
 
+// One CTA per row for long products (coarse levels: thousands of products per row, few
+// rows).  Warp w takes a contiguous range of the row's A entries (ranges in increasing k)
+// and forms its products into a private shared table as the flat tiers do; the tables are
+// then merged into one in warp order, so every output is (((t_0 + t_1) + t_2) + ...) of
+// the warps' partial sums: deterministic, independent of scheduling.  A row whose A row
+// exceeds SGC_WARPS * SGC_PCAP entries, or whose warp tables or merged table overflow,
+// gets count -1 (symbolic) and goes to the large table.
+constexpr int SGC_WARPS = 8;
+constexpr int SGC_WCAP = 1024;  // slots of each warp's table
+constexpr int SGC_MCAP = 4096;  // slots of the merged table
+constexpr int SGC_PCAP = 256;   // A entries per warp
+
+__host__ __device__ constexpr size_t sgc_bytes(bool numeric) {
+  return SGC_WARPS * (sizeof(int) * SGC_WCAP + (numeric ? sizeof(double) * SGC_WCAP : 0) +
+                      sizeof(int) * (SGC_PCAP + 8) + sizeof(double) * 32) +
+         sizeof(int) * SGC_MCAP + (numeric ? sizeof(double) * SGC_MCAP : 0) +
+         sizeof(int) * (32 * SGC_WARPS + 8);
+}
+
+template <bool NUMERIC>
+__global__ void __launch_bounds__(32 * SGC_WARPS)
+spgemm_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
+           const double* __restrict__ Aval, const int* __restrict__ Brp,
+           const int* __restrict__ Bcol, const double* __restrict__ Bval, int rows,
+           const int* __restrict__ route, int* __restrict__ count, const int* __restrict__ Crp,
+           int* __restrict__ Ccol, double* __restrict__ Cval) {
+  extern __shared__ __align__(16) unsigned char sgc_smem[];
+  constexpr int NT = 32 * SGC_WARPS;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
+  // layout: doubles first (8-byte aligned), then ints
+  double* wvals_all = reinterpret_cast<double*>(sgc_smem);                       // WARPS x WCAP
+  double* mvals = wvals_all + (NUMERIC ? SGC_WARPS * SGC_WCAP : 0);              // MCAP
+  double* stage_all = mvals + (NUMERIC ? SGC_MCAP : 0);                          // WARPS x 32
+  int* wkeys_all = reinterpret_cast<int*>(stage_all + SGC_WARPS * 32);           // WARPS x WCAP
+  int* mkeys = wkeys_all + SGC_WARPS * SGC_WCAP;                                 // MCAP
+  int* pre_all = mkeys + SGC_MCAP;                                               // WARPS x (PCAP+8)
+  int* part = pre_all + SGC_WARPS * (SGC_PCAP + 8);                              // NT + 8
+  __shared__ int s_full, s_total;
+  double* wvals = wvals_all + w * SGC_WCAP;
+  double* stage = stage_all + w * 32;
+  int* wkeys = wkeys_all + w * SGC_WCAP;
+  int* prefix = pre_all + w * (SGC_PCAP + 8);
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {  // block-uniform
+    const int a0 = Arp[r], nA = Arp[r + 1] - a0;
+    if (nA > SGC_WARPS * SGC_PCAP) {
+      if (!NUMERIC && t == 0) count[r] = -1;
+      continue;
+    }
+    if (NUMERIC && route[r]) continue;  // the large table computes this row
+    if (t == 0) {
+      s_full = 0;
+      s_total = 0;
+    }
+    for (int q = t; q < SGC_MCAP; q += NT) {
+      mkeys[q] = -1;
+      if (NUMERIC) mvals[q] = 0.0;
+    }
+    for (int q = lane; q < SGC_WCAP; q += 32) {
+      wkeys[q] = -1;
+      if (NUMERIC) wvals[q] = 0.0;
+    }
+    __syncthreads();  // the row's flags are reset before any warp can raise one
+    // this warp's A entries [lo, hi) and the prefix of their B-row lengths
+    const int chunk = (nA + SGC_WARPS - 1) / SGC_WARPS;
+    const int lo = min(nA, w * chunk), hi = min(nA, lo + chunk), nw = hi - lo;
+    int base = 0;
+    for (int c = 0; c < nw; c += 32) {
+      int len = 0;
+      if (c + lane < nw) {
+        const int k = Acol[a0 + lo + c + lane];
+        len = Brp[k + 1] - Brp[k];
+      }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (c + lane < nw) prefix[c + lane + 1] = base + incl;
+      base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) prefix[0] = 0;
+    __syncwarp();
+    const int total = base;
+    bool full = false;
+    for (int p0 = 0; p0 < total; p0 += 32) {
+      const int p = p0 + lane;
+      int slot = -1;
+      double prod = 0.0;
+      if (p < total) {
+        int l = 0, h = nw;  // largest t with prefix[t] <= p
+        while (h - l > 1) {
+          const int mid = (l + h) >> 1;
+          if (prefix[mid] <= p) l = mid; else h = mid;
+        }
+        const int ea = a0 + lo + l;
+        const int k = Acol[ea];
+        const int eb = Brp[k] + (p - prefix[l]);
+        bool is_new = false;
+        slot = sg_insert(wkeys, SGC_WCAP, Bcol[eb], &is_new);
+        if (slot < 0) full = true;
+        if (NUMERIC) prod = __dmul_rn(Aval[ea], Bval[eb]);
+      }
+      if (__any_sync(0xffffffffu, full)) break;
+      if (NUMERIC) {
+        stage[lane] = prod;
+        const unsigned grp = __match_any_sync(0xffffffffu, slot);
+        __syncwarp();
+        if (slot >= 0 && lane == __ffs(grp) - 1) {
+          double sum = prod;
+          for (unsigned g = grp & (grp - 1); g; g &= g - 1) sum = __dadd_rn(sum, stage[__ffs(g) - 1]);
+          wvals[slot] = __dadd_rn(wvals[slot], sum);
+        }
+        __syncwarp();
+      }
+    }
+    const bool wfull = __any_sync(0xffffffffu, full);  // the whole warp votes
+    if (wfull && lane == 0) s_full = 1;
+    __syncthreads();
+    // merge the warp tables into the merged table, one warp's table after another
+    for (int v = 0; v < SGC_WARPS && !s_full; ++v) {
+      const int* vk = wkeys_all + v * SGC_WCAP;
+      const double* vv = wvals_all + v * SGC_WCAP;
+      for (int q = t; q < SGC_WCAP; q += NT) {
+        const int key = vk[q];
+        if (key < 0) continue;
+        bool is_new = false;
+        const int slot = sg_insert(mkeys, SGC_MCAP, key, &is_new);
+        if (slot < 0) {
+          s_full = 1;
+        } else {
+          if (is_new) atomicAdd(&s_total, 1);
+          if (NUMERIC) mvals[slot] = __dadd_rn(mvals[slot], vv[q]);  // keys distinct per table
+        }
+      }
+      __syncthreads();
+    }
+    if (s_full) {  // block-uniform after the barrier
+      if (!NUMERIC && t == 0) count[r] = -1;
+      __syncthreads();
+      continue;
+    }
+    const int ntot = s_total;
+    if (!NUMERIC) {
+      if (t == 0) count[r] = ntot;
+      __syncthreads();
+      continue;
+    }
+    // compact the merged table (thread t owns slots [t*16, t*16+16)) into warp 0's arrays
+    constexpr int PER = SGC_MCAP / NT;
+    int c = 0;
+    for (int q = t * PER; q < (t + 1) * PER; ++q) c += mkeys[q] >= 0;
+    part[t + 1] = c;
+    if (t == 0) part[0] = 0;
+    __syncthreads();
+    if (t == 0)
+      for (int q = 1; q <= NT; ++q) part[q] += part[q - 1];
+    __syncthreads();
+    int o = part[t];
+    for (int q = t * PER; q < (t + 1) * PER; ++q)
+      if (mkeys[q] >= 0) {
+        wkeys_all[o] = mkeys[q];
+        wvals_all[o] = mvals[q];
+        ++o;
+      }
+    __syncthreads();
+    const int cbase = Crp[r];
+    for (int q = t; q < ntot; q += NT) {
+      const int key = wkeys_all[q];
+      int rank = 0;
+      for (int u = 0; u < ntot; ++u) rank += wkeys_all[u] < key;
+      Ccol[cbase + rank] = key;
+      Cval[cbase + rank] = wvals_all[q];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void sg_mark_rows(const int* __restrict__ list, const int* __restrict__ dn,
+                             int* __restrict__ route) {
+  const int n = *dn;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+    route[list[q]] = 1;
+}
+
 // Lists (from `src` rows, or all rows when src == nullptr) the rows with count == -1
 // (mode 0) or, mode 1, the rows a numeric tier left out: more than `lim_cnt` output
 // entries or more than `lim_nA` A entries.
@@ -999,6 +1184,70 @@ void drop_zeros(Csr& C, cudaStream_t s) {
   C.nnz = nnz;
 }
 
+// Long products: the CTA-per-row kernel for every row, the large table for the rows it
+// could not hold.
+static void spgemm_cta_path(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
+  const int rows = A.rows;
+  static bool attr = false;
+  if (!attr) {
+    CLAIR_CUDA(cudaFuncSetAttribute(spgemm_cta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sgc_bytes(false)));
+    CLAIR_CUDA(cudaFuncSetAttribute(spgemm_cta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sgc_bytes(true)));
+    CLAIR_CUDA(cudaFuncSetAttribute(spgemm_large<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(int) * SG_LARGE)));
+    CLAIR_CUDA(cudaFuncSetAttribute(spgemm_large<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((sizeof(int) + sizeof(double)) * SG_LARGE)));
+    attr = true;
+  }
+  const int sms = sm_count();
+  int* count = dalloc<int>(rows + 1, s);
+  int* route = dalloc<int>(rows, s);
+  int* list = dalloc<int>(rows, s);
+  int* list2 = dalloc<int>(rows, s);
+  int* nlist = dalloc<int>(2, s);
+  CLAIR_CUDA(cudaMemsetAsync(route, 0, sizeof(int) * rows, s));
+  CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 2 * sizeof(int), s));
+  const int gsym = std::min(rows, 3 * sms), gnum = std::min(rows, sms);
+  spgemm_cta<false><<<gsym, 32 * SGC_WARPS, sgc_bytes(false), s>>>(
+      A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, rows, route, count, nullptr, nullptr, nullptr); ::clair::count_launch();
+  spgemm_collect<<<std::max(1, std::min(ceil_div(rows, 256), sms * 8)), 256, 0, s>>>(
+      count, nullptr, A.rowptr, nullptr, rows, nullptr, 0, 0, 0, list, nlist); ::clair::count_launch();
+  sg_mark_rows<<<std::max(1, std::min(ceil_div(rows, 256), sms * 8)), 256, 0, s>>>(list, nlist, route); ::clair::count_launch();
+  spgemm_large<false><<<std::max(1, std::min(rows, sms)), 32, sizeof(int) * SG_LARGE, s>>>(
+      A.rowptr, A.col, A.val, list, nlist, B.rowptr, B.col, B.val, count, nullptr, nullptr, nullptr); ::clair::count_launch();
+  spgemm_collect<<<std::max(1, std::min(ceil_div(rows, 256), sms * 8)), 256, 0, s>>>(
+      count, nullptr, A.rowptr, list, rows, nlist, 0, 0, 0, list2, nlist + 1); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  C.rowptr = dalloc<int>(rows + 1, s);
+  C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true);  // synchronises s
+  int still = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&still, nlist + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  if (still) {
+    dfree(count, s);
+    dfree(route, s);
+    dfree(list, s);
+    dfree(list2, s);
+    dfree(nlist, s);
+    dfree(C.rowptr, s);
+    CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "SpGEMM: %d rows exceed %d distinct columns", still,
+                  SG_LARGE);
+  }
+  C.col = dalloc<int>(C.nnz, s);
+  C.val = dalloc<double>(C.nnz, s);
+  spgemm_cta<true><<<gnum, 32 * SGC_WARPS, sgc_bytes(true), s>>>(
+      A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, rows, route, count, C.rowptr, C.col, C.val); ::clair::count_launch();
+  spgemm_large<true><<<std::max(1, std::min(rows, sms)), 32, (sizeof(int) + sizeof(double)) * SG_LARGE, s>>>(
+      A.rowptr, A.col, A.val, list, nlist, B.rowptr, B.col, B.val, count, C.rowptr, C.col, C.val); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  dfree(count, s);
+  dfree(route, s);
+  dfree(list, s);
+  dfree(list2, s);
+  dfree(nlist, s);
+}
+
 // Tier 0 runs over every row; each later tier (and the large table) runs over the rows the
 // previous one listed, with a grid-stride loop over a count it reads on the device, so the
 // tiers follow one another without a host round trip.  The host reads back once, with the
@@ -1007,6 +1256,13 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   C.rows = A.rows;
   C.cols = B.cols;
   const int rows = A.rows;
+  // long products (mean products per row ~ mean A row x mean B row): one CTA per row
+  const double mean_products =
+      (rows ? (double)A.nnz / rows : 0.0) * (B.rows ? (double)B.nnz / B.rows : 0.0);
+  if (rows && mean_products >= 1024.0) {
+    spgemm_cta_path(A, B, C, s);
+    return;
+  }
   int* count = dalloc<int>(rows + 1, s);
   int* lists[2] = {dalloc<int>(std::max(rows, 1), s), dalloc<int>(std::max(rows, 1), s)};
   int* nlist = dalloc<int>(8, s);
