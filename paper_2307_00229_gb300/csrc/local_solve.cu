@@ -66,6 +66,7 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
   __shared__ int rs[LS_WARPS * GPW][G];  // start of each pattern row in Ahat
   __shared__ Real rhs_s[LS_WARPS * GPW][G];
   __shared__ Real tile[LS_WARPS * GPW][G][G + 1];
+  __shared__ int pivlane[LS_WARPS * GPW][G];  // lane that pivoted each elimination step
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int gsub = lane / G;          // group within warp
@@ -142,7 +143,6 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
   const int Tw = __reduce_max_sync(0xffffffffu, live ? T : 0);
   bool done = !(live && p < T);
   int mystep = -1;
-  int pivlane[G];
   bool singular = false;
 #pragma unroll
   for (int k = 0; k < G; ++k) {
@@ -158,7 +158,7 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
         who = w2;
       }
     }
-    pivlane[k] = who;
+    if (p == 0) pivlane[gib][k] = who;
     const bool step = k < T;
     if (step && !(v > Real(0))) singular = true;
     const Real pk = __shfl_sync(0xffffffffu, a[k], who, G);
@@ -177,12 +177,13 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
     }
     b -= l * pb;
   }
+  __syncwarp();  // the pivot lanes lane 0 stored are read by every lane below
   // back substitution (right-looking): x_k from the lane that pivoted step k
   Real myx = 0;
 #pragma unroll
   for (int k = G - 1; k >= 0; --k) {
     if (k >= Tw) continue;
-    const int own = pivlane[k];
+    const int own = pivlane[gib][k];
     Real xk = (p == own && a[k] != Real(0)) ? b / a[k] : Real(0);
     xk = __shfl_sync(0xffffffffu, xk, own, G);
     if (k < T) {
