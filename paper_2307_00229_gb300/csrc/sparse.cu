@@ -235,14 +235,18 @@ __global__ void count_cols(const int* __restrict__ col, int nnz, int* __restrict
     atomicAdd(&cnt[col[e]], 1);
 }
 
+// W lanes per row, so a long row is not one thread's chain of atomics; the slot order
+// within a column is arbitrary here and fixed by the segment sort that follows.
+template <int W>
 __global__ void transpose_fill(const int* __restrict__ rowptr, const int* __restrict__ col,
                                int rows, int* __restrict__ cursor, int* __restrict__ col_t,
                                int* __restrict__ perm) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long r = g / W;
   if (r >= rows) return;
-  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
-    int pos = atomicAdd(&cursor[col[e]], 1);
-    col_t[pos] = r;
+  for (int e = rowptr[r] + (int)(g % W); e < rowptr[r + 1]; e += W) {
+    const int pos = atomicAdd(&cursor[col[e]], 1);
+    col_t[pos] = (int)r;
     perm[pos] = e;
   }
 }
@@ -329,8 +333,18 @@ void csr_transpose(const Csr& A, Csr& At, int** perm_out, cudaStream_t s) {
   int* perm_fill = dalloc<int>(A.nnz, s);
   At.col = dalloc<int>(A.nnz, s);
   int* perm = dalloc<int>(A.nnz, s);
-  if (A.rows) transpose_fill<<<ceil_div(A.rows, 256), 256, 0, s>>>(A.rowptr, A.col, A.rows, cnt,
-                                                                     col_fill, perm_fill); ::clair::count_launch();
+  if (A.rows) {
+    const double mean = (double)A.nnz / A.rows;
+    const int W = mean <= 2.0 ? 1 : mean <= 8.0 ? 4 : mean <= 32.0 ? 8 : 32;
+    const int grid = (int)ceil_div((long long)A.rows * W, 256);
+    switch (W) {
+      case 1: transpose_fill<1><<<grid, 256, 0, s>>>(A.rowptr, A.col, A.rows, cnt, col_fill, perm_fill); break;
+      case 4: transpose_fill<4><<<grid, 256, 0, s>>>(A.rowptr, A.col, A.rows, cnt, col_fill, perm_fill); break;
+      case 8: transpose_fill<8><<<grid, 256, 0, s>>>(A.rowptr, A.col, A.rows, cnt, col_fill, perm_fill); break;
+      default: transpose_fill<32><<<grid, 256, 0, s>>>(A.rowptr, A.col, A.rows, cnt, col_fill, perm_fill); break;
+    }
+    ::clair::count_launch();
+  }
   if (At.rows) sort_segments_warp<<<ceil_div((long long)At.rows * 32, 256), 256, 0, s>>>(
       At.rowptr, At.rows, col_fill, perm_fill, At.col, perm); ::clair::count_launch();
   CLAIR_LAUNCHED();
@@ -945,6 +959,11 @@ constexpr int SGC_WARPS = 8;
 constexpr int SGC_WCAP = 1024;  // slots of each warp's table
 constexpr int SGC_MCAP = 4096;  // slots of the merged table
 constexpr int SGC_PCAP = 256;   // A entries per warp
+// Output order by a column bitmap over B's columns: rank(key) = set bits below key.  The
+// bitmap reuses the warp value tables (SGC_WARPS * SGC_WCAP doubles = 2 * that many
+// 32-bit words), and one prefix per group of 8 words reuses the warp key tables.
+constexpr int SGC_BITWORDS = 2 * SGC_WARPS * SGC_WCAP;   // 16384 words: 524288 columns
+constexpr int SGC_BITGROUPS = SGC_BITWORDS / 8;
 
 __host__ __device__ constexpr size_t sgc_bytes(bool numeric) {
   return SGC_WARPS * (sizeof(int) * SGC_WCAP + (numeric ? sizeof(double) * SGC_WCAP : 0) +
@@ -954,12 +973,12 @@ __host__ __device__ constexpr size_t sgc_bytes(bool numeric) {
 }
 
 template <bool NUMERIC>
-__global__ void __launch_bounds__(32 * SGC_WARPS)
+__global__ void __launch_bounds__(32 * SGC_WARPS, 2)  // shared memory allows 1-3 blocks per SM
 spgemm_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
            const double* __restrict__ Aval, const int* __restrict__ Brp,
            const int* __restrict__ Bcol, const double* __restrict__ Bval, int rows,
-           const int* __restrict__ route, int* __restrict__ count, const int* __restrict__ Crp,
-           int* __restrict__ Ccol, double* __restrict__ Cval) {
+           int ncols, const int* __restrict__ route, int* __restrict__ count,
+           const int* __restrict__ Crp, int* __restrict__ Ccol, double* __restrict__ Cval) {
   extern __shared__ __align__(16) unsigned char sgc_smem[];
   constexpr int NT = 32 * SGC_WARPS;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
@@ -1082,7 +1101,63 @@ spgemm_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
       __syncthreads();
       continue;
     }
-    // compact the merged table (thread t owns slots [t*16, t*16+16)) into warp 0's arrays
+    const int cbase = Crp[r];
+    const int nwords = (ncols + 31) >> 5;
+    if (nwords <= SGC_BITWORDS) {
+      // every output's position is the number of the row's columns below it: set one bit
+      // per column, prefix the bit counts of 8-word groups, then count within the group
+      unsigned* bits = reinterpret_cast<unsigned*>(wvals_all);
+      int* gpre = wkeys_all;
+      const int ngroups = (nwords + 7) >> 3;
+      for (int q = t; q < ngroups * 8; q += NT) bits[q] = 0u;
+      __syncthreads();
+      for (int q = t; q < SGC_MCAP; q += NT) {
+        const int key = mkeys[q];
+        if (key >= 0) atomicOr(&bits[key >> 5], 1u << (key & 31));
+      }
+      __syncthreads();
+      constexpr int GPT = SGC_BITGROUPS / NT;  // groups per thread, consecutive
+      const int g0 = t * GPT, g1 = min(ngroups, g0 + GPT);
+      int sum = 0;
+      for (int u = g0 * 8; u < g1 * 8; ++u) sum += __popc(bits[u]);
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (lane == 31) part[w] = incl;
+      __syncthreads();
+      if (w == 0) {
+        int x = lane < SGC_WARPS ? part[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += v;
+        }
+        if (lane < SGC_WARPS) part[lane] = x;  // inclusive warp totals
+      }
+      __syncthreads();
+      int run = incl - sum + (w > 0 ? part[w - 1] : 0);
+      for (int g = g0; g < g1; ++g) {
+        gpre[g] = run;
+        for (int u = 0; u < 8; ++u) run += __popc(bits[g * 8 + u]);
+      }
+      __syncthreads();
+      for (int q = t; q < SGC_MCAP; q += NT) {
+        const int key = mkeys[q];
+        if (key < 0) continue;
+        const int wd = key >> 5, g = key >> 8;
+        int rank = gpre[g] + __popc(bits[wd] & ((1u << (key & 31)) - 1u));
+        for (int u = g * 8; u < wd; ++u) rank += __popc(bits[u]);
+        Ccol[cbase + rank] = key;
+        Cval[cbase + rank] = mvals[q];
+      }
+      __syncthreads();
+      continue;
+    }
+    // wider B: compact the merged table (thread t owns slots [t*16, t*16+16)) into warp
+    // 0's arrays and rank each key by counting the smaller ones
     constexpr int PER = SGC_MCAP / NT;
     int c = 0;
     for (int q = t * PER; q < (t + 1) * PER; ++q) c += mkeys[q] >= 0;
@@ -1100,7 +1175,6 @@ spgemm_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
         ++o;
       }
     __syncthreads();
-    const int cbase = Crp[r];
     for (int q = t; q < ntot; q += NT) {
       const int key = wkeys_all[q];
       int rank = 0;
@@ -1210,7 +1284,8 @@ static void spgemm_cta_path(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) 
   CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 2 * sizeof(int), s));
   const int gsym = std::min(rows, 3 * sms), gnum = std::min(rows, sms);
   spgemm_cta<false><<<gsym, 32 * SGC_WARPS, sgc_bytes(false), s>>>(
-      A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, rows, route, count, nullptr, nullptr, nullptr); ::clair::count_launch();
+      A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, rows, B.cols, route, count, nullptr, nullptr,
+      nullptr); ::clair::count_launch();
   spgemm_collect<<<std::max(1, std::min(ceil_div(rows, 256), sms * 8)), 256, 0, s>>>(
       count, nullptr, A.rowptr, nullptr, rows, nullptr, 0, 0, 0, list, nlist); ::clair::count_launch();
   sg_mark_rows<<<std::max(1, std::min(ceil_div(rows, 256), sms * 8)), 256, 0, s>>>(list, nlist, route); ::clair::count_launch();
@@ -1237,7 +1312,8 @@ static void spgemm_cta_path(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) 
   C.col = dalloc<int>(C.nnz, s);
   C.val = dalloc<double>(C.nnz, s);
   spgemm_cta<true><<<gnum, 32 * SGC_WARPS, sgc_bytes(true), s>>>(
-      A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, rows, route, count, C.rowptr, C.col, C.val); ::clair::count_launch();
+      A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, rows, B.cols, route, count, C.rowptr, C.col,
+      C.val); ::clair::count_launch();
   spgemm_large<true><<<std::max(1, std::min(rows, sms)), 32, (sizeof(int) + sizeof(double)) * SG_LARGE, s>>>(
       A.rowptr, A.col, A.val, list, nlist, B.rowptr, B.col, B.val, count, C.rowptr, C.col, C.val); ::clair::count_launch();
   CLAIR_LAUNCHED();
@@ -1417,8 +1493,8 @@ void csr_transpose_ws(const Csr& A, Csr& At, int* perm, int* cnt, long long* sum
   if (A.nnz) count_cols<<<grid_for(A.nnz), 256, 0, s>>>(A.col, A.nnz, cnt); ::clair::count_launch();
   exclusive_scan_ws(cnt, At.rowptr, A.cols, s, false, sums, ovf);
   CLAIR_CUDA(cudaMemcpyAsync(cnt, At.rowptr, sizeof(int) * A.cols, cudaMemcpyDeviceToDevice, s));
-  if (A.rows) transpose_fill<<<ceil_div(A.rows, 256), 256, 0, s>>>(A.rowptr, A.col, A.rows, cnt,
-                                                                     At.col, perm); ::clair::count_launch();
+  if (A.rows) transpose_fill<1><<<ceil_div(A.rows, 256), 256, 0, s>>>(A.rowptr, A.col, A.rows, cnt,
+                                                                        At.col, perm); ::clair::count_launch();
   if (At.rows) sort_segments<<<ceil_div(At.rows, 128), 128, 0, s>>>(At.rowptr, At.rows, At.col, perm); ::clair::count_launch();
   CLAIR_LAUNCHED();
   if (A.val && At.val) gather(A.val, perm, At.val, A.nnz, s);
