@@ -52,6 +52,10 @@ __device__ __forceinline__ int find_sorted(const int* z, int T, int c) {
 // Sub-warp path: G lanes per system, G in {8, 16, 32}, T <= G.
 // ------------------------------------------------------------------------------------
 constexpr int LS_WARPS = 4;  // warps per block in the sub-warp path
+// Row updates of the shared- and global-tile solves read LS_CHUNK entries of the pivot
+// row and of the own row before writing any: both rows live in one array, so without
+// that the compiler must order every load after the previous store.
+constexpr int LS_CHUNK = 8;
 
 template <class Real, class VT, int G>
 __global__ void __launch_bounds__(32 * LS_WARPS)
@@ -205,8 +209,10 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
 // CTA path: one system per block of TMAX threads, T <= TMAX (64 or 128); the matrix
 // lives in shared memory, thread r owns row r.
 // ------------------------------------------------------------------------------------
+// shared memory holds these to about 1024 resident threads per SM, so the register
+// budget is set for that many (64 each) rather than for full occupancy
 template <class Real, class VT, int TMAX>
-__global__ void __launch_bounds__(TMAX)
+__global__ void __launch_bounds__(TMAX, 1024 / TMAX)
 lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
            const VT* __restrict__ Aval, const int* __restrict__ Zrp,
            const int* __restrict__ Zcol, const int* __restrict__ cpts,
@@ -319,7 +325,18 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
       mystep = k;
     } else if (!done && pk != Real(0)) {
       const Real l = row[k] / pk;
-      for (int j = k + 1; j < T; ++j) row[j] -= l * prow[j];
+      for (int j0 = k + 1; j0 < T; j0 += LS_CHUNK) {
+        Real pv[LS_CHUNK], rv[LS_CHUNK];
+#pragma unroll
+        for (int u = 0; u < LS_CHUNK; ++u)
+          if (j0 + u < T) {
+            pv[u] = prow[j0 + u];
+            rv[u] = row[j0 + u];
+          }
+#pragma unroll
+        for (int u = 0; u < LS_CHUNK; ++u)
+          if (j0 + u < T) row[j0 + u] = rv[u] - l * pv[u];
+      }
       rhs[t] -= l * rhs[piv];
     }
     __syncthreads();
@@ -356,7 +373,7 @@ constexpr int LB_THREADS = 256;
 
 template <class Real>
 __host__ __device__ constexpr size_t big_smem(int pitch) {
-  return (size_t)pitch * (3 * sizeof(int) + 2 * sizeof(Real)) + 2 * sizeof(Real);
+  return (size_t)pitch * (3 * sizeof(int) + 3 * sizeof(Real)) + 2 * sizeof(Real);
 }
 
 template <class Real, class VT>
@@ -369,7 +386,8 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
   extern __shared__ __align__(16) unsigned char lb_smem[];
   Real* rhs = reinterpret_cast<Real*>(lb_smem);
   Real* xs = rhs + pitch;
-  int* zl = reinterpret_cast<int*>(xs + pitch);
+  Real* prow = xs + pitch;  // the step's pivot row, columns k+1 .. T-1
+  int* zl = reinterpret_cast<int*>(prow + pitch);
   int* stepof = zl + pitch;
   int* steprow = stepof + pitch;
   __shared__ Real red_v[LB_THREADS / 32];
@@ -455,12 +473,22 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
     __syncthreads();
     const int piv = s_piv;
     const Real pk = colk[piv];
+    for (int j = k + 1 + t; j < T; j += LB_THREADS) prow[j] = M[(size_t)j * pitch + piv];
+    __syncthreads();
     for (int p = t; p < T; p += LB_THREADS)
       if (stepof[p] < 0 && pk != Real(0)) {
         const Real l = colk[p] / pk;
-        for (int j = k + 1; j < T; ++j) {
-          Real* colj = M + (size_t)j * pitch;
-          colj[p] -= l * colj[piv];
+        for (int j0 = k + 1; j0 < T; j0 += LS_CHUNK) {
+          Real pv[LS_CHUNK], rv[LS_CHUNK];
+#pragma unroll
+          for (int u = 0; u < LS_CHUNK; ++u)
+            if (j0 + u < T) {
+              pv[u] = prow[j0 + u];
+              rv[u] = M[(size_t)(j0 + u) * pitch + p];
+            }
+#pragma unroll
+          for (int u = 0; u < LS_CHUNK; ++u)
+            if (j0 + u < T) M[(size_t)(j0 + u) * pitch + p] = rv[u] - l * pv[u];
         }
         rhs[p] -= l * rhs[piv];
       }
