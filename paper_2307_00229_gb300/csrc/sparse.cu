@@ -956,13 +956,13 @@ spgemm_large(const int* __restrict__ Arp, const int* __restrict__ Acol,
 // exceeds SGC_WARPS * SGC_PCAP entries, or whose warp tables or merged table overflow,
 // gets count -1 (symbolic) and goes to the large table.
 constexpr int SGC_WARPS = 8;
-constexpr int SGC_WCAP = 1024;  // slots of each warp's table
+constexpr int SGC_WCAP = 512;   // slots of each warp's table (two numeric blocks fit an SM)
 constexpr int SGC_MCAP = 4096;  // slots of the merged table
 constexpr int SGC_PCAP = 256;   // A entries per warp
 // Output order by a column bitmap over B's columns: rank(key) = set bits below key.  The
 // bitmap reuses the warp value tables (SGC_WARPS * SGC_WCAP doubles = 2 * that many
 // 32-bit words), and one prefix per group of 8 words reuses the warp key tables.
-constexpr int SGC_BITWORDS = 2 * SGC_WARPS * SGC_WCAP;   // 16384 words: 524288 columns
+constexpr int SGC_BITWORDS = 2 * SGC_WARPS * SGC_WCAP;   // 8192 words: 262144 columns
 constexpr int SGC_BITGROUPS = SGC_BITWORDS / 8;
 
 __host__ __device__ constexpr size_t sgc_bytes(bool numeric) {
@@ -973,7 +973,7 @@ __host__ __device__ constexpr size_t sgc_bytes(bool numeric) {
 }
 
 template <bool NUMERIC>
-__global__ void __launch_bounds__(32 * SGC_WARPS, 2)  // shared memory allows 1-3 blocks per SM
+__global__ void __launch_bounds__(32 * SGC_WARPS, 2)  // shared memory: 2 numeric or 4 symbolic blocks per SM
 spgemm_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
            const double* __restrict__ Aval, const int* __restrict__ Brp,
            const int* __restrict__ Bcol, const double* __restrict__ Bval, int rows,
@@ -1282,7 +1282,7 @@ static void spgemm_cta_path(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) 
   int* nlist = dalloc<int>(2, s);
   CLAIR_CUDA(cudaMemsetAsync(route, 0, sizeof(int) * rows, s));
   CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 2 * sizeof(int), s));
-  const int gsym = std::min(rows, 3 * sms), gnum = std::min(rows, sms);
+  const int gsym = std::min(rows, 4 * sms), gnum = std::min(rows, 2 * sms);
   spgemm_cta<false><<<gsym, 32 * SGC_WARPS, sgc_bytes(false), s>>>(
       A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, rows, B.cols, route, count, nullptr, nullptr,
       nullptr); ::clair::count_launch();
