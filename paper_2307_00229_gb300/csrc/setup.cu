@@ -144,12 +144,17 @@ void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsign
   const int g = ceil_div(n, 256);
   pmis_init<<<g, 256, 0, s>>>(At.rowptr, sAt, n, lbase, key, state, mark); ::clair::count_launch();
   CLAIR_LAUNCHED();
-  for (int round = 0;; ++round) {
+  // Rounds go in groups of PMIS_ROUNDS between host checks: a round after the last
+  // undecided point is decided changes nothing, and the check reads the last round's count.
+  constexpr int PMIS_ROUNDS = 3;
+  for (int round = 0;;) {
     CLAIR_REQUIRE(round < 10000, CLAIR_ERR_CAPACITY, "C/F splitting did not terminate");
-    CLAIR_CUDA(cudaMemsetAsync(remaining, 0, sizeof(int), s));
-    pmis_select<<<g, 256, 0, s>>>(A.rowptr, A.col, sA, At.rowptr, At.col, sAt, n, key, state, mark,
-                                  round); ::clair::count_launch();
-    pmis_update<<<g, 256, 0, s>>>(A.rowptr, A.col, sA, n, mark, state, round, remaining); ::clair::count_launch();
+    for (int q = 0; q < PMIS_ROUNDS; ++q, ++round) {
+      CLAIR_CUDA(cudaMemsetAsync(remaining, 0, sizeof(int), s));
+      pmis_select<<<g, 256, 0, s>>>(A.rowptr, A.col, sA, At.rowptr, At.col, sAt, n, key, state,
+                                    mark, round); ::clair::count_launch();
+      pmis_update<<<g, 256, 0, s>>>(A.rowptr, A.col, sA, n, mark, state, round, remaining); ::clair::count_launch();
+    }
     CLAIR_LAUNCHED();
     int h = 0;
     CLAIR_CUDA(cudaMemcpyAsync(&h, remaining, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -268,15 +268,16 @@ __global__ void sort_segments(const int* __restrict__ rowptr, int rows, int* __r
   }
 }
 
-// One warp per segment: every entry goes to its rank among the segment's (distinct) keys.
+// W lanes per segment: every entry goes to its rank among the segment's (distinct) keys.
+template <int W>
 __global__ void sort_segments_warp(const int* __restrict__ rowptr, int rows,
                                    const int* __restrict__ key, const int* __restrict__ perm,
                                    int* __restrict__ key_out, int* __restrict__ perm_out) {
-  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= rows) return;  // warp-uniform
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long w = g / W;
+  if (w >= rows) return;
   const int b = rowptr[w], L = rowptr[w + 1] - b;
-  for (int t = lane; t < L; t += 32) {
+  for (int t = (int)(g % W); t < L; t += W) {
     const int k = key[b + t];
     int rank = 0;
     for (int u = 0; u < L; ++u) rank += key[b + u] < k;
@@ -345,8 +346,18 @@ void csr_transpose(const Csr& A, Csr& At, int** perm_out, cudaStream_t s) {
     }
     ::clair::count_launch();
   }
-  if (At.rows) sort_segments_warp<<<ceil_div((long long)At.rows * 32, 256), 256, 0, s>>>(
-      At.rowptr, At.rows, col_fill, perm_fill, At.col, perm); ::clair::count_launch();
+  if (At.rows) {
+    const double mean = (double)A.nnz / At.rows;
+    const int W = mean <= 4.0 ? 4 : mean <= 8.0 ? 8 : mean <= 16.0 ? 16 : 32;
+    const int grid = ceil_div((long long)At.rows * W, 256);
+    switch (W) {
+      case 4: sort_segments_warp<4><<<grid, 256, 0, s>>>(At.rowptr, At.rows, col_fill, perm_fill, At.col, perm); break;
+      case 8: sort_segments_warp<8><<<grid, 256, 0, s>>>(At.rowptr, At.rows, col_fill, perm_fill, At.col, perm); break;
+      case 16: sort_segments_warp<16><<<grid, 256, 0, s>>>(At.rowptr, At.rows, col_fill, perm_fill, At.col, perm); break;
+      default: sort_segments_warp<32><<<grid, 256, 0, s>>>(At.rowptr, At.rows, col_fill, perm_fill, At.col, perm); break;
+    }
+    ::clair::count_launch();
+  }
   CLAIR_LAUNCHED();
   dfree(col_fill, s);
   dfree(perm_fill, s);
