@@ -207,8 +207,37 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
 
 // ------------------------------------------------------------------------------------
 // CTA path: one system per block of TMAX threads, T <= TMAX (64 or 128); the matrix
-// lives in shared memory, thread r owns row r.
+// lives in shared memory, thread r owns row r.  Rows are padded to a multiple of 16
+// bytes so that a row update moves 16-byte vectors; it starts at the vector holding
+// column k+1, which also rewrites columns <= k of the row: those are never read again
+// (a row's entries left of its own pivot step take no part in back substitution).
 // ------------------------------------------------------------------------------------
+template <class Real>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+__device__ __forceinline__ void sub_scaled(float4& r, float l, const float4& p) {
+  r.x = r.x - l * p.x;
+  r.y = r.y - l * p.y;
+  r.z = r.z - l * p.z;
+  r.w = r.w - l * p.w;
+}
+__device__ __forceinline__ void sub_scaled(double2& r, double l, const double2& p) {
+  r.x = r.x - l * p.x;
+  r.y = r.y - l * p.y;
+}
+
+template <class Real, int TMAX>
+__host__ __device__ constexpr int cta_pitch() {
+  return TMAX + 16 / (int)sizeof(Real);  // 16-byte rows, row starts 4 banks apart
+}
+
 // shared memory holds these to about 1024 resident threads per SM, so the register
 // budget is set for that many (64 each) rather than for full occupancy
 template <class Real, class VT, int TMAX>
@@ -218,16 +247,20 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
            const int* __restrict__ Zcol, const int* __restrict__ cpts,
            const int* __restrict__ work, double* __restrict__ Zval,
            unsigned long long* __restrict__ nsingular) {
-  extern __shared__ unsigned char smem_raw[];
-  constexpr int PITCH = TMAX + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using V = typename Vec16<Real>::type;
+  constexpr int VN = 16 / (int)sizeof(Real);
+  constexpr int PITCH = cta_pitch<Real, TMAX>();
+  constexpr int NW = TMAX / 32;
   Real* tile = reinterpret_cast<Real*>(smem_raw);                 // TMAX x PITCH
   Real* rhs = tile + TMAX * PITCH;                                  // TMAX
   Real* xs = rhs + TMAX;                                            // TMAX
   int* zl = reinterpret_cast<int*>(xs + TMAX);                      // TMAX
   int* steprow = zl + TMAX;                                         // TMAX
-  __shared__ Real red_v[TMAX / 32];
-  __shared__ int red_w[TMAX / 32];
-  __shared__ int s_piv, s_d, s_sing;
+  __shared__ unsigned red_k[NW];   // FP32: largest pivot key of each warp
+  __shared__ Real red_v[NW];       // FP64: largest |value| of each warp
+  __shared__ int red_w[NW];        // and its row
+  __shared__ int s_d, s_sing;
 
   const int t = threadIdx.x;
   const int lane = t & 31, wid = t >> 5;
@@ -246,12 +279,12 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
   const int d = s_d;
   if (t < T) zl[t] = Zcol[base + t + (t >= d ? 1 : 0)];
   Real* row = tile + t * PITCH;
-  for (int q = 0; q < TMAX; ++q) row[q] = Real(0);
+  for (int q = 0; q < TMAX; q += VN) *reinterpret_cast<V*>(row + q) = V{};
   rhs[t] = Real(0);
   __syncthreads();
   // flattened gather: block scan of the row lengths, then all threads over the entries
   __shared__ int pre[TMAX + 1];
-  __shared__ int wsum[TMAX / 32];
+  __shared__ int wsum[NW];
   __shared__ int rs[TMAX];  // start of each pattern row in Ahat
   const int rstart = t < T ? Arp[zl[t]] : 0;
   rs[t] = rstart;
@@ -288,67 +321,95 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
   int mystep = -1;
   __syncthreads();
   for (int k = 0; k < T; ++k) {
-    Real v = done ? Real(-1) : (row[k] < 0 ? -row[k] : row[k]);
-    int who = t;
+    // pivot: largest |a| of column k among the rows not yet eliminated, lowest row on
+    // ties; each warp posts its candidate, every thread then reads the block's
+    const Real rk = row[k];
+    if constexpr (sizeof(Real) == 4) {
+      // non-negative floats order as their bit patterns; key 0 marks eliminated rows
+      const unsigned key = done ? 0u : __float_as_uint(fabsf(rk)) + 1u;
+      const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
+      const unsigned bal = __ballot_sync(0xffffffffu, key == wmax);
+      if (lane == 0) {
+        red_k[wid] = wmax;
+        red_w[wid] = wid * 32 + __ffs(bal) - 1;
+      }
+    } else {
+      Real v = done ? Real(-1) : (rk < 0 ? -rk : rk);
+      int who = t;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      Real v2 = __shfl_xor_sync(0xffffffffu, v, o);
-      int w2 = __shfl_xor_sync(0xffffffffu, who, o);
-      if (v2 > v || (v2 == v && w2 < who)) {
-        v = v2;
-        who = w2;
+      for (int o = 16; o > 0; o >>= 1) {
+        const Real v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int w2 = __shfl_xor_sync(0xffffffffu, who, o);
+        if (v2 > v || (v2 == v && w2 < who)) {
+          v = v2;
+          who = w2;
+        }
+      }
+      if (lane == 0) {
+        red_v[wid] = v;
+        red_w[wid] = who;
       }
     }
-    if (lane == 0) {
-      red_v[wid] = v;
-      red_w[wid] = who;
-    }
     __syncthreads();
-    if (t == 0) {
-      Real bv = red_v[0];
-      int bw = red_w[0];
-      for (int w = 1; w < TMAX / 32; ++w)
-        if (red_v[w] > bv || (red_v[w] == bv && red_w[w] < bw)) {
-          bv = red_v[w];
-          bw = red_w[w];
+    int piv = red_w[0];
+    if constexpr (sizeof(Real) == 4) {
+      unsigned bk = red_k[0];
+#pragma unroll
+      for (int w = 1; w < NW; ++w)
+        if (red_k[w] > bk) {  // warps hold increasing rows: strict keeps the lowest
+          bk = red_k[w];
+          piv = red_w[w];
         }
-      s_piv = bw;
-      steprow[k] = bw;
-      if (!(bv > Real(0))) s_sing = 1;
+    } else {
+      Real bv = red_v[0];
+#pragma unroll
+      for (int w = 1; w < NW; ++w)
+        if (red_v[w] > bv) {
+          bv = red_v[w];
+          piv = red_w[w];
+        }
     }
-    __syncthreads();
-    const int piv = s_piv;
     const Real* prow = tile + piv * PITCH;
     const Real pk = prow[k];
+    if (t == 0) {
+      steprow[k] = piv;
+      if (!((pk < 0 ? -pk : pk) > Real(0))) s_sing = 1;
+    }
     if (t == piv) {
       done = true;
       mystep = k;
     } else if (!done && pk != Real(0)) {
-      const Real l = row[k] / pk;
-      for (int j0 = k + 1; j0 < T; j0 += LS_CHUNK) {
-        Real pv[LS_CHUNK], rv[LS_CHUNK];
-#pragma unroll
-        for (int u = 0; u < LS_CHUNK; ++u)
-          if (j0 + u < T) {
-            pv[u] = prow[j0 + u];
-            rv[u] = row[j0 + u];
-          }
-#pragma unroll
-        for (int u = 0; u < LS_CHUNK; ++u)
-          if (j0 + u < T) row[j0 + u] = rv[u] - l * pv[u];
+      const Real l = rk / pk;
+      for (int j0 = (k + 1) & ~(VN - 1); j0 < T; j0 += 2 * VN) {
+        const bool two = j0 + VN < T;
+        const V p0 = *reinterpret_cast<const V*>(prow + j0);
+        V r0 = *reinterpret_cast<const V*>(row + j0);
+        V p1 = p0, r1 = r0;
+        if (two) {
+          p1 = *reinterpret_cast<const V*>(prow + j0 + VN);
+          r1 = *reinterpret_cast<const V*>(row + j0 + VN);
+        }
+        sub_scaled(r0, l, p0);
+        *reinterpret_cast<V*>(row + j0) = r0;
+        if (two) {
+          sub_scaled(r1, l, p1);
+          *reinterpret_cast<V*>(row + j0 + VN) = r1;
+        }
       }
       rhs[t] -= l * rhs[piv];
     }
     __syncthreads();
   }
+  // back substitution: one barrier per step suffices, each thread updates only its own
+  // right-hand side and every x_k has its own slot
   for (int k = T - 1; k >= 0; --k) {
     const int own = steprow[k];
     if (t == own) xs[k] = row[k] != Real(0) ? rhs[t] / row[k] : Real(0);
     __syncthreads();
     const Real xk = xs[k];
     if (mystep >= 0 && mystep < k) rhs[t] -= row[k] * xk;
-    __syncthreads();
   }
+  __syncthreads();
   const bool sing = s_sing != 0;
   if (t < T) Zval[base + t + (t >= d ? 1 : 0)] = sing ? 0.0 : (double)xs[t];
   if (t == 0) {
@@ -359,7 +420,7 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
 
 template <class Real, int TMAX>
 static size_t cta_smem() {
-  return sizeof(Real) * ((size_t)TMAX * (TMAX + 1) + 2 * TMAX) + sizeof(int) * 2 * TMAX;
+  return sizeof(Real) * ((size_t)TMAX * cta_pitch<Real, TMAX>() + 2 * TMAX) + sizeof(int) * 2 * TMAX;
 }
 
 // ------------------------------------------------------------------------------------
