@@ -12,9 +12,10 @@
 //
 // Layout: the pattern is a CSR with one row per coarse point (the transposed P_hat), each
 // row holding the coarse point's own column (identity weight 1) and its F-points sorted.
-// Systems are bucketed by T: T <= 8, 16, 32 use G lanes of a warp per system (row p of
-// the local matrix lives in the registers of lane p; the pivot row is broadcast with
-// shuffles); 32 < T <= 128 uses one CTA per system with the matrix in shared memory.
+// Systems are bucketed by T: T <= 8, 16 use G lanes of a warp per system (row p of the
+// local matrix lives in the registers of lane p; the pivot row is broadcast with
+// shuffles); 16 < T <= 128 uses one CTA of 32, 64 or 128 threads per system with the
+// matrix in shared memory.
 // Pivoting is partial (largest |entry| among rows not yet used, lowest row on ties),
 // done implicitly by marking rows instead of swapping them.
 #include <algorithm>
@@ -703,16 +704,18 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
                                     (int)big_smem<Real>(LS_TBIG)));
     attr = true;
   }
-  const int per_block[3] = {LS_WARPS * 4, LS_WARPS * 2, LS_WARPS};
+  const int per_block[2] = {LS_WARPS * 4, LS_WARPS * 2};
   if (counts_h[0])
     lsolve_group<Real, VT, 8><<<ceil_div(counts_h[0], per_block[0]), 32 * LS_WARPS, 0, s>>>(
         Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 0LL * nc, counts_h[0], Zval, nsing); ::clair::count_launch();
   if (counts_h[1])
     lsolve_group<Real, VT, 16><<<ceil_div(counts_h[1], per_block[1]), 32 * LS_WARPS, 0, s>>>(
         Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 1LL * nc, counts_h[1], Zval, nsing); ::clair::count_launch();
+  // 16 < T <= 32: the CTA kernel with one warp per block (rolled loops; a 32-lane register
+  // elimination unrolls into more code than the instruction cache holds)
   if (counts_h[2])
-    lsolve_group<Real, VT, 32><<<ceil_div(counts_h[2], per_block[2]), 32 * LS_WARPS, 0, s>>>(
-        Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 2LL * nc, counts_h[2], Zval, nsing); ::clair::count_launch();
+    lsolve_cta<Real, VT, 32><<<counts_h[2], 32, cta_smem<Real, 32>(), s>>>(
+        Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 2LL * nc, Zval, nsing); ::clair::count_launch();
   if (counts_h[3])
     lsolve_cta<Real, VT, 64><<<counts_h[3], 64, cta_smem<Real, 64>(), s>>>(
         Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 3LL * nc, Zval, nsing); ::clair::count_launch();
