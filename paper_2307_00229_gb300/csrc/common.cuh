@@ -167,7 +167,10 @@ __host__ __device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
 // Host-callable building blocks (sparse.cu).
 // ------------------------------------------------------------------------------------
 // out[0] = 0, out[i+1] = sum_{k<=i} in[k]; returns out[n] (synchronises s).
-long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s, bool want_total = true);
+// want_total: returns out[n] after synchronising s; a device int `extra_dev` (optional) is
+// read back into *extra_host by the same synchronisation.
+long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s, bool want_total = true,
+                         const int* extra_dev = nullptr, int* extra_host = nullptr);
 // Transpose (structure + values; perm[k] = source entry of output entry k); output
 // arrays are allocated here.  Rows of the result are sorted by column.
 void csr_transpose(const Csr& A, Csr& At, int** perm, cudaStream_t s);

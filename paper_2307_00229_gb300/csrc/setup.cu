@@ -444,6 +444,38 @@ __device__ __forceinline__ void pt_insert(int* keys, int key, int* fresh, int* e
   atomicExch(err, 1);
 }
 
+// Second hop for up to 32 first-hop rows at once: lane q holds row q's start and length
+// (length 0 for no row); the rows' entries are flattened over the lanes (a warp scan of
+// the lengths, then each lane finds its entry's row by binary search), so the loads of
+// different rows are independent.  Called by all 32 lanes.
+__device__ __forceinline__ void pt_second_hop(int start, int len, int lane, int* P, int* S,
+                                              const int* __restrict__ Wcol,
+                                              const unsigned char* __restrict__ sW,
+                                              const signed char* __restrict__ cf, int* K,
+                                              int* fresh, int* err) {
+  int incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  P[lane + 1] = incl;
+  if (lane == 0) P[0] = 0;
+  S[lane] = start;
+  __syncwarp();
+  const int tot = P[32];
+  for (int f = lane; f < tot; f += 32) {
+    int lo = 0, hi = 32;  // row with P[lo] <= f < P[lo + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (P[mid] <= f) lo = mid; else hi = mid;
+    }
+    const int e = S[lo] + (f - P[lo]);
+    if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], fresh, err);
+  }
+  __syncwarp();  // P and S are rewritten by the next call
+}
+
 template <bool COUNT, bool AGG>
 __global__ void __launch_bounds__(32 * PT_WARPS)
 pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
@@ -452,6 +484,8 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
                const int* __restrict__ Mcol, int* __restrict__ count,
                const int* __restrict__ Zrp, int* __restrict__ Zcol, int* __restrict__ err) {
   __shared__ int keys[PT_WARPS][PT_CAP];
+  __shared__ int hop_pre[PT_WARPS][33];
+  __shared__ int hop_start[PT_WARPS][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * PT_WARPS + w;
   if (r >= nc) return;  // warp-uniform
@@ -466,12 +500,19 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
     for (int e = Wrp[i] + lane; e < Wrp[i + 1]; e += 32)
       if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], &fresh, err);
     if (degree >= 2) {
-      // second hop from every first-hop F-point, one first-hop point at a time
-      for (int e1 = Wrp[i]; e1 < Wrp[i + 1]; ++e1) {
-        const int k = Wcol[e1];
-        if (!sW[e1] || cf[k]) continue;
-        for (int e = Wrp[k] + lane; e < Wrp[k + 1]; e += 32)
-          if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], &fresh, err);
+      // second hop from every first-hop F-point, 32 first-hop points at a time
+      const int e_end = Wrp[i + 1];
+      for (int c0 = Wrp[i]; c0 < e_end; c0 += 32) {
+        const int e1 = c0 + lane;
+        int start = 0, len = 0;
+        if (e1 < e_end) {
+          const int k = Wcol[e1];
+          if (sW[e1] && !cf[k]) {
+            start = Wrp[k];
+            len = Wrp[k + 1] - start;
+          }
+        }
+        pt_second_hop(start, len, lane, hop_pre[w], hop_start[w], Wcol, sW, cf, K, &fresh, err);
       }
     }
   } else {
@@ -479,11 +520,17 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
     for (int m = Mrp[r] + lane; m < Mrp[r + 1]; m += 32)
       if (!cf[Mcol[m]]) pt_insert(K, Mcol[m], &fresh, err);
     if (degree >= 2) {
-      // second hop: F-points j with S_jk for every member k
-      for (int m = Mrp[r]; m < Mrp[r + 1]; ++m) {
-        const int k = Mcol[m];
-        for (int e = Wrp[k] + lane; e < Wrp[k + 1]; e += 32)
-          if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], &fresh, err);
+      // second hop: F-points j with S_jk for every member k, 32 members at a time
+      const int m_end = Mrp[r + 1];
+      for (int c0 = Mrp[r]; c0 < m_end; c0 += 32) {
+        const int m = c0 + lane;
+        int start = 0, len = 0;
+        if (m < m_end) {
+          const int k = Mcol[m];
+          start = Wrp[k];
+          len = Wrp[k + 1] - start;
+        }
+        pt_second_hop(start, len, lane, hop_pre[w], hop_start[w], Wcol, sW, cf, K, &fresh, err);
       }
     }
   }
@@ -539,8 +586,18 @@ void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf
     ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
+  // a row that overflows the table does so in the counting pass (the filling pass inserts
+  // the same keys), so its flag is read back with the scan total
   Z.rowptr = dalloc<int>(nc + 1, s);
-  Z.nnz = (int)exclusive_scan(count, Z.rowptr, nc, s, true);
+  int h = 0;
+  Z.nnz = (int)exclusive_scan(count, Z.rowptr, nc, s, true, err, &h);
+  if (h) {
+    dfree(count, s);
+    dfree(err, s);
+    dfree(Z.rowptr, s);
+    Z.rowptr = nullptr;
+    CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "pattern row exceeds %d entries", PT_CAP);
+  }
   Z.col = dalloc<int>(Z.nnz, s);
   if (nc) {
     if (agg)
@@ -554,12 +611,8 @@ void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf
     ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
-  int h = 0;
-  CLAIR_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CLAIR_CUDA(cudaStreamSynchronize(s));
   dfree(count, s);
   dfree(err, s);
-  CLAIR_REQUIRE(h == 0, CLAIR_ERR_CAPACITY, "pattern row exceeds %d entries", PT_CAP);
 }
 
 // ------------------------------------------------------------------------------------

@@ -201,7 +201,8 @@ __global__ void scan_apply(const int* __restrict__ in, int n, const long long* _
   if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
 }
 
-long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s, bool want_total) {
+long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s, bool want_total,
+                         const int* extra_dev, int* extra_host) {
   const int nb = std::max(1, ceil_div(n, SCAN_TILE));
   CLAIR_REQUIRE(nb <= SCAN_TILE, CLAIR_ERR_CAPACITY, "scan of %d items exceeds capacity", n);
   long long* sums = dalloc<long long>(nb + 1, s);
@@ -216,6 +217,8 @@ long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s, bool wa
     int total32 = 0, h_ovf = 0;
     CLAIR_CUDA(cudaMemcpyAsync(&total32, out + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     CLAIR_CUDA(cudaMemcpyAsync(&h_ovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (extra_dev)
+      CLAIR_CUDA(cudaMemcpyAsync(extra_host, extra_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     CLAIR_CUDA(cudaStreamSynchronize(s));
     CLAIR_REQUIRE(!h_ovf, CLAIR_ERR_CAPACITY, "scan total exceeds int32");
     total = total32;
@@ -1306,10 +1309,8 @@ static void spgemm_cta_path(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) 
       count, nullptr, A.rowptr, list, rows, nlist, 0, 0, 0, list2, nlist + 1); ::clair::count_launch();
   CLAIR_LAUNCHED();
   C.rowptr = dalloc<int>(rows + 1, s);
-  C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true);  // synchronises s
-  int still = 0;
-  CLAIR_CUDA(cudaMemcpyAsync(&still, nlist + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CLAIR_CUDA(cudaStreamSynchronize(s));
+  int still = 0;  // rows no table could hold, read back with the scan total
+  C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true, nlist + 1, &still);
   if (still) {
     dfree(count, s);
     dfree(route, s);
@@ -1416,10 +1417,8 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   }
   // rows still unplaced after the large table: nlist[3]; the scan's read-back carries it
   C.rowptr = dalloc<int>(rows + 1, s);
-  C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true);  // synchronises s
-  int still = 0;  // the stream is idle here: a short read
-  CLAIR_CUDA(cudaMemcpyAsync(&still, nlist + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CLAIR_CUDA(cudaStreamSynchronize(s));
+  int still = 0;
+  C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true, nlist + 3, &still);
   if (still) {
     dfree(count, s);
     dfree(lists[0], s);
