@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <utility>
 #include <new>
 #include <vector>
 
@@ -690,14 +691,19 @@ void jacobi(const Csr& A, const T* vals, const T* dinv, const signed char* cf, i
 
 // Mode-vector smoothing B <- CFF^sweeps(B) with a zero right-hand side and the weight
 // read from device memory (so it can follow the Arnoldi step without a host round trip).
+// The sweeps alternate between Bv and tmp (every sweep writes all rows); one copy at the
+// end when the result sits in tmp.
 void smooth_modes(const Csr& M, const double* dinv, const signed char* cf, const double* omega_dev,
                   int sweeps, double* Bv, double* tmp, cudaStream_t s) {
+  double* x = Bv;
+  double* y = tmp;
   for (int it = 0; it < sweeps; ++it) {
-    jacobi<double>(M, M.val, dinv, cf, 1, 1.0, nullptr, Bv, tmp, s, omega_dev);
-    jacobi<double>(M, M.val, dinv, cf, 0, 1.0, nullptr, tmp, Bv, s, omega_dev);
-    jacobi<double>(M, M.val, dinv, cf, 0, 1.0, nullptr, Bv, tmp, s, omega_dev);
-    CLAIR_CUDA(cudaMemcpyAsync(Bv, tmp, sizeof(double) * M.rows, cudaMemcpyDeviceToDevice, s));
+    jacobi<double>(M, M.val, dinv, cf, 1, 1.0, nullptr, x, y, s, omega_dev);
+    jacobi<double>(M, M.val, dinv, cf, 0, 1.0, nullptr, y, x, s, omega_dev);
+    jacobi<double>(M, M.val, dinv, cf, 0, 1.0, nullptr, x, y, s, omega_dev);
+    std::swap(x, y);
   }
+  if (x != Bv) CLAIR_CUDA(cudaMemcpyAsync(Bv, x, sizeof(double) * M.rows, cudaMemcpyDeviceToDevice, s));
 }
 template void jacobi<double>(const Csr&, const double*, const double*, const signed char*, int,
                              double, const double*, const double*, double*, cudaStream_t,
