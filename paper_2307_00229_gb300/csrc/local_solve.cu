@@ -302,20 +302,37 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
   if (t == 0) pre[0] = 0;
   __syncthreads();
   const int total = pre[TMAX];
-#pragma unroll 4
-  for (int f = t; f < total; f += TMAX) {
-    int lo = 0, hi = TMAX;  // row r with pre[r] <= f < pre[r + 1]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (pre[mid] <= f) lo = mid; else hi = mid;
+  // entries in batches of GB per thread: all loads of a batch, then its column searches,
+  // then its stores (zl shares the dynamic array with the tile, so a store would order
+  // every later load after it)
+  constexpr int GB = 4;
+  for (int f0 = t; f0 < total; f0 += GB * TMAX) {
+    int row_of[GB], col_of[GB];
+    Real val_of[GB];
+#pragma unroll
+    for (int u = 0; u < GB; ++u) {
+      const int f = f0 + u * TMAX;
+      row_of[u] = -1;
+      if (f < total) {
+        int lo = 0, hi = TMAX;  // row r with pre[r] <= f < pre[r + 1]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (pre[mid] <= f) lo = mid; else hi = mid;
+        }
+        const int e = rs[lo] + (f - pre[lo]);
+        row_of[u] = lo;
+        col_of[u] = Acol[e];
+        val_of[u] = Real(Aval[e]);
+      }
     }
-    const int e = rs[lo] + (f - pre[lo]);
-    const int c = Acol[e];
-    if (c == i) {
-      rhs[lo] = Real(-Aval[e]);
-    } else {
-      const int q = find_sorted(zl, T, c);
-      if (q >= 0) tile[lo * PITCH + q] = Real(Aval[e]);
+    int q_of[GB];
+#pragma unroll
+    for (int u = 0; u < GB; ++u)
+      q_of[u] = row_of[u] < 0 ? -1 : (col_of[u] == i ? T : find_sorted(zl, T, col_of[u]));
+#pragma unroll
+    for (int u = 0; u < GB; ++u) {
+      if (q_of[u] == T) rhs[row_of[u]] = -val_of[u];
+      else if (q_of[u] >= 0) tile[row_of[u] * PITCH + q_of[u]] = val_of[u];
     }
   }
   bool done = t >= T;
