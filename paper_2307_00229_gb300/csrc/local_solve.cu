@@ -58,8 +58,10 @@ constexpr int LS_WARPS = 4;  // warps per block in the sub-warp path
 // that the compiler must order every load after the previous store.
 constexpr int LS_CHUNK = 8;
 
+// register budget: 8 blocks per SM (6 for the FP64 16-lane variant), which shared
+// memory and the rows held in registers allow without spills
 template <class Real, class VT, int G>
-__global__ void __launch_bounds__(32 * LS_WARPS)
+__global__ void __launch_bounds__(32 * LS_WARPS, (sizeof(Real) == 8 && G >= 16) ? 6 : 8)
 lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
              const VT* __restrict__ Aval, const int* __restrict__ Zrp,
              const int* __restrict__ Zcol, const int* __restrict__ cpts,
@@ -120,21 +122,36 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
   __syncwarp();
   const int total = pre[gib][G];
   // entry indices come from shared memory, so the loads of different entries are
-  // independent (no global row-pointer load in front of each)
-#pragma unroll 4
-  for (int t = p; t < total; t += G) {
-    int lo = 0, hi = G;  // row r with pre[r] <= t < pre[r + 1]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (pre[gib][mid] <= t) lo = mid; else hi = mid;
+  // independent (no global row-pointer load in front of each); entries go in batches of
+  // GB per lane, all loads and column searches of a batch before its stores
+  constexpr int GB = 4;
+  for (int t0 = p; t0 < total; t0 += GB * G) {
+    int row_of[GB], col_of[GB];
+    Real val_of[GB];
+#pragma unroll
+    for (int u = 0; u < GB; ++u) {
+      const int t = t0 + u * G;
+      row_of[u] = -1;
+      if (t < total) {
+        int lo = 0, hi = G;  // row r with pre[r] <= t < pre[r + 1]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (pre[gib][mid] <= t) lo = mid; else hi = mid;
+        }
+        const int e = rs[gib][lo] + (t - pre[gib][lo]);
+        row_of[u] = lo;
+        col_of[u] = Acol[e];
+        val_of[u] = Real(Aval[e]);
+      }
     }
-    const int e = rs[gib][lo] + (t - pre[gib][lo]);
-    const int c = Acol[e];
-    if (c == i) {
-      rhs_s[gib][lo] = Real(-Aval[e]);
-    } else {
-      const int q = find_sorted(zl[gib], T, c);
-      if (q >= 0) tile[gib][lo][q] = Real(Aval[e]);
+    int q_of[GB];
+#pragma unroll
+    for (int u = 0; u < GB; ++u)
+      q_of[u] = row_of[u] < 0 ? -1 : (col_of[u] == i ? T : find_sorted(zl[gib], T, col_of[u]));
+#pragma unroll
+    for (int u = 0; u < GB; ++u) {
+      if (q_of[u] == T) rhs_s[gib][row_of[u]] = -val_of[u];
+      else if (q_of[u] >= 0) tile[gib][row_of[u]][q_of[u]] = val_of[u];
     }
   }
   __syncwarp();
@@ -496,15 +513,26 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
   for (int q = 0; q < T; ++q)
     for (int p = t; p < T; p += LB_THREADS) M[(size_t)q * pitch + p] = Real(0);
   __syncthreads();
+  // row p's entries in batches of 4: loads and column searches before the stores
   for (int p = t; p < T; p += LB_THREADS) {
     const int l = zl[p];
-    for (int e = Arp[l]; e < Arp[l + 1]; ++e) {
-      const int c = Acol[e];
-      if (c == i) {
-        rhs[p] = Real(-Aval[e]);
-      } else {
-        const int q = find_sorted(zl, T, c);
-        if (q >= 0) M[(size_t)q * pitch + p] = Real(Aval[e]);
+    const int e_end = Arp[l + 1];
+    for (int e0 = Arp[l]; e0 < e_end; e0 += 4) {
+      int col_of[4], q_of[4];
+      Real val_of[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = e0 + u < e_end;
+        col_of[u] = in ? Acol[e0 + u] : -1;
+        val_of[u] = in ? Real(Aval[e0 + u]) : Real(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        q_of[u] = col_of[u] < 0 ? -1 : (col_of[u] == i ? T : find_sorted(zl, T, col_of[u]));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (q_of[u] == T) rhs[p] = -val_of[u];
+        else if (q_of[u] >= 0) M[(size_t)q_of[u] * pitch + p] = val_of[u];
       }
     }
   }
