@@ -1008,7 +1008,6 @@ spgemm_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
   double* wvals = wvals_all + w * SGC_WCAP;
   double* stage = stage_all + w * 32;
   int* wkeys = wkeys_all + w * SGC_WCAP;
-  int* prefix = pre_all + w * (SGC_PCAP + 8);
   for (int r = blockIdx.x; r < rows; r += gridDim.x) {  // block-uniform
     const int a0 = Arp[r], nA = Arp[r + 1] - a0;
     if (nA > SGC_WARPS * SGC_PCAP) {
@@ -1029,15 +1028,22 @@ spgemm_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
       if (NUMERIC) wvals[q] = 0.0;
     }
     __syncthreads();  // the row's flags are reset before any warp can raise one
-    // this warp's A entries [lo, hi) and the prefix of their B-row lengths
+    // this warp's A entries [lo, hi), 32 at a time: lane q holds entry q's B-row start,
+    // length and value in registers; the chunk's products (k-major) are taken 32 at a
+    // time, each lane finding its product's entry by a binary search over the lanes'
+    // exclusive prefix (shuffles), so a product costs one dependent load of B
     const int chunk = (nA + SGC_WARPS - 1) / SGC_WARPS;
     const int lo = min(nA, w * chunk), hi = min(nA, lo + chunk), nw = hi - lo;
-    int base = 0;
-    for (int c = 0; c < nw; c += 32) {
-      int len = 0;
-      if (c + lane < nw) {
-        const int k = Acol[a0 + lo + c + lane];
-        len = Brp[k + 1] - Brp[k];
+    bool full = false;
+    for (int c0 = 0; c0 < nw; c0 += 32) {
+      int bst = 0, len = 0;
+      double av = 0.0;
+      if (c0 + lane < nw) {
+        const int ea = a0 + lo + c0 + lane;
+        const int k = Acol[ea];
+        bst = Brp[k];
+        len = Brp[k + 1] - bst;
+        if (NUMERIC) av = Aval[ea];
       }
       int incl = len;
 #pragma unroll
@@ -1045,43 +1051,42 @@ spgemm_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
         const int v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
       }
-      if (c + lane < nw) prefix[c + lane + 1] = base + incl;
-      base += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (lane == 0) prefix[0] = 0;
-    __syncwarp();
-    const int total = base;
-    bool full = false;
-    for (int p0 = 0; p0 < total; p0 += 32) {
-      const int p = p0 + lane;
-      int slot = -1;
-      double prod = 0.0;
-      if (p < total) {
-        int l = 0, h = nw;  // largest t with prefix[t] <= p
-        while (h - l > 1) {
+      const int excl = incl - len;
+      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      for (int p0 = 0; p0 < tot; p0 += 32) {
+        const int p = p0 + lane;
+        int l = 0, h = 32;  // largest lane l with excl_l <= p (lanes past the chunk: excl = tot)
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
           const int mid = (l + h) >> 1;
-          if (prefix[mid] <= p) l = mid; else h = mid;
+          if (__shfl_sync(0xffffffffu, excl, mid) <= p) l = mid; else h = mid;
         }
-        const int ea = a0 + lo + l;
-        const int k = Acol[ea];
-        const int eb = Brp[k] + (p - prefix[l]);
-        bool is_new = false;
-        slot = sg_insert(wkeys, SGC_WCAP, Bcol[eb], &is_new);
-        if (slot < 0) full = true;
-        if (NUMERIC) prod = __dmul_rn(Aval[ea], Bval[eb]);
+        const int ob = __shfl_sync(0xffffffffu, bst, l);
+        const int oe = __shfl_sync(0xffffffffu, excl, l);
+        const double oa = NUMERIC ? __shfl_sync(0xffffffffu, av, l) : 0.0;
+        int slot = -1;
+        double prod = 0.0;
+        if (p < tot) {
+          const int eb = ob + (p - oe);
+          bool is_new = false;
+          slot = sg_insert(wkeys, SGC_WCAP, Bcol[eb], &is_new);
+          if (slot < 0) full = true;
+          if (NUMERIC) prod = __dmul_rn(oa, Bval[eb]);
+        }
+        if (__any_sync(0xffffffffu, full)) break;
+        if (NUMERIC) {
+          stage[lane] = prod;
+          const unsigned grp = __match_any_sync(0xffffffffu, slot);
+          __syncwarp();
+          if (slot >= 0 && lane == __ffs(grp) - 1) {
+            double sum = prod;
+            for (unsigned g = grp & (grp - 1); g; g &= g - 1) sum = __dadd_rn(sum, stage[__ffs(g) - 1]);
+            wvals[slot] = __dadd_rn(wvals[slot], sum);
+          }
+          __syncwarp();
+        }
       }
       if (__any_sync(0xffffffffu, full)) break;
-      if (NUMERIC) {
-        stage[lane] = prod;
-        const unsigned grp = __match_any_sync(0xffffffffu, slot);
-        __syncwarp();
-        if (slot >= 0 && lane == __ffs(grp) - 1) {
-          double sum = prod;
-          for (unsigned g = grp & (grp - 1); g; g &= g - 1) sum = __dadd_rn(sum, stage[__ffs(g) - 1]);
-          wvals[slot] = __dadd_rn(wvals[slot], sum);
-        }
-        __syncwarp();
-      }
     }
     const bool wfull = __any_sync(0xffffffffu, full);  // the whole warp votes
     if (wfull && lane == 0) s_full = 1;
