@@ -34,7 +34,7 @@ PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes (read + write) of the local-solve launches of one step of the default workload,
 # from the ncu capture summarised in profiles/launches_setup_solve_1024sq.md; None once those
 # kernels change without a new capture.
-LSOLVE_DRAM_BYTES_PER_STEP = 508_626_432
+LSOLVE_DRAM_BYTES_PER_STEP = 506_859_520
 
 
 def parse():
