@@ -204,6 +204,96 @@ def test_pattern_matches_bruteforce(degree, eps):
         assert got == pattern_bruteforce(Ahat, cf, 0.05, degree)
 
 
+def agg_pattern_bruteforce(Ahat, agg, cf, theta, degree):
+    """Column i of the aggregation-based pattern, written out from its definition
+    (Algorithm 1 with T = the aggregation operator of the footnote to Section 3.1.3):
+    start from every member of aggregate i (its root included), add j whenever j
+    strongly depends on a point already reached, degree-1 times, keep the F-points."""
+    S = strength_bruteforce(Ahat.toarray(), theta)
+    n = cf.size
+    nagg = int(cf.sum())
+    cols = []
+    for a in range(nagg):
+        reach = {j for j in range(n) if agg[j] == a}
+        for _ in range(degree - 1):
+            reach = reach | {j for j in range(n) if any(S[j, k] for k in reach)}
+        cols.append(sorted(j for j in reach if cf[j] == 0))
+    return cols
+
+
+def tiny_3d(nside=4, eps=1e-2):
+    vel = lambda x, y, z: (2 * y * (1 - x * x), -2 * x * (1 - y * y), 0.5 + 0 * z)
+    return O.csr_of(workloads.advdiff_3d(nside, vel, eps))
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3])
+@pytest.mark.parametrize("which", ["2d_eps1", "2d_eps1e-3", "3d"])
+def test_agg_pattern_matches_bruteforce(degree, which):
+    """Agg base pattern + expansion (Algorithm 1, T = aggregation operator) against a
+    brute-force walk that starts from every aggregate member, for R (A^T) and P (A)."""
+    A = {"2d_eps1": lambda: small_problem(8, eps=1.0),
+         "2d_eps1e-3": lambda: small_problem(8, eps=1e-3),
+         "3d": lambda: tiny_3d(4, 1e-2)}[which]()
+    cf, agg = O.aggregate(A, 0.25)
+    assert cf.sum() >= 2
+    for Ahat in (A, A.T.tocsr()):
+        S = O.strength(Ahat, 0.05)
+        T = O.base_pattern(S, cf, "AGG", agg)
+        # T is the 0/1 aggregation operator itself: column i = members of aggregate i
+        Td = T.toarray()
+        for a in range(int(cf.sum())):
+            np.testing.assert_array_equal(np.flatnonzero(Td[:, a]), np.flatnonzero(agg == a))
+        W = O.clair_pattern(S, T, cf, degree)
+        got = [list(W.indices[W.indptr[i]:W.indptr[i + 1]]) for i in range(W.shape[1])]
+        assert got == agg_pattern_bruteforce(Ahat, agg, cf, 0.05, degree)
+
+
+def cff_propagator(Ad, cf, omega):
+    """Dense error propagator of one CFF sweep with zero right-hand side: a Jacobi sweep
+    on the point set X maps x to (I - omega E_X D^-1 A) x, with E_X the 0/1 selector of X;
+    CFF applies the C set once, then the F set twice (Section 4)."""
+    n = Ad.shape[0]
+    Dinv = np.diag(1.0 / np.diag(Ad))
+    EC = np.diag((cf == 1).astype(float))
+    EF = np.diag((cf == 0).astype(float))
+    MC = np.eye(n) - omega * EC @ Dinv @ Ad
+    MF = np.eye(n) - omega * EF @ Dinv @ Ad
+    return MF @ MF @ MC
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-2, 1.0])
+def test_smooth_modes_closed_form(eps):
+    """B_P = (CFF propagator of A)^5 B and B_R = (CFF propagator of A^T)^5 B on the fine
+    level, and the same on level 1 from the injected vectors (Section 4.1 parameters:
+    five CFF sweeps per level; A for interpolation, A^T for restriction)."""
+    A = small_problem(6, eps=eps)                   # n = 36
+    n = A.shape[0]
+    B = np.ones(n)
+    p = O.Params(coarse_max=4)
+    H = O.build_hierarchy(A, B, p)
+    assert len(H.levels) >= 3
+    Bp, Br = B.copy(), B.copy()
+    for k in range(2):
+        lev = H.levels[k]
+        Ad = lev.A.toarray()
+        Mp = np.linalg.matrix_power(cff_propagator(Ad, lev.cf, lev.omega), 5)
+        Mr = np.linalg.matrix_power(cff_propagator(Ad.T, lev.cf, lev.omega), 5)
+        Bp, Br = Mp @ Bp, Mr @ Br
+        scale = max(np.abs(Bp).max(), 1e-300)
+        np.testing.assert_allclose(lev.B_P.ravel(), Bp, rtol=0, atol=1e-13 * scale)
+        scale = max(np.abs(Br).max(), 1e-300)
+        np.testing.assert_allclose(lev.B_R.ravel(), Br, rtol=0, atol=1e-13 * scale)
+        if k == 0:  # A is nonsymmetric, so the two sides differ: a swap would fail
+            assert np.abs(Bp - Br).max() > 1e-6 * np.abs(Bp).max()
+        C = np.flatnonzero(lev.cf == 1)
+        Bp, Br = Bp[C], Br[C]
+    # with the sweep count taken from the parameters: 2 sweeps give a different vector
+    lev = H.levels[0]
+    B2 = O.smooth_modes(lev.A, B, lev.cf, lev.omega, 2)
+    M2 = np.linalg.matrix_power(cff_propagator(lev.A.toarray(), lev.cf, lev.omega), 2)
+    np.testing.assert_allclose(B2, M2 @ B, rtol=0, atol=1e-13)
+
+
 # ---------------------------------------------------------------------------------------
 # Local systems and constraint (Remarks 3.1, 3.2; Eqs. 2.5-2.8, 2.12, 3.3)
 # ---------------------------------------------------------------------------------------
