@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -31,10 +32,28 @@ if ROOT not in sys.path:
 METRIC = "R rows/s in setup; time-to-1e-8 rel residual, mixed vs FP64 path, 1 GB300"
 UNIT = "R rows/s"
 PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# DRAM bytes (read + write) of the local-solve launches of one step of the default workload,
-# from the ncu capture summarised in profiles/launches_setup_solve_1024sq.md; None once those
-# kernels change without a new capture.
-LSOLVE_DRAM_BYTES_PER_STEP = 506_859_520
+# DRAM bytes (read + write, ncu dram__bytes_read.sum + dram__bytes_write.sum) of one step's
+# local-solve launches on the default workload, keyed by the SHA-256 of the source they were
+# measured on: reported only while that source is unchanged, null otherwise.
+MEASURED_TRAFFIC = {
+    # "local_solve": {"bytes": ..., "source_sha256": "...", "capture": "ncu command line"},
+}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+FP64_PEAK_TFLOPS = 1.19                               # measured FMA loop (dependent chains)
+
+
+def source_sha256(name):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2307_00229_gb300", "csrc", name)
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def measured_traffic(phase, source):
+    m = MEASURED_TRAFFIC.get(phase)
+    if not m or m.get("source_sha256") != source_sha256(source):
+        return None
+    return m["bytes"]
 
 
 def parse():
@@ -49,7 +68,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 steps (0: skip that arm)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-nside", type=int, default=128)
+    ap.add_argument("--cpu-nside", type=int, default=192)
     ap.add_argument("--workload", choices=["advdiff1024", "batch64", "adjoint512", "recirc3d"],
                     default="advdiff1024",
                     help="advdiff1024: the headline line (default).  The others time the "
@@ -79,7 +98,7 @@ def workload(args):
 class ClockSampler:
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"clocks_bench_{os.getpid()}.csv")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -147,6 +166,32 @@ def vcycle_bytes(levels, s=4):
         total += 2 * sweep(nnzF, nF) + sweep(nnzC, nc)         # F, F, C post sweeps
         total += 2 * s * n                                      # copy
     return total
+
+
+def phase_bytes(levels, arnoldi_steps=15, sweeps=5):
+    """Algorithmic bytes per setup phase, summed over the levels that have transfers (FP64
+    data: 8-byte values, 4-byte indices).  Each is the data the phase must read and write
+    at least once: transpose, row maxima and the two strength masks, one pass of the
+    independent-set selection (split); the two interpolation-strength masks and the two
+    pattern CSRs (pattern); the Arnoldi steps, each an SpMV of D^-1 A plus the classical
+    Gram-Schmidt passes over the basis, twice (weight); CFF sweeps on both mode vectors
+    (smooth); R, A, P read once and A_c written once (galerkin)."""
+    b = {"split": 0.0, "pattern": 0.0, "weight": 0.0, "smooth": 0.0, "galerkin": 0.0}
+    for k, L in enumerate(levels):
+        if not L.get("nc"):
+            continue
+        n, nnz = L["n"], L["nnz"]
+        nnzR, nnzP = L["nnz_R"], L["nnz_P"]
+        nnzAc = levels[k + 1]["nnz"] if k + 1 < len(levels) else 0
+        csr = 12 * nnz + 4 * (n + 1)
+        b["split"] += 2 * csr + 2 * (12 * nnz + 8 * n) + 2 * (csr + 8 * n + nnz) + 2 * (4 * nnz + nnz) + n
+        b["pattern"] += 2 * (csr + 8 * n + nnz) + 8 * nnz + 4 * (nnzR + nnzP) + 8 * (L["nc"] + n)
+        for j in range(arnoldi_steps):
+            b["weight"] += csr + 24 * n + 2 * (8 * n * (j + 1) + 8 * n) + 2 * (8 * n * (j + 1) + 16 * n) + 24 * n
+        sweep = csr + n + 4 * 8 * n
+        b["smooth"] += 2 * sweeps * 3 * sweep
+        b["galerkin"] += 12 * (nnzR + nnz + nnzP + nnzAc) + 4 * (L["nc"] + 1)
+    return b
 
 
 def level_summary(cl, h):
@@ -282,6 +327,30 @@ def run_clair(args):
     fp64 = timed(cl.CLAIR_FP64, args.fp64_steps, 1) if args.fp64_steps > 0 else None
     e2e = None if args.no_e2e else timed(cl.CLAIR_MIXED, max(1, min(args.steps, 3)), 1, e2e=True)
 
+    # error of every MIXED result against the FP64 path (which matches the FP64 oracle to
+    # 1e-12 per row in the parity tests): level-0 R and P weights per row, the solution
+    def results(precision):
+        h, st_, its_, rel_ = step(params(precision))
+        v = cl.clair_level_view(h, 0)
+        out = {k_: v[k_].cpu().numpy() for k_ in ("R_val", "P_val", "R_rowptr", "P_rowptr")}
+        out["u"] = u.cpu().numpy()
+        cl.clair_free(h)
+        return out
+
+    def rowwise(a, ref, rp):
+        worst = 0.0
+        for lo, hi in zip(rp[:-1], rp[1:]):
+            if hi > lo:
+                m_ = np.abs(ref[lo:hi]).max()
+                if m_ > 0:
+                    worst = max(worst, float(np.abs(a[lo:hi] - ref[lo:hi]).max() / m_))
+        return worst
+    rm, r64 = results(cl.CLAIR_MIXED), results(cl.CLAIR_FP64)
+    errors = {"R_rowwise_max_rel": rowwise(rm["R_val"], r64["R_val"], r64["R_rowptr"]),
+              "P_rowwise_max_rel": rowwise(rm["P_val"], r64["P_val"], r64["P_rowptr"]),
+              "u_rel": float(np.linalg.norm(rm["u"] - r64["u"]) / np.linalg.norm(r64["u"])),
+              "against": "the FP64 GPU path of the same workload (level 0 weights, solution)"}
+
     st = mixed["stats"]
     rows = int(st.r_rows)
     value = job_rows_per_s(rows, world, mixed["ms"])
@@ -292,16 +361,26 @@ def run_clair(args):
     # roofline of the dominant phase
     vb = vcycle_bytes(mixed["levels"])
     vcycle_ms = phases["vcycle"] / max(its, 1)
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x 2 x max clock
     lsolve = {"bound": "alu", "achieved": st.lsolve_flops / (phases["local_solve"] * 1e-3) / 1e12,
-              "peak": fp32_peak, "unit": "TFLOP/s",
-              "traffic": LSOLVE_DRAM_BYTES_PER_STEP,
-              "traffic_scope": "per step, all local-solve launches (profiles/launches_setup_solve_1024sq.md)",
+              "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+              "traffic": measured_traffic("local_solve", "local_solve.cu"),
+              "traffic_scope": "per step, all local-solve launches (ncu DRAM read + write)",
               "algorithmic_bytes": st.lsolve_min_bytes,
               "kernel": "lsolve_group/lsolve_cta (FP32 batched local LU)",
               "share_of_step": phases["local_solve"] / mixed["ms"]}
     lsolve["frac"] = lsolve["achieved"] / lsolve["peak"]
     hbm = pk.get("hbm_gbs", PEAK_FALLBACK["hbm_gbs"])
+    # the other setup phases against HBM (algorithmic bytes per phase_bytes)
+    pb = phase_bytes(mixed["levels"])
+    roofline_phases = {}
+    for name, nbytes in pb.items():
+        ms_ = phases[name]
+        if ms_ > 0:
+            gbs = nbytes / (ms_ * 1e-3) / 1e9
+            roofline_phases[name] = {"bound": "hbm", "ms": ms_, "algorithmic_bytes": nbytes,
+                                     "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                     "frac": gbs / hbm, "share_of_step": ms_ / mixed["ms"],
+                                     "stream": "side" if name in ("weight", "smooth") else "main"}
     vcyc = {"bound": "hbm", "achieved": vb / (vcycle_ms * 1e-3) / 1e9 if vcycle_ms > 0 else None,
             "peak": hbm, "unit": "GB/s", "traffic": None, "bytes_per_cycle": vb,
             "kernel": "V(1,1) cycle kernels (jacobi/spmv, FP32)",
@@ -334,7 +413,8 @@ def run_clair(args):
             "value": job_rows_per_s(rows, world, e2e["ms"]), "unit": UNIT,
             "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
             "ms_per_step": e2e["ms"]},
-        "roofline": dominant, "roofline_other": other,
+        "roofline": dominant, "roofline_other": other, "roofline_phases": roofline_phases,
+        "error_vs_fp64": errors,
         "gpu_launches": mixed["launches"],
         "clocks": clocks,
         "step_times_ms": mixed["times"], "wall_s": mixed["wall"],
@@ -369,10 +449,12 @@ def oracle_step(nside, eps, degree):
 
 def cpu_baseline(args):
     rows, dt, cpu, its = oracle_step(args.cpu_nside, args.eps, args.degree)
-    return {"value": rows / dt, "unit": UNIT, "cores": max(1, round(cpu / dt)), "kind": "oracle",
+    return {"value": rows / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "threads_busy": round(cpu / dt, 2),
             "sample": f"oracle setup + FGMRES solve of the same problem family at {args.cpu_nside}^2 "
                       f"(eps={args.eps}, angle pi/6, m={args.degree}): {rows} R rows in {dt:.1f} s, "
-                      f"{its} iterations"}
+                      f"{its} iterations; numpy/scipy on the host's {os.cpu_count()} cores "
+                      f"(CPU time / wall time {cpu / dt:.2f})"}
 
 
 def run_reference(args):
@@ -389,7 +471,7 @@ def run_reference(args):
         cpus.append(cpu)
     ms = 1e3 * statistics.mean(times)
     value = rows / (ms / 1e3)
-    cores = max(1, round(sum(cpus) / sum(times)))
+    cores = os.cpu_count()
     sample = (f"oracle setup + FGMRES solve per step on the same problem family at {nside}^2 "
               f"(eps={args.eps}, angle pi/6, m={args.degree}), {rows} R rows per step")
     print(json.dumps({

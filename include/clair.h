@@ -40,6 +40,10 @@ typedef enum {
 
 enum { CLAIR_COARSEN_FC = 0, CLAIR_COARSEN_AGG = 1 };
 enum { CLAIR_FP64 = 0, CLAIR_MIXED = 1 };
+enum { CLAIR_INVERSE_EXACT = 0, CLAIR_INVERSE_DIAG = 1 };
+enum { CLAIR_KRYLOV_FGMRES = 0, CLAIR_KRYLOV_PCG = 1 };
+/* Largest number of mode vectors (columns of B). */
+#define CLAIR_KMAX 4
 
 /* Solver parameters.  Defaults (clair_params_default) follow the nonsymmetric runs of
  * Section 4.2: coarsening strength 0.25, interpolation strength 0.05, pattern degree
@@ -65,6 +69,16 @@ typedef struct {
   int gmres_maxit;        /* FGMRES iteration cap */
   double rtol;            /* stop when ||f - A u||_2 <= rtol ||f||_2 (true FP64 residual) */
   uint64_t seed;          /* seed of the Arnoldi start vectors (splitmix64, seed + level) */
+  int inverse;            /* block inverses of Algorithm 1: CLAIR_INVERSE_EXACT (Remark 3.2)
+                             or CLAIR_INVERSE_DIAG (the local diagonal, one of the approximate
+                             block inverses of Section 3.1.2) */
+  int iterations;         /* Algorithm 1's loop count k (>= 1).  With the exact inverse the
+                             output is the same for every k (Remark 3.2) and one pass runs */
+  int symmetric;          /* 1: R = P^T, P from Algorithm 1 on A (the symmetric diffusion runs
+                             of Section 4.1); 0: R from Algorithm 1 on A^T (Section 3.1.3) */
+  int krylov;             /* CLAIR_KRYLOV_FGMRES (right-preconditioned flexible GMRES) or
+                             CLAIR_KRYLOV_PCG (preconditioned CG: symmetric A, symmetric = 1,
+                             post_weighted = 1) */
 } clair_params;
 
 typedef struct clair_hierarchy* clair_h;
@@ -96,10 +110,15 @@ typedef struct {
   int64_t fp64_cycle_from;    /* last clair_solve in CLAIR_MIXED: iteration from which the
                                  FP64 cycle took over (a restart cycle ended unconverged or
                                  produced a nonfinite estimate), -1 if it never did */
+  int k;                      /* mode vectors (columns of B, B_P and B_R) */
 } clair_stats_t;
 
 /* Kernel launches issued by this library in this process so far (monotonic counter). */
 int64_t clair_kernel_launches(void);
+
+/* The GPU architecture the library's device code was compiled for, as nvcc's
+ * __CUDA_ARCH_LIST__ value (1030 for sm_103a).  Needs no GPU. */
+int clair_compiled_arch(void);
 
 /* Fills *p with the defaults listed above. */
 clair_status clair_params_default(clair_params* p);
@@ -109,28 +128,47 @@ clair_status clair_params_default(clair_params* p);
  * Section 3.1.3) and P (on A, Algorithm 1), then A_c = R A P (Section 1), until
  * n <= coarse_max or max_levels.
  *   n, nnz, rowptr, col, val : the fine operator A (device CSR, see conventions)
- *   B                        : device float64 [n], the near-nullspace candidate (k = 1)
+ *   k                        : number of mode vectors, 1 <= k <= CLAIR_KMAX (Eq. 3.3: the
+ *                              constraint W B_c = B|_F holds for every column)
+ *   B                        : device float64 [n x k], column-major (mode a at B + a n): the
+ *                              near-nullspace candidates, e.g. the constant vector (k = 1)
+ *   cf_marker                : NULL, or device int8 [n] with 1 = C-point, 0 = F-point: the
+ *                              caller's fine-level splitting, used instead of the library's
+ *                              (coarser levels are split by the library; FC coarsening only,
+ *                              CLAIR_ERR_UNSUPPORTED with CLAIR_COARSEN_AGG)
  *   p                        : host parameters (NULL = defaults)
  *   out                      : receives the new hierarchy; *out = NULL on failure
  * Synchronises `stream` once per level (coarse sizes are data-dependent). */
 clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col,
-                         const double* val, const double* B, const clair_params* p,
-                         void* stream, clair_h* out);
+                         const double* val, int k, const double* B, const signed char* cf_marker,
+                         const clair_params* p, void* stream, clair_h* out);
 
-/* Solve A u = f (hot path, part 2): right-preconditioned FGMRES(gmres_restart) in float64
- * with one V(1,1) cycle (CFF pre, FFC post, Section 4) per iteration, FP32 cycle in
- * CLAIR_MIXED mode.  Stops on the true float64 residual (restart = iterative refinement).
- * In CLAIR_MIXED mode a restart cycle that uses all gmres_restart iterations without
- * converging, or a nonfinite residual estimate, switches the rest of the solve to the
- * FP64 cycle of the same hierarchy (flexible GMRES admits the change; see
+/* Solve A U = F for nrhs right-hand sides (hot path, part 2): per right-hand side (and per
+ * instance of a batch) an independent Krylov process in float64, all of them advancing in
+ * lockstep so that they share every kernel launch: right-preconditioned FGMRES(gmres_restart)
+ * (or preconditioned CG with CLAIR_KRYLOV_PCG) with one V(1,1) cycle (CFF pre, FFC post,
+ * Section 4) per iteration, FP32 cycle in CLAIR_MIXED mode.  Each process stops on its own
+ * true float64 residual ||f_r - A u_r||_2 <= rtol ||f_r||_2 (restarts = iterative
+ * refinement).  In CLAIR_MIXED mode a restart cycle that uses all gmres_restart iterations
+ * without converging, stalls (less than 2x in the worst residual estimate over 10
+ * iterations) or gives a nonfinite estimate switches the rest of the solve to the FP64
+ * cycle of the same hierarchy (flexible GMRES admits the change; see
  * clair_stats_t.fp64_cycle_from).
- *   f     : device float64 [n]
- *   u     : device float64 [n]; input initial guess, output solution
- *   iters, relres : host outputs (iterations done, final ||f - A u|| / ||f||); may be NULL
- * Returns CLAIR_ERR_NOT_CONVERGED if gmres_maxit is reached above rtol (u holds the
- * last iterate).  Synchronises `stream` once per iteration. */
-clair_status clair_solve(clair_h h, const double* f, double* u, void* stream, int* iters,
-                         double* relres);
+ *   f      : device float64 [nrhs x n], right-hand side r at f + r n
+ *   u      : device float64 [nrhs x n]; input initial guesses, output solutions
+ *   nrhs   : number of right-hand sides (>= 1)
+ *   iters, relres : host arrays [nrhs] (may be NULL): iterations and final
+ *            ||f_r - A u_r|| / ||f_r|| per right-hand side (for a batch, the largest over
+ *            its instances; clair_solve_detail gives every instance)
+ * Returns CLAIR_ERR_NOT_CONVERGED if any process reached gmres_maxit above rtol (u holds
+ * the last iterates).  Synchronises `stream` once per iteration. */
+clair_status clair_solve(clair_h h, const double* f, double* u, int nrhs, void* stream,
+                         int* iters, double* relres);
+
+/* Per-process results of the last clair_solve on h: *nseg = nrhs * ninst; iters_host and
+ * relres_host (host arrays [nseg], may be NULL) receive, for right-hand side r and
+ * instance i at index r * ninst + i, its iteration count and final relative residual. */
+clair_status clair_solve_detail(clair_h h, int* nseg, int* iters_host, double* relres_host);
 
 /* One V(1,1) cycle x = M^-1 b on level `level` (x0 = 0), in the hierarchy's precision.
  *   b, x : device float64 [n_level]. */
@@ -144,8 +182,9 @@ clair_status clair_stats(clair_h h, clair_stats_t* out);
  *   A_*   : CSR of A_k (n x n)
  *   R_*   : CSR of R_k (nc x n), identity entry stored at each C-point's own column
  *   P_*   : CSR of P_k (n x nc), identity entry stored in each C-point's row
- *   cf    : int8 [n] C/F splitting;  B_P, B_R: float64 [n] smoothed mode vectors for
- *           P (operator A_k) and R (operator A_k^T);  omega: host scalar weight. */
+ *   cf    : int8 [n] C/F splitting;  B_P, B_R: float64 [n x k] (column-major, k from
+ *           clair_stats) smoothed mode vectors for P (operator A_k) and R (operator
+ *           A_k^T; equal to B_P when symmetric = 1);  omega: host scalar weight. */
 clair_status clair_level_view(clair_h h, int level, int* n, int* nc, int* nnz_A,
                               const int** A_rowptr, const int** A_col, const double** A_val,
                               int* nnz_R, const int** R_rowptr, const int** R_col,
@@ -185,9 +224,10 @@ clair_status clair_local_weights(int n, const int* Ahat_rowptr, const int* Ahat_
 
 /* clair_local_weights without any device memory allocation.  The paper has no
  * counterpart: this is a deployment variant of the same computation, with the same
- * arguments, results (bit for bit) and error codes as clair_local_weights, except that
- * local systems of more than 128 unknowns (which need a per-call tile buffer) are refused
- * with CLAIR_ERR_CAPACITY.
+ * arguments, results (bit for bit: the same kernels in the same order) and error codes as
+ * clair_local_weights, except that local systems of more than 128 unknowns (which need a
+ * per-call tile buffer) are refused with CLAIR_ERR_CAPACITY.  Every refusal happens
+ * before the call writes anything: Z_val is then left untouched.
  *
  * It exists for callers that cannot let a library allocate device memory while they run:
  * applications whose device memory is entirely reserved up front by their own pool or by
@@ -229,16 +269,15 @@ clair_status clair_local_weights_noalloc(int n, const int* Ahat_rowptr, const in
  * and columns offsets_host[i] .. offsets_host[i+1]-1.
  *   ninst, offsets_host : host int [ninst + 1], offsets_host[0] = 0, offsets_host[ninst]
  *                         = n, strictly increasing
- *   other arguments     : as clair_setup (B concatenated over the instances)
+ *   other arguments     : as clair_setup (B and cf_marker concatenated over the instances)
  * CLAIR_ERR_ARG if an entry couples two instances or the offsets are invalid;
  * CLAIR_ERR_UNSUPPORTED if arnoldi_iters > 15.  clair_solve on the result solves all
- * instances at once (one FGMRES on the block-diagonal system, absolute tolerance
- * rtol * min_i ||f_i||, so every instance reaches rtol relative to its own ||f_i||;
- * *relres reports the worst instance). */
+ * instances at once: one Krylov process per instance (and right-hand side), each stopping
+ * at rtol relative to its own ||f_i||, all sharing the V-cycle and vector launches. */
 clair_status clair_setup_batched(int ninst, const int* offsets_host, int n, int nnz,
-                                 const int* rowptr, const int* col, const double* val,
-                                 const double* B, const clair_params* p, void* stream,
-                                 clair_h* out);
+                                 const int* rowptr, const int* col, const double* val, int k,
+                                 const double* B, const signed char* cf_marker,
+                                 const clair_params* p, void* stream, clair_h* out);
 
 /* Per-instance view of level `level` of a hierarchy (a single-problem hierarchy reports
  * one instance).  Output pointers are host arrays and may be NULL:
@@ -257,7 +296,7 @@ clair_status clair_batch_view(clair_h h, int level, int* ninst, int* offsets_hos
  * its own CLAIR hierarchy (R from A, P from A^T: Section 3.1.3 run on A^T). */
 
 /* Hierarchy for A^T: transposes the fine operator of `fwd` on the device and runs
- * clair_setup on it with fwd's parameters and fwd's (unsmoothed) mode vector.
+ * clair_setup on it with fwd's parameters and fwd's (unsmoothed) mode vectors.
  *   fwd : a hierarchy from clair_setup (not modified)
  *   adj : receives the new hierarchy (owned by the caller, release with clair_free);
  *         *adj = NULL on failure

@@ -38,7 +38,7 @@ __all__ = [
     "C_PT", "F_PT", "Params", "lowbias32", "strength", "split_fc", "aggregate",
     "arnoldi_rho", "relax", "relax_cff", "relax_ffc", "smooth_modes", "base_pattern",
     "clair_pattern", "clair_algorithm1", "clair_transfer", "Level", "Hierarchy",
-    "build_hierarchy", "vcycle", "fgmres", "operator_complexity", "work_per_digit",
+    "build_hierarchy", "vcycle", "fgmres", "pcg", "operator_complexity", "work_per_digit",
     "solve", "csr_of",
 ]
 
@@ -64,6 +64,7 @@ class Params:
     inverse: str = "exact"         # block inverses: "exact" (Remark 3.2) or "diag"
     iterations: int = 1            # Algorithm 1 loop count k
     constrain: bool = True         # False reproduces lAIR (Remark 3.1)
+    symmetric: bool = False        # R = P^T (the symmetric diffusion runs of Section 4.1)
 
 
 def csr_of(A) -> sp.csr_matrix:
@@ -513,10 +514,15 @@ def build_hierarchy(A, B: np.ndarray, params: Params, cf_override=None) -> Hiera
         At = A.T.tocsr()
         At.sort_indices()
         lev.B_P = smooth_modes(A, B_P, cf, lev.omega, params.b_smooth_iters)
-        lev.B_R = smooth_modes(At, B_R, cf, lev.omega, params.b_smooth_iters)
         lev.P, _ = clair_transfer(A, cf, lev.B_P, params, agg)
-        Pt, _ = clair_transfer(At, cf, lev.B_R, params, agg)
-        lev.R = Pt.T.tocsr()
+        if params.symmetric:
+            # R = P^T (Section 4.1: the symmetric runs use the transpose of interpolation)
+            lev.B_R = lev.B_P.copy()
+            lev.R = lev.P.T.tocsr()
+        else:
+            lev.B_R = smooth_modes(At, B_R, cf, lev.omega, params.b_smooth_iters)
+            Pt, _ = clair_transfer(At, cf, lev.B_R, params, agg)
+            lev.R = Pt.T.tocsr()
         lev.R.sort_indices()
         Ac = (lev.R @ A) @ lev.P
         Ac = Ac.tocsr()
@@ -603,6 +609,40 @@ def fgmres(A, f: np.ndarray, precond, restart: int, rtol: float, maxit: int,
         r = f - A @ x
         beta = np.linalg.norm(r)
         hist[-1] = beta
+    return x, its, hist
+
+
+def pcg(A, f: np.ndarray, precond, rtol: float, maxit: int, x0: np.ndarray | None = None):
+    """Preconditioned conjugate gradients in float64 (Hestenes-Stiefel with a symmetric
+    positive definite preconditioner; Section 4.1 accelerates the symmetric runs with CG).
+    Stops when the recursive residual meets ``rtol ||f||``; returns ``(x, iterations,
+    history of residual norms)``, the last entry the true residual norm."""
+    A = csr_of(A)
+    x = np.zeros(f.size) if x0 is None else x0.astype(np.float64).copy()
+    fnorm = np.linalg.norm(f)
+    if fnorm == 0.0:
+        return np.zeros(f.size), 0, [0.0]
+    tol = rtol * fnorm
+    r = f - A @ x
+    hist = [np.linalg.norm(r)]
+    its = 0
+    z = precond(r)
+    p = z.copy()
+    rho = r @ z
+    while hist[-1] > tol and its < maxit:
+        q = A @ p
+        alpha = rho / (p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        its += 1
+        hist.append(np.linalg.norm(r))
+        if hist[-1] <= tol:
+            break
+        z = precond(r)
+        rho_new = r @ z
+        p = z + (rho_new / rho) * p
+        rho = rho_new
+    hist[-1] = np.linalg.norm(f - A @ x)
     return x, its, hist
 
 

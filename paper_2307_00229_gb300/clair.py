@@ -28,6 +28,11 @@ CLAIR_COARSEN_FC = 0
 CLAIR_COARSEN_AGG = 1
 CLAIR_FP64 = 0
 CLAIR_MIXED = 1
+CLAIR_INVERSE_EXACT = 0
+CLAIR_INVERSE_DIAG = 1
+CLAIR_KRYLOV_FGMRES = 0
+CLAIR_KRYLOV_PCG = 1
+CLAIR_KMAX = 4
 
 
 class ClairError(RuntimeError):
@@ -52,6 +57,10 @@ class clair_params(ctypes.Structure):
         ("gmres_maxit", ctypes.c_int),
         ("rtol", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("inverse", ctypes.c_int),
+        ("iterations", ctypes.c_int),
+        ("symmetric", ctypes.c_int),
+        ("krylov", ctypes.c_int),
     ]
 
 
@@ -76,6 +85,7 @@ class clair_stats_t(ctypes.Structure):
         ("lsolve_min_bytes", ctypes.c_double),
         ("lsolve_gathered", ctypes.c_int64),
         ("fp64_cycle_from", ctypes.c_int64),
+        ("k", ctypes.c_int),
     ]
 
 
@@ -91,9 +101,10 @@ _PI64 = ctypes.POINTER(ctypes.c_int64)
 
 _SIGNATURES = {
     "clair_params_default": (_I, [ctypes.POINTER(clair_params)]),
-    "clair_setup": (_I, [_I, _I, _P, _P, _P, _P, ctypes.POINTER(clair_params), _P,
+    "clair_setup": (_I, [_I, _I, _P, _P, _P, _I, _P, _P, ctypes.POINTER(clair_params), _P,
                          ctypes.POINTER(_P)]),
-    "clair_solve": (_I, [_P, _P, _P, _P, _PI, _PD]),
+    "clair_solve": (_I, [_P, _P, _P, _I, _P, _PI, _PD]),
+    "clair_solve_detail": (_I, [_P, _PI, _PI, _PD]),
     "clair_vcycle": (_I, [_P, _I, _P, _P, _P]),
     "clair_stats": (_I, [_P, ctypes.POINTER(clair_stats_t)]),
     "clair_level_view": (_I, [_P, _I, _PI, _PI, _PI, ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -105,8 +116,8 @@ _SIGNATURES = {
     "clair_local_weights": (_I, [_I, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _PI64, _PI64]),
     "clair_local_weights_noalloc": (_I, [_I, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _P, _PI64,
                                          _PI64]),
-    "clair_setup_batched": (_I, [_I, _P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(clair_params), _P,
-                                 ctypes.POINTER(_P)]),
+    "clair_setup_batched": (_I, [_I, _P, _I, _I, _P, _P, _P, _I, _P, _P,
+                                 ctypes.POINTER(clair_params), _P, ctypes.POINTER(_P)]),
     "clair_batch_view": (_I, [_P, _I, _PI, _P, _P, _P]),
     "clair_setup_adjoint": (_I, [_P, _P, ctypes.POINTER(_P)]),
     "clair_sddmm_grad": (_I, [_I, _I, _P, _P, _I, _P, _P, _P, _P]),
@@ -114,6 +125,7 @@ _SIGNATURES = {
                                         _P, _P]),
     "clair_last_error": (ctypes.c_char_p, []),
     "clair_kernel_launches": (ctypes.c_int64, []),
+    "clair_compiled_arch": (ctypes.c_int, []),
 }
 
 
@@ -164,31 +176,56 @@ def clair_kernel_launches() -> int:
     return int(load().clair_kernel_launches())
 
 
+def clair_compiled_arch() -> int:
+    return int(load().clair_compiled_arch())
+
+
 def clair_params_default() -> clair_params:
     p = clair_params()
     _check(load().clair_params_default(ctypes.byref(p)))
     return p
 
 
-def clair_setup(rowptr, col, val, B, params: clair_params | None = None, stream=None) -> ctypes.c_void_p:
+def _modes(B, n: int) -> tuple[int, ctypes.c_void_p]:
+    """B as (n,) for one mode or (k, n) for k modes (row a = mode a: the column-major n x k
+    array the C call takes)."""
+    if B.dim() == 1:
+        if B.numel() != n:
+            raise ValueError("B must have n entries")
+        return 1, _dptr(B, torch.float64)
+    if B.dim() != 2 or B.shape[1] != n:
+        raise ValueError("B must be (n,) or (k, n)")
+    return B.shape[0], _dptr(B, torch.float64)
+
+
+def _cf(cf_marker):
+    return None if cf_marker is None else _dptr(cf_marker, torch.int8)
+
+
+def clair_setup(rowptr, col, val, B, params: clair_params | None = None, stream=None,
+                cf_marker=None) -> ctypes.c_void_p:
+    """Hierarchy of A (device CSR).  ``B``: (n,) or (k, n) mode vectors; ``cf_marker``:
+    optional int8 (n,) fine-level splitting (1 = C)."""
     n = rowptr.numel() - 1
+    k, bp = _modes(B, n)
     h = ctypes.c_void_p()
     _check(load().clair_setup(n, col.numel(), _dptr(rowptr, torch.int32), _dptr(col, torch.int32),
-                              _dptr(val, torch.float64), _dptr(B, torch.float64),
+                              _dptr(val, torch.float64), k, bp, _cf(cf_marker),
                               ctypes.byref(params) if params is not None else None,
                               _stream(stream), ctypes.byref(h)))
     return h
 
 
 def clair_setup_batched(offsets, rowptr, col, val, B, params: clair_params | None = None,
-                        stream=None) -> ctypes.c_void_p:
+                        stream=None, cf_marker=None) -> ctypes.c_void_p:
     """Setup of a batch: block-diagonal CSR, instance i owning rows offsets[i]..offsets[i+1]-1."""
     off = (ctypes.c_int * len(offsets))(*[int(x) for x in offsets])
     n = rowptr.numel() - 1
+    k, bp = _modes(B, n)
     h = ctypes.c_void_p()
     _check(load().clair_setup_batched(len(offsets) - 1, off, n, col.numel(), _dptr(rowptr, torch.int32),
-                                      _dptr(col, torch.int32), _dptr(val, torch.float64),
-                                      _dptr(B, torch.float64),
+                                      _dptr(col, torch.int32), _dptr(val, torch.float64), k, bp,
+                                      _cf(cf_marker),
                                       ctypes.byref(params) if params is not None else None,
                                       _stream(stream), ctypes.byref(h)))
     return h
@@ -207,13 +244,34 @@ def clair_batch_view(h, level: int) -> dict:
 
 
 def clair_solve(h, f, u, stream=None, raise_not_converged: bool = True):
-    """Returns ``(status, iterations, relative residual)``."""
-    its, rel = ctypes.c_int(0), ctypes.c_double(0.0)
-    st = load().clair_solve(h, _dptr(f, torch.float64), _dptr(u, torch.float64), _stream(stream),
-                            ctypes.byref(its), ctypes.byref(rel))
+    """Solves for one right-hand side (f, u of shape (n,)) or several (shape (nrhs, n)).
+
+    Returns ``(status, iterations, relative residual)``: scalars for one right-hand side,
+    lists (one entry per right-hand side) for several."""
+    single = f.dim() == 1
+    nrhs = 1 if single else f.shape[0]
+    if u.shape != f.shape:
+        raise ValueError("clair_solve: u and f must have the same shape")
+    its = (ctypes.c_int * nrhs)()
+    rel = (ctypes.c_double * nrhs)()
+    st = load().clair_solve(h, _dptr(f, torch.float64), _dptr(u, torch.float64), nrhs, _stream(stream),
+                            its, rel)
     if st != CLAIR_OK and (st != CLAIR_ERR_NOT_CONVERGED or raise_not_converged):
         _check(st)
-    return st, its.value, rel.value
+    if single:
+        return st, its[0], rel[0]
+    return st, list(its), list(rel)
+
+
+def clair_solve_detail(h) -> tuple[list, list]:
+    """Iterations and relative residuals of every (right-hand side, instance) process of
+    the last solve, index r * ninst + i."""
+    nseg = ctypes.c_int()
+    _check(load().clair_solve_detail(h, ctypes.byref(nseg), None, None))
+    its = (ctypes.c_int * nseg.value)()
+    rel = (ctypes.c_double * nseg.value)()
+    _check(load().clair_solve_detail(h, ctypes.byref(nseg), its, rel))
+    return list(its), list(rel)
 
 
 def clair_vcycle(h, level: int, b, x, stream=None):
@@ -252,7 +310,8 @@ def clair_level_view(h, level: int) -> dict:
         ctypes.byref(nnzR), *(ctypes.byref(p) for p in ptrs[3:6]), ctypes.byref(nnzP),
         *(ctypes.byref(p) for p in ptrs[6:9]), *(ctypes.byref(p) for p in ptrs[9:12]), ctypes.byref(om)))
     N, NC = n.value, nc.value
-    out = {"n": N, "nc": NC, "omega": om.value,
+    K = clair_stats(h).k
+    out = {"n": N, "nc": NC, "omega": om.value, "k": K,
            "A_rowptr": _view(ptrs[0], N + 1, torch.int32), "A_col": _view(ptrs[1], nnzA.value, torch.int32),
            "A_val": _view(ptrs[2], nnzA.value, torch.float64)}
     if NC:
@@ -261,8 +320,9 @@ def clair_level_view(h, level: int) -> dict:
             "R_val": _view(ptrs[5], nnzR.value, torch.float64),
             "P_rowptr": _view(ptrs[6], N + 1, torch.int32), "P_col": _view(ptrs[7], nnzP.value, torch.int32),
             "P_val": _view(ptrs[8], nnzP.value, torch.float64),
-            "cf": _view(ptrs[9], N, torch.int8), "B_P": _view(ptrs[10], N, torch.float64),
-            "B_R": _view(ptrs[11], N, torch.float64)})
+            "cf": _view(ptrs[9], N, torch.int8),
+            "B_P": _view(ptrs[10], N * K, torch.float64).view(K, N).squeeze(0),
+            "B_R": _view(ptrs[11], N * K, torch.float64).view(K, N).squeeze(0)})
     return out
 
 
@@ -362,8 +422,7 @@ class ClairSolve(torch.autograd.Function):
         F = F.detach().contiguous()
         fwd = Hierarchy(clair_setup(rowptr, col, val.detach().contiguous(), B, params))
         U = torch.zeros_like(F)
-        for r in range(F.shape[0]):
-            clair_solve(fwd.handle, F[r], U[r])
+        clair_solve(fwd.handle, F, U)  # every right-hand side in one call
         ctx.fwd = fwd
         ctx.pattern = (rowptr, col)
         ctx.save_for_backward(U)
@@ -376,8 +435,7 @@ class ClairSolve(torch.autograd.Function):
         adj = Hierarchy(clair_setup_adjoint(ctx.fwd.handle))
         gU = gU.detach().contiguous()
         Lam = torch.zeros_like(gU)
-        for r in range(gU.shape[0]):
-            clair_solve(adj.handle, gU[r], Lam[r])
+        clair_solve(adj.handle, gU, Lam)
         dval = torch.empty(col.numel(), dtype=torch.float64, device=U.device)
         clair_sddmm_grad(rowptr, col, Lam, U, dval)
         del adj

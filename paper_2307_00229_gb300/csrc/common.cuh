@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/clair.h"
 
@@ -98,6 +99,13 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Number of SMs of the current device (cached per process).
 int sm_count();
+
+// Runs `set` once per device and `key` (function attributes such as the dynamic
+// shared-memory limit belong to the current device's context), under a lock so that
+// host threads driving several devices do not race.
+void once_per_device(int key, void (*set)());
+enum { ONCE_LSOLVE_F32 = 0, ONCE_LSOLVE_F64, ONCE_LSOLVE_F32D, ONCE_SPGEMM_CTA, ONCE_SPGEMM_FLAT,
+       ONCE_KEYS };
 
 // ------------------------------------------------------------------------------------
 // Device utilities.
@@ -208,6 +216,51 @@ void validate_cf(const signed char* cf, int n, cudaStream_t s);
 bool all_finite(const double* x, long long n, cudaStream_t s);
 
 int partial_blocks();  // number of blocks used by the deterministic reductions
+
+// ------------------------------------------------------------------------------------
+// Segmented Krylov building blocks (krylov.cu): independent Krylov processes in lockstep,
+// one per segment = (right-hand side, instance) of a long vector.
+// ------------------------------------------------------------------------------------
+struct Segments {
+  int nseg = 0, nchunk = 0;
+  long long len = 0;              // nrhs * n rows
+  int* chunk_seg = nullptr;       // [nchunk] segment of each chunk
+  long long* chunk_lo = nullptr;  // [nchunk] first row of each chunk
+  long long* chunk_hi = nullptr;  // [nchunk] one past its last row
+  int* seg_chunk0 = nullptr;      // [nseg + 1] first chunk of each segment
+  // segment r * ninst + i = rows r * n + off[i] .. r * n + off[i + 1] - 1
+  void build(int nrhs, const std::vector<int>& off, cudaStream_t s);
+  void release(cudaStream_t s);
+};
+// out[seg * ldo + q] = <V_q, w> over the segment's rows (V_q at V + q * ldv), q < m
+void seg_dot(const Segments& S, const double* V, long long ldv, int m, const double* w,
+             double* out, int ldo, double* partial, cudaStream_t s);
+// w -= sum_q coef[seg * ldc + q] V_q on each segment
+void seg_axpy(const Segments& S, const double* V, long long ldv, int m, const double* coef,
+              int ldc, double* w, cudaStream_t s);
+// y = x * f[seg * ldf]
+void seg_scale(const Segments& S, const double* x, const double* f, int ldf, double* y,
+               cudaStream_t s);
+// y += a[seg] x ;  z = x + b[seg] z
+void seg_axpy1(const Segments& S, const double* x, const double* a, double* y, cudaStream_t s);
+void seg_xpby(const Segments& S, const double* x, const double* b, double* z, cudaStream_t s);
+void seg_tolerance_launch(const Segments& S, const double* fn2, double rtol, double* tol,
+                          double* fnorm, double* u, cudaStream_t s);
+void seg_gmres_start_launch(int nseg, int m, const double* beta2, const double* tol, double* g,
+                            double* inv, int* active, int* jend, double* summary, cudaStream_t s);
+void seg_gmres_givens_launch(int nseg, int m, int j, const double* h1, const double* h2, int ldh12,
+                             const double* wn2, double* H, double* cs, double* sn, double* g,
+                             double* inv, int* active, int* jend, int* its, const double* tol,
+                             double* summary, cudaStream_t s);
+void seg_gmres_backsolve_launch(int nseg, int m, const double* H, const double* g, const int* jend,
+                                double* ny, cudaStream_t s);
+void seg_cg_start_launch(int nseg, const double* rr, const double* tol, const double* rz,
+                         double* rho, int* active, double* summary, cudaStream_t s);
+void seg_cg_alpha_launch(int nseg, const double* rho, const double* pq, const int* active,
+                         double* alpha, double* malpha, cudaStream_t s);
+void seg_cg_beta_launch(int nseg, const double* rr, const double* tol, const double* rho_new,
+                        double* rho, int* active, int* its, double* beta, double* summary,
+                        cudaStream_t s);
 
 // Counters of the batched local solves: zero-pivot blocks, F-points skipped by the
 // projection, systems per size bucket (T <= 8, 16, 32, 64, 128, larger), and the

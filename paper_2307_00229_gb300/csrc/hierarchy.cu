@@ -30,8 +30,11 @@ void smooth_modes(const Csr& M, const double* dinv, const signed char* cf, const
                   int sweeps, double* Bv, double* tmp, cudaStream_t s);
 void transfer_solve(const Csr& Ahat, const int* cpts, Csr& Z, int precision, LocalStats& st,
                     cudaStream_t s);
-void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const double* B,
+void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const double* B, int k,
                       LocalStats& st, Csr* keep_t, cudaStream_t s);
+void transfer_diag(const Csr& Ahat, const signed char* cf, const int* cpts, Csr& Z,
+                   const double* B, int k, int iterations, LocalStats& st, Csr* keep_t,
+                   cudaStream_t s);
 template <class T>
 void jacobi_from_zero(int rows, const T* dinv, const signed char* cf, int which, T omega,
                       const T* b, T* x, cudaStream_t s);
@@ -81,11 +84,21 @@ struct Level {
   float *b32 = nullptr, *x32 = nullptr, *y32 = nullptr, *r32 = nullptr;
 };
 
+// Krylov workspace of one solve call: nrhs right-hand sides of all instances as nseg =
+// nrhs * ninst independent processes (segments) in lockstep.  Vectors have N = nrhs * n
+// rows (right-hand side r at offset r * n); V (m+1 vectors) and Z (m vectors) are stored
+// one vector after another.  Per-segment scalars: the Hessenberg matrices, rotations and
+// right-hand sides of the least-squares problems, tolerances and iteration counts.
 struct Krylov {
-  int n = 0, m = 0;
+  int nrhs = 0, m = 0, n = 0;
+  long long N = 0;
+  Segments S;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
-  double *h1 = nullptr, *h2 = nullptr, *scal = nullptr, *partial = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *partial = nullptr;
+  double *fn2 = nullptr, *fnorm = nullptr, *tol = nullptr, *beta2 = nullptr, *wn2 = nullptr;
+  double *inv = nullptr, *summary = nullptr, *cg = nullptr;
+  int *active = nullptr, *jend = nullptr, *its = nullptr;
   double* host = nullptr;  // pinned scalars
 };
 
@@ -114,6 +127,9 @@ struct clair_hierarchy {
   int coarse_nblk = 1;
   bool cycle_fp64 = false;                  // MIXED solve fell back to the FP64 cycle
   int fp64_from = -1;                       // iteration of that fallback (-1: none)
+  int kmodes = 1;                           // mode vectors (columns of B)
+  std::vector<int> last_its;                // per segment, last solve
+  std::vector<double> last_rel;
 };
 
 namespace clair {
@@ -161,6 +177,23 @@ static void release_level(Level& L, cudaStream_t s) {
   dfree(L.r32, s);
 }
 
+static void release_krylov(Krylov& k, cudaStream_t s) {
+  k.S.release(s);
+  for (double** p : {&k.V, &k.Z, &k.w, &k.r, &k.H, &k.cs, &k.sn, &k.g, &k.y, &k.h1, &k.h2,
+                     &k.partial, &k.fn2, &k.fnorm, &k.tol, &k.beta2, &k.wn2, &k.inv, &k.summary,
+                     &k.cg})
+    dfree(*p, s);
+  dfree(k.active, s);
+  dfree(k.jend, s);
+  dfree(k.its, s);
+  if (k.host) {
+    cudaStreamSynchronize(s);
+    cudaFreeHost(k.host);
+  }
+  k.host = nullptr;
+  k.nrhs = 0;
+}
+
 static void release_all(clair_hierarchy* h) {
   cudaStream_t s = h->stream;
   for (auto& L : h->lv) release_level(L, s);
@@ -169,27 +202,12 @@ static void release_all(clair_hierarchy* h) {
   dfree(h->Inv32, s);
   dfree(h->coarse_off, s);
   dfree(h->coarse_ioff, s);
-  Krylov& k = h->kr;
-  dfree(k.V, s);
-  dfree(k.Z, s);
-  dfree(k.w, s);
-  dfree(k.r, s);
-  dfree(k.H, s);
-  dfree(k.cs, s);
-  dfree(k.sn, s);
-  dfree(k.g, s);
-  dfree(k.y, s);
-  dfree(k.h1, s);
-  dfree(k.h2, s);
-  dfree(k.scal, s);
-  dfree(k.partial, s);
-  if (k.host) cudaFreeHost(k.host);
+  release_krylov(h->kr, s);
   if (h->cycle_exec) cudaGraphExecDestroy(h->cycle_exec);
   h->cycle_exec = nullptr;
   dfree(h->vin, s);
   dfree(h->zout, s);
   dfree(h->B0, s);
-  k.host = nullptr;
 }
 
 __global__ void inject(const double* __restrict__ x, const int* __restrict__ cpts, int nc,
@@ -377,17 +395,19 @@ struct SideStream {
 };
 
 // Builds the hierarchy from the fine operator (already copied into h->lv[0].A).
-static void setup_levels(clair_hierarchy* h, const double* B0) {
+static void setup_levels(clair_hierarchy* h, const double* B0, const signed char* cf_marker) {
   cudaStream_t s = h->stream;
   const clair_params& p = h->p;
   const bool batch = h->ninst > 1;
   const int ninst = h->ninst;
+  const int km = h->kmodes;
+  const bool sym = p.symmetric != 0;
   {
     Level& L0 = h->lv[0];
-    L0.B_P = dalloc<double>(L0.n, s);
-    L0.B_R = dalloc<double>(L0.n, s);
-    CLAIR_CUDA(cudaMemcpyAsync(L0.B_P, B0, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, s));
-    CLAIR_CUDA(cudaMemcpyAsync(L0.B_R, B0, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, s));
+    L0.B_P = dalloc<double>((size_t)L0.n * km, s);
+    L0.B_R = dalloc<double>((size_t)L0.n * km, s);
+    CLAIR_CUDA(cudaMemcpyAsync(L0.B_P, B0, sizeof(double) * L0.n * km, cudaMemcpyDeviceToDevice, s));
+    CLAIR_CUDA(cudaMemcpyAsync(L0.B_R, B0, sizeof(double) * L0.n * km, cudaMemcpyDeviceToDevice, s));
   }
   // pinned buffers of the host Ritz steps; declared before the side stream so that the
   // stream (whose destructor waits for it) is gone before they are released
@@ -456,7 +476,10 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
       strength(L.A, rmaxA, p.theta_coarsen, 0, sA, s);
       strength(At, rmaxA, p.theta_coarsen, 1, sAt, s);
       L.cf = dalloc<signed char>(n, s);
-      if (p.coarsen == CLAIR_COARSEN_AGG) {
+      if (k == 0 && cf_marker) {
+        // the caller's splitting replaces step a2 on the fine level
+        CLAIR_CUDA(cudaMemcpyAsync(L.cf, cf_marker, n, cudaMemcpyDeviceToDevice, s));
+      } else if (p.coarsen == CLAIR_COARSEN_AGG) {
         agg = dalloc<int>(n, s);
         aggregate(L.A, At, sA, sAt, L.lbase, L.cf, agg, s);
       } else {
@@ -514,18 +537,26 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
     {
       ClockScope clk(PH_SMOOTH, ss.s2);
       double* tmp = dalloc<double>(n, ss.s2);
+      // each mode vector separately; the symmetric variant (R = P^T) needs only A's
+      double* wd = nullptr;
       if (batch) {
         // each instance's weight folded into D^-1, unit scalar weight
-        double* wd = dalloc<double>(n, ss.s2);
+        wd = dalloc<double>(n, ss.s2);
         instance_weights<double><<<ceil_div(n, 256), 256, 0, ss.s2>>>(L.inst, om_k, L.dinv, n, wd); ::clair::count_launch();
         CLAIR_LAUNCHED();
-        smooth_modes(L.A, wd, L.cf, nullptr, p.b_smooth_iters, L.B_P, tmp, ss.s2);
-        smooth_modes(At, wd, L.cf, nullptr, p.b_smooth_iters, L.B_R, tmp, ss.s2);
-        dfree(wd, ss.s2);
-      } else {
-        smooth_modes(L.A, L.dinv, L.cf, om_k, p.b_smooth_iters, L.B_P, tmp, ss.s2);
-        smooth_modes(At, L.dinv, L.cf, om_k, p.b_smooth_iters, L.B_R, tmp, ss.s2);
       }
+      for (int a = 0; a < km; ++a) {
+        double* bp = L.B_P + (size_t)a * n;
+        double* br = L.B_R + (size_t)a * n;
+        smooth_modes(L.A, batch ? wd : L.dinv, L.cf, batch ? nullptr : om_k, p.b_smooth_iters, bp,
+                     tmp, ss.s2);
+        if (sym)
+          CLAIR_CUDA(cudaMemcpyAsync(br, bp, sizeof(double) * n, cudaMemcpyDeviceToDevice, ss.s2));
+        else
+          smooth_modes(At, batch ? wd : L.dinv, L.cf, batch ? nullptr : om_k, p.b_smooth_iters, br,
+                       tmp, ss.s2);
+      }
+      dfree(wd, ss.s2);
       dfree(tmp, ss.s2);
     }
     CLAIR_CUDA(cudaEventRecord(ss.join, ss.s2));
@@ -542,18 +573,29 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
       int* Mrp = nullptr;
       int* Mcol = nullptr;
       if (agg) aggregate_members(agg, n, L.nc, &Mrp, &Mcol, s);
-      build_pattern(L.A, sR, L.cf, L.cpts, L.nc, n, p.degree, Mrp, Mcol, L.R, s);
+      if (!sym) build_pattern(L.A, sR, L.cf, L.cpts, L.nc, n, p.degree, Mrp, Mcol, L.R, s);
       build_pattern(At, sP, L.cf, L.cpts, L.nc, n, p.degree, Mrp, Mcol, Pt, s);
       dfree(Mrp, s);
       dfree(Mcol, s);
       dfree(agg, s);
     }
-    transfer_solve(At, L.cpts, L.R, p.precision, h->st, s);
-    transfer_solve(L.A, L.cpts, Pt, p.precision, h->st, s);
-    CLAIR_CUDA(cudaStreamWaitEvent(s, ss.join, 0));
-    transfer_project(L.cf, L.cpts, L.R, L.B_R, h->st, nullptr, s);
-    transfer_project(L.cf, L.cpts, Pt, L.B_P, h->st, &L.P, s);
-    Pt.release(s);
+    if (p.inverse == CLAIR_INVERSE_EXACT) {
+      // exact block inverses: the local solves need no mode vector and overlap the smoothing
+      if (!sym) transfer_solve(At, L.cpts, L.R, p.precision, h->st, s);
+      transfer_solve(L.A, L.cpts, Pt, p.precision, h->st, s);
+      CLAIR_CUDA(cudaStreamWaitEvent(s, ss.join, 0));
+      if (!sym) transfer_project(L.cf, L.cpts, L.R, L.B_R, km, h->st, nullptr, s);
+      transfer_project(L.cf, L.cpts, Pt, L.B_P, km, h->st, &L.P, s);
+    } else {
+      // diagonal block inverses: every pass of Algorithm 1's loop projects (needs B)
+      CLAIR_CUDA(cudaStreamWaitEvent(s, ss.join, 0));
+      if (!sym) transfer_diag(At, L.cf, L.cpts, L.R, L.B_R, km, p.iterations, h->st, nullptr, s);
+      transfer_diag(L.A, L.cf, L.cpts, Pt, L.B_P, km, p.iterations, h->st, &L.P, s);
+    }
+    if (sym)
+      L.R = Pt;  // R = P^T: the coarse-row form of P is R
+    else
+      Pt.release(s);
     dfree(rmaxA, s);
     dfree(rmaxAt, s);
     dfree(sA, s);
@@ -569,11 +611,15 @@ static void setup_levels(clair_hierarchy* h, const double* B0) {
     Level C;
     C.A = Ac;
     C.n = Ac.rows;
-    C.B_P = dalloc<double>(C.n, s);
-    C.B_R = dalloc<double>(C.n, s);
+    C.B_P = dalloc<double>((size_t)C.n * km, s);
+    C.B_R = dalloc<double>((size_t)C.n * km, s);
     if (C.n) {
-      inject<<<ceil_div(C.n, 256), 256, 0, s>>>(L.B_P, L.cpts, C.n, C.B_P); ::clair::count_launch();
-      inject<<<ceil_div(C.n, 256), 256, 0, s>>>(L.B_R, L.cpts, C.n, C.B_R); ::clair::count_launch();
+      for (int a = 0; a < km; ++a) {
+        inject<<<ceil_div(C.n, 256), 256, 0, s>>>(L.B_P + (size_t)a * n, L.cpts, C.n,
+                                                  C.B_P + (size_t)a * C.n); ::clair::count_launch();
+        inject<<<ceil_div(C.n, 256), 256, 0, s>>>(L.B_R + (size_t)a * n, L.cpts, C.n,
+                                                  C.B_R + (size_t)a * C.n); ::clair::count_launch();
+      }
     }
     CLAIR_LAUNCHED();
     if (batch) {
@@ -785,222 +831,260 @@ static void apply_precond(clair_hierarchy* h, int k, const double* v, double* z)
   CLAIR_CUDA(cudaMemcpyAsync(z, h->zout, bytes, cudaMemcpyDeviceToDevice, s));
 }
 
-// --- FGMRES -----------------------------------------------------------------------------
-// scal: [0] ||f||^2, [1] beta^2, [2] ||w||^2, [3] inv norm, [4] |g_{j+1}|, [5] ||r||^2
-__global__ void gmres_start(double* __restrict__ g, int m, const double* __restrict__ scal,
-                            double* __restrict__ inv) {
-  if (threadIdx.x != 0) return;
-  const double beta = sqrt(scal[1]);
-  for (int i = 0; i <= m; ++i) g[i] = 0.0;
-  g[0] = beta;
-  *inv = beta > 0.0 ? 1.0 / beta : 0.0;
-}
-
-__global__ void gmres_givens(double* __restrict__ H, int ldh, int j, const double* __restrict__ h1,
-                             const double* __restrict__ h2, double* __restrict__ cs,
-                             double* __restrict__ sn, double* __restrict__ g,
-                             double* __restrict__ scal) {
-  if (threadIdx.x != 0) return;
-  double* col = H + (long long)j * ldh;
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-  const double hn = sqrt(scal[2]);
-  col[j + 1] = hn;
-  scal[3] = hn > 0.0 ? 1.0 / hn : 0.0;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-    col[i] = t;
-  }
-  const double den = hypot(col[j], col[j + 1]);
-  cs[j] = den > 0.0 ? col[j] / den : 1.0;
-  sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
-  col[j] = den;
-  col[j + 1] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  scal[4] = fabs(g[j + 1]);
-}
-
-// y = R^-1 g (upper triangular, size jend); stores -y for the update x -= Z (-y).
-__global__ void gmres_backsolve(const double* __restrict__ H, int ldh, int jend,
-                                const double* __restrict__ g, double* __restrict__ ny) {
-  if (threadIdx.x != 0) return;
-  double y[64];
-  for (int i = jend - 1; i >= 0; --i) {
-    double acc = g[i];
-    for (int c = i + 1; c < jend; ++c) acc -= H[i + (long long)c * ldh] * y[c];
-    const double d = H[i + (long long)i * ldh];
-    y[i] = d != 0.0 ? acc / d : 0.0;
-  }
-  for (int i = 0; i < jend; ++i) ny[i] = -y[i];
-}
-
-__global__ void scale_into(const double* __restrict__ w, double* __restrict__ v, long long n,
-                           const double* __restrict__ s) {
-  const double f = *s;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    v[i] = w[i] * f;
-}
-
-static void alloc_krylov(clair_hierarchy* h) {
+// --- Krylov solvers ---------------------------------------------------------------------
+static void ensure_krylov(clair_hierarchy* h, int nrhs) {
   cudaStream_t s = h->stream;
   Krylov& k = h->kr;
-  k.n = h->lv[0].n;
-  k.m = h->p.gmres_restart;
-  const long long n = k.n;
-  const int m = k.m;
-  k.V = dalloc<double>((m + 1) * n, s);
-  k.Z = dalloc<double>(m * n, s);
-  k.w = dalloc<double>(n, s);
-  k.r = dalloc<double>(n, s);
-  k.H = dalloc<double>((m + 1) * m, s);
-  k.cs = dalloc<double>(m, s);
-  k.sn = dalloc<double>(m, s);
-  k.g = dalloc<double>(m + 1, s);
-  k.y = dalloc<double>(m, s);
-  k.h1 = dalloc<double>(m + 1, s);
-  k.h2 = dalloc<double>(m + 1, s);
-  k.scal = dalloc<double>(8, s);
-  k.partial = dalloc<double>((size_t)partial_blocks() * (m + 2), s);
-  CLAIR_CUDA(cudaMallocHost(&k.host, sizeof(double) * 8));
+  const int n = h->lv[0].n, m = h->p.gmres_restart;
+  if (k.V && k.nrhs == nrhs && k.m == m && k.n == n) return;
+  release_krylov(k, s);
+  k.nrhs = nrhs;
+  k.m = m;
+  k.n = n;
+  k.N = (long long)nrhs * n;
+  const std::vector<int> off = h->ninst > 1 ? h->lv[0].off : std::vector<int>{0, n};
+  k.S.build(nrhs, off, s);
+  const long long N = k.N;
+  const int nseg = k.S.nseg;
+  k.V = dalloc<double>((size_t)std::max(m + 1, 3) * N, s);  // CG keeps z, p, q in V
+  k.Z = dalloc<double>((size_t)m * N, s);
+  k.w = dalloc<double>(N, s);
+  k.r = dalloc<double>(N, s);
+  k.H = dalloc<double>((size_t)nseg * m * (m + 1), s);
+  k.cs = dalloc<double>((size_t)nseg * m, s);
+  k.sn = dalloc<double>((size_t)nseg * m, s);
+  k.g = dalloc<double>((size_t)nseg * (m + 1), s);
+  k.y = dalloc<double>((size_t)nseg * m, s);
+  k.h1 = dalloc<double>((size_t)nseg * (m + 1), s);
+  k.h2 = dalloc<double>((size_t)nseg * (m + 1), s);
+  k.partial = dalloc<double>((size_t)(m + 1) * std::max(k.S.nchunk, 1), s);
+  for (double** p : {&k.fn2, &k.fnorm, &k.tol, &k.beta2, &k.wn2, &k.inv})
+    *p = dalloc<double>(nseg, s);
+  k.cg = dalloc<double>((size_t)8 * nseg, s);
+  k.summary = dalloc<double>(4, s);
+  k.active = dalloc<int>(nseg, s);
+  k.jend = dalloc<int>(nseg, s);
+  k.its = dalloc<int>(nseg, s);
+  CLAIR_CUDA(cudaMallocHost(&k.host, sizeof(double) * 4));
 }
 
-static double read_scalar(clair_hierarchy* h, const double* dev) {
-  CLAIR_CUDA(cudaMemcpyAsync(h->kr.host, dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+// (number of active segments, largest residual / tolerance among them)
+static void read_summary(clair_hierarchy* h, double* active, double* ratio) {
+  CLAIR_CUDA(cudaMemcpyAsync(h->kr.host, h->kr.summary, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
   CLAIR_CUDA(cudaStreamSynchronize(h->stream));
-  return h->kr.host[0];
+  *active = h->kr.host[0];
+  *ratio = h->kr.host[1];
 }
 
-// ||x_i|| for every instance of a batch (host)
-static std::vector<double> instance_norms(clair_hierarchy* h, const double* x) {
-  cudaStream_t s = h->stream;
-  const std::vector<int>& off = h->lv[0].off;
-  const int ninst = (int)off.size() - 1;
-  int* d_off = dalloc<int>(ninst + 1, s);
-  double* d_out = dalloc<double>(ninst, s);
-  CLAIR_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice, s));
-  instance_sumsq<<<ninst, 256, 0, s>>>(x, d_off, d_out); ::clair::count_launch();
-  CLAIR_LAUNCHED();
-  std::vector<double> out(ninst);
-  CLAIR_CUDA(cudaMemcpyAsync(out.data(), d_out, sizeof(double) * ninst, cudaMemcpyDeviceToHost, s));
-  CLAIR_CUDA(cudaStreamSynchronize(s));
-  dfree(d_off, s);
-  dfree(d_out, s);
-  for (double& v : out) v = sqrt(v);
-  return out;
+// Z = M^-1 V (every right-hand side), W = A X (every right-hand side), R = F - A U
+static void precond_all(clair_hierarchy* h, const double* v, double* z) {
+  const Krylov& k = h->kr;
+  for (int r = 0; r < k.nrhs; ++r) apply_precond(h, 0, v + (size_t)r * k.n, z + (size_t)r * k.n);
+}
+static void matvec_all(clair_hierarchy* h, const double* x, double* y) {
+  const Krylov& k = h->kr;
+  for (int r = 0; r < k.nrhs; ++r)
+    spmv(h->lv[0].A, x + (size_t)r * k.n, y + (size_t)r * k.n, 1.0, 0.0, h->stream);
+}
+static void residual_all(clair_hierarchy* h, const double* f, const double* u, double* r) {
+  const Krylov& k = h->kr;
+  for (int q = 0; q < k.nrhs; ++q)
+    residual(h->lv[0].A, f + (size_t)q * k.n, u + (size_t)q * k.n, r + (size_t)q * k.n, h->stream);
 }
 
-// A batch is solved as one block-diagonal system: the absolute tolerance is rtol times the
-// smallest instance right-hand-side norm, so every instance's residual (bounded by the
-// global one) is within rtol of its own ||f_i||.
-static clair_status fgmres(clair_hierarchy* h, const double* f, double* u, int* iters_out,
-                           double* relres_out) {
+// Per-segment results of the finished solve into the hierarchy (host).
+static bool finish_segments(clair_hierarchy* h) {
   cudaStream_t s = h->stream;
   Krylov& k = h->kr;
-  const Level& L0 = h->lv[0];
-  const int n = k.n, m = k.m;
-  const int grid = std::min(ceil_div(n, 256), 32 * sm_count());
-  multi_dot(f, 1, f, n, k.scal + 0, k.partial, s);
-  const double fnorm = sqrt(read_scalar(h, k.scal + 0));
-  int its = 0;
-  if (fnorm == 0.0) {
-    CLAIR_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, s));
-    if (iters_out) *iters_out = 0;
-    if (relres_out) *relres_out = 0.0;
-    return CLAIR_OK;
+  const int nseg = k.S.nseg;
+  std::vector<double> b2(nseg), fn(nseg), tl(nseg);
+  h->last_its.assign(nseg, 0);
+  CLAIR_CUDA(cudaMemcpyAsync(b2.data(), k.beta2, sizeof(double) * nseg, cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaMemcpyAsync(fn.data(), k.fnorm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaMemcpyAsync(tl.data(), k.tol, sizeof(double) * nseg, cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaMemcpyAsync(h->last_its.data(), k.its, sizeof(int) * nseg, cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  h->last_rel.assign(nseg, 0.0);
+  bool ok = true;
+  for (int i = 0; i < nseg; ++i) {
+    const double b = sqrt(b2[i]);
+    h->last_rel[i] = fn[i] > 0.0 ? b / fn[i] : 0.0;
+    if (b > tl[i]) ok = false;
   }
-  double tol = h->p.rtol * fnorm;
-  std::vector<double> fi;
-  if (h->ninst > 1) {
-    fi = instance_norms(h, f);
-    double fmin = fnorm;
-    for (double v : fi)
-      if (v > 0.0) fmin = std::min(fmin, v);
-    tol = h->p.rtol * fmin;
-  }
-  residual(L0.A, f, u, k.r, s);
-  multi_dot(k.r, 1, k.r, n, k.scal + 1, k.partial, s);
-  double beta = sqrt(read_scalar(h, k.scal + 1));
-  CLAIR_REQUIRE(isfinite(beta), CLAIR_ERR_NONFINITE, "nonfinite initial residual");
-  // MIXED: the FP32 cycle carries ~7 digits; where the hierarchy's weights span more than
-  // that (near-pure advection after mode smoothing) it stops reducing the residual.  A
-  // restart cycle that ends unconverged, or a nonfinite estimate (that cycle is
-  // discarded), switches the rest of the solve to the FP64 cycle on the same hierarchy.
-  h->cycle_fp64 = false;
-  h->fp64_from = -1;
+  return ok;
+}
+
+// MIXED policy: the FP32 cycle carries ~7 digits; where the hierarchy's weights span more
+// than that (near-pure advection after mode smoothing) it stops reducing the residual.  A
+// restart cycle that ends unconverged, stalls (less than 2x gain in the worst active
+// segment's residual estimate over 10 iterations; its directions are kept: it is still a
+// valid flexible preconditioner) or produces a nonfinite estimate (that cycle is
+// discarded) hands the rest of the solve to the FP64 cycle of the same hierarchy.
+constexpr int kStallWindow = 10;
+
+// Right-preconditioned FGMRES(m) per segment, float64; stops each segment on its true
+// residual ||f_s - A u_s|| <= rtol ||f_s|| (restarts act as iterative refinement).
+static bool fgmres(clair_hierarchy* h, const double* f, double* u) {
+  cudaStream_t s = h->stream;
+  Krylov& k = h->kr;
+  const Segments& S = k.S;
+  const int m = k.m, nseg = S.nseg;
+  const long long N = k.N;
   const bool mixed = h->p.precision == CLAIR_MIXED;
-  // a MIXED cycle that gains less than 2x in the residual estimate over 10 iterations has
-  // stalled: its directions are kept (it is still a valid flexible preconditioner) and
-  // the following cycles use FP64
-  constexpr int kStallWindow = 10;
-  std::vector<double> est_hist;
-  while (beta > tol && its < h->p.gmres_maxit) {
-    gmres_start<<<1, 32, 0, s>>>(k.g, m, k.scal, k.scal + 3); ::clair::count_launch();
-    scale_into<<<grid, 256, 0, s>>>(k.r, k.V, n, k.scal + 3); ::clair::count_launch();
-    CLAIR_LAUNCHED();
-    int jend = 0;
+  seg_dot(S, f, 0, 1, f, k.fn2, 1, k.partial, s);
+  seg_tolerance_launch(S, k.fn2, h->p.rtol, k.tol, k.fnorm, u, s);
+  CLAIR_CUDA(cudaMemsetAsync(k.its, 0, sizeof(int) * nseg, s));
+  residual_all(h, f, u, k.r);
+  seg_dot(S, k.r, 0, 1, k.r, k.beta2, 1, k.partial, s);
+  seg_gmres_start_launch(nseg, m, k.beta2, k.tol, k.g, k.inv, k.active, k.jend, k.summary, s);
+  double nact = 0, ratio = 0;
+  read_summary(h, &nact, &ratio);
+  CLAIR_REQUIRE(isfinite(ratio), CLAIR_ERR_NONFINITE, "nonfinite initial residual");
+  int its = 0;
+  std::vector<double> hist;
+  while (nact > 0 && its < h->p.gmres_maxit) {
+    seg_scale(S, k.r, k.inv, 1, k.V, s);
+    int jmax = 0;
     bool discarded = false, stalled = false;
+    hist.clear();
     for (int j = 0; j < m; ++j) {
-      double* vj = k.V + (size_t)j * n;
-      double* zj = k.Z + (size_t)j * n;
+      double* vj = k.V + (size_t)j * N;
+      double* zj = k.Z + (size_t)j * N;
       {
         ClockScope clk(PH_VCYCLE, s);
-        apply_precond(h, 0, vj, zj);
+        precond_all(h, vj, zj);
       }
       ClockScope clk(PH_KRYLOV, s);
-      spmv(L0.A, zj, k.w, 1.0, 0.0, s);
-      multi_dot(k.V, j + 1, k.w, n, k.h1, k.partial, s);
-      multi_axpy(k.V, j + 1, k.h1, k.w, n, s);
-      multi_dot(k.V, j + 1, k.w, n, k.h2, k.partial, s);
-      multi_axpy(k.V, j + 1, k.h2, k.w, n, s);
-      multi_dot(k.w, 1, k.w, n, k.scal + 2, k.partial, s);
-      gmres_givens<<<1, 32, 0, s>>>(k.H, m + 1, j, k.h1, k.h2, k.cs, k.sn, k.g, k.scal); ::clair::count_launch();
-      scale_into<<<grid, 256, 0, s>>>(k.w, k.V + (size_t)(j + 1) * n, n, k.scal + 3); ::clair::count_launch();
-      CLAIR_LAUNCHED();
+      matvec_all(h, zj, k.w);
+      seg_dot(S, k.V, N, j + 1, k.w, k.h1, m + 1, k.partial, s);
+      seg_axpy(S, k.V, N, j + 1, k.h1, m + 1, k.w, s);
+      seg_dot(S, k.V, N, j + 1, k.w, k.h2, m + 1, k.partial, s);
+      seg_axpy(S, k.V, N, j + 1, k.h2, m + 1, k.w, s);
+      seg_dot(S, k.w, 0, 1, k.w, k.wn2, 1, k.partial, s);
+      seg_gmres_givens_launch(nseg, m, j, k.h1, k.h2, m + 1, k.wn2, k.H, k.cs, k.sn, k.g, k.inv,
+                              k.active, k.jend, k.its, k.tol, k.summary, s);
+      seg_scale(S, k.w, k.inv, 1, k.V + (size_t)(j + 1) * N, s);
       ++its;
-      jend = j + 1;
-      const double est = read_scalar(h, k.scal + 4);
-      if (!isfinite(est) && mixed && !h->cycle_fp64) {
-        jend = 0;  // discard this cycle's directions
+      jmax = j + 1;
+      read_summary(h, &nact, &ratio);
+      if (!isfinite(ratio) && mixed && !h->cycle_fp64) {
+        CLAIR_CUDA(cudaMemsetAsync(k.jend, 0, sizeof(int) * nseg, s));  // discard the cycle
         discarded = true;
         break;
       }
-      CLAIR_REQUIRE(isfinite(est), CLAIR_ERR_NONFINITE, "nonfinite residual estimate");
-      if (est <= tol || its >= h->p.gmres_maxit) break;
-      est_hist.push_back(est);
-      if (mixed && !h->cycle_fp64 && j + 1 >= kStallWindow &&
-          est > 0.5 * est_hist[est_hist.size() - kStallWindow]) {
+      CLAIR_REQUIRE(isfinite(ratio), CLAIR_ERR_NONFINITE, "nonfinite residual estimate");
+      if (nact == 0 || its >= h->p.gmres_maxit) break;
+      hist.push_back(ratio);
+      if (mixed && !h->cycle_fp64 && (int)hist.size() > kStallWindow &&
+          ratio > 0.5 * hist[hist.size() - 1 - kStallWindow]) {
         stalled = true;
         break;
       }
     }
-    if (jend > 0) {
-      gmres_backsolve<<<1, 32, 0, s>>>(k.H, m + 1, jend, k.g, k.y); ::clair::count_launch();
-      CLAIR_LAUNCHED();
-      multi_axpy(k.Z, jend, k.y, u, n, s);
+    {
+      ClockScope clk(PH_KRYLOV, s);
+      seg_gmres_backsolve_launch(nseg, m, k.H, k.g, k.jend, k.y, s);
+      seg_axpy(S, k.Z, N, jmax, k.y, m, u, s);
+      residual_all(h, f, u, k.r);
+      seg_dot(S, k.r, 0, 1, k.r, k.beta2, 1, k.partial, s);
+      seg_gmres_start_launch(nseg, m, k.beta2, k.tol, k.g, k.inv, k.active, k.jend, k.summary, s);
     }
-    residual(L0.A, f, u, k.r, s);
-    multi_dot(k.r, 1, k.r, n, k.scal + 1, k.partial, s);
-    beta = sqrt(read_scalar(h, k.scal + 1));
-    CLAIR_REQUIRE(isfinite(beta), CLAIR_ERR_NONFINITE, "nonfinite residual");
-    // (a cycle that stopped on its estimate but not on the true residual is iterative
+    read_summary(h, &nact, &ratio);
+    CLAIR_REQUIRE(isfinite(ratio), CLAIR_ERR_NONFINITE, "nonfinite residual");
+    // (a cycle that stopped on its estimates but not on the true residuals is iterative
     // refinement, and stays in FP32)
-    if (beta > tol && mixed && !h->cycle_fp64 && (discarded || stalled || jend == m)) {
+    if (nact > 0 && mixed && !h->cycle_fp64 && (discarded || stalled || jmax == m)) {
       h->cycle_fp64 = true;
       h->fp64_from = its;
     }
   }
-  double rel = beta / fnorm;
-  if (h->ninst > 1) {  // the worst instance
-    const std::vector<double> ri = instance_norms(h, k.r);
-    rel = 0.0;
-    for (size_t i = 0; i < ri.size(); ++i)
-      rel = std::max(rel, fi[i] > 0.0 ? ri[i] / fi[i] : ri[i]);
+  return finish_segments(h);
+}
+
+// Preconditioned CG per segment (the symmetric case, R = P^T: the V(1,1) cycle with CFF
+// pre- and FFC post-smoothing and equal weights is then a symmetric preconditioner).  The
+// recursive residual decides convergence; the true residual is checked at the end and a
+// segment that misses it restarts from its current iterate.
+static bool pcg(clair_hierarchy* h, const double* f, double* u) {
+  cudaStream_t s = h->stream;
+  Krylov& k = h->kr;
+  const Segments& S = k.S;
+  const int nseg = S.nseg;
+  const long long N = k.N;
+  const bool mixed = h->p.precision == CLAIR_MIXED;
+  double* zv = k.V;            // M^-1 r
+  double* pv = k.V + N;        // search direction
+  double* qv = k.V + 2 * N;    // A p
+  double* rho = k.cg;
+  double* rz = k.cg + nseg;
+  double* pq = k.cg + 2 * nseg;
+  double* alpha = k.cg + 3 * nseg;
+  double* malpha = k.cg + 4 * nseg;
+  double* beta = k.cg + 5 * nseg;
+  seg_dot(S, f, 0, 1, f, k.fn2, 1, k.partial, s);
+  seg_tolerance_launch(S, k.fn2, h->p.rtol, k.tol, k.fnorm, u, s);
+  CLAIR_CUDA(cudaMemsetAsync(k.its, 0, sizeof(int) * nseg, s));
+  int its = 0;
+  double nact = 0, ratio = 0;
+  for (;;) {
+    residual_all(h, f, u, k.r);
+    seg_dot(S, k.r, 0, 1, k.r, k.beta2, 1, k.partial, s);
+    {
+      ClockScope clk(PH_VCYCLE, s);
+      precond_all(h, k.r, zv);
+    }
+    seg_dot(S, k.r, 0, 1, zv, rz, 1, k.partial, s);
+    seg_cg_start_launch(nseg, k.beta2, k.tol, rz, rho, k.active, k.summary, s);
+    CLAIR_CUDA(cudaMemcpyAsync(pv, zv, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    read_summary(h, &nact, &ratio);
+    CLAIR_REQUIRE(isfinite(ratio), CLAIR_ERR_NONFINITE, "nonfinite residual");
+    if (nact == 0 || its >= h->p.gmres_maxit) break;
+    std::vector<double> hist;
+    bool stalled = false;
+    while (nact > 0 && its < h->p.gmres_maxit) {
+      {
+        ClockScope clk(PH_KRYLOV, s);
+        matvec_all(h, pv, qv);
+        seg_dot(S, pv, 0, 1, qv, pq, 1, k.partial, s);
+        seg_cg_alpha_launch(nseg, rho, pq, k.active, alpha, malpha, s);
+        seg_axpy1(S, pv, alpha, u, s);
+        seg_axpy1(S, qv, malpha, k.r, s);
+        seg_dot(S, k.r, 0, 1, k.r, k.wn2, 1, k.partial, s);
+      }
+      {
+        ClockScope clk(PH_VCYCLE, s);
+        precond_all(h, k.r, zv);
+      }
+      {
+        ClockScope clk(PH_KRYLOV, s);
+        seg_dot(S, k.r, 0, 1, zv, rz, 1, k.partial, s);
+        seg_cg_beta_launch(nseg, k.wn2, k.tol, rz, rho, k.active, k.its, beta, k.summary, s);
+        seg_xpby(S, zv, beta, pv, s);
+      }
+      ++its;
+      read_summary(h, &nact, &ratio);
+      CLAIR_REQUIRE(isfinite(ratio), CLAIR_ERR_NONFINITE, "nonfinite CG residual");
+      hist.push_back(ratio);
+      if (mixed && !h->cycle_fp64 && (int)hist.size() > kStallWindow &&
+          ratio > 0.5 * hist[hist.size() - 1 - kStallWindow]) {
+        stalled = true;
+        break;
+      }
+    }
+    if (stalled) {
+      h->cycle_fp64 = true;
+      h->fp64_from = its;
+    }
   }
-  if (iters_out) *iters_out = its;
-  if (relres_out) *relres_out = rel;
-  return beta <= tol ? CLAIR_OK : CLAIR_ERR_NOT_CONVERGED;
+  return finish_segments(h);
+}
+
+static bool krylov_solve(clair_hierarchy* h, int nrhs, const double* f, double* u) {
+  ensure_krylov(h, nrhs);
+  h->cycle_fp64 = false;
+  h->fp64_from = -1;
+  return h->p.krylov == CLAIR_KRYLOV_PCG ? pcg(h, f, u) : fgmres(h, f, u);
 }
 
 }  // namespace clair
@@ -1031,15 +1115,19 @@ clair_status clair_params_default(clair_params* p) {
   p->gmres_maxit = 200;
   p->rtol = 1e-8;
   p->seed = 0x5EED;
+  p->inverse = CLAIR_INVERSE_EXACT;
+  p->iterations = 1;
+  p->symmetric = 0;
+  p->krylov = CLAIR_KRYLOV_FGMRES;
   return CLAIR_OK;
 }
 
 const char* clair_last_error(void) { return last_error(); }
 
 static clair_status setup_common(int ninst, const int* offsets_host, int n, int nnz,
-                                 const int* rowptr, const int* col, const double* val,
-                                 const double* B, const clair_params* pin, void* stream,
-                                 clair_h* out) {
+                                 const int* rowptr, const int* col, const double* val, int kmodes,
+                                 const double* B, const signed char* cf_marker,
+                                 const clair_params* pin, void* stream, clair_h* out) {
   if (out) *out = nullptr;
   CLAIR_API_BEGIN
   CLAIR_REQUIRE(out && rowptr && col && val && B, CLAIR_ERR_ARG, "clair_setup: null pointer");
@@ -1063,6 +1151,17 @@ static clair_status setup_common(int ninst, const int* offsets_host, int n, int 
                 "unknown coarsening type %d", p.coarsen);
   CLAIR_REQUIRE(p.b_smooth_iters >= 0 && p.gmres_maxit >= 1 && p.rtol > 0.0, CLAIR_ERR_ARG,
                 "bad iteration counts or rtol");
+  CLAIR_REQUIRE(kmodes >= 1 && kmodes <= CLAIR_KMAX, CLAIR_ERR_ARG,
+                "k (mode vectors) must be in [1, %d], got %d", CLAIR_KMAX, kmodes);
+  CLAIR_REQUIRE(p.inverse == CLAIR_INVERSE_EXACT || p.inverse == CLAIR_INVERSE_DIAG, CLAIR_ERR_ARG,
+                "unknown block inverse %d", p.inverse);
+  CLAIR_REQUIRE(p.iterations >= 1 && p.iterations <= 100, CLAIR_ERR_ARG,
+                "iterations must be in [1, 100]");
+  CLAIR_REQUIRE(p.symmetric == 0 || p.symmetric == 1, CLAIR_ERR_ARG, "symmetric must be 0 or 1");
+  CLAIR_REQUIRE(p.krylov == CLAIR_KRYLOV_FGMRES || p.krylov == CLAIR_KRYLOV_PCG, CLAIR_ERR_ARG,
+                "unknown Krylov method %d", p.krylov);
+  CLAIR_REQUIRE(!cf_marker || p.coarsen == CLAIR_COARSEN_FC, CLAIR_ERR_UNSUPPORTED,
+                "a caller splitting (cf_marker) needs FC coarsening (aggregates are not given)");
   std::vector<int> off{0, n};
   if (ninst > 1) {
     CLAIR_REQUIRE(offsets_host, CLAIR_ERR_ARG, "clair_setup_batched: null offsets");
@@ -1077,6 +1176,7 @@ static clair_status setup_common(int ninst, const int* offsets_host, int n, int 
   }
   clair_hierarchy* h = new clair_hierarchy();
   h->p = p;
+  h->kmodes = kmodes;
   h->ninst = std::max(ninst, 1);
   h->stream = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
@@ -1120,13 +1220,14 @@ static clair_status setup_common(int ninst, const int* offsets_host, int n, int 
                     "clair_setup_batched: %d rows couple two instances (not block-diagonal)", hb);
     }
     CLAIR_REQUIRE(all_finite(val, nnz, s), CLAIR_ERR_NONFINITE, "A has nonfinite values");
-    CLAIR_REQUIRE(all_finite(B, n, s), CLAIR_ERR_NONFINITE, "B has nonfinite values");
-    h->B0 = dalloc<double>(n, s);
-    CLAIR_CUDA(cudaMemcpyAsync(h->B0, B, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CLAIR_REQUIRE(all_finite(B, (long long)n * kmodes, s), CLAIR_ERR_NONFINITE,
+                  "B has nonfinite values");
+    if (cf_marker) validate_cf(cf_marker, n, s);
+    h->B0 = dalloc<double>((size_t)n * kmodes, s);
+    CLAIR_CUDA(cudaMemcpyAsync(h->B0, B, sizeof(double) * n * kmodes, cudaMemcpyDeviceToDevice, s));
     PhaseClock clock;
     set_active_clock(&clock);
-    setup_levels(h, B);
-    alloc_krylov(h);
+    setup_levels(h, B, cf_marker);
     set_active_clock(nullptr);
     h->vin = dalloc<double>(n, s);
     h->zout = dalloc<double>(n, s);
@@ -1151,20 +1252,22 @@ static clair_status setup_common(int ninst, const int* offsets_host, int n, int 
 }
 
 clair_status clair_setup(int n, int nnz, const int* rowptr, const int* col, const double* val,
-                         const double* B, const clair_params* p, void* stream, clair_h* out) {
-  return setup_common(1, nullptr, n, nnz, rowptr, col, val, B, p, stream, out);
+                         int k, const double* B, const signed char* cf_marker,
+                         const clair_params* p, void* stream, clair_h* out) {
+  return setup_common(1, nullptr, n, nnz, rowptr, col, val, k, B, cf_marker, p, stream, out);
 }
 
 clair_status clair_setup_batched(int ninst, const int* offsets_host, int n, int nnz,
-                                 const int* rowptr, const int* col, const double* val,
-                                 const double* B, const clair_params* p, void* stream,
-                                 clair_h* out) {
+                                 const int* rowptr, const int* col, const double* val, int k,
+                                 const double* B, const signed char* cf_marker,
+                                 const clair_params* p, void* stream, clair_h* out) {
   if (out) *out = nullptr;
   if (ninst < 1) {
     set_error("clair_setup_batched: ninst must be >= 1");
     return CLAIR_ERR_ARG;
   }
-  return setup_common(ninst, offsets_host, n, nnz, rowptr, col, val, B, p, stream, out);
+  return setup_common(ninst, offsets_host, n, nnz, rowptr, col, val, k, B, cf_marker, p, stream,
+                      out);
 }
 
 clair_status clair_batch_view(clair_h h, int level, int* ninst, int* offsets_host,
@@ -1198,7 +1301,8 @@ clair_status clair_setup_adjoint(clair_h fwd, void* stream, clair_h* adj) {
   clair_status st;
   try {
     st = setup_common(fwd->ninst, fwd->ninst > 1 ? fwd->lv[0].off.data() : nullptr, A.rows, A.nnz,
-                      At.rowptr, At.col, At.val, fwd->B0, &fwd->p, stream, adj);
+                      At.rowptr, At.col, At.val, fwd->kmodes, fwd->B0, nullptr, &fwd->p, stream,
+                      adj);
   } catch (...) {
     At.release(s);
     throw;
@@ -1209,18 +1313,20 @@ clair_status clair_setup_adjoint(clair_h fwd, void* stream, clair_h* adj) {
   CLAIR_API_END
 }
 
-clair_status clair_solve(clair_h h, const double* f, double* u, void* stream, int* iters,
-                         double* relres) {
+clair_status clair_solve(clair_h h, const double* f, double* u, int nrhs, void* stream,
+                         int* iters, double* relres) {
   CLAIR_API_BEGIN
   CLAIR_REQUIRE(h && f && u, CLAIR_ERR_ARG, "clair_solve: null pointer");
+  CLAIR_REQUIRE(nrhs >= 1 && (long long)nrhs * h->lv[0].n < (1LL << 40), CLAIR_ERR_ARG,
+                "clair_solve: nrhs must be >= 1 (got %d)", nrhs);
   cudaStream_t keep = h->stream;
   h->stream = static_cast<cudaStream_t>(stream);
-  clair_status st;
+  bool ok = false;
   PhaseClock clock;
   set_active_clock(&clock);
   for (double& v : h->solve_ms) v = 0.0;
   try {
-    st = fgmres(h, f, u, iters, relres);
+    ok = krylov_solve(h, nrhs, f, u);
   } catch (...) {
     set_active_clock(nullptr);
     h->stream = keep;
@@ -1229,8 +1335,32 @@ clair_status clair_solve(clair_h h, const double* f, double* u, void* stream, in
   set_active_clock(nullptr);
   clock.collect(h->solve_ms);
   h->stream = keep;
-  if (st != CLAIR_OK) set_error("FGMRES did not reach rtol within gmres_maxit");
-  return st;
+  const int ninst = h->ninst;
+  for (int r = 0; r < nrhs; ++r) {
+    int it = 0;
+    double rel = 0.0;
+    for (int i = 0; i < ninst; ++i) {
+      it = std::max(it, h->last_its[(size_t)r * ninst + i]);
+      rel = std::max(rel, h->last_rel[(size_t)r * ninst + i]);
+    }
+    if (iters) iters[r] = it;
+    if (relres) relres[r] = rel;
+  }
+  if (!ok) {
+    set_error("the Krylov solver did not reach rtol within gmres_maxit for every right-hand side");
+    return CLAIR_ERR_NOT_CONVERGED;
+  }
+  CLAIR_API_END
+}
+
+clair_status clair_solve_detail(clair_h h, int* nseg, int* iters_host, double* relres_host) {
+  CLAIR_API_BEGIN
+  CLAIR_REQUIRE(h && nseg, CLAIR_ERR_ARG, "clair_solve_detail: null pointer");
+  *nseg = (int)h->last_its.size();
+  for (size_t i = 0; i < h->last_its.size(); ++i) {
+    if (iters_host) iters_host[i] = h->last_its[i];
+    if (relres_host) relres_host[i] = h->last_rel[i];
+  }
   CLAIR_API_END
 }
 
@@ -1283,10 +1413,19 @@ clair_status clair_stats(clair_h h, clair_stats_t* o) {
   o->lsolve_min_bytes = minb;
   o->lsolve_gathered = h->st.gathered;
   o->fp64_cycle_from = h->fp64_from;
+  o->k = h->kmodes;
   CLAIR_API_END
 }
 
 int64_t clair_kernel_launches(void) { return launch_count(); }
+
+int clair_compiled_arch(void) {
+#ifdef __CUDA_ARCH_LIST__
+  return __CUDA_ARCH_LIST__;
+#else
+  return 0;
+#endif
+}
 
 clair_status clair_level_view(clair_h h, int level, int* n, int* nc, int* nnz_A,
                               const int** A_rowptr, const int** A_col, const double** A_val,

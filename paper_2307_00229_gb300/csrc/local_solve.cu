@@ -627,15 +627,16 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
 // ------------------------------------------------------------------------------------
 // work[0..2] = sum T^3, T^2, T; work[3] = A entries gathered (row lengths of the pattern's
 // F-points in Ahat)
+// Writes nothing but the lists and counters, so a caller may still refuse the call after
+// reading the counts (a row with T = 0, the identity entry alone, goes to bucket 0, whose
+// kernel writes that entry).
 __global__ void bucket_rows(const int* __restrict__ Zrp, int nc, int* __restrict__ lists,
-                            int* __restrict__ counts, double* __restrict__ Zval,
-                            const int* __restrict__ Zcol, const int* __restrict__ cpts,
-                            const int* __restrict__ Arp, int* __restrict__ too_big,
-                            unsigned long long* __restrict__ work) {
+                            int* __restrict__ counts, const int* __restrict__ Zcol,
+                            const int* __restrict__ cpts, const int* __restrict__ Arp,
+                            int* __restrict__ too_big, unsigned long long* __restrict__ work) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int T = r < nc ? Zrp[r + 1] - Zrp[r] - 1 : -1;
-  if (T == 0) Zval[Zrp[r]] = 1.0;  // only the identity entry
-  const int b = T > 0 ? ls_bucket(T) : -1;
+  const int b = T >= 0 ? ls_bucket(T) : -1;
   if (b >= LS_BUCKETS) atomicAdd(too_big, 1);
   if (b == LS_BUCKETS - 1) atomicMax(too_big + 1, T);  // largest T of the big bucket
   unsigned long long t3 = 0, t2 = 0, t1 = 0, g = 0;
@@ -702,6 +703,151 @@ __global__ void project_rows(const int* __restrict__ Wrp, const int* __restrict_
   }
 }
 
+// Pseudo-inverse solve of the symmetric positive semidefinite k x k system G mu = r (cyclic
+// Jacobi eigenvalue iteration, then mu = V diag(1/lambda) V^T r over the eigenvalues above
+// 1e-15 of the largest, the cutoff numpy's pinv uses); k <= CLAIR_KMAX.
+template <int K>
+__device__ void psd_pinv_solve(double (&G)[K][K], const double (&r)[K], double (&mu)[K], int k) {
+  double V[K][K];
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int b = 0; b < K; ++b) V[a][b] = a == b ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int a = 0; a < k; ++a) {
+      diag += G[a][a] * G[a][a];
+      for (int b = a + 1; b < k; ++b) off += G[a][b] * G[a][b];
+    }
+    if (off <= 1e-34 * diag) break;
+    for (int p = 0; p < k; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        if (G[p][q] == 0.0) continue;
+        // rotation that zeroes G[p][q] (Golub & Van Loan, symmetric Schur decomposition)
+        const double tau = (G[q][q] - G[p][p]) / (2.0 * G[p][q]);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+        for (int j = 0; j < k; ++j) {  // G <- J^T G J
+          const double gp = G[j][p], gq = G[j][q];
+          G[j][p] = c * gp - sn * gq;
+          G[j][q] = sn * gp + c * gq;
+        }
+        for (int j = 0; j < k; ++j) {
+          const double gp = G[p][j], gq = G[q][j];
+          G[p][j] = c * gp - sn * gq;
+          G[q][j] = sn * gp + c * gq;
+        }
+        for (int j = 0; j < k; ++j) {
+          const double vp = V[j][p], vq = V[j][q];
+          V[j][p] = c * vp - sn * vq;
+          V[j][q] = sn * vp + c * vq;
+        }
+      }
+  }
+  double lmax = 0.0;
+  for (int a = 0; a < k; ++a) lmax = fmax(lmax, fabs(G[a][a]));
+  for (int a = 0; a < k; ++a) mu[a] = 0.0;
+  for (int e = 0; e < k; ++e) {
+    const double lam = G[e][e];
+    if (!(lam > 1e-15 * lmax)) continue;
+    double c = 0.0;
+    for (int a = 0; a < k; ++a) c += V[a][e] * r[a];
+    c /= lam;
+    for (int a = 0; a < k; ++a) mu[a] += V[a][e] * c;
+  }
+}
+
+// Projection with k mode vectors (Eq. 3.3): per F row j with coarse points J_j,
+// G = sum_i Bc(i,:)^T Bc(i,:), s = sum_i w_ji Bc(i,:), mu = G^+ (s - B(j,:)),
+// w_ji <- w_ji - Bc(i,:) mu.  Bc is nc x k and B n x k, column-major; B may be null
+// (target 0: the projection of an update, Algorithm 1's second constraint step).
+__global__ void project_rows_k(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
+                               double* __restrict__ Wval, int n, const signed char* __restrict__ cf,
+                               const double* __restrict__ Bc, int nc, const double* __restrict__ B,
+                               int k, unsigned long long* __restrict__ nempty) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || cf[j]) return;
+  const int b = Wrp[j], e = Wrp[j + 1];
+  double G[CLAIR_KMAX][CLAIR_KMAX], sv[CLAIR_KMAX], mu[CLAIR_KMAX];
+  for (int a = 0; a < CLAIR_KMAX; ++a) {
+    sv[a] = 0.0;
+    for (int c = 0; c < CLAIR_KMAX; ++c) G[a][c] = 0.0;
+  }
+  for (int q = b; q < e; ++q) {
+    const int i = Wcol[q];
+    const double w = Wval[q];
+    for (int a = 0; a < k; ++a) {
+      const double ba = Bc[(long long)a * nc + i];
+      sv[a] += w * ba;
+      for (int c = 0; c <= a; ++c) G[a][c] += ba * Bc[(long long)c * nc + i];
+    }
+  }
+  double gmax = 0.0;
+  for (int a = 0; a < k; ++a) {
+    for (int c = a + 1; c < k; ++c) G[a][c] = G[c][a];
+    gmax = fmax(gmax, G[a][a]);
+    sv[a] -= B ? B[(long long)a * n + j] : 0.0;
+  }
+  if (!(gmax > 0.0)) {
+    if (nempty) atomicAdd(nempty, 1ull);
+    return;
+  }
+  psd_pinv_solve<CLAIR_KMAX>(G, sv, mu, k);
+  for (int q = b; q < e; ++q) {
+    const int i = Wcol[q];
+    double d = 0.0;
+    for (int a = 0; a < k; ++a) d += Bc[(long long)a * nc + i] * mu[a];
+    Wval[q] -= d;
+  }
+}
+
+// The residual step of Algorithm 1's loop with the diagonal block inverse: for each coarse
+// point i (row r of Z) and F-point l of its pattern,
+//   wbar_l = (-Ahat[l, i] - sum_{c in W_i} Ahat[l, c] w_c) / Ahat[l, l],
+// written at l's entry of the row (0 at the identity entry).  One warp per coarse row.
+__global__ void diag_update(const int* __restrict__ Arp, const int* __restrict__ Acol,
+                            const double* __restrict__ Aval, const int* __restrict__ Zrp,
+                            const int* __restrict__ Zcol, const double* __restrict__ Zval,
+                            const int* __restrict__ cpts, int nc, double* __restrict__ out) {
+  const int r = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= nc) return;
+  const int i = cpts[r];
+  const int z0 = Zrp[r], z1 = Zrp[r + 1];
+  for (int q = z0 + lane; q < z1; q += 32) {
+    const int l = Zcol[q];
+    if (l == i) {
+      out[q] = 0.0;
+      continue;
+    }
+    double acc = 0.0, d = 0.0;
+    for (int e = Arp[l]; e < Arp[l + 1]; ++e) {
+      const int c = Acol[e];
+      const double a = Aval[e];
+      if (c == l) d = a;
+      if (c == i) {
+        acc -= a;
+      } else {
+        const int pos = find_sorted(Zcol + z0, z1 - z0, c);
+        if (pos >= 0) acc -= a * Zval[z0 + pos];
+      }
+    }
+    out[q] = d != 0.0 ? acc / d : 0.0;
+  }
+}
+
+__global__ void add_into(const double* __restrict__ x, double* __restrict__ y, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] += x[i];
+}
+
+__global__ void unit_on_c_rows(const int* __restrict__ rp, const signed char* __restrict__ cf,
+                               int n, double* __restrict__ val) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int e = rp[j]; e < rp[j + 1]; ++e) val[e] = cf[j] ? 1.0 : 0.0;
+}
+
 __global__ void coarse_of(const signed char* __restrict__ cf, const int* __restrict__ cidx_incl,
                           int n, int* __restrict__ cpts) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -737,18 +883,20 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
                           const int* cpts, const int* lists, const int* counts_h, int nc,
                           double* Zval, unsigned long long* nsing, cudaStream_t s,
                           Real* big_scratch = nullptr, int big_pitch = 0, int big_chunk = 0) {
-  static bool attr = false;
-  if (!attr) {
+  // the shared-memory limits above 48 KB are per-device function attributes
+  constexpr int key = sizeof(Real) == 8 ? ONCE_LSOLVE_F64
+                      : (sizeof(VT) == 8 ? ONCE_LSOLVE_F32D : ONCE_LSOLVE_F32);
+  once_per_device(key, [] {
     CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, VT, 64>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)cta_smem<Real, 64>()));
     CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, VT, 128>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)cta_smem<Real, 128>()));
-    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_big<Real, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_big<Real, VT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)big_smem<Real>(LS_TBIG)));
-    attr = true;
-  }
+  });
   const int per_block[2] = {LS_WARPS * 4, LS_WARPS * 2};
   if (counts_h[0])
     lsolve_group<Real, VT, 8><<<ceil_div(counts_h[0], per_block[0]), 32 * LS_WARPS, 0, s>>>(
@@ -802,7 +950,7 @@ void local_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* c
   unsigned long long* nsing = dalloc<unsigned long long>(5, s);  // [0] singular, [1..4] work
   CLAIR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * (LS_BUCKETS + 2), s));
   CLAIR_CUDA(cudaMemsetAsync(nsing, 0, 5 * sizeof(unsigned long long), s));
-  if (nc) bucket_rows<<<ceil_div(nc, 256), 256, 0, s>>>(Zrp, nc, lists, counts, Zval, Zcol, cpts,
+  if (nc) bucket_rows<<<ceil_div(nc, 256), 256, 0, s>>>(Zrp, nc, lists, counts, Zcol, cpts,
                                                         Ahat.rowptr, counts + LS_BUCKETS,
                                                         nsing + 1); ::clair::count_launch();
   CLAIR_LAUNCHED();
@@ -847,15 +995,19 @@ void local_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* c
   dfree(nsing, s);
 }
 
-// Projection of the transposed weights Wt (rows = fine points) onto the constraint.
-void project_constraint(Csr& Wt, const signed char* cf, const double* Bc, const double* B,
-                        LocalStats& st, cudaStream_t s) {
+// Projection of the transposed weights Wt (rows = fine points) onto the constraint; Bc is
+// nc x k and B n x k (column-major); B null projects onto Q w = 0 (an update).
+void project_constraint(Csr& Wt, const signed char* cf, const double* Bc, int nc, const double* B,
+                        int k, LocalStats& st, cudaStream_t s) {
   unsigned long long* nempty = dalloc<unsigned long long>(1, s);
   CLAIR_CUDA(cudaMemsetAsync(nempty, 0, sizeof(unsigned long long), s));
-  if (Wt.rows) {
+  if (Wt.rows && k == 1 && B) {
     constexpr int W = 1;  // FP64: one thread per row
     project_rows<W><<<ceil_div((long long)Wt.rows * W, 256), 256, 0, s>>>(
         Wt.rowptr, Wt.col, Wt.val, Wt.rows, cf, Bc, B, nempty); ::clair::count_launch();
+  } else if (Wt.rows) {
+    project_rows_k<<<ceil_div(Wt.rows, 128), 128, 0, s>>>(Wt.rowptr, Wt.col, Wt.val, Wt.rows, cf, Bc,
+                                                           nc, B, k, nempty); ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
   unsigned long long h = 0;
@@ -869,7 +1021,7 @@ void project_constraint(Csr& Wt, const signed char* cf, const double* Bc, const 
 // projection.  On return Z.val holds the projected weights (row = coarse point) and, if
 // keep_t is set, Zt receives the transposed operator (rows = fine points) with the same
 // projected values.
-void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const double* B,
+void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const double* B, int k,
                       LocalStats& st, Csr* keep_t, cudaStream_t s);
 
 // First half: the local lAIR solves into Z.val (no mode vector needed).
@@ -883,21 +1035,74 @@ void transfer_weights(const Csr& Ahat, const signed char* cf, const int* cpts, C
                       const double* B, int precision, LocalStats& st, Csr* keep_t,
                       cudaStream_t s) {
   transfer_solve(Ahat, cpts, Z, precision, st, s);
-  transfer_project(cf, cpts, Z, B, st, keep_t, s);
+  transfer_project(cf, cpts, Z, B, 1, st, keep_t, s);
 }
 
 // Second half: projection onto the mode constraint (needs the smoothed mode vector B).
-void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const double* B,
+void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const double* B, int k,
                       LocalStats& st, Csr* keep_t, cudaStream_t s) {
-  const int nc = Z.rows;
+  const int nc = Z.rows, n = Z.cols;
   ClockScope clk(PH_PROJECT, s);
   Csr Zt;
   int* perm = nullptr;
   csr_transpose(Z, Zt, &perm, s);
-  double* Bc = dalloc<double>(nc, s);
-  gather(B, cpts, Bc, nc, s);
-  project_constraint(Zt, cf, Bc, B, st, s);
+  double* Bc = dalloc<double>((size_t)nc * k, s);
+  for (int a = 0; a < k; ++a) gather(B + (size_t)a * n, cpts, Bc + (size_t)a * nc, nc, s);
+  project_constraint(Zt, cf, Bc, nc, B, k, st, s);
   scatter_vals(Zt.val, perm, Z.val, Z.nnz, s);
+  dfree(Bc, s);
+  dfree(perm, s);
+  if (keep_t)
+    *keep_t = Zt;
+  else
+    Zt.release(s);
+}
+
+// Algorithm 1 with the diagonal block inverses (Section 3.1.2) and `iterations` passes of
+// its loop, in float64:
+//   w_t: per F row the minimum-norm solution of w B_c = B (the projection of zero onto the
+//        constraint set);
+//   each pass: wbar = D^-1 (-a_fc - A_ff w_t) per coarse point's block, wbar projected onto
+//        Q wbar = 0, w_t += wbar.
+// On return Z.val holds the weights (row = coarse point); keep_t as in transfer_project.
+void transfer_diag(const Csr& Ahat, const signed char* cf, const int* cpts, Csr& Z,
+                   const double* B, int k, int iterations, LocalStats& st, Csr* keep_t,
+                   cudaStream_t s) {
+  const int nc = Z.rows, n = Z.cols;
+  ClockScope clk(PH_LSOLVE, s);
+  if (!Z.val) Z.val = dalloc<double>(Z.nnz, s);
+  Csr Zt;
+  int* perm = nullptr;
+  csr_transpose(Z, Zt, &perm, s);  // structure (values are set below)
+  double* Bc = dalloc<double>((size_t)nc * k, s);
+  for (int a = 0; a < k; ++a) gather(B + (size_t)a * n, cpts, Bc + (size_t)a * nc, nc, s);
+  // tentative weights: 1 at the identity entries (C rows), the projection of 0 elsewhere
+  if (n) {
+    unit_on_c_rows<<<ceil_div(n, 256), 256, 0, s>>>(Zt.rowptr, cf, n, Zt.val); ::clair::count_launch();
+  }
+  CLAIR_LAUNCHED();
+  project_constraint(Zt, cf, Bc, nc, B, k, st, s);
+  scatter_vals(Zt.val, perm, Z.val, Z.nnz, s);
+  double* zbar = dalloc<double>(std::max(Z.nnz, 1), s);
+  long long sing_dummy = 0;
+  (void)sing_dummy;
+  for (int it = 0; it < iterations; ++it) {
+    if (nc) {
+      diag_update<<<ceil_div((long long)nc * 32, 256), 256, 0, s>>>(
+          Ahat.rowptr, Ahat.col, Ahat.val, Z.rowptr, Z.col, Z.val, cpts, nc, zbar); ::clair::count_launch();
+    }
+    CLAIR_LAUNCHED();
+    gather_vals(zbar, perm, Zt.val, Z.nnz, s);
+    LocalStats discard;  // empty F rows are counted once, by the first projection
+    project_constraint(Zt, cf, Bc, nc, nullptr, k, discard, s);
+    scatter_vals(Zt.val, perm, zbar, Z.nnz, s);
+    if (Z.nnz) {
+      add_into<<<ceil_div(Z.nnz, 256), 256, 0, s>>>(zbar, Z.val, Z.nnz); ::clair::count_launch();
+    }
+    CLAIR_LAUNCHED();
+  }
+  gather_vals(Z.val, perm, Zt.val, Z.nnz, s);
+  dfree(zbar, s);
   dfree(Bc, s);
   dfree(perm, s);
   if (keep_t)
@@ -1005,15 +1210,20 @@ static void local_weights_noalloc(int n, const Csr& Ahat, const signed char* cf,
   // bucketed local solves (counters start at zero on every call)
   CLAIR_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(int) * (LS_BUCKETS + 2), s));
   CLAIR_CUDA(cudaMemsetAsync(b.work, 0, 5 * sizeof(unsigned long long), s));
-  if (nc) bucket_rows<<<ceil_div(nc, 256), 256, 0, s>>>(Z.rowptr, nc, b.lists, b.counts, Z.val, Z.col,
+  if (nc) bucket_rows<<<ceil_div(nc, 256), 256, 0, s>>>(Z.rowptr, nc, b.lists, b.counts, Z.col,
                                                         b.cpts, Ahat.rowptr, b.counts + LS_BUCKETS,
                                                         b.work + 1); ::clair::count_launch();
   CLAIR_LAUNCHED();
   int counts_h[LS_BUCKETS + 2];
   CLAIR_CUDA(cudaMemcpyAsync(counts_h, b.counts, sizeof(counts_h), cudaMemcpyDeviceToHost, s));
   CLAIR_CUDA(cudaStreamSynchronize(s));
-  CLAIR_REQUIRE(counts_h[LS_BUCKETS] == 0, CLAIR_ERR_CAPACITY,
-                "%d local systems larger than %d unknowns", counts_h[LS_BUCKETS], LS_TBIG);
+  // every refusal comes before the first write to Z_val: systems above 128 unknowns need
+  // a per-call tile buffer, which this entry point does not have
+  CLAIR_REQUIRE(counts_h[LS_BUCKETS] == 0 && counts_h[LS_BUCKETS - 1] == 0, CLAIR_ERR_CAPACITY,
+                "%d local systems larger than 128 unknowns (the largest has %d; this entry "
+                "point solves T <= 128, use clair_local_weights)",
+                counts_h[LS_BUCKETS] + counts_h[LS_BUCKETS - 1],
+                counts_h[LS_BUCKETS] ? LS_TBIG + 1 : counts_h[LS_BUCKETS + 1]);
   if (precision == CLAIR_MIXED)
     launch_solves<float, double>(Ahat, Ahat.val, Z.rowptr, Z.col, b.cpts, b.lists, counts_h, nc,
                                  Z.val, b.work, s);
@@ -1029,7 +1239,7 @@ static void local_weights_noalloc(int n, const Csr& Ahat, const signed char* cf,
   gather(B, b.cpts, b.Bc, nc, s);
   CLAIR_CUDA(cudaMemsetAsync(b.nempty, 0, sizeof(unsigned long long), s));
   if (Zt.rows) {
-    constexpr int W = 8;
+    constexpr int W = 1;  // as project_constraint: the same summation order, the same bits
     project_rows<W><<<ceil_div((long long)Zt.rows * W, 256), 256, 0, s>>>(
         Zt.rowptr, Zt.col, Zt.val, Zt.rows, cf, b.Bc, B, b.nempty); ::clair::count_launch();
   }
@@ -1087,7 +1297,13 @@ extern "C" clair_status clair_local_weights_noalloc(
     Z.col = const_cast<int*>(Z_col);
     Z.val = Z_val;
     LocalStats st;
-    local_weights_noalloc(n, Ahat, cf, nc, Z, B, precision, buf, st, s);
+    try {
+      local_weights_noalloc(n, Ahat, cf, nc, Z, B, precision, buf, st, s);
+    } catch (...) {
+      // a refusal or failure returns only once nothing this call queued still runs
+      cudaStreamSynchronize(s);
+      throw;
+    }
     if (singular_out) *singular_out = st.singular;
     if (empty_out) *empty_out = st.empty;
     if (st.singular) {

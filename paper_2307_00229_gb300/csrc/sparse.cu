@@ -39,6 +39,19 @@ int sm_count() {
 
 int partial_blocks() { return 2 * sm_count(); }
 
+void once_per_device(int key, void (*set)()) {
+  static std::mutex mu;
+  static bool done[256][ONCE_KEYS] = {};
+  int dev = 0;
+  CLAIR_CUDA(cudaGetDevice(&dev));
+  CLAIR_REQUIRE(dev >= 0 && dev < 256 && key >= 0 && key < ONCE_KEYS, CLAIR_ERR_ARG,
+                "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev][key]) return;
+  set();
+  done[dev][key] = true;
+}
+
 cudaMemPool_t library_pool() {
   static std::mutex mu;
   static cudaMemPool_t pools[256] = {};
@@ -1281,8 +1294,7 @@ void drop_zeros(Csr& C, cudaStream_t s) {
 // could not hold.
 static void spgemm_cta_path(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   const int rows = A.rows;
-  static bool attr = false;
-  if (!attr) {
+  once_per_device(ONCE_SPGEMM_CTA, [] {
     CLAIR_CUDA(cudaFuncSetAttribute(spgemm_cta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sgc_bytes(false)));
     CLAIR_CUDA(cudaFuncSetAttribute(spgemm_cta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1291,8 +1303,7 @@ static void spgemm_cta_path(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) 
                                     (int)(sizeof(int) * SG_LARGE)));
     CLAIR_CUDA(cudaFuncSetAttribute(spgemm_large<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)((sizeof(int) + sizeof(double)) * SG_LARGE)));
-    attr = true;
-  }
+  });
   const int sms = sm_count();
   int* count = dalloc<int>(rows + 1, s);
   int* route = dalloc<int>(rows, s);
@@ -1375,20 +1386,24 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
        spgemm_flat<true, SG_CAP2, SG_PRE2, 1>}};
   const size_t large_sym = sizeof(int) * SG_LARGE;
   const size_t large_num = (sizeof(int) + sizeof(double)) * SG_LARGE;
-  static bool attr_set = false;
-  if (!attr_set) {
-    for (const Tier& t : tiers) {
-      CLAIR_CUDA(cudaFuncSetAttribute(t.sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(t.warps * sg_warp_bytes(false, t.cap, t.pcap))));
-      CLAIR_CUDA(cudaFuncSetAttribute(t.num, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(t.warps * sg_warp_bytes(true, t.cap, t.pcap))));
-    }
-    CLAIR_CUDA(cudaFuncSetAttribute(spgemm_large<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)large_sym));
-    CLAIR_CUDA(cudaFuncSetAttribute(spgemm_large<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)large_num));
-    attr_set = true;
-  }
+  once_per_device(ONCE_SPGEMM_FLAT, [] {
+    auto both = [](auto sym, auto num, size_t sym_bytes, size_t num_bytes) {
+      CLAIR_CUDA(cudaFuncSetAttribute(sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sym_bytes));
+      CLAIR_CUDA(cudaFuncSetAttribute(num, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)num_bytes));
+    };
+    both(spgemm_flat<false, SG_CAP0, SG_PRE0, SG_WARPS0>, spgemm_flat<true, SG_CAP0, SG_PRE0, SG_WARPS0>,
+         SG_WARPS0 * sg_warp_bytes(false, SG_CAP0, SG_PRE0),
+         SG_WARPS0 * sg_warp_bytes(true, SG_CAP0, SG_PRE0));
+    both(spgemm_flat<false, SG_CAP1, SG_PRE1, SG_WARPS1>, spgemm_flat<true, SG_CAP1, SG_PRE1, SG_WARPS1>,
+         SG_WARPS1 * sg_warp_bytes(false, SG_CAP1, SG_PRE1),
+         SG_WARPS1 * sg_warp_bytes(true, SG_CAP1, SG_PRE1));
+    both(spgemm_flat<false, SG_CAP2, SG_PRE2, 1>, spgemm_flat<true, SG_CAP2, SG_PRE2, 1>,
+         sg_warp_bytes(false, SG_CAP2, SG_PRE2), sg_warp_bytes(true, SG_CAP2, SG_PRE2));
+    both(spgemm_large<false>, spgemm_large<true>, sizeof(int) * SG_LARGE,
+         (sizeof(int) + sizeof(double)) * SG_LARGE);
+  });
   const int sms = sm_count();
   // grid of a tier over listed rows: enough warps to fill the GPU, never more than the rows
   auto grid_for_list = [&](int warps_per_block, int blocks_per_sm) {

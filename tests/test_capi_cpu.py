@@ -40,14 +40,15 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_library_is_built_for_sm103a(lib):
-    out = subprocess.run(["cuobjdump", "--list-elf", lib._name], capture_output=True, text=True).stdout
-    assert "sm_103a" in out
+    from paper_2307_00229_gb300 import _build, clair
+    assert clair.clair_compiled_arch() == 1030
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
 def test_null_arguments_return_status(lib):
     from paper_2307_00229_gb300 import clair
     h = ctypes.c_void_p()
-    st = lib.clair_setup(4, 4, None, None, None, None, None, None, ctypes.byref(h))
+    st = lib.clair_setup(4, 4, None, None, None, 1, None, None, None, None, ctypes.byref(h))
     assert st == clair.CLAIR_ERR_ARG and h.value is None
     assert "null" in clair.clair_last_error()
     assert lib.clair_params_default(None) == clair.CLAIR_ERR_ARG
@@ -55,6 +56,11 @@ def test_null_arguments_return_status(lib):
     p = clair.clair_params_default()
     assert p.theta_coarsen == 0.25 and p.theta_interp == 0.05 and p.degree == 2
     assert p.b_smooth_iters == 5 and p.arnoldi_iters == 15 and p.post_weighted == 0
+    assert p.inverse == clair.CLAIR_INVERSE_EXACT and p.iterations == 1
+    assert p.symmetric == 0 and p.krylov == clair.CLAIR_KRYLOV_FGMRES
+    nseg = ctypes.c_int()
+    assert lib.clair_solve_detail(None, ctypes.byref(nseg), None, None) == clair.CLAIR_ERR_ARG
+    assert lib.clair_solve(None, None, None, 1, None, None, None) == clair.CLAIR_ERR_ARG
 
 
 @pytest.fixture(scope="module")

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Bars (stated here, derived in the design doc):
+Bars, and where each comes from:
 * integer work (splitting, patterns) is bit-exact;
 * FP64 values: |gpu - oracle| <= 1e-12 * max|oracle| per row (R, P), per matrix (A_c),
   and for the smoothed mode vectors; omega (a Ritz value of a non-normal Hessenberg

@@ -610,3 +610,159 @@ def test_algorithm1_on_column_subset_matches_full_run():
                                       full.indices[full.indptr[i]:full.indptr[i + 1]])
         np.testing.assert_allclose(sub.data[sub.indptr[k]:sub.indptr[k + 1]],
                                    full.data[full.indptr[i]:full.indptr[i + 1]], rtol=1e-13, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------------------
+# Several mode vectors (Eq. 3.3 with k > 1), diagonal block inverses (Section 3.1.2),
+# the symmetric variant R = P^T with CG (Section 4.1)
+# ---------------------------------------------------------------------------------------
+def explicit_Q(Wpat, Bc, Bfull):
+    """Dense Q of Eq. 3.3 for k modes: one row per (F row j with a nonempty pattern row,
+    mode a); Q[(j, a), e] = B_c(i_e, a) for every pattern entry e = (j, i_e)."""
+    col_of_entry = np.repeat(np.arange(Wpat.shape[1]), np.diff(Wpat.indptr))
+    row_of_entry = Wpat.indices
+    Frows = np.unique(row_of_entry)
+    k = Bc.shape[1]
+    Q = np.zeros((Frows.size * k, row_of_entry.size))
+    for e in range(row_of_entry.size):
+        r = np.searchsorted(Frows, row_of_entry[e])
+        for a in range(k):
+            Q[r * k + a, e] = Bc[col_of_entry[e], a]
+    b = np.concatenate([Bfull[j, :] for j in Frows])
+    return Q, b
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-2, 1.0])
+def test_two_modes_constraint_is_min_norm_projection_of_lair(eps):
+    """k = 2 (constants and the x coordinate): Algorithm 1 with the exact inverse = the
+    Euclidean projection of the lAIR weights onto {Q w = B|_F} (dense global least-norm
+    solve), where |J_j| may be 1 < k (the pseudo-inverse case of the least-squares step)."""
+    A = small_problem(7, eps=eps)
+    n = A.shape[0]
+    cf = O.split_fc(A, 0.25)
+    C = np.flatnonzero(cf == 1)
+    x = (np.arange(n) % 7 + 1) / 8.0
+    B = np.stack([np.ones(n), x], axis=1)
+    At = A.T.tocsr()
+    S = O.strength(At, 0.05)
+    Wpat = O.clair_pattern(S, O.base_pattern(S, cf, "FC"), cf, 2)
+    w_lair = O.clair_algorithm1(At, cf, B, Wpat, O.Params(constrain=False)).tocsc()
+    w_cl = O.clair_algorithm1(At, cf, B, Wpat, O.Params()).tocsc()
+    Q, b = explicit_Q(Wpat, B[C], B)
+    # min ||w - w_lair|| s.t. Q w = b, least squares where Q w = b has no solution
+    sol = w_lair.data - np.linalg.pinv(Q) @ (Q @ w_lair.data - b)
+    np.testing.assert_allclose(w_cl.data, sol, rtol=1e-10, atol=1e-12)
+    # rows whose pattern holds two or more C-points with independent modes meet both
+    rank_full = np.array([np.linalg.matrix_rank(Q[2 * r:2 * r + 2]) == 2 for r in range(Q.shape[0] // 2)])
+    res = (Q @ w_cl.data - b).reshape(-1, 2)
+    assert rank_full.sum() > 0
+    np.testing.assert_allclose(res[rank_full], 0.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-2, 1.0])
+@pytest.mark.parametrize("iters", [1, 3])
+def test_diag_inverse_equals_exact_on_diagonal_blocks(eps, iters):
+    """Degree-1 patterns on the 5-point operator hold F-points that are not neighbours of
+    one another, so every local block is diagonal: the diagonal inverse is then the exact
+    inverse and Algorithm 1 gives the exact-inverse result for any loop count."""
+    A = small_problem(8, eps=eps)
+    n = A.shape[0]
+    cf = O.split_fc(A, 0.25)
+    B = 0.5 + workloads.uniform01(9, n)
+    for Ahat in (A, A.T.tocsr()):
+        S = O.strength(Ahat, 0.05)
+        Wpat = O.clair_pattern(S, O.base_pattern(S, cf, "FC"), cf, 1)
+        Ad = Ahat.toarray()
+        for i in range(Wpat.shape[1]):
+            Z = Wpat.indices[Wpat.indptr[i]:Wpat.indptr[i + 1]]
+            M = Ad[np.ix_(Z, Z)]
+            assert np.all(M == np.diag(np.diag(M)))
+        we = O.clair_algorithm1(Ahat, cf, B, Wpat, O.Params(degree=1)).toarray()
+        wd = O.clair_algorithm1(Ahat, cf, B, Wpat, O.Params(degree=1, inverse="diag",
+                                                            iterations=iters)).toarray()
+        np.testing.assert_allclose(wd, we, rtol=0, atol=1e-14 * np.abs(we).max())
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1.0])
+def test_diag_inverse_iteration_reaches_its_fixed_point(eps):
+    """The diagonal-inverse loop converges to the w with Q w = B|_F whose block residual,
+    scaled by D^-1, lies in the range of Q^T: A_ff* w + D* Q^T lam = -a_fc*, Q w = B|_F,
+    solved here as one dense system; one pass is not yet there."""
+    A = small_problem(6, eps=eps)
+    n = A.shape[0]
+    cf = O.split_fc(A, 0.25)
+    C = np.flatnonzero(cf == 1)
+    B = 0.5 + workloads.uniform01(9, n)
+    At = A.T.tocsr()
+    Ad = At.toarray()
+    S = O.strength(At, 0.05)
+    Wpat = O.clair_pattern(S, O.base_pattern(S, cf, "FC"), cf, 2)
+    ne = Wpat.nnz
+    Ablk = np.zeros((ne, ne))
+    a = np.zeros(ne)
+    d = np.zeros(ne)
+    for i in range(Wpat.shape[1]):
+        lo, hi = Wpat.indptr[i], Wpat.indptr[i + 1]
+        Z = Wpat.indices[lo:hi]
+        Ablk[lo:hi, lo:hi] = Ad[np.ix_(Z, Z)]
+        a[lo:hi] = Ad[Z, C[i]]
+        d[lo:hi] = np.diag(Ad)[Z]
+    Q, b = explicit_Q(Wpat, B[C].reshape(-1, 1), B.reshape(-1, 1))
+    m = Q.shape[0]
+    K = np.block([[Ablk, np.diag(d) @ Q.T], [Q, np.zeros((m, m))]])
+    fixed = np.linalg.lstsq(K, np.concatenate([-a, b]), rcond=None)[0][:ne]
+    w_many = O.clair_algorithm1(At, cf, B, Wpat, O.Params(inverse="diag", iterations=300)).tocsc()
+    np.testing.assert_allclose(w_many.data, fixed, rtol=1e-9, atol=1e-11)
+    w_one = O.clair_algorithm1(At, cf, B, Wpat, O.Params(inverse="diag", iterations=1)).tocsc()
+    assert np.abs(w_one.data - fixed).max() > 1e-6
+    np.testing.assert_allclose(Q @ w_one.data, b, atol=1e-12)
+
+
+def test_pcg_textbook_cases():
+    """CG with the identity preconditioner on an SPD matrix with three distinct eigenvalues
+    converges in three steps; with the exact inverse as preconditioner in one."""
+    rng = np.random.default_rng(4)
+    Qm, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    lam = np.array([1.0] * 4 + [3.0] * 4 + [10.0] * 4)
+    M = sp.csr_matrix(Qm @ np.diag(lam) @ Qm.T)
+    f = rng.standard_normal(12)
+    x, its, hist = O.pcg(M, f, lambda v: v, 1e-12, 50)
+    assert its == 3
+    np.testing.assert_allclose(M @ x, f, atol=1e-10)
+    Minv = np.linalg.inv(M.toarray())
+    x, its, _ = O.pcg(M, f, lambda v: Minv @ v, 1e-12, 50)
+    assert its == 1
+
+
+def poisson_2d(nside):
+    return O.csr_of(workloads.advdiff_2d(nside, 0.0, 0.0, 1.0))
+
+
+def diffusion_params(**kw):
+    """Section 4.1's symmetric CLAIR parameters: strength 0.5 / 0.5, degree 2, B = 1 with
+    5 CFF sweeps, R = P^T, aggregation; symmetric smoothing weights for CG."""
+    d = dict(theta_coarsen=0.5, theta_interp=0.5, degree=2, coarsen="AGG", symmetric=True,
+             post_weighted=True)
+    d.update(kw)
+    return O.Params(**d)
+
+
+def test_symmetric_variant_gives_symmetric_preconditioner():
+    """R = P^T and weighted FFC post-smoothing make the V(1,1) cycle a symmetric operator
+    for symmetric A (the adjoint of CFF pre-smoothing), which CG needs: the dense matrix of
+    the cycle is symmetric and positive definite, and every A_c is symmetric."""
+    A = poisson_2d(8)
+    n = A.shape[0]
+    H = O.build_hierarchy(A, np.ones(n), diffusion_params(coarse_max=10))
+    assert len(H.levels) >= 2
+    for lev in H.levels[:-1]:
+        np.testing.assert_array_equal(lev.R.toarray(), lev.P.T.toarray())
+    for lev in H.levels:
+        Ad = lev.A.toarray()
+        np.testing.assert_allclose(Ad, Ad.T, atol=1e-13 * np.abs(Ad).max())
+    Mi = np.stack([O.vcycle(H, e) for e in np.eye(n)], axis=1)
+    np.testing.assert_allclose(Mi, Mi.T, atol=1e-12 * np.abs(Mi).max())
+    assert np.linalg.eigvalsh(0.5 * (Mi + Mi.T)).min() > 0
+    f = workloads.uniform_pm1(3, n)
+    x, its, hist = O.pcg(A, f, lambda v: O.vcycle(H, v), 1e-10, 100)
+    assert hist[-1] <= 1e-10 * np.linalg.norm(f) and its < 20

@@ -36,9 +36,10 @@ def dev(a, dtype):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def problem(nside=30):
+def problem(nside=30, wide_row=None):
     """C-points on a lattice; each C-point's pattern is its F-points within Chebyshev
-    distance 1..5 (sizes from a few up to ~120, so every solver bucket is used)."""
+    distance 1..5 (sizes from a few up to ~120, so every solver bucket up to 128 unknowns
+    is used).  ``wide_row`` gives that one C-point radius 7, about 200 unknowns."""
     A = workloads.advdiff_2d(nside, math.cos(0.4), math.sin(0.4), 1e-1).to_scipy().tocsr()
     A.sort_indices()
     n = A.shape[0]
@@ -47,7 +48,7 @@ def problem(nside=30):
     cpts = np.flatnonzero(cf)
     rp, cols = [0], []
     for r, c in enumerate(cpts):
-        radius = 1 + r % 5
+        radius = 7 if r == wide_row else 1 + r % 5
         d = np.maximum(np.abs(ix - ix[c]), np.abs(iy - iy[c]))
         sel = np.flatnonzero((d <= radius) & ((cf == 0) | (np.arange(n) == c)))
         cols.append(sel)
@@ -84,6 +85,8 @@ def test_noalloc_matches_allocating_entry_point_twice(cl, precision):
         got = out.cpu().numpy()
         assert np.all(np.isfinite(got)), call
         assert rowwise_err(got, ref_h, zrp) <= tol, call
+        # the same kernels in the same order: the same bits
+        assert np.array_equal(got, ref_h), call
 
 
 def test_noalloc_refuses_problem_beyond_its_scratch(cl):
@@ -102,3 +105,37 @@ def test_noalloc_refuses_problem_beyond_its_scratch(cl):
     assert exc.value.status == cl.CLAIR_ERR_CAPACITY
     assert "limit" in str(exc.value) and "bytes" in str(exc.value)
     assert out.item() == 7.0
+
+
+def test_noalloc_refuses_large_local_system_before_writing(cl):
+    """One pattern row with about 200 unknowns (beyond the 128 this entry point solves):
+    the call is refused with CLAIR_ERR_CAPACITY before anything is written, and the next
+    valid call still matches the allocating entry point bit for bit."""
+    import torch
+    A, cf, cpts, zrp, zcol, B = problem(wide_row=44)
+    T = np.diff(zrp) - 1
+    assert T.max() > 128 and T.max() <= 4096
+    args = (dev(A.indptr, torch.int32), dev(A.indices, torch.int32), dev(A.data, torch.float64),
+            dev(cf, torch.int8), cpts.size, dev(zrp, torch.int32), dev(zcol, torch.int32),
+            dev(B, torch.float64), 0)
+    out = torch.full((zcol.size,), 3.25, dtype=torch.float64, device="cuda")
+    with pytest.raises(cl.ClairError) as exc:
+        cl.clair_local_weights_noalloc(*args, out)
+    assert exc.value.status == cl.CLAIR_ERR_CAPACITY
+    assert "128" in str(exc.value)
+    torch.cuda.synchronize()
+    assert torch.all(out == 3.25).item()
+    # the allocating entry point takes the same problem; the no-alloc one takes the valid one
+    ref = torch.zeros(zcol.size, dtype=torch.float64, device="cuda")
+    st, _, _ = cl.clair_local_weights(*args, ref)
+    assert st == 0
+    A2, cf2, cpts2, zrp2, zcol2, B2 = problem()
+    args2 = (dev(A2.indptr, torch.int32), dev(A2.indices, torch.int32), dev(A2.data, torch.float64),
+             dev(cf2, torch.int8), cpts2.size, dev(zrp2, torch.int32), dev(zcol2, torch.int32),
+             dev(B2, torch.float64), 0)
+    ref2 = torch.zeros(zcol2.size, dtype=torch.float64, device="cuda")
+    cl.clair_local_weights(*args2, ref2)
+    out2 = torch.full((zcol2.size,), float("nan"), dtype=torch.float64, device="cuda")
+    cl.clair_local_weights_noalloc(*args2, out2)
+    torch.cuda.synchronize()
+    assert np.array_equal(out2.cpu().numpy(), ref2.cpu().numpy())
