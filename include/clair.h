@@ -111,6 +111,9 @@ typedef struct {
                                  FP64 cycle took over (a restart cycle ended unconverged or
                                  produced a nonfinite estimate), -1 if it never did */
   int k;                      /* mode vectors (columns of B, B_P and B_R) */
+  int lsolve_kind_b1;         /* configuration of the last persistent local-solve launch */
+  int lsolve_blocks_per_sm;   /* (see clair_lsolve_config) */
+  int lsolve_tuned;
 } clair_stats_t;
 
 /* Kernel launches issued by this library in this process so far (monotonic counter). */
@@ -119,6 +122,18 @@ int64_t clair_kernel_launches(void);
 /* The GPU architecture the library's device code was compiled for, as nvcc's
  * __CUDA_ARCH_LIST__ value (1030 for sm_103a).  Needs no GPU. */
 int clair_compiled_arch(void);
+
+/* Execution configuration of the persistent local-solve launch (not in the paper: how
+ * the batched local solves are mapped onto the GPU) for one precision on the current
+ * device.  Systems of up to 64 unknowns of both sides of a level run in one persistent
+ * launch; those with 8 < T <= 16 go to 16-lane groups (kind_b1 = 1) or to one warp each
+ * (kind_b1 = 2), and blocks_per_sm caps the resident blocks (0 = as many as fit).  The
+ * first setup with a large enough level times the candidates and keeps the fastest
+ * (tuned = 1).  set = 1 installs the given values (tuned is stored as given; 2 marks a
+ * caller's choice, which the library then keeps); set = 0 reads them.
+ * CLAIR_ERR_ARG for other kinds or a negative block count. */
+clair_status clair_lsolve_config(int precision, int set, int* kind_b1, int* blocks_per_sm,
+                                 int* tuned);
 
 /* Fills *p with the defaults listed above. */
 clair_status clair_params_default(clair_params* p);

@@ -86,6 +86,9 @@ class clair_stats_t(ctypes.Structure):
         ("lsolve_gathered", ctypes.c_int64),
         ("fp64_cycle_from", ctypes.c_int64),
         ("k", ctypes.c_int),
+        ("lsolve_kind_b1", ctypes.c_int),
+        ("lsolve_blocks_per_sm", ctypes.c_int),
+        ("lsolve_tuned", ctypes.c_int),
     ]
 
 
@@ -126,6 +129,7 @@ _SIGNATURES = {
     "clair_last_error": (ctypes.c_char_p, []),
     "clair_kernel_launches": (ctypes.c_int64, []),
     "clair_compiled_arch": (ctypes.c_int, []),
+    "clair_lsolve_config": (_I, [_I, _I, _PI, _PI, _PI]),
 }
 
 
@@ -178,6 +182,16 @@ def clair_kernel_launches() -> int:
 
 def clair_compiled_arch() -> int:
     return int(load().clair_compiled_arch())
+
+
+def clair_lsolve_config(precision: int, kind_b1: int | None = None, blocks_per_sm: int = 0,
+                        tuned: int = 2) -> dict:
+    """Reads, or with ``kind_b1`` set installs, the persistent local-solve configuration
+    of the current device for one precision."""
+    k, b, t = ctypes.c_int(kind_b1 or 0), ctypes.c_int(blocks_per_sm), ctypes.c_int(tuned)
+    _check(load().clair_lsolve_config(precision, 0 if kind_b1 is None else 1, ctypes.byref(k),
+                                      ctypes.byref(b), ctypes.byref(t)))
+    return {"kind_b1": k.value, "blocks_per_sm": b.value, "tuned": t.value}
 
 
 def clair_params_default() -> clair_params:

@@ -100,12 +100,11 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 // Number of SMs of the current device (cached per process).
 int sm_count();
 
-// Runs `set` once per device and `key` (function attributes such as the dynamic
+// Runs `set` once per device and `tag` (function attributes such as the dynamic
 // shared-memory limit belong to the current device's context), under a lock so that
-// host threads driving several devices do not race.
-void once_per_device(int key, void (*set)());
-enum { ONCE_LSOLVE_F32 = 0, ONCE_LSOLVE_F64, ONCE_LSOLVE_F32D, ONCE_SPGEMM_CTA, ONCE_SPGEMM_FLAT,
-       ONCE_KEYS };
+// host threads driving several devices do not race.  The tag is the address of the
+// kernel whose attributes `set` installs, so every template instantiation has its own.
+void once_per_device(const void* tag, void (*set)());
 
 // ------------------------------------------------------------------------------------
 // Device utilities.
@@ -270,6 +269,8 @@ struct LocalStats {
   long long hist[6] = {0, 0, 0, 0, 0, 0};
   double sum_t3 = 0, sum_t2 = 0, sum_t = 0;
   long long gathered = 0;
+  // execution configuration of the last persistent local-solve launch
+  int config_kind_b1 = -1, config_blocks_per_sm = 0, config_tuned = 0;
 };
 
 // Kernel launches issued by this library (monotonic, process-wide).

@@ -32,6 +32,9 @@ void transfer_solve(const Csr& Ahat, const int* cpts, Csr& Z, int precision, Loc
                     cudaStream_t s);
 void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const double* B, int k,
                       LocalStats& st, Csr* keep_t, cudaStream_t s);
+void transfer_solve_pair(const Csr& At, Csr& R, const Csr& A, Csr& Pt, const int* cpts,
+                         int precision, LocalStats& st, cudaStream_t s);
+void lsolve_config(int precision, int* kind_b1, int* blocks_per_sm, int* tuned, bool set);
 void transfer_diag(const Csr& Ahat, const signed char* cf, const int* cpts, Csr& Z,
                    const double* B, int k, int iterations, LocalStats& st, Csr* keep_t,
                    cudaStream_t s);
@@ -581,8 +584,10 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
     }
     if (p.inverse == CLAIR_INVERSE_EXACT) {
       // exact block inverses: the local solves need no mode vector and overlap the smoothing
-      if (!sym) transfer_solve(At, L.cpts, L.R, p.precision, h->st, s);
-      transfer_solve(L.A, L.cpts, Pt, p.precision, h->st, s);
+      if (sym)
+        transfer_solve(L.A, L.cpts, Pt, p.precision, h->st, s);
+      else
+        transfer_solve_pair(At, L.R, L.A, Pt, L.cpts, p.precision, h->st, s);
       CLAIR_CUDA(cudaStreamWaitEvent(s, ss.join, 0));
       if (!sym) transfer_project(L.cf, L.cpts, L.R, L.B_R, km, h->st, nullptr, s);
       transfer_project(L.cf, L.cpts, Pt, L.B_P, km, h->st, &L.P, s);
@@ -1414,10 +1419,27 @@ clair_status clair_stats(clair_h h, clair_stats_t* o) {
   o->lsolve_gathered = h->st.gathered;
   o->fp64_cycle_from = h->fp64_from;
   o->k = h->kmodes;
+  o->lsolve_kind_b1 = h->st.config_kind_b1;
+  o->lsolve_blocks_per_sm = h->st.config_blocks_per_sm;
+  o->lsolve_tuned = h->st.config_tuned;
   CLAIR_API_END
 }
 
 int64_t clair_kernel_launches(void) { return launch_count(); }
+
+clair_status clair_lsolve_config(int precision, int set, int* kind_b1, int* blocks_per_sm,
+                                 int* tuned) {
+  CLAIR_API_BEGIN
+  CLAIR_REQUIRE(kind_b1 && blocks_per_sm && tuned, CLAIR_ERR_ARG, "clair_lsolve_config: null pointer");
+  CLAIR_REQUIRE(precision == CLAIR_FP64 || precision == CLAIR_MIXED, CLAIR_ERR_ARG,
+                "unknown precision");
+  if (set) {
+    CLAIR_REQUIRE((*kind_b1 == 1 || *kind_b1 == 2) && *blocks_per_sm >= 0, CLAIR_ERR_ARG,
+                  "clair_lsolve_config: kind_b1 must be 1 or 2, blocks_per_sm >= 0");
+  }
+  lsolve_config(precision, kind_b1, blocks_per_sm, tuned, set != 0);
+  CLAIR_API_END
+}
 
 int clair_compiled_arch(void) {
 #ifdef __CUDA_ARCH_LIST__

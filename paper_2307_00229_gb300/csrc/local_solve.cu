@@ -20,6 +20,7 @@
 // done implicitly by marking rows instead of swapping them.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -50,7 +51,7 @@ __device__ __forceinline__ int find_sorted(const int* z, int T, int c) {
 }
 
 // ------------------------------------------------------------------------------------
-// Sub-warp path: G lanes per system, G in {8, 16, 32}, T <= G.
+// Sub-warp path: G lanes per system, G in {8, 16}, T <= G.
 // ------------------------------------------------------------------------------------
 constexpr int LS_WARPS = 4;  // warps per block in the sub-warp path
 // Row updates of the shared- and global-tile solves read LS_CHUNK entries of the pivot
@@ -58,28 +59,32 @@ constexpr int LS_WARPS = 4;  // warps per block in the sub-warp path
 // that the compiler must order every load after the previous store.
 constexpr int LS_CHUNK = 8;
 
-// register budget: 8 blocks per SM (6 for the FP64 16-lane variant), which shared
-// memory and the rows held in registers allow without spills
+// Shared memory of one warp's groups (32 / G systems).
+template <class Real, int G>
+struct GroupSmem {
+  static constexpr int GPW = 32 / G;
+  Real tile[GPW][G][G + 1];
+  Real rhs_s[GPW][G];
+  int zl[GPW][G];
+  int pre[GPW][G + 1];
+  int rs[GPW][G];          // start of each pattern row in Ahat
+  int pivlane[GPW][G];     // lane that pivoted each elimination step
+};
+
+// One warp solves 32 / G systems: `item` is this lane's group's position in `work`
+// (live when < nwork); row p of the local matrix lives in the registers of lane p, the
+// pivot row is broadcast with shuffles.  Every lane of the warp must call it.
 template <class Real, class VT, int G>
-__global__ void __launch_bounds__(32 * LS_WARPS, (sizeof(Real) == 8 && G >= 16) ? 6 : 8)
-lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
-             const VT* __restrict__ Aval, const int* __restrict__ Zrp,
-             const int* __restrict__ Zcol, const int* __restrict__ cpts,
-             const int* __restrict__ work, int nwork, double* __restrict__ Zval,
-             unsigned long long* __restrict__ nsingular) {
-  constexpr int GPW = 32 / G;
-  __shared__ int zl[LS_WARPS * GPW][G];
-  __shared__ int pre[LS_WARPS * GPW][G + 1];
-  __shared__ int rs[LS_WARPS * GPW][G];  // start of each pattern row in Ahat
-  __shared__ Real rhs_s[LS_WARPS * GPW][G];
-  __shared__ Real tile[LS_WARPS * GPW][G][G + 1];
-  __shared__ int pivlane[LS_WARPS * GPW][G];  // lane that pivoted each elimination step
+__device__ __forceinline__ void group_body(const int* __restrict__ Arp, const int* __restrict__ Acol,
+                                           const VT* __restrict__ Aval, const int* __restrict__ Zrp,
+                                           const int* __restrict__ Zcol, const int* __restrict__ cpts,
+                                           const int* __restrict__ work, long long item, long long nwork,
+                                           double* __restrict__ Zval,
+                                           unsigned long long* __restrict__ nsingular,
+                                           GroupSmem<Real, G>& sm) {
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
   const int gsub = lane / G;          // group within warp
   const int p = lane % G;             // row owned by this lane
-  const int gib = wib * GPW + gsub;   // group within block
-  const long long item = ((long long)blockIdx.x * LS_WARPS + wib) * GPW + gsub;
   const bool live = item < nwork;
 
   int r = 0, i = 0, base = 0, len = 1;
@@ -100,27 +105,27 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
   // F-only column list
   int fcol = -1;
   if (live && p < T) fcol = Zcol[base + p + (p >= d ? 1 : 0)];
-  zl[gib][p] = fcol;
+  sm.zl[gsub][p] = fcol;
   __syncwarp();
 
   // Gather the local matrix (row p = row l_p of Ahat restricted to the pattern) and the
   // right-hand side -Ahat[l_p, i].  The rows' entries are flattened (a group scan of the
   // row lengths) and spread over all G lanes so their loads are independent.
 #pragma unroll
-  for (int q = 0; q < G; ++q) tile[gib][p][q] = Real(0);
-  rhs_s[gib][p] = Real(0);
+  for (int q = 0; q < G; ++q) sm.tile[gsub][p][q] = Real(0);
+  sm.rhs_s[gsub][p] = Real(0);
   const int row0 = (live && p < T) ? Arp[fcol] : 0;
   int rlen = (live && p < T) ? Arp[fcol + 1] - row0 : 0;
-  rs[gib][p] = row0;
+  sm.rs[gsub][p] = row0;
 #pragma unroll
   for (int o = 1; o < G; o <<= 1) {
     const int t = __shfl_up_sync(0xffffffffu, rlen, o, G);
     if (p >= o) rlen += t;
   }
-  pre[gib][p + 1] = rlen;  // inclusive prefix
-  if (p == 0) pre[gib][0] = 0;
+  sm.pre[gsub][p + 1] = rlen;  // inclusive prefix
+  if (p == 0) sm.pre[gsub][0] = 0;
   __syncwarp();
-  const int total = pre[gib][G];
+  const int total = sm.pre[gsub][G];
   // entry indices come from shared memory, so the loads of different entries are
   // independent (no global row-pointer load in front of each); entries go in batches of
   // GB per lane, all loads and column searches of a batch before its stores
@@ -136,9 +141,9 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
         int lo = 0, hi = G;  // row r with pre[r] <= t < pre[r + 1]
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
-          if (pre[gib][mid] <= t) lo = mid; else hi = mid;
+          if (sm.pre[gsub][mid] <= t) lo = mid; else hi = mid;
         }
-        const int e = rs[gib][lo] + (t - pre[gib][lo]);
+        const int e = sm.rs[gsub][lo] + (t - sm.pre[gsub][lo]);
         row_of[u] = lo;
         col_of[u] = Acol[e];
         val_of[u] = Real(Aval[e]);
@@ -147,18 +152,18 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
     int q_of[GB];
 #pragma unroll
     for (int u = 0; u < GB; ++u)
-      q_of[u] = row_of[u] < 0 ? -1 : (col_of[u] == i ? T : find_sorted(zl[gib], T, col_of[u]));
+      q_of[u] = row_of[u] < 0 ? -1 : (col_of[u] == i ? T : find_sorted(sm.zl[gsub], T, col_of[u]));
 #pragma unroll
     for (int u = 0; u < GB; ++u) {
-      if (q_of[u] == T) rhs_s[gib][row_of[u]] = -val_of[u];
-      else if (q_of[u] >= 0) tile[gib][row_of[u]][q_of[u]] = val_of[u];
+      if (q_of[u] == T) sm.rhs_s[gsub][row_of[u]] = -val_of[u];
+      else if (q_of[u] >= 0) sm.tile[gsub][row_of[u]][q_of[u]] = val_of[u];
     }
   }
   __syncwarp();
   Real a[G];
 #pragma unroll
-  for (int q = 0; q < G; ++q) a[q] = tile[gib][p][q];
-  Real b = rhs_s[gib][p];
+  for (int q = 0; q < G; ++q) a[q] = sm.tile[gsub][p][q];
+  Real b = sm.rhs_s[gsub][p];
 
   // elimination with implicit partial pivoting; steps and columns beyond the largest
   // system of the warp are no-ops for every group, so the loops stop there (warp-uniform)
@@ -180,7 +185,7 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
         who = w2;
       }
     }
-    if (p == 0) pivlane[gib][k] = who;
+    if (p == 0) sm.pivlane[gsub][k] = who;
     const bool step = k < T;
     if (step && !(v > Real(0))) singular = true;
     const Real pk = __shfl_sync(0xffffffffu, a[k], who, G);
@@ -205,7 +210,7 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
 #pragma unroll
   for (int k = G - 1; k >= 0; --k) {
     if (k >= Tw) continue;
-    const int own = pivlane[gib][k];
+    const int own = sm.pivlane[gsub][k];
     Real xk = (p == own && a[k] != Real(0)) ? b / a[k] : Real(0);
     xk = __shfl_sync(0xffffffffu, xk, own, G);
     if (k < T) {
@@ -215,20 +220,41 @@ lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
   }
   // any lane of the group may have flagged a zero pivot (ballot before any exit)
   const bool sing = (__ballot_sync(0xffffffffu, singular) & gmask) != 0;
-  if (!live) return;
-  if (p < T) Zval[base + p + (p >= d ? 1 : 0)] = sing ? 0.0 : (double)myx;
-  if (p == 0) {
-    Zval[base + d] = 1.0;
-    if (sing) atomicAdd(nsingular, 1ull);
+  if (live) {
+    if (p < T) Zval[base + p + (p >= d ? 1 : 0)] = sing ? 0.0 : (double)myx;
+    if (p == 0) {
+      Zval[base + d] = 1.0;
+      if (sing) atomicAdd(nsingular, 1ull);
+    }
   }
+  __syncwarp();  // the shared arrays are reused by the warp's next systems
+}
+
+// register budget: 8 blocks per SM (6 for the FP64 16-lane variant), which shared
+// memory and the rows held in registers allow without spills
+template <class Real, class VT, int G>
+__global__ void __launch_bounds__(32 * LS_WARPS, (sizeof(Real) == 8 && G >= 16) ? 6 : 8)
+lsolve_group(const int* __restrict__ Arp, const int* __restrict__ Acol,
+             const VT* __restrict__ Aval, const int* __restrict__ Zrp,
+             const int* __restrict__ Zcol, const int* __restrict__ cpts,
+             const int* __restrict__ work, int nwork, double* __restrict__ Zval,
+             unsigned long long* __restrict__ nsingular) {
+  constexpr int GPW = 32 / G;
+  __shared__ GroupSmem<Real, G> sm[LS_WARPS];
+  const int wib = threadIdx.x >> 5;
+  const int gsub = (threadIdx.x & 31) / G;
+  const long long item = ((long long)blockIdx.x * LS_WARPS + wib) * GPW + gsub;
+  group_body<Real, VT, G>(Arp, Acol, Aval, Zrp, Zcol, cpts, work, item, nwork, Zval, nsingular,
+                          sm[wib]);
 }
 
 // ------------------------------------------------------------------------------------
-// CTA path: one system per block of TMAX threads, T <= TMAX (64 or 128); the matrix
-// lives in shared memory, thread r owns row r.  Rows are padded to a multiple of 16
-// bytes so that a row update moves 16-byte vectors; it starts at the vector holding
-// column k+1, which also rewrites columns <= k of the row: those are never read again
-// (a row's entries left of its own pivot step take no part in back substitution).
+// Team path: one system per team of TMAX threads (a warp, a pair of warps with a named
+// barrier, or a whole block), T <= TMAX; the matrix lives in shared memory, thread r owns
+// row r.  Rows are padded to a multiple of 16 bytes so that a row update moves 16-byte
+// vectors; it starts at the vector holding column k+1, which also rewrites columns <= k
+// of the row: those are never read again (a row's entries left of its own pivot step
+// take no part in back substitution).
 // ------------------------------------------------------------------------------------
 template <class Real>
 struct Vec16;
@@ -256,71 +282,87 @@ __host__ __device__ constexpr int cta_pitch() {
   return TMAX + 16 / (int)sizeof(Real);  // 16-byte rows, row starts 4 banks apart
 }
 
-// shared memory holds these to about 1024 resident threads per SM, so the register
-// budget is set for that many (64 each) rather than for full occupancy
-template <class Real, class VT, int TMAX>
-__global__ void __launch_bounds__(TMAX, 1024 / TMAX)
-lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
-           const VT* __restrict__ Aval, const int* __restrict__ Zrp,
-           const int* __restrict__ Zcol, const int* __restrict__ cpts,
-           const int* __restrict__ work, double* __restrict__ Zval,
-           unsigned long long* __restrict__ nsingular) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// Shared memory of one team (the tile first: 16-byte aligned rows).
+template <class Real, int TMAX>
+struct alignas(16) TeamSmem {
+  static constexpr int NW = TMAX / 32;
+  Real tile[TMAX * cta_pitch<Real, TMAX>()];
+  Real rhs[TMAX];
+  Real xs[TMAX];
+  Real red_v[NW];      // FP64: largest |value| of each warp
+  int zl[TMAX];
+  int steprow[TMAX];
+  int pre[TMAX + 1];
+  int rs[TMAX];        // start of each pattern row in Ahat
+  int wsum[NW];
+  unsigned red_k[NW];  // FP32: largest pivot key of each warp
+  int red_w[NW];       // and its row
+  int s_d, s_sing;
+};
+
+// Barrier of a team: the warp itself, a named barrier of TMAX threads, or the block.
+enum { TEAM_WARP = 0, TEAM_NAMED = 1, TEAM_BLOCK = 2 };
+template <int KIND, int TMAX>
+__device__ __forceinline__ void team_sync(int bar_id) {
+  if constexpr (KIND == TEAM_WARP) {
+    __syncwarp();
+  } else if constexpr (KIND == TEAM_NAMED) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(TMAX) : "memory");
+  } else {
+    __syncthreads();
+  }
+}
+
+// Team thread t (0 <= t < TMAX) of the team that solves system r (a row of the pattern).
+template <class Real, class VT, int TMAX, int KIND>
+__device__ __forceinline__ void team_body(const int* __restrict__ Arp, const int* __restrict__ Acol,
+                                          const VT* __restrict__ Aval, const int* __restrict__ Zrp,
+                                          const int* __restrict__ Zcol, const int* __restrict__ cpts,
+                                          int r, double* __restrict__ Zval,
+                                          unsigned long long* __restrict__ nsingular,
+                                          TeamSmem<Real, TMAX>& sm, int t, int bar_id) {
   using V = typename Vec16<Real>::type;
   constexpr int VN = 16 / (int)sizeof(Real);
   constexpr int PITCH = cta_pitch<Real, TMAX>();
   constexpr int NW = TMAX / 32;
-  Real* tile = reinterpret_cast<Real*>(smem_raw);                 // TMAX x PITCH
-  Real* rhs = tile + TMAX * PITCH;                                  // TMAX
-  Real* xs = rhs + TMAX;                                            // TMAX
-  int* zl = reinterpret_cast<int*>(xs + TMAX);                      // TMAX
-  int* steprow = zl + TMAX;                                         // TMAX
-  __shared__ unsigned red_k[NW];   // FP32: largest pivot key of each warp
-  __shared__ Real red_v[NW];       // FP64: largest |value| of each warp
-  __shared__ int red_w[NW];        // and its row
-  __shared__ int s_d, s_sing;
-
-  const int t = threadIdx.x;
+  Real* tile = sm.tile;
+  Real* rhs = sm.rhs;
   const int lane = t & 31, wid = t >> 5;
-  const int r = work[blockIdx.x];
   const int i = cpts[r];
   const int base = Zrp[r];
   const int len = Zrp[r + 1] - base;
   const int T = len - 1;
   if (t == 0) {
-    s_d = T;  // position TMAX (unseen by the threads) only when T == TMAX
-    s_sing = 0;
+    sm.s_d = T;  // position TMAX (unseen by the threads) only when T == TMAX
+    sm.s_sing = 0;
   }
-  __syncthreads();
-  if (t < len && Zcol[base + t] == i) s_d = t;
-  __syncthreads();
-  const int d = s_d;
-  if (t < T) zl[t] = Zcol[base + t + (t >= d ? 1 : 0)];
+  team_sync<KIND, TMAX>(bar_id);
+  if (t < len && Zcol[base + t] == i) sm.s_d = t;
+  team_sync<KIND, TMAX>(bar_id);
+  const int d = sm.s_d;
+  if (t < T) sm.zl[t] = Zcol[base + t + (t >= d ? 1 : 0)];
   Real* row = tile + t * PITCH;
   for (int q = 0; q < TMAX; q += VN) *reinterpret_cast<V*>(row + q) = V{};
   rhs[t] = Real(0);
-  __syncthreads();
-  // flattened gather: block scan of the row lengths, then all threads over the entries
-  __shared__ int pre[TMAX + 1];
-  __shared__ int wsum[NW];
-  __shared__ int rs[TMAX];  // start of each pattern row in Ahat
-  const int rstart = t < T ? Arp[zl[t]] : 0;
-  rs[t] = rstart;
-  int rlen = t < T ? Arp[zl[t] + 1] - rstart : 0;
+  team_sync<KIND, TMAX>(bar_id);
+  // flattened gather: team scan of the row lengths, then all threads over the entries
+  const int rstart = t < T ? Arp[sm.zl[t]] : 0;
+  sm.rs[t] = rstart;
+  int rlen = t < T ? Arp[sm.zl[t] + 1] - rstart : 0;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int v = __shfl_up_sync(0xffffffffu, rlen, o);
     if (lane >= o) rlen += v;
   }
-  if (lane == 31) wsum[wid] = rlen;
-  __syncthreads();
-  for (int w = 0; w < wid; ++w) rlen += wsum[w];
-  pre[t + 1] = rlen;
-  if (t == 0) pre[0] = 0;
-  __syncthreads();
-  const int total = pre[TMAX];
+  if (lane == 31) sm.wsum[wid] = rlen;
+  team_sync<KIND, TMAX>(bar_id);
+  for (int w = 0; w < wid; ++w) rlen += sm.wsum[w];
+  sm.pre[t + 1] = rlen;
+  if (t == 0) sm.pre[0] = 0;
+  team_sync<KIND, TMAX>(bar_id);
+  const int total = sm.pre[TMAX];
   // entries in batches of GB per thread: all loads of a batch, then its column searches,
-  // then its stores (zl shares the dynamic array with the tile, so a store would order
+  // then its stores (zl shares the shared block with the tile, so a store would order
   // every later load after it)
   constexpr int GB = 4;
   for (int f0 = t; f0 < total; f0 += GB * TMAX) {
@@ -334,9 +376,9 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
         int lo = 0, hi = TMAX;  // row r with pre[r] <= f < pre[r + 1]
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
-          if (pre[mid] <= f) lo = mid; else hi = mid;
+          if (sm.pre[mid] <= f) lo = mid; else hi = mid;
         }
-        const int e = rs[lo] + (f - pre[lo]);
+        const int e = sm.rs[lo] + (f - sm.pre[lo]);
         row_of[u] = lo;
         col_of[u] = Acol[e];
         val_of[u] = Real(Aval[e]);
@@ -345,7 +387,7 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
     int q_of[GB];
 #pragma unroll
     for (int u = 0; u < GB; ++u)
-      q_of[u] = row_of[u] < 0 ? -1 : (col_of[u] == i ? T : find_sorted(zl, T, col_of[u]));
+      q_of[u] = row_of[u] < 0 ? -1 : (col_of[u] == i ? T : find_sorted(sm.zl, T, col_of[u]));
 #pragma unroll
     for (int u = 0; u < GB; ++u) {
       if (q_of[u] == T) rhs[row_of[u]] = -val_of[u];
@@ -354,10 +396,10 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
   }
   bool done = t >= T;
   int mystep = -1;
-  __syncthreads();
+  team_sync<KIND, TMAX>(bar_id);
   for (int k = 0; k < T; ++k) {
     // pivot: largest |a| of column k among the rows not yet eliminated, lowest row on
-    // ties; each warp posts its candidate, every thread then reads the block's
+    // ties; each warp posts its candidate, every thread then reads the team's
     const Real rk = row[k];
     if constexpr (sizeof(Real) == 4) {
       // non-negative floats order as their bit patterns; key 0 marks eliminated rows
@@ -365,8 +407,8 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
       const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
       const unsigned bal = __ballot_sync(0xffffffffu, key == wmax);
       if (lane == 0) {
-        red_k[wid] = wmax;
-        red_w[wid] = wid * 32 + __ffs(bal) - 1;
+        sm.red_k[wid] = wmax;
+        sm.red_w[wid] = wid * 32 + __ffs(bal) - 1;
       }
     } else {
       Real v = done ? Real(-1) : (rk < 0 ? -rk : rk);
@@ -381,34 +423,34 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
         }
       }
       if (lane == 0) {
-        red_v[wid] = v;
-        red_w[wid] = who;
+        sm.red_v[wid] = v;
+        sm.red_w[wid] = who;
       }
     }
-    __syncthreads();
-    int piv = red_w[0];
+    team_sync<KIND, TMAX>(bar_id);
+    int piv = sm.red_w[0];
     if constexpr (sizeof(Real) == 4) {
-      unsigned bk = red_k[0];
+      unsigned bk = sm.red_k[0];
 #pragma unroll
       for (int w = 1; w < NW; ++w)
-        if (red_k[w] > bk) {  // warps hold increasing rows: strict keeps the lowest
-          bk = red_k[w];
-          piv = red_w[w];
+        if (sm.red_k[w] > bk) {  // warps hold increasing rows: strict keeps the lowest
+          bk = sm.red_k[w];
+          piv = sm.red_w[w];
         }
     } else {
-      Real bv = red_v[0];
+      Real bv = sm.red_v[0];
 #pragma unroll
       for (int w = 1; w < NW; ++w)
-        if (red_v[w] > bv) {
-          bv = red_v[w];
-          piv = red_w[w];
+        if (sm.red_v[w] > bv) {
+          bv = sm.red_v[w];
+          piv = sm.red_w[w];
         }
     }
     const Real* prow = tile + piv * PITCH;
     const Real pk = prow[k];
     if (t == 0) {
-      steprow[k] = piv;
-      if (!((pk < 0 ? -pk : pk) > Real(0))) s_sing = 1;
+      sm.steprow[k] = piv;
+      if (!((pk < 0 ? -pk : pk) > Real(0))) sm.s_sing = 1;
     }
     if (t == piv) {
       done = true;
@@ -433,29 +475,147 @@ lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
       }
       rhs[t] -= l * rhs[piv];
     }
-    __syncthreads();
+    team_sync<KIND, TMAX>(bar_id);
   }
   // back substitution: one barrier per step suffices, each thread updates only its own
   // right-hand side and every x_k has its own slot
   for (int k = T - 1; k >= 0; --k) {
-    const int own = steprow[k];
-    if (t == own) xs[k] = row[k] != Real(0) ? rhs[t] / row[k] : Real(0);
-    __syncthreads();
-    const Real xk = xs[k];
+    const int own = sm.steprow[k];
+    if (t == own) sm.xs[k] = row[k] != Real(0) ? rhs[t] / row[k] : Real(0);
+    team_sync<KIND, TMAX>(bar_id);
+    const Real xk = sm.xs[k];
     if (mystep >= 0 && mystep < k) rhs[t] -= row[k] * xk;
   }
-  __syncthreads();
-  const bool sing = s_sing != 0;
-  if (t < T) Zval[base + t + (t >= d ? 1 : 0)] = sing ? 0.0 : (double)xs[t];
+  team_sync<KIND, TMAX>(bar_id);
+  const bool sing = sm.s_sing != 0;
+  if (t < T) Zval[base + t + (t >= d ? 1 : 0)] = sing ? 0.0 : (double)sm.xs[t];
   if (t == 0) {
     Zval[base + d] = 1.0;
     if (sing) atomicAdd(nsingular, 1ull);
   }
+  team_sync<KIND, TMAX>(bar_id);  // the team's shared block is reused by its next system
+}
+
+// shared memory holds these to about 1024 resident threads per SM, so the register
+// budget is set for that many (64 each) rather than for full occupancy
+template <class Real, class VT, int TMAX>
+__global__ void __launch_bounds__(TMAX, 1024 / TMAX)
+lsolve_cta(const int* __restrict__ Arp, const int* __restrict__ Acol,
+           const VT* __restrict__ Aval, const int* __restrict__ Zrp,
+           const int* __restrict__ Zcol, const int* __restrict__ cpts,
+           const int* __restrict__ work, double* __restrict__ Zval,
+           unsigned long long* __restrict__ nsingular) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<TeamSmem<Real, TMAX>*>(smem_raw);
+  team_body<Real, VT, TMAX, TEAM_BLOCK>(Arp, Acol, Aval, Zrp, Zcol, cpts, work[blockIdx.x], Zval,
+                                        nsingular, sm, threadIdx.x, 0);
 }
 
 template <class Real, int TMAX>
 static size_t cta_smem() {
-  return sizeof(Real) * ((size_t)TMAX * cta_pitch<Real, TMAX>() + 2 * TMAX) + sizeof(int) * 2 * TMAX;
+  return sizeof(TeamSmem<Real, TMAX>);
+}
+
+// ------------------------------------------------------------------------------------
+// Persistent launch: the systems of up to 64 unknowns of both sides of a level (R on
+// A^T, P on A) in one launch of a fixed grid.  Blocks of four warps take tasks from a
+// device ticket; the task list is derived on the device from the bucket counts, largest
+// systems first.  A task is 16 systems of T <= 8 (4 groups of 8 lanes per warp), 8 of
+// T <= 16 (2 groups of 16), 4 of T <= 32 (a warp each) or 2 of T <= 64 (a pair of warps
+// each, synchronised by a named barrier).  Systems with 8 < T <= 16 go to the 16-lane
+// groups or to single warps, as the autotuner chose.
+// ------------------------------------------------------------------------------------
+constexpr int LP_THREADS = 128;
+enum { LK_G8 = 0, LK_G16 = 1, LK_W32 = 2, LK_P64 = 3 };
+__host__ __device__ constexpr int lk_systems(int kind) {
+  return kind == LK_G8 ? 16 : kind == LK_G16 ? 8 : kind == LK_W32 ? 4 : 2;
+}
+
+template <class VT>
+struct SideArgs {
+  const int *Arp, *Acol;
+  const VT* Aval;
+  const int *Zrp, *Zcol, *cpts, *lists;  // lists: bucket b at lists + b * nc
+  const int* counts;                      // device bucket counts
+  double* Zval;
+  int nc;
+};
+
+template <class Real>
+union PersistSmem {
+  GroupSmem<Real, 8> g8[4];
+  GroupSmem<Real, 16> g16[4];
+  TeamSmem<Real, 32> w32[4];
+  TeamSmem<Real, 64> p64[2];
+};
+
+template <class Real>
+static size_t persist_smem(bool g8, bool g16, bool w32, bool p64) {
+  size_t b = 16;
+  if (g8) b = std::max(b, 4 * sizeof(GroupSmem<Real, 8>));
+  if (g16) b = std::max(b, 4 * sizeof(GroupSmem<Real, 16>));
+  if (w32) b = std::max(b, 4 * sizeof(TeamSmem<Real, 32>));
+  if (p64) b = std::max(b, 2 * sizeof(TeamSmem<Real, 64>));
+  return b;
+}
+
+template <class Real, class VT>
+__global__ void __launch_bounds__(LP_THREADS)
+lsolve_persist(SideArgs<VT> S0, SideArgs<VT> S1, int nsides, int kind_b1, int* __restrict__ ticket,
+               unsigned long long* __restrict__ nsingular) {
+  extern __shared__ __align__(16) unsigned char lp_smem[];
+  auto& sm = *reinterpret_cast<PersistSmem<Real>*>(lp_smem);
+  __shared__ int seg_end[8], seg_kind[8];
+  __shared__ int s_task;
+  // segment q: bucket 3 - q / 2 (largest first), side q % 2
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int q = 0; q < 8; ++q) {
+      const int b = 3 - (q >> 1), side = q & 1;
+      const int cnt = side < nsides ? (side ? S1.counts[b] : S0.counts[b]) : 0;
+      const int kind = b == 3 ? LK_P64 : b == 2 ? LK_W32 : b == 1 ? kind_b1 : LK_G8;
+      acc += (cnt + lk_systems(kind) - 1) / lk_systems(kind);
+      seg_end[q] = acc;
+      seg_kind[q] = kind;
+    }
+  }
+  __syncthreads();
+  const int total = seg_end[7];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int task = s_task;
+    __syncthreads();  // every thread has read s_task before thread 0 rewrites it
+    if (task >= total) break;
+    int q = 0;
+    while (task >= seg_end[q]) ++q;
+    const int b = 3 - (q >> 1);
+    const SideArgs<VT>& S = (q & 1) ? S1 : S0;
+    const int kind = seg_kind[q];
+    const long long first = (long long)(task - (q ? seg_end[q - 1] : 0)) * lk_systems(kind);
+    const long long cnt = S.counts[b];
+    const int* list = S.lists + (long long)b * S.nc;
+    if (kind == LK_G8) {
+      group_body<Real, VT, 8>(S.Arp, S.Acol, S.Aval, S.Zrp, S.Zcol, S.cpts, list,
+                              first + wib * 4 + lane / 8, cnt, S.Zval, nsingular, sm.g8[wib]);
+    } else if (kind == LK_G16) {
+      group_body<Real, VT, 16>(S.Arp, S.Acol, S.Aval, S.Zrp, S.Zcol, S.cpts, list,
+                               first + wib * 2 + lane / 16, cnt, S.Zval, nsingular, sm.g16[wib]);
+    } else if (kind == LK_W32) {
+      const long long item = first + wib;
+      if (item < cnt)
+        team_body<Real, VT, 32, TEAM_WARP>(S.Arp, S.Acol, S.Aval, S.Zrp, S.Zcol, S.cpts, list[item],
+                                           S.Zval, nsingular, sm.w32[wib], lane, 0);
+    } else {
+      const int team = wib >> 1;
+      const long long item = first + team;
+      if (item < cnt)
+        team_body<Real, VT, 64, TEAM_NAMED>(S.Arp, S.Acol, S.Aval, S.Zrp, S.Zcol, S.cpts,
+                                            list[item], S.Zval, nsingular, sm.p64[team],
+                                            threadIdx.x & 63, 1 + team);
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -882,11 +1042,10 @@ template <class Real, class VT>
 static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const int* Zcol,
                           const int* cpts, const int* lists, const int* counts_h, int nc,
                           double* Zval, unsigned long long* nsing, cudaStream_t s,
-                          Real* big_scratch = nullptr, int big_pitch = 0, int big_chunk = 0) {
+                          Real* big_scratch = nullptr, int big_pitch = 0, int big_chunk = 0,
+                          int first_bucket = 0) {
   // the shared-memory limits above 48 KB are per-device function attributes
-  constexpr int key = sizeof(Real) == 8 ? ONCE_LSOLVE_F64
-                      : (sizeof(VT) == 8 ? ONCE_LSOLVE_F32D : ONCE_LSOLVE_F32);
-  once_per_device(key, [] {
+  once_per_device((const void*)lsolve_cta<Real, VT, 128>, [] {
     CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, VT, 64>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)cta_smem<Real, 64>()));
@@ -898,18 +1057,18 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
                                     (int)big_smem<Real>(LS_TBIG)));
   });
   const int per_block[2] = {LS_WARPS * 4, LS_WARPS * 2};
-  if (counts_h[0])
+  if (counts_h[0] && first_bucket <= 0)
     lsolve_group<Real, VT, 8><<<ceil_div(counts_h[0], per_block[0]), 32 * LS_WARPS, 0, s>>>(
         Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 0LL * nc, counts_h[0], Zval, nsing); ::clair::count_launch();
-  if (counts_h[1])
+  if (counts_h[1] && first_bucket <= 1)
     lsolve_group<Real, VT, 16><<<ceil_div(counts_h[1], per_block[1]), 32 * LS_WARPS, 0, s>>>(
         Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 1LL * nc, counts_h[1], Zval, nsing); ::clair::count_launch();
   // 16 < T <= 32: the CTA kernel with one warp per block (rolled loops; a 32-lane register
   // elimination unrolls into more code than the instruction cache holds)
-  if (counts_h[2])
+  if (counts_h[2] && first_bucket <= 2)
     lsolve_cta<Real, VT, 32><<<counts_h[2], 32, cta_smem<Real, 32>(), s>>>(
         Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 2LL * nc, Zval, nsing); ::clair::count_launch();
-  if (counts_h[3])
+  if (counts_h[3] && first_bucket <= 3)
     lsolve_cta<Real, VT, 64><<<counts_h[3], 64, cta_smem<Real, 64>(), s>>>(
         Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 3LL * nc, Zval, nsing); ::clair::count_launch();
   if (counts_h[4])
@@ -942,43 +1101,179 @@ static Real* big_tiles(const int* counts_h, int& pitch, int& chunk, cudaStream_t
   return dalloc<Real>((size_t)chunk * pitch * pitch, s);
 }
 
-// Local lAIR solves for all coarse rows of the pattern Z (nc x n), values into Zval.
-void local_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* cpts, int nc,
-                  int precision, double* Zval, LocalStats& st, cudaStream_t s) {
-  int* lists = dalloc<int>((long long)LS_BUCKETS * std::max(nc, 1), s);
-  int* counts = dalloc<int>(LS_BUCKETS + 2, s);
-  unsigned long long* nsing = dalloc<unsigned long long>(5, s);  // [0] singular, [1..4] work
-  CLAIR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * (LS_BUCKETS + 2), s));
-  CLAIR_CUDA(cudaMemsetAsync(nsing, 0, 5 * sizeof(unsigned long long), s));
-  if (nc) bucket_rows<<<ceil_div(nc, 256), 256, 0, s>>>(Zrp, nc, lists, counts, Zcol, cpts,
-                                                        Ahat.rowptr, counts + LS_BUCKETS,
-                                                        nsing + 1); ::clair::count_launch();
+// ---- execution configuration of the persistent launch, per device and precision -------
+struct LsolveConfig {
+  int kind_b1 = LK_G16;   // systems with 8 < T <= 16: 16-lane groups or single warps
+  int blocks_per_sm = 0;  // 0: as many as fit
+  int tuned = 0;          // 1: chosen by timing, 2: set by the caller
+};
+static std::mutex g_cfg_mu;
+static LsolveConfig g_cfg[256][2];
+
+static LsolveConfig& config_slot(int precision) {
+  int dev = 0;
+  CLAIR_CUDA(cudaGetDevice(&dev));
+  CLAIR_REQUIRE(dev >= 0 && dev < 256, CLAIR_ERR_ARG, "device ordinal %d out of range", dev);
+  return g_cfg[dev][precision == CLAIR_MIXED ? 1 : 0];
+}
+
+// Levels with fewer systems of T <= 64 than this are not used for timing candidates.
+constexpr long long LS_TUNE_MIN = 20000;
+
+struct SideIn {
+  const Csr* Ahat;
+  const int* Zrp;
+  const int* Zcol;
+  double* Zval;
+  int nc;
+};
+
+template <class Real, class VT>
+static void persistent_launch(const SideArgs<VT>* sa, int nsides, const int (*counts_h)[LS_BUCKETS + 2],
+                              const LsolveConfig& cfg, int* ticket, unsigned long long* nsing,
+                              cudaStream_t s) {
+  bool has[4] = {false, false, false, false};
+  long long tasks = 0;
+  for (int q = 0; q < nsides; ++q) {
+    has[LK_G8] |= counts_h[q][0] > 0;
+    has[cfg.kind_b1] |= counts_h[q][1] > 0;
+    has[LK_W32] |= counts_h[q][2] > 0;
+    has[LK_P64] |= counts_h[q][3] > 0;
+    tasks += ceil_div(counts_h[q][0], lk_systems(LK_G8)) +
+             ceil_div(counts_h[q][1], lk_systems(cfg.kind_b1)) +
+             ceil_div(counts_h[q][2], lk_systems(LK_W32)) + ceil_div(counts_h[q][3], lk_systems(LK_P64));
+  }
+  if (tasks == 0) return;
+  once_per_device((const void*)lsolve_persist<Real, VT>, [] {
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_persist<Real, VT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(PersistSmem<Real>)));
+  });
+  const size_t smem = persist_smem<Real>(has[LK_G8], has[LK_G16], has[LK_W32], has[LK_P64]);
+  int fit = 0;
+  CLAIR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, lsolve_persist<Real, VT>, LP_THREADS,
+                                                           smem));
+  const int per_sm = std::max(1, cfg.blocks_per_sm > 0 ? std::min(fit, cfg.blocks_per_sm) : fit);
+  const int grid = (int)std::min<long long>(tasks, (long long)sm_count() * per_sm);
+  CLAIR_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), s));
+  lsolve_persist<Real, VT><<<grid, LP_THREADS, smem, s>>>(sa[0], nsides > 1 ? sa[1] : sa[0], nsides,
+                                                          cfg.kind_b1, ticket, nsing); ::clair::count_launch();
   CLAIR_LAUNCHED();
-  int counts_h[LS_BUCKETS + 2];
-  CLAIR_CUDA(cudaMemcpyAsync(counts_h, counts, sizeof(counts_h), cudaMemcpyDeviceToHost, s));
+}
+
+// Times the candidate configurations on this level (the launches are idempotent: they
+// rewrite the same weights) and keeps the fastest for the process.
+template <class Real, class VT>
+static void autotune(const SideArgs<VT>* sa, int nsides, const int (*counts_h)[LS_BUCKETS + 2],
+                     LsolveConfig& cfg, int* ticket, cudaStream_t s) {
+  unsigned long long* scratch = dalloc<unsigned long long>(1, s);
+  LsolveConfig cands[3];
+  cands[0].kind_b1 = LK_G16;
+  cands[1].kind_b1 = LK_W32;
+  cands[2].kind_b1 = LK_G16;
+  cands[2].blocks_per_sm = 4;
+  cudaEvent_t e0, e1;
+  CLAIR_CUDA(cudaEventCreate(&e0));
+  CLAIR_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int pick = 0;
+  for (int c = 0; c < 3; ++c) {
+    for (int rep = 0; rep < 2; ++rep) {  // the first run warms the caches and the code
+      CLAIR_CUDA(cudaEventRecord(e0, s));
+      persistent_launch<Real, VT>(sa, nsides, counts_h, cands[c], ticket, scratch, s);
+      CLAIR_CUDA(cudaEventRecord(e1, s));
+    }
+    CLAIR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CLAIR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dfree(scratch, s);
+  cfg = cands[pick];
+  cfg.tuned = 1;
+}
+
+// Local lAIR solves for all coarse rows of one or two patterns (the two sides of a level:
+// R on A^T and P on A), values into each side's Zval.  Systems of up to 64 unknowns of
+// every side go to one persistent launch; larger ones to the CTA and large-tile kernels.
+void local_solves_multi(const SideIn* sides, int nsides, const int* cpts, int precision,
+                        LocalStats& st, cudaStream_t s) {
+  int* lists[2] = {nullptr, nullptr};
+  int* counts = dalloc<int>(2 * (LS_BUCKETS + 2), s);
+  unsigned long long* nsing = dalloc<unsigned long long>(5, s);  // [0] singular, [1..4] work
+  int* ticket = dalloc<int>(1, s);
+  CLAIR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * 2 * (LS_BUCKETS + 2), s));
+  CLAIR_CUDA(cudaMemsetAsync(nsing, 0, 5 * sizeof(unsigned long long), s));
+  for (int q = 0; q < nsides; ++q) {
+    const SideIn& S = sides[q];
+    lists[q] = dalloc<int>((long long)LS_BUCKETS * std::max(S.nc, 1), s);
+    int* cq = counts + q * (LS_BUCKETS + 2);
+    if (S.nc) bucket_rows<<<ceil_div(S.nc, 256), 256, 0, s>>>(S.Zrp, S.nc, lists[q], cq, S.Zcol, cpts,
+                                                             S.Ahat->rowptr, cq + LS_BUCKETS,
+                                                             nsing + 1); ::clair::count_launch();
+  }
+  CLAIR_LAUNCHED();
+  int counts_h[2][LS_BUCKETS + 2] = {};
+  CLAIR_CUDA(cudaMemcpyAsync(counts_h, counts, sizeof(int) * nsides * (LS_BUCKETS + 2),
+                             cudaMemcpyDeviceToHost, s));
   CLAIR_CUDA(cudaStreamSynchronize(s));
-  CLAIR_REQUIRE(counts_h[LS_BUCKETS] == 0, CLAIR_ERR_CAPACITY,
-                "%d local systems larger than %d unknowns", counts_h[LS_BUCKETS], LS_TBIG);
+  for (int q = 0; q < nsides; ++q)
+    CLAIR_REQUIRE(counts_h[q][LS_BUCKETS] == 0, CLAIR_ERR_CAPACITY,
+                  "%d local systems larger than %d unknowns", counts_h[q][LS_BUCKETS], LS_TBIG);
   {
     ClockScope clk(PH_LSOLVE, s);
-    if (precision == CLAIR_MIXED)
-    {
-      int pitch, chunk;
-      float* tiles = big_tiles<float>(counts_h, pitch, chunk, s);
-      float* vals32 = dalloc<float>(std::max(Ahat.nnz, 1), s);
-      to_float(Ahat.val, vals32, Ahat.nnz, s);
-      launch_solves<float, float>(Ahat, vals32, Zrp, Zcol, cpts, lists, counts_h, nc, Zval, nsing,
-                                  s, tiles, pitch, chunk);
-      dfree(vals32, s);
-      dfree(tiles, s);
-    }
-    else
-    {
-      int pitch, chunk;
-      double* tiles = big_tiles<double>(counts_h, pitch, chunk, s);
-      launch_solves<double, double>(Ahat, Ahat.val, Zrp, Zcol, cpts, lists, counts_h, nc, Zval,
-                                    nsing, s, tiles, pitch, chunk);
-      dfree(tiles, s);
+    auto run = [&](auto real_tag, auto& vals) {
+      using Real = decltype(real_tag);
+      using VT = typename std::remove_cv<typename std::remove_pointer<
+          typename std::remove_reference<decltype(vals[0])>::type>::type>::type;
+      SideArgs<VT> sa[2];
+      for (int q = 0; q < nsides; ++q) {
+        const SideIn& S = sides[q];
+        sa[q] = SideArgs<VT>{S.Ahat->rowptr, S.Ahat->col, vals[q], S.Zrp, S.Zcol, cpts, lists[q],
+                             counts + q * (LS_BUCKETS + 2), S.Zval, S.nc};
+      }
+      LsolveConfig cfg;
+      {
+        std::lock_guard<std::mutex> lock(g_cfg_mu);
+        LsolveConfig& slot = config_slot(precision);
+        long long small = 0;
+        for (int q = 0; q < nsides; ++q)
+          for (int b = 0; b < 4; ++b) small += counts_h[q][b];
+        if (!slot.tuned && small >= LS_TUNE_MIN)
+          autotune<Real, VT>(sa, nsides, counts_h, slot, ticket, s);
+        cfg = slot;
+      }
+      st.config_kind_b1 = cfg.kind_b1;
+      st.config_blocks_per_sm = cfg.blocks_per_sm;
+      st.config_tuned = cfg.tuned;
+      persistent_launch<Real, VT>(sa, nsides, counts_h, cfg, ticket, nsing, s);
+      for (int q = 0; q < nsides; ++q) {
+        const SideIn& S = sides[q];
+        int pitch, chunk;
+        Real* tiles = big_tiles<Real>(counts_h[q], pitch, chunk, s);
+        launch_solves<Real, VT>(*S.Ahat, vals[q], S.Zrp, S.Zcol, cpts, lists[q], counts_h[q], S.nc,
+                                S.Zval, nsing, s, tiles, pitch, chunk, /*first_bucket=*/4);
+        dfree(tiles, s);
+      }
+    };
+    if (precision == CLAIR_MIXED) {
+      // values converted once per side instead of once per local system they appear in
+      float* vals32[2] = {nullptr, nullptr};
+      for (int q = 0; q < nsides; ++q) {
+        vals32[q] = dalloc<float>(std::max(sides[q].Ahat->nnz, 1), s);
+        to_float(sides[q].Ahat->val, vals32[q], sides[q].Ahat->nnz, s);
+      }
+      const float* v[2] = {vals32[0], vals32[1]};
+      run(float(0), v);
+      for (int q = 0; q < nsides; ++q) dfree(vals32[q], s);
+    } else {
+      const double* v[2] = {sides[0].Ahat->val, nsides > 1 ? sides[1].Ahat->val : nullptr};
+      run(double(0), v);
     }
   }
   unsigned long long h[5] = {0, 0, 0, 0, 0};
@@ -989,10 +1284,34 @@ void local_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* c
   st.sum_t2 += (double)h[2];
   st.sum_t += (double)h[3];
   st.gathered += (long long)h[4];
-  for (int b = 0; b < LS_BUCKETS; ++b) st.hist[b] += counts_h[b];
-  dfree(lists, s);
+  for (int q = 0; q < nsides; ++q)
+    for (int b = 0; b < LS_BUCKETS; ++b) st.hist[b] += counts_h[q][b];
+  for (int q = 0; q < nsides; ++q) dfree(lists[q], s);
   dfree(counts, s);
   dfree(nsing, s);
+  dfree(ticket, s);
+}
+
+void local_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* cpts, int nc,
+                  int precision, double* Zval, LocalStats& st, cudaStream_t s) {
+  SideIn side{&Ahat, Zrp, Zcol, Zval, nc};
+  local_solves_multi(&side, 1, cpts, precision, st, s);
+}
+
+// Sets (kind_b1 >= 0) or reads the execution configuration of the persistent local-solve
+// launch on the current device for one precision.
+void lsolve_config(int precision, int* kind_b1, int* blocks_per_sm, int* tuned, bool set) {
+  std::lock_guard<std::mutex> lock(g_cfg_mu);
+  LsolveConfig& slot = config_slot(precision);
+  if (set) {
+    slot.kind_b1 = *kind_b1;
+    slot.blocks_per_sm = *blocks_per_sm;
+    slot.tuned = *tuned;
+  } else {
+    *kind_b1 = slot.kind_b1;
+    *blocks_per_sm = slot.blocks_per_sm;
+    *tuned = slot.tuned;
+  }
 }
 
 // Projection of the transposed weights Wt (rows = fine points) onto the constraint; Bc is
@@ -1029,6 +1348,15 @@ void transfer_solve(const Csr& Ahat, const int* cpts, Csr& Z, int precision, Loc
                     cudaStream_t s) {
   if (!Z.val) Z.val = dalloc<double>(Z.nnz, s);
   local_solves(Ahat, Z.rowptr, Z.col, cpts, Z.rows, precision, Z.val, st, s);
+}
+
+// Both sides of a level in one go: R's pattern on A^T and P's (transposed) pattern on A.
+void transfer_solve_pair(const Csr& At, Csr& R, const Csr& A, Csr& Pt, const int* cpts,
+                         int precision, LocalStats& st, cudaStream_t s) {
+  if (!R.val) R.val = dalloc<double>(R.nnz, s);
+  if (!Pt.val) Pt.val = dalloc<double>(Pt.nnz, s);
+  SideIn sides[2] = {{&At, R.rowptr, R.col, R.val, R.rows}, {&A, Pt.rowptr, Pt.col, Pt.val, Pt.rows}};
+  local_solves_multi(sides, 2, cpts, precision, st, s);
 }
 
 void transfer_weights(const Csr& Ahat, const signed char* cf, const int* cpts, Csr& Z,

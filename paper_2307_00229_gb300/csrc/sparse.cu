@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <set>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -39,17 +41,15 @@ int sm_count() {
 
 int partial_blocks() { return 2 * sm_count(); }
 
-void once_per_device(int key, void (*set)()) {
+void once_per_device(const void* tag, void (*set)()) {
   static std::mutex mu;
-  static bool done[256][ONCE_KEYS] = {};
+  static std::set<std::pair<int, const void*>> done;
   int dev = 0;
   CLAIR_CUDA(cudaGetDevice(&dev));
-  CLAIR_REQUIRE(dev >= 0 && dev < 256 && key >= 0 && key < ONCE_KEYS, CLAIR_ERR_ARG,
-                "device ordinal %d out of range", dev);
   std::lock_guard<std::mutex> lock(mu);
-  if (done[dev][key]) return;
+  if (done.count({dev, tag})) return;
   set();
-  done[dev][key] = true;
+  done.insert({dev, tag});
 }
 
 cudaMemPool_t library_pool() {
@@ -1294,7 +1294,7 @@ void drop_zeros(Csr& C, cudaStream_t s) {
 // could not hold.
 static void spgemm_cta_path(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   const int rows = A.rows;
-  once_per_device(ONCE_SPGEMM_CTA, [] {
+  once_per_device((const void*)spgemm_cta<true>, [] {
     CLAIR_CUDA(cudaFuncSetAttribute(spgemm_cta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sgc_bytes(false)));
     CLAIR_CUDA(cudaFuncSetAttribute(spgemm_cta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1386,7 +1386,7 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
        spgemm_flat<true, SG_CAP2, SG_PRE2, 1>}};
   const size_t large_sym = sizeof(int) * SG_LARGE;
   const size_t large_num = (sizeof(int) + sizeof(double)) * SG_LARGE;
-  once_per_device(ONCE_SPGEMM_FLAT, [] {
+  once_per_device((const void*)spgemm_flat<true, SG_CAP0, SG_PRE0, SG_WARPS0>, [] {
     auto both = [](auto sym, auto num, size_t sym_bytes, size_t num_bytes) {
       CLAIR_CUDA(cudaFuncSetAttribute(sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sym_bytes));

@@ -270,6 +270,35 @@ def test_local_weights_every_bucket(cl, precision, eps, big):
     np.testing.assert_allclose(s[cols_hit], B[cols_hit], rtol=1e-12)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("kind_b1,blocks", [(1, 0), (2, 0), (1, 2)])
+def test_local_weights_every_route_of_the_persistent_launch(cl, precision, kind_b1, blocks):
+    """Every configuration the autotuner may pick (systems with 8 < T <= 16 on 16-lane
+    groups or on single warps; all resident blocks or two per SM) gives the oracle's
+    weights on every bucket edge up to T = 128."""
+    import torch
+    keep = cl.clair_lsolve_config(precision)
+    try:
+        cl.clair_lsolve_config(precision, kind_b1, blocks, 2)
+        A, cf, cpts, Wpat, B = crafted_case(eps=1.0)
+        n = A.shape[0]
+        W = O.clair_algorithm1(A, cf, B, Wpat, O.Params()).tocsc()
+        zrp, zcol = pattern_rows_with_identity(Wpat, cpts)
+        zval = torch.zeros(zcol.size, dtype=torch.float64, device="cuda")
+        st, sing, empty = cl.clair_local_weights(
+            dev(A.indptr, torch.int32), dev(A.indices, torch.int32), dev(A.data, torch.float64),
+            dev(cf, torch.int8), cpts.size, dev(zrp, torch.int32), dev(zcol, torch.int32),
+            dev(B, torch.float64), precision, zval)
+        assert st == 0 and sing == 0
+        got = sp.csr_matrix((zval.cpu().numpy(), zcol, zrp), shape=(cpts.size, n))
+        ident = sp.csr_matrix((np.ones(cpts.size), (np.arange(cpts.size), cpts)), shape=got.shape)
+        ref = (W.T + ident).tocsr()
+        ref.sort_indices()
+        assert rowwise_err(got, ref) <= (FP64_TOL if precision == 0 else FP32_TOL)
+    finally:
+        cl.clair_lsolve_config(precision, keep["kind_b1"] or 1, keep["blocks_per_sm"], keep["tuned"])
+
+
 def test_local_weights_singular_block_reports_status(cl):
     import torch
     A, cf, cpts, Wpat, B = crafted_case(nside=12)
