@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 steps (0: skip that arm)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-errors", action="store_true",
+                    help="skip the MIXED-vs-FP64 result comparison (profiling runs)")
     ap.add_argument("--cpu-nside", type=int, default=192)
     ap.add_argument("--workload", choices=["advdiff1024", "batch64", "adjoint512", "recirc3d"],
                     default="advdiff1024",
@@ -345,11 +347,13 @@ def run_clair(args):
                 if m_ > 0:
                     worst = max(worst, float(np.abs(a[lo:hi] - ref[lo:hi]).max() / m_))
         return worst
-    rm, r64 = results(cl.CLAIR_MIXED), results(cl.CLAIR_FP64)
-    errors = {"R_rowwise_max_rel": rowwise(rm["R_val"], r64["R_val"], r64["R_rowptr"]),
-              "P_rowwise_max_rel": rowwise(rm["P_val"], r64["P_val"], r64["P_rowptr"]),
-              "u_rel": float(np.linalg.norm(rm["u"] - r64["u"]) / np.linalg.norm(r64["u"])),
-              "against": "the FP64 GPU path of the same workload (level 0 weights, solution)"}
+    errors = None
+    if not args.no_errors:
+        rm, r64 = results(cl.CLAIR_MIXED), results(cl.CLAIR_FP64)
+        errors = {"R_rowwise_max_rel": rowwise(rm["R_val"], r64["R_val"], r64["R_rowptr"]),
+                  "P_rowwise_max_rel": rowwise(rm["P_val"], r64["P_val"], r64["P_rowptr"]),
+                  "u_rel": float(np.linalg.norm(rm["u"] - r64["u"]) / np.linalg.norm(r64["u"])),
+                  "against": "the FP64 GPU path of the same workload (level 0 weights, solution)"}
 
     st = mixed["stats"]
     rows = int(st.r_rows)
@@ -416,6 +420,8 @@ def run_clair(args):
         "roofline": dominant, "roofline_other": other, "roofline_phases": roofline_phases,
         "error_vs_fp64": errors,
         "gpu_launches": mixed["launches"],
+        "tuning": {"lsolve_kind_b1": st.lsolve_kind_b1, "lsolve_blocks_per_sm": st.lsolve_blocks_per_sm,
+                   "lsolve_tuned": st.lsolve_tuned, "cycle_short_lanes": st.cycle_short_lanes},
         "clocks": clocks,
         "step_times_ms": mixed["times"], "wall_s": mixed["wall"],
     }

@@ -114,6 +114,14 @@ typedef struct {
   int lsolve_kind_b1;         /* configuration of the last persistent local-solve launch */
   int lsolve_blocks_per_sm;   /* (see clair_lsolve_config) */
   int lsolve_tuned;
+  int cycle_short_lanes;      /* FP32 cycle row kernels: 1 = about four entries per lane (one
+                                 thread per row up to 8 entries), 0 = lanes up to the mean
+                                 row length; both are timed on the first MIXED hierarchy of
+                                 the process on each device and the faster kept) */
+  int cycle64_from;           /* CLAIR_MIXED: first level whose part of the cycle runs in FP64
+                                 (its largest |R| or |P| weight, or a finer level's, is above
+                                 1e3: FP32 copies of such weights lose their sums to
+                                 cancellation), -1 if every level runs in FP32 */
 } clair_stats_t;
 
 /* Kernel launches issued by this library in this process so far (monotonic counter). */

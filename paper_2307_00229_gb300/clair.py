@@ -89,6 +89,8 @@ class clair_stats_t(ctypes.Structure):
         ("lsolve_kind_b1", ctypes.c_int),
         ("lsolve_blocks_per_sm", ctypes.c_int),
         ("lsolve_tuned", ctypes.c_int),
+        ("cycle_short_lanes", ctypes.c_int),
+        ("cycle64_from", ctypes.c_int),
     ]
 
 

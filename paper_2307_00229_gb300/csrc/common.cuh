@@ -211,10 +211,19 @@ void scatter_vals(const double* x, const int* perm, double* y, int n, cudaStream
 void validate_csr(const int* rowptr, const int* col, int rows, int cols, int nnz, const char* what,
                   cudaStream_t s);
 void validate_cf(const signed char* cf, int n, cudaStream_t s);
+// *out = max(*out, max |x|) as the bits of a non-negative double (asynchronous).
+void absmax_into(const double* x, long long n, unsigned long long* out, cudaStream_t s);
 // Nonfinite check over a buffer; returns true if all finite (synchronises).
 bool all_finite(const double* x, long long n, cudaStream_t s);
 
 int partial_blocks();  // number of blocks used by the deterministic reductions
+
+// Lanes per row of the FP32 row kernels (SpMV, residual, Jacobi sweeps): 0 = the power of
+// two at or above the mean row length; 1 = about four entries per lane (one thread per
+// row up to 8 entries), the FP64 rule.  A per-thread setting, chosen per hierarchy by
+// timing its cycle graph.
+int cycle_short_lanes();
+void set_cycle_short_lanes(int lanes);
 
 // ------------------------------------------------------------------------------------
 // Segmented Krylov building blocks (krylov.cu): independent Krylov processes in lockstep,
@@ -275,6 +284,7 @@ struct LocalStats {
 
 // Kernel launches issued by this library (monotonic, process-wide).
 void count_launch();
+void count_launches(long long delta);  // graph replays (+), captures that issued nothing (-)
 long long launch_count();
 
 // Device time per phase, measured with CUDA events on the launching stream.  Phases are

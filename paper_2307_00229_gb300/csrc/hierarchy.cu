@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -82,6 +83,10 @@ struct Level {
   std::vector<char> frozen;
   double *wpre64 = nullptr, *wpost64 = nullptr;
   float *wpre32 = nullptr, *wpost32 = nullptr;
+  // MIXED: this level's part of the cycle runs in FP64 (its transfer weights, or those of
+  // a finer level, exceed what FP32 carries; see kCycle64Weight)
+  bool cycle64 = false;
+  double max_weight = 0.0;
   // cycle work vectors
   double *b64 = nullptr, *x64 = nullptr, *y64 = nullptr, *r64 = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *y32 = nullptr, *r32 = nullptr;
@@ -128,6 +133,8 @@ struct clair_hierarchy {
   int* coarse_off = nullptr;                // coarsest diagonal blocks (device offsets)
   long long* coarse_ioff = nullptr;         // and their inverses' offsets in Inv
   int coarse_nblk = 1;
+  int short_lanes = 0;                      // FP32 short-row lanes chosen for the cycle
+  int cycle_lanes_pick = 0;
   bool cycle_fp64 = false;                  // MIXED solve fell back to the FP64 cycle
   int fp64_from = -1;                       // iteration of that fallback (-1: none)
   int kmodes = 1;                           // mode vectors (columns of B)
@@ -136,6 +143,10 @@ struct clair_hierarchy {
 };
 
 namespace clair {
+
+// Largest transfer weight an FP32 cycle level takes (FP32 keeps about 7 digits: weights of
+// this size that cancel to O(1) leave about 4).
+constexpr double kCycle64Weight = 1e3;
 
 static void to_float_copy(const double* x, float** y, long long n, cudaStream_t s) {
   *y = dalloc<float>(n, s);
@@ -668,6 +679,34 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
   h->Inv = dalloc<double>(std::max<long long>(inv_size, 1), s);
   dense_inverse(last.A, blocks, h->Inv, &h->coarse_off, &h->coarse_ioff, s);
   to_float_copy(h->Inv, &h->Inv32, std::max<long long>(inv_size, 1), s);
+  // MIXED: the smoothed mode vectors of nearly pure advection shrink by orders of
+  // magnitude per level, and the projected weights grow in proportion (1e13 seen); an FP32
+  // copy of such R and P loses everything to cancellation.  From the first level whose
+  // largest |R| or |P| weight exceeds kCycle64Weight on, the cycle runs in FP64.
+  {
+    const int nl = (int)h->lv.size();
+    unsigned long long* wmax = dalloc<unsigned long long>(nl, s);
+    CLAIR_CUDA(cudaMemsetAsync(wmax, 0, sizeof(unsigned long long) * nl, s));
+    for (int k = 0; k < nl; ++k) {
+      Level& L = h->lv[k];
+      if (!L.nc) continue;
+      absmax_into(L.R.val, L.R.nnz, wmax + k, s);
+      absmax_into(L.P.val, L.P.nnz, wmax + k, s);
+    }
+    std::vector<unsigned long long> hw(nl);
+    CLAIR_CUDA(cudaMemcpyAsync(hw.data(), wmax, sizeof(unsigned long long) * nl,
+                               cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    dfree(wmax, s);
+    bool on = false;
+    for (int k = 0; k < nl; ++k) {
+      double w;
+      memcpy(&w, &hw[k], sizeof(w));
+      h->lv[k].max_weight = w;
+      on = on || (p.precision == CLAIR_MIXED && w > kCycle64Weight);
+      h->lv[k].cycle64 = on;
+    }
+  }
   for (auto& L : h->lv) {
     to_float_copy(L.A.val, &L.A.val32, L.A.nnz, s);
     to_float_copy(L.dinv, &L.dinv32, L.n, s);
@@ -736,9 +775,10 @@ void residual_t<float>(const Csr& A, const float* b, const float* x, float* r, c
   residual32(A, b, x, r, s);
 }
 
-// Cycle on level k: input in Vec<T>::b(L_k), output in Vec<T>::x(L_k).
+// Cycle on level k: input in Vec<T>::b(L_k); returns where the output is (Vec<T>::x or
+// Vec<T>::y of L_k: the last post-smoothing sweep writes the other buffer, no copy back).
 template <class T>
-static void vcycle_level(clair_hierarchy* h, int k) {
+static T* vcycle_level(clair_hierarchy* h, int k) {
   cudaStream_t s = h->stream;
   Level& L = h->lv[k];
   T* b = Vec<T>::b(L);
@@ -751,7 +791,7 @@ static void vcycle_level(clair_hierarchy* h, int k) {
     else
       Inv = reinterpret_cast<const T*>(h->Inv32);
     coarse_apply<T>(Inv, h->coarse_off, h->coarse_ioff, h->coarse_nblk, L.n, b, x, s);
-    return;
+    return x;
   }
   const T* av = Vec<T>::aval(L.A);
   // a batch folds each instance's weight into D^-1 (0 for frozen instances)
@@ -769,45 +809,63 @@ static void vcycle_level(clair_hierarchy* h, int k) {
   residual_t<T>(L.A, b, x, r, s);
   Level& C = h->lv[k + 1];
   spmv_t<T>(L.R, r, Vec<T>::b(C), T(1), T(0), s);
-  vcycle_level<T>(h, k + 1);
-  spmv_t<T>(L.P, Vec<T>::x(C), x, T(1), T(1), s);
+  const T* xc = nullptr;
+  if constexpr (sizeof(T) == 4) {
+    if (C.cycle64) {  // the coarser levels run in FP64 (MIXED with large weights there)
+      to_double(C.b32, C.b64, C.n, s);
+      const double* xc64 = vcycle_level<double>(h, k + 1);
+      to_float(xc64, C.x32, C.n, s);
+      xc = C.x32;
+    }
+  }
+  if (!xc) xc = vcycle_level<T>(h, k + 1);
+  spmv_t<T>(L.P, xc, x, T(1), T(1), s);
   // FFC post-smoothing
   jacobi<T>(L.A, av, dvpost, L.cf, 0, wpost, b, x, y, s);
   jacobi<T>(L.A, av, dvpost, L.cf, 0, wpost, b, y, x, s);
   jacobi<T>(L.A, av, dvpost, L.cf, 1, wpost, b, x, y, s);
-  CLAIR_CUDA(cudaMemcpyAsync(x, y, sizeof(T) * L.n, cudaMemcpyDeviceToDevice, s));
+  return y;
 }
 
 // z = M^-1 v on level k (float64 in and out), launching every kernel.
 static void apply_precond_direct(clair_hierarchy* h, int k, const double* v, double* z) {
   cudaStream_t s = h->stream;
   Level& L = h->lv[k];
-  if (h->p.precision == CLAIR_MIXED && !h->cycle_fp64) {
+  struct LanesScope {  // the hierarchy's row-kernel lane rule for these launches
+    int keep;
+    explicit LanesScope(int w) : keep(cycle_short_lanes()) { set_cycle_short_lanes(w); }
+    ~LanesScope() { set_cycle_short_lanes(keep); }
+  } lanes(h->short_lanes);
+  if (h->p.precision == CLAIR_MIXED && !h->cycle_fp64 && !L.cycle64) {
     to_float(v, L.b32, L.n, s);
-    vcycle_level<float>(h, k);
-    to_double(L.x32, z, L.n, s);
+    const float* out = vcycle_level<float>(h, k);
+    to_double(out, z, L.n, s);
   } else {
     CLAIR_CUDA(cudaMemcpyAsync(L.b64, v, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
-    vcycle_level<double>(h, k);
-    CLAIR_CUDA(cudaMemcpyAsync(z, L.x64, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
+    const double* out = vcycle_level<double>(h, k);
+    CLAIR_CUDA(cudaMemcpyAsync(z, out, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
   }
 }
 
 // The fine-level cycle is a fixed sequence of about ten kernels per level; it is captured
 // once into a CUDA graph with fixed input / output buffers (h->vin, h->zout) and replayed,
-// so each FGMRES iteration pays one graph launch instead of every kernel launch.
-static void build_cycle_graph(clair_hierarchy* h) {
+// so each FGMRES iteration pays one graph launch instead of every kernel launch.  In
+// MIXED precision the cycle is captured with both lane rules for short FP32 rows (lanes
+// up to the mean row length, or one thread per row), the replays of each are timed, and
+// the faster graph is kept.
+static cudaGraphExec_t capture_cycle(clair_hierarchy* h, long long* kernels) {
   cudaStream_t cs;
   CLAIR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaStream_t keep = h->stream;
   h->stream = cs;
   const long long before = launch_count();
   cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
   try {
     CLAIR_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     apply_precond_direct(h, 0, h->vin, h->zout);
     CLAIR_CUDA(cudaStreamEndCapture(cs, &g));
-    CLAIR_CUDA(cudaGraphInstantiate(&h->cycle_exec, g, 0));
+    CLAIR_CUDA(cudaGraphInstantiate(&exec, g, 0));
   } catch (...) {
     cudaGraph_t dummy;
     cudaStreamEndCapture(cs, &dummy);
@@ -816,10 +874,94 @@ static void build_cycle_graph(clair_hierarchy* h) {
     cudaStreamDestroy(cs);
     throw;
   }
-  h->cycle_kernels = launch_count() - before;
+  *kernels = launch_count() - before;
+  count_launches(-*kernels);  // captured, not launched
   cudaGraphDestroy(g);
   h->stream = keep;
   cudaStreamDestroy(cs);
+  return exec;
+}
+
+static float time_graph(cudaGraphExec_t exec, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  CLAIR_CUDA(cudaEventCreate(&e0));
+  CLAIR_CUDA(cudaEventCreate(&e1));
+  CLAIR_CUDA(cudaGraphLaunch(exec, s));  // warm
+  CLAIR_CUDA(cudaEventRecord(e0, s));
+  for (int i = 0; i < 3; ++i) CLAIR_CUDA(cudaGraphLaunch(exec, s));
+  CLAIR_CUDA(cudaEventRecord(e1, s));
+  CLAIR_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CLAIR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
+}
+
+// The lane rule chosen by the first timed MIXED cycle on each device (-1: not yet timed).
+static std::mutex g_lanes_mu;
+static int g_lanes_pick[256] = {-1};
+static bool g_lanes_init = false;
+
+static int* lanes_slot() {
+  int dev = 0;
+  CLAIR_CUDA(cudaGetDevice(&dev));
+  CLAIR_REQUIRE(dev >= 0 && dev < 256, CLAIR_ERR_ARG, "device ordinal %d out of range", dev);
+  if (!g_lanes_init) {
+    for (int& v : g_lanes_pick) v = -1;
+    g_lanes_init = true;
+  }
+  return &g_lanes_pick[dev];
+}
+
+static void build_cycle_graph(clair_hierarchy* h) {
+  if (h->p.precision != CLAIR_MIXED) {
+    h->short_lanes = 0;
+    h->cycle_exec = capture_cycle(h, &h->cycle_kernels);
+    h->cycle_lanes_pick = 0;
+    return;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_lanes_mu);
+    const int known = *lanes_slot();
+    if (known >= 0) {  // timed once per device: capture the chosen rule only
+      h->short_lanes = h->cycle_lanes_pick = known;
+      h->cycle_exec = capture_cycle(h, &h->cycle_kernels);
+      return;
+    }
+  }
+  CLAIR_CUDA(cudaMemsetAsync(h->vin, 0, sizeof(double) * h->lv[0].n, h->stream));
+  cudaGraphExec_t best = nullptr;
+  long long best_k = 0;
+  float best_ms = 0.f;
+  for (int lanes = 0; lanes <= 1; ++lanes) {
+    h->short_lanes = lanes;
+    long long kk = 0;
+    cudaGraphExec_t e = capture_cycle(h, &kk);
+    float ms = 0.f;
+    try {
+      ms = time_graph(e, h->stream);
+      count_launches(4 * kk);
+    } catch (...) {
+      cudaGraphExecDestroy(e);
+      if (best) cudaGraphExecDestroy(best);
+      throw;
+    }
+    if (!best || ms < best_ms) {
+      if (best) cudaGraphExecDestroy(best);
+      best = e;
+      best_k = kk;
+      best_ms = ms;
+      h->cycle_lanes_pick = lanes;
+    } else {
+      cudaGraphExecDestroy(e);
+    }
+  }
+  h->short_lanes = h->cycle_lanes_pick;
+  h->cycle_exec = best;
+  h->cycle_kernels = best_k;
+  std::lock_guard<std::mutex> lock(g_lanes_mu);
+  *lanes_slot() = h->cycle_lanes_pick;
 }
 
 // z = M^-1 v on level k; the fine level replays the captured cycle.
@@ -1422,6 +1564,13 @@ clair_status clair_stats(clair_h h, clair_stats_t* o) {
   o->lsolve_kind_b1 = h->st.config_kind_b1;
   o->lsolve_blocks_per_sm = h->st.config_blocks_per_sm;
   o->lsolve_tuned = h->st.config_tuned;
+  o->cycle_short_lanes = h->short_lanes;
+  o->cycle64_from = -1;
+  for (size_t k = 0; k < h->lv.size(); ++k)
+    if (h->lv[k].cycle64) {
+      o->cycle64_from = (int)k;
+      break;
+    }
   CLAIR_API_END
 }
 

@@ -26,25 +26,47 @@ namespace clair {
 // (row-relative, thr = row maxima of M); mode 1: iff |m_rc| >= theta * thr[c]
 // (column-relative: thr = row maxima of M^T).  Diagonal and zero entries are never strong.
 // ------------------------------------------------------------------------------------
+// W lanes per row (entries e0 + lane, e0 + lane + W, ...): short rows one per thread,
+// the long rows of coarse levels spread over lanes instead of one thread's serial loop.
+template <int W>
 __global__ void strength_mask(const int* __restrict__ rowptr, const int* __restrict__ col,
                               const double* __restrict__ val, int rows,
                               const double* __restrict__ thr, double theta, int mode,
                               unsigned char* __restrict__ mask) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int r = (int)(t / W), lane = (int)(t % W);
   if (r >= rows) return;
-  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+  const double tr = mode == 0 ? theta * thr[r] : 0.0;
+  for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += W) {
     const int c = col[e];
     const double a = fabs(val[e]);
-    const double t = theta * (mode == 0 ? thr[r] : thr[c]);
-    mask[e] = (c != r && a > 0.0 && a >= t) ? 1 : 0;
+    const double th = mode == 0 ? tr : theta * thr[c];
+    mask[e] = (c != r && a > 0.0 && a >= th) ? 1 : 0;
   }
 }
 
 void strength(const Csr& M, const double* thr, double theta, int mode, unsigned char* mask,
               cudaStream_t s) {
   if (!M.rows) return;
-  strength_mask<<<ceil_div(M.rows, 256), 256, 0, s>>>(M.rowptr, M.col, M.val, M.rows, thr, theta,
-                                                      mode, mask); ::clair::count_launch();
+  const double avg = (double)M.nnz / M.rows;
+  int W = 1;
+  while (W < 32 && 4 * W < avg) W <<= 1;
+  const int blocks = ceil_div((long long)M.rows * W, 256);
+  switch (W) {
+#define CLAIR_SM_CASE(WW)                                                                        \
+  case WW:                                                                                       \
+    strength_mask<WW><<<blocks, 256, 0, s>>>(M.rowptr, M.col, M.val, M.rows, thr, theta, mode, \
+                                             mask);                                              \
+    break;
+    CLAIR_SM_CASE(1)
+    CLAIR_SM_CASE(2)
+    CLAIR_SM_CASE(4)
+    CLAIR_SM_CASE(8)
+    CLAIR_SM_CASE(16)
+    CLAIR_SM_CASE(32)
+#undef CLAIR_SM_CASE
+  }
+  ::clair::count_launch();
   CLAIR_LAUNCHED();
 }
 
@@ -656,7 +678,7 @@ __global__ void jacobi_first(const T* __restrict__ dinv, int rows, const signed 
 // length.
 static int lanes_of(const Csr& A, bool fp64) {
   double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
-  if (fp64) {
+  if (fp64 || cycle_short_lanes() == 1) {
     if (avg <= 8.0) return 1;
     int w = 2;
     while (w < 32 && 4 * w < avg) w <<= 1;

@@ -75,6 +75,7 @@ cudaMemPool_t library_pool() {
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long delta) { g_launches.fetch_add(delta, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(); }
 
 static thread_local PhaseClock* g_clock = nullptr;
@@ -398,9 +399,13 @@ void csr_transpose(const Csr& A, Csr& At, int** perm_out, cudaStream_t s) {
 // with 1 or 32 active lanes, so short rows run one per thread; long rows (coarse levels)
 // would then be one thread's chain of dependent index and value loads, so they get lanes
 // at about four entries per lane.
+static thread_local int g_short_lanes = 0;
+int cycle_short_lanes() { return g_short_lanes; }
+void set_cycle_short_lanes(int lanes) { g_short_lanes = lanes; }
+
 static int lanes_for(const Csr& A, bool fp64) {
   double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
-  if (fp64) {
+  if (fp64 || g_short_lanes == 1) {
     if (avg <= 8.0) return 1;
     int w = 2;
     while (w < 32 && 4 * w < avg) w <<= 1;
@@ -612,6 +617,24 @@ __global__ void finite_kernel(const double* __restrict__ x, long long n, int* ba
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     if (!isfinite(x[i])) *bad = 1;
+}
+
+// max |x| (non-negative doubles order as their bit patterns)
+__global__ void absmax_kernel(const double* __restrict__ x, long long n,
+                              unsigned long long* __restrict__ out) {
+  double m = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+void absmax_into(const double* x, long long n, unsigned long long* out, cudaStream_t s) {
+  if (n <= 0) return;
+  absmax_kernel<<<grid_for(n), 256, 0, s>>>(x, n, out); ::clair::count_launch();
+  CLAIR_LAUNCHED();
 }
 
 bool all_finite(const double* x, long long n, cudaStream_t s) {
