@@ -408,6 +408,9 @@ def run_clair(args):
         "operator_complexity": st.operator_complexity,
         "setup_rows_per_s": rows / (st.setup_ms / 1e3),
         "phases_ms": phases,
+        "levels_ms": [{"n": L["n"], "span": round(st.level_span_ms[k], 3),
+                       **{name: round(st.level_phase_ms[k][i], 3) for i, name in enumerate(cl.PHASES[:8])}}
+                      for k, L in enumerate(mixed["levels"])],
         "fp64": None if fp64 is None else {
             "ms_per_step": fp64["ms"], "iterations": fp64["its"][-1], "relres": fp64["rel"][-1],
             "setup_ms": fp64["stats"].setup_ms, "value": job_rows_per_s(rows, world, fp64["ms"]),
@@ -420,7 +423,8 @@ def run_clair(args):
         "roofline": dominant, "roofline_other": other, "roofline_phases": roofline_phases,
         "error_vs_fp64": errors,
         "gpu_launches": mixed["launches"],
-        "tuning": {"lsolve_kind_b1": st.lsolve_kind_b1, "lsolve_blocks_per_sm": st.lsolve_blocks_per_sm,
+        "tuning": {"lsolve_kind_b1": st.lsolve_kind_b1, "lsolve_kind_b3": st.lsolve_kind_b3,
+                   "lsolve_blocks_per_sm": st.lsolve_blocks_per_sm,
                    "lsolve_tuned": st.lsolve_tuned, "cycle_short_lanes": st.cycle_short_lanes},
         "clocks": clocks,
         "step_times_ms": mixed["times"], "wall_s": mixed["wall"],

@@ -112,6 +112,7 @@ typedef struct {
                                  produced a nonfinite estimate), -1 if it never did */
   int k;                      /* mode vectors (columns of B, B_P and B_R) */
   int lsolve_kind_b1;         /* configuration of the last persistent local-solve launch */
+  int lsolve_kind_b3;
   int lsolve_blocks_per_sm;   /* (see clair_lsolve_config) */
   int lsolve_tuned;
   int cycle_short_lanes;      /* FP32 cycle row kernels: 1 = about four entries per lane (one
@@ -122,6 +123,8 @@ typedef struct {
                                  (its largest |R| or |P| weight, or a finer level's, is above
                                  1e3: FP32 copies of such weights lose their sums to
                                  cancellation), -1 if every level runs in FP32 */
+  double level_span_ms[32];   /* setup: main-stream time from the start of level k to the next */
+  double level_phase_ms[32][8]; /* setup: device time of phases 0-7 (see phase_ms) per level */
 } clair_stats_t;
 
 /* Kernel launches issued by this library in this process so far (monotonic counter). */
@@ -135,13 +138,14 @@ int clair_compiled_arch(void);
  * the batched local solves are mapped onto the GPU) for one precision on the current
  * device.  Systems of up to 64 unknowns of both sides of a level run in one persistent
  * launch; those with 8 < T <= 16 go to 16-lane groups (kind_b1 = 1) or to one warp each
- * (kind_b1 = 2), and blocks_per_sm caps the resident blocks (0 = as many as fit).  The
- * first setup with a large enough level times the candidates and keeps the fastest
- * (tuned = 1).  set = 1 installs the given values (tuned is stored as given; 2 marks a
- * caller's choice, which the library then keeps); set = 0 reads them.
+ * (kind_b1 = 2); those with 32 < T <= 64 to a pair of warps (kind_b3 = 3) or to one warp
+ * with two rows per lane (kind_b3 = 4); blocks_per_sm caps the resident blocks (0 = as
+ * many as fit).  The first setup with a large enough level times the candidates and keeps
+ * the fastest (tuned = 1).  set = 1 installs the given values (tuned is stored as given; 2
+ * marks a caller's choice, which the library then keeps); set = 0 reads them.
  * CLAIR_ERR_ARG for other kinds or a negative block count. */
-clair_status clair_lsolve_config(int precision, int set, int* kind_b1, int* blocks_per_sm,
-                                 int* tuned);
+clair_status clair_lsolve_config(int precision, int set, int* kind_b1, int* kind_b3,
+                                 int* blocks_per_sm, int* tuned);
 
 /* Fills *p with the defaults listed above. */
 clair_status clair_params_default(clair_params* p);
@@ -359,6 +363,22 @@ clair_status clair_advdiff2d_param_grad(int nside, double h, const double* eps, 
                                         const double* vy, const int* rowptr, const int* col,
                                         int nnz, const double* dA, double* deps, double* dvx,
                                         double* dvy, void* stream);
+
+/* Sparse product C = A B (the building block of the Galerkin step A_c = (R A) P, Section
+ * 1): deterministic sums (each output entry adds its products in A's row order, in
+ * float64, with separate multiply and add), columns of each output row sorted, exact
+ * zeros kept.  Rows are routed by their distinct-column count through shared-memory hash
+ * tables of growing size and, beyond 16384 columns, a dense accumulator in global memory.
+ *   m, kdim, ncols : A is m x kdim, B is kdim x ncols (device CSR, see conventions)
+ *   rowptr_out     : device int [m + 1], written: C's row pointers
+ *   nnz_out        : host, written: nnz(C)
+ *   col_out, val_out : device buffers of at least *cap entries (cap: host, in), or NULL
+ *                    to query the size only; CLAIR_ERR_CAPACITY if nnz(C) > cap
+ * Synchronises `stream`. */
+clair_status clair_spgemm(int m, int kdim, int ncols, const int* A_rowptr, const int* A_col,
+                          const double* A_val, const int* B_rowptr, const int* B_col,
+                          const double* B_val, void* stream, int* rowptr_out, int64_t* nnz_out,
+                          int64_t cap, int* col_out, double* val_out);
 
 /* One-line description of the last error on the calling thread ("" if none). */
 const char* clair_last_error(void);

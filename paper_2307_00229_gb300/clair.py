@@ -87,10 +87,13 @@ class clair_stats_t(ctypes.Structure):
         ("fp64_cycle_from", ctypes.c_int64),
         ("k", ctypes.c_int),
         ("lsolve_kind_b1", ctypes.c_int),
+        ("lsolve_kind_b3", ctypes.c_int),
         ("lsolve_blocks_per_sm", ctypes.c_int),
         ("lsolve_tuned", ctypes.c_int),
         ("cycle_short_lanes", ctypes.c_int),
         ("cycle64_from", ctypes.c_int),
+        ("level_span_ms", ctypes.c_double * 32),
+        ("level_phase_ms", (ctypes.c_double * 8) * 32),
     ]
 
 
@@ -131,7 +134,8 @@ _SIGNATURES = {
     "clair_last_error": (ctypes.c_char_p, []),
     "clair_kernel_launches": (ctypes.c_int64, []),
     "clair_compiled_arch": (ctypes.c_int, []),
-    "clair_lsolve_config": (_I, [_I, _I, _PI, _PI, _PI]),
+    "clair_spgemm": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _PI64, ctypes.c_int64, _P, _P]),
+    "clair_lsolve_config": (_I, [_I, _I, _PI, _PI, _PI, _PI]),
 }
 
 
@@ -186,14 +190,30 @@ def clair_compiled_arch() -> int:
     return int(load().clair_compiled_arch())
 
 
-def clair_lsolve_config(precision: int, kind_b1: int | None = None, blocks_per_sm: int = 0,
-                        tuned: int = 2) -> dict:
+def clair_lsolve_config(precision: int, kind_b1: int | None = None, kind_b3: int = 3,
+                        blocks_per_sm: int = 0, tuned: int = 2) -> dict:
     """Reads, or with ``kind_b1`` set installs, the persistent local-solve configuration
     of the current device for one precision."""
-    k, b, t = ctypes.c_int(kind_b1 or 0), ctypes.c_int(blocks_per_sm), ctypes.c_int(tuned)
+    k, k3 = ctypes.c_int(kind_b1 or 0), ctypes.c_int(kind_b3)
+    b, t = ctypes.c_int(blocks_per_sm), ctypes.c_int(tuned)
     _check(load().clair_lsolve_config(precision, 0 if kind_b1 is None else 1, ctypes.byref(k),
-                                      ctypes.byref(b), ctypes.byref(t)))
-    return {"kind_b1": k.value, "blocks_per_sm": b.value, "tuned": t.value}
+                                      ctypes.byref(k3), ctypes.byref(b), ctypes.byref(t)))
+    return {"kind_b1": k.value, "kind_b3": k3.value, "blocks_per_sm": b.value, "tuned": t.value}
+
+
+def clair_spgemm(A_rowptr, A_col, A_val, B_rowptr, B_col, B_val, ncols: int, stream=None):
+    """C = A B on the device; returns (rowptr, col, val) torch tensors."""
+    m, kdim = A_rowptr.numel() - 1, B_rowptr.numel() - 1
+    rp = torch.empty(m + 1, dtype=torch.int32, device=A_rowptr.device)
+    nnz = ctypes.c_int64()
+    args = [m, kdim, ncols, _dptr(A_rowptr, torch.int32), _dptr(A_col, torch.int32),
+            _dptr(A_val, torch.float64), _dptr(B_rowptr, torch.int32), _dptr(B_col, torch.int32),
+            _dptr(B_val, torch.float64), _stream(stream), _dptr(rp, torch.int32), ctypes.byref(nnz)]
+    _check(load().clair_spgemm(*args, 0, None, None))
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=A_rowptr.device)
+    val = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=A_rowptr.device)
+    _check(load().clair_spgemm(*args, nnz.value, _dptr(col, torch.int32), _dptr(val, torch.float64)))
+    return rp, col[:nnz.value], val[:nnz.value]
 
 
 def clair_params_default() -> clair_params:

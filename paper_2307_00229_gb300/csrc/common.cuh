@@ -279,7 +279,7 @@ struct LocalStats {
   double sum_t3 = 0, sum_t2 = 0, sum_t = 0;
   long long gathered = 0;
   // execution configuration of the last persistent local-solve launch
-  int config_kind_b1 = -1, config_blocks_per_sm = 0, config_tuned = 0;
+  int config_kind_b1 = -1, config_kind_b3 = -1, config_blocks_per_sm = 0, config_tuned = 0;
 };
 
 // Kernel launches issued by this library (monotonic, process-wide).
@@ -307,16 +307,19 @@ class PhaseClock {
  public:
   int begin(int ph, cudaStream_t s);    // returns the mark to close
   void end(int mark, cudaStream_t s);
-  void collect(double* ms_out);  // synchronises; adds elapsed ms per phase; clears
+  // synchronises; adds elapsed ms per phase (and, with level_ms, per level and phase:
+  // level_ms[level * PH_COUNT + phase] for levels below max_levels); clears
+  void collect(double* ms_out, double* level_ms = nullptr, int max_levels = 0);
+  void set_level(int level) { level_ = level; }
   ~PhaseClock();
 
  private:
   struct Mark {
-    int ph;
+    int ph, level;
     cudaEvent_t a, b;
   };
   Mark* marks_ = nullptr;
-  int n_ = 0, cap_ = 0;
+  int n_ = 0, cap_ = 0, level_ = 0;
 };
 PhaseClock* active_clock();
 void set_active_clock(PhaseClock* c);

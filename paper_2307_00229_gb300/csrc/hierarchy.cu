@@ -35,7 +35,8 @@ void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const doub
                       LocalStats& st, Csr* keep_t, cudaStream_t s);
 void transfer_solve_pair(const Csr& At, Csr& R, const Csr& A, Csr& Pt, const int* cpts,
                          int precision, LocalStats& st, cudaStream_t s);
-void lsolve_config(int precision, int* kind_b1, int* blocks_per_sm, int* tuned, bool set);
+void lsolve_config(int precision, int* kind_b1, int* kind_b3, int* blocks_per_sm, int* tuned,
+                   bool set);
 void transfer_diag(const Csr& Ahat, const signed char* cf, const int* cpts, Csr& Z,
                    const double* B, int k, int iterations, LocalStats& st, Csr* keep_t,
                    cudaStream_t s);
@@ -123,6 +124,8 @@ struct clair_hierarchy {
   clair::LocalStats st;
   double setup_ms = 0.0;
   double phase_ms[clair::PH_COUNT] = {};   // setup, per phase
+  double level_phase_ms[32 * clair::PH_COUNT] = {};  // setup, per level and phase
+  double level_span_ms[32] = {};           // setup: main-stream time from level to level
   double solve_ms[clair::PH_COUNT] = {};   // last solve, per phase
   cudaGraphExec_t cycle_exec = nullptr;     // captured fine-level V(1,1) cycle
   long long cycle_kernels = 0;              // kernels in that graph
@@ -436,9 +439,24 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
   SideStream ss;
   // one weight per level (per level and instance for a batch), on the device
   double* omega_dev = dalloc<double>((size_t)p.max_levels * ninst, s);
+  // main-stream marks at every level start (level spans for clair_stats)
+  struct Marks {
+    std::vector<cudaEvent_t> v;
+    ~Marks() {
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+    void record(cudaStream_t st) {
+      cudaEvent_t e;
+      CLAIR_CUDA(cudaEventCreate(&e));
+      v.push_back(e);
+      CLAIR_CUDA(cudaEventRecord(e, st));
+    }
+  } marks;
   for (int k = 0;; ++k) {
     Level& L = h->lv[k];
     const int n = L.n;
+    if (active_clock()) active_clock()->set_level(k);
+    marks.record(s);
     L.dinv = dalloc<double>(n, s);
     inverse_diagonal(L.A, L.dinv, s);
     if (!batch) {
@@ -649,6 +667,14 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
   // coarsest after its splitting)
   CLAIR_CUDA(cudaEventRecord(ss.join, ss.s2));
   CLAIR_CUDA(cudaStreamWaitEvent(s, ss.join, 0));
+  marks.record(s);
+  CLAIR_CUDA(cudaEventSynchronize(marks.v.back()));
+  for (size_t k = 0; k + 1 < marks.v.size() && k < 32; ++k) {
+    float ms = 0.f;
+    CLAIR_CUDA(cudaEventElapsedTime(&ms, marks.v[k], marks.v[k + 1]));
+    h->level_span_ms[k] = ms;
+  }
+  if (active_clock()) active_clock()->set_level((int)h->lv.size() - 1);
   {
     std::vector<double> om((size_t)p.max_levels * ninst, 1.0);
     CLAIR_CUDA(cudaMemcpyAsync(om.data(), omega_dev, sizeof(double) * om.size(),
@@ -1380,7 +1406,7 @@ static clair_status setup_common(int ninst, const int* offsets_host, int n, int 
     h->zout = dalloc<double>(n, s);
     CLAIR_CUDA(cudaStreamSynchronize(s));
     build_cycle_graph(h);
-    clock.collect(h->phase_ms);
+    clock.collect(h->phase_ms, h->level_phase_ms, 32);
     CLAIR_CUDA(cudaEventRecord(e1, s));
     CLAIR_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -1562,9 +1588,14 @@ clair_status clair_stats(clair_h h, clair_stats_t* o) {
   o->fp64_cycle_from = h->fp64_from;
   o->k = h->kmodes;
   o->lsolve_kind_b1 = h->st.config_kind_b1;
+  o->lsolve_kind_b3 = h->st.config_kind_b3;
   o->lsolve_blocks_per_sm = h->st.config_blocks_per_sm;
   o->lsolve_tuned = h->st.config_tuned;
   o->cycle_short_lanes = h->short_lanes;
+  for (int k = 0; k < 32; ++k) {
+    o->level_span_ms[k] = h->level_span_ms[k];
+    for (int q = 0; q < 8; ++q) o->level_phase_ms[k][q] = h->level_phase_ms[k * PH_COUNT + q];
+  }
   o->cycle64_from = -1;
   for (size_t k = 0; k < h->lv.size(); ++k)
     if (h->lv[k].cycle64) {
@@ -1576,17 +1607,68 @@ clair_status clair_stats(clair_h h, clair_stats_t* o) {
 
 int64_t clair_kernel_launches(void) { return launch_count(); }
 
-clair_status clair_lsolve_config(int precision, int set, int* kind_b1, int* blocks_per_sm,
-                                 int* tuned) {
+clair_status clair_lsolve_config(int precision, int set, int* kind_b1, int* kind_b3,
+                                 int* blocks_per_sm, int* tuned) {
   CLAIR_API_BEGIN
-  CLAIR_REQUIRE(kind_b1 && blocks_per_sm && tuned, CLAIR_ERR_ARG, "clair_lsolve_config: null pointer");
+  CLAIR_REQUIRE(kind_b1 && kind_b3 && blocks_per_sm && tuned, CLAIR_ERR_ARG,
+                "clair_lsolve_config: null pointer");
   CLAIR_REQUIRE(precision == CLAIR_FP64 || precision == CLAIR_MIXED, CLAIR_ERR_ARG,
                 "unknown precision");
   if (set) {
-    CLAIR_REQUIRE((*kind_b1 == 1 || *kind_b1 == 2) && *blocks_per_sm >= 0, CLAIR_ERR_ARG,
-                  "clair_lsolve_config: kind_b1 must be 1 or 2, blocks_per_sm >= 0");
+    CLAIR_REQUIRE((*kind_b1 == 1 || *kind_b1 == 2) && (*kind_b3 == 3 || *kind_b3 == 4) &&
+                      *blocks_per_sm >= 0,
+                  CLAIR_ERR_ARG,
+                  "clair_lsolve_config: kind_b1 in {1, 2}, kind_b3 in {3, 4}, blocks_per_sm >= 0");
   }
-  lsolve_config(precision, kind_b1, blocks_per_sm, tuned, set != 0);
+  lsolve_config(precision, kind_b1, kind_b3, blocks_per_sm, tuned, set != 0);
+  CLAIR_API_END
+}
+
+clair_status clair_spgemm(int m, int kdim, int ncols, const int* A_rowptr, const int* A_col,
+                          const double* A_val, const int* B_rowptr, const int* B_col,
+                          const double* B_val, void* stream, int* rowptr_out, int64_t* nnz_out,
+                          int64_t cap, int* col_out, double* val_out) {
+  CLAIR_API_BEGIN
+  CLAIR_REQUIRE(A_rowptr && A_col && A_val && B_rowptr && B_col && B_val && rowptr_out && nnz_out,
+                CLAIR_ERR_ARG, "clair_spgemm: null pointer");
+  CLAIR_REQUIRE(m > 0 && kdim > 0 && ncols > 0, CLAIR_ERR_ARG, "clair_spgemm: bad sizes");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int nnzA = 0, nnzB = 0;
+  CLAIR_CUDA(cudaMemcpyAsync(&nnzA, A_rowptr + m, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaMemcpyAsync(&nnzB, B_rowptr + kdim, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  validate_csr(A_rowptr, A_col, m, kdim, nnzA, "A", s);
+  validate_csr(B_rowptr, B_col, kdim, ncols, nnzB, "B", s);
+  Csr A, B, C;
+  A.rows = m;
+  A.cols = kdim;
+  A.nnz = nnzA;
+  A.rowptr = const_cast<int*>(A_rowptr);
+  A.col = const_cast<int*>(A_col);
+  A.val = const_cast<double*>(A_val);
+  B.rows = kdim;
+  B.cols = ncols;
+  B.nnz = nnzB;
+  B.rowptr = const_cast<int*>(B_rowptr);
+  B.col = const_cast<int*>(B_col);
+  B.val = const_cast<double*>(B_val);
+  spgemm(A, B, C, s);
+  *nnz_out = C.nnz;
+  try {
+    CLAIR_CUDA(cudaMemcpyAsync(rowptr_out, C.rowptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToDevice, s));
+    if (col_out && val_out) {
+      CLAIR_REQUIRE(C.nnz <= cap, CLAIR_ERR_CAPACITY, "clair_spgemm: nnz(C) = %d exceeds cap %lld",
+                    C.nnz, (long long)cap);
+      CLAIR_CUDA(cudaMemcpyAsync(col_out, C.col, sizeof(int) * C.nnz, cudaMemcpyDeviceToDevice, s));
+      CLAIR_CUDA(cudaMemcpyAsync(val_out, C.val, sizeof(double) * C.nnz, cudaMemcpyDeviceToDevice, s));
+    }
+  } catch (...) {
+    C.release(s);
+    cudaStreamSynchronize(s);
+    throw;
+  }
+  C.release(s);
+  CLAIR_CUDA(cudaStreamSynchronize(s));
   CLAIR_API_END
 }
 

@@ -496,6 +496,207 @@ __device__ __forceinline__ void team_body(const int* __restrict__ Arp, const int
   team_sync<KIND, TMAX>(bar_id);  // the team's shared block is reused by its next system
 }
 
+// One warp solves a system of up to 32 * RPT unknowns: lane l owns rows l, l + 32, ...
+// The same arithmetic as team_body (same pivots, same operations per row, hence the same
+// bits), but the pivot search is two warp reductions and no step needs a block barrier.
+template <class Real, class VT, int RPT>
+__device__ __forceinline__ void warp_body(const int* __restrict__ Arp, const int* __restrict__ Acol,
+                                          const VT* __restrict__ Aval, const int* __restrict__ Zrp,
+                                          const int* __restrict__ Zcol, const int* __restrict__ cpts,
+                                          int r, double* __restrict__ Zval,
+                                          unsigned long long* __restrict__ nsingular,
+                                          TeamSmem<Real, 32 * RPT>& sm, int lane) {
+  using V = typename Vec16<Real>::type;
+  constexpr int VN = 16 / (int)sizeof(Real);
+  constexpr int TMAX = 32 * RPT;
+  constexpr int PITCH = cta_pitch<Real, TMAX>();
+  constexpr unsigned FULL = 0xffffffffu;
+  Real* tile = sm.tile;
+  Real* rhs = sm.rhs;
+  const int i = cpts[r];
+  const int base = Zrp[r];
+  const int len = Zrp[r + 1] - base;
+  const int T = len - 1;
+  // position of the identity column (TMAX, unseen, only when T == TMAX)
+  int d = T;
+#pragma unroll
+  for (int q = RPT - 1; q >= 0; --q) {
+    const int tq = lane + 32 * q;
+    const unsigned m = __ballot_sync(FULL, tq < len && Zcol[base + tq] == i);
+    if (m) d = 32 * q + __ffs(m) - 1;
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int tq = lane + 32 * q;
+    if (tq < T) sm.zl[tq] = Zcol[base + tq + (tq >= d ? 1 : 0)];
+    Real* row = tile + tq * PITCH;
+    for (int c = 0; c < TMAX; c += VN) *reinterpret_cast<V*>(row + c) = V{};
+    rhs[tq] = Real(0);
+  }
+  __syncwarp();
+  // row starts and the prefix of the row lengths in row order
+  int off = 0;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int tq = lane + 32 * q;
+    const int rstart = tq < T ? Arp[sm.zl[tq]] : 0;
+    int rlen = tq < T ? Arp[sm.zl[tq] + 1] - rstart : 0;
+    sm.rs[tq] = rstart;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, rlen, o);
+      if (lane >= o) rlen += v;
+    }
+    sm.pre[tq + 1] = off + rlen;
+    off += __shfl_sync(FULL, rlen, 31);
+  }
+  if (lane == 0) sm.pre[0] = 0;
+  __syncwarp();
+  const int total = sm.pre[TMAX];
+  constexpr int GB = 4;
+  for (int f0 = lane; f0 < total; f0 += GB * 32) {
+    int row_of[GB], col_of[GB];
+    Real val_of[GB];
+#pragma unroll
+    for (int u = 0; u < GB; ++u) {
+      const int f = f0 + u * 32;
+      row_of[u] = -1;
+      if (f < total) {
+        int lo = 0, hi = TMAX;  // row with pre[row] <= f < pre[row + 1]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (sm.pre[mid] <= f) lo = mid; else hi = mid;
+        }
+        const int e = sm.rs[lo] + (f - sm.pre[lo]);
+        row_of[u] = lo;
+        col_of[u] = Acol[e];
+        val_of[u] = Real(Aval[e]);
+      }
+    }
+    int q_of[GB];
+#pragma unroll
+    for (int u = 0; u < GB; ++u)
+      q_of[u] = row_of[u] < 0 ? -1 : (col_of[u] == i ? T : find_sorted(sm.zl, T, col_of[u]));
+#pragma unroll
+    for (int u = 0; u < GB; ++u) {
+      if (q_of[u] == T) rhs[row_of[u]] = -val_of[u];
+      else if (q_of[u] >= 0) tile[row_of[u] * PITCH + q_of[u]] = val_of[u];
+    }
+  }
+  __syncwarp();
+  bool done[RPT];
+  int mystep[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    done[q] = lane + 32 * q >= T;
+    mystep[q] = -1;
+  }
+  bool sing = false;
+  for (int k = 0; k < T; ++k) {
+    // pivot: largest |a| of column k among the rows not yet eliminated, lowest row on ties
+    int piv;
+    if constexpr (sizeof(Real) == 4) {
+      unsigned key = 0u;
+      int row = 0x7fffffff;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q)
+        if (!done[q]) {
+          const unsigned kq = __float_as_uint(fabsf(tile[(lane + 32 * q) * PITCH + k])) + 1u;
+          if (kq > key) {
+            key = kq;
+            row = lane + 32 * q;
+          }
+        }
+      const unsigned wmax = __reduce_max_sync(FULL, key);
+      piv = __reduce_min_sync(FULL, key == wmax ? row : 0x7fffffff);
+    } else {
+      Real v = Real(-1);
+      int who = 0x7fffffff;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q)
+        if (!done[q]) {
+          const Real a = tile[(lane + 32 * q) * PITCH + k];
+          const Real m = a < 0 ? -a : a;
+          if (m > v) {
+            v = m;
+            who = lane + 32 * q;
+          }
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const Real v2 = __shfl_xor_sync(FULL, v, o);
+        const int w2 = __shfl_xor_sync(FULL, who, o);
+        if (v2 > v || (v2 == v && w2 < who)) {
+          v = v2;
+          who = w2;
+        }
+      }
+      piv = who;
+    }
+    const Real* prow = tile + piv * PITCH;
+    const Real pk = prow[k];
+    if (!((pk < 0 ? -pk : pk) > Real(0))) sing = true;
+    if (lane == 0) sm.steprow[k] = piv;
+    const Real rpiv = rhs[piv];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int tq = lane + 32 * q;
+      if (tq == piv) {
+        done[q] = true;
+        mystep[q] = k;
+      } else if (!done[q] && pk != Real(0)) {
+        Real* row = tile + tq * PITCH;
+        const Real l = row[k] / pk;
+        for (int j0 = (k + 1) & ~(VN - 1); j0 < T; j0 += 2 * VN) {
+          const bool two = j0 + VN < T;
+          const V p0 = *reinterpret_cast<const V*>(prow + j0);
+          V r0 = *reinterpret_cast<const V*>(row + j0);
+          V p1 = p0, r1 = r0;
+          if (two) {
+            p1 = *reinterpret_cast<const V*>(prow + j0 + VN);
+            r1 = *reinterpret_cast<const V*>(row + j0 + VN);
+          }
+          sub_scaled(r0, l, p0);
+          *reinterpret_cast<V*>(row + j0) = r0;
+          if (two) {
+            sub_scaled(r1, l, p1);
+            *reinterpret_cast<V*>(row + j0 + VN) = r1;
+          }
+        }
+        rhs[tq] -= l * rpiv;
+      }
+    }
+    __syncwarp();
+  }
+  // back substitution
+  for (int k = T - 1; k >= 0; --k) {
+    const int own = sm.steprow[k];
+    if (lane == (own & 31)) {
+      const Real dk = tile[own * PITCH + k];
+      sm.xs[k] = dk != Real(0) ? rhs[own] / dk : Real(0);
+    }
+    __syncwarp();
+    const Real xk = sm.xs[k];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+      if (mystep[q] >= 0 && mystep[q] < k) {
+        const int tq = lane + 32 * q;
+        rhs[tq] -= tile[tq * PITCH + k] * xk;
+      }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int tq = lane + 32 * q;
+    if (tq < T) Zval[base + tq + (tq >= d ? 1 : 0)] = sing ? 0.0 : (double)sm.xs[tq];
+  }
+  if (lane == 0) {
+    Zval[base + d] = 1.0;
+    if (sing) atomicAdd(nsingular, 1ull);
+  }
+  __syncwarp();  // the warp's shared block is reused by its next system
+}
+
 // shared memory holds these to about 1024 resident threads per SM, so the register
 // budget is set for that many (64 each) rather than for full occupancy
 template <class Real, class VT, int TMAX>
@@ -526,9 +727,9 @@ static size_t cta_smem() {
 // groups or to single warps, as the autotuner chose.
 // ------------------------------------------------------------------------------------
 constexpr int LP_THREADS = 128;
-enum { LK_G8 = 0, LK_G16 = 1, LK_W32 = 2, LK_P64 = 3 };
+enum { LK_G8 = 0, LK_G16 = 1, LK_W32 = 2, LK_P64 = 3, LK_W64 = 4 };
 __host__ __device__ constexpr int lk_systems(int kind) {
-  return kind == LK_G8 ? 16 : kind == LK_G16 ? 8 : kind == LK_W32 ? 4 : 2;
+  return kind == LK_G8 ? 16 : kind == LK_G16 ? 8 : kind == LK_W32 ? 4 : kind == LK_P64 ? 2 : 4;
 }
 
 template <class VT>
@@ -547,22 +748,24 @@ union PersistSmem {
   GroupSmem<Real, 16> g16[4];
   TeamSmem<Real, 32> w32[4];
   TeamSmem<Real, 64> p64[2];
+  TeamSmem<Real, 64> w64[4];
 };
 
 template <class Real>
-static size_t persist_smem(bool g8, bool g16, bool w32, bool p64) {
+static size_t persist_smem(const bool* has) {
   size_t b = 16;
-  if (g8) b = std::max(b, 4 * sizeof(GroupSmem<Real, 8>));
-  if (g16) b = std::max(b, 4 * sizeof(GroupSmem<Real, 16>));
-  if (w32) b = std::max(b, 4 * sizeof(TeamSmem<Real, 32>));
-  if (p64) b = std::max(b, 2 * sizeof(TeamSmem<Real, 64>));
+  if (has[LK_G8]) b = std::max(b, 4 * sizeof(GroupSmem<Real, 8>));
+  if (has[LK_G16]) b = std::max(b, 4 * sizeof(GroupSmem<Real, 16>));
+  if (has[LK_W32]) b = std::max(b, 4 * sizeof(TeamSmem<Real, 32>));
+  if (has[LK_P64]) b = std::max(b, 2 * sizeof(TeamSmem<Real, 64>));
+  if (has[LK_W64]) b = std::max(b, 4 * sizeof(TeamSmem<Real, 64>));
   return b;
 }
 
 template <class Real, class VT>
 __global__ void __launch_bounds__(LP_THREADS)
-lsolve_persist(SideArgs<VT> S0, SideArgs<VT> S1, int nsides, int kind_b1, int* __restrict__ ticket,
-               unsigned long long* __restrict__ nsingular) {
+lsolve_persist(SideArgs<VT> S0, SideArgs<VT> S1, int nsides, int kind_b1, int kind_b3,
+               int* __restrict__ ticket, unsigned long long* __restrict__ nsingular) {
   extern __shared__ __align__(16) unsigned char lp_smem[];
   auto& sm = *reinterpret_cast<PersistSmem<Real>*>(lp_smem);
   __shared__ int seg_end[8], seg_kind[8];
@@ -573,7 +776,7 @@ lsolve_persist(SideArgs<VT> S0, SideArgs<VT> S1, int nsides, int kind_b1, int* _
     for (int q = 0; q < 8; ++q) {
       const int b = 3 - (q >> 1), side = q & 1;
       const int cnt = side < nsides ? (side ? S1.counts[b] : S0.counts[b]) : 0;
-      const int kind = b == 3 ? LK_P64 : b == 2 ? LK_W32 : b == 1 ? kind_b1 : LK_G8;
+      const int kind = b == 3 ? kind_b3 : b == 2 ? LK_W32 : b == 1 ? kind_b1 : LK_G8;
       acc += (cnt + lk_systems(kind) - 1) / lk_systems(kind);
       seg_end[q] = acc;
       seg_kind[q] = kind;
@@ -607,13 +810,18 @@ lsolve_persist(SideArgs<VT> S0, SideArgs<VT> S1, int nsides, int kind_b1, int* _
       if (item < cnt)
         team_body<Real, VT, 32, TEAM_WARP>(S.Arp, S.Acol, S.Aval, S.Zrp, S.Zcol, S.cpts, list[item],
                                            S.Zval, nsingular, sm.w32[wib], lane, 0);
-    } else {
+    } else if (kind == LK_P64) {
       const int team = wib >> 1;
       const long long item = first + team;
       if (item < cnt)
         team_body<Real, VT, 64, TEAM_NAMED>(S.Arp, S.Acol, S.Aval, S.Zrp, S.Zcol, S.cpts,
                                             list[item], S.Zval, nsingular, sm.p64[team],
                                             threadIdx.x & 63, 1 + team);
+    } else {
+      const long long item = first + wib;
+      if (item < cnt)
+        warp_body<Real, VT, 2>(S.Arp, S.Acol, S.Aval, S.Zrp, S.Zcol, S.cpts, list[item], S.Zval,
+                               nsingular, sm.w64[wib], lane);
     }
   }
 }
@@ -1104,6 +1312,7 @@ static Real* big_tiles(const int* counts_h, int& pitch, int& chunk, cudaStream_t
 // ---- execution configuration of the persistent launch, per device and precision -------
 struct LsolveConfig {
   int kind_b1 = LK_G16;   // systems with 8 < T <= 16: 16-lane groups or single warps
+  int kind_b3 = LK_P64;   // systems with 32 < T <= 64: warp pairs or single warps
   int blocks_per_sm = 0;  // 0: as many as fit
   int tuned = 0;          // 1: chosen by timing, 2: set by the caller
 };
@@ -1132,16 +1341,17 @@ template <class Real, class VT>
 static void persistent_launch(const SideArgs<VT>* sa, int nsides, const int (*counts_h)[LS_BUCKETS + 2],
                               const LsolveConfig& cfg, int* ticket, unsigned long long* nsing,
                               cudaStream_t s) {
-  bool has[4] = {false, false, false, false};
+  bool has[5] = {false, false, false, false, false};
   long long tasks = 0;
   for (int q = 0; q < nsides; ++q) {
     has[LK_G8] |= counts_h[q][0] > 0;
     has[cfg.kind_b1] |= counts_h[q][1] > 0;
     has[LK_W32] |= counts_h[q][2] > 0;
-    has[LK_P64] |= counts_h[q][3] > 0;
+    has[cfg.kind_b3] |= counts_h[q][3] > 0;
     tasks += ceil_div(counts_h[q][0], lk_systems(LK_G8)) +
              ceil_div(counts_h[q][1], lk_systems(cfg.kind_b1)) +
-             ceil_div(counts_h[q][2], lk_systems(LK_W32)) + ceil_div(counts_h[q][3], lk_systems(LK_P64));
+             ceil_div(counts_h[q][2], lk_systems(LK_W32)) +
+             ceil_div(counts_h[q][3], lk_systems(cfg.kind_b3));
   }
   if (tasks == 0) return;
   once_per_device((const void*)lsolve_persist<Real, VT>, [] {
@@ -1149,7 +1359,7 @@ static void persistent_launch(const SideArgs<VT>* sa, int nsides, const int (*co
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sizeof(PersistSmem<Real>)));
   });
-  const size_t smem = persist_smem<Real>(has[LK_G8], has[LK_G16], has[LK_W32], has[LK_P64]);
+  const size_t smem = persist_smem<Real>(has);
   int fit = 0;
   CLAIR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, lsolve_persist<Real, VT>, LP_THREADS,
                                                            smem));
@@ -1157,7 +1367,7 @@ static void persistent_launch(const SideArgs<VT>* sa, int nsides, const int (*co
   const int grid = (int)std::min<long long>(tasks, (long long)sm_count() * per_sm);
   CLAIR_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), s));
   lsolve_persist<Real, VT><<<grid, LP_THREADS, smem, s>>>(sa[0], nsides > 1 ? sa[1] : sa[0], nsides,
-                                                          cfg.kind_b1, ticket, nsing); ::clair::count_launch();
+                                                          cfg.kind_b1, cfg.kind_b3, ticket, nsing); ::clair::count_launch();
   CLAIR_LAUNCHED();
 }
 
@@ -1167,17 +1377,19 @@ template <class Real, class VT>
 static void autotune(const SideArgs<VT>* sa, int nsides, const int (*counts_h)[LS_BUCKETS + 2],
                      LsolveConfig& cfg, int* ticket, cudaStream_t s) {
   unsigned long long* scratch = dalloc<unsigned long long>(1, s);
-  LsolveConfig cands[3];
-  cands[0].kind_b1 = LK_G16;
+  constexpr int NC = 5;
+  LsolveConfig cands[NC];
   cands[1].kind_b1 = LK_W32;
-  cands[2].kind_b1 = LK_G16;
   cands[2].blocks_per_sm = 4;
+  cands[3].kind_b3 = LK_W64;
+  cands[4].kind_b1 = LK_W32;
+  cands[4].kind_b3 = LK_W64;
   cudaEvent_t e0, e1;
   CLAIR_CUDA(cudaEventCreate(&e0));
   CLAIR_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int pick = 0;
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < NC; ++c) {
     for (int rep = 0; rep < 2; ++rep) {  // the first run warms the caches and the code
       CLAIR_CUDA(cudaEventRecord(e0, s));
       persistent_launch<Real, VT>(sa, nsides, counts_h, cands[c], ticket, scratch, s);
@@ -1241,14 +1453,18 @@ void local_solves_multi(const SideIn* sides, int nsides, const int* cpts, int pr
       {
         std::lock_guard<std::mutex> lock(g_cfg_mu);
         LsolveConfig& slot = config_slot(precision);
-        long long small = 0;
-        for (int q = 0; q < nsides; ++q)
+        long long small = 0, b3 = 0;
+        for (int q = 0; q < nsides; ++q) {
           for (int b = 0; b < 4; ++b) small += counts_h[q][b];
-        if (!slot.tuned && small >= LS_TUNE_MIN)
+          b3 += counts_h[q][3];
+        }
+        // timed on the first level with enough systems, among them enough of 32 < T <= 64
+        if (!slot.tuned && small >= LS_TUNE_MIN && b3 >= LS_TUNE_MIN / 10)
           autotune<Real, VT>(sa, nsides, counts_h, slot, ticket, s);
         cfg = slot;
       }
       st.config_kind_b1 = cfg.kind_b1;
+      st.config_kind_b3 = cfg.kind_b3;
       st.config_blocks_per_sm = cfg.blocks_per_sm;
       st.config_tuned = cfg.tuned;
       persistent_launch<Real, VT>(sa, nsides, counts_h, cfg, ticket, nsing, s);
@@ -1300,15 +1516,18 @@ void local_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* c
 
 // Sets (kind_b1 >= 0) or reads the execution configuration of the persistent local-solve
 // launch on the current device for one precision.
-void lsolve_config(int precision, int* kind_b1, int* blocks_per_sm, int* tuned, bool set) {
+void lsolve_config(int precision, int* kind_b1, int* kind_b3, int* blocks_per_sm, int* tuned,
+                   bool set) {
   std::lock_guard<std::mutex> lock(g_cfg_mu);
   LsolveConfig& slot = config_slot(precision);
   if (set) {
     slot.kind_b1 = *kind_b1;
+    slot.kind_b3 = *kind_b3;
     slot.blocks_per_sm = *blocks_per_sm;
     slot.tuned = *tuned;
   } else {
     *kind_b1 = slot.kind_b1;
+    *kind_b3 = slot.kind_b3;
     *blocks_per_sm = slot.blocks_per_sm;
     *tuned = slot.tuned;
   }

@@ -93,6 +93,7 @@ int PhaseClock::begin(int ph, cudaStream_t s) {
   }
   Mark& m = marks_[n_++];
   m.ph = ph;
+  m.level = level_;
   cudaEventCreate(&m.a);
   cudaEventCreate(&m.b);
   cudaEventRecord(m.a, s);
@@ -103,11 +104,15 @@ void PhaseClock::end(int mark, cudaStream_t s) {
   if (mark >= 0 && mark < n_) cudaEventRecord(marks_[mark].b, s);
 }
 
-void PhaseClock::collect(double* ms_out) {
+void PhaseClock::collect(double* ms_out, double* level_ms, int max_levels) {
   for (int i = 0; i < n_; ++i) cudaEventSynchronize(marks_[i].b);
   for (int i = 0; i < n_; ++i) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, marks_[i].a, marks_[i].b) == cudaSuccess) ms_out[marks_[i].ph] += ms;
+    if (cudaEventElapsedTime(&ms, marks_[i].a, marks_[i].b) == cudaSuccess) {
+      ms_out[marks_[i].ph] += ms;
+      if (level_ms && marks_[i].level < max_levels)
+        level_ms[marks_[i].level * PH_COUNT + marks_[i].ph] += ms;
+    }
     cudaEventDestroy(marks_[i].a);
     cudaEventDestroy(marks_[i].b);
   }
@@ -992,8 +997,75 @@ spgemm_large(const int* __restrict__ Arp, const int* __restrict__ Acol,
   int* keys = reinterpret_cast<int*>(smem + (NUMERIC ? sizeof(double) * SG_LARGE : 0));
   const int nrows = *dnrows;
   for (int idx = blockIdx.x; idx < nrows; idx += gridDim.x) {
+    if (NUMERIC && count[list[idx]] > SG_LARGE) continue;  // the dense tier writes it
     spgemm_row<NUMERIC>(list[idx], Arp, Acol, Aval, Brp, Bcol, Bval, keys,
                         NUMERIC ? vals : nullptr, SG_LARGE, count, Crp, Ccol, Cval);
+    __syncwarp();
+  }
+}
+
+// Rows beyond the large table (more than SG_LARGE distinct columns: coarse levels of 3D
+// problems with slow coarsening): one warp per listed row with a dense accumulator over
+// all of B's columns and a column bitmap, both in global memory (one slot per block,
+// left zeroed after each row).  Products are added in the row's A order, all lanes of one
+// A entry before the next (distinct columns within a B row), as in the other tiers; the
+// outputs come out in column order from the bitmap.
+template <bool NUMERIC>
+__global__ void __launch_bounds__(32)
+spgemm_dense(const int* __restrict__ Arp, const int* __restrict__ Acol,
+             const double* __restrict__ Aval, const int* __restrict__ list,
+             const int* __restrict__ dnrows, const int* __restrict__ Brp,
+             const int* __restrict__ Bcol, const double* __restrict__ Bval, int ncols,
+             double* __restrict__ dense, unsigned* __restrict__ bits, int* __restrict__ count,
+             const int* __restrict__ Crp, int* __restrict__ Ccol, double* __restrict__ Cval) {
+  const int lane = threadIdx.x;
+  const int nwords = (ncols + 31) >> 5;
+  double* acc = dense + (size_t)blockIdx.x * ncols;
+  unsigned* bw = bits + (size_t)blockIdx.x * nwords;
+  const int nrows = *dnrows;
+  for (int idx = blockIdx.x; idx < nrows; idx += gridDim.x) {
+    const int r = list[idx];
+    if (NUMERIC && count[r] <= SG_LARGE) continue;  // held by the large table
+    for (int ea = Arp[r]; ea < Arp[r + 1]; ++ea) {
+      const int k = Acol[ea];
+      const double a = NUMERIC ? Aval[ea] : 0.0;
+      for (int eb = Brp[k] + lane; eb < Brp[k + 1]; eb += 32) {
+        const int c = Bcol[eb];
+        if (NUMERIC) acc[c] = __dadd_rn(acc[c], __dmul_rn(a, Bval[eb]));
+        atomicOr(&bw[c >> 5], 1u << (c & 31));
+      }
+      __syncwarp();  // the next A entry's products may hit the same columns
+    }
+    __threadfence_block();
+    __syncwarp();
+    int total = 0;
+    const int base = NUMERIC ? Crp[r] : 0;
+    for (int w0 = 0; w0 < nwords; w0 += 32) {
+      const int w = w0 + lane;
+      unsigned word = w < nwords ? bw[w] : 0u;
+      const int cnt = __popc(word);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (NUMERIC) {
+        int pos = base + total + incl - cnt;
+        while (word) {
+          const int b = __ffs(word) - 1;
+          word &= word - 1;
+          const int c = w * 32 + b;
+          Ccol[pos] = c;
+          Cval[pos] = acc[c];
+          acc[c] = 0.0;
+          ++pos;
+        }
+      }
+      if (w < nwords) bw[w] = 0u;
+      total += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (!NUMERIC && lane == 0) count[r] = total;
     __syncwarp();
   }
 }
@@ -1313,6 +1385,28 @@ void drop_zeros(Csr& C, cudaStream_t s) {
   C.nnz = nnz;
 }
 
+// The dense tier for the `dn` rows listed in `list` (symbolic: count; numeric: values).
+// Its accumulators are allocated only when rows reach it; the host reads the list length
+// with the scan that follows the symbolic pass, so `still` rows need no further check.
+struct DenseTier {
+  double* dense = nullptr;
+  unsigned* bits = nullptr;
+  int slots = 0;
+  void ensure(int ncols, int rows, cudaStream_t s) {
+    if (dense) return;
+    slots = std::max(1, std::min(rows, 2 * sm_count()));
+    const size_t nwords = (size_t)(ncols + 31) / 32;
+    dense = dalloc<double>((size_t)slots * ncols, s);
+    bits = dalloc<unsigned>((size_t)slots * nwords, s);
+    CLAIR_CUDA(cudaMemsetAsync(dense, 0, sizeof(double) * slots * ncols, s));
+    CLAIR_CUDA(cudaMemsetAsync(bits, 0, sizeof(unsigned) * slots * nwords, s));
+  }
+  void release(cudaStream_t s) {
+    dfree(dense, s);
+    dfree(bits, s);
+  }
+};
+
 // Long products: the CTA-per-row kernel for every row, the large table for the rows it
 // could not hold.
 static void spgemm_cta_path(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
@@ -1347,18 +1441,20 @@ static void spgemm_cta_path(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) 
   spgemm_collect<<<std::max(1, std::min(ceil_div(rows, 256), sms * 8)), 256, 0, s>>>(
       count, nullptr, A.rowptr, list, rows, nlist, 0, 0, 0, list2, nlist + 1); ::clair::count_launch();
   CLAIR_LAUNCHED();
+  // rows no table could hold (list2, nlist[1], read back with the scan total) go to the
+  // dense tier, and the scan is redone
   C.rowptr = dalloc<int>(rows + 1, s);
-  int still = 0;  // rows no table could hold, read back with the scan total
+  int still = 0;
   C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true, nlist + 1, &still);
-  if (still) {
-    dfree(count, s);
-    dfree(route, s);
-    dfree(list, s);
-    dfree(list2, s);
-    dfree(nlist, s);
-    dfree(C.rowptr, s);
-    CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "SpGEMM: %d rows exceed %d distinct columns", still,
-                  SG_LARGE);
+  DenseTier dt;
+  const bool may_overflow = still > 0;
+  if (may_overflow) {
+    dt.ensure(B.cols, still, s);
+    spgemm_dense<false><<<dt.slots, 32, 0, s>>>(A.rowptr, A.col, A.val, list2, nlist + 1, B.rowptr,
+                                                B.col, B.val, B.cols, dt.dense, dt.bits, count,
+                                                nullptr, nullptr, nullptr); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+    C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true);
   }
   C.col = dalloc<int>(C.nnz, s);
   C.val = dalloc<double>(C.nnz, s);
@@ -1367,7 +1463,13 @@ static void spgemm_cta_path(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) 
       C.val); ::clair::count_launch();
   spgemm_large<true><<<std::max(1, std::min(rows, sms)), 32, (sizeof(int) + sizeof(double)) * SG_LARGE, s>>>(
       A.rowptr, A.col, A.val, list, nlist, B.rowptr, B.col, B.val, count, C.rowptr, C.col, C.val); ::clair::count_launch();
+  if (may_overflow) {
+    spgemm_dense<true><<<dt.slots, 32, 0, s>>>(A.rowptr, A.col, A.val, list2, nlist + 1, B.rowptr,
+                                               B.col, B.val, B.cols, dt.dense, dt.bits, count,
+                                               C.rowptr, C.col, C.val); ::clair::count_launch();
+  }
   CLAIR_LAUNCHED();
+  dt.release(s);
   dfree(count, s);
   dfree(route, s);
   dfree(list, s);
@@ -1458,24 +1560,31 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
       cur ^= 1;
     }
   }
-  // rows still unplaced after the large table: nlist[3]; the scan's read-back carries it
+  // rows still unplaced after the large table (lists[1], nlist[3], read back with the scan
+  // total) go to the dense tier, and the scan is redone; they keep a list of their own for
+  // the numeric pass
   C.rowptr = dalloc<int>(rows + 1, s);
   int still = 0;
   C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true, nlist + 3, &still);
-  if (still) {
-    dfree(count, s);
-    dfree(lists[0], s);
-    dfree(lists[1], s);
-    dfree(nlist, s);
-    dfree(C.rowptr, s);
-    CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "SpGEMM: %d rows exceed %d distinct columns", still,
-                  SG_LARGE);
+  DenseTier dt;
+  int* dense_list = nullptr;
+  const bool may_overflow = still > 0;
+  if (may_overflow) {
+    dt.ensure(B.cols, still, s);
+    dense_list = dalloc<int>(std::max(rows, 1), s);
+    CLAIR_CUDA(cudaMemcpyAsync(dense_list, lists[1], sizeof(int) * rows, cudaMemcpyDeviceToDevice, s));
+    CLAIR_CUDA(cudaMemcpyAsync(nlist + 4, nlist + 3, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    spgemm_dense<false><<<dt.slots, 32, 0, s>>>(A.rowptr, A.col, A.val, dense_list, nlist + 4,
+                                                B.rowptr, B.col, B.val, B.cols, dt.dense, dt.bits,
+                                                count, nullptr, nullptr, nullptr); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+    C.nnz = (int)exclusive_scan(count, C.rowptr, rows, s, true);
   }
   C.col = dalloc<int>(C.nnz, s);
   C.val = dalloc<double>(C.nnz, s);
   // ---- numeric: each row in the first tier that holds it (output count <= cap / 2, A row
   // <= prefix capacity) ----
-  CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 8 * sizeof(int), s));
+  CLAIR_CUDA(cudaMemsetAsync(nlist, 0, 4 * sizeof(int), s));
   {
     const int* src = nullptr;
     const int* dn = nullptr;
@@ -1502,6 +1611,14 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
       }
     }
   }
+  if (may_overflow) {
+    spgemm_dense<true><<<dt.slots, 32, 0, s>>>(A.rowptr, A.col, A.val, dense_list, nlist + 4,
+                                               B.rowptr, B.col, B.val, B.cols, dt.dense, dt.bits,
+                                               count, C.rowptr, C.col, C.val); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+  }
+  dt.release(s);
+  dfree(dense_list, s);
   dfree(count, s);
   dfree(lists[0], s);
   dfree(lists[1], s);

@@ -218,3 +218,36 @@ def test_full_size_properties(cl, eps, degree, sweeps, converge):
         assert not np.any(~cf & has & ~dep_c)
     if len(its) == 2 and not fell_back[1]:
         assert abs(its[0] - its[1]) <= 1, its
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-4])
+def test_advection_dominated_iterations_match_oracle_256(cl, eps):
+    """The variants whose 1024^2 MIXED solve hands over to the FP64 cycle, at 256^2 where
+    the oracle's own iteration count is available (degree 2, five CFF sweeps on B): the
+    FP64 path within one iteration of the oracle.  The MIXED cycle is a different
+    preconditioner (FP32 rounding on its finer levels); it must not need more than one
+    iteration beyond the oracle, or, where its FP32 cycle stalled (fp64_cycle_from >= 0),
+    more than that plus the stall window (10 iterations) and the restart that hands over.
+    (At eps = 0 it needs fewer: 9 against the oracle's 14.)"""
+    import torch
+    prob = workloads.constdir_2d(256, math.pi / 6, eps, seed=1, degree=2)
+    A = O.csr_of(prob.A)
+    H = O.build_hierarchy(prob.A, prob.B, O.Params())
+    _, its_o, hist = O.fgmres(A, prob.f, lambda v: O.vcycle(H, v), 50, 1e-8, 200)
+    assert hist[-1] <= 1e-8 * np.linalg.norm(prob.f)
+    for precision in (0, 1):
+        h = setup_gpu(cl, prob, precision)
+        try:
+            f = dev(prob.f, torch.float64)
+            u = torch.zeros_like(f)
+            st, its, rel = cl.clair_solve(h, f, u)
+            uh = u.cpu().numpy()
+            assert np.linalg.norm(prob.f - A @ uh) <= 1e-8 * np.linalg.norm(prob.f)
+            fb = cl.clair_stats(h).fp64_cycle_from
+            if precision == 0:
+                assert abs(its - its_o) <= 1, (its, its_o)
+            else:
+                slack = 1 if fb < 0 else 1 + 10 + 1
+                assert its <= its_o + slack, (its, its_o, fb)
+        finally:
+            cl.clair_free(h)

@@ -271,15 +271,16 @@ def test_local_weights_every_bucket(cl, precision, eps, big):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("kind_b1,blocks", [(1, 0), (2, 0), (1, 2)])
-def test_local_weights_every_route_of_the_persistent_launch(cl, precision, kind_b1, blocks):
+@pytest.mark.parametrize("kind_b1,kind_b3,blocks", [(1, 3, 0), (2, 3, 0), (1, 3, 2), (1, 4, 0),
+                                                    (2, 4, 0)])
+def test_local_weights_every_route_of_the_persistent_launch(cl, precision, kind_b1, kind_b3, blocks):
     """Every configuration the autotuner may pick (systems with 8 < T <= 16 on 16-lane
-    groups or on single warps; all resident blocks or two per SM) gives the oracle's
-    weights on every bucket edge up to T = 128."""
+    groups or on single warps; 32 < T <= 64 on warp pairs or single warps; all resident
+    blocks or two per SM) gives the oracle's weights on every bucket edge up to T = 128."""
     import torch
     keep = cl.clair_lsolve_config(precision)
     try:
-        cl.clair_lsolve_config(precision, kind_b1, blocks, 2)
+        cl.clair_lsolve_config(precision, kind_b1, kind_b3, blocks, 2)
         A, cf, cpts, Wpat, B = crafted_case(eps=1.0)
         n = A.shape[0]
         W = O.clair_algorithm1(A, cf, B, Wpat, O.Params()).tocsc()
@@ -296,7 +297,8 @@ def test_local_weights_every_route_of_the_persistent_launch(cl, precision, kind_
         ref.sort_indices()
         assert rowwise_err(got, ref) <= (FP64_TOL if precision == 0 else FP32_TOL)
     finally:
-        cl.clair_lsolve_config(precision, keep["kind_b1"] or 1, keep["blocks_per_sm"], keep["tuned"])
+        cl.clair_lsolve_config(precision, keep["kind_b1"] or 1, keep["kind_b3"] or 3,
+                               keep["blocks_per_sm"], keep["tuned"])
 
 
 def test_local_weights_singular_block_reports_status(cl):
