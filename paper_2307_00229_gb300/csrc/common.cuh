@@ -280,6 +280,10 @@ struct LocalStats {
   long long gathered = 0;
   // execution configuration of the last persistent local-solve launch
   int config_kind_b1 = -1, config_kind_b3 = -1, config_blocks_per_sm = 0, config_tuned = 0;
+  // Optional device counters [singular, empty, sum T^3, sum T^2, sum T, gathered]: when set,
+  // kernels add into them and no host read happens per call (read once by the owner).
+  unsigned long long* dev = nullptr;
+  void absorb_device(cudaStream_t s);  // adds the device counters in, zeroes them (syncs)
 };
 
 // Kernel launches issued by this library (monotonic, process-wide).

@@ -1400,7 +1400,12 @@ static clair_status setup_common(int ninst, const int* offsets_host, int n, int 
     CLAIR_CUDA(cudaMemcpyAsync(h->B0, B, sizeof(double) * n * kmodes, cudaMemcpyDeviceToDevice, s));
     PhaseClock clock;
     set_active_clock(&clock);
+    // per-level counters stay on the device until the end of the setup
+    h->st.dev = dalloc<unsigned long long>(6, s);
+    CLAIR_CUDA(cudaMemsetAsync(h->st.dev, 0, 6 * sizeof(unsigned long long), s));
     setup_levels(h, B, cf_marker);
+    h->st.absorb_device(s);
+    dfree(h->st.dev, s);
     set_active_clock(nullptr);
     h->vin = dalloc<double>(n, s);
     h->zout = dalloc<double>(n, s);

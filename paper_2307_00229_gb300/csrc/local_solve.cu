@@ -1417,17 +1417,29 @@ void local_solves_multi(const SideIn* sides, int nsides, const int* cpts, int pr
                         LocalStats& st, cudaStream_t s) {
   int* lists[2] = {nullptr, nullptr};
   int* counts = dalloc<int>(2 * (LS_BUCKETS + 2), s);
-  unsigned long long* nsing = dalloc<unsigned long long>(5, s);  // [0] singular, [1..4] work
+  // [0] singular, [1..4] work: the owner's device counters when it has them (layout
+  // [singular, empty, work...]: the work counters follow at +2), else read back here
+  unsigned long long* own = nullptr;
+  unsigned long long* nsing = nullptr;
+  unsigned long long* work = nullptr;
+  if (st.dev) {
+    nsing = st.dev;
+    work = st.dev + 2;
+  } else {
+    own = dalloc<unsigned long long>(5, s);
+    CLAIR_CUDA(cudaMemsetAsync(own, 0, 5 * sizeof(unsigned long long), s));
+    nsing = own;
+    work = own + 1;
+  }
   int* ticket = dalloc<int>(1, s);
   CLAIR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * 2 * (LS_BUCKETS + 2), s));
-  CLAIR_CUDA(cudaMemsetAsync(nsing, 0, 5 * sizeof(unsigned long long), s));
   for (int q = 0; q < nsides; ++q) {
     const SideIn& S = sides[q];
     lists[q] = dalloc<int>((long long)LS_BUCKETS * std::max(S.nc, 1), s);
     int* cq = counts + q * (LS_BUCKETS + 2);
     if (S.nc) bucket_rows<<<ceil_div(S.nc, 256), 256, 0, s>>>(S.Zrp, S.nc, lists[q], cq, S.Zcol, cpts,
                                                              S.Ahat->rowptr, cq + LS_BUCKETS,
-                                                             nsing + 1); ::clair::count_launch();
+                                                             work); ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
   int counts_h[2][LS_BUCKETS + 2] = {};
@@ -1492,20 +1504,36 @@ void local_solves_multi(const SideIn* sides, int nsides, const int* cpts, int pr
       run(double(0), v);
     }
   }
-  unsigned long long h[5] = {0, 0, 0, 0, 0};
-  CLAIR_CUDA(cudaMemcpyAsync(h, nsing, sizeof(h), cudaMemcpyDeviceToHost, s));
-  CLAIR_CUDA(cudaStreamSynchronize(s));
-  st.singular += (long long)h[0];
-  st.sum_t3 += (double)h[1];
-  st.sum_t2 += (double)h[2];
-  st.sum_t += (double)h[3];
-  st.gathered += (long long)h[4];
+  if (own) {
+    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    CLAIR_CUDA(cudaMemcpyAsync(h, own, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    st.singular += (long long)h[0];
+    st.sum_t3 += (double)h[1];
+    st.sum_t2 += (double)h[2];
+    st.sum_t += (double)h[3];
+    st.gathered += (long long)h[4];
+  }
   for (int q = 0; q < nsides; ++q)
     for (int b = 0; b < LS_BUCKETS; ++b) st.hist[b] += counts_h[q][b];
   for (int q = 0; q < nsides; ++q) dfree(lists[q], s);
   dfree(counts, s);
-  dfree(nsing, s);
+  dfree(own, s);
   dfree(ticket, s);
+}
+
+void LocalStats::absorb_device(cudaStream_t s) {
+  if (!dev) return;
+  unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
+  CLAIR_CUDA(cudaMemcpyAsync(h, dev, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaMemsetAsync(dev, 0, sizeof(h), s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  singular += (long long)h[0];
+  empty += (long long)h[1];
+  sum_t3 += (double)h[2];
+  sum_t2 += (double)h[3];
+  sum_t += (double)h[4];
+  gathered += (long long)h[5];
 }
 
 void local_solves(const Csr& Ahat, const int* Zrp, const int* Zcol, const int* cpts, int nc,
@@ -1537,8 +1565,8 @@ void lsolve_config(int precision, int* kind_b1, int* kind_b3, int* blocks_per_sm
 // nc x k and B n x k (column-major); B null projects onto Q w = 0 (an update).
 void project_constraint(Csr& Wt, const signed char* cf, const double* Bc, int nc, const double* B,
                         int k, LocalStats& st, cudaStream_t s) {
-  unsigned long long* nempty = dalloc<unsigned long long>(1, s);
-  CLAIR_CUDA(cudaMemsetAsync(nempty, 0, sizeof(unsigned long long), s));
+  unsigned long long* nempty = st.dev ? st.dev + 1 : dalloc<unsigned long long>(1, s);
+  if (!st.dev) CLAIR_CUDA(cudaMemsetAsync(nempty, 0, sizeof(unsigned long long), s));
   if (Wt.rows && k == 1 && B) {
     constexpr int W = 1;  // FP64: one thread per row
     project_rows<W><<<ceil_div((long long)Wt.rows * W, 256), 256, 0, s>>>(
@@ -1548,6 +1576,7 @@ void project_constraint(Csr& Wt, const signed char* cf, const double* Bc, int nc
                                                            nc, B, k, nempty); ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
+  if (st.dev) return;
   unsigned long long h = 0;
   CLAIR_CUDA(cudaMemcpyAsync(&h, nempty, sizeof(h), cudaMemcpyDeviceToHost, s));
   CLAIR_CUDA(cudaStreamSynchronize(s));
@@ -1631,8 +1660,7 @@ void transfer_diag(const Csr& Ahat, const signed char* cf, const int* cpts, Csr&
   project_constraint(Zt, cf, Bc, nc, B, k, st, s);
   scatter_vals(Zt.val, perm, Z.val, Z.nnz, s);
   double* zbar = dalloc<double>(std::max(Z.nnz, 1), s);
-  long long sing_dummy = 0;
-  (void)sing_dummy;
+  unsigned long long* scratch6 = dalloc<unsigned long long>(6, s);
   for (int it = 0; it < iterations; ++it) {
     if (nc) {
       diag_update<<<ceil_div((long long)nc * 32, 256), 256, 0, s>>>(
@@ -1641,6 +1669,7 @@ void transfer_diag(const Csr& Ahat, const signed char* cf, const int* cpts, Csr&
     CLAIR_LAUNCHED();
     gather_vals(zbar, perm, Zt.val, Z.nnz, s);
     LocalStats discard;  // empty F rows are counted once, by the first projection
+    discard.dev = scratch6;
     project_constraint(Zt, cf, Bc, nc, nullptr, k, discard, s);
     scatter_vals(Zt.val, perm, zbar, Z.nnz, s);
     if (Z.nnz) {
@@ -1649,6 +1678,7 @@ void transfer_diag(const Csr& Ahat, const signed char* cf, const int* cpts, Csr&
     CLAIR_LAUNCHED();
   }
   gather_vals(Z.val, perm, Zt.val, Z.nnz, s);
+  dfree(scratch6, s);
   dfree(zbar, s);
   dfree(Bc, s);
   dfree(perm, s);

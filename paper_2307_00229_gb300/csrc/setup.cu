@@ -449,22 +449,30 @@ void aggregate_members(const int* agg, int n, int nc, int** rp_out, int** member
 constexpr int PT_CAP = 1024;
 constexpr int PT_WARPS = 4;
 
-__device__ __forceinline__ int pt_hash(int key) {
-  return (int)(((unsigned)key * 2654435761u) & (unsigned)(PT_CAP - 1));
+__device__ __forceinline__ int pt_hash(int key, int cap) {
+  return (int)(((unsigned)key * 2654435761u) & (unsigned)(cap - 1));
 }
 
-__device__ __forceinline__ void pt_insert(int* keys, int key, int* fresh, int* err) {
-  int h = pt_hash(key);
-  for (int probe = 0; probe < PT_CAP; ++probe) {
+// cap: the row's table size, a power of two (32 .. PT_CAP) at least twice an upper bound
+// of the row's pattern size, so clearing and compacting cost what the row needs
+__device__ __forceinline__ void pt_insert(int* keys, int cap, int key, int* fresh, int* err) {
+  int h = pt_hash(key, cap);
+  for (int probe = 0; probe < cap; ++probe) {
     int prev = atomicCAS(&keys[h], -1, key);
     if (prev == -1) {
       ++*fresh;
       return;
     }
     if (prev == key) return;
-    h = (h + 1) & (PT_CAP - 1);
+    h = (h + 1) & (cap - 1);
   }
   atomicExch(err, 1);
+}
+
+__device__ __forceinline__ int pt_cap_for(int bound) {
+  int cap = 32;
+  while (cap < PT_CAP && cap < 2 * bound) cap <<= 1;
+  return cap;
 }
 
 // Second hop for up to 32 first-hop rows at once: lane q holds row q's start and length
@@ -474,7 +482,7 @@ __device__ __forceinline__ void pt_insert(int* keys, int key, int* fresh, int* e
 __device__ __forceinline__ void pt_second_hop(int start, int len, int lane, int* P, int* S,
                                               const int* __restrict__ Wcol,
                                               const unsigned char* __restrict__ sW,
-                                              const signed char* __restrict__ cf, int* K,
+                                              const signed char* __restrict__ cf, int* K, int cap,
                                               int* fresh, int* err) {
   int incl = len;
 #pragma unroll
@@ -494,7 +502,7 @@ __device__ __forceinline__ void pt_second_hop(int start, int len, int lane, int*
       if (P[mid] <= f) lo = mid; else hi = mid;
     }
     const int e = S[lo] + (f - P[lo]);
-    if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], fresh, err);
+    if (sW[e] && !cf[Wcol[e]]) pt_insert(K, cap, Wcol[e], fresh, err);
   }
   __syncwarp();  // P and S are rewritten by the next call
 }
@@ -513,15 +521,34 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
   const int r = blockIdx.x * PT_WARPS + w;
   if (r >= nc) return;  // warp-uniform
   int* K = keys[w];
-  for (int t = lane; t < PT_CAP; t += 32) K[t] = -1;
-  __syncwarp();
   const int i = cpts[r];
+  // upper bound of the row's pattern: the base points plus every second-hop candidate
+  int bound = 0;
+  if (!AGG) {
+    for (int e = Wrp[i] + lane; e < Wrp[i + 1]; e += 32) {
+      bound += 1;
+      if (degree >= 2) {
+        const int k = Wcol[e];
+        if (sW[e] && !cf[k]) bound += Wrp[k + 1] - Wrp[k];
+      }
+    }
+  } else {
+    for (int m = Mrp[r] + lane; m < Mrp[r + 1]; m += 32) {
+      bound += 1;
+      if (degree >= 2) bound += Wrp[Mcol[m] + 1] - Wrp[Mcol[m]];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bound += __shfl_xor_sync(0xffffffffu, bound, o);
+  const int cap = pt_cap_for(bound + 1);
+  for (int t = lane; t < cap; t += 32) K[t] = -1;
+  __syncwarp();
   int fresh = 0;
-  if (lane == 0) pt_insert(K, i, &fresh, err);
+  if (lane == 0) pt_insert(K, cap, i, &fresh, err);
   if (!AGG) {
     // T column i = i and the F-points j with S_ji
     for (int e = Wrp[i] + lane; e < Wrp[i + 1]; e += 32)
-      if (sW[e] && !cf[Wcol[e]]) pt_insert(K, Wcol[e], &fresh, err);
+      if (sW[e] && !cf[Wcol[e]]) pt_insert(K, cap, Wcol[e], &fresh, err);
     if (degree >= 2) {
       // second hop from every first-hop F-point, 32 first-hop points at a time
       const int e_end = Wrp[i + 1];
@@ -535,13 +562,13 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
             len = Wrp[k + 1] - start;
           }
         }
-        pt_second_hop(start, len, lane, hop_pre[w], hop_start[w], Wcol, sW, cf, K, &fresh, err);
+        pt_second_hop(start, len, lane, hop_pre[w], hop_start[w], Wcol, sW, cf, K, cap, &fresh, err);
       }
     }
   } else {
     // T column i = the members of aggregate r (its root i included)
     for (int m = Mrp[r] + lane; m < Mrp[r + 1]; m += 32)
-      if (!cf[Mcol[m]]) pt_insert(K, Mcol[m], &fresh, err);
+      if (!cf[Mcol[m]]) pt_insert(K, cap, Mcol[m], &fresh, err);
     if (degree >= 2) {
       // second hop: F-points j with S_jk for every member k, 32 members at a time
       const int m_end = Mrp[r + 1];
@@ -553,7 +580,7 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
           start = Wrp[k];
           len = Wrp[k + 1] - start;
         }
-        pt_second_hop(start, len, lane, hop_pre[w], hop_start[w], Wcol, sW, cf, K, &fresh, err);
+        pt_second_hop(start, len, lane, hop_pre[w], hop_start[w], Wcol, sW, cf, K, cap, &fresh, err);
       }
     }
   }
@@ -566,7 +593,7 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
   }
   // compact occupied slots in place (reads of a chunk precede its writes), then rank-sort
   int total = 0;
-  for (int c = 0; c < PT_CAP; c += 32) {
+  for (int c = 0; c < cap; c += 32) {
     const int v = K[c + lane];
     const unsigned occ = __ballot_sync(0xffffffffu, v >= 0);
     __syncwarp();

@@ -220,16 +220,54 @@ __global__ void scan_apply(const int* __restrict__ in, int n, const long long* _
   if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
 }
 
+// The whole scan in one block (n <= SCAN_TILE, every coarse level): one launch instead of
+// three; writes the overflow flag whether or not it is set.
+__global__ void scan_single(const int* __restrict__ in, int n, int* __restrict__ out,
+                            int* __restrict__ overflow) {
+  __shared__ long long sh[32];
+  __shared__ int s_ovf;
+  if (threadIdx.x == 0) s_ovf = 0;
+  long long loc[SCAN_ITEMS];
+  long long acc = 0;
+  const int base = threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int i = base + k;
+    loc[k] = i < n ? in[i] : 0;
+    acc += loc[k];
+  }
+  long long run = block_inclusive_scan(acc, sh) - acc;  // (its barriers order s_ovf = 0)
+  bool ov = false;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int i = base + k;
+    run += loc[k];
+    if (i < n) {
+      ov = ov || run > 0x7fffffffLL;
+      out[i + 1] = (int)run;
+    }
+  }
+  if (ov) s_ovf = 1;
+  if (threadIdx.x == 0) out[0] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) *overflow = s_ovf;
+}
+
 long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s, bool want_total,
                          const int* extra_dev, int* extra_host) {
   const int nb = std::max(1, ceil_div(n, SCAN_TILE));
   CLAIR_REQUIRE(nb <= SCAN_TILE, CLAIR_ERR_CAPACITY, "scan of %d items exceeds capacity", n);
-  long long* sums = dalloc<long long>(nb + 1, s);
+  long long* sums = nullptr;
   int* ovf = dalloc<int>(1, s);
-  CLAIR_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
-  scan_block_sums<<<nb, SCAN_THREADS, 0, s>>>(in, n, sums); ::clair::count_launch();
-  scan_sums<<<1, SCAN_THREADS, 0, s>>>(sums, nb); ::clair::count_launch();
-  scan_apply<<<nb, SCAN_THREADS, 0, s>>>(in, n, sums, out, ovf); ::clair::count_launch();
+  if (nb == 1) {
+    scan_single<<<1, SCAN_THREADS, 0, s>>>(in, n, out, ovf); ::clair::count_launch();
+  } else {
+    sums = dalloc<long long>(nb + 1, s);
+    CLAIR_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+    scan_block_sums<<<nb, SCAN_THREADS, 0, s>>>(in, n, sums); ::clair::count_launch();
+    scan_sums<<<1, SCAN_THREADS, 0, s>>>(sums, nb); ::clair::count_launch();
+    scan_apply<<<nb, SCAN_THREADS, 0, s>>>(in, n, sums, out, ovf); ::clair::count_launch();
+  }
   CLAIR_LAUNCHED();
   long long total = 0;
   if (want_total) {
