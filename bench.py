@@ -685,9 +685,15 @@ def run_recirc3d(args):
                             "degree": 2, "eps": 1e-3, "precision": "mixed"},
           {"r_rows": int(sts.r_rows), "levels": sts.levels, "operator_complexity": sts.operator_complexity,
            "phases_ms": {n_: sts.phase_ms[i] for i, n_ in enumerate(cl.PHASES[:8])},
+           "t_hist": list(sts.t_hist)[:7],
+           "levels_ms": [{"n": int(sts.n[k]), "span": round(sts.level_span_ms[k], 2),
+                          "local_solve": round(sts.level_phase_ms[k][4], 2)}
+                         for k in range(sts.levels)],
            "solve": {"status": st, "iterations": its, "relres": rel,
                      "note": "the paper's aggregation variant did not converge at alpha <= 1e-3 either"},
            "fc_fallback": {"time_to_1e8_ms": fc_ms, "setup_ms": fsts.setup_ms, "status": fst,
+                           "t_hist": list(fsts.t_hist)[:7],
+                           "phases_ms": {n_: fsts.phase_ms[i] for i, n_ in enumerate(cl.PHASES[:8])},
                            "iterations": fits, "relres": frel, "levels": fsts.levels,
                            "operator_complexity": fsts.operator_complexity,
                            "r_rows": int(fsts.r_rows)}})

@@ -275,7 +275,7 @@ void seg_cg_beta_launch(int nseg, const double* rr, const double* tol, const dou
 // algorithmic work: sum over systems of T^3, T^2 and T, and the gathered A entries.
 struct LocalStats {
   long long singular = 0, empty = 0;
-  long long hist[6] = {0, 0, 0, 0, 0, 0};
+  long long hist[7] = {0, 0, 0, 0, 0, 0, 0};
   double sum_t3 = 0, sum_t2 = 0, sum_t = 0;
   long long gathered = 0;
   // execution configuration of the last persistent local-solve launch

@@ -393,8 +393,9 @@ struct SideStream {
   cudaStream_t s2 = nullptr;
   cudaEvent_t fork = nullptr, split = nullptr, join = nullptr;
   SideStream() {
-    // the weight chain is the longer branch on the fine levels: its blocks go first, the
-    // splitting, patterns and local solves use the SMs it leaves
+    // the weight chain's blocks go first, the splitting, patterns and local solves use the
+    // SMs it leaves (measured: the reverse order, the main stream first, lengthens every
+    // level by its wait for the slower weight chain at the join)
     int lo = 0, hi = 0;
     CLAIR_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     CLAIR_CUDA(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi));
@@ -1576,7 +1577,7 @@ clair_status clair_stats(clair_h h, clair_stats_t* o) {
     o->p_cols += L.nc;
   }
   o->operator_complexity = sum / nnz0;
-  for (int b = 0; b < 6; ++b) o->t_hist[b] = h->st.hist[b];
+  for (int b = 0; b < 7; ++b) o->t_hist[b] = h->st.hist[b];
   o->singular_blocks = h->st.singular;
   o->empty_constraints = h->st.empty;
   o->setup_ms = h->setup_ms;

@@ -27,12 +27,16 @@
 
 namespace clair {
 
-// Solvable buckets: T in [1,8], (8,16], (16,32], (32,64], (64,128], (128,4096]; bucket 6
-// counts systems larger than LS_TBIG (refused).
-constexpr int LS_BUCKETS = 6;
+// Solvable buckets: T in [0,8], (8,16], (16,32], (32,64], (64,128], (128,tmed] (one CTA
+// per system, the tile in shared memory: tmed = LS_TMED32 in FP32, LS_TMED64 in FP64),
+// (tmed,4096] (global tile); bucket 7 counts systems larger than LS_TBIG (refused).
+constexpr int LS_BUCKETS = 7;
 constexpr int LS_TBIG = 4096;
-__host__ __device__ inline int ls_bucket(int T) {
-  return T <= 8 ? 0 : T <= 16 ? 1 : T <= 32 ? 2 : T <= 64 ? 3 : T <= 128 ? 4 : T <= LS_TBIG ? 5 : 6;
+constexpr int LS_TMED32 = 224;  // 224 x 228 floats: 204 KB of shared memory
+constexpr int LS_TMED64 = 160;  // 160 x 162 doubles: 207 KB
+__host__ __device__ inline int ls_bucket(int T, int tmed) {
+  return T <= 8 ? 0 : T <= 16 ? 1 : T <= 32 ? 2 : T <= 64 ? 3 : T <= 128 ? 4
+       : T <= tmed ? 5 : T <= LS_TBIG ? 6 : 7;
 }
 
 // Position of column c in the sorted list z[0..T-1], or -1.
@@ -289,14 +293,14 @@ struct alignas(16) TeamSmem {
   Real tile[TMAX * cta_pitch<Real, TMAX>()];
   Real rhs[TMAX];
   Real xs[TMAX];
-  Real red_v[NW];      // FP64: largest |value| of each warp
+  Real red_v[2][NW];      // FP64: largest |value| of each warp (by step parity)
   int zl[TMAX];
   int steprow[TMAX];
   int pre[TMAX + 1];
-  int rs[TMAX];        // start of each pattern row in Ahat
+  int rs[TMAX];           // start of each pattern row in Ahat
   int wsum[NW];
-  unsigned red_k[NW];  // FP32: largest pivot key of each warp
-  int red_w[NW];       // and its row
+  unsigned red_k[2][NW];  // FP32: largest pivot key of each warp (by step parity)
+  int red_w[2][NW];       // and its row
   int s_d, s_sing;
 };
 
@@ -397,7 +401,12 @@ __device__ __forceinline__ void team_body(const int* __restrict__ Arp, const int
   bool done = t >= T;
   int mystep = -1;
   team_sync<KIND, TMAX>(bar_id);
+  // One barrier per step: each thread updates only its own row and right-hand side, and
+  // the barrier after the next step's candidate posts orders the pivot owner's last update
+  // before anyone reads the pivot row; the candidate arrays alternate by step parity, so
+  // a fast thread's next post cannot overwrite what a slow one is still reading.
   for (int k = 0; k < T; ++k) {
+    const int par = k & 1;
     // pivot: largest |a| of column k among the rows not yet eliminated, lowest row on
     // ties; each warp posts its candidate, every thread then reads the team's
     const Real rk = row[k];
@@ -407,8 +416,8 @@ __device__ __forceinline__ void team_body(const int* __restrict__ Arp, const int
       const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
       const unsigned bal = __ballot_sync(0xffffffffu, key == wmax);
       if (lane == 0) {
-        sm.red_k[wid] = wmax;
-        sm.red_w[wid] = wid * 32 + __ffs(bal) - 1;
+        sm.red_k[par][wid] = wmax;
+        sm.red_w[par][wid] = wid * 32 + __ffs(bal) - 1;
       }
     } else {
       Real v = done ? Real(-1) : (rk < 0 ? -rk : rk);
@@ -423,27 +432,27 @@ __device__ __forceinline__ void team_body(const int* __restrict__ Arp, const int
         }
       }
       if (lane == 0) {
-        sm.red_v[wid] = v;
-        sm.red_w[wid] = who;
+        sm.red_v[par][wid] = v;
+        sm.red_w[par][wid] = who;
       }
     }
     team_sync<KIND, TMAX>(bar_id);
-    int piv = sm.red_w[0];
+    int piv = sm.red_w[par][0];
     if constexpr (sizeof(Real) == 4) {
-      unsigned bk = sm.red_k[0];
+      unsigned bk = sm.red_k[par][0];
 #pragma unroll
       for (int w = 1; w < NW; ++w)
-        if (sm.red_k[w] > bk) {  // warps hold increasing rows: strict keeps the lowest
-          bk = sm.red_k[w];
-          piv = sm.red_w[w];
+        if (sm.red_k[par][w] > bk) {  // warps hold increasing rows: strict keeps the lowest
+          bk = sm.red_k[par][w];
+          piv = sm.red_w[par][w];
         }
     } else {
-      Real bv = sm.red_v[0];
+      Real bv = sm.red_v[par][0];
 #pragma unroll
       for (int w = 1; w < NW; ++w)
-        if (sm.red_v[w] > bv) {
-          bv = sm.red_v[w];
-          piv = sm.red_w[w];
+        if (sm.red_v[par][w] > bv) {
+          bv = sm.red_v[par][w];
+          piv = sm.red_w[par][w];
         }
     }
     const Real* prow = tile + piv * PITCH;
@@ -475,8 +484,8 @@ __device__ __forceinline__ void team_body(const int* __restrict__ Arp, const int
       }
       rhs[t] -= l * rhs[piv];
     }
-    team_sync<KIND, TMAX>(bar_id);
   }
+  team_sync<KIND, TMAX>(bar_id);  // the last updates and steprow before back substitution
   // back substitution: one barrier per step suffices, each thread updates only its own
   // right-hand side and every x_k has its own slot
   for (int k = T - 1; k >= 0; --k) {
@@ -998,13 +1007,13 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
 // Writes nothing but the lists and counters, so a caller may still refuse the call after
 // reading the counts (a row with T = 0, the identity entry alone, goes to bucket 0, whose
 // kernel writes that entry).
-__global__ void bucket_rows(const int* __restrict__ Zrp, int nc, int* __restrict__ lists,
+__global__ void bucket_rows(const int* __restrict__ Zrp, int nc, int tmed, int* __restrict__ lists,
                             int* __restrict__ counts, const int* __restrict__ Zcol,
                             const int* __restrict__ cpts, const int* __restrict__ Arp,
                             int* __restrict__ too_big, unsigned long long* __restrict__ work) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int T = r < nc ? Zrp[r + 1] - Zrp[r] - 1 : -1;
-  const int b = T >= 0 ? ls_bucket(T) : -1;
+  const int b = T >= 0 ? ls_bucket(T, tmed) : -1;
   if (b >= LS_BUCKETS) atomicAdd(too_big, 1);
   if (b == LS_BUCKETS - 1) atomicMax(too_big + 1, T);  // largest T of the big bucket
   unsigned long long t3 = 0, t2 = 0, t1 = 0, g = 0;
@@ -1246,13 +1255,32 @@ int coarse_points(const signed char* cf, int n, int** cpts_out, cudaStream_t s) 
 // vals: Ahat's values in the gather's type (a float copy in MIXED mode, so each value is
 // converted once instead of once per local system it appears in; converting the copy
 // gives the same floats).
+// Size classes of the global-tile systems and the tile memory one launch may take (more
+// concurrent tiles than this spill out of L2 and the launch slows down; measured on the
+// 3D aggregation hierarchies).
+constexpr int LB_CLASSES = 5;
+constexpr size_t LB_BUDGET = 256ull << 20;
+
+// cls[c * nb + k]: the systems of list[0 .. nb) with T <= 256 << c and above the previous
+// class's limit, in list order per class (one atomic per system: these are rare)
+__global__ void class_big(const int* __restrict__ list, int nb, const int* __restrict__ Zrp,
+                          int* __restrict__ cls, int* __restrict__ ccount) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nb) return;
+  const int r = list[k];
+  const int T = Zrp[r + 1] - Zrp[r] - 1;
+  int c = 0;
+  while (c < LB_CLASSES - 1 && T > (256 << c)) ++c;
+  cls[(size_t)c * nb + atomicAdd(&ccount[c], 1)] = r;
+}
+
 template <class Real, class VT>
 static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const int* Zcol,
                           const int* cpts, const int* lists, const int* counts_h, int nc,
                           double* Zval, unsigned long long* nsing, cudaStream_t s,
-                          Real* big_scratch = nullptr, int big_pitch = 0, int big_chunk = 0,
-                          int first_bucket = 0) {
+                          bool big_scratch_forbidden = false, int first_bucket = 0) {
   // the shared-memory limits above 48 KB are per-device function attributes
+  constexpr int TMED = sizeof(Real) == 8 ? LS_TMED64 : LS_TMED32;
   once_per_device((const void*)lsolve_cta<Real, VT, 128>, [] {
     CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, VT, 64>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1260,6 +1288,9 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
     CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, VT, 128>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)cta_smem<Real, 128>()));
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, VT, TMED>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)cta_smem<Real, TMED>()));
     CLAIR_CUDA(cudaFuncSetAttribute(lsolve_big<Real, VT>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)big_smem<Real>(LS_TBIG)));
@@ -1282,32 +1313,44 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
   if (counts_h[4])
     lsolve_cta<Real, VT, 128><<<counts_h[4], 128, cta_smem<Real, 128>(), s>>>(
         Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 4LL * nc, Zval, nsing); ::clair::count_launch();
-  if (counts_h[5]) {
-    CLAIR_REQUIRE(big_scratch && big_chunk > 0, CLAIR_ERR_CAPACITY,
-                  "%d local systems larger than 128 unknowns (this entry point solves T <= 128)",
-                  counts_h[5]);
-    for (int off = 0; off < counts_h[5]; off += big_chunk) {
-      const int cnt = std::min(big_chunk, counts_h[5] - off);
-      lsolve_big<Real, VT><<<cnt, LB_THREADS, big_smem<Real>(big_pitch), s>>>(
-          Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 5LL * nc + off, Zval, nsing,
-          big_scratch, big_pitch); ::clair::count_launch();
+  if (counts_h[5] && first_bucket <= 5) {
+    lsolve_cta<Real, VT, TMED><<<counts_h[5], TMED, cta_smem<Real, TMED>(), s>>>(
+        Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 5LL * nc, Zval, nsing); ::clair::count_launch();
+  }
+  if (counts_h[6]) {
+    // by size class (T up to 256, 512, ..., 4096), each with its own tile pitch, so a few
+    // systems near 4096 unknowns do not shrink the batch of all the others
+    CLAIR_REQUIRE(!big_scratch_forbidden, CLAIR_ERR_CAPACITY,
+                  "%d local systems larger than %d unknowns need a tile buffer", counts_h[6], TMED);
+    const int nb = counts_h[6];
+    int* cls = dalloc<int>((size_t)LB_CLASSES * nb, s);
+    int* ccount = dalloc<int>(LB_CLASSES, s);
+    CLAIR_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int) * LB_CLASSES, s));
+    class_big<<<ceil_div(nb, 256), 256, 0, s>>>(lists + 6LL * nc, nb, Zrp, cls, ccount); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+    int ch[LB_CLASSES];
+    CLAIR_CUDA(cudaMemcpyAsync(ch, ccount, sizeof(ch), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < LB_CLASSES; ++c) {
+      if (!ch[c]) continue;
+      const int pitch = std::min(LS_TBIG, 256 << c);
+      const size_t tile = (size_t)pitch * pitch * sizeof(Real);
+      const int chunk = (int)std::max<size_t>(1, std::min<size_t>(ch[c], LB_BUDGET / tile));
+      Real* tiles = dalloc<Real>((size_t)chunk * pitch * pitch, s);
+      for (int off = 0; off < ch[c]; off += chunk) {
+        const int cnt = std::min(chunk, ch[c] - off);
+        lsolve_big<Real, VT><<<cnt, LB_THREADS, big_smem<Real>(pitch), s>>>(
+            Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, cls + (size_t)c * nb + off, Zval, nsing,
+            tiles, pitch); ::clair::count_launch();
+      }
+      dfree(tiles, s);
     }
+    dfree(cls, s);
+    dfree(ccount, s);
   }
   CLAIR_LAUNCHED();
 }
 
-// Scratch for the large-system bucket: `chunk` tiles of pitch x pitch values, at most
-// 256 MiB, pitch = the bucket's largest T.
-template <class Real>
-static Real* big_tiles(const int* counts_h, int& pitch, int& chunk, cudaStream_t s) {
-  pitch = 0;
-  chunk = 0;
-  if (!counts_h[5]) return nullptr;
-  pitch = counts_h[LS_BUCKETS + 1];
-  const size_t tile = (size_t)pitch * pitch * sizeof(Real);
-  chunk = (int)std::max<size_t>(1, std::min<size_t>(counts_h[5], (256ull << 20) / tile));
-  return dalloc<Real>((size_t)chunk * pitch * pitch, s);
-}
 
 // ---- execution configuration of the persistent launch, per device and precision -------
 struct LsolveConfig {
@@ -1437,7 +1480,8 @@ void local_solves_multi(const SideIn* sides, int nsides, const int* cpts, int pr
     const SideIn& S = sides[q];
     lists[q] = dalloc<int>((long long)LS_BUCKETS * std::max(S.nc, 1), s);
     int* cq = counts + q * (LS_BUCKETS + 2);
-    if (S.nc) bucket_rows<<<ceil_div(S.nc, 256), 256, 0, s>>>(S.Zrp, S.nc, lists[q], cq, S.Zcol, cpts,
+    const int tmed = precision == CLAIR_MIXED ? LS_TMED32 : LS_TMED64;
+    if (S.nc) bucket_rows<<<ceil_div(S.nc, 256), 256, 0, s>>>(S.Zrp, S.nc, tmed, lists[q], cq, S.Zcol, cpts,
                                                              S.Ahat->rowptr, cq + LS_BUCKETS,
                                                              work); ::clair::count_launch();
   }
@@ -1482,11 +1526,8 @@ void local_solves_multi(const SideIn* sides, int nsides, const int* cpts, int pr
       persistent_launch<Real, VT>(sa, nsides, counts_h, cfg, ticket, nsing, s);
       for (int q = 0; q < nsides; ++q) {
         const SideIn& S = sides[q];
-        int pitch, chunk;
-        Real* tiles = big_tiles<Real>(counts_h[q], pitch, chunk, s);
         launch_solves<Real, VT>(*S.Ahat, vals[q], S.Zrp, S.Zcol, cpts, lists[q], counts_h[q], S.nc,
-                                S.Zval, nsing, s, tiles, pitch, chunk, /*first_bucket=*/4);
-        dfree(tiles, s);
+                                S.Zval, nsing, s, false, /*first_bucket=*/4);
       }
     };
     if (precision == CLAIR_MIXED) {
@@ -1787,7 +1828,8 @@ static void local_weights_noalloc(int n, const Csr& Ahat, const signed char* cf,
   // bucketed local solves (counters start at zero on every call)
   CLAIR_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(int) * (LS_BUCKETS + 2), s));
   CLAIR_CUDA(cudaMemsetAsync(b.work, 0, 5 * sizeof(unsigned long long), s));
-  if (nc) bucket_rows<<<ceil_div(nc, 256), 256, 0, s>>>(Z.rowptr, nc, b.lists, b.counts, Z.col,
+  const int tmed = precision == CLAIR_MIXED ? LS_TMED32 : LS_TMED64;
+  if (nc) bucket_rows<<<ceil_div(nc, 256), 256, 0, s>>>(Z.rowptr, nc, tmed, b.lists, b.counts, Z.col,
                                                         b.cpts, Ahat.rowptr, b.counts + LS_BUCKETS,
                                                         b.work + 1); ::clair::count_launch();
   CLAIR_LAUNCHED();
@@ -1796,17 +1838,16 @@ static void local_weights_noalloc(int n, const Csr& Ahat, const signed char* cf,
   CLAIR_CUDA(cudaStreamSynchronize(s));
   // every refusal comes before the first write to Z_val: systems above 128 unknowns need
   // a per-call tile buffer, which this entry point does not have
-  CLAIR_REQUIRE(counts_h[LS_BUCKETS] == 0 && counts_h[LS_BUCKETS - 1] == 0, CLAIR_ERR_CAPACITY,
-                "%d local systems larger than 128 unknowns (the largest has %d; this entry "
-                "point solves T <= 128, use clair_local_weights)",
-                counts_h[LS_BUCKETS] + counts_h[LS_BUCKETS - 1],
-                counts_h[LS_BUCKETS] ? LS_TBIG + 1 : counts_h[LS_BUCKETS + 1]);
+  const int over128 = counts_h[5] + counts_h[6] + counts_h[7];
+  CLAIR_REQUIRE(over128 == 0, CLAIR_ERR_CAPACITY,
+                "%d local systems larger than 128 unknowns (this entry point solves T <= 128, "
+                "use clair_local_weights)", over128);
   if (precision == CLAIR_MIXED)
     launch_solves<float, double>(Ahat, Ahat.val, Z.rowptr, Z.col, b.cpts, b.lists, counts_h, nc,
-                                 Z.val, b.work, s);
+                                 Z.val, b.work, s, /*big_scratch_forbidden=*/true);
   else
     launch_solves<double, double>(Ahat, Ahat.val, Z.rowptr, Z.col, b.cpts, b.lists, counts_h, nc,
-                                  Z.val, b.work, s);
+                                  Z.val, b.work, s, /*big_scratch_forbidden=*/true);
   // column view of the weights, projection, values back into the row view
   Csr Zt;
   Zt.rowptr = b.zt_rowptr;
