@@ -565,6 +565,7 @@ def run_batch(args):
         ms, times, (st, its, rel, sts) = _events_ms(step, steps, args.warmup, flush)
         res[name] = {"ms": ms, "times": times, "its": its, "rel": rel, "status": st,
                      "setup_ms": sts.setup_ms, "rows": int(sts.r_rows), "levels": sts.levels,
+                     "cycle64_from": sts.cycle64_from, "fp64_cycle_from": int(sts.fp64_cycle_from),
                      "launches": (cl.clair_kernel_launches() - l0) // (steps + args.warmup),
                      "phases_ms": {n_: sts.phase_ms[i] for i, n_ in enumerate(cl.PHASES[:8])},
                      "solve_phases_ms": {n_: sts.solve_phase_ms[i] for i, n_ in enumerate(cl.PHASES) if i >= 8}}
@@ -594,6 +595,7 @@ def run_batch(args):
            "sides": [pr.meta["nside"] for pr in probs], "coarsen": "FC", "degree": 2,
            "precision": "mixed (FP32 local solves and V-cycle, FP64 FGMRES)"},
           {"iterations": m["its"], "worst_instance_relres": m["rel"], "status": m["status"],
+           "cycle64_from": m["cycle64_from"], "fp64_cycle_from": m["fp64_cycle_from"],
            "setup_ms": m["setup_ms"], "r_rows": m["rows"], "levels": m["levels"],
            "phases_ms": m["phases_ms"], "solve_phases_ms": m["solve_phases_ms"],
            "gpu_launches": m["launches"],

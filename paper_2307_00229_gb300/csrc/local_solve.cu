@@ -1331,20 +1331,45 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
     int ch[LB_CLASSES];
     CLAIR_CUDA(cudaMemcpyAsync(ch, ccount, sizeof(ch), cudaMemcpyDeviceToHost, s));
     CLAIR_CUDA(cudaStreamSynchronize(s));
+    // the classes run side by side, one stream each (forked from and joined back to s):
+    // a launch lasts as long as its slowest system, so classes in sequence would add up
+    struct Fork {
+      cudaStream_t st[LB_CLASSES] = {};
+      cudaEvent_t ev[LB_CLASSES + 1] = {};
+      ~Fork() {
+        for (cudaStream_t x : st)
+          if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t e : ev)
+          if (e) cudaEventDestroy(e);
+      }
+    } fk;
+    Real* tiles[LB_CLASSES] = {};
+    int chunk[LB_CLASSES] = {}, pitch[LB_CLASSES] = {};
     for (int c = 0; c < LB_CLASSES; ++c) {
       if (!ch[c]) continue;
-      const int pitch = std::min(LS_TBIG, 256 << c);
-      const size_t tile = (size_t)pitch * pitch * sizeof(Real);
-      const int chunk = (int)std::max<size_t>(1, std::min<size_t>(ch[c], LB_BUDGET / tile));
-      Real* tiles = dalloc<Real>((size_t)chunk * pitch * pitch, s);
-      for (int off = 0; off < ch[c]; off += chunk) {
-        const int cnt = std::min(chunk, ch[c] - off);
-        lsolve_big<Real, VT><<<cnt, LB_THREADS, big_smem<Real>(pitch), s>>>(
-            Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, cls + (size_t)c * nb + off, Zval, nsing,
-            tiles, pitch); ::clair::count_launch();
-      }
-      dfree(tiles, s);
+      pitch[c] = std::min(LS_TBIG, 256 << c);
+      const size_t tile = (size_t)pitch[c] * pitch[c] * sizeof(Real);
+      chunk[c] = (int)std::max<size_t>(1, std::min<size_t>(ch[c], LB_BUDGET / tile));
+      tiles[c] = dalloc<Real>((size_t)chunk[c] * pitch[c] * pitch[c], s);
     }
+    CLAIR_CUDA(cudaEventCreateWithFlags(&fk.ev[LB_CLASSES], cudaEventDisableTiming));
+    CLAIR_CUDA(cudaEventRecord(fk.ev[LB_CLASSES], s));
+    for (int c = 0; c < LB_CLASSES; ++c) {
+      if (!ch[c]) continue;
+      CLAIR_CUDA(cudaStreamCreateWithFlags(&fk.st[c], cudaStreamNonBlocking));
+      CLAIR_CUDA(cudaEventCreateWithFlags(&fk.ev[c], cudaEventDisableTiming));
+      CLAIR_CUDA(cudaStreamWaitEvent(fk.st[c], fk.ev[LB_CLASSES], 0));
+      for (int off = 0; off < ch[c]; off += chunk[c]) {
+        const int cnt = std::min(chunk[c], ch[c] - off);
+        lsolve_big<Real, VT><<<cnt, LB_THREADS, big_smem<Real>(pitch[c]), fk.st[c]>>>(
+            Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, cls + (size_t)c * nb + off, Zval, nsing,
+            tiles[c], pitch[c]); ::clair::count_launch();
+      }
+      CLAIR_CUDA(cudaEventRecord(fk.ev[c], fk.st[c]));
+      CLAIR_CUDA(cudaStreamWaitEvent(s, fk.ev[c], 0));
+    }
+    CLAIR_LAUNCHED();
+    for (int c = 0; c < LB_CLASSES; ++c) dfree(tiles[c], s);
     dfree(cls, s);
     dfree(ccount, s);
   }
