@@ -36,7 +36,7 @@ F_PT = 0
 
 __all__ = [
     "C_PT", "F_PT", "Params", "lowbias32", "strength", "split_fc", "aggregate",
-    "arnoldi_rho", "relax", "relax_cff", "relax_ffc", "smooth_modes", "base_pattern",
+    "arnoldi", "arnoldi_rho", "relax", "relax_cff", "relax_ffc", "smooth_modes", "base_pattern",
     "clair_pattern", "clair_algorithm1", "clair_transfer", "Level", "Hierarchy",
     "build_hierarchy", "vcycle", "fgmres", "pcg", "operator_complexity", "work_per_digit",
     "solve", "csr_of",
@@ -234,8 +234,13 @@ def aggregate(A, theta: float) -> tuple[np.ndarray, np.ndarray]:
 # Relaxation weight and relaxation (Section 4: weight 1/rho(D^-1 A), rho from 15 Arnoldi
 # iterations; CFF pre- and FFC post-smoothing; B smoothed by 5 CFF sweeps, Section 4.1)
 # --------------------------------------------------------------------------------------
-def arnoldi_rho(A, iters: int, seed: int) -> float:
-    """Spectral radius estimate of ``D^-1 A`` from ``iters`` Arnoldi steps (MGS)."""
+def arnoldi(A, iters: int, seed: int):
+    """``iters`` Arnoldi steps on ``D^-1 A`` (Section 4) from the seeded start vector, each new
+    vector orthogonalised against the basis by classical Gram-Schmidt applied twice, so the
+    basis stays orthonormal to working precision (a single Gram-Schmidt pass loses that on
+    the small, strongly non-normal coarse operators).  A step whose new vector has norm at
+    most 1e-10 of its norm before orthogonalisation ends the run (invariant subspace).
+    Returns (H, V, steps): H is (m + 1) x m upper Hessenberg, V holds the basis in rows."""
     A = csr_of(A)
     n = A.shape[0]
     dinv = 1.0 / A.diagonal()
@@ -248,14 +253,24 @@ def arnoldi_rho(A, iters: int, seed: int) -> float:
     for j in range(m):
         w = dinv * (A @ V[j])
         wnorm0 = np.linalg.norm(w)
-        for i in range(j + 1):
-            H[i, j] = V[i] @ w
-            w = w - H[i, j] * V[i]
+        Vj = V[: j + 1]
+        h1 = Vj @ w
+        w = w - Vj.T @ h1
+        h2 = Vj @ w
+        w = w - Vj.T @ h2
+        H[: j + 1, j] = h1 + h2
         H[j + 1, j] = np.linalg.norm(w)
         if H[j + 1, j] <= 1e-10 * wnorm0:
             steps = j + 1
             break
         V[j + 1] = w / H[j + 1, j]
+    return H, V, steps
+
+
+def arnoldi_rho(A, iters: int, seed: int) -> float:
+    """Spectral radius estimate of ``D^-1 A``: the largest Ritz value modulus of ``iters``
+    Arnoldi steps (Section 4)."""
+    H, _, steps = arnoldi(A, iters, seed)
     ritz = np.linalg.eigvals(H[:steps, :steps])
     return float(np.max(np.abs(ritz)))
 
