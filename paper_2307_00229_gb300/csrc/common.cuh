@@ -97,6 +97,11 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
   }                                                      \
   return CLAIR_OK;
 
+// Pinned host memory for small per-setup and per-solve buffers, recycled by size class
+// for the life of the process (returned with the size it was taken with).
+void* pinned_get(size_t bytes);
+void pinned_put(void* p, size_t bytes);
+
 // Number of SMs of the current device (cached per process).
 int sm_count();
 
@@ -194,7 +199,9 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s);
 // Removes entries whose value is exactly zero (structure follows the values).
 void drop_zeros(Csr& C, cudaStream_t s);
 // Inverse diagonal (error if a diagonal entry is missing or zero).
-void inverse_diagonal(const Csr& A, double* dinv, cudaStream_t s);
+// dinv = 1 / diag(A); rows with a missing, zero or nonfinite diagonal are an error, raised
+// here (bad_acc null, one host synchronisation) or counted into *bad_acc for the caller.
+void inverse_diagonal(const Csr& A, double* dinv, cudaStream_t s, int* bad_acc = nullptr);
 // Float copies.
 void to_float(const double* x, float* y, long long n, cudaStream_t s);
 void to_double(const float* x, double* y, long long n, cudaStream_t s);
@@ -213,6 +220,26 @@ void validate_csr(const int* rowptr, const int* col, int rows, int cols, int nnz
 void validate_cf(const signed char* cf, int n, cudaStream_t s);
 // *out = max(*out, max |x|) as the bits of a non-negative double (asynchronous).
 void absmax_into(const double* x, long long n, unsigned long long* out, cudaStream_t s);
+
+// Up to kMax (source, length) segments for one launch: FP64 -> FP32 copies (dst), or the
+// largest |x| of each segment folded into out[slot] (as the bits of a nonnegative double).
+struct SegList {
+  static constexpr int kMax = 48;
+  const double* src[kMax];
+  float* dst[kMax];
+  long long n[kMax];
+  int slot[kMax];
+  int count = 0;
+};
+// Collects segments and launches them kMax at a time (out null: conversions, else maxima).
+struct SegBatch {
+  SegBatch(cudaStream_t st, unsigned long long* o = nullptr) : s(st), out(o) {}
+  void add(const double* src, float* dst, long long n, int slot = 0);
+  void flush();
+  cudaStream_t s;
+  unsigned long long* out;
+  SegList cur;
+};
 // Nonfinite check over a buffer; returns true if all finite (synchronises).
 bool all_finite(const double* x, long long n, cudaStream_t s);
 

@@ -151,11 +151,6 @@ namespace clair {
 // this size that cancel to O(1) leave about 4).
 constexpr double kCycle64Weight = 1e3;
 
-static void to_float_copy(const double* x, float** y, long long n, cudaStream_t s) {
-  *y = dalloc<float>(n, s);
-  to_float(x, *y, n, s);
-}
-
 static void alloc_cycle(Level& L, cudaStream_t s) {
   const int n = L.n;
   L.b64 = dalloc<double>(n, s);
@@ -205,7 +200,7 @@ static void release_krylov(Krylov& k, cudaStream_t s) {
   dfree(k.its, s);
   if (k.host) {
     cudaStreamSynchronize(s);
-    cudaFreeHost(k.host);
+    pinned_put(k.host, sizeof(double) * 4);
   }
   k.host = nullptr;
   k.nrhs = 0;
@@ -440,6 +435,8 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
   SideStream ss;
   // one weight per level (per level and instance for a batch), on the device
   double* omega_dev = dalloc<double>((size_t)p.max_levels * ninst, s);
+  int* bad_coarse = dalloc<int>(1, s);  // coarse rows without a usable diagonal
+  CLAIR_CUDA(cudaMemsetAsync(bad_coarse, 0, sizeof(int), s));
   // main-stream marks at every level start (level spans for clair_stats)
   struct Marks {
     std::vector<cudaEvent_t> v;
@@ -459,7 +456,9 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
     if (active_clock()) active_clock()->set_level(k);
     marks.record(s);
     L.dinv = dalloc<double>(n, s);
-    inverse_diagonal(L.A, L.dinv, s);
+    // the fine operator is checked at once; a coarse operator's count is read with the
+    // weights after the last level
+    inverse_diagonal(L.A, L.dinv, s, k > 0 ? bad_coarse : nullptr);
     if (!batch) {
       if (n <= p.coarse_max || k + 1 >= p.max_levels) break;
     } else {
@@ -482,7 +481,9 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
     CLAIR_CUDA(cudaEventRecord(ss.fork, s));
     CLAIR_CUDA(cudaStreamWaitEvent(ss.s2, ss.fork, 0));
     double* om_k = omega_dev + (size_t)k * ninst;
-    {
+    // enqueued after the first splitting kernels, so that the main stream has work while
+    // the host issues the Arnoldi launches
+    auto enqueue_weight = [&]() {
       ClockScope clk(PH_WEIGHT, ss.s2);
       ritz.push_back(ritz_host_alloc(ninst));
       if (batch)
@@ -491,7 +492,7 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
       else
         arnoldi_weight(L.A, L.dinv, p.arnoldi_iters, p.seed + (uint64_t)k, om_k, ritz.back(),
                        ss.s2);
-    }
+    };
 
     Csr At;
     int* agg = nullptr;                           // aggregate of each point (Agg coarsening)
@@ -508,6 +509,7 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
       // coarsening strength S(A, theta_c): on A row-relative, on A^T via A's row maxima
       strength(L.A, rmaxA, p.theta_coarsen, 0, sA, s);
       strength(At, rmaxA, p.theta_coarsen, 1, sAt, s);
+      enqueue_weight();
       L.cf = dalloc<signed char>(n, s);
       if (k == 0 && cf_marker) {
         // the caller's splitting replaces step a2 on the fine level
@@ -669,28 +671,62 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
   CLAIR_CUDA(cudaEventRecord(ss.join, ss.s2));
   CLAIR_CUDA(cudaStreamWaitEvent(s, ss.join, 0));
   marks.record(s);
-  CLAIR_CUDA(cudaEventSynchronize(marks.v.back()));
-  for (size_t k = 0; k + 1 < marks.v.size() && k < 32; ++k) {
-    float ms = 0.f;
-    CLAIR_CUDA(cudaEventElapsedTime(&ms, marks.v[k], marks.v[k + 1]));
-    h->level_span_ms[k] = ms;
-  }
   if (active_clock()) active_clock()->set_level((int)h->lv.size() - 1);
+  ClockScope clk(PH_COARSE, s);
+  // MIXED: the smoothed mode vectors of nearly pure advection shrink by orders of
+  // magnitude per level, and the projected weights grow in proportion (1e13 seen); an FP32
+  // copy of such R and P loses everything to cancellation.  From the first level whose
+  // largest |R| or |P| weight exceeds kCycle64Weight on, the cycle runs in FP64.  The
+  // maxima, the weights and the coarse diagonal check come back in one read.
+  const int nl = (int)h->lv.size();
+  unsigned long long* wmax = dalloc<unsigned long long>(nl, s);
+  CLAIR_CUDA(cudaMemsetAsync(wmax, 0, sizeof(unsigned long long) * nl, s));
+  {
+    SegBatch mx(s, wmax);
+    for (int k = 0; k < nl; ++k) {
+      Level& L = h->lv[k];
+      if (!L.nc) continue;
+      mx.add(L.R.val, nullptr, L.R.nnz, k);
+      mx.add(L.P.val, nullptr, L.P.nnz, k);
+    }
+    mx.flush();
+  }
   {
     std::vector<double> om((size_t)p.max_levels * ninst, 1.0);
+    std::vector<unsigned long long> hw(nl);
+    int nbad = 0;
     CLAIR_CUDA(cudaMemcpyAsync(om.data(), omega_dev, sizeof(double) * om.size(),
                                cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaMemcpyAsync(&nbad, bad_coarse, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaMemcpyAsync(hw.data(), wmax, sizeof(unsigned long long) * nl,
+                               cudaMemcpyDeviceToHost, s));
     CLAIR_CUDA(cudaStreamSynchronize(s));
+    dfree(bad_coarse, s);
+    dfree(wmax, s);
+    CLAIR_REQUIRE(nbad == 0, CLAIR_ERR_ARG,
+                  "%d coarse rows with a missing, zero or nonfinite diagonal", nbad);
+    for (size_t k = 0; k + 1 < marks.v.size() && k < 32; ++k) {
+      float ms = 0.f;
+      CLAIR_CUDA(cudaEventElapsedTime(&ms, marks.v[k], marks.v[k + 1]));
+      h->level_span_ms[k] = ms;
+    }
     for (size_t k = 0; k < h->lv.size(); ++k) {
       Level& L = h->lv[k];
       if (!L.nc) continue;
       L.omega = om[k * ninst];
       if (batch) L.omega_inst.assign(om.begin() + k * ninst, om.begin() + (k + 1) * ninst);
     }
+    bool on = false;
+    for (int k = 0; k < nl; ++k) {
+      double w;
+      memcpy(&w, &hw[k], sizeof(w));
+      h->lv[k].max_weight = w;
+      on = on || (p.precision == CLAIR_MIXED && w > kCycle64Weight);
+      h->lv[k].cycle64 = on;
+    }
   }
   dfree(omega_dev, s);
   // coarsest level: dense inverse; float copies and work vectors everywhere
-  ClockScope clk(PH_COARSE, s);
   Level& last = h->lv.back();
   h->nL = last.n;
   // coarsest level: one dense block, or each instance's diagonal block of a batch
@@ -705,43 +741,23 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
   h->coarse_nblk = (int)blocks.size() - 1;
   h->Inv = dalloc<double>(std::max<long long>(inv_size, 1), s);
   dense_inverse(last.A, blocks, h->Inv, &h->coarse_off, &h->coarse_ioff, s);
-  to_float_copy(h->Inv, &h->Inv32, std::max<long long>(inv_size, 1), s);
-  // MIXED: the smoothed mode vectors of nearly pure advection shrink by orders of
-  // magnitude per level, and the projected weights grow in proportion (1e13 seen); an FP32
-  // copy of such R and P loses everything to cancellation.  From the first level whose
-  // largest |R| or |P| weight exceeds kCycle64Weight on, the cycle runs in FP64.
-  {
-    const int nl = (int)h->lv.size();
-    unsigned long long* wmax = dalloc<unsigned long long>(nl, s);
-    CLAIR_CUDA(cudaMemsetAsync(wmax, 0, sizeof(unsigned long long) * nl, s));
-    for (int k = 0; k < nl; ++k) {
-      Level& L = h->lv[k];
-      if (!L.nc) continue;
-      absmax_into(L.R.val, L.R.nnz, wmax + k, s);
-      absmax_into(L.P.val, L.P.nnz, wmax + k, s);
-    }
-    std::vector<unsigned long long> hw(nl);
-    CLAIR_CUDA(cudaMemcpyAsync(hw.data(), wmax, sizeof(unsigned long long) * nl,
-                               cudaMemcpyDeviceToHost, s));
-    CLAIR_CUDA(cudaStreamSynchronize(s));
-    dfree(wmax, s);
-    bool on = false;
-    for (int k = 0; k < nl; ++k) {
-      double w;
-      memcpy(&w, &hw[k], sizeof(w));
-      h->lv[k].max_weight = w;
-      on = on || (p.precision == CLAIR_MIXED && w > kCycle64Weight);
-      h->lv[k].cycle64 = on;
+  SegBatch conv(s);
+  auto to_float_later = [&](const double* x, float** y, long long n) {
+    *y = dalloc<float>(n, s);
+    conv.add(x, *y, n);
+  };
+  to_float_later(h->Inv, &h->Inv32, std::max<long long>(inv_size, 1));
+  for (auto& L : h->lv) {
+    to_float_later(L.A.val, &L.A.val32, L.A.nnz);
+    to_float_later(L.dinv, &L.dinv32, L.n);
+    if (L.nc) {
+      to_float_later(L.R.val, &L.R.val32, L.R.nnz);
+      to_float_later(L.P.val, &L.P.val32, L.P.nnz);
     }
   }
+  conv.flush();
   for (auto& L : h->lv) {
-    to_float_copy(L.A.val, &L.A.val32, L.A.nnz, s);
-    to_float_copy(L.dinv, &L.dinv32, L.n, s);
-    if (L.nc) {
-      to_float_copy(L.R.val, &L.R.val32, L.R.nnz, s);
-      to_float_copy(L.P.val, &L.P.val32, L.P.nnz, s);
-      if (batch) batch_cycle_weights(L, p.post_weighted != 0, s);
-    }
+    if (L.nc && batch) batch_cycle_weights(L, p.post_weighted != 0, s);
     alloc_cycle(L, s);
   }
 }
@@ -1039,7 +1055,7 @@ static void ensure_krylov(clair_hierarchy* h, int nrhs) {
   k.active = dalloc<int>(nseg, s);
   k.jend = dalloc<int>(nseg, s);
   k.its = dalloc<int>(nseg, s);
-  CLAIR_CUDA(cudaMallocHost(&k.host, sizeof(double) * 4));
+  k.host = static_cast<double*>(pinned_get(sizeof(double) * 4));
 }
 
 // (number of active segments, largest residual / tolerance among them)
@@ -1405,13 +1421,13 @@ static clair_status setup_common(int ninst, const int* offsets_host, int n, int 
     h->st.dev = dalloc<unsigned long long>(6, s);
     CLAIR_CUDA(cudaMemsetAsync(h->st.dev, 0, 6 * sizeof(unsigned long long), s));
     setup_levels(h, B, cf_marker);
-    h->st.absorb_device(s);
-    dfree(h->st.dev, s);
     set_active_clock(nullptr);
     h->vin = dalloc<double>(n, s);
     h->zout = dalloc<double>(n, s);
-    CLAIR_CUDA(cudaStreamSynchronize(s));
+    // captured and instantiated on the host while the stream finishes the setup
     build_cycle_graph(h);
+    h->st.absorb_device(s);  // the one synchronisation at the end
+    dfree(h->st.dev, s);
     clock.collect(h->phase_ms, h->level_phase_ms, 32);
     CLAIR_CUDA(cudaEventRecord(e1, s));
     CLAIR_CUDA(cudaEventSynchronize(e1));

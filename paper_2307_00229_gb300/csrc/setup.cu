@@ -16,6 +16,8 @@
 #include <new>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "hessenberg.cuh"
 
@@ -77,13 +79,38 @@ void strength(const Csr& M, const double* thr, double theta, int mode, unsigned 
 // ------------------------------------------------------------------------------------
 enum : signed char { ST_U = 0, ST_C = 1, ST_F = 2 };
 
+#define CLAIR_DISPATCH_W2(W, ...)                            \
+  switch (W) {                                               \
+    case 1: { constexpr int WW = 1; __VA_ARGS__; ::clair::count_launch(); } break;   \
+    case 2: { constexpr int WW = 2; __VA_ARGS__; ::clair::count_launch(); } break;   \
+    case 4: { constexpr int WW = 4; __VA_ARGS__; ::clair::count_launch(); } break;   \
+    case 8: { constexpr int WW = 8; __VA_ARGS__; ::clair::count_launch(); } break;   \
+    case 16: { constexpr int WW = 16; __VA_ARGS__; ::clair::count_launch(); } break; \
+    default: { constexpr int WW = 32; __VA_ARGS__; ::clair::count_launch(); } break; \
+  }
+
+// The splitting kernels take W lanes per point (coarse operators have rows of a hundred
+// entries; one lane per row would walk them one dependent load at a time).  Rows of a
+// warp's groups are consecutive; every lane takes part in the group reductions.
+template <int W>
+__device__ __forceinline__ int group_or(int v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o, W);
+  return v;
+}
+
+template <int W>
 __global__ void pmis_init(const int* __restrict__ Atrp, const unsigned char* __restrict__ sAt,
                           int n, const int* __restrict__ lbase, unsigned long long* __restrict__ key,
                           signed char* __restrict__ state, int* __restrict__ mark) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int i = (int)(t / W), sub = (int)(t % W);
+  const bool ok = i < n;
   unsigned lam = 0;
-  for (int e = Atrp[i]; e < Atrp[i + 1]; ++e) lam += sAt[e];
+  if (ok)
+    for (int e = Atrp[i] + sub; e < Atrp[i + 1]; e += W) lam += sAt[e];
+  lam = group_sum<W>(lam);
+  if (!ok || sub != 0) return;
   // the hash takes the index within the point's instance (a batch is block-diagonal)
   key[i] = ((unsigned long long)lam << 32) | lowbias32((uint32_t)(i - (lbase ? lbase[i] : 0)));
   state[i] = lam == 0 ? ST_F : ST_U;
@@ -91,62 +118,79 @@ __global__ void pmis_init(const int* __restrict__ Atrp, const unsigned char* __r
 }
 
 // An undecided point whose key exceeds every undecided strong neighbour's becomes C.
+template <int W>
 __global__ void pmis_select(const int* __restrict__ Arp, const int* __restrict__ Acol,
                             const unsigned char* __restrict__ sA, const int* __restrict__ Atrp,
                             const int* __restrict__ Atcol, const unsigned char* __restrict__ sAt,
                             int n, const unsigned long long* __restrict__ key,
                             const signed char* __restrict__ state, int* __restrict__ mark,
                             int round) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || state[i] != ST_U) return;
-  const unsigned long long k = key[i];
-  for (int e = Arp[i]; e < Arp[i + 1]; ++e)
-    if (sA[e]) {
-      const int j = Acol[e];
-      if (state[j] == ST_U && key[j] > k) return;
-    }
-  for (int e = Atrp[i]; e < Atrp[i + 1]; ++e)
-    if (sAt[e]) {
-      const int j = Atcol[e];
-      if (state[j] == ST_U && key[j] > k) return;
-    }
-  mark[i] = round;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int i = (int)(t / W), sub = (int)(t % W);
+  const bool act = i < n && state[i] == ST_U;
+  int beaten = 0;
+  if (act) {
+    const unsigned long long k = key[i];
+    for (int e = Arp[i] + sub; e < Arp[i + 1] && !beaten; e += W)
+      if (sA[e]) {
+        const int j = Acol[e];
+        beaten = state[j] == ST_U && key[j] > k;
+      }
+    for (int e = Atrp[i] + sub; e < Atrp[i + 1] && !beaten; e += W)
+      if (sAt[e]) {
+        const int j = Atcol[e];
+        beaten = state[j] == ST_U && key[j] > k;
+      }
+  }
+  beaten = group_or<W>(beaten);
+  if (act && sub == 0 && !beaten) mark[i] = round;
 }
 
 // New C-points are fixed; undecided points strongly depending on one become F.
+template <int W>
 __global__ void pmis_update(const int* __restrict__ Arp, const int* __restrict__ Acol,
                             const unsigned char* __restrict__ sA, int n,
                             const int* __restrict__ mark, signed char* __restrict__ state,
                             int round, int* __restrict__ remaining) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || state[i] != ST_U) return;
-  if (mark[i] == round) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int i = (int)(t / W), sub = (int)(t % W);
+  const bool act = i < n && state[i] == ST_U;
+  const bool newc = act && mark[i] == round;
+  int dep = 0;
+  if (act && !newc)
+    for (int e = Arp[i] + sub; e < Arp[i + 1] && !dep; e += W)
+      dep = sA[e] && mark[Acol[e]] == round;
+  dep = group_or<W>(dep);
+  if (!act || sub != 0) return;
+  if (newc)
     state[i] = ST_C;
-    return;
-  }
-  for (int e = Arp[i]; e < Arp[i + 1]; ++e)
-    if (sA[e] && mark[Acol[e]] == round) {
-      state[i] = ST_F;
-      return;
-    }
-  atomicAdd(remaining, 1);
+  else if (dep)
+    state[i] = ST_F;
+  else
+    atomicAdd(remaining, 1);
 }
 
 // F-points with a strong dependence but none on a C-point.
+template <int W>
 __global__ void pmis_fixup_find(const int* __restrict__ Arp, const int* __restrict__ Acol,
                                 const unsigned char* __restrict__ sA, int n,
                                 const signed char* __restrict__ state, int* __restrict__ mark) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  mark[i] = 0;
-  if (state[i] != ST_F) return;
-  bool has = false, hasc = false;
-  for (int e = Arp[i]; e < Arp[i + 1]; ++e)
-    if (sA[e]) {
-      has = true;
-      if (state[Acol[e]] == ST_C) hasc = true;
-    }
-  if (has && !hasc) mark[i] = 1;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int i = (int)(t / W), sub = (int)(t % W);
+  const bool act = i < n && state[i] == ST_F;
+  int has = 0, hasc = 0;
+  if (act)
+    for (int e = Arp[i] + sub; e < Arp[i + 1]; e += W)
+      if (sA[e]) {
+        has = 1;
+        if (state[Acol[e]] == ST_C) {
+          hasc = 1;
+          break;
+        }
+      }
+  has = group_or<W>(has);
+  hasc = group_or<W>(hasc);
+  if (i < n && sub == 0) mark[i] = (act && has && !hasc) ? 1 : 0;
 }
 
 __global__ void pmis_finish(int n, const int* __restrict__ mark, const signed char* __restrict__ state,
@@ -165,7 +209,12 @@ void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsign
   int* mark = dalloc<int>(n, s);
   int* remaining = dalloc<int>(1, s);
   const int g = ceil_div(n, 256);
-  pmis_init<<<g, 256, 0, s>>>(At.rowptr, sAt, n, lbase, key, state, mark); ::clair::count_launch();
+  // lanes per point from the mean row length of A (the longer of the two walks)
+  const double avg = (double)A.nnz / n;
+  int W = 1;
+  while (W < 32 && 4 * W < avg) W <<= 1;
+  const int gw = (int)ceil_div((long long)n * W, 256);
+  CLAIR_DISPATCH_W2(W, (pmis_init<WW><<<gw, 256, 0, s>>>(At.rowptr, sAt, n, lbase, key, state, mark)));
   CLAIR_LAUNCHED();
   // Rounds go in groups of PMIS_ROUNDS between host checks: a round after the last
   // undecided point is decided changes nothing, and the check reads the last round's count.
@@ -174,9 +223,10 @@ void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsign
     CLAIR_REQUIRE(round < 10000, CLAIR_ERR_CAPACITY, "C/F splitting did not terminate");
     for (int q = 0; q < PMIS_ROUNDS; ++q, ++round) {
       CLAIR_CUDA(cudaMemsetAsync(remaining, 0, sizeof(int), s));
-      pmis_select<<<g, 256, 0, s>>>(A.rowptr, A.col, sA, At.rowptr, At.col, sAt, n, key, state,
-                                    mark, round); ::clair::count_launch();
-      pmis_update<<<g, 256, 0, s>>>(A.rowptr, A.col, sA, n, mark, state, round, remaining); ::clair::count_launch();
+      CLAIR_DISPATCH_W2(W, (pmis_select<WW><<<gw, 256, 0, s>>>(A.rowptr, A.col, sA, At.rowptr, At.col,
+                                                             sAt, n, key, state, mark, round)));
+      CLAIR_DISPATCH_W2(W, (pmis_update<WW><<<gw, 256, 0, s>>>(A.rowptr, A.col, sA, n, mark, state,
+                                                             round, remaining)));
     }
     CLAIR_LAUNCHED();
     int h = 0;
@@ -184,7 +234,7 @@ void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsign
     CLAIR_CUDA(cudaStreamSynchronize(s));
     if (h == 0) break;
   }
-  pmis_fixup_find<<<g, 256, 0, s>>>(A.rowptr, A.col, sA, n, state, mark); ::clair::count_launch();
+  CLAIR_DISPATCH_W2(W, (pmis_fixup_find<WW><<<gw, 256, 0, s>>>(A.rowptr, A.col, sA, n, state, mark)));
   pmis_finish<<<g, 256, 0, s>>>(n, mark, state, cf); ::clair::count_launch();
   CLAIR_LAUNCHED();
   dfree(key, s);
@@ -507,19 +557,37 @@ __device__ __forceinline__ void pt_second_hop(int start, int len, int lane, int*
   __syncwarp();  // P and S are rewritten by the next call
 }
 
+// Stash of the first pass: rows that fit are written, sorted, at a position taken from a
+// bump counter, so the second pass copies them instead of building them again.
+struct PatternStash {
+  int* start;                // per row: position in `buf`, -1 if the row did not fit
+  int* buf;
+  long long cap;             // entries of buf
+  unsigned long long* bump;  // next free entry
+};
+
 template <bool COUNT, bool AGG>
 __global__ void __launch_bounds__(32 * PT_WARPS)
 pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
                const unsigned char* __restrict__ sW, const signed char* __restrict__ cf,
                const int* __restrict__ cpts, int nc, int degree, const int* __restrict__ Mrp,
                const int* __restrict__ Mcol, int* __restrict__ count,
-               const int* __restrict__ Zrp, int* __restrict__ Zcol, int* __restrict__ err) {
+               const int* __restrict__ Zrp, int* __restrict__ Zcol, int* __restrict__ err,
+               PatternStash st) {
   __shared__ int keys[PT_WARPS][PT_CAP];
   __shared__ int hop_pre[PT_WARPS][33];
   __shared__ int hop_start[PT_WARPS][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * PT_WARPS + w;
   if (r >= nc) return;  // warp-uniform
+  if (!COUNT && st.buf) {
+    const int p0 = st.start[r];
+    if (p0 >= 0) {  // built by the first pass
+      const int base = Zrp[r], len = Zrp[r + 1] - base;
+      for (int t = lane; t < len; t += 32) Zcol[base + t] = st.buf[p0 + t];
+      return;
+    }
+  }
   int* K = keys[w];
   const int i = cpts[r];
   // upper bound of the row's pattern: the base points plus every second-hop candidate
@@ -587,9 +655,20 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
   __syncwarp();
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fresh += __shfl_xor_sync(0xffffffffu, fresh, o);
+  int* out = nullptr;
   if (COUNT) {
     if (lane == 0) count[r] = fresh;
-    return;
+    if (!st.buf) return;
+    // take room for the row in the stash; a row that does not fit is built again later
+    unsigned long long p0 = 0;
+    if (lane == 0) p0 = atomicAdd(st.bump, (unsigned long long)fresh);
+    p0 = __shfl_sync(0xffffffffu, p0, 0);
+    const bool fits = p0 + (unsigned long long)fresh <= (unsigned long long)st.cap;
+    if (lane == 0) st.start[r] = fits ? (int)p0 : -1;
+    if (!fits) return;
+    out = st.buf + p0;
+  } else {
+    out = Zcol + Zrp[r];
   }
   // compact occupied slots in place (reads of a chunk precede its writes), then rank-sort
   int total = 0;
@@ -601,12 +680,11 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
     total += __popc(occ);
     __syncwarp();
   }
-  const int base = Zrp[r];
   for (int t = lane; t < total; t += 32) {
     const int v = K[t];
     int rank = 0;
     for (int u = 0; u < total; ++u) rank += K[u] < v;
-    Zcol[base + rank] = v;
+    out[rank] = v;
   }
 }
 
@@ -624,15 +702,22 @@ void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf
   CLAIR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   const int g = ceil_div(nc, PT_WARPS);
   const bool agg = Mrp != nullptr;
+  // the stash: room for about twice the entries of Wm (rows beyond it are built twice)
+  PatternStash st{};
   if (nc) {
+    st.cap = std::min<long long>(2LL * Wm.nnz + 8LL * nc + 1024, 64LL << 20);
+    st.start = dalloc<int>(nc, s);
+    st.buf = dalloc<int>((size_t)st.cap, s);
+    st.bump = dalloc<unsigned long long>(1, s);
+    CLAIR_CUDA(cudaMemsetAsync(st.bump, 0, sizeof(unsigned long long), s));
     if (agg)
       pattern_kernel<true, true><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
                                                              degree, Mrp, Mcol, count, nullptr,
-                                                             nullptr, err);
+                                                             nullptr, err, st);
     else
       pattern_kernel<true, false><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
                                                               degree, nullptr, nullptr, count,
-                                                              nullptr, nullptr, err);
+                                                              nullptr, nullptr, err, st);
     ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
@@ -645,24 +730,31 @@ void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf
     dfree(count, s);
     dfree(err, s);
     dfree(Z.rowptr, s);
+    dfree(st.start, s);
+    dfree(st.buf, s);
+    dfree(st.bump, s);
     Z.rowptr = nullptr;
     CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "pattern row exceeds %d entries", PT_CAP);
   }
   Z.col = dalloc<int>(Z.nnz, s);
   if (nc) {
+    // stashed rows are copied, the others built again
     if (agg)
       pattern_kernel<false, true><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
                                                               degree, Mrp, Mcol, nullptr, Z.rowptr,
-                                                              Z.col, err);
+                                                              Z.col, err, st);
     else
       pattern_kernel<false, false><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts,
                                                                nc, degree, nullptr, nullptr,
-                                                               nullptr, Z.rowptr, Z.col, err);
+                                                               nullptr, Z.rowptr, Z.col, err, st);
     ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
   dfree(count, s);
   dfree(err, s);
+  dfree(st.start, s);
+  dfree(st.buf, s);
+  dfree(st.bump, s);
 }
 
 // ------------------------------------------------------------------------------------
@@ -716,15 +808,6 @@ static int lanes_of(const Csr& A, bool fp64) {
   return w;
 }
 
-#define CLAIR_DISPATCH_W2(W, ...)                            \
-  switch (W) {                                               \
-    case 1: { constexpr int WW = 1; __VA_ARGS__; ::clair::count_launch(); } break;   \
-    case 2: { constexpr int WW = 2; __VA_ARGS__; ::clair::count_launch(); } break;   \
-    case 4: { constexpr int WW = 4; __VA_ARGS__; ::clair::count_launch(); } break;   \
-    case 8: { constexpr int WW = 8; __VA_ARGS__; ::clair::count_launch(); } break;   \
-    case 16: { constexpr int WW = 16; __VA_ARGS__; ::clair::count_launch(); } break; \
-    default: { constexpr int WW = 32; __VA_ARGS__; ::clair::count_launch(); } break; \
-  }
 
 template <class T>
 void jacobi(const Csr& A, const T* vals, const T* dinv, const signed char* cf, int which, T omega,
@@ -838,35 +921,23 @@ __global__ void __launch_bounds__(32) ritz_kernel(const double* __restrict__ H, 
 }
 
 // ---- fused Arnoldi step (m <= AR_MAXV): three launches per step -------------------------
-// K1  v_j = w_prev * scale (stored for j > 0), w = D^-1 A v_j, dots of w with v_0..v_j and
-//     with itself                              -> h1, ||w||^2 before CGS
+// K1  v_j = w_prev * scale (stored), w = D^-1 A v_j, dots of w with v_0..v_j and with
+//     itself                                   -> h1, ||w||^2 before CGS
 // K2  w -= V h1, dots of the new w with v_0..v_j  -> h2
 // K3  w -= V h2, ||w||^2                        -> H column, breakdown, scale of v_{j+1}
-// Each block writes its partial sums; the last block to arrive (atomic ticket) adds them
-// in block order and publishes the step's scalars, so the next kernel reads finished
-// values, no finalize launch sits between the kernels, the grid can fill the GPU, and the
-// result does not depend on scheduling.  steps_hist[t] is the breakdown state after step
-// t-1 (-1: none).
+// Block b owns the rows [b R, (b + 1) R).  FP64 is the scarce pipe on this part (an FP64
+// warp instruction holds it for tens of cycles), so nothing beyond v_j is touched: after
+// the row updates, warp q of the block takes the dot products q, q + 8, ... over the
+// block's rows (two running sums per lane, one warp tree), and writes the block's partial
+// of each.  The kernels hold no shared-memory table, so they fit beside the other
+// stream's blocks.  The last block to arrive (atomic ticket) adds the partials in block
+// order and publishes the step's scalars, so the next kernel reads finished values, no
+// finalize launch sits between the kernels, and the result does not depend on
+// scheduling.  steps_hist[t] is the breakdown state after step t-1 (-1: none).
 constexpr int AR_MAXV = 15;
 constexpr int AR_THREADS = 256;
-
-template <int NV>
-__device__ __forceinline__ void block_reduce_to_partial(double (&acc)[NV], int nv,
-                                                        double* __restrict__ partial) {
-  __shared__ double sh[NV][AR_THREADS / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const double t = warp_sum(acc[v]);
-    if (lane == 0) sh[v][wid] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    double t = 0.0;
-    for (int k = 0; k < AR_THREADS / 32; ++k) t += sh[threadIdx.x][k];
-    partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = t;
-  }
-}
+constexpr int AR_WARPS = AR_THREADS / 32;
+constexpr int AR_SLOTS = AR_MAXV + 2;  // 0..AR_MAXV-1: projections, AR_MAXV+1: squared norm
 
 struct ArnoldiState {
   double* H;            // ldh x m, column-major
@@ -878,6 +949,212 @@ struct ArnoldiState {
   int* steps_hist;      // m + 1 entries, [0] = -1
   unsigned* ticket;     // arrival counter (0 between kernels)
 };
+
+// Row dot with four entries per lane in flight (indices and values first, then the four
+// gathers) and two partial sums; the order is fixed, so the result is reproducible.
+template <int W>
+__device__ __forceinline__ double csr_row_dot_cl(const int* __restrict__ col,
+                                                 const double* __restrict__ val,
+                                                 const double* x, int e0, int e1, int lane) {
+  double a0 = 0.0, a1 = 0.0;
+  int e = e0 + lane;
+  for (; e + 3 * W < e1; e += 4 * W) {
+    const int c0 = col[e], c1 = col[e + W], c2 = col[e + 2 * W], c3 = col[e + 3 * W];
+    const double v0 = val[e], v1 = val[e + W], v2 = val[e + 2 * W], v3 = val[e + 3 * W];
+    const double x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+    a0 = fma(v0, x0, a0);
+    a1 = fma(v1, x1, a1);
+    a0 = fma(v2, x2, a0);
+    a1 = fma(v3, x3, a1);
+  }
+  for (; e < e1; e += W) a0 = fma(val[e], x[col[e]], a0);
+  return a0 + a1;
+}
+
+// Sum over i in [lo, hi) of a[i] * b[i], by one warp (all lanes get the result): eight
+// entries per lane in flight (sixteen independent loads) into four running sums, so the
+// loop waits on one memory round trip per 256 entries, not per entry.
+__device__ __forceinline__ double warp_dot(const double* a, const double* b, int lo, int hi,
+                                           int lane) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int i = lo + lane;
+  for (; i + 224 < hi; i += 256) {
+    double x[8], y[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      x[u] = a[i + 32 * u];
+      y[u] = b[i + 32 * u];
+    }
+    s0 = fma(x[0], y[0], s0);
+    s1 = fma(x[1], y[1], s1);
+    s2 = fma(x[2], y[2], s2);
+    s3 = fma(x[3], y[3], s3);
+    s0 = fma(x[4], y[4], s0);
+    s1 = fma(x[5], y[5], s1);
+    s2 = fma(x[6], y[6], s2);
+    s3 = fma(x[7], y[7], s3);
+  }
+  for (; i < hi; i += 32) s0 = fma(a[i], b[i], s0);
+  return warp_sum((s0 + s1) + (s2 + s3));
+}
+
+// Block partials of the dots <a_q, w> (a_q = v_q for q <= nproj - 1) and, with `norm`,
+// <w, w> into partial[slot][block]; the rows are the block's own, w complete (synced).
+__device__ __forceinline__ void block_dots(const double* V, long long n, int nproj, bool norm,
+                                           const double* w, int lo, int hi,
+                                           double* __restrict__ partial) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nq = nproj + (norm ? 1 : 0);
+  for (int q = wid; q < nq; q += AR_WARPS) {
+    const bool is_norm = q >= nproj;
+    const double v = warp_dot(is_norm ? w : V + (long long)q * n, w, lo, hi, lane);
+    if (lane == 0) partial[(long long)(is_norm ? AR_SLOTS - 1 : q) * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+// After the block's partials are written: true in the block that arrives last, which then
+// holds the grand sums of the live slots in red[] (slot order, block order within).
+__device__ __forceinline__ bool finish_slots(const double* partial, int nproj, bool norm,
+                                             unsigned* ticket, double* red) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nb = gridDim.x;
+  const int nq = nproj + (norm ? 1 : 0);
+  for (int q = wid; q < nq; q += AR_WARPS) {
+    const int k = q < nproj ? q : AR_SLOTS - 1;
+    double t = 0.0;
+    for (int b = lane; b < nb; b += 32) t += __ldcg(&partial[(long long)k * nb + b]);
+    t = warp_sum(t);
+    if (lane == 0) red[k] = t;
+  }
+  __syncthreads();
+  return true;
+}
+
+template <int W>
+__global__ void __launch_bounds__(AR_THREADS, 6)
+arnoldi_k1(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ av,
+           const double* __restrict__ dinv, int n, double* __restrict__ V, int j,
+           const double* __restrict__ wprev, ArnoldiState st, double* __restrict__ w,
+           double* __restrict__ partial) {
+  __shared__ double red[AR_SLOTS];
+  const double sc = j > 0 ? *st.scale : 1.0;  // v_0 is normalised already
+  const long long R = (n + (long long)gridDim.x - 1) / gridDim.x;
+  const int lo = (int)min((long long)n, R * blockIdx.x), hi = (int)min((long long)n, lo + R);
+  constexpr int GPW = 32 / W;
+  const int lane = threadIdx.x & 31, sub = lane % W, grp = lane / W, warp = threadIdx.x >> 5;
+  double* __restrict__ Vj = V + (long long)j * n;
+  for (int base = lo + warp * GPW; base < hi; base += AR_WARPS * GPW) {
+    const int i = base + grp;
+    double s = 0.0;
+    if (i < hi) s = csr_row_dot_cl<W>(ci, av, wprev, rp[i], rp[i + 1], sub);
+    s = group_sum<W>(s);
+    if (sub == 0 && i < hi) {
+      w[i] = dinv[i] * (sc * s);
+      if (j > 0) Vj[i] = wprev[i] * sc;
+    }
+  }
+  __syncthreads();  // w and v_j of the block's rows, written above
+  block_dots(V, n, j + 1, true, w, lo, hi, partial);
+  if (!finish_slots(partial, j + 1, true, st.ticket, red)) return;
+  if (threadIdx.x <= j) st.h1[threadIdx.x] = red[threadIdx.x];
+  if (threadIdx.x == 0) {
+    *st.w0n2 = red[AR_SLOTS - 1];
+    *st.ticket = 0u;
+  }
+}
+
+// FIRST: w -= V h1, dots of the new w with v_0..v_j -> h2.  Otherwise: w -= V h2,
+// ||w||^2 -> the step's H column, breakdown state and the scale of v_{j+1}.
+template <bool FIRST>
+__global__ void __launch_bounds__(AR_THREADS, 6)
+arnoldi_cgs(const double* __restrict__ V, int j, int n, ArnoldiState st, double* __restrict__ w,
+            double* __restrict__ partial) {
+  __shared__ double red[AR_SLOTS];
+  __shared__ double hk[AR_MAXV];
+  const double* h = FIRST ? st.h1 : st.h2;
+  if (threadIdx.x <= j) hk[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  const long long R = (n + (long long)gridDim.x - 1) / gridDim.x;
+  const int lo = (int)min((long long)n, R * blockIdx.x), hi = (int)min((long long)n, lo + R);
+  for (int i = lo + threadIdx.x; i < hi; i += AR_THREADS) {
+    double wi = w[i];
+    for (int k = 0; k <= j; ++k) wi = fma(-hk[k], V[(long long)k * n + i], wi);
+    w[i] = wi;
+  }
+  __syncthreads();  // the block's rows of w
+  block_dots(V, n, FIRST ? j + 1 : 0, !FIRST, w, lo, hi, partial);
+  if (!finish_slots(partial, FIRST ? j + 1 : 0, !FIRST, st.ticket, red)) return;
+  if (FIRST) {
+    if (threadIdx.x <= j) st.h2[threadIdx.x] = red[threadIdx.x];
+    if (threadIdx.x == 0) *st.ticket = 0u;
+    return;
+  }
+  if (threadIdx.x != 0) return;
+  // close step j: H column, breakdown test, scale of the next basis vector
+  const bool active = st.steps_hist[j] < 0;
+  const double hn = sqrt(red[AR_SLOTS - 1]);
+  for (int i = 0; i <= j; ++i) st.H[i + (long long)j * st.ldh] = active ? st.h1[i] + st.h2[i] : 0.0;
+  st.H[j + 1 + (long long)j * st.ldh] = active ? hn : 0.0;
+  st.steps_hist[j + 1] = (active && hn <= 1e-10 * sqrt(*st.w0n2)) ? j + 1 : st.steps_hist[j];
+  *st.scale = (active && hn > 0.0) ? 1.0 / hn : 0.0;
+  *st.ticket = 0u;
+}
+
+// w of step j lives in wbuf[j & 1] while K1 gathers v_j from the previous step's w in the
+// other buffer.  nb blocks: one or two per SM, fewer on small levels.
+static void arnoldi_fused_steps(const Csr& A, const double* dinv, int m, double* V,
+                                double* const wbuf[2], const ArnoldiState& st, double* partial,
+                                int nb, cudaStream_t s) {
+  const int n = A.rows;
+  // at most four lanes per row: eight or more rows per warp in flight
+  const int W = std::min(lanes_of(A, true), 4);
+  for (int j = 0; j < m; ++j) {
+    double* w = wbuf[j & 1];
+    const double* wprev = j == 0 ? V : wbuf[(j + 1) & 1];
+    if (W == 1)
+      arnoldi_k1<1><<<nb, AR_THREADS, 0, s>>>(A.rowptr, A.col, A.val, dinv, n, V, j, wprev, st, w,
+                                             partial);
+    else if (W == 2)
+      arnoldi_k1<2><<<nb, AR_THREADS, 0, s>>>(A.rowptr, A.col, A.val, dinv, n, V, j, wprev, st, w,
+                                             partial);
+    else
+      arnoldi_k1<4><<<nb, AR_THREADS, 0, s>>>(A.rowptr, A.col, A.val, dinv, n, V, j, wprev, st, w,
+                                             partial);
+    ::clair::count_launch();
+    arnoldi_cgs<true><<<nb, AR_THREADS, 0, s>>>(V, j, n, st, w, partial); ::clair::count_launch();
+    arnoldi_cgs<false><<<nb, AR_THREADS, 0, s>>>(V, j, n, st, w, partial); ::clair::count_launch();
+    CLAIR_LAUNCHED();
+  }
+}
+
+// Register-accumulator reductions of the segmented (batch) Arnoldi below: the block's
+// warp sums of the live values (v < nv), one partial per value and block.
+template <int NV>
+__device__ __forceinline__ void block_reduce_to_partial(double (&acc)[NV], int nv,
+                                                        double* __restrict__ partial) {
+  __shared__ double sh[NV][AR_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (v < nv) {  // warp-uniform: no FP64 shuffle-adds for dead values
+      const double t = warp_sum(acc[v]);
+      if (lane == 0) sh[v][wid] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    for (int k = 0; k < AR_THREADS / 32; ++k) t += sh[threadIdx.x][k];
+    partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+}
 
 // After the block's partials are written: true in the block that arrives last.
 __device__ __forceinline__ bool last_block(unsigned* ticket) {
@@ -903,116 +1180,201 @@ __device__ __forceinline__ void sum_partials(const double* partial, int nv, doub
   __syncthreads();
 }
 
+// ---- one-launch Arnoldi on a thread-block cluster (levels of a few thousand rows) ----
+// The whole run (start vector, m steps of CGS2, the H columns) is one launch of one
+// cluster of C CTAs; CTA r owns rows [r n / C, (r + 1) n / C).  Every reduction is: warp
+// sums, the CTA's partial in its shared memory, a hardware cluster barrier, then every
+// CTA adds the C partials in rank order through distributed shared memory, so all CTAs
+// hold the same sums and take the same breakdown decisions, and there is no spin-wait.
+// Partials alternate between two buffers: a CTA rewrites a buffer two reductions later,
+// after a barrier that every reader of its previous contents has passed.  The next basis
+// vector is kept unscaled (w) and its scale applied when the SpMV reads it, as in the
+// multi-launch path.  Other CTAs' rows of w are read with ordinary (coherent, L1-cached)
+// loads: the barrier's release by the writers and an acquire fence after it make them
+// visible; the read-only path (ld.global.nc) is never used for w.
+constexpr int AC_THREADS = 256;
+constexpr int AC_WARPS = AC_THREADS / 32;
+
+struct ClusterSums {
+  double part[2][AR_SLOTS];
+  double out[AR_SLOTS];
+};
+
+// The CTA's partials of <v_q, w> (q < nproj) and, with `norm`, <w, w> over its rows (warp q
+// takes dots q, q + 8, ...), then out[slot] = the cluster-wide sums; called by every
+// thread of every CTA once the CTA's rows of w are written.
+__device__ __forceinline__ void cluster_dots(const double* V, long long n, int nproj, bool norm,
+                                             const double* w, int lo, int hi, ClusterSums& cs,
+                                             int& buf) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nq = nproj + (norm ? 1 : 0);
+  for (int q = wid; q < nq; q += AC_WARPS) {
+    const bool is_norm = q >= nproj;
+    const double v = warp_dot(is_norm ? w : V + (long long)q * n, w, lo, hi, lane);
+    if (lane == 0) cs.part[buf][is_norm ? AR_SLOTS - 1 : q] = v;
+  }
+  __threadfence();  // this CTA's global writes before the barrier, for the other CTAs
+  cl.sync();
+  __threadfence();  // acquire: the other CTAs' writes before the barrier, for this CTA
+  if ((int)threadIdx.x < nq) {
+    const int k = (int)threadIdx.x < nproj ? (int)threadIdx.x : AR_SLOTS - 1;
+    double v = 0.0;
+    const int C = (int)cl.num_blocks();
+    for (int c = 0; c < C; ++c) v += *cl.map_shared_rank(&cs.part[buf][k], c);
+    cs.out[k] = v;
+  }
+  __syncthreads();
+  buf ^= 1;
+}
+
 template <int W>
-__global__ void __launch_bounds__(AR_THREADS)
-arnoldi_k1(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ av,
-           const double* __restrict__ dinv, int n, double* __restrict__ V, int j,
-           const double* __restrict__ wprev, ArnoldiState st, double* __restrict__ w,
-           double* __restrict__ partial) {
-  __shared__ double hs[AR_MAXV + 2];
-  const double sc = j > 0 ? *st.scale : 1.0;  // v_0 is normalised already
+__global__ void __launch_bounds__(AC_THREADS, 2)
+arnoldi_cluster(const int* __restrict__ rp, const int* __restrict__ ci,
+                const double* __restrict__ av, const double* __restrict__ dinv, int n, int m,
+                uint64_t seed, double* __restrict__ V, double* wb0, double* wb1,
+                double* __restrict__ H, int ldh, int* __restrict__ steps_out) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ ClusterSums cs;
+  __shared__ double h1s[AR_MAXV], h2s[AR_MAXV];
+  const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+  const int lo = (int)((long long)n * r / C), hi = (int)((long long)n * (r + 1) / C);
+  const int tid = threadIdx.x;
+  int buf = 0;
+  // start vector, unscaled, in wb1 (the "previous w" of step 0); its squared norm
+  for (int i = lo + tid; i < hi; i += AC_THREADS) wb1[i] = splitmix_pm1(seed, (uint64_t)i);
+  cluster_dots(V, n, 0, true, wb1, lo, hi, cs, buf);
+  double sc = 1.0 / sqrt(cs.out[AR_SLOTS - 1]);
+  int steps = -1;  // breakdown step, -1 while none
   constexpr int GPW = 32 / W;
-  double acc[AR_MAXV + 2];
-#pragma unroll
-  for (int v = 0; v < AR_MAXV + 2; ++v) acc[v] = 0.0;
-  const int lane = threadIdx.x & 31, sub = lane % W, grp = lane / W;
-  const long long warp = (blockIdx.x * (long long)AR_THREADS + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * AR_THREADS) >> 5;
-  for (long long base = warp * GPW; base < n; base += nwarps * GPW) {  // warp-uniform trips
-    const long long i = base + grp;
-    double s = 0.0;
-    if (i < n) s = csr_row_dot<W>(ci, av, wprev, rp[i], rp[i + 1], sub);
-    s = group_sum<W>(s);
-    if (sub == 0 && i < n) {
-      const double wi = dinv[i] * (sc * s);
-      const double vj = wprev[i] * sc;
-      w[i] = wi;
-      if (j > 0) V[(long long)j * n + i] = vj;
-      // every accumulator index is static: slot k <= j holds <v_k, w>, slot AR_MAXV + 1
-      // holds <w, w>
-#pragma unroll
-      for (int k = 0; k < AR_MAXV; ++k)
-        if (k <= j) acc[k] += (k < j ? V[(long long)k * n + i] : vj) * wi;
-      acc[AR_MAXV + 1] += wi * wi;
-    }
-  }
-  block_reduce_to_partial<AR_MAXV + 2>(acc, AR_MAXV + 2, partial);
-  if (!last_block(st.ticket)) return;
-  sum_partials(partial, AR_MAXV + 2, hs);
-  if (threadIdx.x == 0) {
-    for (int k = 0; k <= j; ++k) st.h1[k] = hs[k];
-    *st.w0n2 = hs[AR_MAXV + 1];
-    *st.ticket = 0u;
-  }
-}
-
-// FIRST: w -= V h1, dots of the new w with v_0..v_j -> h2.  Otherwise: w -= V h2,
-// ||w||^2 -> the step's H column, breakdown state and the scale of v_{j+1}.
-template <bool FIRST>
-__global__ void __launch_bounds__(AR_THREADS)
-arnoldi_cgs(const double* __restrict__ V, int j, int n, ArnoldiState st, double* __restrict__ w,
-            double* __restrict__ partial) {
-  __shared__ double hs[AR_MAXV + 1];
-  const double* h = FIRST ? st.h1 : st.h2;
-  double acc[AR_MAXV + 1];
-#pragma unroll
-  for (int v = 0; v < AR_MAXV + 1; ++v) acc[v] = 0.0;
-  double hk[AR_MAXV];
-#pragma unroll
-  for (int k = 0; k < AR_MAXV; ++k) hk[k] = k <= j ? h[k] : 0.0;
-  for (long long i = blockIdx.x * (long long)AR_THREADS + threadIdx.x; i < n;
-       i += (long long)gridDim.x * AR_THREADS) {
-    double vk[AR_MAXV];
-    double wi = w[i];
-#pragma unroll
-    for (int k = 0; k < AR_MAXV; ++k) {
-      vk[k] = k <= j ? V[(long long)k * n + i] : 0.0;
-      if (k <= j) wi = fma(-hk[k], vk[k], wi);
-    }
-    w[i] = wi;
-    if (FIRST) {
-#pragma unroll
-      for (int k = 0; k < AR_MAXV; ++k)
-        if (k <= j) acc[k] += vk[k] * wi;
-    } else {
-      acc[0] += wi * wi;
-    }
-  }
-  block_reduce_to_partial<AR_MAXV + 1>(acc, FIRST ? j + 1 : 1, partial);
-  if (!last_block(st.ticket)) return;
-  sum_partials(partial, FIRST ? j + 1 : 1, hs);
-  if (threadIdx.x != 0) return;
-  if (FIRST) {
-    for (int k = 0; k <= j; ++k) st.h2[k] = hs[k];
-  } else {
-    // close step j: H column, breakdown test, scale of the next basis vector
-    const bool active = st.steps_hist[j] < 0;
-    const double hn = sqrt(hs[0]);
-    for (int i = 0; i <= j; ++i) st.H[i + (long long)j * st.ldh] = active ? st.h1[i] + st.h2[i] : 0.0;
-    st.H[j + 1 + (long long)j * st.ldh] = active ? hn : 0.0;
-    st.steps_hist[j + 1] = (active && hn <= 1e-10 * sqrt(*st.w0n2)) ? j + 1 : st.steps_hist[j];
-    *st.scale = (active && hn > 0.0) ? 1.0 / hn : 0.0;
-  }
-  *st.ticket = 0u;
-}
-
-// w of step j lives in wbuf[j & 1] while K1 gathers v_j from the previous step's w in the
-// other buffer.  nb blocks: up to four per SM (the register limit of these kernels), fewer
-// on small levels.
-static void arnoldi_fused_steps(const Csr& A, const double* dinv, int m, double* V,
-                                double* const wbuf[2], const ArnoldiState& st, double* partial,
-                                int nb, cudaStream_t s) {
-  const int n = A.rows;
-  const int W = lanes_of(A, true);
+  const int lane = tid & 31, sub = lane % W, grp = lane / W, warp = tid >> 5;
   for (int j = 0; j < m; ++j) {
-    double* w = wbuf[j & 1];
-    const double* wprev = j == 0 ? V : wbuf[(j + 1) & 1];
-    CLAIR_DISPATCH_W2(W, (arnoldi_k1<WW><<<nb, AR_THREADS, 0, s>>>(A.rowptr, A.col, A.val, dinv, n,
-                                                                  V, j, wprev, st, w, partial)));
-    arnoldi_cgs<true><<<nb, AR_THREADS, 0, s>>>(V, j, n, st, w, partial); ::clair::count_launch();
-    arnoldi_cgs<false><<<nb, AR_THREADS, 0, s>>>(V, j, n, st, w, partial); ::clair::count_launch();
-    CLAIR_LAUNCHED();
+    const double* wprev = (j & 1) ? wb0 : wb1;
+    double* w = (j & 1) ? wb1 : wb0;
+    double* Vj = V + (long long)j * n;
+    // P1: v_j = sc * w_prev (own rows), w = D^-1 A v_j, then <v_k, w> and <w, w>
+    for (int base = lo + warp * GPW; base < hi; base += AC_WARPS * GPW) {
+      const int i = base + grp;
+      double s = 0.0;
+      if (i < hi) s = csr_row_dot_cl<W>(ci, av, wprev, rp[i], rp[i + 1], sub);
+      s = group_sum<W>(s);
+      if (sub == 0 && i < hi) {
+        w[i] = dinv[i] * (sc * s);
+        Vj[i] = wprev[i] * sc;
+      }
+    }
+    cluster_dots(V, n, j + 1, true, w, lo, hi, cs, buf);
+    const double w0n2 = cs.out[AR_SLOTS - 1];
+    if (tid <= j) h1s[tid] = cs.out[tid];
+    __syncthreads();
+    // P2: w -= V h1, then the projections again
+    for (int i = lo + tid; i < hi; i += AC_THREADS) {
+      double wi = w[i];
+      for (int k = 0; k <= j; ++k) wi = fma(-h1s[k], V[(long long)k * n + i], wi);
+      w[i] = wi;
+    }
+    cluster_dots(V, n, j + 1, false, w, lo, hi, cs, buf);
+    if (tid <= j) h2s[tid] = cs.out[tid];
+    __syncthreads();
+    // P3: w -= V h2, ||w||^2 -> the H column, the breakdown test, the next scale
+    for (int i = lo + tid; i < hi; i += AC_THREADS) {
+      double wi = w[i];
+      for (int k = 0; k <= j; ++k) wi = fma(-h2s[k], V[(long long)k * n + i], wi);
+      w[i] = wi;
+    }
+    cluster_dots(V, n, 0, true, w, lo, hi, cs, buf);
+    const bool active = steps < 0;
+    const double hn = sqrt(cs.out[AR_SLOTS - 1]);
+    if (r == 0 && tid <= j) H[tid + (long long)j * ldh] = active ? h1s[tid] + h2s[tid] : 0.0;
+    if (r == 0 && tid == 0) H[j + 1 + (long long)j * ldh] = active ? hn : 0.0;
+    if (active && hn <= 1e-10 * sqrt(w0n2)) steps = j + 1;
+    sc = (active && hn > 0.0) ? 1.0 / hn : 0.0;
   }
+  if (r == 0 && tid == 0) *steps_out = steps;
+  cl.sync();  // no CTA leaves while another may still read its partials
+}
+
+template <int W>
+static void allow_cluster16() {
+  CLAIR_CUDA(cudaFuncSetAttribute(arnoldi_cluster<W>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+}
+
+// Largest cluster (16 or 8) the device schedules for this kernel, per device.
+static int ac_cluster_max() {
+  static int cmax[256] = {};
+  int dev = 0;
+  CLAIR_CUDA(cudaGetDevice(&dev));
+  once_per_device((const void*)&ac_cluster_max, [] {
+    int d = 0;
+    CLAIR_CUDA(cudaGetDevice(&d));
+    allow_cluster16<1>();
+    allow_cluster16<2>();
+    allow_cluster16<4>();
+    int best = 8;
+    for (int c : {16, 12}) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = c;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(c);
+      cfg.blockDim = dim3(AC_THREADS);
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, arnoldi_cluster<4>, &cfg) == cudaSuccess &&
+          nclusters >= 1) {
+        best = c;
+        break;
+      }
+      cudaGetLastError();
+    }
+    if (d >= 0 && d < 256) cmax[d] = best;
+  });
+  return (dev >= 0 && dev < 256 && cmax[dev]) ? cmax[dev] : 8;
+}
+
+// Levels this small take the one-launch path: its cluster's FP64 pipes do the level's
+// work in less time than the multi-launch path spends on its 3 m launches.
+static bool arnoldi_on_cluster(const Csr& A, int m) {
+  return m <= AR_MAXV && A.rows >= 1 && A.nnz <= (1 << 20);
+}
+
+static void arnoldi_cluster_run(const Csr& A, const double* dinv, int m, uint64_t seed,
+                                double* V, double* w0, double* w1, double* H, int ldh,
+                                int* steps, cudaStream_t s) {
+  // every SM of the cluster adds FP64 throughput; at least 64 rows per CTA
+  int C = std::max(1, std::min(ac_cluster_max(), (A.rows + 63) / 64));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(AC_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  // at most four lanes per row: a CTA then keeps eight rows per warp in flight, and its
+  // FP64 pipe, not the latency of one row, sets the pace
+  const int W = std::min(lanes_of(A, true), 4);
+  if (W == 1)
+    CLAIR_CUDA(cudaLaunchKernelEx(&cfg, arnoldi_cluster<1>, A.rowptr, A.col, A.val, dinv, A.rows,
+                                  m, seed, V, w0, w1, H, ldh, steps));
+  else if (W == 2)
+    CLAIR_CUDA(cudaLaunchKernelEx(&cfg, arnoldi_cluster<2>, A.rowptr, A.col, A.val, dinv, A.rows,
+                                  m, seed, V, w0, w1, H, ldh, steps));
+  else
+    CLAIR_CUDA(cudaLaunchKernelEx(&cfg, arnoldi_cluster<4>, A.rowptr, A.col, A.val, dinv, A.rows,
+                                  m, seed, V, w0, w1, H, ldh, steps));
+  ::clair::count_launch();
+  CLAIR_LAUNCHED();
 }
 
 // ---- Ritz values on the host --------------------------------------------------------
@@ -1022,6 +1384,7 @@ static void arnoldi_fused_steps(const Csr& A, const double* dinv, int m, double*
 // the next copy puts them back on the device, all in stream order.
 struct RitzHost {
   int ldh = 0, m = 0, ninst = 0;
+  size_t bytes = 0;         // the pinned block holding this header and the arrays
   double* H = nullptr;      // ninst x ldh x m, pinned
   int* steps = nullptr;     // ninst, pinned
   double* omega = nullptr;  // ninst, pinned
@@ -1040,26 +1403,31 @@ static void CUDART_CB ritz_on_host(void* data) {
   }
 }
 
-// Pinned buffers for one Arnoldi run's Ritz step (released by the caller after the
-// stream has passed the run).
+// Pinned buffers for one Arnoldi run's Ritz step, one recycled block (released by the
+// caller after the stream has passed the run).
 RitzHost* ritz_host_alloc(int ninst) {
-  RitzHost* r = nullptr;
-  CLAIR_CUDA(cudaHostAlloc(&r, sizeof(RitzHost), cudaHostAllocDefault));
-  new (r) RitzHost();
-  r->ninst = ninst;
   const int ldh = AR_MAXV + 1;
-  CLAIR_CUDA(cudaHostAlloc(&r->H, sizeof(double) * ninst * ldh * AR_MAXV, cudaHostAllocDefault));
-  CLAIR_CUDA(cudaHostAlloc(&r->steps, sizeof(int) * ninst, cudaHostAllocDefault));
-  CLAIR_CUDA(cudaHostAlloc(&r->omega, sizeof(double) * ninst, cudaHostAllocDefault));
+  const size_t head = 64;
+  const size_t hbytes = sizeof(double) * (size_t)ninst * ldh * AR_MAXV;
+  const size_t obytes = sizeof(double) * (size_t)ninst;
+  const size_t sbytes = sizeof(int) * (size_t)ninst;
+  const size_t bytes = head + hbytes + obytes + sbytes;
+  static_assert(sizeof(RitzHost) <= 64, "RitzHost header must fit its slot");
+  char* base = static_cast<char*>(pinned_get(bytes));
+  RitzHost* r = new (base) RitzHost();
+  r->bytes = bytes;
+  r->ninst = ninst;
+  r->H = reinterpret_cast<double*>(base + head);
+  r->omega = reinterpret_cast<double*>(base + head + hbytes);
+  r->steps = reinterpret_cast<int*>(base + head + hbytes + obytes);
   return r;
 }
 
 void ritz_host_free(RitzHost* r) {
   if (!r) return;
-  cudaFreeHost(r->H);
-  cudaFreeHost(r->steps);
-  cudaFreeHost(r->omega);
-  cudaFreeHost(r);
+  const size_t bytes = r->bytes;
+  r->~RitzHost();
+  pinned_put(r, bytes);
 }
 
 // Enqueues: H, steps -> host; the callback; weights -> omega_dev.
@@ -1321,6 +1689,25 @@ double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed
   const int n = A.rows;
   const int m = std::max(1, std::min(iters, n));
   const int ldh = m + 1;
+  if (arnoldi_on_cluster(A, m)) {
+    double* V = dalloc<double>((size_t)m * n, s);
+    double* w = dalloc<double>((size_t)2 * n, s);
+    double* H = dalloc<double>((size_t)ldh * m, s);
+    int* steps = dalloc<int>(1, s);
+    CLAIR_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * ldh * m, s));
+    arnoldi_cluster_run(A, dinv, m, seed, V, w, w + n, H, ldh, steps, s);
+    if (rh) {
+      ritz_via_host(H, ldh, m, steps, 1, omega_dev, rh, s);
+    } else {
+      ritz_kernel<<<1, 32, 0, s>>>(H, ldh, m, steps, omega_dev); ::clair::count_launch();
+      CLAIR_LAUNCHED();
+    }
+    dfree(V, s);
+    dfree(w, s);
+    dfree(H, s);
+    dfree(steps, s);
+    return 0.0;
+  }
   double* V = dalloc<double>((size_t)(m + 1) * n, s);
   double* w = dalloc<double>(n, s);
   double* H = dalloc<double>((size_t)ldh * m, s);
@@ -1342,8 +1729,8 @@ double arnoldi_weight(const Csr& A, const double* dinv, int iters, uint64_t seed
   CLAIR_LAUNCHED();
   int* steps_hist = nullptr;
   if (m <= AR_MAXV) {
-    const int W = lanes_of(A, true);
-    const int nb = std::max(1, std::min(4 * sm_count(), ceil_div((long long)n * W, AR_THREADS)));
+    // up to six blocks per SM (the kernels' registers allow it), at least 32 rows a block
+    const int nb = std::max(1, std::min(6 * sm_count(), ceil_div(n, 32)));
     double* w2 = dalloc<double>(n, s);
     double* p2 = dalloc<double>((size_t)nb * (AR_MAXV + 2), s);
     steps_hist = dalloc<int>(m + 1, s);

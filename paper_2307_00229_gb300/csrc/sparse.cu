@@ -52,6 +52,44 @@ void once_per_device(const void* tag, void (*set)()) {
   done.insert({dev, tag});
 }
 
+// Pinned host blocks, kept for the life of the process: a setup takes a few small ones
+// per level (the Ritz steps) and a solve one (the Krylov summary), and pinning pages in
+// the driver costs far more than the copies they serve.  Blocks are recycled by size
+// class (powers of two from 256 bytes); portable, so any device's context may use them.
+static std::mutex g_pinned_mu;
+static std::vector<void*> g_pinned_free[48];
+
+static int pinned_class(size_t bytes, size_t* rounded) {
+  int c = 8;
+  while (((size_t)1 << c) < bytes) ++c;
+  *rounded = (size_t)1 << c;
+  return c;
+}
+
+void* pinned_get(size_t bytes) {
+  size_t rb = 0;
+  const int c = pinned_class(bytes, &rb);
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    if (!g_pinned_free[c].empty()) {
+      void* p = g_pinned_free[c].back();
+      g_pinned_free[c].pop_back();
+      return p;
+    }
+  }
+  void* p = nullptr;
+  CLAIR_CUDA(cudaHostAlloc(&p, rb, cudaHostAllocPortable));
+  return p;
+}
+
+void pinned_put(void* p, size_t bytes) {
+  if (!p) return;
+  size_t rb = 0;
+  const int c = pinned_class(bytes, &rb);
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  g_pinned_free[c].push_back(p);
+}
+
 cudaMemPool_t library_pool() {
   static std::mutex mu;
   static cudaMemPool_t pools[256] = {};
@@ -537,23 +575,42 @@ void residual32(const Csr& A, const float* b, const float* x, float* r, cudaStre
   spmv_launch<float, true>(A, A.val32, x, b, r, 1.f, 0.f, s);
 }
 
+// W lanes per row; the row's last entry in column r is its diagonal.
+template <int W>
 __global__ void inv_diag_kernel(const int* __restrict__ rowptr, const int* __restrict__ col,
                                 const double* __restrict__ val, int rows, double* __restrict__ dinv,
                                 int* __restrict__ bad) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= rows) return;
-  double d = 0.0;
-  for (int e = rowptr[r]; e < rowptr[r + 1]; ++e)
-    if (col[e] == r) d = val[e];
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int r = (int)(t / W), sub = (int)(t % W);
+  int last = -1;
+  if (r < rows)
+    for (int e = rowptr[r] + sub; e < rowptr[r + 1]; e += W)
+      if (col[e] == r) last = e;
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o, W));
+  if (r >= rows || sub != 0) return;
+  const double d = last >= 0 ? val[last] : 0.0;
   if (d == 0.0 || !isfinite(d)) atomicAdd(bad, 1);
   dinv[r] = d != 0.0 ? 1.0 / d : 0.0;
 }
 
-void inverse_diagonal(const Csr& A, double* dinv, cudaStream_t s) {
+void inverse_diagonal(const Csr& A, double* dinv, cudaStream_t s, int* bad_acc) {
+  const double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
+  int W = 1;
+  while (W < 32 && 4 * W < avg) W <<= 1;
+  const int blocks = (int)ceil_div((long long)A.rows * W, 256);
+  if (bad_acc) {  // the caller reads the count later, at a synchronisation it makes anyway
+    if (A.rows)
+      CLAIR_DISPATCH_W(W, (inv_diag_kernel<WW><<<blocks, 256, 0, s>>>(A.rowptr, A.col, A.val,
+                                                                       A.rows, dinv, bad_acc)));
+    CLAIR_LAUNCHED();
+    return;
+  }
   int* bad = dalloc<int>(1, s);
   CLAIR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-  if (A.rows) inv_diag_kernel<<<ceil_div(A.rows, 256), 256, 0, s>>>(A.rowptr, A.col, A.val, A.rows,
-                                                                      dinv, bad); ::clair::count_launch();
+  if (A.rows)
+    CLAIR_DISPATCH_W(W, (inv_diag_kernel<WW><<<blocks, 256, 0, s>>>(A.rowptr, A.col, A.val, A.rows,
+                                                                     dinv, bad)));
   CLAIR_LAUNCHED();
   int h = 0;
   CLAIR_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -678,6 +735,59 @@ void absmax_into(const double* x, long long n, unsigned long long* out, cudaStre
   if (n <= 0) return;
   absmax_kernel<<<grid_for(n), 256, 0, s>>>(x, n, out); ::clair::count_launch();
   CLAIR_LAUNCHED();
+}
+
+// Many short conversions or maxima in one launch: blockIdx.y picks the segment, the x
+// blocks stride over it (the end of a setup holds a few per level).
+__global__ void to_float_segments(SegList L) {
+  const int g = blockIdx.y;
+  const double* __restrict__ x = L.src[g];
+  float* __restrict__ y = L.dst[g];
+  const long long n = L.n[g];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+__global__ void absmax_segments(SegList L, unsigned long long* __restrict__ out) {
+  const int g = blockIdx.y;
+  const double* __restrict__ x = L.src[g];
+  const long long n = L.n[g];
+  double m = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(out + L.slot[g], (unsigned long long)__double_as_longlong(m));
+}
+
+static dim3 seg_grid(const SegList& L) {
+  long long mx = 1;
+  for (int g = 0; g < L.count; ++g) mx = std::max(mx, L.n[g]);
+  return dim3((unsigned)std::min<long long>(ceil_div(mx, 256), 4LL * sm_count()), (unsigned)L.count);
+}
+
+void SegBatch::add(const double* src, float* dst, long long n, int slot) {
+  if (n <= 0) return;
+  if (cur.count == SegList::kMax) flush();
+  cur.src[cur.count] = src;
+  cur.dst[cur.count] = dst;
+  cur.n[cur.count] = n;
+  cur.slot[cur.count] = slot;
+  ++cur.count;
+}
+
+void SegBatch::flush() {
+  if (!cur.count) return;
+  if (out)
+    absmax_segments<<<seg_grid(cur), 256, 0, s>>>(cur, out);
+  else
+    to_float_segments<<<seg_grid(cur), 256, 0, s>>>(cur);
+  ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  cur.count = 0;
 }
 
 bool all_finite(const double* x, long long n, cudaStream_t s) {

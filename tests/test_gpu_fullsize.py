@@ -42,12 +42,14 @@ def dev(a, dtype):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def setup_gpu(cl, prob, precision, degree=2, sweeps=5):
+def setup_gpu(cl, prob, precision, degree=2, sweeps=5, maxit=None):
     import torch
     p = cl.clair_params_default()
     p.precision = precision
     p.degree = degree
     p.b_smooth_iters = sweeps
+    if maxit:
+        p.gmres_maxit = maxit
     A = prob.A
     h = cl.clair_setup(dev(A.rowptr, torch.int32), dev(A.col, torch.int32),
                        dev(A.val, torch.float64), dev(prob.B, torch.float64), p)
@@ -187,7 +189,10 @@ def test_full_size_properties(cl, eps, degree, sweeps, converge):
     A = O.csr_of(prob.A)
     its, fell_back = {}, {}
     for precision in (0, 1):
-        h = setup_gpu(cl, prob, precision, degree, sweeps)
+        # pure advection: D^-1 A is I plus a nilpotent part, the coarse levels' Arnoldi
+        # weights are set by rounding (see omega_spread) and the FP64 iteration count moves
+        # with them (150 to 230 seen), so that case gets a larger iteration budget
+        h = setup_gpu(cl, prob, precision, degree, sweeps, maxit=400 if eps == 0.0 else None)
         try:
             g = level0(cl, h)
             check_galerkin(cl, h)
@@ -218,6 +223,51 @@ def test_full_size_properties(cl, eps, degree, sweeps, converge):
         assert not np.any(~cf & has & ~dep_c)
     if len(its) == 2 and not fell_back[1]:
         assert abs(its[0] - its[1]) <= 1, its
+
+
+def omega_spread(A, iters, seed, trials=2):
+    """Largest relative change of the oracle's weight when A's values are scaled entry by
+    entry by 1 + 1e-15 r (r uniform in [-1, 1], seeded): the part of omega that FP64
+    arithmetic does not determine.  Nearly pure advection makes D^-1 A close to I plus a
+    nilpotent part, whose Ritz values move like the k-th root of a perturbation; on such
+    a level no two summation orders need agree."""
+    ref = 1.0 / O.arnoldi_rho(A, iters, seed)
+    rng = np.random.default_rng(17)
+    out = 0.0
+    for _ in range(trials):
+        Ap = A.copy()
+        Ap.data = Ap.data * (1.0 + 1e-15 * rng.uniform(-1.0, 1.0, Ap.nnz))
+        out = max(out, abs(1.0 / O.arnoldi_rho(Ap, iters, seed) - ref) / ref)
+    return ref, out
+
+
+@pytest.mark.parametrize("eps,degree,sweeps", [(1e-2, 2, 5), (0.0, 1, 5)])
+def test_weights_of_every_level_match_oracle(cl, eps, degree, sweeps):
+    """Section 4's relaxation weight on every level of a full-size hierarchy: the GPU's
+    omega against the oracle's Arnoldi (same steps, same seeded start vector, seed + level)
+    on that level's own operator, as the GPU built it.  The large levels take the
+    multi-launch Arnoldi, the small ones the one-launch cluster run.  The bar is the
+    Ritz-value bar of the small parity cases plus 100 x what rounding-size changes of the
+    operator move the oracle's own weight (omega_spread); on the advection-diffusion
+    workload every level is held to the plain bar."""
+    prob = workloads.config2(eps=eps, degree=degree)
+    p = O.Params()
+    for precision in (0, 1):
+        h = setup_gpu(cl, prob, precision, degree, sweeps)
+        try:
+            nlev = cl.clair_stats(h).levels
+            for k in range(nlev - 1):
+                g = level0(cl, h, k)
+                if not g["nc"]:
+                    continue
+                ref, spread = omega_spread(g["A"], p.arnoldi_iters, p.seed + k)
+                if eps > 0:
+                    assert spread <= 1e-9, (k, spread)
+                dom = abs(g["omega"] - ref) / ref
+                assert dom <= OMEGA_TOL + 100.0 * spread, (precision, k, g["n"], g["omega"], ref,
+                                                            spread)
+        finally:
+            cl.clair_free(h)
 
 
 @pytest.mark.parametrize("eps", [0.0, 1e-4])
