@@ -117,10 +117,11 @@ typedef struct {
   int lsolve_kind_b3;
   int lsolve_blocks_per_sm;   /* (see clair_lsolve_config) */
   int lsolve_tuned;
-  int cycle_short_lanes;      /* FP32 cycle row kernels: 1 = about four entries per lane (one
-                                 thread per row up to 8 entries), 0 = lanes up to the mean
-                                 row length; both are timed on the first MIXED hierarchy of
-                                 the process on each device and the faster kept) */
+  int cycle_short_lanes;      /* FP32 cycle row kernels: 2 = about eight entries per lane (one
+                                 thread per row up to 16 entries), 1 = about four (one thread
+                                 up to 8), 0 = lanes up to the mean row length; all three are
+                                 timed on the first MIXED hierarchy of the process on each
+                                 device and the fastest kept */
   int cycle64_from;           /* CLAIR_MIXED: first level whose part of the cycle runs in FP64
                                  (its largest |R| or |P| weight, or a finer level's, is above
                                  1e3: FP32 copies of such weights lose their sums to

@@ -128,10 +128,10 @@ __device__ __forceinline__ T group_sum(T v) {
 }
 
 // Sum over CSR entries e0 <= e < e1 of val[e] * x[col[e]], in increasing e (lane `lane`
-// of W takes every W-th entry).  With one lane per row the row's indices and values are
-// loaded eight at a time before their gathers, so a short row costs two dependent memory
-// round trips instead of two per entry; the order and the contraction (acc + v * x into
-// one fma) are the same either way.
+// of W takes every W-th entry).  The row's indices and values are loaded eight (one lane
+// per row) or four (W lanes) at a time before their gathers, so a row costs two dependent
+// memory round trips per batch instead of two per entry; the order and the contraction
+// (acc + v * x into one fma) are the same as one entry at a time.
 template <int W, class T, class X>
 __device__ __forceinline__ T csr_row_dot(const int* __restrict__ col, const T* __restrict__ val,
                                          const X* __restrict__ x, int e0, int e1, int lane) {
@@ -151,7 +151,19 @@ __device__ __forceinline__ T csr_row_dot(const int* __restrict__ col, const T* _
         if (eb + q < e1) acc += v[q] * __ldg(&x[c[q]]);
     }
   } else {
-    for (int e = e0 + lane; e < e1; e += W) acc += val[e] * __ldg(&x[col[e]]);
+    // four entries per lane in flight: indices and values first, then the four gathers,
+    // then the same running sum in the same order as one entry at a time
+    int e = e0 + lane;
+    for (; e + 3 * W < e1; e += 4 * W) {
+      const int c0 = col[e], c1 = col[e + W], c2 = col[e + 2 * W], c3 = col[e + 3 * W];
+      const T v0 = val[e], v1 = val[e + W], v2 = val[e + 2 * W], v3 = val[e + 3 * W];
+      const X x0 = __ldg(&x[c0]), x1 = __ldg(&x[c1]), x2 = __ldg(&x[c2]), x3 = __ldg(&x[c3]);
+      acc += v0 * x0;
+      acc += v1 * x1;
+      acc += v2 * x2;
+      acc += v3 * x3;
+    }
+    for (; e < e1; e += W) acc += val[e] * __ldg(&x[col[e]]);
   }
   return acc;
 }

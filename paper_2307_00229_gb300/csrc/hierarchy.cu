@@ -977,7 +977,7 @@ static void build_cycle_graph(clair_hierarchy* h) {
   cudaGraphExec_t best = nullptr;
   long long best_k = 0;
   float best_ms = 0.f;
-  for (int lanes = 0; lanes <= 1; ++lanes) {
+  for (int lanes = 0; lanes <= 2; ++lanes) {
     h->short_lanes = lanes;
     long long kk = 0;
     cudaGraphExec_t e = capture_cycle(h, &kk);

@@ -69,6 +69,36 @@ void Segments::release(cudaStream_t s) {
   len = 0;
 }
 
+// MG dot products (compile-time count, so no FP64 work for absent vectors) of the chunk's
+// rows, summed over the block: warp trees, then the warps in order.
+template <int MG>
+__device__ __forceinline__ void dot_group(const double* __restrict__ V, long long ldv, int q0,
+                                          const double* __restrict__ w, long long lo, long long hi,
+                                          int nchunk, double* __restrict__ partial,
+                                          double (*sh)[KR_THREADS / 32]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double acc[MG];
+#pragma unroll
+  for (int g = 0; g < MG; ++g) acc[g] = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += KR_THREADS) {
+    const double wi = w[i];
+#pragma unroll
+    for (int g = 0; g < MG; ++g) acc[g] = fma(V[(long long)(q0 + g) * ldv + i], wi, acc[g]);
+  }
+#pragma unroll
+  for (int g = 0; g < MG; ++g) {
+    const double v = warp_sum(acc[g]);
+    if (lane == 0) sh[g][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < MG) {
+    double v = 0.0;
+    for (int k = 0; k < KR_THREADS / 32; ++k) v += sh[threadIdx.x][k];
+    partial[(long long)(q0 + threadIdx.x) * nchunk + blockIdx.x] = v;
+  }
+  __syncthreads();
+}
+
 // partial[q * nchunk + c] = sum over the rows of chunk c of V_q[i] * w[i], q < m
 // (V_q at V + q * ldv); rows in increasing order per thread, threads in a fixed tree.
 __global__ void __launch_bounds__(KR_THREADS)
@@ -78,29 +108,17 @@ seg_dot_partial(const double* __restrict__ V, long long ldv, int m, const double
   __shared__ double sh[KR_GROUP][KR_THREADS / 32];
   const int c = blockIdx.x;
   const long long lo = clo[c], hi = chi[c];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int q0 = 0; q0 < m; q0 += KR_GROUP) {
-    double acc[KR_GROUP];
-#pragma unroll
-    for (int g = 0; g < KR_GROUP; ++g) acc[g] = 0.0;
-    for (long long i = lo + threadIdx.x; i < hi; i += KR_THREADS) {
-      const double wi = w[i];
-#pragma unroll
-      for (int g = 0; g < KR_GROUP; ++g)
-        if (q0 + g < m) acc[g] = fma(V[(long long)(q0 + g) * ldv + i], wi, acc[g]);
+    switch (min(KR_GROUP, m - q0)) {  // block-uniform
+      case 1: dot_group<1>(V, ldv, q0, w, lo, hi, nchunk, partial, sh); break;
+      case 2: dot_group<2>(V, ldv, q0, w, lo, hi, nchunk, partial, sh); break;
+      case 3: dot_group<3>(V, ldv, q0, w, lo, hi, nchunk, partial, sh); break;
+      case 4: dot_group<4>(V, ldv, q0, w, lo, hi, nchunk, partial, sh); break;
+      case 5: dot_group<5>(V, ldv, q0, w, lo, hi, nchunk, partial, sh); break;
+      case 6: dot_group<6>(V, ldv, q0, w, lo, hi, nchunk, partial, sh); break;
+      case 7: dot_group<7>(V, ldv, q0, w, lo, hi, nchunk, partial, sh); break;
+      default: dot_group<8>(V, ldv, q0, w, lo, hi, nchunk, partial, sh); break;
     }
-#pragma unroll
-    for (int g = 0; g < KR_GROUP; ++g) {
-      const double v = warp_sum(acc[g]);
-      if (lane == 0) sh[g][wid] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < KR_GROUP && q0 + threadIdx.x < m) {
-      double v = 0.0;
-      for (int k = 0; k < KR_THREADS / 32; ++k) v += sh[threadIdx.x][k];
-      partial[(long long)(q0 + threadIdx.x) * nchunk + c] = v;
-    }
-    __syncthreads();
   }
 }
 

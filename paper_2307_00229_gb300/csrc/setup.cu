@@ -803,6 +803,12 @@ static int lanes_of(const Csr& A, bool fp64) {
     while (w < 32 && 4 * w < avg) w <<= 1;
     return w;
   }
+  if (cycle_short_lanes() == 2) {  // FP32, about eight entries per lane (one thread up to 16 entries)
+    if (avg <= 16.0) return 1;
+    int w = 2;
+    while (w < 32 && 8 * w < avg) w <<= 1;
+    return w;
+  }
   int w = 2;
   while (w < 32 && w < avg) w <<= 1;
   return w;
