@@ -216,6 +216,8 @@ void drop_zeros(Csr& C, cudaStream_t s);
 void inverse_diagonal(const Csr& A, double* dinv, cudaStream_t s, int* bad_acc = nullptr);
 // Float copies.
 void to_float(const double* x, float* y, long long n, cudaStream_t s);
+// y = x as a kernel (a node the cycle graph can chain by programmatic dependence)
+void copy_f64(const double* x, double* y, long long n, cudaStream_t s);
 void to_double(const float* x, double* y, long long n, cudaStream_t s);
 // Deterministic dot products: out[j] = <V_j, w> for j < m (V column-major n x m, ld = n).
 void multi_dot(const double* V, int m, const double* w, int n, double* out, double* partial,
@@ -263,6 +265,40 @@ int partial_blocks();  // number of blocks used by the deterministic reductions
 // timing its cycle graph.
 int cycle_short_lanes();
 void set_cycle_short_lanes(int lanes);
+
+// Programmatic dependent launch for the captured V-cycle.  While pdl_launches() is set
+// (the capture of the cycle graph), the cycle's row kernels are launched with
+// programmatic stream serialization: a kernel's blocks may be scheduled while its
+// predecessor runs, and wait at pdl_prologue() until the predecessor has completed and
+// its writes are visible, so the graph's kernel-to-kernel gaps shrink to that wait.
+// Launched without the attribute, the prologue returns at once.
+bool pdl_launches();
+void set_pdl_launches(bool on);
+
+__device__ __forceinline__ void pdl_prologue() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args... args) {
+  if (!pdl_launches()) {
+    kernel<<<grid, block, smem, s>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  CLAIR_CUDA(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+}
 
 // ------------------------------------------------------------------------------------
 // Segmented Krylov building blocks (krylov.cu): independent Krylov processes in lockstep,

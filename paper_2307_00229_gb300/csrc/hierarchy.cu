@@ -884,9 +884,9 @@ static void apply_precond_direct(clair_hierarchy* h, int k, const double* v, dou
     const float* out = vcycle_level<float>(h, k);
     to_double(out, z, L.n, s);
   } else {
-    CLAIR_CUDA(cudaMemcpyAsync(L.b64, v, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
+    copy_f64(v, L.b64, L.n, s);
     const double* out = vcycle_level<double>(h, k);
-    CLAIR_CUDA(cudaMemcpyAsync(z, out, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
+    copy_f64(out, z, L.n, s);
   }
 }
 
@@ -904,9 +904,16 @@ static cudaGraphExec_t capture_cycle(clair_hierarchy* h, long long* kernels) {
   const long long before = launch_count();
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
+  struct PdlScope {  // the captured kernels chain by programmatic dependence
+    PdlScope() { set_pdl_launches(true); }
+    ~PdlScope() { set_pdl_launches(false); }
+  };
   try {
     CLAIR_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    apply_precond_direct(h, 0, h->vin, h->zout);
+    {
+      PdlScope pdl;
+      apply_precond_direct(h, 0, h->vin, h->zout);
+    }
     CLAIR_CUDA(cudaStreamEndCapture(cs, &g));
     CLAIR_CUDA(cudaGraphInstantiate(&exec, g, 0));
   } catch (...) {

@@ -767,6 +767,7 @@ __global__ void jacobi_kernel(const int* __restrict__ rowptr, const int* __restr
                               const signed char* __restrict__ cf, int which, T omega,
                               const T* __restrict__ b, const T* __restrict__ xin,
                               T* __restrict__ xout, const T* __restrict__ omega_dev) {
+  pdl_prologue();
   if (omega_dev) omega = *omega_dev;  // weight produced on the device by the Arnoldi step
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int r = (int)(t / W), lane = (int)(t % W);
@@ -786,6 +787,7 @@ __global__ void jacobi_kernel(const int* __restrict__ rowptr, const int* __restr
 template <class T>
 __global__ void jacobi_first(const T* __restrict__ dinv, int rows, const signed char* __restrict__ cf,
                              int which, T omega, const T* __restrict__ b, T* __restrict__ x) {
+  pdl_prologue();
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
        r += (long long)gridDim.x * blockDim.x)
     x[r] = cf[r] == which ? omega * dinv[r] * b[r] : T(0);
@@ -821,9 +823,8 @@ void jacobi(const Csr& A, const T* vals, const T* dinv, const signed char* cf, i
   if (!A.rows) return;
   const int W = lanes_of(A, sizeof(T) == 8);
   const int blocks = ceil_div((long long)A.rows * W, 256);
-  CLAIR_DISPATCH_W2(W, (jacobi_kernel<WW, T><<<blocks, 256, 0, s>>>(A.rowptr, A.col, vals, dinv,
-                                                                    A.rows, cf, which, omega, b,
-                                                                    xin, xout, omega_dev)));
+  CLAIR_DISPATCH_W2(W, launch_k(jacobi_kernel<WW, T>, blocks, 256, 0, s, A.rowptr, A.col, vals,
+                                 dinv, A.rows, cf, which, omega, b, xin, xout, omega_dev));
   CLAIR_LAUNCHED();
 }
 
@@ -853,8 +854,8 @@ template <class T>
 void jacobi_from_zero(int rows, const T* dinv, const signed char* cf, int which, T omega,
                       const T* b, T* x, cudaStream_t s) {
   if (!rows) return;
-  jacobi_first<T><<<std::min(ceil_div(rows, 256), 32 * sm_count()), 256, 0, s>>>(dinv, rows, cf,
-                                                                                 which, omega, b, x); ::clair::count_launch();
+  launch_k(jacobi_first<T>, std::min(ceil_div(rows, 256), 32 * sm_count()), 256, 0, s, dinv, rows,
+           cf, which, omega, b, x); ::clair::count_launch();
   CLAIR_LAUNCHED();
 }
 template void jacobi_from_zero<double>(int, const double*, const signed char*, int, double,
@@ -1900,6 +1901,7 @@ template <class T>
 __global__ void dense_gemv_blocks(const T* __restrict__ Inv, const int* __restrict__ off,
                                   const long long* __restrict__ ioff, int nblk, int n,
                                   const T* __restrict__ b, T* __restrict__ x) {
+  pdl_prologue();
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     int lo = 0, hi = nblk;  // block holding row r: largest i with off[i] <= r
     while (hi - lo > 1) {
@@ -1917,7 +1919,7 @@ template <class T>
 void coarse_apply(const T* Inv, const int* d_off, const long long* d_ioff, int nblk, int n,
                   const T* b, T* x, cudaStream_t s) {
   if (!n) return;
-  dense_gemv_blocks<T><<<ceil_div(n, 128), 128, 0, s>>>(Inv, d_off, d_ioff, nblk, n, b, x); ::clair::count_launch();
+  launch_k(dense_gemv_blocks<T>, ceil_div(n, 128), 128, 0, s, Inv, d_off, d_ioff, nblk, n, b, x); ::clair::count_launch();
   CLAIR_LAUNCHED();
 }
 template void coarse_apply<double>(const double*, const int*, const long long*, int, int,

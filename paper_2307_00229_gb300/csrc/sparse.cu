@@ -483,6 +483,9 @@ void csr_transpose(const Csr& A, Csr& At, int** perm_out, cudaStream_t s) {
 static thread_local int g_short_lanes = 0;
 int cycle_short_lanes() { return g_short_lanes; }
 void set_cycle_short_lanes(int lanes) { g_short_lanes = lanes; }
+static thread_local bool g_pdl = false;
+bool pdl_launches() { return g_pdl; }
+void set_pdl_launches(bool on) { g_pdl = on; }
 
 static int lanes_for(const Csr& A, bool fp64) {
   double avg = A.rows ? (double)A.nnz / A.rows : 1.0;
@@ -541,6 +544,7 @@ template <int W, class T, bool RESID>
 __global__ void spmv_kernel(const int* __restrict__ rowptr, const int* __restrict__ col,
                             const T* __restrict__ val, int rows, const T* __restrict__ x,
                             const T* __restrict__ b, T* __restrict__ y, T alpha, T beta) {
+  pdl_prologue();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int r = (int)(t / W), lane = (int)(t % W);
   const bool ok = r < rows;  // no early exit: every lane takes part in the shuffles
@@ -563,8 +567,8 @@ static void spmv_launch(const Csr& A, const T* vals, const T* x, const T* b, T* 
   int W = lanes_for(A, sizeof(T) == 8);
   long long threads = (long long)A.rows * W;
   int blocks = ceil_div(threads, 256);
-  CLAIR_DISPATCH_W(W, (spmv_kernel<WW, T, RESID><<<blocks, 256, 0, s>>>(A.rowptr, A.col, vals, A.rows,
-                                                                       x, b, y, alpha, beta)));
+  CLAIR_DISPATCH_W(W, launch_k(spmv_kernel<WW, T, RESID>, blocks, 256, 0, s, A.rowptr, A.col, vals,
+                                A.rows, x, b, y, alpha, beta));
   CLAIR_LAUNCHED();
 }
 
@@ -626,23 +630,36 @@ void inverse_diagonal(const Csr& A, double* dinv, cudaStream_t s, int* bad_acc) 
 }
 
 __global__ void to_float_kernel(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  pdl_prologue();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     y[i] = (float)x[i];
 }
 __global__ void to_double_kernel(const float* __restrict__ x, double* __restrict__ y, long long n) {
+  pdl_prologue();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     y[i] = (double)x[i];
 }
+__global__ void copy_f64_kernel(const double* __restrict__ x, double* __restrict__ y, long long n) {
+  pdl_prologue();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i];
+}
+void copy_f64(const double* x, double* y, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  launch_k(copy_f64_kernel, grid_for(n), 256, 0, s, x, y, n); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+}
 void to_float(const double* x, float* y, long long n, cudaStream_t s) {
   if (n <= 0) return;
-  to_float_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n); ::clair::count_launch();
+  launch_k(to_float_kernel, grid_for(n), 256, 0, s, x, y, n); ::clair::count_launch();
   CLAIR_LAUNCHED();
 }
 void to_double(const float* x, double* y, long long n, cudaStream_t s) {
   if (n <= 0) return;
-  to_double_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n); ::clair::count_launch();
+  launch_k(to_double_kernel, grid_for(n), 256, 0, s, x, y, n); ::clair::count_launch();
   CLAIR_LAUNCHED();
 }
 
