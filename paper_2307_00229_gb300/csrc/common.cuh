@@ -214,6 +214,42 @@ void drop_zeros(Csr& C, cudaStream_t s);
 // dinv = 1 / diag(A); rows with a missing, zero or nonfinite diagonal are an error, raised
 // here (bad_acc null, one host synchronisation) or counted into *bad_acc for the caller.
 void inverse_diagonal(const Csr& A, double* dinv, cudaStream_t s, int* bad_acc = nullptr);
+
+// The sparsity pattern of Algorithm 1 in two stages, so that other work can be issued
+// between them: pattern_count launches the counting pass, pattern_fill reads the count
+// back and builds the rows (and releases the job's buffers).
+struct PatternJob {
+  Csr Wm;
+  const unsigned char* sW = nullptr;
+  const signed char* cf = nullptr;
+  const int* cpts = nullptr;
+  int nc = 0, n = 0, degree = 0;
+  const int* Mrp = nullptr;
+  const int* Mcol = nullptr;
+  int* count = nullptr;
+  int* err = nullptr;
+  int* start = nullptr;
+  int* buf = nullptr;
+  long long cap = 0;
+  unsigned long long* bump = nullptr;
+};
+PatternJob pattern_count(const Csr& Wm, const unsigned char* sW, const signed char* cf,
+                         const int* cpts, int nc, int n, int degree, const int* Mrp,
+                         const int* Mcol, cudaStream_t s);
+void pattern_fill(PatternJob& j, Csr& Z, cudaStream_t s);
+
+// Vectors relaxed together by the mode smoothing: side g = blockIdx.y relaxes x[g] with its
+// own operator (A for the P side, A^T for the R side, one entry per mode) and ping-pongs
+// with y[g]; D^-1, the splitting and the weight are shared.
+struct SmoothSides {
+  static constexpr int kMax = 2 * CLAIR_KMAX;
+  const int* rowptr[kMax];
+  const int* col[kMax];
+  const double* val[kMax];
+  double* x[kMax];
+  double* y[kMax];
+  int count;
+};
 // Float copies.
 void to_float(const double* x, float* y, long long n, cudaStream_t s);
 // y = x as a kernel (a node the cycle graph can chain by programmatic dependence)

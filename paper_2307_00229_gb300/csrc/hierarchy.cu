@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -29,6 +30,9 @@ void jacobi(const Csr& A, const T* vals, const T* dinv, const signed char* cf, i
             const T* b, const T* xin, T* xout, cudaStream_t s, const T* omega_dev = nullptr);
 void smooth_modes(const Csr& M, const double* dinv, const signed char* cf, const double* omega_dev,
                   int sweeps, double* Bv, double* tmp, cudaStream_t s);
+void smooth_modes_sides(const SmoothSides& sides, int rows, double avg_row, const double* dinv,
+                        const signed char* cf, const double* omega_dev, double omega, int sweeps,
+                        cudaStream_t s);
 void transfer_solve(const Csr& Ahat, const int* cpts, Csr& Z, int precision, LocalStats& st,
                     cudaStream_t s);
 void transfer_project(const signed char* cf, const int* cpts, Csr& Z, const double* B, int k,
@@ -125,6 +129,9 @@ struct clair_hierarchy {
   double setup_ms = 0.0;
   double phase_ms[clair::PH_COUNT] = {};   // setup, per phase
   double level_phase_ms[32 * clair::PH_COUNT] = {};  // setup, per level and phase
+  // event marks of the last setup and solve, read when the statistics are asked for (an
+  // instrument, kept off the setup's and the solve's own time)
+  std::unique_ptr<clair::PhaseClock> setup_clock, solve_clock;
   double level_span_ms[32] = {};           // setup: main-stream time from level to level
   double solve_ms[clair::PH_COUNT] = {};   // last solve, per phase
   cudaGraphExec_t cycle_exec = nullptr;     // captured fine-level V(1,1) cycle
@@ -568,10 +575,27 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
       break;
     }
     CLAIR_CUDA(cudaEventRecord(ss.split, s));
+    // interpolation-strength masks for the two patterns
+    // R: Algorithm 1 on A^T, walked on A, S(A^T) uses the row maxima of A^T
+    // P: Algorithm 1 on A,   walked on A^T, S(A) uses the row maxima of A
+    unsigned char* sR = sA;   // reuse buffers (the splitting is done)
+    unsigned char* sP = sAt;
+    Csr Pt;
+    int* Mrp = nullptr;
+    int* Mcol = nullptr;
+    PatternJob jobR, jobP;
+    {
+      ClockScope clk(PH_PATTERN, s);
+      strength(L.A, rmaxAt, p.theta_interp, 1, sR, s);
+      strength(At, rmaxA, p.theta_interp, 1, sP, s);
+      if (agg) aggregate_members(agg, n, L.nc, &Mrp, &Mcol, s);
+      if (!sym) jobR = pattern_count(L.A, sR, L.cf, L.cpts, L.nc, n, p.degree, Mrp, Mcol, s);
+      jobP = pattern_count(At, sP, L.cf, L.cpts, L.nc, n, p.degree, Mrp, Mcol, s);
+    }
+    // the mode smoothing on s2 is issued while the counting passes run on s
     CLAIR_CUDA(cudaStreamWaitEvent(ss.s2, ss.split, 0));
     {
       ClockScope clk(PH_SMOOTH, ss.s2);
-      double* tmp = dalloc<double>(n, ss.s2);
       // each mode vector separately; the symmetric variant (R = P^T) needs only A's
       double* wd = nullptr;
       if (batch) {
@@ -580,36 +604,34 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
         instance_weights<double><<<ceil_div(n, 256), 256, 0, ss.s2>>>(L.inst, om_k, L.dinv, n, wd); ::clair::count_launch();
         CLAIR_LAUNCHED();
       }
+      // every mode of both sides in one launch per relaxation (A for P, A^T for R)
+      SmoothSides sides{};
+      double* tmps = dalloc<double>((size_t)n * km * (sym ? 1 : 2), ss.s2);
       for (int a = 0; a < km; ++a) {
-        double* bp = L.B_P + (size_t)a * n;
-        double* br = L.B_R + (size_t)a * n;
-        smooth_modes(L.A, batch ? wd : L.dinv, L.cf, batch ? nullptr : om_k, p.b_smooth_iters, bp,
-                     tmp, ss.s2);
-        if (sym)
-          CLAIR_CUDA(cudaMemcpyAsync(br, bp, sizeof(double) * n, cudaMemcpyDeviceToDevice, ss.s2));
-        else
-          smooth_modes(At, batch ? wd : L.dinv, L.cf, batch ? nullptr : om_k, p.b_smooth_iters, br,
-                       tmp, ss.s2);
+        for (int side = 0; side < (sym ? 1 : 2); ++side) {
+          const Csr& M = side == 0 ? L.A : At;
+          const int g = sides.count++;
+          sides.rowptr[g] = M.rowptr;
+          sides.col[g] = M.col;
+          sides.val[g] = M.val;
+          sides.x[g] = (side == 0 ? L.B_P : L.B_R) + (size_t)a * n;
+          sides.y[g] = tmps + (size_t)g * n;
+        }
       }
+      smooth_modes_sides(sides, n, (double)L.A.nnz / n, batch ? wd : L.dinv, L.cf,
+                         batch ? nullptr : om_k, 1.0, p.b_smooth_iters, ss.s2);
+      if (sym)
+        for (int a = 0; a < km; ++a)
+          CLAIR_CUDA(cudaMemcpyAsync(L.B_R + (size_t)a * n, L.B_P + (size_t)a * n,
+                                     sizeof(double) * n, cudaMemcpyDeviceToDevice, ss.s2));
+      dfree(tmps, ss.s2);
       dfree(wd, ss.s2);
-      dfree(tmp, ss.s2);
     }
     CLAIR_CUDA(cudaEventRecord(ss.join, ss.s2));
-    // interpolation-strength masks for the two patterns
-    // R: Algorithm 1 on A^T, walked on A, S(A^T) uses the row maxima of A^T
-    // P: Algorithm 1 on A,   walked on A^T, S(A) uses the row maxima of A
-    unsigned char* sR = sA;   // reuse buffers (the splitting is done)
-    unsigned char* sP = sAt;
-    Csr Pt;
     {
       ClockScope clk(PH_PATTERN, s);
-      strength(L.A, rmaxAt, p.theta_interp, 1, sR, s);
-      strength(At, rmaxA, p.theta_interp, 1, sP, s);
-      int* Mrp = nullptr;
-      int* Mcol = nullptr;
-      if (agg) aggregate_members(agg, n, L.nc, &Mrp, &Mcol, s);
-      if (!sym) build_pattern(L.A, sR, L.cf, L.cpts, L.nc, n, p.degree, Mrp, Mcol, L.R, s);
-      build_pattern(At, sP, L.cf, L.cpts, L.nc, n, p.degree, Mrp, Mcol, Pt, s);
+      if (!sym) pattern_fill(jobR, L.R, s);
+      pattern_fill(jobP, Pt, s);
       dfree(Mrp, s);
       dfree(Mcol, s);
       dfree(agg, s);
@@ -1422,8 +1444,8 @@ static clair_status setup_common(int ninst, const int* offsets_host, int n, int 
     if (cf_marker) validate_cf(cf_marker, n, s);
     h->B0 = dalloc<double>((size_t)n * kmodes, s);
     CLAIR_CUDA(cudaMemcpyAsync(h->B0, B, sizeof(double) * n * kmodes, cudaMemcpyDeviceToDevice, s));
-    PhaseClock clock;
-    set_active_clock(&clock);
+    h->setup_clock.reset(new PhaseClock());
+    set_active_clock(h->setup_clock.get());
     // per-level counters stay on the device until the end of the setup
     h->st.dev = dalloc<unsigned long long>(6, s);
     CLAIR_CUDA(cudaMemsetAsync(h->st.dev, 0, 6 * sizeof(unsigned long long), s));
@@ -1435,7 +1457,6 @@ static clair_status setup_common(int ninst, const int* offsets_host, int n, int 
     build_cycle_graph(h);
     h->st.absorb_device(s);  // the one synchronisation at the end
     dfree(h->st.dev, s);
-    clock.collect(h->phase_ms, h->level_phase_ms, 32);
     CLAIR_CUDA(cudaEventRecord(e1, s));
     CLAIR_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -1524,8 +1545,8 @@ clair_status clair_solve(clair_h h, const double* f, double* u, int nrhs, void* 
   cudaStream_t keep = h->stream;
   h->stream = static_cast<cudaStream_t>(stream);
   bool ok = false;
-  PhaseClock clock;
-  set_active_clock(&clock);
+  h->solve_clock.reset(new PhaseClock());
+  set_active_clock(h->solve_clock.get());
   for (double& v : h->solve_ms) v = 0.0;
   try {
     ok = krylov_solve(h, nrhs, f, u);
@@ -1535,7 +1556,6 @@ clair_status clair_solve(clair_h h, const double* f, double* u, int nrhs, void* 
     throw;
   }
   set_active_clock(nullptr);
-  clock.collect(h->solve_ms);
   h->stream = keep;
   const int ninst = h->ninst;
   for (int r = 0; r < nrhs; ++r) {
@@ -1585,6 +1605,14 @@ clair_status clair_vcycle(clair_h h, int level, const double* b, double* x, void
 clair_status clair_stats(clair_h h, clair_stats_t* o) {
   CLAIR_API_BEGIN
   CLAIR_REQUIRE(h && o, CLAIR_ERR_ARG, "clair_stats: null pointer");
+  if (h->setup_clock) {
+    h->setup_clock->collect(h->phase_ms, h->level_phase_ms, 32);
+    h->setup_clock.reset();
+  }
+  if (h->solve_clock) {
+    h->solve_clock->collect(h->solve_ms);
+    h->solve_clock.reset();
+  }
   memset(o, 0, sizeof(*o));
   o->levels = (int)h->lv.size();
   double nnz0 = h->lv[0].A.nnz, sum = 0.0;

@@ -771,10 +771,12 @@ static size_t persist_smem(const bool* has) {
   return b;
 }
 
+constexpr int LP_WAVES = 4;  // blocks launched per resident block of the persistent launch
+
 template <class Real, class VT>
 __global__ void __launch_bounds__(LP_THREADS)
 lsolve_persist(SideArgs<VT> S0, SideArgs<VT> S1, int nsides, int kind_b1, int kind_b3,
-               int* __restrict__ ticket, unsigned long long* __restrict__ nsingular) {
+               int* __restrict__ ticket, unsigned long long* __restrict__ nsingular, int budget) {
   extern __shared__ __align__(16) unsigned char lp_smem[];
   auto& sm = *reinterpret_cast<PersistSmem<Real>*>(lp_smem);
   __shared__ int seg_end[8], seg_kind[8];
@@ -794,7 +796,7 @@ lsolve_persist(SideArgs<VT> S0, SideArgs<VT> S1, int nsides, int kind_b1, int ki
   __syncthreads();
   const int total = seg_end[7];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (;;) {
+  for (int taken = 0; taken < budget; ++taken) {
     if (threadIdx.x == 0) s_task = atomicAdd(ticket, 1);
     __syncthreads();
     const int task = s_task;
@@ -1432,10 +1434,17 @@ static void persistent_launch(const SideArgs<VT>* sa, int nsides, const int (*co
   CLAIR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, lsolve_persist<Real, VT>, LP_THREADS,
                                                            smem));
   const int per_sm = std::max(1, cfg.blocks_per_sm > 0 ? std::min(fit, cfg.blocks_per_sm) : fit);
-  const int grid = (int)std::min<long long>(tasks, (long long)sm_count() * per_sm);
+  // LP_WAVES times the resident blocks, each taking at most an even share of the tasks
+  // from the ticket and then leaving: the budgets add up to every task, and a leaving
+  // block frees its slot for the other stream's waiting blocks (the mode smoothing, of
+  // higher priority), which a block that stays to the end would hold off
+  const long long resident = (long long)sm_count() * per_sm;
+  const int grid = (int)std::min<long long>(tasks, resident * LP_WAVES);
+  const int budget = (int)((tasks + grid - 1) / grid);
   CLAIR_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), s));
   lsolve_persist<Real, VT><<<grid, LP_THREADS, smem, s>>>(sa[0], nsides > 1 ? sa[1] : sa[0], nsides,
-                                                          cfg.kind_b1, cfg.kind_b3, ticket, nsing); ::clair::count_launch();
+                                                          cfg.kind_b1, cfg.kind_b3, ticket, nsing,
+                                                          budget); ::clair::count_launch();
   CLAIR_LAUNCHED();
 }
 

@@ -690,71 +690,99 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
 
 // Builds the pattern CSR Z (nc rows) for Algorithm 1 on Ahat, walking Wm = Ahat^T with
 // its strength mask sW.
-void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf, const int* cpts,
-                   int nc, int n, int degree, const int* Mrp, const int* Mcol, Csr& Z,
-                   cudaStream_t s) {
+// First stage of the pattern: the counting pass (with the stash), launched only.
+PatternJob pattern_count(const Csr& Wm, const unsigned char* sW, const signed char* cf,
+                         const int* cpts, int nc, int n, int degree, const int* Mrp,
+                         const int* Mcol, cudaStream_t s) {
   CLAIR_REQUIRE(degree == 1 || degree == 2, CLAIR_ERR_UNSUPPORTED,
                 "pattern degree %d not supported (1 or 2)", degree);
-  Z.rows = nc;
-  Z.cols = n;
-  int* count = dalloc<int>(nc + 1, s);
-  int* err = dalloc<int>(1, s);
-  CLAIR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  PatternJob j;
+  j.Wm = Wm;
+  j.sW = sW;
+  j.cf = cf;
+  j.cpts = cpts;
+  j.nc = nc;
+  j.n = n;
+  j.degree = degree;
+  j.Mrp = Mrp;
+  j.Mcol = Mcol;
+  j.count = dalloc<int>(nc + 1, s);
+  j.err = dalloc<int>(1, s);
+  CLAIR_CUDA(cudaMemsetAsync(j.err, 0, sizeof(int), s));
   const int g = ceil_div(nc, PT_WARPS);
   const bool agg = Mrp != nullptr;
   // the stash: room for about twice the entries of Wm (rows beyond it are built twice)
-  PatternStash st{};
   if (nc) {
-    st.cap = std::min<long long>(2LL * Wm.nnz + 8LL * nc + 1024, 64LL << 20);
-    st.start = dalloc<int>(nc, s);
-    st.buf = dalloc<int>((size_t)st.cap, s);
-    st.bump = dalloc<unsigned long long>(1, s);
-    CLAIR_CUDA(cudaMemsetAsync(st.bump, 0, sizeof(unsigned long long), s));
+    j.cap = std::min<long long>(2LL * Wm.nnz + 8LL * nc + 1024, 64LL << 20);
+    j.start = dalloc<int>(nc, s);
+    j.buf = dalloc<int>((size_t)j.cap, s);
+    j.bump = dalloc<unsigned long long>(1, s);
+    CLAIR_CUDA(cudaMemsetAsync(j.bump, 0, sizeof(unsigned long long), s));
+    const PatternStash st{j.start, j.buf, j.cap, j.bump};
     if (agg)
       pattern_kernel<true, true><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
-                                                             degree, Mrp, Mcol, count, nullptr,
-                                                             nullptr, err, st);
+                                                             degree, Mrp, Mcol, j.count, nullptr,
+                                                             nullptr, j.err, st);
     else
       pattern_kernel<true, false><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
-                                                              degree, nullptr, nullptr, count,
-                                                              nullptr, nullptr, err, st);
+                                                              degree, nullptr, nullptr, j.count,
+                                                              nullptr, nullptr, j.err, st);
     ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
-  // a row that overflows the table does so in the counting pass (the filling pass inserts
-  // the same keys), so its flag is read back with the scan total
+  return j;
+}
+
+// Second stage: the row lengths' scan (one host read: the entry count and the overflow
+// flag of the counting pass), then the rows: stashed rows copied, the others built again.
+void pattern_fill(PatternJob& j, Csr& Z, cudaStream_t s) {
+  Z.rows = j.nc;
+  Z.cols = j.n;
+  const int nc = j.nc;
+  const int g = ceil_div(nc, PT_WARPS);
+  const bool agg = j.Mrp != nullptr;
+  const PatternStash st{j.start, j.buf, j.cap, j.bump};
   Z.rowptr = dalloc<int>(nc + 1, s);
   int h = 0;
-  Z.nnz = (int)exclusive_scan(count, Z.rowptr, nc, s, true, err, &h);
+  Z.nnz = (int)exclusive_scan(j.count, Z.rowptr, nc, s, true, j.err, &h);
+  auto release = [&]() {
+    dfree(j.count, s);
+    dfree(j.err, s);
+    dfree(j.start, s);
+    dfree(j.buf, s);
+    dfree(j.bump, s);
+  };
   if (h) {
-    dfree(count, s);
-    dfree(err, s);
+    release();
     dfree(Z.rowptr, s);
-    dfree(st.start, s);
-    dfree(st.buf, s);
-    dfree(st.bump, s);
     Z.rowptr = nullptr;
     CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "pattern row exceeds %d entries", PT_CAP);
   }
   Z.col = dalloc<int>(Z.nnz, s);
   if (nc) {
-    // stashed rows are copied, the others built again
+    const Csr& Wm = j.Wm;
     if (agg)
-      pattern_kernel<false, true><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
-                                                              degree, Mrp, Mcol, nullptr, Z.rowptr,
-                                                              Z.col, err, st);
+      pattern_kernel<false, true><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, j.sW, j.cf, j.cpts,
+                                                              nc, j.degree, j.Mrp, j.Mcol, nullptr,
+                                                              Z.rowptr, Z.col, j.err, st);
     else
-      pattern_kernel<false, false><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts,
-                                                               nc, degree, nullptr, nullptr,
-                                                               nullptr, Z.rowptr, Z.col, err, st);
+      pattern_kernel<false, false><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, j.sW, j.cf,
+                                                               j.cpts, nc, j.degree, nullptr,
+                                                               nullptr, nullptr, Z.rowptr, Z.col,
+                                                               j.err, st);
     ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
-  dfree(count, s);
-  dfree(err, s);
-  dfree(st.start, s);
-  dfree(st.buf, s);
-  dfree(st.bump, s);
+  release();
+}
+
+// Builds the pattern CSR Z (nc rows) for Algorithm 1 on Ahat, walking Wm = Ahat^T with
+// its strength mask sW.
+void build_pattern(const Csr& Wm, const unsigned char* sW, const signed char* cf, const int* cpts,
+                   int nc, int n, int degree, const int* Mrp, const int* Mcol, Csr& Z,
+                   cudaStream_t s) {
+  PatternJob j = pattern_count(Wm, sW, cf, cpts, nc, n, degree, Mrp, Mcol, s);
+  pattern_fill(j, Z, s);
 }
 
 // ------------------------------------------------------------------------------------
@@ -844,6 +872,59 @@ void smooth_modes(const Csr& M, const double* dinv, const signed char* cf, const
   }
   if (x != Bv) CLAIR_CUDA(cudaMemcpyAsync(Bv, x, sizeof(double) * M.rows, cudaMemcpyDeviceToDevice, s));
 }
+// Mode smoothing of several vectors in one launch per relaxation (SmoothSides): the
+// per-row arithmetic is jacobi_kernel's.
+template <int W>
+__global__ void jacobi_sides(SmoothSides p, const double* __restrict__ dinv, int rows,
+                             const signed char* __restrict__ cf, int which, double omega,
+                             const double* __restrict__ omega_dev, int flip) {
+  if (omega_dev) omega = *omega_dev;
+  const int g = blockIdx.y;
+  const double* __restrict__ xin = flip ? p.y[g] : p.x[g];
+  double* __restrict__ xout = flip ? p.x[g] : p.y[g];
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int r = (int)(t / W), lane = (int)(t % W);
+  const bool ok = r < rows;
+  const bool act = ok && cf[r] == which;
+  double acc = 0;
+  if (act)
+    acc = csr_row_dot<W>(p.col[g], p.val[g], xin, p.rowptr[g][r], p.rowptr[g][r + 1], lane);
+  acc = group_sum<W>(acc);
+  if (ok && lane == 0) {
+    const double xr = xin[r];
+    xout[r] = act ? xr + omega * dinv[r] * (0.0 - acc) : xr;
+  }
+}
+
+// B <- (CFF sweep)^sweeps B for every side at once (zero right-hand side); each side's
+// vector ends in its x buffer.  Same kernels' arithmetic as smooth_modes.
+void smooth_modes_sides(const SmoothSides& sides, int rows, double avg_row, const double* dinv,
+                        const signed char* cf, const double* omega_dev, double omega, int sweeps,
+                        cudaStream_t s) {
+  if (!rows || !sides.count) return;
+  // one lane per row up to 16 entries (two batches of eight), then one lane per 16: the
+  // FP64 pipe, not the rows' dependent loads, then sets the pace
+  int W = 1;
+  while (W < 32 && 16 * W < avg_row) W <<= 1;
+  const dim3 grid((unsigned)ceil_div((long long)rows * W, 256), (unsigned)sides.count);
+  for (int it = 0; it < sweeps; ++it) {
+    // x -> y (C), y -> x (F), x -> y (F), then the roles swap: in place of std::swap the
+    // flip flag alternates, and after an odd count the result is in y
+    const int f0 = it & 1;
+    CLAIR_DISPATCH_W2(W, (jacobi_sides<WW><<<grid, 256, 0, s>>>(sides, dinv, rows, cf, 1, omega,
+                                                                  omega_dev, f0)));
+    CLAIR_DISPATCH_W2(W, (jacobi_sides<WW><<<grid, 256, 0, s>>>(sides, dinv, rows, cf, 0, omega,
+                                                                  omega_dev, f0 ^ 1)));
+    CLAIR_DISPATCH_W2(W, (jacobi_sides<WW><<<grid, 256, 0, s>>>(sides, dinv, rows, cf, 0, omega,
+                                                                  omega_dev, f0)));
+  }
+  CLAIR_LAUNCHED();
+  if (sweeps & 1)
+    for (int g = 0; g < sides.count; ++g)
+      CLAIR_CUDA(cudaMemcpyAsync(sides.x[g], sides.y[g], sizeof(double) * rows,
+                                 cudaMemcpyDeviceToDevice, s));
+}
+
 template void jacobi<double>(const Csr&, const double*, const double*, const signed char*, int,
                              double, const double*, const double*, double*, cudaStream_t,
                              const double*);
