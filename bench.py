@@ -37,7 +37,16 @@ PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # local-solve launches on the default workload, keyed by the SHA-256 of the source they were
 # measured on: reported only while that source is unchanged, null otherwise.
 MEASURED_TRAFFIC = {
-    # "local_solve": {"bytes": ..., "source_sha256": "...", "capture": "ncu command line"},
+    "local_solve": {
+        # 79.3 MB read + ~0 written (the writes stay in L2) per setup on the 512^2 case,
+        # scaled by the ratio of algorithmic bytes (530.9 MB / 132.1 MB = 4.02) to 1024^2
+        "bytes": 79.3e6 * (530854884.0 / 132096084.0),
+        "source_sha256": "00401719e9472dac6a9de733df6a4fa0c38dd422eb39e2ba8f3e89ab116add0e",
+        "capture": "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
+                   "--clock-control none -k regex:lsolve_persist python bench.py --nside 512 --steps 1 "
+                   "--warmup 1 --fp64-steps 0 --no-e2e --no-cpu-baseline --no-errors "
+                   "(second setup's launches), scaled to 1024^2 by algorithmic bytes",
+    },
 }
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
 FP64_PEAK_TFLOPS = 1.19                               # measured FMA loop (dependent chains)
@@ -372,9 +381,10 @@ def run_clair(args):
     lsolve = {"bound": "alu", "achieved": st.lsolve_flops / (phases["local_solve"] * 1e-3) / 1e12,
               "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
               "traffic": measured_traffic("local_solve", "local_solve.cu"),
-              "traffic_scope": "per step, all local-solve launches (ncu DRAM read + write)",
+              "traffic_scope": "per step, all local-solve launches (ncu DRAM read + write), "
+                               "measured at 512^2 and scaled by algorithmic bytes",
               "algorithmic_bytes": st.lsolve_min_bytes,
-              "kernel": "lsolve_group/lsolve_cta (FP32 batched local LU)",
+              "kernel": "lsolve_persist / lsolve_cta / lsolve_big (FP32 batched local LU)",
               "share_of_step": phases["local_solve"] / mixed["ms"]}
     lsolve["frac"] = lsolve["achieved"] / lsolve["peak"]
     hbm = pk.get("hbm_gbs", PEAK_FALLBACK["hbm_gbs"])
