@@ -232,6 +232,7 @@ struct PatternJob {
   int* buf = nullptr;
   long long cap = 0;
   unsigned long long* bump = nullptr;
+  unsigned char* done = nullptr;  // points counted by the short-row group pass
 };
 PatternJob pattern_count(const Csr& Wm, const unsigned char* sW, const signed char* cf,
                          const int* cpts, int nc, int n, int degree, const int* Mrp,

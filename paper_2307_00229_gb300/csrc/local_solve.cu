@@ -1379,6 +1379,23 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
 }
 
 
+// A stream of the highest priority per device for the large local systems (the ones
+// whose single-system latency sets a level's time), created once.
+static cudaStream_t large_stream() {
+  static std::mutex mu;
+  static cudaStream_t st[256] = {};
+  int dev = 0;
+  CLAIR_CUDA(cudaGetDevice(&dev));
+  CLAIR_REQUIRE(dev >= 0 && dev < 256, CLAIR_ERR_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!st[dev]) {
+    int lo = 0, hi = 0;
+    CLAIR_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CLAIR_CUDA(cudaStreamCreateWithPriority(&st[dev], cudaStreamNonBlocking, hi));
+  }
+  return st[dev];
+}
+
 // ---- execution configuration of the persistent launch, per device and precision -------
 struct LsolveConfig {
   int kind_b1 = LK_G16;   // systems with 8 < T <= 16: 16-lane groups or single warps
@@ -1557,11 +1574,40 @@ void local_solves_multi(const SideIn* sides, int nsides, const int* cpts, int pr
       st.config_kind_b3 = cfg.kind_b3;
       st.config_blocks_per_sm = cfg.blocks_per_sm;
       st.config_tuned = cfg.tuned;
+      // the systems with T > 64 (one CTA each, or a global tile) beside the persistent
+      // launch on a second stream: a coarse level's time is then the longer of the two
+      bool large = false;
+      for (int q = 0; q < nsides; ++q)
+        large = large || counts_h[q][4] + counts_h[q][5] + counts_h[q][6] > 0;
+      cudaStream_t ls = large ? large_stream() : s;
+      cudaEvent_t fork = nullptr, join = nullptr;
+      if (large) {
+        CLAIR_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        CLAIR_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        CLAIR_CUDA(cudaEventRecord(fork, s));
+        CLAIR_CUDA(cudaStreamWaitEvent(ls, fork, 0));
+      }
       persistent_launch<Real, VT>(sa, nsides, counts_h, cfg, ticket, nsing, s);
-      for (int q = 0; q < nsides; ++q) {
-        const SideIn& S = sides[q];
-        launch_solves<Real, VT>(*S.Ahat, vals[q], S.Zrp, S.Zcol, cpts, lists[q], counts_h[q], S.nc,
-                                S.Zval, nsing, s, false, /*first_bucket=*/4);
+      try {
+        for (int q = 0; q < nsides; ++q) {
+          const SideIn& S = sides[q];
+          launch_solves<Real, VT>(*S.Ahat, vals[q], S.Zrp, S.Zcol, cpts, lists[q], counts_h[q],
+                                  S.nc, S.Zval, nsing, ls, false, /*first_bucket=*/4);
+        }
+      } catch (...) {
+        if (large) {
+          cudaEventRecord(join, ls);
+          cudaStreamWaitEvent(s, join, 0);
+          cudaEventDestroy(fork);
+          cudaEventDestroy(join);
+        }
+        throw;
+      }
+      if (large) {
+        CLAIR_CUDA(cudaEventRecord(join, ls));
+        CLAIR_CUDA(cudaStreamWaitEvent(s, join, 0));
+        cudaEventDestroy(fork);
+        cudaEventDestroy(join);
       }
     };
     if (precision == CLAIR_MIXED) {

@@ -573,13 +573,14 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
                const int* __restrict__ cpts, int nc, int degree, const int* __restrict__ Mrp,
                const int* __restrict__ Mcol, int* __restrict__ count,
                const int* __restrict__ Zrp, int* __restrict__ Zcol, int* __restrict__ err,
-               PatternStash st) {
+               PatternStash st, const unsigned char* __restrict__ done) {
   __shared__ int keys[PT_WARPS][PT_CAP];
   __shared__ int hop_pre[PT_WARPS][33];
   __shared__ int hop_start[PT_WARPS][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * PT_WARPS + w;
   if (r >= nc) return;  // warp-uniform
+  if (COUNT && done && done[r]) return;  // counted (and stashed) by the group pass
   if (!COUNT && st.buf) {
     const int p0 = st.start[r];
     if (p0 >= 0) {  // built by the first pass
@@ -690,6 +691,151 @@ pattern_kernel(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
 
 // Builds the pattern CSR Z (nc rows) for Algorithm 1 on Ahat, walking Wm = Ahat^T with
 // its strength mask sW.
+// Counting pass for short rows: PS_G lanes per coarse point, 32 / PS_G points per warp,
+// each with a hash set of PS_CAP slots; the steps are pattern_kernel's, every warp
+// primitive restricted to the point's lane group (the groups of a warp run independent
+// trip counts).  A point whose bound does not fit is left to pattern_kernel (done = 0).
+constexpr int PS_G = 8;
+constexpr int PS_RPW = 32 / PS_G;
+constexpr int PS_CAP = 256;
+constexpr int PS_WARPS = 4;
+
+template <bool AGG>
+__global__ void __launch_bounds__(32 * PS_WARPS)
+pattern_small(const int* __restrict__ Wrp, const int* __restrict__ Wcol,
+              const unsigned char* __restrict__ sW, const signed char* __restrict__ cf,
+              const int* __restrict__ cpts, int nc, int degree, const int* __restrict__ Mrp,
+              const int* __restrict__ Mcol, int* __restrict__ count, int* __restrict__ err,
+              PatternStash st, unsigned char* __restrict__ done) {
+  __shared__ int keys[PS_WARPS][PS_RPW][PS_CAP];
+  __shared__ int hop_pre[PS_WARPS][PS_RPW][PS_G + 1];
+  __shared__ int hop_start[PS_WARPS][PS_RPW][PS_G];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / PS_G, sub = lane % PS_G;
+  const unsigned gmask = ((1u << PS_G) - 1u) << (g * PS_G);
+  const int r = (blockIdx.x * PS_WARPS + w) * PS_RPW + g;
+  if (r >= nc) return;  // group-uniform; the group primitives below name only live lanes
+  int* K = keys[w][g];
+  int* P = hop_pre[w][g];
+  int* S = hop_start[w][g];
+  const int i = cpts[r];
+  int bound = 0;
+  if (!AGG) {
+    for (int e = Wrp[i] + sub; e < Wrp[i + 1]; e += PS_G) {
+      bound += 1;
+      if (degree >= 2) {
+        const int k = Wcol[e];
+        if (sW[e] && !cf[k]) bound += Wrp[k + 1] - Wrp[k];
+      }
+    }
+  } else {
+    for (int m = Mrp[r] + sub; m < Mrp[r + 1]; m += PS_G) {
+      bound += 1;
+      if (degree >= 2) bound += Wrp[Mcol[m] + 1] - Wrp[Mcol[m]];
+    }
+  }
+#pragma unroll
+  for (int o = PS_G / 2; o > 0; o >>= 1) bound += __shfl_xor_sync(gmask, bound, o, PS_G);
+  if (2 * (bound + 1) > PS_CAP) {  // group-uniform: the warp-per-point pass takes it
+    if (sub == 0) done[r] = 0;
+    return;
+  }
+  const int cap = pt_cap_for(bound + 1);  // <= PS_CAP
+  for (int t = sub; t < cap; t += PS_G) K[t] = -1;
+  __syncwarp(gmask);
+  int fresh = 0;
+  if (sub == 0) pt_insert(K, cap, i, &fresh, err);
+  // candidates of a batch of up to PS_G first-hop rows, flattened over the group's lanes
+  auto second_hop = [&](int start, int len) {
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < PS_G; o <<= 1) {
+      const int v = __shfl_up_sync(gmask, incl, o, PS_G);
+      if (sub >= o) incl += v;
+    }
+    P[sub + 1] = incl;
+    if (sub == 0) P[0] = 0;
+    S[sub] = start;
+    __syncwarp(gmask);
+    const int tot = P[PS_G];
+    for (int f = sub; f < tot; f += PS_G) {
+      int lo = 0, hi = PS_G;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (P[mid] <= f) lo = mid; else hi = mid;
+      }
+      const int e = S[lo] + (f - P[lo]);
+      if (sW[e] && !cf[Wcol[e]]) pt_insert(K, cap, Wcol[e], &fresh, err);
+    }
+    __syncwarp(gmask);
+  };
+  if (!AGG) {
+    for (int e = Wrp[i] + sub; e < Wrp[i + 1]; e += PS_G)
+      if (sW[e] && !cf[Wcol[e]]) pt_insert(K, cap, Wcol[e], &fresh, err);
+    if (degree >= 2) {
+      const int e_end = Wrp[i + 1];
+      for (int c0 = Wrp[i]; c0 < e_end; c0 += PS_G) {
+        const int e1 = c0 + sub;
+        int start = 0, len = 0;
+        if (e1 < e_end) {
+          const int k = Wcol[e1];
+          if (sW[e1] && !cf[k]) {
+            start = Wrp[k];
+            len = Wrp[k + 1] - start;
+          }
+        }
+        second_hop(start, len);
+      }
+    }
+  } else {
+    for (int m = Mrp[r] + sub; m < Mrp[r + 1]; m += PS_G)
+      if (!cf[Mcol[m]]) pt_insert(K, cap, Mcol[m], &fresh, err);
+    if (degree >= 2) {
+      const int m_end = Mrp[r + 1];
+      for (int c0 = Mrp[r]; c0 < m_end; c0 += PS_G) {
+        const int m = c0 + sub;
+        int start = 0, len = 0;
+        if (m < m_end) {
+          const int k = Mcol[m];
+          start = Wrp[k];
+          len = Wrp[k + 1] - start;
+        }
+        second_hop(start, len);
+      }
+    }
+  }
+  __syncwarp(gmask);
+#pragma unroll
+  for (int o = PS_G / 2; o > 0; o >>= 1) fresh += __shfl_xor_sync(gmask, fresh, o, PS_G);
+  if (sub == 0) {
+    count[r] = fresh;
+    done[r] = 1;
+  }
+  if (!st.buf) return;
+  unsigned long long p0 = 0;
+  if (sub == 0) p0 = atomicAdd(st.bump, (unsigned long long)fresh);
+  p0 = __shfl_sync(gmask, p0, 0, PS_G);
+  const bool fits = p0 + (unsigned long long)fresh <= (unsigned long long)st.cap;
+  if (sub == 0) st.start[r] = fits ? (int)p0 : -1;
+  if (!fits) return;
+  int* out = st.buf + p0;
+  int total = 0;
+  for (int c = 0; c < cap; c += PS_G) {
+    const int v = K[c + sub];
+    const unsigned occ = (__ballot_sync(gmask, v >= 0) >> (g * PS_G)) & ((1u << PS_G) - 1u);
+    __syncwarp(gmask);
+    if (v >= 0) K[total + __popc(occ & ((1u << sub) - 1u))] = v;
+    total += __popc(occ);
+    __syncwarp(gmask);
+  }
+  for (int t = sub; t < total; t += PS_G) {
+    const int v = K[t];
+    int rank = 0;
+    for (int u = 0; u < total; ++u) rank += K[u] < v;
+    out[rank] = v;
+  }
+}
+
 // First stage of the pattern: the counting pass (with the stash), launched only.
 PatternJob pattern_count(const Csr& Wm, const unsigned char* sW, const signed char* cf,
                          const int* cpts, int nc, int n, int degree, const int* Mrp,
@@ -719,14 +865,30 @@ PatternJob pattern_count(const Csr& Wm, const unsigned char* sW, const signed ch
     j.bump = dalloc<unsigned long long>(1, s);
     CLAIR_CUDA(cudaMemsetAsync(j.bump, 0, sizeof(unsigned long long), s));
     const PatternStash st{j.start, j.buf, j.cap, j.bump};
+    // short rows (a fine stencil level): the group pass counts every point whose bound
+    // fits its table, the warp-per-point pass the rest; with longer rows eight lanes walk
+    // too many candidates per point and the warp per point is faster
+    const bool short_rows = Wm.rows && (double)Wm.nnz / Wm.rows <= 8.0;
+    if (short_rows) {
+      j.done = dalloc<unsigned char>(nc, s);
+      const int gs = ceil_div(nc, PS_WARPS * PS_RPW);
+      if (agg)
+        pattern_small<true><<<gs, 32 * PS_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc, degree,
+                                                          Mrp, Mcol, j.count, j.err, st, j.done);
+      else
+        pattern_small<false><<<gs, 32 * PS_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
+                                                           degree, nullptr, nullptr, j.count,
+                                                           j.err, st, j.done);
+      ::clair::count_launch();
+    }
     if (agg)
       pattern_kernel<true, true><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
                                                              degree, Mrp, Mcol, j.count, nullptr,
-                                                             nullptr, j.err, st);
+                                                             nullptr, j.err, st, j.done);
     else
       pattern_kernel<true, false><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, sW, cf, cpts, nc,
                                                               degree, nullptr, nullptr, j.count,
-                                                              nullptr, nullptr, j.err, st);
+                                                              nullptr, nullptr, j.err, st, j.done);
     ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
@@ -746,6 +908,7 @@ void pattern_fill(PatternJob& j, Csr& Z, cudaStream_t s) {
   int h = 0;
   Z.nnz = (int)exclusive_scan(j.count, Z.rowptr, nc, s, true, j.err, &h);
   auto release = [&]() {
+    dfree(j.done, s);
     dfree(j.count, s);
     dfree(j.err, s);
     dfree(j.start, s);
@@ -764,12 +927,12 @@ void pattern_fill(PatternJob& j, Csr& Z, cudaStream_t s) {
     if (agg)
       pattern_kernel<false, true><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, j.sW, j.cf, j.cpts,
                                                               nc, j.degree, j.Mrp, j.Mcol, nullptr,
-                                                              Z.rowptr, Z.col, j.err, st);
+                                                              Z.rowptr, Z.col, j.err, st, nullptr);
     else
       pattern_kernel<false, false><<<g, 32 * PT_WARPS, 0, s>>>(Wm.rowptr, Wm.col, j.sW, j.cf,
                                                                j.cpts, nc, j.degree, nullptr,
                                                                nullptr, nullptr, Z.rowptr, Z.col,
-                                                               j.err, st);
+                                                               j.err, st, nullptr);
     ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
