@@ -1659,7 +1659,9 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   // long products (mean products per row ~ mean A row x mean B row): one CTA per row
   const double mean_products =
       (rows ? (double)A.nnz / rows : 0.0) * (B.rows ? (double)B.nnz / B.rows : 0.0);
-  if (rows && mean_products >= 1024.0) {
+  // (thresholds measured on the 1024^2 hierarchy: the flat tiers win from 1024 to 2048
+  // products per row on levels of many rows, the CTA path on short matrices)
+  if (rows && (mean_products >= 2048.0 || (mean_products >= 1024.0 && rows < 8192))) {
     spgemm_cta_path(A, B, C, s);
     return;
   }
