@@ -233,11 +233,19 @@ struct PatternJob {
   long long cap = 0;
   unsigned long long* bump = nullptr;
   unsigned char* done = nullptr;  // points counted by the short-row group pass
+  int* ovf = nullptr;             // scan overflow flag (device)
 };
 PatternJob pattern_count(const Csr& Wm, const unsigned char* sW, const signed char* cf,
                          const int* cpts, int nc, int n, int degree, const int* Mrp,
                          const int* Mcol, cudaStream_t s);
 void pattern_fill(PatternJob& j, Csr& Z, cudaStream_t s);
+// pattern_fill in three steps, so that several patterns share one host read: the row
+// pointers (device only), the entry counts and overflow flags of all jobs (one
+// synchronisation), then the rows
+void pattern_scan(PatternJob& j, Csr& Z, cudaStream_t s);
+void pattern_read(PatternJob* const* jobs, Csr* const* Z, int k, cudaStream_t s);
+void pattern_build(PatternJob& j, Csr& Z, cudaStream_t s);
+void exclusive_scan_into(const int* in, int* out, int n, int* ovf, cudaStream_t s);
 
 // Vectors relaxed together by the mode smoothing: side g = blockIdx.y relaxes x[g] with its
 // own operator (A for the P side, A^T for the R side, one entry per mode) and ping-pongs

@@ -630,8 +630,21 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
     CLAIR_CUDA(cudaEventRecord(ss.join, ss.s2));
     {
       ClockScope clk(PH_PATTERN, s);
-      if (!sym) pattern_fill(jobR, L.R, s);
-      pattern_fill(jobP, Pt, s);
+      // both patterns' entry counts in one host read
+      PatternJob* jobs[2];
+      Csr* zs[2];
+      int nj = 0;
+      if (!sym) {
+        pattern_scan(jobR, L.R, s);
+        jobs[nj] = &jobR;
+        zs[nj++] = &L.R;
+      }
+      pattern_scan(jobP, Pt, s);
+      jobs[nj] = &jobP;
+      zs[nj++] = &Pt;
+      pattern_read(jobs, zs, nj, s);
+      if (!sym) pattern_build(jobR, L.R, s);
+      pattern_build(jobP, Pt, s);
       dfree(Mrp, s);
       dfree(Mcol, s);
       dfree(agg, s);

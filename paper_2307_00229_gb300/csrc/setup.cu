@@ -216,12 +216,13 @@ void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsign
   const int gw = (int)ceil_div((long long)n * W, 256);
   CLAIR_DISPATCH_W2(W, (pmis_init<WW><<<gw, 256, 0, s>>>(At.rowptr, sAt, n, lbase, key, state, mark)));
   CLAIR_LAUNCHED();
-  // Rounds go in groups of PMIS_ROUNDS between host checks: a round after the last
-  // undecided point is decided changes nothing, and the check reads the last round's count.
-  constexpr int PMIS_ROUNDS = 3;
+  // Rounds go in groups between host checks (six, then three: the stencil hierarchies
+  // here take six to nine): a round after the last undecided point is decided changes
+  // nothing, and the check reads the last round's count.
   for (int round = 0;;) {
     CLAIR_REQUIRE(round < 10000, CLAIR_ERR_CAPACITY, "C/F splitting did not terminate");
-    for (int q = 0; q < PMIS_ROUNDS; ++q, ++round) {
+    const int group = round == 0 ? 6 : 3;
+    for (int q = 0; q < group; ++q, ++round) {
       CLAIR_CUDA(cudaMemsetAsync(remaining, 0, sizeof(int), s));
       CLAIR_DISPATCH_W2(W, (pmis_select<WW><<<gw, 256, 0, s>>>(A.rowptr, A.col, sA, At.rowptr, At.col,
                                                              sAt, n, key, state, mark, round)));
@@ -895,32 +896,61 @@ PatternJob pattern_count(const Csr& Wm, const unsigned char* sW, const signed ch
   return j;
 }
 
-// Second stage: the row lengths' scan (one host read: the entry count and the overflow
-// flag of the counting pass), then the rows: stashed rows copied, the others built again.
-void pattern_fill(PatternJob& j, Csr& Z, cudaStream_t s) {
+static void pattern_release(PatternJob& j, cudaStream_t s) {
+  dfree(j.done, s);
+  dfree(j.count, s);
+  dfree(j.err, s);
+  dfree(j.start, s);
+  dfree(j.buf, s);
+  dfree(j.bump, s);
+  dfree(j.ovf, s);
+}
+
+// Row pointers of the pattern from the counting pass (device only).
+void pattern_scan(PatternJob& j, Csr& Z, cudaStream_t s) {
   Z.rows = j.nc;
   Z.cols = j.n;
+  Z.rowptr = dalloc<int>(j.nc + 1, s);
+  j.ovf = dalloc<int>(1, s);
+  exclusive_scan_into(j.count, Z.rowptr, j.nc, j.ovf, s);
+}
+
+// One host read for k scanned patterns: entry counts, scan overflow, table overflow of the
+// counting pass (a row that overflows its table does so there: the filling pass inserts the
+// same keys).  On an error every job's buffers are released.
+void pattern_read(PatternJob* const* jobs, Csr* const* Z, int k, cudaStream_t s) {
+  int h[3 * 2] = {0, 0, 0, 0, 0, 0};
+  CLAIR_REQUIRE(k >= 1 && k <= 2, CLAIR_ERR_ARG, "pattern_read: %d jobs", k);
+  for (int q = 0; q < k; ++q) {
+    CLAIR_CUDA(cudaMemcpyAsync(&h[3 * q], Z[q]->rowptr + jobs[q]->nc, sizeof(int),
+                               cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaMemcpyAsync(&h[3 * q + 1], jobs[q]->ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CLAIR_CUDA(cudaMemcpyAsync(&h[3 * q + 2], jobs[q]->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  bool bad_ovf = false, bad_cap = false;
+  for (int q = 0; q < k; ++q) {
+    Z[q]->nnz = h[3 * q];
+    bad_ovf = bad_ovf || h[3 * q + 1];
+    bad_cap = bad_cap || h[3 * q + 2];
+  }
+  if (bad_ovf || bad_cap) {
+    for (int q = 0; q < k; ++q) {
+      pattern_release(*jobs[q], s);
+      dfree(Z[q]->rowptr, s);
+      Z[q]->rowptr = nullptr;
+    }
+    CLAIR_REQUIRE(!bad_ovf, CLAIR_ERR_CAPACITY, "scan total exceeds int32");
+    CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "pattern row exceeds %d entries", PT_CAP);
+  }
+}
+
+// The rows: stashed rows copied, the others built again; releases the job's buffers.
+void pattern_build(PatternJob& j, Csr& Z, cudaStream_t s) {
   const int nc = j.nc;
   const int g = ceil_div(nc, PT_WARPS);
   const bool agg = j.Mrp != nullptr;
   const PatternStash st{j.start, j.buf, j.cap, j.bump};
-  Z.rowptr = dalloc<int>(nc + 1, s);
-  int h = 0;
-  Z.nnz = (int)exclusive_scan(j.count, Z.rowptr, nc, s, true, j.err, &h);
-  auto release = [&]() {
-    dfree(j.done, s);
-    dfree(j.count, s);
-    dfree(j.err, s);
-    dfree(j.start, s);
-    dfree(j.buf, s);
-    dfree(j.bump, s);
-  };
-  if (h) {
-    release();
-    dfree(Z.rowptr, s);
-    Z.rowptr = nullptr;
-    CLAIR_REQUIRE(false, CLAIR_ERR_CAPACITY, "pattern row exceeds %d entries", PT_CAP);
-  }
   Z.col = dalloc<int>(Z.nnz, s);
   if (nc) {
     const Csr& Wm = j.Wm;
@@ -936,7 +966,16 @@ void pattern_fill(PatternJob& j, Csr& Z, cudaStream_t s) {
     ::clair::count_launch();
   }
   CLAIR_LAUNCHED();
-  release();
+  pattern_release(j, s);
+}
+
+// Second stage of the pattern: scan, the host read, the rows.
+void pattern_fill(PatternJob& j, Csr& Z, cudaStream_t s) {
+  pattern_scan(j, Z, s);
+  PatternJob* jp = &j;
+  Csr* zp = &Z;
+  pattern_read(&jp, &zp, 1, s);
+  pattern_build(j, Z, s);
 }
 
 // Builds the pattern CSR Z (nc rows) for Algorithm 1 on Ahat, walking Wm = Ahat^T with

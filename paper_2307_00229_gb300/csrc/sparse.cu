@@ -291,6 +291,24 @@ __global__ void scan_single(const int* __restrict__ in, int n, int* __restrict__
   if (threadIdx.x == 0) *overflow = s_ovf;
 }
 
+// out = exclusive scan of in (out[n] = total), *ovf = 1 if the total exceeds int32; no
+// host synchronisation (the caller reads out[n] and *ovf when it synchronises anyway).
+void exclusive_scan_into(const int* in, int* out, int n, int* ovf, cudaStream_t s) {
+  const int nb = std::max(1, ceil_div(n, SCAN_TILE));
+  CLAIR_REQUIRE(nb <= SCAN_TILE, CLAIR_ERR_CAPACITY, "scan of %d items exceeds capacity", n);
+  CLAIR_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+  if (nb == 1) {
+    scan_single<<<1, SCAN_THREADS, 0, s>>>(in, n, out, ovf); ::clair::count_launch();
+  } else {
+    long long* sums = dalloc<long long>(nb + 1, s);
+    scan_block_sums<<<nb, SCAN_THREADS, 0, s>>>(in, n, sums); ::clair::count_launch();
+    scan_sums<<<1, SCAN_THREADS, 0, s>>>(sums, nb); ::clair::count_launch();
+    scan_apply<<<nb, SCAN_THREADS, 0, s>>>(in, n, sums, out, ovf); ::clair::count_launch();
+    dfree(sums, s);
+  }
+  CLAIR_LAUNCHED();
+}
+
 long long exclusive_scan(const int* in, int* out, int n, cudaStream_t s, bool want_total,
                          const int* extra_dev, int* extra_host) {
   const int nb = std::max(1, ceil_div(n, SCAN_TILE));
