@@ -38,12 +38,13 @@ PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # measured on: reported only while that source is unchanged, null otherwise.
 MEASURED_TRAFFIC = {
     "local_solve": {
-        # 79.3 MB read + ~0 written (the writes stay in L2) per setup on the 512^2 case,
-        # scaled by the ratio of algorithmic bytes (530.9 MB / 132.1 MB = 4.02) to 1024^2
-        "bytes": 79.3e6 * (530854884.0 / 132096084.0),
-        "source_sha256": "00401719e9472dac6a9de733df6a4fa0c38dd422eb39e2ba8f3e89ab116add0e",
+        # 80.8 MB read + ~0 written (the writes stay in L2) per setup on the 512^2 case by
+        # every local-solve launch (lsolve_persist and lsolve_cta), scaled by the ratio of
+        # algorithmic bytes (530.9 MB / 132.1 MB = 4.02) to 1024^2
+        "bytes": 80.8e6 * (530854884.0 / 132096084.0),
+        "source_sha256": "8a991541926500b79c3fadb4faf5cd9a8637b6def42dc5515a4c8a7390c13eeb",
         "capture": "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
-                   "--clock-control none -k regex:lsolve_persist python bench.py --nside 512 --steps 1 "
+                   "--clock-control none -k regex:lsolve_ python bench.py --nside 512 --steps 1 "
                    "--warmup 1 --fp64-steps 0 --no-e2e --no-cpu-baseline --no-errors "
                    "(second setup's launches), scaled to 1024^2 by algorithmic bytes",
     },
