@@ -29,7 +29,8 @@ namespace clair {
 
 // Solvable buckets: T in [0,8], (8,16], (16,32], (32,64], (64,128], (128,tmed] (one CTA
 // per system, the tile in shared memory: tmed = LS_TMED32 in FP32, LS_TMED64 in FP64),
-// (tmed,4096] (global tile); bucket 7 counts systems larger than LS_TBIG (refused).
+// (tmed,4096] (a global tile, eliminated in panels where a panel fits shared memory, else
+// step by step); bucket 7 counts systems larger than LS_TBIG (refused).
 constexpr int LS_BUCKETS = 7;
 constexpr int LS_TBIG = 4096;
 constexpr int LS_TMED32 = 224;  // 224 x 228 floats: 204 KB of shared memory
@@ -1002,6 +1003,293 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
 }
 
 // ------------------------------------------------------------------------------------
+// Large systems, blocked (128 < T up to a few thousand): one block of 256 threads per
+// system at a time, the matrix in a global scratch tile stored row-major (row p at
+// M + p * pitch), eliminated in panels of NB columns.  Each panel's columns are loaded
+// into shared memory and factored there step by step (the same implicit partial pivoting,
+// one barrier per step); the pivot rows' entries right of the panel (the rows of U) and
+// then the remaining rows are updated once per panel, by a thread per column holding the
+// panel's NB entries of U in registers.  Every entry receives the same updates, in the
+// same order and with the same operands, as in the unblocked elimination; the trailing
+// matrix is read and written once per panel instead of once per step.  Back substitution
+// runs in blocks of 32 steps: the dot products with the solved tail by warps (coalesced
+// row reads), then the 32 x 32 triangle by one warp from shared memory.
+// Blocks take systems from a device ticket, the largest size class first.
+// ------------------------------------------------------------------------------------
+constexpr int LK_THREADS = 256;
+
+template <class Real>
+__host__ __device__ constexpr int blk_ps(int nb) {
+  return nb + 16 / (int)sizeof(Real);  // panel row stride: 16-byte aligned rows
+}
+
+template <class Real>
+static size_t blk_smem(int pitch, int nb) {
+  return (size_t)pitch * blk_ps<Real>(nb) * sizeof(Real) + 2 * (size_t)pitch * sizeof(Real) +
+         32 * 33 * sizeof(Real) + 3 * (size_t)pitch * sizeof(int);
+}
+
+template <class Real, class VT, int NB>
+__global__ void __launch_bounds__(LK_THREADS, sizeof(Real) == 4 ? 2 : 1)
+lsolve_blk(const int* __restrict__ Arp, const int* __restrict__ Acol,
+           const VT* __restrict__ Aval, const int* __restrict__ Zrp,
+           const int* __restrict__ Zcol, const int* __restrict__ cpts,
+           const int* __restrict__ cls, const int* __restrict__ ccount, int cls_stride, int ncls,
+           int* __restrict__ ticket, double* __restrict__ Zval,
+           unsigned long long* __restrict__ nsingular, Real* __restrict__ scratch, int pitch) {
+  using V = typename Vec16<Real>::type;
+  constexpr int VN = 16 / (int)sizeof(Real);
+  constexpr int PS = NB + VN;
+  extern __shared__ __align__(16) unsigned char kb_smem[];
+  Real* Pn = reinterpret_cast<Real*>(kb_smem);  // panel: row p at Pn + p * PS
+  Real* rhs = Pn + (size_t)pitch * PS;
+  Real* xs = rhs + pitch;
+  Real* tri = xs + pitch;  // 32 x 33: a block of back substitution
+  int* zl = reinterpret_cast<int*>(tri + 32 * 33);
+  int* steprow = zl + pitch;
+  int* ulist = steprow + pitch;
+  __shared__ Real red_v[2][LK_THREADS / 32];
+  __shared__ int red_w[2][LK_THREADS / 32];
+  __shared__ int s_task, s_d, s_sing, s_nu;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  Real* M = scratch + (size_t)blockIdx.x * pitch * pitch;
+  for (;;) {
+    if (t == 0) s_task = atomicAdd(ticket, 1);
+    __syncthreads();
+    int task = s_task, r = -1;
+    for (int c = ncls - 1; c >= 0; --c) {  // largest class first
+      const int n = ccount[c];
+      if (task < n) {
+        r = cls[(size_t)c * cls_stride + task];
+        break;
+      }
+      task -= n;
+    }
+    if (r < 0) break;  // the same for every thread of the block
+    const int i = cpts[r];
+    const int base = Zrp[r];
+    const int len = Zrp[r + 1] - base;
+    const int T = len - 1;  // T <= pitch (the host sized the tiles for the largest class)
+    if (t == 0) {
+      s_d = T;
+      s_sing = 0;
+    }
+    __syncthreads();
+    for (int q = t; q < len; q += LK_THREADS)
+      if (Zcol[base + q] == i) s_d = q;
+    __syncthreads();
+    const int d = s_d;
+    for (int p = t; p < T; p += LK_THREADS) {
+      zl[p] = Zcol[base + p + (p >= d ? 1 : 0)];
+      rhs[p] = Real(0);
+    }
+    for (int p = wid; p < T; p += LK_THREADS / 32)
+      for (int q = lane; q < T; q += 32) M[(size_t)p * pitch + q] = Real(0);
+    __syncthreads();
+    // row p's entries in batches of 4: loads and column searches before the stores
+    for (int p = t; p < T; p += LK_THREADS) {
+      const int l = zl[p];
+      const int e_end = Arp[l + 1];
+      for (int e0 = Arp[l]; e0 < e_end; e0 += 4) {
+        int col_of[4], q_of[4];
+        Real val_of[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool in = e0 + u < e_end;
+          col_of[u] = in ? Acol[e0 + u] : -1;
+          val_of[u] = in ? Real(Aval[e0 + u]) : Real(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          q_of[u] = col_of[u] < 0 ? -1 : (col_of[u] == i ? T : find_sorted(zl, T, col_of[u]));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (q_of[u] == T) rhs[p] = -val_of[u];
+          else if (q_of[u] >= 0) M[(size_t)p * pitch + q_of[u]] = val_of[u];
+        }
+      }
+    }
+    // thread t owns rows t + 256 rr; bit rr of `done`: that row is eliminated (or absent)
+    const int nr = (T + LK_THREADS - 1) / LK_THREADS;
+    unsigned done = 0;
+    for (int rr = 0; rr < nr; ++rr)
+      if (t + LK_THREADS * rr >= T) done |= 1u << rr;
+    __syncthreads();
+    for (int k0 = 0; k0 < T; k0 += NB) {
+      const int nb = min(NB, T - k0);
+      for (int e = t; e < T * NB; e += LK_THREADS) {
+        const int p = e / NB, kk = e % NB;
+        if (kk < nb) Pn[p * PS + kk] = M[(size_t)p * pitch + k0 + kk];
+      }
+      if (t == 0) s_nu = 0;
+      __syncthreads();
+      // the panel's steps: one barrier each (each thread updates only its own rows; the
+      // candidate arrays alternate by step parity, as in the shared-memory CTA solve)
+      for (int kk = 0; kk < nb; ++kk) {
+        const int k = k0 + kk, par = k & 1;
+        Real v = Real(-1);
+        int who = 0x7fffffff;
+        for (int rr = 0; rr < nr; ++rr)
+          if (!((done >> rr) & 1u)) {
+            const int p = t + LK_THREADS * rr;
+            const Real a = Pn[p * PS + kk];
+            Real m = a < 0 ? -a : a;
+            if (!(m >= Real(0))) m = Real(-0.5);  // NaN: still a row to take, after any number
+            if (m > v) {  // rows visited in increasing order: ties keep the lowest
+              v = m;
+              who = p;
+            }
+          }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const Real v2 = __shfl_xor_sync(0xffffffffu, v, o);
+          const int w2 = __shfl_xor_sync(0xffffffffu, who, o);
+          if (v2 > v || (v2 == v && w2 < who)) {
+            v = v2;
+            who = w2;
+          }
+        }
+        if (lane == 0) {
+          red_v[par][wid] = v;
+          red_w[par][wid] = who;
+        }
+        __syncthreads();
+        Real bv = red_v[par][0];
+        int piv = red_w[par][0];
+#pragma unroll
+        for (int w = 1; w < LK_THREADS / 32; ++w)
+          if (red_v[par][w] > bv || (red_v[par][w] == bv && red_w[par][w] < piv)) {
+            bv = red_v[par][w];
+            piv = red_w[par][w];
+          }
+        // piv is a row not yet eliminated: T - k of them are left at step k < T
+        const Real* prow = Pn + piv * PS;
+        const Real pk = prow[kk];
+        if (t == 0) {
+          steprow[k] = piv;
+          if (!((pk < 0 ? -pk : pk) > Real(0))) s_sing = 1;
+        }
+        const Real rpiv = rhs[piv];
+        for (int rr = 0; rr < nr; ++rr) {
+          if ((done >> rr) & 1u) continue;
+          const int p = t + LK_THREADS * rr;
+          if (p == piv) {
+            done |= 1u << rr;
+            continue;
+          }
+          if (pk == Real(0)) continue;
+          Real* row = Pn + p * PS;
+          const Real l = row[kk] / pk;
+          row[kk] = l;  // the multiplier, read by the updates right of the panel
+          for (int k2 = kk + 1; k2 < nb; ++k2) row[k2] = row[k2] - l * prow[k2];
+          rhs[p] -= l * rpiv;
+        }
+      }
+      __syncthreads();  // the panel's last updates and its pivot rows
+      for (int e = t; e < T * NB; e += LK_THREADS) {
+        const int p = e / NB, kk = e % NB;
+        if (kk < nb) M[(size_t)p * pitch + k0 + kk] = Pn[p * PS + kk];
+      }
+      for (int rr = 0; rr < nr; ++rr)
+        if (!((done >> rr) & 1u)) ulist[atomicAdd(&s_nu, 1)] = t + LK_THREADS * rr;
+      __syncthreads();
+      const int jt0 = k0 + NB;  // columns right of a full panel (a partial one ends at T)
+      if (jt0 < T) {
+        const int nu = s_nu;
+        const int width = T - jt0;
+        const int cw = width > 128 ? 256 : width > 64 ? 128 : width > 32 ? 64 : 32;
+        const int G = LK_THREADS / cw, g = t / cw, cl = t % cw;
+        for (int jc = jt0; jc < T; jc += cw) {
+          const int j = jc + cl;
+          const bool act = j < T;
+          Real u[NB];
+#pragma unroll
+          for (int kk = 0; kk < NB; ++kk)
+            u[kk] = act ? M[(size_t)steprow[k0 + kk] * pitch + j] : Real(0);
+          // the pivot rows' updates by the earlier pivots of the panel, in step order
+#pragma unroll
+          for (int kk = 1; kk < NB; ++kk) {
+            const Real* lrow = Pn + steprow[k0 + kk] * PS;
+#pragma unroll
+            for (int k2 = 0; k2 < kk; ++k2) u[kk] = u[kk] - lrow[k2] * u[k2];
+          }
+          if (act && g == 0) {
+#pragma unroll
+            for (int kk = 0; kk < NB; ++kk) M[(size_t)steprow[k0 + kk] * pitch + j] = u[kk];
+          }
+          for (int i0 = g; i0 < nu; i0 += 4 * G) {
+            int pr[4];
+            Real c[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              const int ii = i0 + m * G;
+              pr[m] = ii < nu ? ulist[ii] : -1;
+              c[m] = (act && pr[m] >= 0) ? M[(size_t)pr[m] * pitch + j] : Real(0);
+            }
+#pragma unroll
+            for (int kk = 0; kk < NB; kk += VN) {
+#pragma unroll
+              for (int m = 0; m < 4; ++m) {
+                const V l4 = *reinterpret_cast<const V*>(Pn + (pr[m] < 0 ? 0 : pr[m]) * PS + kk);
+                if constexpr (VN == 4) {
+                  c[m] = c[m] - l4.x * u[kk];
+                  c[m] = c[m] - l4.y * u[kk + 1];
+                  c[m] = c[m] - l4.z * u[kk + 2];
+                  c[m] = c[m] - l4.w * u[kk + 3];
+                } else {
+                  c[m] = c[m] - l4.x * u[kk];
+                  c[m] = c[m] - l4.y * u[kk + 1];
+                }
+              }
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+              if (act && pr[m] >= 0) M[(size_t)pr[m] * pitch + j] = c[m];
+          }
+        }
+      }
+      __syncthreads();  // the tile's updates before the next panel is loaded
+    }
+    // back substitution, 32 steps at a time from the last
+    for (int ke = T; ke > 0; ke -= 32) {
+      const int kb = ke > 32 ? ke - 32 : 0, nbk = ke - kb;
+      for (int kq = wid; kq < nbk; kq += LK_THREADS / 32) {
+        const Real* urow = M + (size_t)steprow[kb + kq] * pitch;
+        Real acc = Real(0);
+        for (int q = ke + lane; q < T; q += 32) acc += urow[q] * xs[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) xs[kb + kq] = rhs[steprow[kb + kq]] - acc;
+        if (lane < nbk) tri[kq * 33 + lane] = urow[kb + lane];
+      }
+      __syncthreads();
+      if (wid == 0) {
+        Real rr = lane < nbk ? xs[kb + lane] : Real(0);
+        for (int c = nbk - 1; c >= 0; --c) {
+          Real xc = Real(0);
+          if (lane == c) {
+            const Real dk = tri[c * 33 + c];
+            xc = dk != Real(0) ? rr / dk : Real(0);
+            xs[kb + c] = xc;
+          }
+          xc = __shfl_sync(0xffffffffu, xc, c);
+          if (lane < c) rr -= tri[lane * 33 + c] * xc;
+        }
+      }
+      __syncthreads();
+    }
+    const bool sing = s_sing != 0;
+    for (int p = t; p < T; p += LK_THREADS)
+      Zval[base + p + (p >= d ? 1 : 0)] = sing ? 0.0 : (double)xs[p];
+    if (t == 0) {
+      Zval[base + d] = 1.0;
+      if (sing) atomicAdd(nsingular, 1ull);
+    }
+    __syncthreads();  // the shared arrays are reused by the block's next system
+  }
+}
+
+// ------------------------------------------------------------------------------------
 // Bucketing and the projection.
 // ------------------------------------------------------------------------------------
 // work[0..2] = sum T^3, T^2, T; work[3] = A entries gathered (row lengths of the pattern's
@@ -1276,6 +1564,96 @@ __global__ void class_big(const int* __restrict__ list, int nb, const int* __res
   cls[(size_t)c * nb + atomicAdd(&ccount[c], 1)] = r;
 }
 
+// Panel width of the blocked kernel for a tile pitch: 32 columns where its shared memory
+// allows, else 16, else 0 (those systems take the unblocked global-tile kernel).
+constexpr size_t LK_SMEM_MAX = 225u << 10;
+template <class Real>
+static int blk_nb(int pitch) {
+  return blk_smem<Real>(pitch, 32) <= LK_SMEM_MAX ? 32 : blk_smem<Real>(pitch, 16) <= LK_SMEM_MAX ? 16 : 0;
+}
+
+// One launch of the blocked kernel over the classes [0, ncls) of cls (sizes in ccount on
+// the device), tiles of `pitch`; returns the tile buffer (freed by the caller after the
+// launch on the same stream).
+template <class Real, class VT>
+static Real* launch_blocked(const Csr& Ahat, const VT* vals, const int* Zrp, const int* Zcol,
+                            const int* cpts, const int* cls, const int* ccount, int cls_stride,
+                            int ncls, int* ticket, double* Zval, unsigned long long* nsing,
+                            int pitch, int nsys, cudaStream_t s) {
+  const int nbw = blk_nb<Real>(pitch);
+  const size_t smem = blk_smem<Real>(pitch, nbw);
+  auto kernel = nbw == 32 ? lsolve_blk<Real, VT, 32> : lsolve_blk<Real, VT, 16>;
+  once_per_device((const void*)lsolve_blk<Real, VT, 32>, [] {
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_blk<Real, VT, 32>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LK_SMEM_MAX));
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_blk<Real, VT, 16>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LK_SMEM_MAX));
+  });
+  int dev = 0, sms = 0, per_sm = 0;
+  CLAIR_CUDA(cudaGetDevice(&dev));
+  CLAIR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CLAIR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, LK_THREADS, smem));
+  const size_t tile = (size_t)pitch * pitch * sizeof(Real);
+  const int grid = (int)std::max<long long>(
+      1, std::min<long long>({(long long)nsys, (long long)std::max(per_sm, 1) * sms,
+                              (long long)(LB_BUDGET / tile)}));
+  Real* tiles = dalloc<Real>((size_t)grid * pitch * pitch, s);
+  kernel<<<grid, LK_THREADS, smem, s>>>(Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, cls, ccount,
+                                        cls_stride, ncls, ticket, Zval, nsing, tiles, pitch); ::clair::count_launch();
+  CLAIR_LAUNCHED();
+  return tiles;
+}
+
+// The classes [c0, LB_CLASSES) of cls with the unblocked global-tile kernel (systems too
+// large for the blocked kernel's shared memory; rare), each class on a stream of its own.
+template <class Real, class VT>
+static void big_classes(const Csr& Ahat, const VT* vals, const int* Zrp, const int* Zcol,
+                        const int* cpts, const int* cls, const int* ccount, int nb, int c0,
+                        double* Zval, unsigned long long* nsing, cudaStream_t s) {
+  int ch[LB_CLASSES];
+  CLAIR_CUDA(cudaMemcpyAsync(ch, ccount, sizeof(ch), cudaMemcpyDeviceToHost, s));
+  CLAIR_CUDA(cudaStreamSynchronize(s));
+  // the classes run side by side, one stream each (forked from and joined back to s):
+  // a launch lasts as long as its slowest system, so classes in sequence would add up
+  struct Fork {
+    cudaStream_t st[LB_CLASSES] = {};
+    cudaEvent_t ev[LB_CLASSES + 1] = {};
+    ~Fork() {
+      for (cudaStream_t x : st)
+        if (x) cudaStreamDestroy(x);
+      for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    }
+  } fk;
+  Real* tiles[LB_CLASSES] = {};
+  int chunk[LB_CLASSES] = {}, pitch[LB_CLASSES] = {};
+  for (int c = c0; c < LB_CLASSES; ++c) {
+    if (!ch[c]) continue;
+    pitch[c] = std::min(LS_TBIG, 256 << c);
+    const size_t tile = (size_t)pitch[c] * pitch[c] * sizeof(Real);
+    chunk[c] = (int)std::max<size_t>(1, std::min<size_t>(ch[c], LB_BUDGET / tile));
+    tiles[c] = dalloc<Real>((size_t)chunk[c] * pitch[c] * pitch[c], s);
+  }
+  CLAIR_CUDA(cudaEventCreateWithFlags(&fk.ev[LB_CLASSES], cudaEventDisableTiming));
+  CLAIR_CUDA(cudaEventRecord(fk.ev[LB_CLASSES], s));
+  for (int c = c0; c < LB_CLASSES; ++c) {
+    if (!ch[c]) continue;
+    CLAIR_CUDA(cudaStreamCreateWithFlags(&fk.st[c], cudaStreamNonBlocking));
+    CLAIR_CUDA(cudaEventCreateWithFlags(&fk.ev[c], cudaEventDisableTiming));
+    CLAIR_CUDA(cudaStreamWaitEvent(fk.st[c], fk.ev[LB_CLASSES], 0));
+    for (int off = 0; off < ch[c]; off += chunk[c]) {
+      const int cnt = std::min(chunk[c], ch[c] - off);
+      lsolve_big<Real, VT><<<cnt, LB_THREADS, big_smem<Real>(pitch[c]), fk.st[c]>>>(
+          Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, cls + (size_t)c * nb + off, Zval, nsing,
+          tiles[c], pitch[c]); ::clair::count_launch();
+    }
+    CLAIR_CUDA(cudaEventRecord(fk.ev[c], fk.st[c]));
+    CLAIR_CUDA(cudaStreamWaitEvent(s, fk.ev[c], 0));
+  }
+  CLAIR_LAUNCHED();
+  for (int c = c0; c < LB_CLASSES; ++c) dfree(tiles[c], s);
+}
+
 template <class Real, class VT>
 static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const int* Zcol,
                           const int* cpts, const int* lists, const int* counts_h, int nc,
@@ -1320,58 +1698,27 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
         Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 5LL * nc, Zval, nsing); ::clair::count_launch();
   }
   if (counts_h[6]) {
-    // by size class (T up to 256, 512, ..., 4096), each with its own tile pitch, so a few
-    // systems near 4096 unknowns do not shrink the batch of all the others
     CLAIR_REQUIRE(!big_scratch_forbidden, CLAIR_ERR_CAPACITY,
                   "%d local systems larger than %d unknowns need a tile buffer", counts_h[6], TMED);
     const int nb = counts_h[6];
+    const int tmax = counts_h[LS_BUCKETS + 1];  // the bucket's largest T
     int* cls = dalloc<int>((size_t)LB_CLASSES * nb, s);
-    int* ccount = dalloc<int>(LB_CLASSES, s);
-    CLAIR_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int) * LB_CLASSES, s));
+    int* ccount = dalloc<int>(LB_CLASSES + 1, s);  // class sizes, then the blocked ticket
+    CLAIR_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int) * (LB_CLASSES + 1), s));
     class_big<<<ceil_div(nb, 256), 256, 0, s>>>(lists + 6LL * nc, nb, Zrp, cls, ccount); ::clair::count_launch();
     CLAIR_LAUNCHED();
-    int ch[LB_CLASSES];
-    CLAIR_CUDA(cudaMemcpyAsync(ch, ccount, sizeof(ch), cudaMemcpyDeviceToHost, s));
-    CLAIR_CUDA(cudaStreamSynchronize(s));
-    // the classes run side by side, one stream each (forked from and joined back to s):
-    // a launch lasts as long as its slowest system, so classes in sequence would add up
-    struct Fork {
-      cudaStream_t st[LB_CLASSES] = {};
-      cudaEvent_t ev[LB_CLASSES + 1] = {};
-      ~Fork() {
-        for (cudaStream_t x : st)
-          if (x) cudaStreamDestroy(x);
-        for (cudaEvent_t e : ev)
-          if (e) cudaEventDestroy(e);
-      }
-    } fk;
-    Real* tiles[LB_CLASSES] = {};
-    int chunk[LB_CLASSES] = {}, pitch[LB_CLASSES] = {};
-    for (int c = 0; c < LB_CLASSES; ++c) {
-      if (!ch[c]) continue;
-      pitch[c] = std::min(LS_TBIG, 256 << c);
-      const size_t tile = (size_t)pitch[c] * pitch[c] * sizeof(Real);
-      chunk[c] = (int)std::max<size_t>(1, std::min<size_t>(ch[c], LB_BUDGET / tile));
-      tiles[c] = dalloc<Real>((size_t)chunk[c] * pitch[c] * pitch[c], s);
+    // the blocked kernel takes the classes whose tile pitch fits its shared memory
+    int cblk = 0;
+    while (cblk < LB_CLASSES && blk_nb<Real>(256 << cblk) > 0) ++cblk;
+    Real* blk_tiles = nullptr;
+    if (cblk > 0) {
+      const int pitch = std::min(256 << (cblk - 1), ceil_div(tmax, 32) * 32);
+      blk_tiles = launch_blocked<Real, VT>(Ahat, vals, Zrp, Zcol, cpts, cls, ccount, nb, cblk,
+                                           ccount + LB_CLASSES, Zval, nsing, pitch, nb, s);
     }
-    CLAIR_CUDA(cudaEventCreateWithFlags(&fk.ev[LB_CLASSES], cudaEventDisableTiming));
-    CLAIR_CUDA(cudaEventRecord(fk.ev[LB_CLASSES], s));
-    for (int c = 0; c < LB_CLASSES; ++c) {
-      if (!ch[c]) continue;
-      CLAIR_CUDA(cudaStreamCreateWithFlags(&fk.st[c], cudaStreamNonBlocking));
-      CLAIR_CUDA(cudaEventCreateWithFlags(&fk.ev[c], cudaEventDisableTiming));
-      CLAIR_CUDA(cudaStreamWaitEvent(fk.st[c], fk.ev[LB_CLASSES], 0));
-      for (int off = 0; off < ch[c]; off += chunk[c]) {
-        const int cnt = std::min(chunk[c], ch[c] - off);
-        lsolve_big<Real, VT><<<cnt, LB_THREADS, big_smem<Real>(pitch[c]), fk.st[c]>>>(
-            Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, cls + (size_t)c * nb + off, Zval, nsing,
-            tiles[c], pitch[c]); ::clair::count_launch();
-      }
-      CLAIR_CUDA(cudaEventRecord(fk.ev[c], fk.st[c]));
-      CLAIR_CUDA(cudaStreamWaitEvent(s, fk.ev[c], 0));
-    }
-    CLAIR_LAUNCHED();
-    for (int c = 0; c < LB_CLASSES; ++c) dfree(tiles[c], s);
+    if (tmax > (256 << (cblk - 1))) big_classes<Real, VT>(Ahat, vals, Zrp, Zcol, cpts, cls, ccount,
+                                                        nb, cblk, Zval, nsing, s);
+    dfree(blk_tiles, s);
     dfree(cls, s);
     dfree(ccount, s);
   }
@@ -1379,21 +1726,21 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
 }
 
 
-// A stream of the highest priority per device for the large local systems (the ones
-// whose single-system latency sets a level's time), created once.
-static cudaStream_t large_stream() {
+// Streams of the highest priority per device for the large local systems (the ones whose
+// single-system latency sets a level's time), one per side, created once.
+static cudaStream_t large_stream(int side) {
   static std::mutex mu;
-  static cudaStream_t st[256] = {};
+  static cudaStream_t st[256][2] = {};
   int dev = 0;
   CLAIR_CUDA(cudaGetDevice(&dev));
   CLAIR_REQUIRE(dev >= 0 && dev < 256, CLAIR_ERR_ARG, "device ordinal %d out of range", dev);
   std::lock_guard<std::mutex> lock(mu);
-  if (!st[dev]) {
+  if (!st[dev][side]) {
     int lo = 0, hi = 0;
     CLAIR_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    CLAIR_CUDA(cudaStreamCreateWithPriority(&st[dev], cudaStreamNonBlocking, hi));
+    CLAIR_CUDA(cudaStreamCreateWithPriority(&st[dev][side], cudaStreamNonBlocking, hi));
   }
-  return st[dev];
+  return st[dev][side];
 }
 
 // ---- execution configuration of the persistent launch, per device and precision -------
@@ -1575,40 +1922,45 @@ void local_solves_multi(const SideIn* sides, int nsides, const int* cpts, int pr
       st.config_blocks_per_sm = cfg.blocks_per_sm;
       st.config_tuned = cfg.tuned;
       // the systems with T > 64 (one CTA each, or a global tile) beside the persistent
-      // launch on a second stream: a coarse level's time is then the longer of the two
+      // launch, each side on a stream of its own: a coarse level's time is then the
+      // longest of the three
       bool large = false;
       for (int q = 0; q < nsides; ++q)
         large = large || counts_h[q][4] + counts_h[q][5] + counts_h[q][6] > 0;
-      cudaStream_t ls = large ? large_stream() : s;
-      cudaEvent_t fork = nullptr, join = nullptr;
+      cudaStream_t ls[2] = {s, s};
+      cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+      auto join_all = [&]() {
+        for (int q = 0; q < nsides; ++q)
+          if (join[q]) {
+            cudaEventRecord(join[q], ls[q]);
+            cudaStreamWaitEvent(s, join[q], 0);
+            cudaEventDestroy(join[q]);
+            join[q] = nullptr;
+          }
+        if (fork) cudaEventDestroy(fork);
+        fork = nullptr;
+      };
       if (large) {
         CLAIR_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        CLAIR_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
         CLAIR_CUDA(cudaEventRecord(fork, s));
-        CLAIR_CUDA(cudaStreamWaitEvent(ls, fork, 0));
+        for (int q = 0; q < nsides; ++q) {
+          ls[q] = large_stream(q);
+          CLAIR_CUDA(cudaEventCreateWithFlags(&join[q], cudaEventDisableTiming));
+          CLAIR_CUDA(cudaStreamWaitEvent(ls[q], fork, 0));
+        }
       }
       persistent_launch<Real, VT>(sa, nsides, counts_h, cfg, ticket, nsing, s);
       try {
         for (int q = 0; q < nsides; ++q) {
           const SideIn& S = sides[q];
           launch_solves<Real, VT>(*S.Ahat, vals[q], S.Zrp, S.Zcol, cpts, lists[q], counts_h[q],
-                                  S.nc, S.Zval, nsing, ls, false, /*first_bucket=*/4);
+                                  S.nc, S.Zval, nsing, ls[q], false, /*first_bucket=*/4);
         }
       } catch (...) {
-        if (large) {
-          cudaEventRecord(join, ls);
-          cudaStreamWaitEvent(s, join, 0);
-          cudaEventDestroy(fork);
-          cudaEventDestroy(join);
-        }
+        join_all();
         throw;
       }
-      if (large) {
-        CLAIR_CUDA(cudaEventRecord(join, ls));
-        CLAIR_CUDA(cudaStreamWaitEvent(s, join, 0));
-        cudaEventDestroy(fork);
-        cudaEventDestroy(join);
-      }
+      join_all();
     };
     if (precision == CLAIR_MIXED) {
       // values converted once per side instead of once per local system they appear in
