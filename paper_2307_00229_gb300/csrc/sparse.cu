@@ -1035,18 +1035,20 @@ template <bool NUMERIC, int CAP, int PCAP>
 __device__ void spgemm_row_flat(int r, const int* __restrict__ Arp, const int* __restrict__ Acol,
                                 const double* __restrict__ Aval, const int* __restrict__ Brp,
                                 const int* __restrict__ Bcol, const double* __restrict__ Bval,
-                                int* keys, double* vals, int* prefix, double* stage,
+                                int* keys, double* vals, int* prefix, int* bst, double* stage,
                                 int* __restrict__ count, const int* __restrict__ Crp,
                                 int* __restrict__ Ccol, double* __restrict__ Cval) {
   const int lane = threadIdx.x & 31;
   const int a0 = Arp[r], nA = Arp[r + 1] - a0;  // nA <= PCAP (checked by the caller)
-  // prefix[t] = number of products of A entries 0..t-1
+  // prefix[t] = number of products of A entries 0..t-1; bst[t] = start of B's row Acol[t]
   int base = 0;
   for (int c = 0; c < nA; c += 32) {
     int len = 0;
     if (c + lane < nA) {
       const int k = Acol[a0 + c + lane];
-      len = Brp[k + 1] - Brp[k];
+      const int b0 = Brp[k];
+      len = Brp[k + 1] - b0;
+      bst[c + lane] = b0;
     }
     int incl = len;
 #pragma unroll
@@ -1065,26 +1067,34 @@ __device__ void spgemm_row_flat(int r, const int* __restrict__ Arp, const int* _
     if (NUMERIC) vals[s] = 0.0;
   }
   __syncwarp();
+  // product p: A entry lo (largest t with prefix[t] <= p), B entry bst[lo] + p - prefix[lo];
+  // the next chunk's loads are issued before this chunk's table inserts
+  auto locate = [&](int p, int& col, double& prod) {
+    int lo = 0, hi = nA;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (prefix[mid] <= p) lo = mid; else hi = mid;
+    }
+    const int eb = bst[lo] + (p - prefix[lo]);
+    col = Bcol[eb];
+    if (NUMERIC) prod = __dmul_rn(Aval[a0 + lo], Bval[eb]);
+  };
+  int ncol = -1;
+  double nprod = 0.0;
+  if (lane < total) locate(lane, ncol, nprod);
   int mine = 0;
   bool full = false;
   for (int p0 = 0; p0 < total; p0 += 32) {
-    const int p = p0 + lane;
+    const int col = ncol;
+    const double prod = nprod;
+    const bool here = p0 + lane < total;
+    if (p0 + 32 + lane < total) locate(p0 + 32 + lane, ncol, nprod);
     int slot = -1;
-    double prod = 0.0;
-    if (p < total) {
-      int lo = 0, hi = nA;  // largest t with prefix[t] <= p
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (prefix[mid] <= p) lo = mid; else hi = mid;
-      }
-      const int ea = a0 + lo;
-      const int k = Acol[ea];
-      const int eb = Brp[k] + (p - prefix[lo]);
+    if (here) {
       bool is_new = false;
-      slot = sg_insert(keys, rcap, Bcol[eb], &is_new);
+      slot = sg_insert(keys, rcap, col, &is_new);
       if (slot < 0) full = true;
       if (is_new) ++mine;
-      if (NUMERIC) prod = __dmul_rn(Aval[ea], Bval[eb]);
     }
     if (__any_sync(0xffffffffu, full)) break;
     if (NUMERIC) {
@@ -1131,10 +1141,10 @@ __device__ void spgemm_row_flat(int r, const int* __restrict__ Arp, const int* _
   }
 }
 
-// shared memory of one warp of a flat tier: stage, (vals), keys, prefix
+// shared memory of one warp of a flat tier: stage, (vals), keys, prefix, B-row starts
 __host__ __device__ constexpr size_t sg_warp_bytes(bool numeric, int cap, int pcap) {
   return sizeof(double) * 32 + (numeric ? sizeof(double) * cap : 0) + sizeof(int) * cap +
-         sizeof(int) * (pcap + 8);
+         sizeof(int) * (pcap + 8) + sizeof(int) * pcap;
 }
 
 // One warp per row, rows 0..nrows-1 or list[0..nrows-1].  Symbolic: rows whose A row is
@@ -1156,6 +1166,7 @@ spgemm_flat(const int* __restrict__ Arp, const int* __restrict__ Acol,
   int* keys = reinterpret_cast<int*>(mine + sizeof(double) * 32 +
                                      (NUMERIC ? sizeof(double) * CAP : 0));
   int* prefix = keys + CAP;
+  int* bst = prefix + PCAP + 8;
   if (dnrows) nrows = *dnrows;  // rows listed by the previous tier, counted on the device
   for (int idx = blockIdx.x * WARPS + w; idx < nrows; idx += gridDim.x * WARPS) {  // warp-uniform
     const int r = list ? list[idx] : idx;
@@ -1166,7 +1177,7 @@ spgemm_flat(const int* __restrict__ Arp, const int* __restrict__ Acol,
     }
     if (NUMERIC && ((Crp[r + 1] - Crp[r]) > CAP / 2 || long_row)) continue;
     spgemm_row_flat<NUMERIC, CAP, PCAP>(r, Arp, Acol, Aval, Brp, Bcol, Bval, keys, vals, prefix,
-                                        stage, count, Crp, Ccol, Cval);
+                                        bst, stage, count, Crp, Ccol, Cval);
     __syncwarp();
   }
 }
