@@ -115,6 +115,17 @@ struct Krylov {
   double* host = nullptr;  // pinned scalars
 };
 
+// The captured fine-level cycle: head and tail graphs, replayed one after the other.
+struct CycleGraph {
+  cudaGraphExec_t head = nullptr, tail = nullptr;
+  long long kernels = 0;  // kernels in both
+};
+inline void destroy_cycle(CycleGraph& c) {
+  if (c.head) cudaGraphExecDestroy(c.head);
+  if (c.tail) cudaGraphExecDestroy(c.tail);
+  c = CycleGraph{};
+}
+
 }  // namespace clair
 
 struct clair_hierarchy {
@@ -134,8 +145,7 @@ struct clair_hierarchy {
   std::unique_ptr<clair::PhaseClock> setup_clock, solve_clock;
   double level_span_ms[32] = {};           // setup: main-stream time from level to level
   double solve_ms[clair::PH_COUNT] = {};   // last solve, per phase
-  cudaGraphExec_t cycle_exec = nullptr;     // captured fine-level V(1,1) cycle
-  long long cycle_kernels = 0;              // kernels in that graph
+  clair::CycleGraph cycle;                  // captured fine-level V(1,1) cycle
   double* vin = nullptr;                    // its fixed input and output vectors
   double* zout = nullptr;
   double* B0 = nullptr;                     // the caller's mode vector, unsmoothed
@@ -222,8 +232,7 @@ static void release_all(clair_hierarchy* h) {
   dfree(h->coarse_off, s);
   dfree(h->coarse_ioff, s);
   release_krylov(h->kr, s);
-  if (h->cycle_exec) cudaGraphExecDestroy(h->cycle_exec);
-  h->cycle_exec = nullptr;
+  destroy_cycle(h->cycle);
   dfree(h->vin, s);
   dfree(h->zout, s);
   dfree(h->B0, s);
@@ -855,8 +864,31 @@ void residual_t<float>(const Csr& A, const float* b, const float* x, float* r, c
 
 // Cycle on level k: input in Vec<T>::b(L_k); returns where the output is (Vec<T>::x or
 // Vec<T>::y of L_k: the last post-smoothing sweep writes the other buffer, no copy back).
+// vcycle_pre is the CFF pre-smoothing from x = 0, vcycle_post the rest (on the coarsest
+// level, its solve): the fine level's two halves are captured as graphs of their own.
 template <class T>
-static T* vcycle_level(clair_hierarchy* h, int k) {
+static T* vcycle_level(clair_hierarchy* h, int k);
+
+template <class T>
+static void vcycle_pre(clair_hierarchy* h, int k) {
+  if (k == (int)h->lv.size() - 1) return;
+  cudaStream_t s = h->stream;
+  Level& L = h->lv[k];
+  T* b = Vec<T>::b(L);
+  T* x = Vec<T>::x(L);
+  T* y = Vec<T>::y(L);
+  const T* av = Vec<T>::aval(L.A);
+  // a batch folds each instance's weight into D^-1 (0 for frozen instances)
+  const bool batch = h->ninst > 1;
+  const T* dv = batch ? Vec<T>::wpre(L) : Vec<T>::dinv(L);
+  const T w = batch ? T(1) : (T)L.omega;
+  jacobi_from_zero<T>(L.n, dv, L.cf, 1, w, b, x, s);
+  jacobi<T>(L.A, av, dv, L.cf, 0, w, b, x, y, s);
+  jacobi<T>(L.A, av, dv, L.cf, 0, w, b, y, x, s);
+}
+
+template <class T>
+static T* vcycle_post(clair_hierarchy* h, int k) {
   cudaStream_t s = h->stream;
   Level& L = h->lv[k];
   T* b = Vec<T>::b(L);
@@ -872,16 +904,10 @@ static T* vcycle_level(clair_hierarchy* h, int k) {
     return x;
   }
   const T* av = Vec<T>::aval(L.A);
-  // a batch folds each instance's weight into D^-1 (0 for frozen instances)
   const bool batch = h->ninst > 1;
-  const T* dv = batch ? Vec<T>::wpre(L) : Vec<T>::dinv(L);
   const T* dvpost = batch ? Vec<T>::wpost(L) : Vec<T>::dinv(L);
   const T w = batch ? T(1) : (T)L.omega;
   const T wpost = batch ? T(1) : (h->p.post_weighted ? w : T(1));
-  // CFF pre-smoothing from x = 0
-  jacobi_from_zero<T>(L.n, dv, L.cf, 1, w, b, x, s);
-  jacobi<T>(L.A, av, dv, L.cf, 0, w, b, x, y, s);
-  jacobi<T>(L.A, av, dv, L.cf, 0, w, b, y, x, s);
   // residual, restriction, coarse cycle, interpolation
   T* r = Vec<T>::r(L);
   residual_t<T>(L.A, b, x, r, s);
@@ -905,38 +931,57 @@ static T* vcycle_level(clair_hierarchy* h, int k) {
   return y;
 }
 
-// z = M^-1 v on level k (float64 in and out), launching every kernel.
-static void apply_precond_direct(clair_hierarchy* h, int k, const double* v, double* z) {
-  cudaStream_t s = h->stream;
+template <class T>
+static T* vcycle_level(clair_hierarchy* h, int k) {
+  vcycle_pre<T>(h, k);
+  return vcycle_post<T>(h, k);
+}
+
+// z = M^-1 v on level k (float64 in and out), launching every kernel: the input's
+// conversion and the pre-smoothing (head), then the rest of the cycle and the output's
+// conversion (tail).
+static bool precond_fp32(const clair_hierarchy* h, const Level& L) {
+  return h->p.precision == CLAIR_MIXED && !h->cycle_fp64 && !L.cycle64;
+}
+static void precond_head(clair_hierarchy* h, int k, const double* v) {
   Level& L = h->lv[k];
-  struct LanesScope {  // the hierarchy's row-kernel lane rule for these launches
-    int keep;
-    explicit LanesScope(int w) : keep(cycle_short_lanes()) { set_cycle_short_lanes(w); }
-    ~LanesScope() { set_cycle_short_lanes(keep); }
-  } lanes(h->short_lanes);
-  if (h->p.precision == CLAIR_MIXED && !h->cycle_fp64 && !L.cycle64) {
-    to_float(v, L.b32, L.n, s);
-    const float* out = vcycle_level<float>(h, k);
-    to_double(out, z, L.n, s);
+  if (precond_fp32(h, L)) {
+    to_float(v, L.b32, L.n, h->stream);
+    vcycle_pre<float>(h, k);
   } else {
-    copy_f64(v, L.b64, L.n, s);
-    const double* out = vcycle_level<double>(h, k);
-    copy_f64(out, z, L.n, s);
+    copy_f64(v, L.b64, L.n, h->stream);
+    vcycle_pre<double>(h, k);
   }
+}
+static void precond_tail(clair_hierarchy* h, int k, double* z) {
+  Level& L = h->lv[k];
+  if (precond_fp32(h, L)) {
+    const float* out = vcycle_post<float>(h, k);
+    to_double(out, z, L.n, h->stream);
+  } else {
+    const double* out = vcycle_post<double>(h, k);
+    copy_f64(out, z, L.n, h->stream);
+  }
+}
+struct LanesScope {  // the hierarchy's row-kernel lane rule for these launches
+  int keep;
+  explicit LanesScope(int w) : keep(cycle_short_lanes()) { set_cycle_short_lanes(w); }
+  ~LanesScope() { set_cycle_short_lanes(keep); }
+};
+static void apply_precond_direct(clair_hierarchy* h, int k, const double* v, double* z) {
+  LanesScope lanes(h->short_lanes);
+  precond_head(h, k, v);
+  precond_tail(h, k, z);
 }
 
 // The fine-level cycle is a fixed sequence of about ten kernels per level; it is captured
-// once into a CUDA graph with fixed input / output buffers (h->vin, h->zout) and replayed,
-// so each FGMRES iteration pays one graph launch instead of every kernel launch.  In
-// MIXED precision the cycle is captured with both lane rules for short FP32 rows (lanes
-// up to the mean row length, or one thread per row), the replays of each are timed, and
-// the faster graph is kept.
-static cudaGraphExec_t capture_cycle(clair_hierarchy* h, long long* kernels) {
-  cudaStream_t cs;
-  CLAIR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  cudaStream_t keep = h->stream;
-  h->stream = cs;
-  const long long before = launch_count();
+// once, with fixed input / output buffers (h->vin, h->zout), into two CUDA graphs that
+// are replayed: the head (input conversion and the fine level's pre-smoothing, four
+// kernels) and the tail (the rest).  The host's launch of the long tail then overlaps the
+// head's execution instead of delaying the cycle's first kernel.  In MIXED precision the
+// cycle is captured with each lane rule for short FP32 rows, the replays of each are
+// timed, and the fastest is kept.
+static cudaGraphExec_t capture_part(clair_hierarchy* h, cudaStream_t cs, bool head) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
   struct PdlScope {  // the captured kernels chain by programmatic dependence
@@ -947,7 +992,11 @@ static cudaGraphExec_t capture_cycle(clair_hierarchy* h, long long* kernels) {
     CLAIR_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     {
       PdlScope pdl;
-      apply_precond_direct(h, 0, h->vin, h->zout);
+      LanesScope lanes(h->short_lanes);
+      if (head)
+        precond_head(h, 0, h->vin);
+      else
+        precond_tail(h, 0, h->zout);
     }
     CLAIR_CUDA(cudaStreamEndCapture(cs, &g));
     CLAIR_CUDA(cudaGraphInstantiate(&exec, g, 0));
@@ -955,25 +1004,47 @@ static cudaGraphExec_t capture_cycle(clair_hierarchy* h, long long* kernels) {
     cudaGraph_t dummy;
     cudaStreamEndCapture(cs, &dummy);
     if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  cudaGraphDestroy(g);
+  return exec;
+}
+
+static CycleGraph capture_cycle(clair_hierarchy* h) {
+  cudaStream_t cs;
+  CLAIR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t keep = h->stream;
+  h->stream = cs;
+  const long long before = launch_count();
+  CycleGraph c;
+  try {
+    c.head = capture_part(h, cs, true);
+    c.tail = capture_part(h, cs, false);
+  } catch (...) {
+    destroy_cycle(c);
     h->stream = keep;
     cudaStreamDestroy(cs);
     throw;
   }
-  *kernels = launch_count() - before;
-  count_launches(-*kernels);  // captured, not launched
-  cudaGraphDestroy(g);
+  c.kernels = launch_count() - before;
+  count_launches(-c.kernels);  // captured, not launched
   h->stream = keep;
   cudaStreamDestroy(cs);
-  return exec;
+  return c;
 }
 
-static float time_graph(cudaGraphExec_t exec, cudaStream_t s) {
+static void launch_cycle(const CycleGraph& c, cudaStream_t s) {
+  CLAIR_CUDA(cudaGraphLaunch(c.head, s));
+  CLAIR_CUDA(cudaGraphLaunch(c.tail, s));
+}
+
+static float time_cycle(const CycleGraph& c, cudaStream_t s) {
   cudaEvent_t e0, e1;
   CLAIR_CUDA(cudaEventCreate(&e0));
   CLAIR_CUDA(cudaEventCreate(&e1));
-  CLAIR_CUDA(cudaGraphLaunch(exec, s));  // warm
+  launch_cycle(c, s);  // warm
   CLAIR_CUDA(cudaEventRecord(e0, s));
-  for (int i = 0; i < 3; ++i) CLAIR_CUDA(cudaGraphLaunch(exec, s));
+  for (int i = 0; i < 3; ++i) launch_cycle(c, s);
   CLAIR_CUDA(cudaEventRecord(e1, s));
   CLAIR_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;
@@ -1002,7 +1073,7 @@ static int* lanes_slot() {
 static void build_cycle_graph(clair_hierarchy* h) {
   if (h->p.precision != CLAIR_MIXED) {
     h->short_lanes = 0;
-    h->cycle_exec = capture_cycle(h, &h->cycle_kernels);
+    h->cycle = capture_cycle(h);
     h->cycle_lanes_pick = 0;
     return;
   }
@@ -1011,55 +1082,51 @@ static void build_cycle_graph(clair_hierarchy* h) {
     const int known = *lanes_slot();
     if (known >= 0) {  // timed once per device: capture the chosen rule only
       h->short_lanes = h->cycle_lanes_pick = known;
-      h->cycle_exec = capture_cycle(h, &h->cycle_kernels);
+      h->cycle = capture_cycle(h);
       return;
     }
   }
   CLAIR_CUDA(cudaMemsetAsync(h->vin, 0, sizeof(double) * h->lv[0].n, h->stream));
-  cudaGraphExec_t best = nullptr;
-  long long best_k = 0;
+  CycleGraph best;
   float best_ms = 0.f;
   for (int lanes = 0; lanes <= 2; ++lanes) {
     h->short_lanes = lanes;
-    long long kk = 0;
-    cudaGraphExec_t e = capture_cycle(h, &kk);
+    CycleGraph e = capture_cycle(h);
     float ms = 0.f;
     try {
-      ms = time_graph(e, h->stream);
-      count_launches(4 * kk);
+      ms = time_cycle(e, h->stream);
+      count_launches(4 * e.kernels);
     } catch (...) {
-      cudaGraphExecDestroy(e);
-      if (best) cudaGraphExecDestroy(best);
+      destroy_cycle(e);
+      destroy_cycle(best);
       throw;
     }
-    if (!best || ms < best_ms) {
-      if (best) cudaGraphExecDestroy(best);
+    if (!best.head || ms < best_ms) {
+      destroy_cycle(best);
       best = e;
-      best_k = kk;
       best_ms = ms;
       h->cycle_lanes_pick = lanes;
     } else {
-      cudaGraphExecDestroy(e);
+      destroy_cycle(e);
     }
   }
   h->short_lanes = h->cycle_lanes_pick;
-  h->cycle_exec = best;
-  h->cycle_kernels = best_k;
+  h->cycle = best;
   std::lock_guard<std::mutex> lock(g_lanes_mu);
   *lanes_slot() = h->cycle_lanes_pick;
 }
 
 // z = M^-1 v on level k; the fine level replays the captured cycle.
 static void apply_precond(clair_hierarchy* h, int k, const double* v, double* z) {
-  if (k != 0 || !h->cycle_exec || h->cycle_fp64) {
+  if (k != 0 || !h->cycle.head || h->cycle_fp64) {
     apply_precond_direct(h, k, v, z);
     return;
   }
   cudaStream_t s = h->stream;
   const size_t bytes = sizeof(double) * h->lv[0].n;
   CLAIR_CUDA(cudaMemcpyAsync(h->vin, v, bytes, cudaMemcpyDeviceToDevice, s));
-  CLAIR_CUDA(cudaGraphLaunch(h->cycle_exec, s));
-  for (long long i = 0; i < h->cycle_kernels; ++i) count_launch();
+  launch_cycle(h->cycle, s);
+  for (long long i = 0; i < h->cycle.kernels; ++i) count_launch();
   CLAIR_CUDA(cudaMemcpyAsync(z, h->zout, bytes, cudaMemcpyDeviceToDevice, s));
 }
 
