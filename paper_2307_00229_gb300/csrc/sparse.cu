@@ -1089,12 +1089,8 @@ __device__ void spgemm_row_flat(int r, const int* __restrict__ Arp, const int* _
     const double prod = nprod;
     const bool here = p0 + lane < total;
     if (p0 + 32 + lane < total) locate(p0 + 32 + lane, ncol, nprod);
-    // lanes whose products share a column: the lowest one inserts it and adds the
-    // group's products in lane order
-    const unsigned grp = __match_any_sync(0xffffffffu, here ? col : -1);
-    const bool lead = here && lane == __ffs(grp) - 1;
     int slot = -1;
-    if (lead) {
+    if (here) {
       bool is_new = false;
       slot = sg_insert(keys, rcap, col, &is_new);
       if (slot < 0) full = true;
@@ -1103,8 +1099,9 @@ __device__ void spgemm_row_flat(int r, const int* __restrict__ Arp, const int* _
     if (__any_sync(0xffffffffu, full)) break;
     if (NUMERIC) {
       stage[lane] = prod;
+      const unsigned grp = __match_any_sync(0xffffffffu, slot);
       __syncwarp();
-      if (lead) {
+      if (slot >= 0 && lane == __ffs(grp) - 1) {
         double sum = prod;
         for (unsigned g = grp & (grp - 1); g; g &= g - 1) sum = __dadd_rn(sum, stage[__ffs(g) - 1]);
         vals[slot] = __dadd_rn(vals[slot], sum);
