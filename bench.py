@@ -42,7 +42,7 @@ MEASURED_TRAFFIC = {
         # every local-solve launch (lsolve_persist and lsolve_cta), scaled by the ratio of
         # algorithmic bytes (530.9 MB / 132.1 MB = 4.02) to 1024^2
         "bytes": 80.8e6 * (530854884.0 / 132096084.0),
-        "source_sha256": "8a991541926500b79c3fadb4faf5cd9a8637b6def42dc5515a4c8a7390c13eeb",
+        "source_sha256": "8fe20bcf8b258ae30f79ff57c99e2dc82b8ec02774a9b279264d057b292a191e",
         "capture": "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
                    "--clock-control none -k regex:lsolve_ python bench.py --nside 512 --steps 1 "
                    "--warmup 1 --fp64-steps 0 --no-e2e --no-cpu-baseline --no-errors "
@@ -184,9 +184,9 @@ def vcycle_bytes(levels, s=4):
 def phase_bytes(levels, arnoldi_steps=15, sweeps=5):
     """Algorithmic bytes per setup phase, summed over the levels that have transfers (FP64
     data: 8-byte values, 4-byte indices).  Each is the data the phase must read and write
-    at least once: transpose, row maxima and the two strength masks, one pass of the
-    independent-set selection (split); the two interpolation-strength masks and the two
-    pattern CSRs (pattern); the Arnoldi steps, each an SpMV of D^-1 A plus the classical
+    at least once: transpose, row maxima, the coarsening- and interpolation-strength masks
+    of A and A^T (one pass over each, two masks written), one pass of the independent-set
+    selection (split); the two pattern CSRs (pattern); the Arnoldi steps, each an SpMV of D^-1 A plus the classical
     Gram-Schmidt passes over the basis, twice (weight); CFF sweeps on both mode vectors
     (smooth); R, A, P read once and A_c written once (galerkin)."""
     b = {"split": 0.0, "pattern": 0.0, "weight": 0.0, "smooth": 0.0, "galerkin": 0.0}
@@ -197,8 +197,8 @@ def phase_bytes(levels, arnoldi_steps=15, sweeps=5):
         nnzR, nnzP = L["nnz_R"], L["nnz_P"]
         nnzAc = levels[k + 1]["nnz"] if k + 1 < len(levels) else 0
         csr = 12 * nnz + 4 * (n + 1)
-        b["split"] += 2 * csr + 2 * (12 * nnz + 8 * n) + 2 * (csr + 8 * n + nnz) + 2 * (4 * nnz + nnz) + n
-        b["pattern"] += 2 * (csr + 8 * n + nnz) + 8 * nnz + 4 * (nnzR + nnzP) + 8 * (L["nc"] + n)
+        b["split"] += 2 * csr + 2 * (12 * nnz + 8 * n) + 2 * (csr + 16 * n + 2 * nnz) + 2 * (4 * nnz + nnz) + n
+        b["pattern"] += 8 * nnz + 4 * (nnzR + nnzP) + 8 * (L["nc"] + n)
         for j in range(arnoldi_steps):
             b["weight"] += csr + 24 * n + 2 * (8 * n * (j + 1) + 8 * n) + 2 * (8 * n * (j + 1) + 16 * n) + 24 * n
         sweep = csr + n + 4 * 8 * n

@@ -14,8 +14,9 @@
 namespace clair {
 
 // --- functions of the other translation units -----------------------------------------
-void strength(const Csr& M, const double* thr, double theta, int mode, unsigned char* mask,
-              cudaStream_t s);
+void strength2(const Csr& M, const double* thr1, double theta1, int mode1, unsigned char* mask1,
+               const double* thr2, double theta2, int mode2, unsigned char* mask2,
+               cudaStream_t s);
 void split_fc(const Csr& A, const Csr& At, const unsigned char* sA, const unsigned char* sAt,
               const int* lbase, signed char* cf, cudaStream_t s);
 void aggregate(const Csr& A, const Csr& At, const unsigned char* sA, const unsigned char* sAt,
@@ -516,15 +517,20 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
     double* rmaxAt = dalloc<double>(n, s);
     unsigned char* sA = dalloc<unsigned char>(L.A.nnz, s);
     unsigned char* sAt = dalloc<unsigned char>(L.A.nnz, s);
+    unsigned char* sR = dalloc<unsigned char>(L.A.nnz, s);
+    unsigned char* sP = dalloc<unsigned char>(L.A.nnz, s);
     std::vector<int> cnt;                         // C-points per instance (batch)
     {
       ClockScope clk(PH_SPLIT, s);
       csr_transpose(L.A, At, nullptr, s);
       row_max_offdiag(L.A, rmaxA, s);
       row_max_offdiag(At, rmaxAt, s);
-      // coarsening strength S(A, theta_c): on A row-relative, on A^T via A's row maxima
-      strength(L.A, rmaxA, p.theta_coarsen, 0, sA, s);
-      strength(At, rmaxA, p.theta_coarsen, 1, sAt, s);
+      // coarsening strength S(A, theta_c): on A row-relative, on A^T via A's row maxima;
+      // in the same passes the interpolation-strength masks of the two patterns:
+      // R: Algorithm 1 on A^T, walked on A, S(A^T) uses the row maxima of A^T
+      // P: Algorithm 1 on A,   walked on A^T, S(A) uses the row maxima of A
+      strength2(L.A, rmaxA, p.theta_coarsen, 0, sA, rmaxAt, p.theta_interp, 1, sR, s);
+      strength2(At, rmaxA, p.theta_coarsen, 1, sAt, rmaxA, p.theta_interp, 1, sP, s);
       enqueue_weight();
       L.cf = dalloc<signed char>(n, s);
       if (k == 0 && cf_marker) {
@@ -581,22 +587,17 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
       dfree(rmaxAt, s);
       dfree(sA, s);
       dfree(sAt, s);
+      dfree(sR, s);
+      dfree(sP, s);
       break;
     }
     CLAIR_CUDA(cudaEventRecord(ss.split, s));
-    // interpolation-strength masks for the two patterns
-    // R: Algorithm 1 on A^T, walked on A, S(A^T) uses the row maxima of A^T
-    // P: Algorithm 1 on A,   walked on A^T, S(A) uses the row maxima of A
-    unsigned char* sR = sA;   // reuse buffers (the splitting is done)
-    unsigned char* sP = sAt;
     Csr Pt;
     int* Mrp = nullptr;
     int* Mcol = nullptr;
     PatternJob jobR, jobP;
     {
       ClockScope clk(PH_PATTERN, s);
-      strength(L.A, rmaxAt, p.theta_interp, 1, sR, s);
-      strength(At, rmaxA, p.theta_interp, 1, sP, s);
       if (agg) aggregate_members(agg, n, L.nc, &Mrp, &Mcol, s);
       if (!sym) jobR = pattern_count(L.A, sR, L.cf, L.cpts, L.nc, n, p.degree, Mrp, Mcol, s);
       jobP = pattern_count(At, sP, L.cf, L.cpts, L.nc, n, p.degree, Mrp, Mcol, s);
@@ -681,6 +682,8 @@ static void setup_levels(clair_hierarchy* h, const double* B0, const signed char
     dfree(rmaxAt, s);
     dfree(sA, s);
     dfree(sAt, s);
+    dfree(sR, s);
+    dfree(sP, s);
     At.release(s);
     // Galerkin coarse operator A_c = (R A) P
     Csr RA, Ac;

@@ -28,49 +28,59 @@ namespace clair {
 // (row-relative, thr = row maxima of M); mode 1: iff |m_rc| >= theta * thr[c]
 // (column-relative: thr = row maxima of M^T).  Diagonal and zero entries are never strong.
 // ------------------------------------------------------------------------------------
-// W lanes per row (entries e0 + lane, e0 + lane + W, ...): short rows one per thread,
-// the long rows of coarse levels spread over lanes instead of one thread's serial loop.
+// Two masks of the same matrix in one pass over its entries (the coarsening and the
+// interpolation thresholds): mask1 with (thr1, theta1, mode1), mask2 with (thr2, theta2,
+// mode2).  W lanes per row (entries e0 + lane, e0 + lane + W, ...): short rows one per
+// thread, the long rows of coarse levels spread over lanes.
 template <int W>
-__global__ void strength_mask(const int* __restrict__ rowptr, const int* __restrict__ col,
-                              const double* __restrict__ val, int rows,
-                              const double* __restrict__ thr, double theta, int mode,
-                              unsigned char* __restrict__ mask) {
+__global__ void strength_mask2(const int* __restrict__ rowptr, const int* __restrict__ col,
+                               const double* __restrict__ val, int rows,
+                               const double* __restrict__ thr1, double theta1, int mode1,
+                               unsigned char* __restrict__ mask1,
+                               const double* __restrict__ thr2, double theta2, int mode2,
+                               unsigned char* __restrict__ mask2) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int r = (int)(t / W), lane = (int)(t % W);
   if (r >= rows) return;
-  const double tr = mode == 0 ? theta * thr[r] : 0.0;
+  const double tr1 = mode1 == 0 ? theta1 * thr1[r] : 0.0;
+  const double tr2 = mode2 == 0 ? theta2 * thr2[r] : 0.0;
   for (int e = rowptr[r] + lane; e < rowptr[r + 1]; e += W) {
     const int c = col[e];
     const double a = fabs(val[e]);
-    const double th = mode == 0 ? tr : theta * thr[c];
-    mask[e] = (c != r && a > 0.0 && a >= th) ? 1 : 0;
+    const double th1 = mode1 == 0 ? tr1 : theta1 * thr1[c];
+    const double th2 = mode2 == 0 ? tr2 : theta2 * thr2[c];
+    const bool off = c != r && a > 0.0;
+    mask1[e] = (off && a >= th1) ? 1 : 0;
+    mask2[e] = (off && a >= th2) ? 1 : 0;
   }
 }
 
-void strength(const Csr& M, const double* thr, double theta, int mode, unsigned char* mask,
-              cudaStream_t s) {
+void strength2(const Csr& M, const double* thr1, double theta1, int mode1, unsigned char* mask1,
+               const double* thr2, double theta2, int mode2, unsigned char* mask2,
+               cudaStream_t s) {
   if (!M.rows) return;
   const double avg = (double)M.nnz / M.rows;
   int W = 1;
   while (W < 32 && 4 * W < avg) W <<= 1;
   const int blocks = ceil_div((long long)M.rows * W, 256);
   switch (W) {
-#define CLAIR_SM_CASE(WW)                                                                        \
-  case WW:                                                                                       \
-    strength_mask<WW><<<blocks, 256, 0, s>>>(M.rowptr, M.col, M.val, M.rows, thr, theta, mode, \
-                                             mask);                                              \
+#define CLAIR_SM2_CASE(WW)                                                                   \
+  case WW:                                                                                   \
+    strength_mask2<WW><<<blocks, 256, 0, s>>>(M.rowptr, M.col, M.val, M.rows, thr1, theta1, \
+                                              mode1, mask1, thr2, theta2, mode2, mask2);    \
     break;
-    CLAIR_SM_CASE(1)
-    CLAIR_SM_CASE(2)
-    CLAIR_SM_CASE(4)
-    CLAIR_SM_CASE(8)
-    CLAIR_SM_CASE(16)
-    CLAIR_SM_CASE(32)
-#undef CLAIR_SM_CASE
+    CLAIR_SM2_CASE(1)
+    CLAIR_SM2_CASE(2)
+    CLAIR_SM2_CASE(4)
+    CLAIR_SM2_CASE(8)
+    CLAIR_SM2_CASE(16)
+    CLAIR_SM2_CASE(32)
+#undef CLAIR_SM2_CASE
   }
   ::clair::count_launch();
   CLAIR_LAUNCHED();
 }
+
 
 // ------------------------------------------------------------------------------------
 // C/F splitting.  sA: mask of S over A's entries (row i of A: S_ij, i depends on j);
