@@ -95,8 +95,8 @@ typedef struct {
   int64_t r_rows;             /* local systems solved for R over all levels */
   int64_t p_cols;             /* local systems solved for P over all levels */
   int64_t t_hist[9];          /* local systems (R and P) with T <= 8, 16, 32, 64, 128, up to
-                                 224 (FP32) / 160 (FP64) in shared memory, up to 4096 on a
-                                 global tile (entries 0-6) */
+                                 224 (FP32) / 160 (FP64), up to 4096 (entries 0-6; the last
+                                 two on global tiles) */
   int64_t singular_blocks;    /* local blocks with a zero pivot */
   int64_t empty_constraints;  /* F-points skipped by the projection (no C-point or B_c = 0) */
   double setup_ms;            /* device time of the last clair_setup */

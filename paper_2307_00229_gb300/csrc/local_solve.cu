@@ -27,14 +27,15 @@
 
 namespace clair {
 
-// Solvable buckets: T in [0,8], (8,16], (16,32], (32,64], (64,128], (128,tmed] (one CTA
-// per system, the tile in shared memory: tmed = LS_TMED32 in FP32, LS_TMED64 in FP64),
-// (tmed,4096] (a global tile, eliminated in panels where a panel fits shared memory, else
-// step by step); bucket 7 counts systems larger than LS_TBIG (refused).
+// Solvable buckets: T in [0,8], (8,16], (16,32], (32,64], (64,128], (128,tmed] and
+// (tmed,4096] (global tiles, eliminated in panels where a panel fits shared memory, else
+// step by step; bucket 5 in one launch of tiles of pitch tmed, 128 threads per system, so
+// that several of its many systems share an SM: tmed = LS_TMED32 in FP32, LS_TMED64 in
+// FP64); bucket 7 counts systems larger than LS_TBIG (refused).
 constexpr int LS_BUCKETS = 7;
 constexpr int LS_TBIG = 4096;
-constexpr int LS_TMED32 = 224;  // 224 x 228 floats: 204 KB of shared memory
-constexpr int LS_TMED64 = 160;  // 160 x 162 doubles: 207 KB
+constexpr int LS_TMED32 = 224;
+constexpr int LS_TMED64 = 160;
 __host__ __device__ inline int ls_bucket(int T, int tmed) {
   return T <= 8 ? 0 : T <= 16 ? 1 : T <= 32 ? 2 : T <= 64 ? 3 : T <= 128 ? 4
        : T <= tmed ? 5 : T <= LS_TBIG ? 6 : 7;
@@ -1003,8 +1004,9 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
 }
 
 // ------------------------------------------------------------------------------------
-// Large systems, blocked (128 < T up to a few thousand): one block of 256 threads per
-// system at a time, the matrix in a global scratch tile stored row-major (row p at
+// Large systems, blocked (128 < T up to a few thousand): one block of NT threads per
+// system at a time (128 for tiles of pitch <= 256, so that several systems share an SM;
+// else 256), the matrix in a global scratch tile stored row-major (row p at
 // M + p * pitch), eliminated in panels of NB columns.  Each panel's columns are loaded
 // into shared memory and factored there step by step (the same implicit partial pivoting,
 // one barrier per step); the pivot rows' entries right of the panel (the rows of U) and
@@ -1016,7 +1018,7 @@ lsolve_big(const int* __restrict__ Arp, const int* __restrict__ Acol,
 // row reads), then the 32 x 32 triangle by one warp from shared memory.
 // Blocks take systems from a device ticket, the largest size class first.
 // ------------------------------------------------------------------------------------
-constexpr int LK_THREADS = 256;
+constexpr int LK_SMALL_PITCH = 256;
 
 template <class Real>
 __host__ __device__ constexpr int blk_ps(int nb) {
@@ -1029,8 +1031,8 @@ static size_t blk_smem(int pitch, int nb) {
          32 * 33 * sizeof(Real) + 3 * (size_t)pitch * sizeof(int);
 }
 
-template <class Real, class VT, int NB>
-__global__ void __launch_bounds__(LK_THREADS, sizeof(Real) == 4 ? 2 : 1)
+template <class Real, class VT, int NB, int NT>
+__global__ void __launch_bounds__(NT, (sizeof(Real) == 4 ? 512 : 256) / NT)
 lsolve_blk(const int* __restrict__ Arp, const int* __restrict__ Acol,
            const VT* __restrict__ Aval, const int* __restrict__ Zrp,
            const int* __restrict__ Zcol, const int* __restrict__ cpts,
@@ -1048,8 +1050,8 @@ lsolve_blk(const int* __restrict__ Arp, const int* __restrict__ Acol,
   int* zl = reinterpret_cast<int*>(tri + 32 * 33);
   int* steprow = zl + pitch;
   int* ulist = steprow + pitch;
-  __shared__ Real red_v[2][LK_THREADS / 32];
-  __shared__ int red_w[2][LK_THREADS / 32];
+  __shared__ Real red_v[2][NT / 32];
+  __shared__ int red_w[2][NT / 32];
   __shared__ int s_task, s_d, s_sing, s_nu;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   Real* M = scratch + (size_t)blockIdx.x * pitch * pitch;
@@ -1075,19 +1077,19 @@ lsolve_blk(const int* __restrict__ Arp, const int* __restrict__ Acol,
       s_sing = 0;
     }
     __syncthreads();
-    for (int q = t; q < len; q += LK_THREADS)
+    for (int q = t; q < len; q += NT)
       if (Zcol[base + q] == i) s_d = q;
     __syncthreads();
     const int d = s_d;
-    for (int p = t; p < T; p += LK_THREADS) {
+    for (int p = t; p < T; p += NT) {
       zl[p] = Zcol[base + p + (p >= d ? 1 : 0)];
       rhs[p] = Real(0);
     }
-    for (int p = wid; p < T; p += LK_THREADS / 32)
+    for (int p = wid; p < T; p += NT / 32)
       for (int q = lane; q < T; q += 32) M[(size_t)p * pitch + q] = Real(0);
     __syncthreads();
     // row p's entries in batches of 4: loads and column searches before the stores
-    for (int p = t; p < T; p += LK_THREADS) {
+    for (int p = t; p < T; p += NT) {
       const int l = zl[p];
       const int e_end = Arp[l + 1];
       for (int e0 = Arp[l]; e0 < e_end; e0 += 4) {
@@ -1110,14 +1112,14 @@ lsolve_blk(const int* __restrict__ Arp, const int* __restrict__ Acol,
       }
     }
     // thread t owns rows t + 256 rr; bit rr of `done`: that row is eliminated (or absent)
-    const int nr = (T + LK_THREADS - 1) / LK_THREADS;
+    const int nr = (T + NT - 1) / NT;
     unsigned done = 0;
     for (int rr = 0; rr < nr; ++rr)
-      if (t + LK_THREADS * rr >= T) done |= 1u << rr;
+      if (t + NT * rr >= T) done |= 1u << rr;
     __syncthreads();
     for (int k0 = 0; k0 < T; k0 += NB) {
       const int nb = min(NB, T - k0);
-      for (int e = t; e < T * NB; e += LK_THREADS) {
+      for (int e = t; e < T * NB; e += NT) {
         const int p = e / NB, kk = e % NB;
         if (kk < nb) Pn[p * PS + kk] = M[(size_t)p * pitch + k0 + kk];
       }
@@ -1131,7 +1133,7 @@ lsolve_blk(const int* __restrict__ Arp, const int* __restrict__ Acol,
         int who = 0x7fffffff;
         for (int rr = 0; rr < nr; ++rr)
           if (!((done >> rr) & 1u)) {
-            const int p = t + LK_THREADS * rr;
+            const int p = t + NT * rr;
             const Real a = Pn[p * PS + kk];
             Real m = a < 0 ? -a : a;
             if (!(m >= Real(0))) m = Real(-0.5);  // NaN: still a row to take, after any number
@@ -1157,7 +1159,7 @@ lsolve_blk(const int* __restrict__ Arp, const int* __restrict__ Acol,
         Real bv = red_v[par][0];
         int piv = red_w[par][0];
 #pragma unroll
-        for (int w = 1; w < LK_THREADS / 32; ++w)
+        for (int w = 1; w < NT / 32; ++w)
           if (red_v[par][w] > bv || (red_v[par][w] == bv && red_w[par][w] < piv)) {
             bv = red_v[par][w];
             piv = red_w[par][w];
@@ -1172,7 +1174,7 @@ lsolve_blk(const int* __restrict__ Arp, const int* __restrict__ Acol,
         const Real rpiv = rhs[piv];
         for (int rr = 0; rr < nr; ++rr) {
           if ((done >> rr) & 1u) continue;
-          const int p = t + LK_THREADS * rr;
+          const int p = t + NT * rr;
           if (p == piv) {
             done |= 1u << rr;
             continue;
@@ -1186,19 +1188,19 @@ lsolve_blk(const int* __restrict__ Arp, const int* __restrict__ Acol,
         }
       }
       __syncthreads();  // the panel's last updates and its pivot rows
-      for (int e = t; e < T * NB; e += LK_THREADS) {
+      for (int e = t; e < T * NB; e += NT) {
         const int p = e / NB, kk = e % NB;
         if (kk < nb) M[(size_t)p * pitch + k0 + kk] = Pn[p * PS + kk];
       }
       for (int rr = 0; rr < nr; ++rr)
-        if (!((done >> rr) & 1u)) ulist[atomicAdd(&s_nu, 1)] = t + LK_THREADS * rr;
+        if (!((done >> rr) & 1u)) ulist[atomicAdd(&s_nu, 1)] = t + NT * rr;
       __syncthreads();
       const int jt0 = k0 + NB;  // columns right of a full panel (a partial one ends at T)
       if (jt0 < T) {
         const int nu = s_nu;
         const int width = T - jt0;
-        const int cw = width > 128 ? 256 : width > 64 ? 128 : width > 32 ? 64 : 32;
-        const int G = LK_THREADS / cw, g = t / cw, cl = t % cw;
+        const int cw = width > 128 && NT > 128 ? 256 : width > 64 ? 128 : width > 32 ? 64 : 32;
+        const int G = NT / cw, g = t / cw, cl = t % cw;
         for (int jc = jt0; jc < T; jc += cw) {
           const int j = jc + cl;
           const bool act = j < T;
@@ -1253,7 +1255,7 @@ lsolve_blk(const int* __restrict__ Arp, const int* __restrict__ Acol,
     // back substitution, 32 steps at a time from the last
     for (int ke = T; ke > 0; ke -= 32) {
       const int kb = ke > 32 ? ke - 32 : 0, nbk = ke - kb;
-      for (int kq = wid; kq < nbk; kq += LK_THREADS / 32) {
+      for (int kq = wid; kq < nbk; kq += NT / 32) {
         const Real* urow = M + (size_t)steprow[kb + kq] * pitch;
         Real acc = Real(0);
         for (int q = ke + lane; q < T; q += 32) acc += urow[q] * xs[q];
@@ -1279,7 +1281,7 @@ lsolve_blk(const int* __restrict__ Arp, const int* __restrict__ Acol,
       __syncthreads();
     }
     const bool sing = s_sing != 0;
-    for (int p = t; p < T; p += LK_THREADS)
+    for (int p = t; p < T; p += NT)
       Zval[base + p + (p >= d ? 1 : 0)] = sing ? 0.0 : (double)xs[p];
     if (t == 0) {
       Zval[base + d] = 1.0;
@@ -1581,25 +1583,30 @@ static Real* launch_blocked(const Csr& Ahat, const VT* vals, const int* Zrp, con
                             int ncls, int* ticket, double* Zval, unsigned long long* nsing,
                             int pitch, int nsys, cudaStream_t s) {
   const int nbw = blk_nb<Real>(pitch);
+  const bool small = pitch <= LK_SMALL_PITCH && nbw == 32;
+  const int nt = small ? 128 : 256;
   const size_t smem = blk_smem<Real>(pitch, nbw);
-  auto kernel = nbw == 32 ? lsolve_blk<Real, VT, 32> : lsolve_blk<Real, VT, 16>;
-  once_per_device((const void*)lsolve_blk<Real, VT, 32>, [] {
-    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_blk<Real, VT, 32>,
+  auto kernel = small ? lsolve_blk<Real, VT, 32, 128>
+                      : nbw == 32 ? lsolve_blk<Real, VT, 32, 256> : lsolve_blk<Real, VT, 16, 256>;
+  once_per_device((const void*)lsolve_blk<Real, VT, 32, 256>, [] {
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_blk<Real, VT, 32, 128>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LK_SMEM_MAX));
-    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_blk<Real, VT, 16>,
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_blk<Real, VT, 32, 256>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LK_SMEM_MAX));
+    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_blk<Real, VT, 16, 256>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LK_SMEM_MAX));
   });
   int dev = 0, sms = 0, per_sm = 0;
   CLAIR_CUDA(cudaGetDevice(&dev));
   CLAIR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  CLAIR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, LK_THREADS, smem));
+  CLAIR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, smem));
   const size_t tile = (size_t)pitch * pitch * sizeof(Real);
   const int grid = (int)std::max<long long>(
       1, std::min<long long>({(long long)nsys, (long long)std::max(per_sm, 1) * sms,
                               (long long)(LB_BUDGET / tile)}));
   Real* tiles = dalloc<Real>((size_t)grid * pitch * pitch, s);
-  kernel<<<grid, LK_THREADS, smem, s>>>(Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, cls, ccount,
-                                        cls_stride, ncls, ticket, Zval, nsing, tiles, pitch); ::clair::count_launch();
+  kernel<<<grid, nt, smem, s>>>(Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, cls, ccount,
+                                cls_stride, ncls, ticket, Zval, nsing, tiles, pitch); ::clair::count_launch();
   CLAIR_LAUNCHED();
   return tiles;
 }
@@ -1658,7 +1665,8 @@ template <class Real, class VT>
 static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const int* Zcol,
                           const int* cpts, const int* lists, const int* counts_h, int nc,
                           double* Zval, unsigned long long* nsing, cudaStream_t s,
-                          bool big_scratch_forbidden = false, int first_bucket = 0) {
+                          bool big_scratch_forbidden = false, int first_bucket = 0,
+                          const int* counts_dev = nullptr) {
   // the shared-memory limits above 48 KB are per-device function attributes
   constexpr int TMED = sizeof(Real) == 8 ? LS_TMED64 : LS_TMED32;
   once_per_device((const void*)lsolve_cta<Real, VT, 128>, [] {
@@ -1668,9 +1676,6 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
     CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, VT, 128>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)cta_smem<Real, 128>()));
-    CLAIR_CUDA(cudaFuncSetAttribute(lsolve_cta<Real, VT, TMED>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)cta_smem<Real, TMED>()));
     CLAIR_CUDA(cudaFuncSetAttribute(lsolve_big<Real, VT>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)big_smem<Real>(LS_TBIG)));
@@ -1693,9 +1698,16 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
   if (counts_h[4])
     lsolve_cta<Real, VT, 128><<<counts_h[4], 128, cta_smem<Real, 128>(), s>>>(
         Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 4LL * nc, Zval, nsing); ::clair::count_launch();
+  Real* b5_tiles = nullptr;
+  int* b5_ticket = nullptr;
   if (counts_h[5] && first_bucket <= 5) {
-    lsolve_cta<Real, VT, TMED><<<counts_h[5], TMED, cta_smem<Real, TMED>(), s>>>(
-        Ahat.rowptr, Ahat.col, vals, Zrp, Zcol, cpts, lists + 5LL * nc, Zval, nsing); ::clair::count_launch();
+    CLAIR_REQUIRE(!big_scratch_forbidden && counts_dev, CLAIR_ERR_CAPACITY,
+                  "%d local systems larger than 128 unknowns need a tile buffer", counts_h[5]);
+    b5_ticket = dalloc<int>(1, s);
+    CLAIR_CUDA(cudaMemsetAsync(b5_ticket, 0, sizeof(int), s));
+    b5_tiles = launch_blocked<Real, VT>(Ahat, vals, Zrp, Zcol, cpts, lists + 5LL * nc,
+                                        counts_dev + 5, 0, 1, b5_ticket, Zval, nsing,
+                                        ceil_div(TMED, 32) * 32, counts_h[5], s);
   }
   if (counts_h[6]) {
     CLAIR_REQUIRE(!big_scratch_forbidden, CLAIR_ERR_CAPACITY,
@@ -1722,6 +1734,8 @@ static void launch_solves(const Csr& Ahat, const VT* vals, const int* Zrp, const
     dfree(cls, s);
     dfree(ccount, s);
   }
+  dfree(b5_tiles, s);
+  dfree(b5_ticket, s);
   CLAIR_LAUNCHED();
 }
 
@@ -1954,7 +1968,8 @@ void local_solves_multi(const SideIn* sides, int nsides, const int* cpts, int pr
         for (int q = 0; q < nsides; ++q) {
           const SideIn& S = sides[q];
           launch_solves<Real, VT>(*S.Ahat, vals[q], S.Zrp, S.Zcol, cpts, lists[q], counts_h[q],
-                                  S.nc, S.Zval, nsing, ls[q], false, /*first_bucket=*/4);
+                                  S.nc, S.Zval, nsing, ls[q], false, /*first_bucket=*/4,
+                                  counts + q * (LS_BUCKETS + 2));
         }
       } catch (...) {
         join_all();
