@@ -42,7 +42,7 @@ MEASURED_TRAFFIC = {
         # every local-solve launch (lsolve_persist and lsolve_cta), scaled by the ratio of
         # algorithmic bytes (530.9 MB / 132.1 MB = 4.02) to 1024^2
         "bytes": 80.8e6 * (530854884.0 / 132096084.0),
-        "source_sha256": "8fe20bcf8b258ae30f79ff57c99e2dc82b8ec02774a9b279264d057b292a191e",
+        "source_sha256": "43e1cdca0215f17a021f9d87110d9d0100555a966049681d0b97a1d8ae609757",
         "capture": "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
                    "--clock-control none -k regex:lsolve_ python bench.py --nside 512 --steps 1 "
                    "--warmup 1 --fp64-steps 0 --no-e2e --no-cpu-baseline --no-errors "
