@@ -29,12 +29,13 @@ def _levels(scale):
 
 
 def test_phase_bytes_scale_with_the_level_sizes():
-    one, two = bench.phase_bytes(_levels(1)), bench.phase_bytes(_levels(2))
+    one, two, three = (bench.phase_bytes(_levels(c)) for c in (1, 2, 3))
     assert set(one) == {"split", "pattern", "weight", "smooth", "galerkin"}
     for k in one:
         assert one[k] > 0
-        # every term is linear in the sizes, up to the row pointers' constant 4 bytes
-        assert abs(two[k] - 2 * one[k]) <= 64, k
+        # every term is affine in the sizes (the row pointers' n + 1 entries)
+        assert three[k] - two[k] == two[k] - one[k], k
+        assert two[k] > one[k], k
 
 
 def test_levels_without_transfers_cost_nothing():
