@@ -385,7 +385,7 @@ def run_clair(args):
               "traffic_scope": "per step, all local-solve launches (ncu DRAM read + write), "
                                "measured at 512^2 and scaled by algorithmic bytes",
               "algorithmic_bytes": st.lsolve_min_bytes,
-              "kernel": "lsolve_persist / lsolve_cta / lsolve_big (FP32 batched local LU)",
+              "kernel": "lsolve_persist / lsolve_cta / lsolve_blk (FP32 batched local LU)",
               "share_of_step": phases["local_solve"] / mixed["ms"]}
     lsolve["frac"] = lsolve["achieved"] / lsolve["peak"]
     hbm = pk.get("hbm_gbs", PEAK_FALLBACK["hbm_gbs"])
